@@ -1,0 +1,311 @@
+"""Benchmark: sweep grind time of the unstructured S_N transport sweep on GB300.
+
+One "step" is one source iteration: source update, the persistent sweep of
+every direction, the phi reduction, and the FP64 stopping test.  The default
+workload is the corner-source box: 48^3 jittered hexes Kuhn-split into
+663,552 tetrahedra, 192 directions (12 polar x 16 azimuthal), 64 groups, FP32
+local solves with FP64 phi/residual.  The metric is grind time: nanoseconds
+per (cell, direction, group) unit; lower is better.
+
+Prints one JSON line (rank 0).  With torchrun, N ranks run N independent
+replicas (the path does not shard across GPUs) and the slowest rank's time
+is reported; `value` counts all ranks' units.
+
+--impl reference times the CPU oracle (the plain FP64 program) on a bounded
+sample of the same workload, on this machine's host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "sweep grind time ns/(cell·dir·group) and time-to-1e-6 vs plain FP64 GPU"
+UNIT = "ns/(cell·dir·group)"
+L2_BYTES = 129 * 1024 * 1024
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.file = None
+
+    def start(self):
+        try:
+            self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.file, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.file.flush()
+        self.file.seek(0)
+        rows = [r.split(",") for r in self.file.read().strip().splitlines() if r.strip()]
+        os.unlink(self.file.name)
+        sm, smax, reasons = [], 0.0, set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                smax = max(smax, float(r[2]))
+                for k, n in enumerate(names):
+                    if r[5 + k].strip().lower() == "active":
+                        reasons.add(n)
+            except (ValueError, IndexError):
+                continue
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def _barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def _max_over_ranks(world, x):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if dist.get_backend() == "nccl" else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def cpu_oracle_sample(cfg, n_dirs=None, threads=None):
+    """Oracle (plain FP64 CPU) grind time on a bounded sample: `n_dirs` directions of the
+    workload's quadrature (all cells, all groups), one source update + sweep."""
+    import oracle
+    threads = threads or os.cpu_count() or 1
+    n_dirs = n_dirs or threads
+    om, w = oracle.product_quadrature(cfg["n_polar"], cfg["n_azimuthal"])
+    D = om.shape[0]
+    idx = np.linspace(0, D - 1, n_dirs).round().astype(int)
+    P = oracle.Problem(cfg, omega=om[idx], w=w[idx])
+    phi = np.random.default_rng(0).uniform(0.0, 1.0, (P.C, P.G, 4))
+    t0 = time.perf_counter()
+    q = P.source(phi)
+    _, _, used = P.sweep(q, threads=threads)
+    dt = time.perf_counter() - t0
+    units = P.C * P.G * n_dirs
+    return {"value": dt / units * 1e9, "unit": UNIT, "cores": used, "kind": "oracle",
+            "sample": f"{n_dirs} of {D} directions x {P.C} cells x {P.G} groups, one source update + sweep, "
+                      f"{dt:.1f} s wall on {used} threads"}
+
+
+def run_reference(args):
+    world, rank, _ = _dist()
+    if rank != 0:
+        return
+    cfg = W.CONFIGS[args.config]()
+    threads = os.cpu_count() or 1
+    # warm-up steps (untimed), then timed steps; each step is a bounded sample
+    for _ in range(args.warmup):
+        cpu_oracle_sample(cfg, n_dirs=max(1, threads // 4), threads=threads)
+    vals = []
+    t0 = time.perf_counter()
+    last = None
+    for _ in range(args.steps):
+        last = cpu_oracle_sample(cfg, n_dirs=threads, threads=threads)
+        vals.append(last["value"])
+    wall = time.perf_counter() - t0
+    v = float(np.mean(vals))
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": wall / max(args.steps, 1) * 1e3,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": cfg["name"], "cells": len(cfg["tets"]),
+                       "directions": cfg["n_polar"] * cfg["n_azimuthal"], "groups": cfg["n_groups"]},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": last["cores"], "kind": "oracle",
+                             "sample": last["sample"]},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+
+    import paper_2510_11513_gb300 as tf
+
+    world, rank, local = _dist()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    cfg = W.CONFIGS[args.config]()
+    prec = tf.TF_FP64 if args.precision == "fp64" else tf.TF_FP32
+    t_setup = time.perf_counter()
+    prob = tf.Problem.from_config(cfg, precision=prec, device=local, cells_per_task=args.cells_per_task,
+                                  warps_per_cta=args.warps_per_cta)
+    t_setup = time.perf_counter() - t_setup
+    C, G, D = prob.n_cells, prob.n_groups, prob.n_dirs
+    units = prob.n_units
+    stream = torch.cuda.current_stream(dev)
+    phi = torch.zeros((C, G, 4), dtype=torch.float64, device=dev)
+    # warm-up: W source iterations from zero
+    prob.source_iterate(phi, 0.0, args.warmup, stream=stream)
+    st0 = prob.stats()
+    clocks = ClockSampler(local)
+    clocks.start()
+    _barrier(world)
+    torch.cuda.synchronize(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    res = prob.source_iterate(phi, 0.0, args.steps, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    _barrier(world)
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    ms = _max_over_ranks(world, ms)
+    st1 = prob.stats()
+    assert res["iterations"] == args.steps
+    ms_per_step = ms / args.steps
+    grind = ms_per_step * 1e6 / units  # ns per unit (per GPU)
+    value = grind / world  # whole job: all ranks' units over the same wall time
+    sweep_s = (st1["cum_sweep_event_seconds"] - st0["cum_sweep_event_seconds"]) / args.steps
+    phi_s = (st1["cum_phi_event_seconds"] - st0["cum_phi_event_seconds"]) / args.steps
+    src_s = (st1["cum_source_event_seconds"] - st0["cum_source_event_seconds"]) / args.steps
+    s = 4 if prec == tf.TF_FP32 else 8
+    # algorithmic bytes of the sweep kernel per unit: q (4 s), psi store (4 s), and the
+    # cell record + cell-list entry once per (cell, direction), amortised over G
+    geo = 128 if prec == tf.TF_FP32 else 256
+    b_unit = 8 * s + (geo + 4) / G
+    peak, peak_kind = _peaks()
+    achieved = b_unit * units / sweep_s / 1e9
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32" if prec == tf.TF_FP32 else "f64", "data": "synthetic",
+            "config": {"workload": cfg["name"], "cells": C, "directions": D, "groups": G,
+                       "units_per_step": units, "precision": args.precision, "phi_accumulate": "fp32-pair->fp64",
+                       "l2": "inputs larger than L2 (psi store %.1f GB)" % (units * 4 * s / 1e9),
+                       "parallelism": f"replicas{world}", "setup_s": round(t_setup, 2)},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None, "kernel": "sweep_kernel",
+                         "bytes_per_unit": b_unit, "peak_kind": peak_kind},
+            "breakdown_ms": {"source": src_s * 1e3, "sweep": sweep_s * 1e3, "phi": phi_s * 1e3,
+                             "other": ms_per_step - (src_s + sweep_s + phi_s) * 1e3},
+            "scheduling": {"n_tasks": st1["n_tasks"], "cells_per_task": st1["cells_per_task"],
+                           "max_level": st1["max_level"], "grid_ctas": st1["grid_ctas"],
+                           "warps_per_cta": st1["warps_per_cta"], "mean_ready": st1["mean_ready"],
+                           "wait_frac": st1["wait_seconds"] / max(st1["wait_seconds"] + st1["busy_seconds"], 1e-30),
+                           "n_chunks": st1["n_chunks"]},
+            "gpu_launches": int((st1["launches_per_step"] + 3) * args.steps),
+            "clocks": clk}
+    # end to end: tf_sweep with pinned host buffers (H2D of phi_in, D2H of phi_out inside)
+    if not args.no_e2e:
+        hin = torch.zeros((C, G, 4), dtype=torch.float64).pin_memory()
+        hin.copy_(phi.cpu())
+        hout = torch.zeros_like(hin).pin_memory()
+        prob.sweep(hin, hout, stream=stream)
+        torch.cuda.synchronize(dev)
+        _barrier(world)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            prob.sweep(hin, hout, stream=stream)
+            hin, hout = hout, hin
+        torch.cuda.synchronize(dev)
+        _barrier(world)
+        e2e_ms = _max_over_ranks(world, (time.perf_counter() - t0) * 1e3) / args.steps
+        nbytes = C * G * 4 * 8
+        line["e2e"] = {"value": e2e_ms * 1e6 / units / world, "unit": UNIT, "h2d_bytes_per_step": nbytes,
+                       "d2h_bytes_per_step": nbytes, "ms_per_step": e2e_ms,
+                       "call": "tf_sweep(host pinned phi_in, host pinned phi_out)"}
+    if args.fp64_compare and prec == tf.TF_FP32:
+        del prob
+        torch.cuda.synchronize(dev)
+        p64 = tf.Problem.from_config(cfg, precision=tf.TF_FP64, device=local)
+        phi64 = torch.zeros((C, G, 4), dtype=torch.float64, device=dev)
+        p64.source_iterate(phi64, 0.0, 1, stream=stream)
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        p64.source_iterate(phi64, 0.0, args.fp64_steps, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms64 = e0.elapsed_time(e1) / args.fp64_steps
+        line["fp64_plain_gpu"] = {"ms_per_step": ms64, "grind": ms64 * 1e6 / units, "unit": UNIT,
+                                  "fp32_speedup": ms64 / ms_per_step, "n_chunks": p64.stats()["n_chunks"]}
+        del p64
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_oracle_sample(cfg)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default="corner_source", choices=sorted(W.CONFIGS))
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--cells-per-task", type=int, default=0)
+    ap.add_argument("--warps-per-cta", type=int, default=0)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--fp64-compare", action="store_true")
+    ap.add_argument("--fp64-steps", type=int, default=2)
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)  # at least 3 untimed warm-up steps
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,220 @@
+/*
+ * tfsweep — unstructured S_N transport sweep on one GB300 (sm_103a).
+ *
+ * C ABI of the library.  Every call returns a tf_status; no exception or C++
+ * type crosses this boundary.  Handles are opaque and reference counted: a
+ * problem keeps its mesh and quadrature alive.  Handles are not thread safe;
+ * use one handle from one host thread at a time.
+ *
+ * The operations follow the problem statement of Elwood et al., "An
+ * Asynchronous Many-Task Algorithm for Unstructured S_N Transport on Shared
+ * Memory Systems":
+ *   - Eq. (1): steady multigroup transport with a total cross section, an
+ *     external source and (here isotropic) scattering;
+ *   - Eq. (2): the scalar flux as the quadrature sum phi = sum_a w_a psi_a;
+ *   - Sec. 2.1 / Algorithm 1: the sweep — each direction's cells are solved
+ *     in dependency order, every group inside one element visit, with the
+ *     upwind face fluxes handed to downwind cells;
+ *   - Eq. (3): the integrated flux per group and in total.
+ * Spatial discretisation: upwind discontinuous Galerkin with linear basis
+ * functions on tetrahedra (4 nodal unknowns per cell, group and direction).
+ *
+ * Memory conventions:
+ *   - creation inputs are host arrays; they are copied, the caller keeps them;
+ *   - phi arrays passed to tf_sweep / tf_source_iterate are caller-owned,
+ *     FP64, layout [n_cells][n_groups][4] (node i of cell c is local vertex i
+ *     of tets[c]); they may live in device memory or in host memory (host
+ *     buffers are copied in and out inside the call);
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream).
+ * Device-side failures (a device wait that ran out, a bounds flag) are read
+ * back when the call synchronises and returned as its status; the handle
+ * stays usable.
+ */
+#ifndef TFSWEEP_H
+#define TFSWEEP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tf_obj *tf_handle;
+
+typedef enum {
+    TF_OK = 0,
+    TF_ERR_ARG = 1,            /* bad argument: NULL pointer, size out of range, wrong handle kind */
+    TF_ERR_MESH = 2,           /* inverted/degenerate tetrahedron, bad vertex index, face shared by >2 cells */
+    TF_ERR_CYCLE = 3,          /* a direction's cell dependency graph has a cycle */
+    TF_ERR_CUDA = 4,           /* a CUDA runtime call failed (message in tf_last_error()) */
+    TF_ERR_NOMEM = 5,          /* host or device allocation failed */
+    TF_ERR_TIMEOUT = 6,        /* a device wait exceeded tf_options.wait_limit_s; the kernel returned */
+    TF_ERR_NOT_CONVERGED = 7,  /* tf_source_iterate reached max_iters above tol (phi is still returned) */
+    TF_ERR_DEVICE = 8          /* the device reported an inconsistent task graph (a bounds flag) */
+} tf_status;
+
+typedef enum { TF_FP32 = 0, TF_FP64 = 1 } tf_precision;
+
+/* How the sweep accumulates phi = sum_a w_a psi_a in FP32 mode.  In FP64 mode
+ * the accumulation is always plain FP64 additions. */
+typedef enum {
+    TF_PHI_PAIR = 0,  /* error-free FP32 pair (TwoProd/TwoSum) accumulation, rounded once to FP64 */
+    TF_PHI_DADD = 1   /* one FP64 multiply-add per direction and node */
+} tf_phi_accumulate;
+
+typedef struct {
+    int32_t precision;       /* tf_precision: arithmetic of local solves and psi storage (default TF_FP32) */
+    int32_t device;          /* CUDA device ordinal (default 0) */
+    int32_t cells_per_task;  /* cells of one t-level grouped into one task; 0 = automatic */
+    int32_t dir_chunk;       /* directions swept per persistent launch; 0 = as many as the memory budget allows */
+    int32_t warps_per_cta;   /* persistent kernel CTA size in warps; 0 = automatic */
+    int32_t ctas_per_sm;     /* persistent CTAs per SM; 0 = as many as are resident */
+    double wait_limit_s;     /* a device wait gives up after this many seconds (default 10) */
+    int32_t phi_accumulate;  /* tf_phi_accumulate (default TF_PHI_PAIR) */
+    int32_t inject_stall;    /* fault injection for tests: 1 = seed no task, so every device wait runs out */
+    double psi_budget_gb;    /* device memory allowed for the angular-flux store; 0 = 80 % of free memory */
+    int32_t task_order;      /* 0 = FIFO ready queue, seeds longest-critical-path first */
+    int32_t reserved_i[7];
+    double reserved_d[4];
+} tf_options;
+
+/* Fills *opt with the defaults above. */
+void tf_options_default(tf_options *opt);
+
+/* Per-problem result of tf_source_iterate. */
+typedef struct {
+    int32_t iterations;        /* sweeps performed */
+    int32_t converged;         /* 1 if the stopping test fell below tol */
+    double residual;           /* last max relative change of phi (floor 1e-10 x per-group max) */
+    double integrated_total;   /* Eq. (3): sum over groups of the integrated flux of the final phi */
+    double *integrated_flux;   /* caller host array [n_groups] or NULL: per-group integral of phi over space */
+    double *residual_history;  /* caller host array [max_iters] or NULL: residual after each sweep */
+} tf_iter_info;
+
+/* Scheduling statistics of the last sweep of a problem (for measurement). */
+typedef struct {
+    int64_t n_tasks;           /* (cell block, direction) tasks per sweep */
+    int64_t n_units;           /* cells x directions x groups */
+    int32_t n_dirs;
+    int32_t max_level;         /* longest dependency chain over directions (t-levels - 1) */
+    int32_t n_chunks;          /* persistent launches per sweep */
+    int32_t grid_ctas;         /* persistent CTAs per launch */
+    int32_t warps_per_cta;
+    int32_t cells_per_task;
+    int64_t tasks_executed;    /* counted on the device in the last sweep */
+    int64_t wait_polls;        /* device polls of an empty queue slot in the last sweep */
+    double wait_seconds;       /* summed over warps: time spent waiting for a ready task */
+    double busy_seconds;       /* summed over warps: time spent executing tasks */
+    double kernel_seconds;     /* first warp start to last warp end, summed over launches */
+    double mean_ready;         /* mean ready-queue depth sampled at pops */
+    /* CUDA-event times on the caller's stream (seconds): last transport step, and summed
+     * over all steps since the problem was created (cum_steps of them) */
+    double source_event_seconds, sweep_event_seconds, phi_event_seconds;
+    double cum_source_event_seconds, cum_sweep_event_seconds, cum_phi_event_seconds;
+    int64_t cum_steps;
+    int64_t launches_per_step;  /* kernels this library launches per transport step */
+    int32_t reserved_i[6];
+    double reserved_d[6];
+} tf_stats;
+
+/* Mesh of tetrahedra.  xyz: host [n_vertices][3] FP64; tets: host [n_cells][4]
+ * vertex indices.  Tetrahedra must be positively oriented (det of the edge
+ * vectors x1-x0, x2-x0, x3-x0 > 0) and conforming (a face is shared by at most
+ * two cells).  Computes volumes, basis gradients (Table tab:arrays' f_i df_j/dx
+ * ingredients), area-weighted outward face normals and face neighbours.
+ * Host-only: no CUDA call.  Errors: TF_ERR_ARG, TF_ERR_MESH, TF_ERR_NOMEM. */
+tf_status tf_mesh_create(int64_t n_vertices, const double *xyz, int64_t n_cells, const int32_t *tets,
+                         tf_handle *out);
+
+/* Angular quadrature.  Either a product rule (omega == NULL): n_polar
+ * Gauss-Legendre cosines times n_azimuthal azimuths (k + 1/2) 2 pi / n_azimuthal,
+ * weights summing to 4 pi, direction index a = polar * n_azimuthal + azimuth;
+ * or explicit directions (omega != NULL): n_dirs unit vectors omega [n_dirs][3]
+ * and weights w [n_dirs] (host FP64).  Directions are the S_N set of Eq. (2).
+ * Host-only.  Errors: TF_ERR_ARG. */
+tf_status tf_quadrature_create(int32_t n_polar, int32_t n_azimuthal, int32_t n_dirs, const double *omega,
+                               const double *w, tf_handle *out);
+
+/* Transport problem: mesh + quadrature + n_groups energy groups + materials
+ * (Eq. (1)).  Host inputs, copied to the device selected by opt->device:
+ *   cell_material [n_cells] in [0, n_materials);
+ *   sigma_t [n_materials][n_groups] total cross section (> 0);
+ *   sigma_s [n_materials][n_groups][n_groups], element [m][g_from][g_to];
+ *   Q [n_cells][n_groups][4] total isotropic volumetric source at the nodes
+ *     (the angular source per steradian is (Q + sum_g' sigma_s phi_g') / 4 pi);
+ *   S1 [n_cells][n_groups][3] or NULL: adds the angular source Omega . S1
+ *     (constant per cell; used by manufactured-solution tests);
+ *   psi_inflow [n_vertices][n_groups] or NULL: isotropic inflow prescribed at
+ *     boundary vertices; NULL means vacuum boundaries.
+ * Builds, per direction, the face classification (inflow iff Omega.N_f <
+ * -1e-12 |N_f|), t-levels (Sec. 2.1), cell-block tasks and their dependency
+ * counts (Sec. 3.5), and allocates the device state.  opt may be NULL.
+ * Errors: TF_ERR_ARG, TF_ERR_CYCLE, TF_ERR_CUDA, TF_ERR_NOMEM. */
+tf_status tf_problem_create(tf_handle mesh, tf_handle quad, int32_t n_groups, int32_t n_materials,
+                            const int32_t *cell_material, const double *sigma_t, const double *sigma_s,
+                            const double *Q, const double *S1, const double *psi_inflow, const tf_options *opt,
+                            tf_handle *out);
+
+/* One transport step per problem: source update q = (Q + sum_g' sigma_s phi_in)/4 pi,
+ * a sweep of every direction (Algorithm 1: dependency counters released by
+ * atomics, ready (cell block, direction) tasks pulled from a device queue),
+ * and phi_out = sum_a w_a psi_a (Eq. 2).  phi_in / phi_out: [n] arrays of FP64
+ * [n_cells][n_groups][4] buffers (device or host); phi_in[k] may equal
+ * phi_out[k].  Synchronises `stream` before returning.
+ * Errors: TF_ERR_ARG, TF_ERR_CUDA, TF_ERR_TIMEOUT, TF_ERR_DEVICE. */
+tf_status tf_sweep(const tf_handle *problems, int32_t n, const double *const *phi_in, double *const *phi_out,
+                   void *stream);
+
+/* Source iteration (group-Jacobi): repeat tf_sweep until the stopping test
+ * max |phi_new - phi_old| / max(|phi_new|, 1e-10 x max over the group of |phi_new|)
+ * falls below tol (evaluated in FP64 on the device) or max_iters sweeps.
+ * phi[k]: in = initial flux (NULL entry = zero start), out = final flux
+ * (a NULL entry is not allowed for the output: pass a buffer).  info: [n] or
+ * NULL.  Returns TF_ERR_NOT_CONVERGED if any problem stopped at max_iters.
+ * Errors: as tf_sweep, plus TF_ERR_NOT_CONVERGED. */
+tf_status tf_source_iterate(const tf_handle *problems, int32_t n, double tol, int32_t max_iters,
+                            double *const *phi, tf_iter_info *info, void *stream);
+
+/* Releases a handle (mesh, quadrature or problem).  Objects live until the last
+ * problem that uses them is destroyed.  NULL is accepted. */
+tf_status tf_destroy(tf_handle h);
+
+/* ---------------------------------------------------------------- inspection */
+
+/* Mesh geometry as computed by tf_mesh_create (host outputs; any may be NULL):
+ * vol [n_cells]; normal [n_cells][4][3] area-weighted outward normal of the face
+ * opposite local vertex f; nbr [n_cells][4] (-1 = boundary); nbr_node
+ * [n_cells][4][4]: local index, in the neighbour across face f, of local vertex
+ * i of the cell (-1 for i == f or a boundary face). */
+tf_status tf_mesh_geometry(tf_handle mesh, int64_t *n_cells, int64_t *n_vertices, double *vol, double *normal,
+                           int32_t *nbr, int32_t *nbr_node);
+
+/* Directions and weights of a quadrature (host outputs; any may be NULL). */
+tf_status tf_quadrature_get(tf_handle quad, int32_t *n_dirs, double *omega, double *w);
+
+/* Host-only: face classification and t-levels for every direction (Sec. 2.1
+ * buckets).  inflow [n_dirs][n_cells]: bit f set iff face f is inflow;
+ * level [n_dirs][n_cells].  Either may be NULL.  Errors: TF_ERR_CYCLE. */
+tf_status tf_graph_levels(tf_handle mesh, tf_handle quad, uint8_t *inflow, int32_t *level);
+
+/* Copies the angular flux of direction `dir` from the last sweep of `problem`
+ * into out (device memory, [n_cells][n_groups][4] in the problem precision:
+ * float or double).  The direction must belong to the last direction chunk
+ * swept (with one chunk: any direction).  Errors: TF_ERR_ARG, TF_ERR_CUDA. */
+tf_status tf_problem_psi(tf_handle problem, int32_t dir, void *out, void *stream);
+
+/* Scheduling statistics of the problem's last sweep. */
+tf_status tf_problem_stats(tf_handle problem, tf_stats *out);
+
+/* Static description of a status code. */
+const char *tf_status_string(tf_status s);
+
+/* Detail of the last error on the calling thread ("" if none). */
+const char *tf_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TFSWEEP_H */

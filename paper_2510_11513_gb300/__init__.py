@@ -1,0 +1,16 @@
+"""tfsweep: the unstructured S_N transport sweep (upwind DG on tetrahedra,
+persistent device-queue sweep) for one GB300 GPU.
+
+The compute lives in the native library built from `csrc/` (CUDA for
+sm_103a plus host C++) behind the C ABI of `include/tfsweep.h`; this package
+only builds, loads and calls it.  There is no CPU or Python fallback: if the
+library cannot be built or loaded, `load()` raises.
+"""
+from .tfsweep import (TF_ERR_ARG, TF_ERR_CUDA, TF_ERR_CYCLE, TF_ERR_DEVICE, TF_ERR_MESH, TF_ERR_NOMEM,  # noqa: F401
+                      TF_ERR_NOT_CONVERGED, TF_ERR_TIMEOUT, TF_FP32, TF_FP64, TF_OK, TF_PHI_DADD, TF_PHI_PAIR,
+                      Mesh, Problem, Quadrature, TfError, library_path, load, options, tf_destroy,
+                      tf_graph_levels, tf_mesh_create, tf_mesh_geometry, tf_problem_create, tf_problem_psi,
+                      tf_problem_stats, tf_quadrature_create, tf_quadrature_get, tf_source_iterate, tf_sweep)
+
+__all__ = [n for n in dir() if n.startswith(("tf_", "TF_")) or n in ("Mesh", "Problem", "Quadrature", "TfError",
+                                                                       "load", "library_path", "options")]

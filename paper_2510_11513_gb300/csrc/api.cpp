@@ -1,0 +1,283 @@
+// The C ABI: handle management, argument validation, error reporting.
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "tf_internal.h"
+
+namespace tf {
+
+namespace {
+thread_local std::string g_last_error;
+}
+
+void set_error(const std::string &msg) { g_last_error = msg; }
+
+tf_status fail(tf_status s, const std::string &msg)
+{
+    g_last_error = msg;
+    return s;
+}
+
+void retain(Object *o)
+{
+    if (o) o->refs.fetch_add(1);
+}
+
+void release(Object *o)
+{
+    if (o && o->refs.fetch_sub(1) == 1) delete o;
+}
+
+Problem::~Problem()
+{
+    device_destroy(*this);
+    release(mesh);
+    release(quad);
+}
+
+namespace {
+
+template <class T>
+T *as(tf_handle h, Kind k)
+{
+    auto *o = reinterpret_cast<Object *>(h);
+    if (!o || o->kind != k) return nullptr;
+    return static_cast<T *>(o);
+}
+
+}  // namespace
+
+}  // namespace tf
+
+using namespace tf;
+
+extern "C" {
+
+void tf_options_default(tf_options *opt)
+{
+    if (!opt) return;
+    std::memset(opt, 0, sizeof(*opt));
+    opt->precision = TF_FP32;
+    opt->device = 0;
+    opt->wait_limit_s = 10.0;
+    opt->phi_accumulate = TF_PHI_PAIR;
+}
+
+const char *tf_status_string(tf_status s)
+{
+    switch (s) {
+    case TF_OK: return "ok";
+    case TF_ERR_ARG: return "invalid argument";
+    case TF_ERR_MESH: return "invalid mesh";
+    case TF_ERR_CYCLE: return "dependency cycle in a sweep graph";
+    case TF_ERR_CUDA: return "CUDA runtime error";
+    case TF_ERR_NOMEM: return "out of memory";
+    case TF_ERR_TIMEOUT: return "device wait timed out";
+    case TF_ERR_NOT_CONVERGED: return "not converged";
+    case TF_ERR_DEVICE: return "device reported an inconsistent task graph";
+    }
+    return "unknown status";
+}
+
+const char *tf_last_error(void) { return g_last_error.c_str(); }
+
+tf_status tf_mesh_create(int64_t n_vertices, const double *xyz, int64_t n_cells, const int32_t *tets, tf_handle *out)
+{
+    if (!out) return fail(TF_ERR_ARG, "tf_mesh_create: out is NULL");
+    *out = nullptr;
+    if (n_vertices < 4 || n_cells < 1 || !xyz || !tets) return fail(TF_ERR_ARG, "tf_mesh_create: empty mesh or NULL array");
+    if (n_vertices >= (int64_t(1) << 31) || n_cells >= (int64_t(1) << 28))
+        return fail(TF_ERR_ARG, "tf_mesh_create: at most 2^31 - 1 vertices and 2^28 - 1 cells");
+    for (int64_t i = 0; i < 3 * n_vertices; ++i)
+        if (!std::isfinite(xyz[i])) return fail(TF_ERR_MESH, "tf_mesh_create: non-finite coordinate");
+    Mesh *m = new (std::nothrow) Mesh();
+    if (!m) return fail(TF_ERR_NOMEM, "tf_mesh_create: allocation failed");
+    tf_status s = build_mesh(n_vertices, xyz, n_cells, tets, *m);
+    if (s != TF_OK) {
+        delete m;
+        return s;
+    }
+    *out = reinterpret_cast<tf_handle>(static_cast<Object *>(m));
+    return TF_OK;
+}
+
+tf_status tf_quadrature_create(int32_t n_polar, int32_t n_azimuthal, int32_t n_dirs, const double *omega,
+                               const double *w, tf_handle *out)
+{
+    if (!out) return fail(TF_ERR_ARG, "tf_quadrature_create: out is NULL");
+    *out = nullptr;
+    Quad *q = new (std::nothrow) Quad();
+    if (!q) return fail(TF_ERR_NOMEM, "tf_quadrature_create: allocation failed");
+    if (omega) {
+        if (!w || n_dirs < 1 || n_dirs > 65535) {
+            delete q;
+            return fail(TF_ERR_ARG, "tf_quadrature_create: explicit set needs 1..65535 directions and weights");
+        }
+        q->D = n_dirs;
+        q->omega.assign(omega, omega + 3 * (size_t)n_dirs);
+        q->w.assign(w, w + n_dirs);
+        for (int32_t a = 0; a < n_dirs; ++a) {
+            const double *o = omega + 3 * a;
+            const double nn = o[0] * o[0] + o[1] * o[1] + o[2] * o[2];
+            if (!(std::fabs(nn - 1.0) < 1e-10) || !std::isfinite(w[a])) {
+                delete q;
+                return fail(TF_ERR_ARG, "tf_quadrature_create: direction " + std::to_string(a) + " is not a unit vector");
+            }
+        }
+    } else {
+        tf_status s = build_quadrature(n_polar, n_azimuthal, *q);
+        if (s != TF_OK) {
+            delete q;
+            return s;
+        }
+    }
+    *out = reinterpret_cast<tf_handle>(static_cast<Object *>(q));
+    return TF_OK;
+}
+
+tf_status tf_problem_create(tf_handle mesh, tf_handle quad, int32_t n_groups, int32_t n_materials,
+                            const int32_t *cell_material, const double *sigma_t, const double *sigma_s,
+                            const double *Q, const double *S1, const double *psi_inflow, const tf_options *opt,
+                            tf_handle *out)
+{
+    if (!out) return fail(TF_ERR_ARG, "tf_problem_create: out is NULL");
+    *out = nullptr;
+    Mesh *m = as<Mesh>(mesh, Kind::Mesh);
+    Quad *q = as<Quad>(quad, Kind::Quad);
+    if (!m || !q) return fail(TF_ERR_ARG, "tf_problem_create: mesh or quadrature handle invalid");
+    if (n_groups < 1 || n_groups > 1024 || n_materials < 1)
+        return fail(TF_ERR_ARG, "tf_problem_create: need 1 <= n_groups <= 1024 and n_materials >= 1");
+    if (!cell_material || !sigma_t || !sigma_s || !Q) return fail(TF_ERR_ARG, "tf_problem_create: NULL input array");
+    for (int64_t c = 0; c < m->nc; ++c)
+        if (cell_material[c] < 0 || cell_material[c] >= n_materials)
+            return fail(TF_ERR_ARG, "tf_problem_create: cell_material out of range at cell " + std::to_string(c));
+    for (int64_t i = 0; i < (int64_t)n_materials * n_groups; ++i)
+        if (!(sigma_t[i] >= 0.0) || !std::isfinite(sigma_t[i]))
+            return fail(TF_ERR_ARG, "tf_problem_create: sigma_t must be finite and >= 0");
+    Problem *p = new (std::nothrow) Problem();
+    if (!p) return fail(TF_ERR_NOMEM, "tf_problem_create: allocation failed");
+    tf_options_default(&p->opt);
+    if (opt) p->opt = *opt;
+    if (p->opt.precision != TF_FP32 && p->opt.precision != TF_FP64) {
+        delete p;
+        return fail(TF_ERR_ARG, "tf_problem_create: precision must be TF_FP32 or TF_FP64");
+    }
+    if (!(p->opt.wait_limit_s > 0.0)) p->opt.wait_limit_s = 10.0;
+    p->mesh = m;
+    p->quad = q;
+    retain(m);
+    retain(q);
+    p->G = n_groups;
+    p->M = n_materials;
+    p->has_S1 = S1 != nullptr;
+    p->has_inflow = psi_inflow != nullptr;
+    int32_t B = p->opt.cells_per_task;
+    if (B <= 0) B = std::max(2, std::min(64, 1024 / n_groups));
+    tf_status s = build_task_graph(*m, *q, B, p->graph);
+    if (s == TF_OK) s = device_create(*p, cell_material, sigma_t, sigma_s, Q, S1, psi_inflow);
+    if (s != TF_OK) {
+        release(p);
+        return s;
+    }
+    *out = reinterpret_cast<tf_handle>(static_cast<Object *>(p));
+    return TF_OK;
+}
+
+tf_status tf_sweep(const tf_handle *problems, int32_t n, const double *const *phi_in, double *const *phi_out,
+                   void *stream)
+{
+    if (!problems || n < 1 || !phi_in || !phi_out) return fail(TF_ERR_ARG, "tf_sweep: bad arguments");
+    for (int32_t k = 0; k < n; ++k) {
+        Problem *p = as<Problem>(problems[k], Kind::Problem);
+        if (!p || !phi_in[k] || !phi_out[k]) return fail(TF_ERR_ARG, "tf_sweep: bad problem handle or phi pointer");
+    }
+    for (int32_t k = 0; k < n; ++k) {
+        tf_status s = device_sweep(*as<Problem>(problems[k], Kind::Problem), phi_in[k], phi_out[k], stream);
+        if (s != TF_OK) return s;
+    }
+    return TF_OK;
+}
+
+tf_status tf_source_iterate(const tf_handle *problems, int32_t n, double tol, int32_t max_iters,
+                            double *const *phi, tf_iter_info *info, void *stream)
+{
+    if (!problems || n < 1 || !phi || max_iters < 1 || !(tol >= 0.0))
+        return fail(TF_ERR_ARG, "tf_source_iterate: bad arguments");
+    for (int32_t k = 0; k < n; ++k) {
+        if (!as<Problem>(problems[k], Kind::Problem) || !phi[k])
+            return fail(TF_ERR_ARG, "tf_source_iterate: bad problem handle or NULL phi buffer");
+    }
+    tf_status worst = TF_OK;
+    for (int32_t k = 0; k < n; ++k) {
+        tf_status s = device_iterate(*as<Problem>(problems[k], Kind::Problem), tol, max_iters, phi[k],
+                                     info ? info + k : nullptr, stream);
+        if (s == TF_ERR_NOT_CONVERGED) {
+            worst = s;
+            continue;
+        }
+        if (s != TF_OK) return s;
+    }
+    return worst;
+}
+
+tf_status tf_destroy(tf_handle h)
+{
+    auto *o = reinterpret_cast<Object *>(h);
+    if (!o) return TF_OK;
+    if (o->kind != Kind::Mesh && o->kind != Kind::Quad && o->kind != Kind::Problem)
+        return fail(TF_ERR_ARG, "tf_destroy: not a tfsweep handle");
+    release(o);
+    return TF_OK;
+}
+
+tf_status tf_mesh_geometry(tf_handle mesh, int64_t *n_cells, int64_t *n_vertices, double *vol, double *normal,
+                           int32_t *nbr, int32_t *nbr_node)
+{
+    Mesh *m = as<Mesh>(mesh, Kind::Mesh);
+    if (!m) return fail(TF_ERR_ARG, "tf_mesh_geometry: not a mesh handle");
+    if (n_cells) *n_cells = m->nc;
+    if (n_vertices) *n_vertices = m->nv;
+    if (vol) std::memcpy(vol, m->vol.data(), sizeof(double) * m->nc);
+    if (normal) std::memcpy(normal, m->normal.data(), sizeof(double) * 12 * m->nc);
+    if (nbr) std::memcpy(nbr, m->nbr.data(), sizeof(int32_t) * 4 * m->nc);
+    if (nbr_node)
+        for (int64_t i = 0; i < 16 * m->nc; ++i) nbr_node[i] = m->nbr_node[i];
+    return TF_OK;
+}
+
+tf_status tf_quadrature_get(tf_handle quad, int32_t *n_dirs, double *omega, double *w)
+{
+    Quad *q = as<Quad>(quad, Kind::Quad);
+    if (!q) return fail(TF_ERR_ARG, "tf_quadrature_get: not a quadrature handle");
+    if (n_dirs) *n_dirs = q->D;
+    if (omega) std::memcpy(omega, q->omega.data(), sizeof(double) * 3 * q->D);
+    if (w) std::memcpy(w, q->w.data(), sizeof(double) * q->D);
+    return TF_OK;
+}
+
+tf_status tf_graph_levels(tf_handle mesh, tf_handle quad, uint8_t *inflow, int32_t *level)
+{
+    Mesh *m = as<Mesh>(mesh, Kind::Mesh);
+    Quad *q = as<Quad>(quad, Kind::Quad);
+    if (!m || !q) return fail(TF_ERR_ARG, "tf_graph_levels: mesh or quadrature handle invalid");
+    return classify_and_level(*m, *q, inflow, level);
+}
+
+tf_status tf_problem_psi(tf_handle problem, int32_t dir, void *out, void *stream)
+{
+    Problem *p = as<Problem>(problem, Kind::Problem);
+    if (!p || !out) return fail(TF_ERR_ARG, "tf_problem_psi: bad handle or NULL output");
+    return device_psi(*p, dir, out, stream);
+}
+
+tf_status tf_problem_stats(tf_handle problem, tf_stats *out)
+{
+    Problem *p = as<Problem>(problem, Kind::Problem);
+    if (!p || !out) return fail(TF_ERR_ARG, "tf_problem_stats: bad handle or NULL output");
+    *out = p->stats;
+    return TF_OK;
+}
+
+}  // extern "C"

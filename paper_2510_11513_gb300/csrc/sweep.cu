@@ -1,0 +1,1195 @@
+// Device state and kernels of the S_N sweep (sm_103a).
+//
+// One transport step (tf_sweep) on the device:
+//   source_kernel   q = (Q + sum_g' sigma_s[g'->g] phi_g') / 4 pi          (Eq. (1) right-hand side)
+//   for each direction chunk:
+//     begin_kernel  new queue epoch, empty queue
+//     fill_kernel   dependency counters <- in-degrees; ready slots <- seed tasks
+//     sweep_kernel  persistent: warps pull ready (cell block, direction) tasks,
+//                   solve the 4x4 upwind-DG systems with lanes over groups,
+//                   store psi, and release downwind counters (Algorithm 1, Sec. 3.5)
+//     phi_kernel    phi (+)= sum_a w_a psi_a over the chunk                   (Eq. (2))
+// Source iteration adds stats_kernel (per-group max and integrated flux,
+// Eq. (3)) and residual_kernel (the FP64 stopping test).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "tf_internal.h"
+
+namespace tf {
+
+// ============================================================== device types
+struct alignas(32) double4a {
+    double x, y, z, w;
+};
+template <class T> struct Vec4;
+template <> struct Vec4<float> { using type = float4; };
+template <> struct Vec4<double> { using type = double4a; };
+template <class T> using V4 = typename Vec4<T>::type;
+
+// Per-cell geometry in the sweep precision.  g*: (V/4) d b_j / d{x,y,z} (the
+// f_i df_j/dx det J integrals, identical for every row i); n*: area-weighted
+// outward normal of face f; mv = V/20 (mass matrix scale); nn packs, for face
+// f and local vertex i != f, the neighbour-local index of that vertex in bits
+// 2*(4f+i) .. 2*(4f+i)+1.
+template <class T> struct alignas(16) CellGeo {
+    T gx[4], gy[4], gz[4];
+    T nx[4], ny[4], nz[4];
+    T mv;
+    int32_t mat;
+    uint32_t nn;
+    int32_t nbr[4];
+};
+static_assert(sizeof(CellGeo<float>) == 128, "float cell record must be one 128-byte line");
+static_assert(sizeof(CellGeo<double>) % 16 == 0, "double cell record must be 16-byte aligned");
+
+// Queue control block.  head/tail live on their own 128-byte lines.
+struct Ctrl {
+    unsigned long long head;  // next ticket to claim
+    unsigned long long pad0[15];
+    unsigned long long tail;  // next slot to fill
+    unsigned long long pad1[15];
+    unsigned int epoch;       // tag of the slots filled in the current launch
+    int error;                // first device error (TF_ERR_*), 0 if none
+    unsigned long long tasks_done;
+    unsigned long long polls;
+    unsigned long long wait_ns;
+    unsigned long long busy_ns;
+    unsigned long long t_first;  // earliest warp start (globaltimer)
+    unsigned long long t_last;   // latest warp end
+    unsigned long long depth_sum;
+    unsigned long long pops;
+    unsigned long long residual_bits;  // max residual as ordered bits of a non-negative double
+    unsigned long long kernel_ns;      // summed over chunks
+};
+
+// ============================================================== PTX helpers
+__device__ __forceinline__ unsigned long long globaltimer()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ unsigned long long ld_acquire(const unsigned long long *p)
+{
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release(unsigned long long *p, unsigned long long v)
+{
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ int atom_add_acq_rel(int *p, int v)
+{
+    int old;
+    asm volatile("atom.acq_rel.gpu.global.add.s32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+__device__ __forceinline__ int ld_volatile(const int *p) { return *(const volatile int *)p; }
+__device__ __forceinline__ unsigned long long ld_volatile(const unsigned long long *p)
+{
+    return *(const volatile unsigned long long *)p;
+}
+
+__device__ __forceinline__ float4 ld_ro(const float4 *p) { return __ldg(p); }
+__device__ __forceinline__ double4a ld_ro(const double4a *p)
+{
+    const double2 a = __ldg(reinterpret_cast<const double2 *>(p)), b = __ldg(reinterpret_cast<const double2 *>(p) + 1);
+    return {a.x, a.y, b.x, b.y};
+}
+// loads of psi written by other warps in the same launch: through L2, never a stale L1 line
+__device__ __forceinline__ float4 ld_l2(const float4 *p) { return __ldcg(p); }
+__device__ __forceinline__ double4a ld_l2(const double4a *p)
+{
+    const double2 a = __ldcg(reinterpret_cast<const double2 *>(p)), b = __ldcg(reinterpret_cast<const double2 *>(p) + 1);
+    return {a.x, a.y, b.x, b.y};
+}
+// streaming loads of the psi store in the phi reduction (read once, evict first)
+__device__ __forceinline__ float4 ld_stream(const float4 *p) { return __ldcs(p); }
+__device__ __forceinline__ double4a ld_stream(const double4a *p)
+{
+    const double2 a = __ldcs(reinterpret_cast<const double2 *>(p)), b = __ldcs(reinterpret_cast<const double2 *>(p) + 1);
+    return {a.x, a.y, b.x, b.y};
+}
+__device__ __forceinline__ void st_psi(float4 *p, float4 v) { *p = v; }
+__device__ __forceinline__ void st_psi(double4a *p, double4a v)
+{
+    reinterpret_cast<double2 *>(p)[0] = make_double2(v.x, v.y);
+    reinterpret_cast<double2 *>(p)[1] = make_double2(v.z, v.w);
+}
+
+template <class T> __device__ __forceinline__ T rcp(T x);
+template <> __device__ __forceinline__ float rcp<float>(float x) { return __frcp_rn(x); }
+template <> __device__ __forceinline__ double rcp<double>(double x) { return __drcp_rn(x); }
+
+template <class V> __device__ __forceinline__ auto comp(const V &v, int k) -> decltype(v.x)
+{
+    return k == 0 ? v.x : (k == 1 ? v.y : (k == 2 ? v.z : v.w));
+}
+
+// ============================================================== sweep kernel
+template <class T> struct SweepArgs {
+    const CellGeo<T> *geo;
+    const uint32_t *cells;      // (cell << 4) | inflow mask
+    const uint4 *task;          // {cell_begin, ncell | dir << 16, down_begin, ndown}
+    const uint32_t *down;       // downwind task ids
+    int *counters;              // dependency counters
+    unsigned long long *slots;  // ready queue, (epoch << 32) | task
+    Ctrl *ctrl;
+    const V4<T> *q;             // [C][G] angular source per steradian (nodal)
+    V4<T> *psi;                 // [Dc][C][G]
+    const T *sigma_t;           // [M][G]
+    const V4<T> *omega;         // [D] (x, y, z, w)
+    const V4<T> *S1;            // [C][G] or NULL
+    const T *psi_in;            // [nv][G] or NULL
+    const int4 *tets;           // [C] (only with psi_in)
+    int64_t C;
+    int32_t G;
+    int32_t dir_begin;          // first direction of the chunk
+    uint32_t task_begin, task_end;
+    unsigned long long n_tasks;  // tasks in the chunk
+    unsigned long long wait_limit_ns;
+};
+
+// Solve one 4x4 system by Gaussian elimination without pivoting: the
+// symmetric part of the upwind-DG matrix, (1/2) sum_f |Omega.N_f| M_f +
+// sigma_t M, is positive definite, so every pivot is positive.
+template <class T> __device__ __forceinline__ void solve4(T a[4][4], T b[4], T x[4])
+{
+    const T r0 = rcp(a[0][0]);
+    const T l10 = a[1][0] * r0, l20 = a[2][0] * r0, l30 = a[3][0] * r0;
+    const T a11 = a[1][1] - l10 * a[0][1], a12 = a[1][2] - l10 * a[0][2], a13 = a[1][3] - l10 * a[0][3];
+    const T a21 = a[2][1] - l20 * a[0][1], a22 = a[2][2] - l20 * a[0][2], a23 = a[2][3] - l20 * a[0][3];
+    const T a31 = a[3][1] - l30 * a[0][1], a32 = a[3][2] - l30 * a[0][2], a33 = a[3][3] - l30 * a[0][3];
+    const T b1 = b[1] - l10 * b[0], b2 = b[2] - l20 * b[0], b3 = b[3] - l30 * b[0];
+    const T r1 = rcp(a11);
+    const T l21 = a21 * r1, l31 = a31 * r1;
+    const T c22 = a22 - l21 * a12, c23 = a23 - l21 * a13, c32 = a32 - l31 * a12, c33 = a33 - l31 * a13;
+    const T d2 = b2 - l21 * b1, d3 = b3 - l31 * b1;
+    const T r2 = rcp(c22);
+    const T l32 = c32 * r2;
+    const T e33 = c33 - l32 * c23;
+    const T e3 = d3 - l32 * d2;
+    x[3] = e3 * rcp(e33);
+    x[2] = (d2 - c23 * x[3]) * r2;
+    x[1] = (b1 - a12 * x[2] - a13 * x[3]) * r1;
+    x[0] = (b[0] - a[0][1] * x[1] - a[0][2] * x[2] - a[0][3] * x[3]) * r0;
+}
+
+template <class T> struct CellSetup {
+    int64_t c;
+    uint32_t mask;
+    T A0[4][4];  // streaming + inflow-face part of the matrix (group independent)
+    T t[4];      // |Omega.N_f| / 12 on inflow faces, 0 otherwise
+    T mv;
+    int32_t mat;
+    uint32_t nn;
+    int32_t nbr[4];
+};
+
+// Group-independent part of the local system of cell c for direction Omega.
+//   A_ij = (V/4) Omega.grad b_j + sum_{f inflow, i,j != f} (|s_f|/12)(1 + delta_ij) + sigma (V/20)(1 + delta_ij)
+// With t_f = |s_f|/12 on inflow faces and T = sum_f t_f the face part is
+// T - t_i - t_j off the diagonal and 2 (T - t_i) on it.
+template <class T>
+__device__ __forceinline__ void cell_setup(const SweepArgs<T> &A, uint32_t entry, T ox, T oy, T oz, CellSetup<T> &s)
+{
+    s.c = entry >> 4;
+    s.mask = entry & 15u;
+    union {
+        CellGeo<T> g;
+        uint4 u[sizeof(CellGeo<T>) / 16];
+    } U;
+    const uint4 *src = reinterpret_cast<const uint4 *>(A.geo + s.c);
+#pragma unroll
+    for (int k = 0; k < (int)(sizeof(CellGeo<T>) / 16); ++k) U.u[k] = __ldg(src + k);
+    const CellGeo<T> &g = U.g;
+    T P[4], tt = T(0);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) P[j] = ox * g.gx[j] + oy * g.gy[j] + oz * g.gz[j];
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+        const T sf = ox * g.nx[f] + oy * g.ny[f] + oz * g.nz[f];
+        s.t[f] = ((s.mask >> f) & 1u) ? fabs(sf) * T(1.0 / 12.0) : T(0);
+        tt += s.t[f];
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) s.A0[i][j] = P[j] + (i == j ? T(2) * (tt - s.t[i]) : tt - s.t[i] - s.t[j]);
+    s.mv = g.mv;
+    s.mat = g.mat;
+    s.nn = g.nn;
+#pragma unroll
+    for (int f = 0; f < 4; ++f) s.nbr[f] = g.nbr[f];
+}
+
+// Solve one (cell, direction, group) unit and store psi.
+template <class T>
+__device__ __forceinline__ void solve_unit(const SweepArgs<T> &A, const CellSetup<T> &s, int g, size_t psi_dir,
+                                           T ox, T oy, T oz)
+{
+    const int G = A.G;
+    const T sig = __ldg(A.sigma_t + (size_t)s.mat * G + g);
+    const T sv = sig * s.mv;
+    const V4<T> q4 = ld_ro(A.q + (size_t)s.c * G + g);
+    const T qs = q4.x + q4.y + q4.z + q4.w;
+    T b[4] = {s.mv * (q4.x + qs), s.mv * (q4.y + qs), s.mv * (q4.z + qs), s.mv * (q4.w + qs)};
+    if (A.S1) {
+        const V4<T> s1 = ld_ro(A.S1 + (size_t)s.c * G + g);
+        const T os = T(5) * s.mv * (ox * s1.x + oy * s1.y + oz * s1.z);  // (V/4) Omega.S1
+#pragma unroll
+        for (int i = 0; i < 4; ++i) b[i] += os;
+    }
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+        if (!((s.mask >> f) & 1u)) continue;
+        const int n = s.nbr[f];
+        T up[4] = {T(0), T(0), T(0), T(0)};
+        bool have = false;
+        if (n >= 0) {
+            const V4<T> u = ld_l2(A.psi + (psi_dir + (size_t)n) * G + g);
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+                if (i != f) up[i] = comp(u, (int)((s.nn >> (2 * (4 * f + i))) & 3u));
+            have = true;
+        } else if (A.psi_in) {
+            const int4 tv = __ldg(A.tets + s.c);
+            const int vi[4] = {tv.x, tv.y, tv.z, tv.w};
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+                if (i != f) up[i] = __ldg(A.psi_in + (size_t)vi[i] * G + g);
+            have = true;
+        }
+        if (have) {
+            const T U = up[0] + up[1] + up[2] + up[3];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+                if (i != f) b[i] += s.t[f] * (up[i] + U);
+        }
+    }
+    T a[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) a[i][j] = s.A0[i][j] + (i == j ? T(2) * sv : sv);
+    T x[4];
+    solve4(a, b, x);
+    V4<T> out;
+    out.x = x[0];
+    out.y = x[1];
+    out.z = x[2];
+    out.w = x[3];
+    st_psi(A.psi + (psi_dir + (size_t)s.c) * G + g, out);
+}
+
+// Persistent sweep: every warp repeatedly claims a ticket (the next queue
+// slot), waits until that slot holds a ready task, executes it with lanes
+// spanning (cell, group) units, then decrements the counters of the task's
+// downwind blocks; the decrement that reaches zero enqueues that block
+// (work-first generation, Algorithm 1; atomic counters, Sec. 3.5).
+// Termination: exactly n_tasks slots get filled, so a warp whose ticket is
+// >= n_tasks exits.  Every wait is bounded by wait_limit_ns.
+template <class T> __global__ void __launch_bounds__(256) sweep_kernel(const SweepArgs<T> A)
+{
+    const int lane = threadIdx.x & 31;
+    const unsigned FULL = 0xffffffffu;
+    const unsigned epoch = *(const volatile unsigned *)&A.ctrl->epoch;
+    unsigned long long polls = 0, wait_ns = 0, busy_ns = 0, done = 0, depth = 0, pops = 0;
+    const unsigned long long t_start = globaltimer();
+    for (;;) {
+        unsigned long long ticket = 0;
+        if (lane == 0) ticket = atomicAdd(&A.ctrl->head, 1ull);
+        ticket = __shfl_sync(FULL, ticket, 0);
+        if (ticket >= A.n_tasks) break;
+        unsigned task = 0;
+        int stop = 0;
+        if (lane == 0) {
+            const unsigned long long t0 = globaltimer();
+            unsigned long long v = ld_acquire(A.slots + ticket);
+            if ((unsigned)(v >> 32) != epoch) {
+                unsigned ns = 64;
+                for (;;) {
+                    __nanosleep(ns);
+                    if (ns < 2048) ns <<= 1;
+                    ++polls;
+                    v = ld_acquire(A.slots + ticket);
+                    if ((unsigned)(v >> 32) == epoch) break;
+                    if (ld_volatile(&A.ctrl->error)) {
+                        stop = 1;
+                        break;
+                    }
+                    if (globaltimer() - t0 > A.wait_limit_ns) {
+                        atomicCAS(&A.ctrl->error, 0, (int)TF_ERR_TIMEOUT);
+                        stop = 1;
+                        break;
+                    }
+                }
+            }
+            const unsigned long long t1 = globaltimer();
+            wait_ns += t1 - t0;
+            const long long dq = (long long)(ld_volatile(&A.ctrl->tail) - ticket);
+            depth += dq > 0 ? (unsigned long long)dq : 0ull;
+            ++pops;
+            task = (unsigned)v;
+            if (!stop && (task < A.task_begin || task >= A.task_end)) {
+                atomicCAS(&A.ctrl->error, 0, (int)TF_ERR_DEVICE);
+                stop = 1;
+            }
+        }
+        __syncwarp();
+        stop = __shfl_sync(FULL, stop, 0);
+        if (stop) break;
+        task = __shfl_sync(FULL, task, 0);
+        const unsigned long long tb = globaltimer();
+
+        const uint4 ti = __ldg(A.task + task);
+        const uint32_t ncell = ti.y & 0xffffu, dir = ti.y >> 16;
+        const V4<T> om = ld_ro(A.omega + dir);
+        const T ox = om.x, oy = om.y, oz = om.z;
+        const size_t psi_dir = (size_t)(dir - (uint32_t)A.dir_begin) * (size_t)A.C;
+        // units u = lane, lane + 32, ... over (cell k, group g), g fastest
+        int g = lane;
+        uint32_t k = 0;
+        while (g >= A.G) {
+            g -= A.G;
+            ++k;
+        }
+        uint32_t kc = 0xffffffffu;
+        CellSetup<T> s;
+        while (k < ncell) {
+            if (k != kc) {
+                cell_setup(A, __ldg(A.cells + ti.x + k), ox, oy, oz, s);
+                kc = k;
+            }
+            solve_unit(A, s, g, psi_dir, ox, oy, oz);
+            g += 32;
+            while (g >= A.G) {
+                g -= A.G;
+                ++k;
+            }
+        }
+        // release: every lane's psi stores are ordered before any counter decrement
+        __threadfence();
+        __syncwarp();
+        for (uint32_t e = lane; e < ti.w; e += 32) {
+            const uint32_t d = __ldg(A.down + ti.z + e);
+            if (atom_add_acq_rel(A.counters + d, -1) == 1) {
+                const unsigned long long slot = atomicAdd(&A.ctrl->tail, 1ull);
+                if (slot < A.n_tasks)
+                    st_release(A.slots + slot, ((unsigned long long)epoch << 32) | d);
+                else  // more releases than tasks: the task graph is inconsistent
+                    atomicCAS(&A.ctrl->error, 0, (int)TF_ERR_DEVICE);
+            }
+        }
+        __syncwarp();
+        busy_ns += globaltimer() - tb;
+        ++done;
+    }
+    const unsigned long long t_end = globaltimer();
+    if (lane == 0) {
+        atomicAdd(&A.ctrl->tasks_done, done);
+        atomicAdd(&A.ctrl->polls, polls);
+        atomicAdd(&A.ctrl->wait_ns, wait_ns);
+        atomicAdd(&A.ctrl->busy_ns, busy_ns);
+        atomicAdd(&A.ctrl->depth_sum, depth);
+        atomicAdd(&A.ctrl->pops, pops);
+        atomicMin(&A.ctrl->t_first, t_start);
+        atomicMax(&A.ctrl->t_last, t_end);
+    }
+}
+
+// New launch: bump the epoch, empty the queue.
+__global__ void begin_kernel(Ctrl *ctrl, unsigned long long n_seeds, int reset_stats)
+{
+    ctrl->epoch = ctrl->epoch + 1u;
+    ctrl->head = 0;
+    ctrl->tail = n_seeds;
+    if (reset_stats) {
+        ctrl->tasks_done = ctrl->polls = ctrl->wait_ns = ctrl->busy_ns = 0;
+        ctrl->depth_sum = ctrl->pops = 0;
+        ctrl->kernel_ns = 0;
+    }
+    ctrl->t_first = ~0ull;
+    ctrl->t_last = 0;
+}
+
+// Counters of the chunk's tasks <- in-degrees; the first n_seeds slots <- seeds.
+__global__ void fill_kernel(Ctrl *ctrl, int *counters, const int *indeg, uint32_t task_begin, uint32_t n_tasks,
+                            unsigned long long *slots, const uint32_t *seeds, uint32_t n_seeds, int inject_stall)
+{
+    const unsigned epoch = ctrl->epoch;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n_tasks; i += gridDim.x * blockDim.x)
+        counters[task_begin + i] = indeg[task_begin + i];
+    if (inject_stall) return;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n_seeds; i += gridDim.x * blockDim.x)
+        slots[i] = ((unsigned long long)epoch << 32) | seeds[i];
+}
+
+__global__ void end_kernel(Ctrl *ctrl)
+{
+    if (ctrl->t_last > ctrl->t_first) ctrl->kernel_ns += ctrl->t_last - ctrl->t_first;
+}
+
+// ============================================================== source update
+// q[c][g][i] = (Q[c][g][i] + sum_g' sigma_s[m][g'][g] phi[c][g'][i]) / (4 pi)
+// One CTA stages the FP64 scalar flux of a few cells (converted to the sweep
+// precision) in shared memory; thread (cell, g) forms the 4 nodal sums.
+template <class T>
+__global__ void __launch_bounds__(256) source_kernel(const double *__restrict__ phi, const V4<T> *__restrict__ Qext,
+                                                     const T *__restrict__ sigma_s, const CellGeo<T> *__restrict__ geo,
+                                                     V4<T> *__restrict__ q, int64_t C, int G, int cells_per_cta)
+{
+    extern __shared__ unsigned char smem_raw[];
+    T *ph = reinterpret_cast<T *>(smem_raw);  // [cells_per_cta][G][4]
+    const T inv4pi = T(1.0 / (4.0 * 3.14159265358979323846));
+    for (int64_t c0 = (int64_t)blockIdx.x * cells_per_cta; c0 < C; c0 += (int64_t)gridDim.x * cells_per_cta) {
+        const int nc = (int)((C - c0) < (int64_t)cells_per_cta ? (C - c0) : (int64_t)cells_per_cta);
+        __syncthreads();
+        for (int e = threadIdx.x; e < nc * G * 4; e += blockDim.x) ph[e] = (T)phi[(size_t)c0 * G * 4 + e];
+        __syncthreads();
+        for (int u = threadIdx.x; u < nc * G; u += blockDim.x) {
+            const int lc = u / G, g = u - lc * G;
+            const int64_t c = c0 + lc;
+            const int m = __ldg(&geo[c].mat);
+            const T *S = sigma_s + (size_t)m * G * G + g;
+            const T *p = ph + (size_t)lc * G * 4;
+            T a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+            for (int h = 0; h < G; ++h) {
+                const T s = __ldg(S + (size_t)h * G);
+                a0 += s * p[4 * h + 0];
+                a1 += s * p[4 * h + 1];
+                a2 += s * p[4 * h + 2];
+                a3 += s * p[4 * h + 3];
+            }
+            const V4<T> Qv = ld_ro(Qext + (size_t)c * G + g);
+            V4<T> o;
+            o.x = (Qv.x + a0) * inv4pi;
+            o.y = (Qv.y + a1) * inv4pi;
+            o.z = (Qv.z + a2) * inv4pi;
+            o.w = (Qv.w + a3) * inv4pi;
+            q[(size_t)c * G + g] = o;
+        }
+    }
+}
+
+// ============================================================== phi reduction
+// phi[c][g][i] (+)= sum over the chunk's directions of w_a psi_a[c][g][i] (Eq. 2).
+// Thread per (cell, group); the directions are summed in registers.
+// FP32 psi with TF_PHI_PAIR: each product w_a psi is formed exactly as a
+// float pair (TwoProd with the weight split into hi + lo) and added with
+// TwoSum into a (hi, lo) float pair; the pair is rounded once to FP64.
+struct WeightPair {
+    float hi, lo;
+    double d;
+};
+
+__device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float p, float e)
+{
+    const float s = hi + p;
+    const float bb = s - hi;
+    const float err = (hi - (s - bb)) + (p - bb);
+    hi = s;
+    lo += err + e;
+}
+
+template <class T, bool PAIR>
+__global__ void __launch_bounds__(256) phi_kernel(const V4<T> *__restrict__ psi, const WeightPair *__restrict__ wts,
+                                                  int Dc, size_t CG, double *__restrict__ phi, int accumulate)
+{
+    for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < CG; idx += (size_t)gridDim.x * blockDim.x) {
+        double r[4];
+        if constexpr (PAIR) {
+            float hi[4] = {0.f, 0.f, 0.f, 0.f}, lo[4] = {0.f, 0.f, 0.f, 0.f};
+            int a = 0;
+            for (; a + 4 <= Dc; a += 4) {
+                V4<T> v[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) v[k] = ld_stream(psi + (size_t)(a + k) * CG + idx);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const WeightPair w = wts[a + k];
+                    const float x[4] = {v[k].x, v[k].y, v[k].z, v[k].w};
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const float p = w.hi * x[i];
+                        const float e = fmaf(w.hi, x[i], -p) + w.lo * x[i];
+                        two_sum_acc(hi[i], lo[i], p, e);
+                    }
+                }
+            }
+            for (; a < Dc; ++a) {
+                const V4<T> v = ld_stream(psi + (size_t)a * CG + idx);
+                const WeightPair w = wts[a];
+                const float x[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const float p = w.hi * x[i];
+                    const float e = fmaf(w.hi, x[i], -p) + w.lo * x[i];
+                    two_sum_acc(hi[i], lo[i], p, e);
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i) r[i] = (double)hi[i] + (double)lo[i];
+        } else {
+            double acc[4] = {0.0, 0.0, 0.0, 0.0};
+            int a = 0;
+            for (; a + 4 <= Dc; a += 4) {
+                V4<T> v[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) v[k] = ld_stream(psi + (size_t)(a + k) * CG + idx);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const double w = wts[a + k].d;
+                    acc[0] = fma(w, (double)v[k].x, acc[0]);
+                    acc[1] = fma(w, (double)v[k].y, acc[1]);
+                    acc[2] = fma(w, (double)v[k].z, acc[2]);
+                    acc[3] = fma(w, (double)v[k].w, acc[3]);
+                }
+            }
+            for (; a < Dc; ++a) {
+                const V4<T> v = ld_stream(psi + (size_t)a * CG + idx);
+                const double w = wts[a].d;
+                acc[0] = fma(w, (double)v.x, acc[0]);
+                acc[1] = fma(w, (double)v.y, acc[1]);
+                acc[2] = fma(w, (double)v.z, acc[2]);
+                acc[3] = fma(w, (double)v.w, acc[3]);
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i) r[i] = acc[i];
+        }
+        double2 *out = reinterpret_cast<double2 *>(phi + idx * 4);
+        if (accumulate) {
+            const double2 o0 = out[0], o1 = out[1];
+            r[0] += o0.x;
+            r[1] += o0.y;
+            r[2] += o1.x;
+            r[3] += o1.y;
+        }
+        out[0] = make_double2(r[0], r[1]);
+        out[1] = make_double2(r[2], r[3]);
+    }
+}
+
+// ============================================================== FP64 statistics
+// Deterministic per-group reductions over cells.  CTA = 32 x 8 threads:
+// threadIdx.x walks groups, threadIdx.y walks cells; per-CTA partials go to
+// scratch [nblk][G][3] = (max |phi|, sum_c (V_c/4) sum_i phi, sum_c sum_i phi),
+// then finish_stats_kernel reduces over CTAs in a fixed order (Eq. (3)) into
+// [G][4] = (max, integrated flux, plain nodal sum, 1/max).
+__global__ void __launch_bounds__(256) stats_kernel(const double *__restrict__ phi, const double *__restrict__ vol4,
+                                                    int64_t C, int G, double *__restrict__ part)
+{
+    __shared__ double sh[3][8][32];
+    for (int g0 = 0; g0 < G; g0 += 32) {
+        const int g = g0 + threadIdx.x;
+        double mx = 0.0, iv = 0.0, pl = 0.0;
+        if (g < G) {
+            for (int64_t c = (int64_t)blockIdx.x * 8 + threadIdx.y; c < C; c += (int64_t)gridDim.x * 8) {
+                const double2 *p = reinterpret_cast<const double2 *>(phi + ((size_t)c * G + g) * 4);
+                const double2 a = p[0], b = p[1];
+                const double s = (a.x + a.y) + (b.x + b.y);
+                mx = fmax(mx, fmax(fmax(fabs(a.x), fabs(a.y)), fmax(fabs(b.x), fabs(b.y))));
+                iv += vol4[c] * s;
+                pl += s;
+            }
+        }
+        sh[0][threadIdx.y][threadIdx.x] = mx;
+        sh[1][threadIdx.y][threadIdx.x] = iv;
+        sh[2][threadIdx.y][threadIdx.x] = pl;
+        __syncthreads();
+        if (threadIdx.y == 0 && g < G) {
+            double m = sh[0][0][threadIdx.x], a = sh[1][0][threadIdx.x], b = sh[2][0][threadIdx.x];
+            for (int y = 1; y < 8; ++y) {
+                m = fmax(m, sh[0][y][threadIdx.x]);
+                a += sh[1][y][threadIdx.x];
+                b += sh[2][y][threadIdx.x];
+            }
+            double *o = part + ((size_t)blockIdx.x * G + g) * 3;
+            o[0] = m;
+            o[1] = a;
+            o[2] = b;
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void finish_stats_kernel(const double *__restrict__ part, int nblk, int G, double *__restrict__ out)
+{
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < G; g += gridDim.x * blockDim.x) {
+        double m = 0.0, a = 0.0, b = 0.0;
+        for (int k = 0; k < nblk; ++k) {
+            const double *p = part + ((size_t)k * G + g) * 3;
+            m = fmax(m, p[0]);
+            a += p[1];
+            b += p[2];
+        }
+        out[4 * g + 0] = m;
+        out[4 * g + 1] = a;
+        out[4 * g + 2] = b;
+        out[4 * g + 3] = m > 0.0 ? 1.0 / m : 0.0;
+    }
+}
+
+// Stopping test: max over (c, g, i) of |phi_new - phi_old| / max(|phi_new|, 1e-10 gmax_g).
+// Difference and denominator are FP64; their quotient, both scaled by the
+// group's 1/gmax, is formed in FP32, which only blurs r itself by ~1e-7.
+// Same 32 (groups) x 8 (cells) CTA shape as stats_kernel.
+__global__ void __launch_bounds__(256) residual_kernel(const double *__restrict__ phi_new, const double *__restrict__ phi_old,
+                                                       const double *__restrict__ gstats, int64_t C, int G, Ctrl *ctrl)
+{
+    float rmax = 0.f;
+    for (int g0 = 0; g0 < G; g0 += 32) {
+        const int g = g0 + threadIdx.x;
+        if (g >= G) continue;
+        const double gmax = gstats[4 * g], inv = gstats[4 * g + 3];
+        const double floor_ = 1e-10 * gmax;
+        for (int64_t c = (int64_t)blockIdx.x * 8 + threadIdx.y; c < C; c += (int64_t)gridDim.x * 8) {
+            const double2 *pn = reinterpret_cast<const double2 *>(phi_new + ((size_t)c * G + g) * 4);
+            const double2 *po = reinterpret_cast<const double2 *>(phi_old + ((size_t)c * G + g) * 4);
+            const double2 n0 = pn[0], n1 = pn[1], o0 = po[0], o1 = po[1];
+            const double nv[4] = {n0.x, n0.y, n1.x, n1.y}, ov[4] = {o0.x, o0.y, o1.x, o1.y};
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const double diff = fabs(nv[i] - ov[i]);
+                if (diff == 0.0) continue;
+                const double den = fmax(fabs(nv[i]), floor_);
+                rmax = fmaxf(rmax, den > 0.0 ? __fdiv_rn((float)(diff * inv), (float)(den * inv)) : INFINITY);
+            }
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) rmax = fmaxf(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
+    if ((threadIdx.x & 31) == 0 && rmax > 0.f)
+        atomicMax(&ctrl->residual_bits, (unsigned long long)__double_as_longlong((double)rmax));
+}
+
+// ============================================================== host side
+struct DeviceState {
+    int device = 0, sm_count = 0;
+    int64_t C = 0, nv = 0;
+    int32_t G = 0, D = 0, M = 0;
+    bool fp64 = false;
+    size_t tsize = 4;  // sizeof(T)
+    void *geo = nullptr;
+    uint32_t *cells = nullptr;
+    uint4 *task = nullptr;
+    uint32_t *down = nullptr;
+    int *indeg = nullptr;
+    int *counters = nullptr;
+    unsigned long long *slots = nullptr;
+    uint32_t *seeds = nullptr;
+    void *omega = nullptr;
+    void *sigma_t = nullptr;
+    void *sigma_s = nullptr;
+    void *Q = nullptr;
+    void *S1 = nullptr;
+    void *psi_in = nullptr;
+    int4 *tets = nullptr;
+    void *q = nullptr;
+    void *psi = nullptr;
+    double *vol4 = nullptr;
+    WeightPair *wts = nullptr;
+    double *phi_buf[2] = {nullptr, nullptr};
+    double *part = nullptr;
+    double *gstats = nullptr;  // [G][4] = (max |phi|, integrated flux, nodal sum, 1/max)
+    Ctrl *ctrl = nullptr;
+    Ctrl *ctrl_host = nullptr;  // pinned
+    double *gstats_host = nullptr;  // pinned [G][3]
+    int Dc = 0, n_chunks = 0;
+    std::vector<int64_t> chunk_task_begin;  // [n_chunks + 1]
+    std::vector<int64_t> chunk_seed_begin;  // [n_chunks + 1]
+    int64_t max_chunk_tasks = 0;
+    int grid = 0, wpc = 0;
+    int stats_blocks = 0;
+    int last_chunk = -1;
+    std::vector<void *> allocs;
+    // event pairs: [0] source, then per chunk (sweep, phi)
+    std::vector<cudaEvent_t> ev_start, ev_stop;
+};
+
+namespace {
+
+tf_status cuda_fail(cudaError_t e, const char *what)
+{
+    return fail(e == cudaErrorMemoryAllocation ? TF_ERR_NOMEM : TF_ERR_CUDA,
+                std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define TF_CUDA(call)                                       \
+    do {                                                    \
+        cudaError_t e_ = (call);                            \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+    } while (0)
+
+template <class P> tf_status dmalloc(DeviceState &d, P **p, size_t bytes)
+{
+    void *q = nullptr;
+    cudaError_t e = cudaMalloc(&q, std::max<size_t>(bytes, 16));
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+    d.allocs.push_back(q);
+    *p = static_cast<P *>(q);
+    return TF_OK;
+}
+
+template <class P> tf_status upload(DeviceState &d, P **p, const void *src, size_t bytes)
+{
+    tf_status s = dmalloc(d, p, bytes);
+    if (s != TF_OK) return s;
+    if (bytes) TF_CUDA(cudaMemcpy(*p, src, bytes, cudaMemcpyHostToDevice));
+    return TF_OK;
+}
+
+template <class T> void pack_geometry(const Mesh &m, const int32_t *cell_material, std::vector<CellGeo<T>> &out)
+{
+    out.resize(m.nc);
+    for (int64_t c = 0; c < m.nc; ++c) {
+        CellGeo<T> &g = out[c];
+        std::memset(&g, 0, sizeof(g));
+        const double V = m.vol[c];
+        for (int j = 0; j < 4; ++j) {
+            g.gx[j] = (T)(0.25 * V * m.grad[12 * c + 3 * j + 0]);
+            g.gy[j] = (T)(0.25 * V * m.grad[12 * c + 3 * j + 1]);
+            g.gz[j] = (T)(0.25 * V * m.grad[12 * c + 3 * j + 2]);
+            g.nx[j] = (T)m.normal[12 * c + 3 * j + 0];
+            g.ny[j] = (T)m.normal[12 * c + 3 * j + 1];
+            g.nz[j] = (T)m.normal[12 * c + 3 * j + 2];
+            g.nbr[j] = m.nbr[4 * c + j];
+        }
+        g.mv = (T)(V / 20.0);
+        g.mat = cell_material[c];
+        uint32_t nn = 0;
+        for (int f = 0; f < 4; ++f)
+            for (int i = 0; i < 4; ++i) {
+                const int k = m.nbr_node[16 * c + 4 * f + i];
+                if (k >= 0) nn |= (uint32_t)k << (2 * (4 * f + i));
+            }
+        g.nn = nn;
+    }
+}
+
+template <class T> tf_status upload_typed(DeviceState &d, void **p, const double *src, size_t n)
+{
+    std::vector<T> tmp(n);
+    for (size_t i = 0; i < n; ++i) tmp[i] = (T)src[i];
+    T *q = nullptr;
+    tf_status s = upload(d, &q, tmp.data(), n * sizeof(T));
+    *p = q;
+    return s;
+}
+
+// [n][3] -> [n] x V4 (fourth component zero / weight)
+template <class T> tf_status upload_vec3(DeviceState &d, void **p, const double *src, size_t n, const double *w4)
+{
+    std::vector<V4<T>> tmp(n);
+    for (size_t i = 0; i < n; ++i) {
+        tmp[i].x = (T)src[3 * i];
+        tmp[i].y = (T)src[3 * i + 1];
+        tmp[i].z = (T)src[3 * i + 2];
+        tmp[i].w = w4 ? (T)w4[i] : T(0);
+    }
+    V4<T> *q = nullptr;
+    tf_status s = upload(d, &q, tmp.data(), n * sizeof(V4<T>));
+    *p = q;
+    return s;
+}
+
+template <class T> tf_status create_typed(Problem &p, DeviceState &d, const int32_t *cell_material, const double *sigma_t,
+                                          const double *sigma_s, const double *Q, const double *S1, const double *psi_in)
+{
+    const Mesh &m = *p.mesh;
+    const TaskGraph &g = p.graph;
+    tf_status s;
+    {
+        std::vector<CellGeo<T>> geo;
+        pack_geometry<T>(m, cell_material, geo);
+        CellGeo<T> *gp = nullptr;
+        if ((s = upload(d, &gp, geo.data(), geo.size() * sizeof(CellGeo<T>))) != TF_OK) return s;
+        d.geo = gp;
+    }
+    if ((s = upload_vec3<T>(d, &d.omega, p.quad->omega.data(), d.D, p.quad->w.data())) != TF_OK) return s;
+    if ((s = upload_typed<T>(d, &d.sigma_t, sigma_t, (size_t)d.M * d.G)) != TF_OK) return s;
+    if ((s = upload_typed<T>(d, &d.sigma_s, sigma_s, (size_t)d.M * d.G * d.G)) != TF_OK) return s;
+    if ((s = upload_typed<T>(d, &d.Q, Q, (size_t)d.C * d.G * 4)) != TF_OK) return s;
+    if (S1) {
+        if ((s = upload_vec3<T>(d, &d.S1, S1, (size_t)d.C * d.G, nullptr)) != TF_OK) return s;
+    }
+    if (psi_in) {
+        if ((s = upload_typed<T>(d, &d.psi_in, psi_in, (size_t)d.nv * d.G)) != TF_OK) return s;
+        if ((s = upload(d, &d.tets, m.tets.data(), sizeof(int4) * m.nc)) != TF_OK) return s;
+    }
+    (void)g;
+    return TF_OK;
+}
+
+}  // namespace
+
+tf_status device_create(Problem &p, const int32_t *cell_material, const double *sigma_t, const double *sigma_s,
+                        const double *Q, const double *S1, const double *psi_in)
+{
+    DeviceState *dp = new (std::nothrow) DeviceState();
+    if (!dp) return fail(TF_ERR_NOMEM, "device state allocation failed");
+    p.dev = dp;
+    DeviceState &d = *dp;
+    const Mesh &m = *p.mesh;
+    const TaskGraph &g = p.graph;
+    d.device = p.opt.device;
+    int ndev = 0;
+    TF_CUDA(cudaGetDeviceCount(&ndev));
+    if (d.device < 0 || d.device >= ndev) return fail(TF_ERR_ARG, "tf_problem_create: no such CUDA device");
+    TF_CUDA(cudaSetDevice(d.device));
+    TF_CUDA(cudaDeviceGetAttribute(&d.sm_count, cudaDevAttrMultiProcessorCount, d.device));
+    d.C = m.nc;
+    d.nv = m.nv;
+    d.G = p.G;
+    d.D = p.quad->D;
+    d.M = p.M;
+    d.fp64 = p.opt.precision == TF_FP64;
+    d.tsize = d.fp64 ? 8 : 4;
+    const int64_t T = g.T();
+    if ((uint64_t)g.down_list.size() >= (1ull << 32)) return fail(TF_ERR_ARG, "graph too large: 2^32 downwind edges");
+    tf_status s;
+    // task graph
+    if ((s = upload(d, &d.cells, g.cell_list.data(), g.cell_list.size() * 4)) != TF_OK) return s;
+    {
+        std::vector<uint4> ti(T);
+        for (int64_t t = 0; t < T; ++t) {
+            ti[t].x = g.task_cell_begin[t];
+            ti[t].y = (uint32_t)g.task_ncell[t] | ((uint32_t)g.task_dir[t] << 16);
+            ti[t].z = (uint32_t)g.down_begin[t];
+            ti[t].w = (uint32_t)(g.down_begin[t + 1] - g.down_begin[t]);
+        }
+        if ((s = upload(d, &d.task, ti.data(), ti.size() * sizeof(uint4))) != TF_OK) return s;
+    }
+    if ((s = upload(d, &d.down, g.down_list.data(), g.down_list.size() * 4)) != TF_OK) return s;
+    if ((s = upload(d, &d.indeg, g.task_indeg.data(), (size_t)T * 4)) != TF_OK) return s;
+    if ((s = dmalloc(d, &d.counters, (size_t)T * 4)) != TF_OK) return s;
+    // cell volumes / 4 (FP64) for the integrated flux
+    {
+        std::vector<double> v4(m.nc);
+        for (int64_t c = 0; c < m.nc; ++c) v4[c] = 0.25 * m.vol[c];
+        if ((s = upload(d, &d.vol4, v4.data(), v4.size() * 8)) != TF_OK) return s;
+    }
+    s = d.fp64 ? create_typed<double>(p, d, cell_material, sigma_t, sigma_s, Q, S1, psi_in)
+               : create_typed<float>(p, d, cell_material, sigma_t, sigma_s, Q, S1, psi_in);
+    if (s != TF_OK) return s;
+    if ((s = dmalloc(d, &d.q, (size_t)d.C * d.G * 4 * d.tsize)) != TF_OK) return s;
+    if ((s = dmalloc(d, &d.phi_buf[0], (size_t)d.C * d.G * 4 * 8)) != TF_OK) return s;
+    if ((s = dmalloc(d, &d.phi_buf[1], (size_t)d.C * d.G * 4 * 8)) != TF_OK) return s;
+    // per-direction weights
+    {
+        std::vector<WeightPair> w(d.D);
+        for (int a = 0; a < d.D; ++a) {
+            w[a].d = p.quad->w[a];
+            w[a].hi = (float)w[a].d;
+            w[a].lo = (float)(w[a].d - (double)w[a].hi);
+        }
+        if ((s = upload(d, &d.wts, w.data(), w.size() * sizeof(WeightPair))) != TF_OK) return s;
+    }
+    // control block and reduction scratch
+    if ((s = dmalloc(d, &d.ctrl, sizeof(Ctrl))) != TF_OK) return s;
+    TF_CUDA(cudaMemset(d.ctrl, 0, sizeof(Ctrl)));
+    TF_CUDA(cudaMallocHost(&d.ctrl_host, sizeof(Ctrl)));
+    TF_CUDA(cudaMallocHost(&d.gstats_host, sizeof(double) * 4 * d.G));
+    d.stats_blocks = std::max(1, std::min<int>(4 * d.sm_count, (int)((d.C + 7) / 8)));
+    if ((s = dmalloc(d, &d.part, sizeof(double) * 3 * d.G * d.stats_blocks)) != TF_OK) return s;
+    if ((s = dmalloc(d, &d.gstats, sizeof(double) * 4 * d.G)) != TF_OK) return s;
+    // direction chunks: as many directions per launch as the psi budget allows
+    const size_t per_dir = (size_t)d.C * d.G * 4 * d.tsize;
+    size_t free_b = 0, total_b = 0;
+    TF_CUDA(cudaMemGetInfo(&free_b, &total_b));
+    double budget = p.opt.psi_budget_gb > 0 ? p.opt.psi_budget_gb * 1e9 : 0.8 * (double)free_b;
+    int Dc = p.opt.dir_chunk > 0 ? std::min(p.opt.dir_chunk, d.D) : (int)std::min<double>(d.D, budget / (double)per_dir);
+    if (Dc < 1) return fail(TF_ERR_NOMEM, "not enough device memory for one direction of angular flux");
+    d.Dc = Dc;
+    d.n_chunks = (d.D + Dc - 1) / Dc;
+    // seeds per chunk, longest remaining critical path first
+    std::vector<uint32_t> seeds;
+    d.chunk_task_begin.assign(d.n_chunks + 1, 0);
+    d.chunk_seed_begin.assign(d.n_chunks + 1, 0);
+    for (int k = 0; k < d.n_chunks; ++k) {
+        const int a0 = k * Dc, a1 = std::min(d.D, a0 + Dc);
+        const int64_t t0 = g.dir_task_begin[a0], t1 = g.dir_task_begin[a1];
+        d.chunk_task_begin[k] = t0;
+        d.chunk_task_begin[k + 1] = t1;
+        d.max_chunk_tasks = std::max(d.max_chunk_tasks, t1 - t0);
+        const size_t sb = seeds.size();
+        for (int64_t t = t0; t < t1; ++t)
+            if (g.task_indeg[t] == 0) seeds.push_back((uint32_t)t);
+        std::stable_sort(seeds.begin() + sb, seeds.end(),
+                         [&](uint32_t x, uint32_t y) { return g.task_blevel[x] > g.task_blevel[y]; });
+        d.chunk_seed_begin[k + 1] = (int64_t)seeds.size();
+    }
+    if ((s = upload(d, &d.seeds, seeds.data(), seeds.size() * 4)) != TF_OK) return s;
+    if ((s = dmalloc(d, &d.slots, (size_t)d.max_chunk_tasks * 8)) != TF_OK) return s;
+    TF_CUDA(cudaMemset(d.slots, 0, (size_t)d.max_chunk_tasks * 8));
+    if ((s = dmalloc(d, &d.psi, per_dir * Dc)) != TF_OK) return s;
+    // persistent grid: resident CTAs per SM x SMs
+    d.wpc = p.opt.warps_per_cta > 0 ? std::min(p.opt.warps_per_cta, 8) : 4;
+    int per_sm = 0;
+    cudaError_t e = d.fp64 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_kernel<double>, 32 * d.wpc, 0)
+                           : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_kernel<float>, 32 * d.wpc, 0);
+    if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
+    if (p.opt.ctas_per_sm > 0) per_sm = std::min(per_sm, p.opt.ctas_per_sm);
+    d.grid = std::max(1, per_sm) * d.sm_count;
+    d.ev_start.resize(1 + 2 * d.n_chunks);
+    d.ev_stop.resize(1 + 2 * d.n_chunks);
+    for (size_t i = 0; i < d.ev_start.size(); ++i) {
+        TF_CUDA(cudaEventCreate(&d.ev_start[i]));
+        TF_CUDA(cudaEventCreate(&d.ev_stop[i]));
+    }
+    TF_CUDA(cudaDeviceSynchronize());
+    p.stats.launches_per_step = 1 + 5 * (int64_t)d.n_chunks;
+    p.stats.n_tasks = T;
+    p.stats.n_units = (int64_t)d.C * d.D * d.G;
+    p.stats.n_dirs = d.D;
+    p.stats.max_level = g.max_level;
+    p.stats.n_chunks = d.n_chunks;
+    p.stats.grid_ctas = d.grid;
+    p.stats.warps_per_cta = d.wpc;
+    p.stats.cells_per_task = g.cells_per_task;
+    return TF_OK;
+}
+
+void device_destroy(Problem &p)
+{
+    DeviceState *d = p.dev;
+    if (!d) return;
+    cudaSetDevice(d->device);
+    cudaDeviceSynchronize();
+    for (cudaEvent_t e : d->ev_start) cudaEventDestroy(e);
+    for (cudaEvent_t e : d->ev_stop) cudaEventDestroy(e);
+    for (void *a : d->allocs) cudaFree(a);
+    if (d->ctrl_host) cudaFreeHost(d->ctrl_host);
+    if (d->gstats_host) cudaFreeHost(d->gstats_host);
+    delete d;
+    p.dev = nullptr;
+}
+
+namespace {
+
+bool is_device_pointer(const void *ptr)
+{
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, ptr) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+template <class T> tf_status launch_step(Problem &p, const double *phi_in, double *phi_out, cudaStream_t st)
+{
+    DeviceState &d = *p.dev;
+    const size_t CG = (size_t)d.C * d.G;
+    // source update
+    {
+        const int cpc = std::max(1, 256 / d.G);
+        const size_t smem = (size_t)cpc * d.G * 4 * sizeof(T);
+        const int blocks = (int)std::min<int64_t>((d.C + cpc - 1) / cpc, (int64_t)d.sm_count * 16);
+        TF_CUDA(cudaEventRecord(d.ev_start[0], st));
+        source_kernel<T><<<blocks, 256, smem, st>>>(phi_in, (const V4<T> *)d.Q, (const T *)d.sigma_s,
+                                                    (const CellGeo<T> *)d.geo, (V4<T> *)d.q, d.C, d.G, cpc);
+        TF_CUDA(cudaGetLastError());
+        TF_CUDA(cudaEventRecord(d.ev_stop[0], st));
+    }
+    for (int k = 0; k < d.n_chunks; ++k) {
+        const int64_t t0 = d.chunk_task_begin[k], t1 = d.chunk_task_begin[k + 1];
+        const int64_t s0 = d.chunk_seed_begin[k], s1 = d.chunk_seed_begin[k + 1];
+        const int a0 = k * d.Dc, a1 = std::min(d.D, a0 + d.Dc);
+        begin_kernel<<<1, 1, 0, st>>>(d.ctrl, (unsigned long long)(s1 - s0), k == 0);
+        const int fb = (int)std::min<int64_t>(std::max<int64_t>(1, (t1 - t0 + 255) / 256), (int64_t)d.sm_count * 8);
+        fill_kernel<<<fb, 256, 0, st>>>(d.ctrl, d.counters, d.indeg, (uint32_t)t0, (uint32_t)(t1 - t0), d.slots,
+                                        d.seeds + s0, (uint32_t)(s1 - s0), p.opt.inject_stall);
+        SweepArgs<T> A;
+        A.geo = (const CellGeo<T> *)d.geo;
+        A.cells = d.cells;
+        A.task = d.task;
+        A.down = d.down;
+        A.counters = d.counters;
+        A.slots = d.slots;
+        A.ctrl = d.ctrl;
+        A.q = (const V4<T> *)d.q;
+        A.psi = (V4<T> *)d.psi;
+        A.sigma_t = (const T *)d.sigma_t;
+        A.omega = (const V4<T> *)d.omega;
+        A.S1 = (const V4<T> *)d.S1;
+        A.psi_in = (const T *)d.psi_in;
+        A.tets = d.tets;
+        A.C = d.C;
+        A.G = d.G;
+        A.dir_begin = a0;
+        A.task_begin = (uint32_t)t0;
+        A.task_end = (uint32_t)t1;
+        A.n_tasks = (unsigned long long)(t1 - t0);
+        A.wait_limit_ns = (unsigned long long)(p.opt.wait_limit_s * 1e9);
+        TF_CUDA(cudaEventRecord(d.ev_start[1 + 2 * k], st));
+        sweep_kernel<T><<<d.grid, 32 * d.wpc, 0, st>>>(A);
+        TF_CUDA(cudaGetLastError());
+        TF_CUDA(cudaEventRecord(d.ev_stop[1 + 2 * k], st));
+        end_kernel<<<1, 1, 0, st>>>(d.ctrl);
+        const int pb = (int)std::min<size_t>((CG + 255) / 256, (size_t)d.sm_count * 32);
+        TF_CUDA(cudaEventRecord(d.ev_start[2 + 2 * k], st));
+        if (!d.fp64 && p.opt.phi_accumulate == TF_PHI_PAIR)
+            phi_kernel<T, true><<<pb, 256, 0, st>>>((const V4<T> *)d.psi, d.wts + a0, a1 - a0, CG, phi_out, k > 0);
+        else
+            phi_kernel<T, false><<<pb, 256, 0, st>>>((const V4<T> *)d.psi, d.wts + a0, a1 - a0, CG, phi_out, k > 0);
+        TF_CUDA(cudaGetLastError());
+        TF_CUDA(cudaEventRecord(d.ev_stop[2 + 2 * k], st));
+        d.last_chunk = k;
+    }
+    return TF_OK;
+}
+
+tf_status step(Problem &p, const double *phi_in, double *phi_out, cudaStream_t st)
+{
+    return p.dev->fp64 ? launch_step<double>(p, phi_in, phi_out, st) : launch_step<float>(p, phi_in, phi_out, st);
+}
+
+// Reads the control block after the stream drained; turns a device error into a status.
+tf_status collect(Problem &p, cudaStream_t st)
+{
+    DeviceState &d = *p.dev;
+    TF_CUDA(cudaMemcpyAsync(d.ctrl_host, d.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
+    TF_CUDA(cudaStreamSynchronize(st));
+    const Ctrl &c = *d.ctrl_host;
+    tf_stats &s = p.stats;
+    s.tasks_executed = (int64_t)c.tasks_done;
+    s.wait_polls = (int64_t)c.polls;
+    s.wait_seconds = c.wait_ns * 1e-9;
+    s.busy_seconds = c.busy_ns * 1e-9;
+    s.kernel_seconds = c.kernel_ns * 1e-9;
+    s.mean_ready = c.pops ? (double)c.depth_sum / (double)c.pops : 0.0;
+    {
+        float ms = 0.f;
+        double src = 0.0, sw = 0.0, ph = 0.0;
+        TF_CUDA(cudaEventElapsedTime(&ms, d.ev_start[0], d.ev_stop[0]));
+        src = ms * 1e-3;
+        for (int k = 0; k < d.n_chunks; ++k) {
+            TF_CUDA(cudaEventElapsedTime(&ms, d.ev_start[1 + 2 * k], d.ev_stop[1 + 2 * k]));
+            sw += ms * 1e-3;
+            TF_CUDA(cudaEventElapsedTime(&ms, d.ev_start[2 + 2 * k], d.ev_stop[2 + 2 * k]));
+            ph += ms * 1e-3;
+        }
+        s.source_event_seconds = src;
+        s.sweep_event_seconds = sw;
+        s.phi_event_seconds = ph;
+        s.cum_source_event_seconds += src;
+        s.cum_sweep_event_seconds += sw;
+        s.cum_phi_event_seconds += ph;
+        s.cum_steps += 1;
+    }
+    if (c.error) {
+        const int err = c.error;
+        int zero = 0;
+        TF_CUDA(cudaMemcpyAsync(&d.ctrl->error, &zero, sizeof(int), cudaMemcpyHostToDevice, st));
+        TF_CUDA(cudaStreamSynchronize(st));
+        return fail((tf_status)err, err == TF_ERR_TIMEOUT ? "sweep: a device wait exceeded the wait limit"
+                                                          : "sweep: device reported an out-of-range task");
+    }
+    if (c.tasks_done != (unsigned long long)p.graph.T())
+        return fail(TF_ERR_DEVICE, "sweep: executed " + std::to_string(c.tasks_done) + " of " +
+                                       std::to_string(p.graph.T()) + " tasks");
+    return TF_OK;
+}
+
+}  // namespace
+
+tf_status device_sweep(Problem &p, const double *phi_in, double *phi_out, void *stream)
+{
+    DeviceState &d = *p.dev;
+    TF_CUDA(cudaSetDevice(d.device));
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t bytes = (size_t)d.C * d.G * 4 * 8;
+    const double *in = phi_in;
+    double *out = phi_out;
+    const bool host_in = !is_device_pointer(phi_in), host_out = !is_device_pointer(phi_out);
+    if (host_in) {
+        TF_CUDA(cudaMemcpyAsync(d.phi_buf[0], phi_in, bytes, cudaMemcpyHostToDevice, st));
+        in = d.phi_buf[0];
+    }
+    if (host_out) out = d.phi_buf[1];
+    tf_status s = step(p, in, out, st);
+    if (s != TF_OK) return s;
+    if (host_out) TF_CUDA(cudaMemcpyAsync(phi_out, out, bytes, cudaMemcpyDeviceToHost, st));
+    return collect(p, st);
+}
+
+tf_status device_iterate(Problem &p, double tol, int32_t max_iters, double *phi, tf_iter_info *info, void *stream)
+{
+    DeviceState &d = *p.dev;
+    TF_CUDA(cudaSetDevice(d.device));
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t CG = (size_t)d.C * d.G;
+    const size_t bytes = CG * 4 * 8;
+    const bool host = !is_device_pointer(phi);
+    double *cur = d.phi_buf[0], *nxt = d.phi_buf[1];
+    if (host)
+        TF_CUDA(cudaMemcpyAsync(cur, phi, bytes, cudaMemcpyHostToDevice, st));
+    else
+        TF_CUDA(cudaMemcpyAsync(cur, phi, bytes, cudaMemcpyDeviceToDevice, st));
+    double r = INFINITY;
+    int it = 0;
+    bool conv = false;
+    for (it = 1; it <= max_iters; ++it) {
+        tf_status s = step(p, cur, nxt, st);
+        if (s != TF_OK) return s;
+        stats_kernel<<<d.stats_blocks, dim3(32, 8), 0, st>>>(nxt, d.vol4, d.C, d.G, d.part);
+        finish_stats_kernel<<<(d.G + 127) / 128, 128, 0, st>>>(d.part, d.stats_blocks, d.G, d.gstats);
+        TF_CUDA(cudaMemsetAsync(&d.ctrl->residual_bits, 0, 8, st));
+        residual_kernel<<<d.stats_blocks, dim3(32, 8), 0, st>>>(nxt, cur, d.gstats, d.C, d.G, d.ctrl);
+        TF_CUDA(cudaGetLastError());
+        s = collect(p, st);
+        if (s != TF_OK) return s;
+        std::memcpy(&r, &d.ctrl_host->residual_bits, sizeof(double));
+        if (info && info->residual_history) info->residual_history[it - 1] = r;
+        std::swap(cur, nxt);
+        if (r < tol) {
+            conv = true;
+            break;
+        }
+    }
+    if (it > max_iters) it = max_iters;
+    // integrated flux of the final phi (already in gstats for the last iterate)
+    TF_CUDA(cudaMemcpyAsync(d.gstats_host, d.gstats, sizeof(double) * 4 * d.G, cudaMemcpyDeviceToHost, st));
+    if (host)
+        TF_CUDA(cudaMemcpyAsync(phi, cur, bytes, cudaMemcpyDeviceToHost, st));
+    else
+        TF_CUDA(cudaMemcpyAsync(phi, cur, bytes, cudaMemcpyDeviceToDevice, st));
+    TF_CUDA(cudaStreamSynchronize(st));
+    if (info) {
+        info->iterations = it;
+        info->converged = conv ? 1 : 0;
+        info->residual = r;
+        double tot = 0.0;
+        for (int g = 0; g < d.G; ++g) {
+            tot += d.gstats_host[4 * g + 1];
+            if (info->integrated_flux) info->integrated_flux[g] = d.gstats_host[4 * g + 1];
+        }
+        info->integrated_total = tot;
+    }
+    return conv ? TF_OK : fail(TF_ERR_NOT_CONVERGED, "source iteration reached max_iters");
+}
+
+tf_status device_psi(Problem &p, int32_t dir, void *out, void *stream)
+{
+    DeviceState &d = *p.dev;
+    if (dir < 0 || dir >= d.D) return fail(TF_ERR_ARG, "tf_problem_psi: direction out of range");
+    if (d.last_chunk < 0) return fail(TF_ERR_ARG, "tf_problem_psi: no sweep has run");
+    const int a0 = d.last_chunk * d.Dc;
+    if (dir < a0 || dir >= std::min(d.D, a0 + d.Dc))
+        return fail(TF_ERR_ARG, "tf_problem_psi: direction not in the last swept chunk");
+    TF_CUDA(cudaSetDevice(d.device));
+    const size_t per_dir = (size_t)d.C * d.G * 4 * d.tsize;
+    TF_CUDA(cudaMemcpyAsync(out, (const char *)d.psi + (size_t)(dir - a0) * per_dir, per_dir, cudaMemcpyDeviceToDevice,
+                            (cudaStream_t)stream));
+    TF_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    return TF_OK;
+}
+
+}  // namespace tf

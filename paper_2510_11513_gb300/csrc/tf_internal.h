@@ -1,0 +1,102 @@
+// Internal declarations of the tfsweep library (host C++ and CUDA).
+#pragma once
+
+#include <atomic>
+#include <cstdint>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "../../include/tfsweep.h"
+
+namespace tf {
+
+// ------------------------------------------------------------------ errors
+void set_error(const std::string &msg);
+tf_status fail(tf_status s, const std::string &msg);
+
+// ------------------------------------------------------------------ objects
+enum class Kind : int32_t { Mesh = 1, Quad = 2, Problem = 3 };
+
+struct Object {
+    explicit Object(Kind k) : kind(k) {}
+    virtual ~Object() = default;
+    Kind kind;
+    std::atomic<int32_t> refs{1};
+};
+
+// Host geometry of a tetrahedral mesh (FP64).
+struct Mesh : Object {
+    Mesh() : Object(Kind::Mesh) {}
+    int64_t nc = 0, nv = 0;
+    std::vector<double> xyz;        // [nv][3]
+    std::vector<int32_t> tets;      // [nc][4]
+    std::vector<double> vol;        // [nc]
+    std::vector<double> grad;       // [nc][4][3]  gradient of basis b_j
+    std::vector<double> normal;     // [nc][4][3]  area-weighted outward normal of face f (opposite vertex f)
+    std::vector<int32_t> nbr;       // [nc][4]
+    std::vector<int8_t> nbr_face;   // [nc][4]     face index of this face inside the neighbour
+    std::vector<int8_t> nbr_node;   // [nc][4][4]  neighbour-local index of local vertex i on face f (-1 if none)
+};
+
+struct Quad : Object {
+    Quad() : Object(Kind::Quad) {}
+    int32_t D = 0;
+    std::vector<double> omega;  // [D][3]
+    std::vector<double> w;      // [D]
+};
+
+tf_status build_mesh(int64_t nv, const double *xyz, int64_t nc, const int32_t *tets, Mesh &m);
+tf_status build_quadrature(int32_t n_polar, int32_t n_az, Quad &q);
+
+// Per-direction sweep graph and cell-block tasks.
+struct TaskGraph {
+    int32_t D = 0;
+    int32_t cells_per_task = 0;
+    int32_t max_level = 0;
+    std::vector<int32_t> dir_levels;       // [D] number of t-levels
+    // tasks, direction-major: tasks of direction a are [dir_task_begin[a], dir_task_begin[a+1])
+    std::vector<int64_t> dir_task_begin;   // [D+1]
+    std::vector<uint32_t> task_cell_begin; // [T]   into cell_list
+    std::vector<uint16_t> task_ncell;      // [T]
+    std::vector<uint16_t> task_dir;        // [T]
+    std::vector<int32_t> task_level;       // [T]
+    std::vector<int32_t> task_indeg;       // [T]   distinct upwind tasks
+    std::vector<int32_t> task_blevel;      // [T]   longest path (in t-levels) from the task to a sink
+    std::vector<uint64_t> down_begin;      // [T+1] into down_list
+    std::vector<uint32_t> down_list;       // downwind task ids (global)
+    std::vector<uint32_t> cell_list;       // (cell << 4) | inflow mask, [D * nc]
+    int64_t T() const { return (int64_t)task_ncell.size(); }
+};
+
+// Face classification and levels only (no tasks); returns TF_ERR_CYCLE on a cycle.
+tf_status classify_and_level(const Mesh &m, const Quad &q, uint8_t *inflow, int32_t *level);
+tf_status build_task_graph(const Mesh &m, const Quad &q, int32_t cells_per_task, TaskGraph &g);
+
+struct DeviceState;  // defined in the CUDA part
+
+struct Problem : Object {
+    Problem() : Object(Kind::Problem) {}
+    ~Problem() override;
+    Mesh *mesh = nullptr;
+    Quad *quad = nullptr;
+    tf_options opt{};
+    int32_t G = 0, M = 0;
+    bool has_S1 = false, has_inflow = false;
+    TaskGraph graph;
+    DeviceState *dev = nullptr;
+    tf_stats stats{};
+};
+
+void retain(Object *o);
+void release(Object *o);
+
+// CUDA side (sweep.cu)
+tf_status device_create(Problem &p, const int32_t *cell_material, const double *sigma_t, const double *sigma_s,
+                        const double *Q, const double *S1, const double *psi_inflow);
+void device_destroy(Problem &p);
+tf_status device_sweep(Problem &p, const double *phi_in, double *phi_out, void *stream);
+tf_status device_iterate(Problem &p, double tol, int32_t max_iters, double *phi, tf_iter_info *info, void *stream);
+tf_status device_psi(Problem &p, int32_t dir, void *out, void *stream);
+
+}  // namespace tf

@@ -1,0 +1,333 @@
+"""ctypes binding of the tfsweep C ABI (include/tfsweep.h).
+
+Argument marshalling only: every computation happens in libtfsweep.so.  The
+functions named tf_* mirror the C calls one to one; the small classes below
+(Mesh, Quadrature, Problem) only own handles and convert arrays.
+
+Arrays: host inputs are numpy arrays (converted to the C types and made
+contiguous).  Scalar-flux buffers for tf_sweep / tf_source_iterate are
+torch tensors (device or host, float64, shape [n_cells, n_groups, 4]) or
+numpy arrays (host); their data pointers are passed through unchanged.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+TF_OK, TF_ERR_ARG, TF_ERR_MESH, TF_ERR_CYCLE, TF_ERR_CUDA, TF_ERR_NOMEM, TF_ERR_TIMEOUT, \
+    TF_ERR_NOT_CONVERGED, TF_ERR_DEVICE = range(9)
+TF_FP32, TF_FP64 = 0, 1
+TF_PHI_PAIR, TF_PHI_DADD = 0, 1
+
+SYMBOLS = (
+    "tf_options_default", "tf_mesh_create", "tf_quadrature_create", "tf_problem_create", "tf_sweep",
+    "tf_source_iterate", "tf_destroy", "tf_mesh_geometry", "tf_quadrature_get", "tf_graph_levels",
+    "tf_problem_psi", "tf_problem_stats", "tf_status_string", "tf_last_error",
+)
+
+
+class tf_options(C.Structure):
+    _fields_ = [
+        ("precision", C.c_int32), ("device", C.c_int32), ("cells_per_task", C.c_int32), ("dir_chunk", C.c_int32),
+        ("warps_per_cta", C.c_int32), ("ctas_per_sm", C.c_int32), ("wait_limit_s", C.c_double),
+        ("phi_accumulate", C.c_int32), ("inject_stall", C.c_int32), ("psi_budget_gb", C.c_double),
+        ("task_order", C.c_int32), ("reserved_i", C.c_int32 * 7), ("reserved_d", C.c_double * 4),
+    ]
+
+
+class tf_iter_info(C.Structure):
+    _fields_ = [
+        ("iterations", C.c_int32), ("converged", C.c_int32), ("residual", C.c_double),
+        ("integrated_total", C.c_double), ("integrated_flux", C.POINTER(C.c_double)),
+        ("residual_history", C.POINTER(C.c_double)),
+    ]
+
+
+class tf_stats(C.Structure):
+    _fields_ = [
+        ("n_tasks", C.c_int64), ("n_units", C.c_int64), ("n_dirs", C.c_int32), ("max_level", C.c_int32),
+        ("n_chunks", C.c_int32), ("grid_ctas", C.c_int32), ("warps_per_cta", C.c_int32),
+        ("cells_per_task", C.c_int32), ("tasks_executed", C.c_int64), ("wait_polls", C.c_int64),
+        ("wait_seconds", C.c_double), ("busy_seconds", C.c_double), ("kernel_seconds", C.c_double),
+        ("mean_ready", C.c_double), ("source_event_seconds", C.c_double), ("sweep_event_seconds", C.c_double),
+        ("phi_event_seconds", C.c_double), ("cum_source_event_seconds", C.c_double),
+        ("cum_sweep_event_seconds", C.c_double), ("cum_phi_event_seconds", C.c_double), ("cum_steps", C.c_int64),
+        ("launches_per_step", C.c_int64), ("reserved_i", C.c_int32 * 6), ("reserved_d", C.c_double * 6),
+    ]
+
+
+class TfError(RuntimeError):
+    def __init__(self, status, where, detail=""):
+        self.status = status
+        super().__init__(f"{where}: status {status} ({_status_name(status)}) {detail}".strip())
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libtfsweep.so; builds it first if it is missing (needs nvcc).
+    Raises if the library cannot be built or loaded: there is no fallback."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.build() if build_if_missing else _build.LIB
+    if not os.path.exists(path):
+        raise ImportError(f"tfsweep: native library missing at {path}")
+    lib = C.CDLL(path)
+    vp, i32, i64, dp = C.c_void_p, C.c_int32, C.c_int64, C.c_double
+    H = C.c_void_p
+    lib.tf_options_default.argtypes = [C.POINTER(tf_options)]
+    lib.tf_options_default.restype = None
+    lib.tf_mesh_create.argtypes = [i64, vp, i64, vp, C.POINTER(H)]
+    lib.tf_quadrature_create.argtypes = [i32, i32, i32, vp, vp, C.POINTER(H)]
+    lib.tf_problem_create.argtypes = [H, H, i32, i32, vp, vp, vp, vp, vp, vp, C.POINTER(tf_options), C.POINTER(H)]
+    lib.tf_sweep.argtypes = [C.POINTER(H), i32, C.POINTER(vp), C.POINTER(vp), vp]
+    lib.tf_source_iterate.argtypes = [C.POINTER(H), i32, dp, i32, C.POINTER(vp), C.POINTER(tf_iter_info), vp]
+    lib.tf_destroy.argtypes = [H]
+    lib.tf_mesh_geometry.argtypes = [H, C.POINTER(i64), C.POINTER(i64), vp, vp, vp, vp]
+    lib.tf_quadrature_get.argtypes = [H, C.POINTER(i32), vp, vp]
+    lib.tf_graph_levels.argtypes = [H, H, vp, vp]
+    lib.tf_problem_psi.argtypes = [H, i32, vp, vp]
+    lib.tf_problem_stats.argtypes = [H, C.POINTER(tf_stats)]
+    lib.tf_status_string.argtypes = [i32]
+    lib.tf_status_string.restype = C.c_char_p
+    lib.tf_last_error.argtypes = []
+    lib.tf_last_error.restype = C.c_char_p
+    for name in SYMBOLS:
+        f = getattr(lib, name)
+        if f.restype is C.c_int:  # default restype: the status enum
+            f.restype = C.c_int
+    _lib = lib
+    return lib
+
+
+def _status_name(s):
+    try:
+        return load(False).tf_status_string(s).decode()
+    except Exception:  # pragma: no cover
+        return str(s)
+
+
+def _check(status, where):
+    if status != TF_OK:
+        detail = load().tf_last_error().decode()
+        raise TfError(status, where, detail)
+    return status
+
+
+def _ptr(a):
+    """Data pointer of a numpy array or torch tensor (None passes NULL)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr()
+    return a.ctypes.data
+
+
+def _stream_handle(stream):
+    if stream is None:
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return stream.cuda_stream
+    return int(stream)
+
+
+def options(**kw) -> tf_options:
+    o = tf_options()
+    load().tf_options_default(C.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise TypeError(f"unknown option {k}")
+        setattr(o, k, v)
+    return o
+
+
+# ----------------------------------------------------------------- raw calls
+def tf_mesh_create(xyz, tets):
+    xyz = np.ascontiguousarray(xyz, dtype=np.float64)
+    tets = np.ascontiguousarray(tets, dtype=np.int32)
+    h = C.c_void_p()
+    _check(load().tf_mesh_create(xyz.shape[0], _ptr(xyz), tets.shape[0], _ptr(tets), C.byref(h)), "tf_mesh_create")
+    return h
+
+
+def tf_quadrature_create(n_polar=0, n_azimuthal=0, omega=None, w=None):
+    h = C.c_void_p()
+    if omega is not None:
+        omega = np.ascontiguousarray(omega, dtype=np.float64)
+        w = np.ascontiguousarray(w, dtype=np.float64)
+        _check(load().tf_quadrature_create(0, 0, omega.shape[0], _ptr(omega), _ptr(w), C.byref(h)),
+               "tf_quadrature_create")
+    else:
+        _check(load().tf_quadrature_create(n_polar, n_azimuthal, 0, None, None, C.byref(h)), "tf_quadrature_create")
+    return h
+
+
+def tf_problem_create(mesh, quad, n_groups, n_materials, cell_material, sigma_t, sigma_s, Q, S1=None,
+                      psi_inflow=None, opt=None):
+    cm = np.ascontiguousarray(cell_material, dtype=np.int32)
+    st = np.ascontiguousarray(sigma_t, dtype=np.float64)
+    ss = np.ascontiguousarray(sigma_s, dtype=np.float64)
+    Qa = np.ascontiguousarray(Q, dtype=np.float64)
+    S1a = None if S1 is None else np.ascontiguousarray(S1, dtype=np.float64)
+    pia = None if psi_inflow is None else np.ascontiguousarray(psi_inflow, dtype=np.float64)
+    h = C.c_void_p()
+    o = opt if opt is not None else options()
+    _check(load().tf_problem_create(mesh, quad, int(n_groups), int(n_materials), _ptr(cm), _ptr(st), _ptr(ss),
+                                    _ptr(Qa), _ptr(S1a), _ptr(pia), C.byref(o), C.byref(h)), "tf_problem_create")
+    return h
+
+
+def tf_sweep(problems, phi_in, phi_out, stream=None):
+    n = len(problems)
+    hs = (C.c_void_p * n)(*[p.value if isinstance(p, C.c_void_p) else p for p in problems])
+    pin = (C.c_void_p * n)(*[_ptr(x) for x in phi_in])
+    pout = (C.c_void_p * n)(*[_ptr(x) for x in phi_out])
+    return _check(load().tf_sweep(hs, n, pin, pout, _stream_handle(stream)), "tf_sweep")
+
+
+def tf_source_iterate(problems, tol, max_iters, phi, infos=None, stream=None):
+    n = len(problems)
+    hs = (C.c_void_p * n)(*[p.value if isinstance(p, C.c_void_p) else p for p in problems])
+    ph = (C.c_void_p * n)(*[_ptr(x) for x in phi])
+    arr = (tf_iter_info * n)(*(infos or [tf_iter_info() for _ in range(n)]))
+    st = load().tf_source_iterate(hs, n, float(tol), int(max_iters), ph, arr, _stream_handle(stream))
+    if st not in (TF_OK, TF_ERR_NOT_CONVERGED):
+        _check(st, "tf_source_iterate")
+    return st, list(arr)
+
+
+def tf_destroy(h):
+    return _check(load().tf_destroy(h), "tf_destroy")
+
+
+def tf_mesh_geometry(mesh):
+    nc, nv = C.c_int64(), C.c_int64()
+    _check(load().tf_mesh_geometry(mesh, C.byref(nc), C.byref(nv), None, None, None, None), "tf_mesh_geometry")
+    C_ = nc.value
+    out = dict(vol=np.zeros(C_), normal=np.zeros((C_, 4, 3)), nbr=np.zeros((C_, 4), np.int32),
+               nbr_node=np.zeros((C_, 4, 4), np.int32))
+    _check(load().tf_mesh_geometry(mesh, None, None, _ptr(out["vol"]), _ptr(out["normal"]), _ptr(out["nbr"]),
+                                   _ptr(out["nbr_node"])), "tf_mesh_geometry")
+    return out
+
+
+def tf_quadrature_get(quad):
+    D = C.c_int32()
+    _check(load().tf_quadrature_get(quad, C.byref(D), None, None), "tf_quadrature_get")
+    om = np.zeros((D.value, 3))
+    w = np.zeros(D.value)
+    _check(load().tf_quadrature_get(quad, None, _ptr(om), _ptr(w)), "tf_quadrature_get")
+    return om, w
+
+
+def tf_graph_levels(mesh, quad, n_cells, n_dirs):
+    inflow = np.zeros((n_dirs, n_cells), np.uint8)
+    level = np.zeros((n_dirs, n_cells), np.int32)
+    _check(load().tf_graph_levels(mesh, quad, _ptr(inflow), _ptr(level)), "tf_graph_levels")
+    return inflow, level
+
+
+def tf_problem_psi(problem, direction, out, stream=None):
+    return _check(load().tf_problem_psi(problem, int(direction), _ptr(out), _stream_handle(stream)), "tf_problem_psi")
+
+
+def tf_problem_stats(problem):
+    s = tf_stats()
+    _check(load().tf_problem_stats(problem, C.byref(s)), "tf_problem_stats")
+    return {name: getattr(s, name) for name, _ in tf_stats._fields_ if not name.startswith("reserved")}
+
+
+# ------------------------------------------------------------- handle owners
+class _Handle:
+    h = None
+
+    def close(self):
+        if self.h is not None and _lib is not None:
+            _lib.tf_destroy(self.h)
+        self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Mesh(_Handle):
+    def __init__(self, xyz, tets):
+        self.h = tf_mesh_create(xyz, tets)
+        self.n_cells = int(np.asarray(tets).shape[0])
+        self.n_vertices = int(np.asarray(xyz).shape[0])
+
+    def geometry(self):
+        return tf_mesh_geometry(self.h)
+
+
+class Quadrature(_Handle):
+    def __init__(self, n_polar=0, n_azimuthal=0, omega=None, w=None):
+        self.h = tf_quadrature_create(n_polar, n_azimuthal, omega, w)
+        self.omega, self.w = tf_quadrature_get(self.h)
+        self.n_dirs = self.omega.shape[0]
+
+
+class Problem(_Handle):
+    """A transport problem on the device (tf_problem_create)."""
+
+    def __init__(self, mesh: Mesh, quad: Quadrature, n_groups, n_materials, cell_material, sigma_t, sigma_s, Q,
+                 S1=None, psi_inflow=None, **opts):
+        self.mesh, self.quad = mesh, quad
+        self.opt = options(**opts)
+        self.h = tf_problem_create(mesh.h, quad.h, n_groups, n_materials, cell_material, sigma_t, sigma_s, Q, S1,
+                                   psi_inflow, self.opt)
+        self.n_groups = int(n_groups)
+        self.n_cells = mesh.n_cells
+        self.n_dirs = quad.n_dirs
+        self.precision = self.opt.precision
+
+    @classmethod
+    def from_config(cls, cfg, S1=None, psi_inflow=None, omega=None, w=None, **opts):
+        mesh = Mesh(cfg["xyz"], cfg["tets"])
+        quad = Quadrature(omega=omega, w=w) if omega is not None else Quadrature(cfg["n_polar"], cfg["n_azimuthal"])
+        return cls(mesh, quad, cfg["n_groups"], cfg["n_materials"], cfg["cell_material"], cfg["sigma_t"],
+                   cfg["sigma_s"], cfg["Q"], S1=S1, psi_inflow=psi_inflow, **opts)
+
+    @property
+    def n_units(self):
+        return self.n_cells * self.n_dirs * self.n_groups
+
+    def sweep(self, phi_in, phi_out, stream=None):
+        tf_sweep([self.h], [phi_in], [phi_out], stream)
+        return phi_out
+
+    def source_iterate(self, phi, tol, max_iters, stream=None, history=False):
+        G = self.n_groups
+        ig = (C.c_double * G)()
+        hist = (C.c_double * max_iters)() if history else None
+        info = tf_iter_info()
+        info.integrated_flux = C.cast(ig, C.POINTER(C.c_double))
+        if hist is not None:
+            info.residual_history = C.cast(hist, C.POINTER(C.c_double))
+        st, out = tf_source_iterate([self.h], tol, max_iters, [phi], [info], stream)
+        i = out[0]
+        res = dict(status=st, iterations=i.iterations, converged=bool(i.converged), residual=i.residual,
+                   integrated_total=i.integrated_total, integrated_flux=np.array(ig[:]))
+        if hist is not None:
+            res["residual_history"] = np.array(hist[: i.iterations])
+        return res
+
+    def psi(self, direction, out, stream=None):
+        tf_problem_psi(self.h, direction, out, stream)
+        return out
+
+    def stats(self):
+        return tf_problem_stats(self.h)

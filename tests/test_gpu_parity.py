@@ -1,0 +1,185 @@
+"""Parity of the CUDA sweep (through the C ABI) with the FP64 CPU oracle.
+
+Tolerances (relative to the max-norm of the oracle result):
+  FP64 mode: 1e-11;  FP32 mode: 2e-5 (phi), the same for psi of one direction.
+Sizes span several tasks, ragged group counts (G not a multiple of 32, G < 32),
+ragged cell blocks and several direction chunks.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+from oracle_checks import FOUR_PI, mms_problem
+
+torch = pytest.importorskip("torch")
+import paper_2510_11513_gb300 as tf  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+TOL = {tf.TF_FP64: 1e-11, tf.TF_FP32: 2e-5}
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+
+
+def _rel(a, b):
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+def _seeded_phi(C, G, seed=11):
+    return np.random.default_rng(seed).uniform(0.0, 1.0, (C, G, 4))
+
+
+@pytest.mark.parametrize("precision", [tf.TF_FP64, tf.TF_FP32])
+@pytest.mark.parametrize("G,cells_per_task,dir_chunk", [(4, 0, 0), (37, 3, 0), (1, 1, 0), (5, 7, 11), (64, 0, 13)])
+def test_one_sweep_matches_oracle(precision, G, cells_per_task, dir_chunk):
+    cfg = W.small_box(n=4 if G >= 37 else 6, G=G, n_polar=4, n_az=8)
+    P = oracle.Problem(cfg)
+    phi_in = _seeded_phi(P.C, G)
+    ref = P.transport_step(phi_in, threads=8)
+    prob = tf.Problem.from_config(cfg, precision=precision, cells_per_task=cells_per_task, dir_chunk=dir_chunk)
+    out = torch.zeros_like(_dev(phi_in))
+    prob.sweep(_dev(phi_in), out)
+    assert _rel(out.cpu().numpy(), ref) < TOL[precision]
+    st = prob.stats()
+    assert st["tasks_executed"] == st["n_tasks"]
+
+
+@pytest.mark.parametrize("precision", [tf.TF_FP64, tf.TF_FP32])
+def test_psi_of_every_direction_matches_oracle(precision):
+    cfg = W.two_material_box(n=6, G=8, n_polar=2, n_az=8)
+    P = oracle.Problem(cfg)
+    phi_in = _seeded_phi(P.C, 8, seed=3)
+    q = P.source(phi_in)
+    prob = tf.Problem.from_config(cfg, precision=precision)
+    out = torch.zeros_like(_dev(phi_in))
+    prob.sweep(_dev(phi_in), out)
+    dt = torch.float64 if precision == tf.TF_FP64 else torch.float32
+    buf = torch.empty((P.C, 8, 4), dtype=dt, device="cuda")
+    for a in range(P.D):
+        ref = P.sweep_direction(a, q)
+        got = prob.psi(a, buf).double().cpu().numpy()
+        assert _rel(got, ref) < TOL[precision], a
+
+
+@pytest.mark.parametrize("precision", [tf.TF_FP64, tf.TF_FP32])
+def test_manufactured_solution(precision):
+    rng = np.random.default_rng(17)
+    xyz, tets = W.jittered_kuhn_mesh(4, 1234)
+    C, G = len(tets), 3
+    base = dict(xyz=xyz, tets=tets, n_groups=G, n_materials=2,
+                cell_material=rng.integers(0, 2, C).astype(np.int32), sigma_t=rng.uniform(0.5, 2.0, (2, G)),
+                sigma_s=rng.uniform(0.0, 0.15, (2, G, G)), Q=np.zeros((C, G, 4)), n_polar=4, n_azimuthal=8)
+    cfg, S1, psi_v, exact = mms_problem(base)
+    prob = tf.Problem.from_config(cfg, S1=S1, psi_inflow=psi_v, precision=precision)
+    phi_exact = FOUR_PI * exact
+    out = torch.zeros((C, G, 4), dtype=torch.float64, device="cuda")
+    prob.sweep(_dev(phi_exact), out)
+    tol = 1e-12 if precision == tf.TF_FP64 else 2e-6
+    assert _rel(out.cpu().numpy(), phi_exact) < tol
+    phi = torch.zeros_like(out)
+    res = prob.source_iterate(phi, 1e-12 if precision == tf.TF_FP64 else 1e-6, 300)
+    assert res["converged"]
+    assert _rel(phi.cpu().numpy(), phi_exact) < (1e-10 if precision == tf.TF_FP64 else 2e-5)
+
+
+def test_source_iteration_fp64_converged_matches_oracle():
+    """small_box 8^3, 32 directions, 4 groups, downscatter: both run to 1e-12."""
+    cfg = W.small_box()
+    P = oracle.Problem(cfg)
+    ref, it_ref, r_ref = P.source_iterate(1e-12, 500, threads=8)
+    prob = tf.Problem.from_config(cfg, precision=tf.TF_FP64)
+    phi = torch.zeros((P.C, P.G, 4), dtype=torch.float64, device="cuda")
+    res = prob.source_iterate(phi, 1e-12, 500, history=True)
+    assert res["converged"]
+    assert abs(res["iterations"] - it_ref) <= 1
+    assert _rel(phi.cpu().numpy(), ref) < 1e-11
+    ig, tot, _, _ = P.integrated_flux(ref)
+    assert np.max(np.abs(res["integrated_flux"] - ig) / np.abs(ig)) < 1e-11
+    assert abs(res["integrated_total"] - tot) / tot < 1e-11
+
+
+def test_same_iterations_fp32_and_fp64_vs_oracle():
+    """(i) after the same number of sweeps from the same phi0 both precisions match the oracle."""
+    cfg = W.two_material_box(n=8, G=16, n_polar=4, n_az=8)
+    P = oracle.Problem(cfg)
+    phi0 = _seeded_phi(P.C, 16, seed=5)
+    ref = phi0.copy()
+    for _ in range(6):
+        ref = P.transport_step(ref, threads=8)
+    for prec in (tf.TF_FP64, tf.TF_FP32):
+        prob = tf.Problem.from_config(cfg, precision=prec)
+        phi = _dev(phi0)
+        res = prob.source_iterate(phi, 0.0, 6)
+        assert res["iterations"] == 6 and not res["converged"]
+        assert _rel(phi.cpu().numpy(), ref) < TOL[prec]
+
+
+def test_fp32_converged_two_material_within_2e5():
+    cfg = W.two_material_box(n=12, G=32, n_polar=4, n_az=8)
+    P = oracle.Problem(cfg)
+    ref, _, _ = P.source_iterate(1e-10, 1000, threads=8)
+    prob = tf.Problem.from_config(cfg, precision=tf.TF_FP32)
+    phi = torch.zeros((P.C, P.G, 4), dtype=torch.float64, device="cuda")
+    res = prob.source_iterate(phi, 1e-6, 1000)
+    assert res["converged"]
+    # the stopping test leaves an iteration error of about tol; the FP32 error is below 2e-5
+    assert _rel(phi.cpu().numpy(), ref) < 2e-5
+
+
+def test_phi_accumulation_modes_agree():
+    cfg = W.small_box(n=6, G=8, n_polar=4, n_az=8)
+    phi_in = _seeded_phi(6 * 216, 8)
+    outs = []
+    for mode in (tf.TF_PHI_PAIR, tf.TF_PHI_DADD):
+        prob = tf.Problem.from_config(cfg, precision=tf.TF_FP32, phi_accumulate=mode)
+        out = torch.zeros((6 * 216, 8, 4), dtype=torch.float64, device="cuda")
+        prob.sweep(_dev(phi_in), out)
+        outs.append(out.cpu().numpy())
+    assert _rel(outs[0], outs[1]) < 1e-12
+
+
+def test_host_buffers_match_device_buffers():
+    cfg = W.small_box(n=5, G=6, n_polar=2, n_az=8)
+    prob = tf.Problem.from_config(cfg, precision=tf.TF_FP64)
+    C = 6 * 125
+    phi_in = _seeded_phi(C, 6)
+    out_h = np.zeros((C, 6, 4))
+    prob.sweep(phi_in, out_h)
+    out_d = torch.zeros((C, 6, 4), dtype=torch.float64, device="cuda")
+    prob.sweep(_dev(phi_in), out_d)
+    assert np.array_equal(out_h, out_d.cpu().numpy())
+    pinned = torch.from_numpy(phi_in).pin_memory()
+    out_p = torch.zeros((C, 6, 4), dtype=torch.float64).pin_memory()
+    prob.sweep(pinned, out_p)
+    assert np.array_equal(out_p.numpy(), out_h)
+
+
+def test_device_wait_limit_returns_timeout_and_handle_stays_usable():
+    """Fault injection on the host side: no task is seeded, so every device wait
+    runs out after wait_limit_s; the kernel returns and the status says so."""
+    cfg = W.small_box(n=3, G=2, n_polar=2, n_az=8)
+    C = 6 * 27
+    bad = tf.Problem.from_config(cfg, precision=tf.TF_FP64, inject_stall=1, wait_limit_s=0.25)
+    phi_in = _dev(_seeded_phi(C, 2))
+    out = torch.zeros_like(phi_in)
+    with pytest.raises(tf.TfError) as e:
+        bad.sweep(phi_in, out)
+    assert e.value.status == tf.TF_ERR_TIMEOUT
+    good = tf.Problem.from_config(cfg, precision=tf.TF_FP64)
+    good.sweep(phi_in, out)
+    ref = oracle.Problem(cfg).transport_step(phi_in.cpu().numpy())
+    assert _rel(out.cpu().numpy(), ref) < 1e-11
+
+
+def test_aliasing_phi_in_equals_phi_out():
+    cfg = W.small_box(n=4, G=4, n_polar=2, n_az=8)
+    C = 6 * 64
+    phi_in = _seeded_phi(C, 4)
+    prob = tf.Problem.from_config(cfg, precision=tf.TF_FP64)
+    buf = _dev(phi_in)
+    prob.sweep(buf, buf)
+    ref = oracle.Problem(cfg).transport_step(phi_in)
+    assert _rel(buf.cpu().numpy(), ref) < 1e-11
