@@ -142,11 +142,25 @@ def cpu_oracle_sample(cfg, n_dirs=None, threads=None):
                       f"{dt:.1f} s wall on {used} threads"}
 
 
+def make_config(args):
+    """The named workload, optionally resized (--n, --groups, --polar, --azimuthal) for profiling runs."""
+    kw = {}
+    if args.n:
+        kw["n"] = args.n
+    if args.groups:
+        kw["G"] = args.groups
+    if args.polar:
+        kw["n_polar"] = args.polar
+    if args.azimuthal:
+        kw["n_az"] = args.azimuthal
+    return W.CONFIGS[args.config](**kw)
+
+
 def run_reference(args):
     world, rank, _ = _dist()
     if rank != 0:
         return
-    cfg = W.CONFIGS[args.config]()
+    cfg = make_config(args)
     threads = os.cpu_count() or 1
     # warm-up steps (untimed), then timed steps; each step is a bounded sample
     for _ in range(args.warmup):
@@ -181,7 +195,7 @@ def run_ours(args):
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    cfg = W.CONFIGS[args.config]()
+    cfg = make_config(args)
     prec = tf.TF_FP64 if args.precision == "fp64" else tf.TF_FP32
     t_setup = time.perf_counter()
     prob = tf.Problem.from_config(cfg, precision=prec, device=local, cells_per_task=args.cells_per_task,
@@ -299,6 +313,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-compare", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--n", type=int, default=0, help="hexes per box edge (default: the workload's)")
+    ap.add_argument("--groups", type=int, default=0)
+    ap.add_argument("--polar", type=int, default=0)
+    ap.add_argument("--azimuthal", type=int, default=0)
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)  # at least 3 untimed warm-up steps
     if args.impl == "reference":

@@ -155,6 +155,7 @@ template <class T> struct SweepArgs {
     uint32_t task_begin, task_end;
     unsigned long long n_tasks;  // tasks in the chunk
     unsigned long long wait_limit_ns;
+    int32_t max_cells;           // largest task (cells)
 };
 
 // Solve one 4x4 system by Gaussian elimination without pivoting: the
@@ -183,17 +184,18 @@ template <class T> __device__ __forceinline__ void solve4(T a[4][4], T b[4], T x
 }
 
 template <class T> struct CellSetup {
-    int64_t c;
+    uint32_t c;
     uint32_t mask;
-    T A0[4][4];  // streaming + inflow-face part of the matrix (group independent)
-    T t[4];      // |Omega.N_f| / 12 on inflow faces, 0 otherwise
-    T mv;
+    T P[4];   // (V/4) Omega.grad b_j
+    T t[4];   // |Omega.N_f| / 12 on inflow faces, 0 otherwise
+    T tt;     // sum_f t_f
+    T mv;     // V/20
     int32_t mat;
     uint32_t nn;
     int32_t nbr[4];
 };
 
-// Group-independent part of the local system of cell c for direction Omega.
+// Group-independent part of the local system of cell c for direction Omega:
 //   A_ij = (V/4) Omega.grad b_j + sum_{f inflow, i,j != f} (|s_f|/12)(1 + delta_ij) + sigma (V/20)(1 + delta_ij)
 // With t_f = |s_f|/12 on inflow faces and T = sum_f t_f the face part is
 // T - t_i - t_j off the diagonal and 2 (T - t_i) on it.
@@ -210,19 +212,15 @@ __device__ __forceinline__ void cell_setup(const SweepArgs<T> &A, uint32_t entry
 #pragma unroll
     for (int k = 0; k < (int)(sizeof(CellGeo<T>) / 16); ++k) U.u[k] = __ldg(src + k);
     const CellGeo<T> &g = U.g;
-    T P[4], tt = T(0);
+    s.tt = T(0);
 #pragma unroll
-    for (int j = 0; j < 4; ++j) P[j] = ox * g.gx[j] + oy * g.gy[j] + oz * g.gz[j];
+    for (int j = 0; j < 4; ++j) s.P[j] = ox * g.gx[j] + oy * g.gy[j] + oz * g.gz[j];
 #pragma unroll
     for (int f = 0; f < 4; ++f) {
         const T sf = ox * g.nx[f] + oy * g.ny[f] + oz * g.nz[f];
         s.t[f] = ((s.mask >> f) & 1u) ? fabs(sf) * T(1.0 / 12.0) : T(0);
-        tt += s.t[f];
+        s.tt += s.t[f];
     }
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) s.A0[i][j] = P[j] + (i == j ? T(2) * (tt - s.t[i]) : tt - s.t[i] - s.t[j]);
     s.mv = g.mv;
     s.mat = g.mat;
     s.nn = g.nn;
@@ -230,17 +228,41 @@ __device__ __forceinline__ void cell_setup(const SweepArgs<T> &A, uint32_t entry
     for (int f = 0; f < 4; ++f) s.nbr[f] = g.nbr[f];
 }
 
-// Solve one (cell, direction, group) unit and store psi.
+// Inputs of one (cell, direction, group) unit, loaded before any arithmetic so
+// that the loads of several units are in flight together.
+template <class T> struct UnitIn {
+    V4<T> q;
+    V4<T> u[4];  // upwind cell's psi across face f (zero if not an interior inflow face)
+    T sig;
+};
+
 template <class T>
-__device__ __forceinline__ void solve_unit(const SweepArgs<T> &A, const CellSetup<T> &s, int g, size_t psi_dir,
-                                           T ox, T oy, T oz)
+__device__ __forceinline__ void unit_load(const SweepArgs<T> &A, const CellSetup<T> &s, int g, size_t psi_dir,
+                                          UnitIn<T> &in)
 {
     const int G = A.G;
-    const T sig = __ldg(A.sigma_t + (size_t)s.mat * G + g);
-    const T sv = sig * s.mv;
-    const V4<T> q4 = ld_ro(A.q + (size_t)s.c * G + g);
-    const T qs = q4.x + q4.y + q4.z + q4.w;
-    T b[4] = {s.mv * (q4.x + qs), s.mv * (q4.y + qs), s.mv * (q4.z + qs), s.mv * (q4.w + qs)};
+    in.sig = __ldg(A.sigma_t + (size_t)s.mat * G + g);
+    in.q = ld_ro(A.q + (size_t)s.c * G + g);
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+        const bool up = ((s.mask >> f) & 1u) && s.nbr[f] >= 0;
+        if (up) {
+            in.u[f] = ld_l2(A.psi + (psi_dir + (size_t)s.nbr[f]) * G + g);
+        } else {
+            in.u[f].x = in.u[f].y = in.u[f].z = in.u[f].w = T(0);
+        }
+    }
+}
+
+// Assemble and solve one unit from its loaded inputs; store psi.
+template <class T>
+__device__ __forceinline__ void unit_solve(const SweepArgs<T> &A, const CellSetup<T> &s, int g, size_t psi_dir,
+                                           const UnitIn<T> &in, T ox, T oy, T oz)
+{
+    const int G = A.G;
+    const T sv = in.sig * s.mv;
+    const T qs = (in.q.x + in.q.y) + (in.q.z + in.q.w);
+    T b[4] = {s.mv * (in.q.x + qs), s.mv * (in.q.y + qs), s.mv * (in.q.z + qs), s.mv * (in.q.w + qs)};
     if (A.S1) {
         const V4<T> s1 = ld_ro(A.S1 + (size_t)s.c * G + g);
         const T os = T(5) * s.mv * (ox * s1.x + oy * s1.y + oz * s1.z);  // (V/4) Omega.S1
@@ -250,35 +272,31 @@ __device__ __forceinline__ void solve_unit(const SweepArgs<T> &A, const CellSetu
 #pragma unroll
     for (int f = 0; f < 4; ++f) {
         if (!((s.mask >> f) & 1u)) continue;
-        const int n = s.nbr[f];
         T up[4] = {T(0), T(0), T(0), T(0)};
-        bool have = false;
-        if (n >= 0) {
-            const V4<T> u = ld_l2(A.psi + (psi_dir + (size_t)n) * G + g);
+        if (s.nbr[f] >= 0) {
 #pragma unroll
             for (int i = 0; i < 4; ++i)
-                if (i != f) up[i] = comp(u, (int)((s.nn >> (2 * (4 * f + i))) & 3u));
-            have = true;
+                if (i != f) up[i] = comp(in.u[f], (int)((s.nn >> (2 * (4 * f + i))) & 3u));
         } else if (A.psi_in) {
             const int4 tv = __ldg(A.tets + s.c);
             const int vi[4] = {tv.x, tv.y, tv.z, tv.w};
 #pragma unroll
             for (int i = 0; i < 4; ++i)
                 if (i != f) up[i] = __ldg(A.psi_in + (size_t)vi[i] * G + g);
-            have = true;
+        } else {
+            continue;  // vacuum: no inflow
         }
-        if (have) {
-            const T U = up[0] + up[1] + up[2] + up[3];
+        const T U = (up[0] + up[1]) + (up[2] + up[3]);
 #pragma unroll
-            for (int i = 0; i < 4; ++i)
-                if (i != f) b[i] += s.t[f] * (up[i] + U);
-        }
+        for (int i = 0; i < 4; ++i)
+            if (i != f) b[i] += s.t[f] * (up[i] + U);
     }
     T a[4][4];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) a[i][j] = s.A0[i][j] + (i == j ? T(2) * sv : sv);
+        for (int j = 0; j < 4; ++j)
+            a[i][j] = s.P[j] + (i == j ? T(2) * (s.tt - s.t[i] + sv) : (s.tt - s.t[i] - s.t[j]) + sv);
     T x[4];
     solve4(a, b, x);
     V4<T> out;
@@ -289,25 +307,109 @@ __device__ __forceinline__ void solve_unit(const SweepArgs<T> &A, const CellSetu
     st_psi(A.psi + (psi_dir + (size_t)s.c) * G + g, out);
 }
 
+__device__ __forceinline__ void prefetch_l1(const void *p) { asm volatile("prefetch.global.L1 [%0];" ::"l"(p)); }
+__device__ __forceinline__ void prefetch_l2(const void *p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
+
+// One task when every cell's groups fill whole warps (G a multiple of 32 and
+// at most 64 cells per task): lane l solves groups l, l+32, ... of each cell,
+// two units' loads in flight at once; the next cell's record and source rows
+// are prefetched into L1 while the current cell is solved.
+template <class T>
+__device__ __forceinline__ void run_task_wide(const SweepArgs<T> &A, uint4 ti, int lane, T ox, T oy, T oz,
+                                              size_t psi_dir)
+{
+    const uint32_t ncell = ti.y & 0xffffu;
+    const unsigned FULL = 0xffffffffu;
+    const uint32_t e_lo = lane < (int)ncell ? __ldg(A.cells + ti.x + lane) : 0u;
+    const uint32_t e_hi = lane + 32 < (int)ncell ? __ldg(A.cells + ti.x + 32 + lane) : 0u;
+    const int G = A.G;
+    const size_t row_bytes = (size_t)G * sizeof(V4<T>);
+    for (uint32_t k = 0; k < ncell; ++k) {
+        const uint32_t e = __shfl_sync(FULL, k < 32 ? e_lo : e_hi, k & 31);
+        if (k + 1 < ncell) {
+            const uint32_t e1 = __shfl_sync(FULL, k + 1 < 32 ? e_lo : e_hi, (k + 1) & 31);
+            const uint32_t c1 = e1 >> 4;
+            const char *qrow = reinterpret_cast<const char *>(A.q + (size_t)c1 * G);
+            for (size_t off = (size_t)lane * 128; off < row_bytes; off += 32 * 128) prefetch_l1(qrow + off);
+            if (lane < (int)((sizeof(CellGeo<T>) + 127) / 128))
+                prefetch_l1(reinterpret_cast<const char *>(A.geo + c1) + 128 * lane);
+        }
+        CellSetup<T> s;
+        cell_setup(A, e, ox, oy, oz, s);
+        int g = lane;
+        for (; g + 32 < G; g += 64) {
+            UnitIn<T> in0, in1;
+            unit_load(A, s, g, psi_dir, in0);
+            unit_load(A, s, g + 32, psi_dir, in1);
+            unit_solve(A, s, g, psi_dir, in0, ox, oy, oz);
+            unit_solve(A, s, g + 32, psi_dir, in1, ox, oy, oz);
+        }
+        if (g < G) {
+            UnitIn<T> in0;
+            unit_load(A, s, g, psi_dir, in0);
+            unit_solve(A, s, g, psi_dir, in0, ox, oy, oz);
+        }
+    }
+}
+
+// Any group count and task size: units u = lane, lane + 32, ... over
+// (cell k, group g), g fastest; the cell setup is redone when k changes.
+template <class T>
+__device__ __forceinline__ void run_task_generic(const SweepArgs<T> &A, uint4 ti, int lane, T ox, T oy, T oz,
+                                                 size_t psi_dir)
+{
+    const uint32_t ncell = ti.y & 0xffffu;
+    int g = lane;
+    uint32_t k = 0;
+    while (g >= A.G) {
+        g -= A.G;
+        ++k;
+    }
+    uint32_t kc = 0xffffffffu;
+    CellSetup<T> s;
+    while (k < ncell) {
+        if (k != kc) {
+            cell_setup(A, __ldg(A.cells + ti.x + k), ox, oy, oz, s);
+            kc = k;
+        }
+        UnitIn<T> in;
+        unit_load(A, s, g, psi_dir, in);
+        unit_solve(A, s, g, psi_dir, in, ox, oy, oz);
+        g += 32;
+        while (g >= A.G) {
+            g -= A.G;
+            ++k;
+        }
+    }
+}
+
+__device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
+
 // Persistent sweep: every warp repeatedly claims a ticket (the next queue
 // slot), waits until that slot holds a ready task, executes it with lanes
 // spanning (cell, group) units, then decrements the counters of the task's
 // downwind blocks; the decrement that reaches zero enqueues that block
 // (work-first generation, Algorithm 1; atomic counters, Sec. 3.5).
-// Termination: exactly n_tasks slots get filled, so a warp whose ticket is
-// >= n_tasks exits.  Every wait is bounded by wait_limit_ns.
-template <class T> __global__ void __launch_bounds__(256) sweep_kernel(const SweepArgs<T> A)
+// A warp claims its next ticket as soon as it starts a task, so the claim's
+// latency overlaps the task.  Termination: exactly n_tasks slots get filled,
+// so a warp whose ticket is >= n_tasks exits.  Every wait is bounded by
+// wait_limit_ns.
+template <class T> __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 3) sweep_kernel(const SweepArgs<T> A)
 {
     const int lane = threadIdx.x & 31;
     const unsigned FULL = 0xffffffffu;
     const unsigned epoch = *(const volatile unsigned *)&A.ctrl->epoch;
-    unsigned long long polls = 0, wait_ns = 0, busy_ns = 0, done = 0, depth = 0, pops = 0;
+    const bool wide = (A.G % 32) == 0 && A.max_cells <= 64;
+    // per-warp counters live in shared memory (lane 0 updates them) to spare registers
+    __shared__ unsigned long long wstat[8][6];  // polls, wait_ns, busy_ns, done, depth, pops
+    unsigned long long *ws = wstat[threadIdx.x >> 5];
+    if (lane < 6) ws[lane] = 0;
+    __syncwarp();
     const unsigned long long t_start = globaltimer();
-    for (;;) {
-        unsigned long long ticket = 0;
-        if (lane == 0) ticket = atomicAdd(&A.ctrl->head, 1ull);
-        ticket = __shfl_sync(FULL, ticket, 0);
-        if (ticket >= A.n_tasks) break;
+    unsigned long long ticket = 0;
+    if (lane == 0) ticket = atomicAdd(&A.ctrl->head, 1ull);
+    ticket = __shfl_sync(FULL, ticket, 0);
+    while (ticket < A.n_tasks) {
         unsigned task = 0;
         int stop = 0;
         if (lane == 0) {
@@ -318,7 +420,7 @@ template <class T> __global__ void __launch_bounds__(256) sweep_kernel(const Swe
                 for (;;) {
                     __nanosleep(ns);
                     if (ns < 2048) ns <<= 1;
-                    ++polls;
+                    ++ws[0];
                     v = ld_acquire(A.slots + ticket);
                     if ((unsigned)(v >> 32) == epoch) break;
                     if (ld_volatile(&A.ctrl->error)) {
@@ -333,10 +435,10 @@ template <class T> __global__ void __launch_bounds__(256) sweep_kernel(const Swe
                 }
             }
             const unsigned long long t1 = globaltimer();
-            wait_ns += t1 - t0;
+            ws[1] += t1 - t0;
             const long long dq = (long long)(ld_volatile(&A.ctrl->tail) - ticket);
-            depth += dq > 0 ? (unsigned long long)dq : 0ull;
-            ++pops;
+            ws[4] += dq > 0 ? (unsigned long long)dq : 0ull;
+            ++ws[5];
             task = (unsigned)v;
             if (!stop && (task < A.task_begin || task >= A.task_end)) {
                 atomicCAS(&A.ctrl->error, 0, (int)TF_ERR_DEVICE);
@@ -347,36 +449,22 @@ template <class T> __global__ void __launch_bounds__(256) sweep_kernel(const Swe
         stop = __shfl_sync(FULL, stop, 0);
         if (stop) break;
         task = __shfl_sync(FULL, task, 0);
-        const unsigned long long tb = globaltimer();
+        unsigned long long tb = 0;
+        if (lane == 0) tb = globaltimer();
+        // claim the next ticket now; its latency overlaps this task
+        unsigned long long next = 0;
+        if (lane == 0) next = atomicAdd(&A.ctrl->head, 1ull);
 
         const uint4 ti = __ldg(A.task + task);
-        const uint32_t ncell = ti.y & 0xffffu, dir = ti.y >> 16;
+        const uint32_t dir = ti.y >> 16;
         const V4<T> om = ld_ro(A.omega + dir);
-        const T ox = om.x, oy = om.y, oz = om.z;
         const size_t psi_dir = (size_t)(dir - (uint32_t)A.dir_begin) * (size_t)A.C;
-        // units u = lane, lane + 32, ... over (cell k, group g), g fastest
-        int g = lane;
-        uint32_t k = 0;
-        while (g >= A.G) {
-            g -= A.G;
-            ++k;
-        }
-        uint32_t kc = 0xffffffffu;
-        CellSetup<T> s;
-        while (k < ncell) {
-            if (k != kc) {
-                cell_setup(A, __ldg(A.cells + ti.x + k), ox, oy, oz, s);
-                kc = k;
-            }
-            solve_unit(A, s, g, psi_dir, ox, oy, oz);
-            g += 32;
-            while (g >= A.G) {
-                g -= A.G;
-                ++k;
-            }
-        }
+        if (wide)
+            run_task_wide(A, ti, lane, om.x, om.y, om.z, psi_dir);
+        else
+            run_task_generic(A, ti, lane, om.x, om.y, om.z, psi_dir);
         // release: every lane's psi stores are ordered before any counter decrement
-        __threadfence();
+        fence_acq_rel_gpu();
         __syncwarp();
         for (uint32_t e = lane; e < ti.w; e += 32) {
             const uint32_t d = __ldg(A.down + ti.z + e);
@@ -389,17 +477,21 @@ template <class T> __global__ void __launch_bounds__(256) sweep_kernel(const Swe
             }
         }
         __syncwarp();
-        busy_ns += globaltimer() - tb;
-        ++done;
+        if (lane == 0) {
+            ws[2] += globaltimer() - tb;
+            ++ws[3];
+        }
+        ticket = __shfl_sync(FULL, next, 0);
     }
     const unsigned long long t_end = globaltimer();
+    __syncwarp();
     if (lane == 0) {
-        atomicAdd(&A.ctrl->tasks_done, done);
-        atomicAdd(&A.ctrl->polls, polls);
-        atomicAdd(&A.ctrl->wait_ns, wait_ns);
-        atomicAdd(&A.ctrl->busy_ns, busy_ns);
-        atomicAdd(&A.ctrl->depth_sum, depth);
-        atomicAdd(&A.ctrl->pops, pops);
+        atomicAdd(&A.ctrl->tasks_done, ws[3]);
+        atomicAdd(&A.ctrl->polls, ws[0]);
+        atomicAdd(&A.ctrl->wait_ns, ws[1]);
+        atomicAdd(&A.ctrl->busy_ns, ws[2]);
+        atomicAdd(&A.ctrl->depth_sum, ws[4]);
+        atomicAdd(&A.ctrl->pops, ws[5]);
         atomicMin(&A.ctrl->t_first, t_start);
         atomicMax(&A.ctrl->t_last, t_end);
     }
@@ -930,7 +1022,7 @@ tf_status device_create(Problem &p, const int32_t *cell_material, const double *
     TF_CUDA(cudaMemset(d.slots, 0, (size_t)d.max_chunk_tasks * 8));
     if ((s = dmalloc(d, &d.psi, per_dir * Dc)) != TF_OK) return s;
     // persistent grid: resident CTAs per SM x SMs
-    d.wpc = p.opt.warps_per_cta > 0 ? std::min(p.opt.warps_per_cta, 8) : 4;
+    d.wpc = p.opt.warps_per_cta > 0 ? std::min(p.opt.warps_per_cta, 4) : 4;  // launch bounds: 128 threads
     int per_sm = 0;
     cudaError_t e = d.fp64 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_kernel<double>, 32 * d.wpc, 0)
                            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_kernel<float>, 32 * d.wpc, 0);
@@ -1028,6 +1120,7 @@ template <class T> tf_status launch_step(Problem &p, const double *phi_in, doubl
         A.task_end = (uint32_t)t1;
         A.n_tasks = (unsigned long long)(t1 - t0);
         A.wait_limit_ns = (unsigned long long)(p.opt.wait_limit_s * 1e9);
+        A.max_cells = p.graph.cells_per_task;
         TF_CUDA(cudaEventRecord(d.ev_start[1 + 2 * k], st));
         sweep_kernel<T><<<d.grid, 32 * d.wpc, 0, st>>>(A);
         TF_CUDA(cudaGetLastError());
