@@ -76,7 +76,11 @@ typedef struct {
     double psi_budget_gb;    /* device memory allowed for the angular-flux store; 0 = 80 % of free memory */
     int32_t task_order;      /* 0 = FIFO ready queue, seeds longest-critical-path first */
     int32_t reserved_i[7];
-    double reserved_d[4];
+    double residual_floor;   /* stopping-test denominator floor, as a fraction of the group's max |phi|:
+                              * 1 (the default; 0 also means 1) = per-group max-norm relative change,
+                              * 1e-10 = pointwise relative change (unreachable in FP32 where DG
+                              * undershoots put |phi| near 0) */
+    double reserved_d[3];
 } tf_options;
 
 /* Fills *opt with the defaults above. */
@@ -86,7 +90,7 @@ void tf_options_default(tf_options *opt);
 typedef struct {
     int32_t iterations;        /* sweeps performed */
     int32_t converged;         /* 1 if the stopping test fell below tol */
-    double residual;           /* last max relative change of phi (floor 1e-10 x per-group max) */
+    double residual;           /* last value of the stopping test r (see tf_source_iterate) */
     double integrated_total;   /* Eq. (3): sum over groups of the integrated flux of the final phi */
     double *integrated_flux;   /* caller host array [n_groups] or NULL: per-group integral of phi over space */
     double *residual_history;  /* caller host array [max_iters] or NULL: residual after each sweep */
@@ -167,8 +171,9 @@ tf_status tf_sweep(const tf_handle *problems, int32_t n, const double *const *ph
                    void *stream);
 
 /* Source iteration (group-Jacobi): repeat tf_sweep until the stopping test
- * max |phi_new - phi_old| / max(|phi_new|, 1e-10 x max over the group of |phi_new|)
- * falls below tol (evaluated in FP64 on the device) or max_iters sweeps.
+ * r = max over (cell, group, node) of |phi_new - phi_old| / max(|phi_new|, f x max over the group of |phi_new|)
+ * falls below tol or max_iters sweeps were done; f = opt.residual_floor (default 1: r is the largest
+ * per-group max-norm relative change).  The difference and the denominator are FP64 on the device.
  * phi[k]: in = initial flux (NULL entry = zero start), out = final flux
  * (a NULL entry is not allowed for the output: pass a buffer).  info: [n] or
  * NULL.  Returns TF_ERR_NOT_CONVERGED if any problem stopped at max_iters.

@@ -200,8 +200,11 @@ class Problem:
         return self.sweep(self.source(phi), threads=threads)[0]
 
     @staticmethod
-    def residual(phi_new, phi_old, floor=1e-10):
-        """max |phi_new - phi_old| / max(|phi_new|, floor * max over (cell, node) of |phi_new| in that group)."""
+    def residual(phi_new, phi_old, floor=1.0):
+        """Stopping test: max over (cell, group, node) of |phi_new - phi_old| /
+        max(|phi_new|, floor * max over (cell, node) of |phi_new| in that group).
+        floor = 1 (default) is the largest per-group max-norm relative change;
+        a small floor (1e-10) gives the pointwise relative change."""
         gmax = np.abs(phi_new).max(axis=(0, 2))  # per group
         den = np.maximum(np.abs(phi_new), floor * gmax[None, :, None])
         diff = np.abs(phi_new - phi_old)
@@ -217,7 +220,7 @@ class Problem:
         plain = phi.sum(axis=(0, 2))
         return ig, float(ig.sum()), plain, float(plain.sum())
 
-    def source_iterate(self, tol, max_iters, phi0=None, threads=1, callback=None):
+    def source_iterate(self, tol, max_iters, phi0=None, threads=1, callback=None, floor=1.0):
         """Group-Jacobi source iteration from phi0 (zeros by default) until the
         stopping test is below tol or max_iters sweeps were done."""
         phi = np.zeros((self.C, self.G, 4)) if phi0 is None else np.array(phi0, dtype=np.float64)
@@ -225,7 +228,7 @@ class Problem:
         it = 0
         for it in range(1, max_iters + 1):
             new = self.transport_step(phi, threads)
-            r = self.residual(new, phi)
+            r = self.residual(new, phi, floor)
             phi = new
             if callback:
                 callback(it, r, phi)

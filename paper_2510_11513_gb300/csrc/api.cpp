@@ -63,6 +63,7 @@ void tf_options_default(tf_options *opt)
     opt->device = 0;
     opt->wait_limit_s = 10.0;
     opt->phi_accumulate = TF_PHI_PAIR;
+    opt->residual_floor = 1.0;
 }
 
 const char *tf_status_string(tf_status s)
@@ -165,6 +166,7 @@ tf_status tf_problem_create(tf_handle mesh, tf_handle quad, int32_t n_groups, in
         return fail(TF_ERR_ARG, "tf_problem_create: precision must be TF_FP32 or TF_FP64");
     }
     if (!(p->opt.wait_limit_s > 0.0)) p->opt.wait_limit_s = 10.0;
+    if (!(p->opt.residual_floor > 0.0) || p->opt.residual_floor > 1.0) p->opt.residual_floor = 1.0;
     p->mesh = m;
     p->quad = q;
     retain(m);

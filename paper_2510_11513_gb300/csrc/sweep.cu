@@ -729,19 +729,20 @@ __global__ void finish_stats_kernel(const double *__restrict__ part, int nblk, i
     }
 }
 
-// Stopping test: max over (c, g, i) of |phi_new - phi_old| / max(|phi_new|, 1e-10 gmax_g).
+// Stopping test: max over (c, g, i) of |phi_new - phi_old| / max(|phi_new|, floor gmax_g).
 // Difference and denominator are FP64; their quotient, both scaled by the
 // group's 1/gmax, is formed in FP32, which only blurs r itself by ~1e-7.
 // Same 32 (groups) x 8 (cells) CTA shape as stats_kernel.
 __global__ void __launch_bounds__(256) residual_kernel(const double *__restrict__ phi_new, const double *__restrict__ phi_old,
-                                                       const double *__restrict__ gstats, int64_t C, int G, Ctrl *ctrl)
+                                                       const double *__restrict__ gstats, int64_t C, int G,
+                                                       double floor_frac, Ctrl *ctrl)
 {
     float rmax = 0.f;
     for (int g0 = 0; g0 < G; g0 += 32) {
         const int g = g0 + threadIdx.x;
         if (g >= G) continue;
         const double gmax = gstats[4 * g], inv = gstats[4 * g + 3];
-        const double floor_ = 1e-10 * gmax;
+        const double floor_ = floor_frac * gmax;
         for (int64_t c = (int64_t)blockIdx.x * 8 + threadIdx.y; c < C; c += (int64_t)gridDim.x * 8) {
             const double2 *pn = reinterpret_cast<const double2 *>(phi_new + ((size_t)c * G + g) * 4);
             const double2 *po = reinterpret_cast<const double2 *>(phi_old + ((size_t)c * G + g) * 4);
@@ -1235,7 +1236,8 @@ tf_status device_iterate(Problem &p, double tol, int32_t max_iters, double *phi,
         stats_kernel<<<d.stats_blocks, dim3(32, 8), 0, st>>>(nxt, d.vol4, d.C, d.G, d.part);
         finish_stats_kernel<<<(d.G + 127) / 128, 128, 0, st>>>(d.part, d.stats_blocks, d.G, d.gstats);
         TF_CUDA(cudaMemsetAsync(&d.ctrl->residual_bits, 0, 8, st));
-        residual_kernel<<<d.stats_blocks, dim3(32, 8), 0, st>>>(nxt, cur, d.gstats, d.C, d.G, d.ctrl);
+        residual_kernel<<<d.stats_blocks, dim3(32, 8), 0, st>>>(nxt, cur, d.gstats, d.C, d.G, p.opt.residual_floor,
+                                                                d.ctrl);
         TF_CUDA(cudaGetLastError());
         s = collect(p, st);
         if (s != TF_OK) return s;

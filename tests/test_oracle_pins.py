@@ -289,8 +289,15 @@ def test_residual_definition_special_cases():
     c = b.copy()
     c[0, 0, 0] = 1.0
     assert oracle.Problem.residual(b, c) == pytest.approx(0.5)
-    # the floor: a tiny value next to a large one in the same group
+    # pointwise with a floor: a tiny value next to a large one in the same group
     b[1, 0, 1] = 1e-30
     c[1, 0, 1] = 0.0
     c[0, 0, 0] = 2.0
-    assert oracle.Problem.residual(b, c) == pytest.approx(1e-30 / (1e-10 * 2.0))
+    assert oracle.Problem.residual(b, c, floor=1e-10) == pytest.approx(1e-30 / (1e-10 * 2.0))
+    # default (max-norm per group): the same change measured against the group's max
+    assert oracle.Problem.residual(b, c) == pytest.approx(1e-30 / 2.0)
+    # groups are normalised separately
+    d, e = np.zeros((1, 2, 4)), np.zeros((1, 2, 4))
+    d[0, 0, 0], d[0, 1, 0] = 1.0, 1e-20
+    e[0, 0, 0], e[0, 1, 0] = 1.0, 0.5e-20
+    assert oracle.Problem.residual(d, e) == pytest.approx(0.5)
