@@ -32,17 +32,22 @@ template <> struct Vec4<float> { using type = float4; };
 template <> struct Vec4<double> { using type = double4a; };
 template <class T> using V4 = typename Vec4<T>::type;
 
-// Per-cell geometry in the sweep precision.  g*: (V/4) d b_j / d{x,y,z} (the
-// f_i df_j/dx det J integrals, identical for every row i); n*: area-weighted
-// outward normal of face f; mv = V/20 (mass matrix scale); nn packs, for face
-// f and local vertex i != f, the neighbour-local index of that vertex in bits
-// 2*(4f+i) .. 2*(4f+i)+1.
+// Per-cell geometry in the sweep precision, with the cell's four nodes in
+// ascending global-vertex order ("sorted" order; face j is the face opposite
+// sorted node j).  In that order the three nodes of a shared face appear in
+// the same relative order in both cells, so the upwind trace on a face is the
+// upwind cell's nodal vector with one component (the node opposite the face)
+// deleted.  g*: (V/4) d b_j / d{x,y,z} (the f_i df_j/dx det J integrals,
+// identical for every row i); n*: area-weighted outward normal of face j;
+// mv = V/20 (mass matrix scale); code: bits 2j..2j+1 = the neighbour's sorted
+// index of the node opposite the shared face j, bits 8+2j..9+2j = the caller's
+// local index of sorted node j.
 template <class T> struct alignas(16) CellGeo {
     T gx[4], gy[4], gz[4];
     T nx[4], ny[4], nz[4];
     T mv;
     int32_t mat;
-    uint32_t nn;
+    uint32_t code;
     int32_t nbr[4];
 };
 static_assert(sizeof(CellGeo<float>) == 128, "float cell record must be one 128-byte line");
@@ -125,12 +130,31 @@ __device__ __forceinline__ void st_psi(double4a *p, double4a v)
 }
 
 template <class T> __device__ __forceinline__ T rcp(T x);
-template <> __device__ __forceinline__ float rcp<float>(float x) { return __frcp_rn(x); }
+template <> __device__ __forceinline__ float rcp<float>(float x)
+{
+    float r;  // one MUFU reciprocal (max error about 1 ulp); the pivots are positive and normal
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
 template <> __device__ __forceinline__ double rcp<double>(double x) { return __drcp_rn(x); }
 
 template <class V> __device__ __forceinline__ auto comp(const V &v, int k) -> decltype(v.x)
 {
     return k == 0 ? v.x : (k == 1 ? v.y : (k == 2 ? v.z : v.w));
+}
+
+// select r[k] for a runtime k in 0..3 without indexing a local array
+template <class T> __device__ __forceinline__ T pick4(const T (&r)[4], uint32_t k)
+{
+    return k == 0u ? r[0] : (k == 1u ? r[1] : (k == 2u ? r[2] : r[3]));
+}
+
+// o[perm(j)] = r[j] for the permutation stored in code bits 8+2j..9+2j, by selects
+template <class T> __device__ __forceinline__ void scatter4(const T (&r)[4], uint32_t code, T (&o)[4])
+{
+    const uint32_t p0 = (code >> 8) & 3u, p1 = (code >> 10) & 3u, p2 = (code >> 12) & 3u;
+#pragma unroll
+    for (uint32_t u = 0; u < 4; ++u) o[u] = p0 == u ? r[0] : (p1 == u ? r[1] : (p2 == u ? r[2] : r[3]));
 }
 
 // ============================================================== sweep kernel
@@ -183,24 +207,23 @@ template <class T> __device__ __forceinline__ void solve4(T a[4][4], T b[4], T x
     x[0] = (b[0] - a[0][1] * x[1] - a[0][2] * x[2] - a[0][3] * x[3]) * r0;
 }
 
-template <class T> struct CellSetup {
-    uint32_t c;
-    uint32_t mask;
+// Group-independent part of one cell's local system for direction Omega, in
+// sorted node order, plus the row pointers of its per-group data.
+//   A_ij = (V/4) Omega.grad b_j + sum_{f inflow, i,j != f} (|s_f|/12)(1 + delta_ij) + sigma (V/20)(1 + delta_ij)
+// With t_f = |s_f|/12 on inflow faces and T = sum_f t_f the face part is
+// T - t_i - t_j off the diagonal and 2 (T - t_i) on it.
+template <class T> struct Cell {
     T P[4];   // (V/4) Omega.grad b_j
     T t[4];   // |Omega.N_f| / 12 on inflow faces, 0 otherwise
     T tt;     // sum_f t_f
     T mv;     // V/20
-    int32_t mat;
-    uint32_t nn;
+    uint32_t c, mask, code;
     int32_t nbr[4];
+    const T *sig;         // sigma_t row of the cell's material
 };
 
-// Group-independent part of the local system of cell c for direction Omega:
-//   A_ij = (V/4) Omega.grad b_j + sum_{f inflow, i,j != f} (|s_f|/12)(1 + delta_ij) + sigma (V/20)(1 + delta_ij)
-// With t_f = |s_f|/12 on inflow faces and T = sum_f t_f the face part is
-// T - t_i - t_j off the diagonal and 2 (T - t_i) on it.
 template <class T>
-__device__ __forceinline__ void cell_setup(const SweepArgs<T> &A, uint32_t entry, T ox, T oy, T oz, CellSetup<T> &s)
+__device__ __forceinline__ void cell_setup(const SweepArgs<T> &A, uint32_t entry, T ox, T oy, T oz, Cell<T> &s)
 {
     s.c = entry >> 4;
     s.mask = entry & 15u;
@@ -222,8 +245,8 @@ __device__ __forceinline__ void cell_setup(const SweepArgs<T> &A, uint32_t entry
         s.tt += s.t[f];
     }
     s.mv = g.mv;
-    s.mat = g.mat;
-    s.nn = g.nn;
+    s.code = g.code;
+    s.sig = A.sigma_t + (size_t)g.mat * A.G;
 #pragma unroll
     for (int f = 0; f < 4; ++f) s.nbr[f] = g.nbr[f];
 }
@@ -237,16 +260,15 @@ template <class T> struct UnitIn {
 };
 
 template <class T>
-__device__ __forceinline__ void unit_load(const SweepArgs<T> &A, const CellSetup<T> &s, int g, size_t psi_dir,
+__device__ __forceinline__ void unit_load(const SweepArgs<T> &A, const Cell<T> &s, int g, size_t psi_dir,
                                           UnitIn<T> &in)
 {
     const int G = A.G;
-    in.sig = __ldg(A.sigma_t + (size_t)s.mat * G + g);
+    in.sig = __ldg(s.sig + g);
     in.q = ld_ro(A.q + (size_t)s.c * G + g);
 #pragma unroll
     for (int f = 0; f < 4; ++f) {
-        const bool up = ((s.mask >> f) & 1u) && s.nbr[f] >= 0;
-        if (up) {
+        if (((s.mask >> f) & 1u) && s.nbr[f] >= 0) {
             in.u[f] = ld_l2(A.psi + (psi_dir + (size_t)s.nbr[f]) * G + g);
         } else {
             in.u[f].x = in.u[f].y = in.u[f].z = in.u[f].w = T(0);
@@ -254,9 +276,9 @@ __device__ __forceinline__ void unit_load(const SweepArgs<T> &A, const CellSetup
     }
 }
 
-// Assemble and solve one unit from its loaded inputs; store psi.
+// Assemble and solve one unit from its loaded inputs; store psi (sorted order).
 template <class T>
-__device__ __forceinline__ void unit_solve(const SweepArgs<T> &A, const CellSetup<T> &s, int g, size_t psi_dir,
+__device__ __forceinline__ void unit_solve(const SweepArgs<T> &A, const Cell<T> &s, int g, size_t psi_dir,
                                            const UnitIn<T> &in, T ox, T oy, T oz)
 {
     const int G = A.G;
@@ -272,24 +294,28 @@ __device__ __forceinline__ void unit_solve(const SweepArgs<T> &A, const CellSetu
 #pragma unroll
     for (int f = 0; f < 4; ++f) {
         if (!((s.mask >> f) & 1u)) continue;
-        T up[4] = {T(0), T(0), T(0), T(0)};
+        T v0, v1, v2;  // upwind trace at the face's nodes, ascending global id
         if (s.nbr[f] >= 0) {
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-                if (i != f) up[i] = comp(in.u[f], (int)((s.nn >> (2 * (4 * f + i))) & 3u));
+            const uint32_t fn = (s.code >> (2 * f)) & 3u;  // upwind node opposite the face
+            const V4<T> &u = in.u[f];
+            v0 = fn == 0u ? u.y : u.x;
+            v1 = fn <= 1u ? u.z : u.y;
+            v2 = fn <= 2u ? u.w : u.z;
         } else if (A.psi_in) {
             const int4 tv = __ldg(A.tets + s.c);
             const int vi[4] = {tv.x, tv.y, tv.z, tv.w};
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-                if (i != f) up[i] = __ldg(A.psi_in + (size_t)vi[i] * G + g);
+            const int i0 = f == 0 ? 1 : 0, i1 = f <= 1 ? 2 : 1, i2 = f <= 2 ? 3 : 2;
+            v0 = __ldg(A.psi_in + (size_t)vi[i0] * G + g);
+            v1 = __ldg(A.psi_in + (size_t)vi[i1] * G + g);
+            v2 = __ldg(A.psi_in + (size_t)vi[i2] * G + g);
         } else {
             continue;  // vacuum: no inflow
         }
-        const T U = (up[0] + up[1]) + (up[2] + up[3]);
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-            if (i != f) b[i] += s.t[f] * (up[i] + U);
+        const T U = v0 + v1 + v2;
+        // the face's nodes in sorted order are {0..3} \ {f}, ascending
+        b[f == 0 ? 1 : 0] += s.t[f] * (v0 + U);
+        b[f <= 1 ? 2 : 1] += s.t[f] * (v1 + U);
+        b[f <= 2 ? 3 : 2] += s.t[f] * (v2 + U);
     }
     T a[4][4];
 #pragma unroll
@@ -308,7 +334,6 @@ __device__ __forceinline__ void unit_solve(const SweepArgs<T> &A, const CellSetu
 }
 
 __device__ __forceinline__ void prefetch_l1(const void *p) { asm volatile("prefetch.global.L1 [%0];" ::"l"(p)); }
-__device__ __forceinline__ void prefetch_l2(const void *p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
 
 // One task when every cell's groups fill whole warps (G a multiple of 32 and
 // at most 64 cells per task): lane l solves groups l, l+32, ... of each cell,
@@ -334,7 +359,7 @@ __device__ __forceinline__ void run_task_wide(const SweepArgs<T> &A, uint4 ti, i
             if (lane < (int)((sizeof(CellGeo<T>) + 127) / 128))
                 prefetch_l1(reinterpret_cast<const char *>(A.geo + c1) + 128 * lane);
         }
-        CellSetup<T> s;
+        Cell<T> s;
         cell_setup(A, e, ox, oy, oz, s);
         int g = lane;
         for (; g + 32 < G; g += 64) {
@@ -366,7 +391,7 @@ __device__ __forceinline__ void run_task_generic(const SweepArgs<T> &A, uint4 ti
         ++k;
     }
     uint32_t kc = 0xffffffffu;
-    CellSetup<T> s;
+    Cell<T> s;
     while (k < ncell) {
         if (k != kc) {
             cell_setup(A, __ldg(A.cells + ti.x + k), ox, oy, oz, s);
@@ -530,7 +555,9 @@ __global__ void end_kernel(Ctrl *ctrl)
 }
 
 // ============================================================== source update
-// q[c][g][i] = (Q[c][g][i] + sum_g' sigma_s[m][g'][g] phi[c][g'][i]) / (4 pi)
+// q[c][g][j] = (Q[c][g][j] + sum_g' sigma_s[m][g'][g] phi[c][g'][perm(j)]) / (4 pi)
+// phi is in the caller's node order; q (and Q, uploaded pre-permuted) are in
+// the cell's sorted node order, perm(j) = caller's index of sorted node j.
 // One CTA stages the FP64 scalar flux of a few cells (converted to the sweep
 // precision) in shared memory; thread (cell, g) forms the 4 nodal sums.
 template <class T>
@@ -550,22 +577,23 @@ __global__ void __launch_bounds__(256) source_kernel(const double *__restrict__ 
             const int lc = u / G, g = u - lc * G;
             const int64_t c = c0 + lc;
             const int m = __ldg(&geo[c].mat);
+            const uint32_t code = __ldg(&geo[c].code);
             const T *S = sigma_s + (size_t)m * G * G + g;
             const T *p = ph + (size_t)lc * G * 4;
-            T a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+            T a[4] = {0, 0, 0, 0};
             for (int h = 0; h < G; ++h) {
                 const T s = __ldg(S + (size_t)h * G);
-                a0 += s * p[4 * h + 0];
-                a1 += s * p[4 * h + 1];
-                a2 += s * p[4 * h + 2];
-                a3 += s * p[4 * h + 3];
+                a[0] += s * p[4 * h + 0];
+                a[1] += s * p[4 * h + 1];
+                a[2] += s * p[4 * h + 2];
+                a[3] += s * p[4 * h + 3];
             }
             const V4<T> Qv = ld_ro(Qext + (size_t)c * G + g);
             V4<T> o;
-            o.x = (Qv.x + a0) * inv4pi;
-            o.y = (Qv.y + a1) * inv4pi;
-            o.z = (Qv.z + a2) * inv4pi;
-            o.w = (Qv.w + a3) * inv4pi;
+            o.x = (Qv.x + pick4(a, (code >> 8) & 3u)) * inv4pi;
+            o.y = (Qv.y + pick4(a, (code >> 10) & 3u)) * inv4pi;
+            o.z = (Qv.z + pick4(a, (code >> 12) & 3u)) * inv4pi;
+            o.w = (Qv.w + pick4(a, (code >> 14) & 3u)) * inv4pi;
             q[(size_t)c * G + g] = o;
         }
     }
@@ -593,10 +621,11 @@ __device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float p, float
 
 template <class T, bool PAIR>
 __global__ void __launch_bounds__(256) phi_kernel(const V4<T> *__restrict__ psi, const WeightPair *__restrict__ wts,
-                                                  int Dc, size_t CG, double *__restrict__ phi, int accumulate)
+                                                  int Dc, size_t CG, int G, const CellGeo<T> *__restrict__ geo,
+                                                  double *__restrict__ phi, int accumulate)
 {
     for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < CG; idx += (size_t)gridDim.x * blockDim.x) {
-        double r[4];
+        double r[4];  // sorted node order
         if constexpr (PAIR) {
             float hi[4] = {0.f, 0.f, 0.f, 0.f}, lo[4] = {0.f, 0.f, 0.f, 0.f};
             int a = 0;
@@ -656,16 +685,40 @@ __global__ void __launch_bounds__(256) phi_kernel(const V4<T> *__restrict__ psi,
 #pragma unroll
             for (int i = 0; i < 4; ++i) r[i] = acc[i];
         }
+        // back to the caller's node order: caller node perm(j) <- sorted node j
+        const uint32_t code = __ldg(&geo[idx / (size_t)G].code);
+        double o[4];
+        scatter4(r, code, o);
         double2 *out = reinterpret_cast<double2 *>(phi + idx * 4);
         if (accumulate) {
             const double2 o0 = out[0], o1 = out[1];
-            r[0] += o0.x;
-            r[1] += o0.y;
-            r[2] += o1.x;
-            r[3] += o1.y;
+            o[0] += o0.x;
+            o[1] += o0.y;
+            o[2] += o1.x;
+            o[3] += o1.y;
         }
-        out[0] = make_double2(r[0], r[1]);
-        out[1] = make_double2(r[2], r[3]);
+        out[0] = make_double2(o[0], o[1]);
+        out[1] = make_double2(o[2], o[3]);
+    }
+}
+
+// psi of one direction from sorted to the caller's node order (inspection only).
+template <class T>
+__global__ void psi_unsort_kernel(const V4<T> *__restrict__ src, V4<T> *__restrict__ dst, size_t CG, int G,
+                                  const CellGeo<T> *__restrict__ geo)
+{
+    for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < CG; idx += (size_t)gridDim.x * blockDim.x) {
+        const uint32_t code = __ldg(&geo[idx / (size_t)G].code);
+        const V4<T> v = src[idx];
+        const T r[4] = {v.x, v.y, v.z, v.w};
+        T o[4];
+        scatter4(r, code, o);
+        V4<T> w;
+        w.x = o[0];
+        w.y = o[1];
+        w.z = o[2];
+        w.w = o[3];
+        dst[idx] = w;
     }
 }
 
@@ -838,6 +891,14 @@ template <class P> tf_status upload(DeviceState &d, P **p, const void *src, size
     return TF_OK;
 }
 
+// Sorted node order of cell c: s2u[j] = caller's local index of the j-th smallest global vertex.
+inline void sorted_order(const int32_t *t, int s2u[4])
+{
+    for (int j = 0; j < 4; ++j) s2u[j] = j;
+    for (int a = 1; a < 4; ++a)
+        for (int b = a; b > 0 && t[s2u[b - 1]] > t[s2u[b]]; --b) std::swap(s2u[b - 1], s2u[b]);
+}
+
 template <class T> void pack_geometry(const Mesh &m, const int32_t *cell_material, std::vector<CellGeo<T>> &out)
 {
     out.resize(m.nc);
@@ -845,24 +906,32 @@ template <class T> void pack_geometry(const Mesh &m, const int32_t *cell_materia
         CellGeo<T> &g = out[c];
         std::memset(&g, 0, sizeof(g));
         const double V = m.vol[c];
+        int s2u[4];
+        sorted_order(&m.tets[4 * c], s2u);
+        uint32_t code = 0;
         for (int j = 0; j < 4; ++j) {
-            g.gx[j] = (T)(0.25 * V * m.grad[12 * c + 3 * j + 0]);
-            g.gy[j] = (T)(0.25 * V * m.grad[12 * c + 3 * j + 1]);
-            g.gz[j] = (T)(0.25 * V * m.grad[12 * c + 3 * j + 2]);
-            g.nx[j] = (T)m.normal[12 * c + 3 * j + 0];
-            g.ny[j] = (T)m.normal[12 * c + 3 * j + 1];
-            g.nz[j] = (T)m.normal[12 * c + 3 * j + 2];
-            g.nbr[j] = m.nbr[4 * c + j];
+            const int u = s2u[j];
+            g.gx[j] = (T)(0.25 * V * m.grad[12 * c + 3 * u + 0]);
+            g.gy[j] = (T)(0.25 * V * m.grad[12 * c + 3 * u + 1]);
+            g.gz[j] = (T)(0.25 * V * m.grad[12 * c + 3 * u + 2]);
+            g.nx[j] = (T)m.normal[12 * c + 3 * u + 0];
+            g.ny[j] = (T)m.normal[12 * c + 3 * u + 1];
+            g.nz[j] = (T)m.normal[12 * c + 3 * u + 2];
+            const int32_t n = m.nbr[4 * c + u];
+            g.nbr[j] = n;
+            if (n >= 0) {
+                int s2u_n[4];
+                sorted_order(&m.tets[4 * (int64_t)n], s2u_n);
+                const int fu = m.nbr_face[4 * c + u];  // neighbour's caller-order face index
+                int fs = 0;
+                while (s2u_n[fs] != fu) ++fs;
+                code |= (uint32_t)fs << (2 * j);
+            }
+            code |= (uint32_t)u << (8 + 2 * j);
         }
         g.mv = (T)(V / 20.0);
         g.mat = cell_material[c];
-        uint32_t nn = 0;
-        for (int f = 0; f < 4; ++f)
-            for (int i = 0; i < 4; ++i) {
-                const int k = m.nbr_node[16 * c + 4 * f + i];
-                if (k >= 0) nn |= (uint32_t)k << (2 * (4 * f + i));
-            }
-        g.nn = nn;
+        g.code = code;
     }
 }
 
@@ -908,13 +977,29 @@ template <class T> tf_status create_typed(Problem &p, DeviceState &d, const int3
     if ((s = upload_vec3<T>(d, &d.omega, p.quad->omega.data(), d.D, p.quad->w.data())) != TF_OK) return s;
     if ((s = upload_typed<T>(d, &d.sigma_t, sigma_t, (size_t)d.M * d.G)) != TF_OK) return s;
     if ((s = upload_typed<T>(d, &d.sigma_s, sigma_s, (size_t)d.M * d.G * d.G)) != TF_OK) return s;
-    if ((s = upload_typed<T>(d, &d.Q, Q, (size_t)d.C * d.G * 4)) != TF_OK) return s;
+    {
+        std::vector<double> Qs((size_t)d.C * d.G * 4);
+        for (int64_t c = 0; c < d.C; ++c) {
+            int s2u[4];
+            sorted_order(&m.tets[4 * c], s2u);
+            for (int gq = 0; gq < d.G; ++gq)
+                for (int j = 0; j < 4; ++j)
+                    Qs[((size_t)c * d.G + gq) * 4 + j] = Q[((size_t)c * d.G + gq) * 4 + s2u[j]];
+        }
+        if ((s = upload_typed<T>(d, &d.Q, Qs.data(), Qs.size())) != TF_OK) return s;
+    }
     if (S1) {
         if ((s = upload_vec3<T>(d, &d.S1, S1, (size_t)d.C * d.G, nullptr)) != TF_OK) return s;
     }
     if (psi_in) {
         if ((s = upload_typed<T>(d, &d.psi_in, psi_in, (size_t)d.nv * d.G)) != TF_OK) return s;
-        if ((s = upload(d, &d.tets, m.tets.data(), sizeof(int4) * m.nc)) != TF_OK) return s;
+        std::vector<int32_t> ts(4 * (size_t)m.nc);
+        for (int64_t c = 0; c < m.nc; ++c) {
+            int s2u[4];
+            sorted_order(&m.tets[4 * c], s2u);
+            for (int j = 0; j < 4; ++j) ts[4 * c + j] = m.tets[4 * c + s2u[j]];
+        }
+        if ((s = upload(d, &d.tets, ts.data(), sizeof(int4) * m.nc)) != TF_OK) return s;
     }
     (void)g;
     return TF_OK;
@@ -948,7 +1033,25 @@ tf_status device_create(Problem &p, const int32_t *cell_material, const double *
     if ((uint64_t)g.down_list.size() >= (1ull << 32)) return fail(TF_ERR_ARG, "graph too large: 2^32 downwind edges");
     tf_status s;
     // task graph
-    if ((s = upload(d, &d.cells, g.cell_list.data(), g.cell_list.size() * 4)) != TF_OK) return s;
+    {
+        // inflow masks of the task cell lists, caller face order -> sorted face order
+        std::vector<uint8_t> remap((size_t)m.nc * 16);
+        for (int64_t c = 0; c < m.nc; ++c) {
+            int s2u[4];
+            sorted_order(&m.tets[4 * c], s2u);
+            for (uint32_t mk = 0; mk < 16; ++mk) {
+                uint32_t r = 0;
+                for (int j = 0; j < 4; ++j) r |= ((mk >> s2u[j]) & 1u) << j;
+                remap[16 * c + mk] = (uint8_t)r;
+            }
+        }
+        std::vector<uint32_t> cl(g.cell_list.size());
+        for (size_t i = 0; i < cl.size(); ++i) {
+            const uint32_t e = g.cell_list[i], c = e >> 4;
+            cl[i] = (c << 4) | remap[16 * (size_t)c + (e & 15u)];
+        }
+        if ((s = upload(d, &d.cells, cl.data(), cl.size() * 4)) != TF_OK) return s;
+    }
     {
         std::vector<uint4> ti(T);
         for (int64_t t = 0; t < T; ++t) {
@@ -1130,9 +1233,11 @@ template <class T> tf_status launch_step(Problem &p, const double *phi_in, doubl
         const int pb = (int)std::min<size_t>((CG + 255) / 256, (size_t)d.sm_count * 32);
         TF_CUDA(cudaEventRecord(d.ev_start[2 + 2 * k], st));
         if (!d.fp64 && p.opt.phi_accumulate == TF_PHI_PAIR)
-            phi_kernel<T, true><<<pb, 256, 0, st>>>((const V4<T> *)d.psi, d.wts + a0, a1 - a0, CG, phi_out, k > 0);
+            phi_kernel<T, true><<<pb, 256, 0, st>>>((const V4<T> *)d.psi, d.wts + a0, a1 - a0, CG, d.G,
+                                                    (const CellGeo<T> *)d.geo, phi_out, k > 0);
         else
-            phi_kernel<T, false><<<pb, 256, 0, st>>>((const V4<T> *)d.psi, d.wts + a0, a1 - a0, CG, phi_out, k > 0);
+            phi_kernel<T, false><<<pb, 256, 0, st>>>((const V4<T> *)d.psi, d.wts + a0, a1 - a0, CG, d.G,
+                                                     (const CellGeo<T> *)d.geo, phi_out, k > 0);
         TF_CUDA(cudaGetLastError());
         TF_CUDA(cudaEventRecord(d.ev_stop[2 + 2 * k], st));
         d.last_chunk = k;
@@ -1280,10 +1385,17 @@ tf_status device_psi(Problem &p, int32_t dir, void *out, void *stream)
     if (dir < a0 || dir >= std::min(d.D, a0 + d.Dc))
         return fail(TF_ERR_ARG, "tf_problem_psi: direction not in the last swept chunk");
     TF_CUDA(cudaSetDevice(d.device));
-    const size_t per_dir = (size_t)d.C * d.G * 4 * d.tsize;
-    TF_CUDA(cudaMemcpyAsync(out, (const char *)d.psi + (size_t)(dir - a0) * per_dir, per_dir, cudaMemcpyDeviceToDevice,
-                            (cudaStream_t)stream));
-    TF_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    const size_t CG = (size_t)d.C * d.G;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int blocks = (int)std::min<size_t>((CG + 255) / 256, (size_t)d.sm_count * 16);
+    if (d.fp64)
+        psi_unsort_kernel<double><<<blocks, 256, 0, st>>>((const V4<double> *)d.psi + (size_t)(dir - a0) * CG,
+                                                          (V4<double> *)out, CG, d.G, (const CellGeo<double> *)d.geo);
+    else
+        psi_unsort_kernel<float><<<blocks, 256, 0, st>>>((const V4<float> *)d.psi + (size_t)(dir - a0) * CG,
+                                                         (V4<float> *)out, CG, d.G, (const CellGeo<float> *)d.geo);
+    TF_CUDA(cudaGetLastError());
+    TF_CUDA(cudaStreamSynchronize(st));
     return TF_OK;
 }
 
