@@ -75,7 +75,10 @@ typedef struct {
     int32_t inject_stall;    /* fault injection for tests: 1 = seed no task, so every device wait runs out */
     double psi_budget_gb;    /* device memory allowed for the angular-flux store; 0 = 80 % of free memory */
     int32_t task_order;      /* 0 = FIFO ready queue, seeds longest-critical-path first */
-    int32_t reserved_i[7];
+    int32_t staging;         /* 0 = automatic: stage each cell's rows in shared memory with bulk
+                              * asynchronous copies when n_groups is a multiple of 32 and they fit;
+                              * 1 = never (registers only) */
+    int32_t reserved_i[6];
     double residual_floor;   /* stopping-test denominator floor, as a fraction of the group's max |phi|:
                               * 1 (the default; 0 also means 1) = per-group max-norm relative change,
                               * 1e-10 = pointwise relative change (unreachable in FP32 where DG

@@ -180,6 +180,7 @@ template <class T> struct SweepArgs {
     unsigned long long n_tasks;  // tasks in the chunk
     unsigned long long wait_limit_ns;
     int32_t max_cells;           // largest task (cells)
+    uint32_t warp_smem;          // dynamic shared memory per warp (staged path)
 };
 
 // Solve one 4x4 system by Gaussian elimination without pivoting: the
@@ -408,6 +409,240 @@ __device__ __forceinline__ void run_task_generic(const SweepArgs<T> &A, uint4 ti
     }
 }
 
+// ------------------------------------------------------------------ TMA staging
+// One warp stages, per cell, its geometry record, its source row q[c][0..G)
+// and the psi rows of its (at most three) interior inflow neighbours into
+// shared memory with bulk asynchronous copies (cp.async.bulk, completion on
+// an mbarrier), three cells ahead of the one being solved.
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_shared() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async_global() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
+
+// Bounded wait on an mbarrier phase; false (and the error word set) after limit_ns.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, unsigned long long limit_ns, int *err)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = globaltimer();
+    while (!mbar_try_wait(bar, parity)) {
+        if (globaltimer() - t0 > limit_ns) {
+            atomicCAS(err, 0, (int)TF_ERR_TIMEOUT);
+            return false;
+        }
+    }
+    return true;
+}
+
+template <class T> struct StageLayout {
+    uint32_t row;    // G psi/q entries
+    uint32_t stage;  // geometry record + q row + 3 upwind rows
+    __device__ __forceinline__ StageLayout(int G)
+        : row((uint32_t)G * (uint32_t)sizeof(V4<T>)), stage((uint32_t)sizeof(CellGeo<T>) + 4u * row)
+    {
+    }
+};
+
+// Bytes of shared memory one warp needs for the staged path (3 stages + 6 mbarriers).
+template <class T> inline size_t staged_warp_bytes(int G)
+{
+    return 3 * (sizeof(CellGeo<T>) + 4 * (size_t)G * sizeof(V4<T>)) + 6 * 8;
+}
+
+// Lane 0: geometry record and source row of cell c into stage s.
+template <class T>
+__device__ __forceinline__ void issue_geoq(const SweepArgs<T> &A, unsigned char *st_base, uint64_t *bar, uint32_t c,
+                                           const StageLayout<T> &L)
+{
+    mbar_arrive_expect_tx(bar, (uint32_t)sizeof(CellGeo<T>) + L.row);
+    bulk_g2s(st_base, A.geo + c, (uint32_t)sizeof(CellGeo<T>), bar);
+    bulk_g2s(st_base + sizeof(CellGeo<T>), A.q + (size_t)c * A.G, L.row, bar);
+}
+
+// Lane 0: psi rows of the interior inflow neighbours (mask from the task list,
+// neighbours from the staged record) into the stage's upwind slots, in face order.
+template <class T>
+__device__ __forceinline__ void issue_up(const SweepArgs<T> &A, unsigned char *st_base, uint64_t *bar, uint32_t mask,
+                                         size_t psi_dir, const StageLayout<T> &L)
+{
+    const CellGeo<T> *g = reinterpret_cast<const CellGeo<T> *>(st_base);
+    uint32_t n_up = 0;
+    int32_t nb[4];
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+        nb[f] = g->nbr[f];
+        n_up += (((mask >> f) & 1u) && nb[f] >= 0) ? 1u : 0u;
+    }
+    mbar_arrive_expect_tx(bar, n_up * L.row);
+    uint32_t slot = 0;
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+        if (((mask >> f) & 1u) && nb[f] >= 0) {
+            bulk_g2s(st_base + sizeof(CellGeo<T>) + (1 + slot) * L.row, A.psi + (psi_dir + (size_t)nb[f]) * A.G, L.row,
+                     bar);
+            ++slot;
+        }
+    }
+}
+
+// Solve every group of one staged cell: lane l takes groups l, l+32, ...
+template <class T>
+__device__ __forceinline__ void solve_staged_cell(const SweepArgs<T> &A, const unsigned char *st_base, uint32_t entry,
+                                                  int lane, T ox, T oy, T oz, size_t psi_dir, const StageLayout<T> &L)
+{
+    const CellGeo<T> &g = *reinterpret_cast<const CellGeo<T> *>(st_base);
+    const V4<T> *qrow = reinterpret_cast<const V4<T> *>(st_base + sizeof(CellGeo<T>));
+    const uint32_t c = entry >> 4, mask = entry & 15u;
+    T P[4], t[4], tt = T(0);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) P[j] = ox * g.gx[j] + oy * g.gy[j] + oz * g.gz[j];
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+        const T sf = ox * g.nx[f] + oy * g.ny[f] + oz * g.nz[f];
+        t[f] = ((mask >> f) & 1u) ? fabs(sf) * T(1.0 / 12.0) : T(0);
+        tt += t[f];
+    }
+    const T mv = g.mv;
+    const uint32_t code = g.code;
+    int32_t nb[4];
+    const V4<T> *uprow[4];
+    uint32_t slot = 0;
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+        nb[f] = g.nbr[f];
+        const bool up = ((mask >> f) & 1u) && nb[f] >= 0;
+        uprow[f] = reinterpret_cast<const V4<T> *>(st_base + sizeof(CellGeo<T>) + (1 + slot) * L.row);
+        slot += up ? 1u : 0u;
+    }
+    const T *sig = A.sigma_t + (size_t)g.mat * A.G;
+    V4<T> *out = A.psi + (psi_dir + (size_t)c) * A.G;
+    for (int gg = lane; gg < A.G; gg += 32) {
+        const T sv = __ldg(sig + gg) * mv;
+        const V4<T> q4 = qrow[gg];
+        const T qs = (q4.x + q4.y) + (q4.z + q4.w);
+        T b[4] = {mv * (q4.x + qs), mv * (q4.y + qs), mv * (q4.z + qs), mv * (q4.w + qs)};
+        if (A.S1) {
+            const V4<T> s1 = ld_ro(A.S1 + (size_t)c * A.G + gg);
+            const T os = T(5) * mv * (ox * s1.x + oy * s1.y + oz * s1.z);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) b[i] += os;
+        }
+#pragma unroll
+        for (int f = 0; f < 4; ++f) {
+            if (!((mask >> f) & 1u)) continue;
+            T v0, v1, v2;
+            if (nb[f] >= 0) {
+                const uint32_t fn = (code >> (2 * f)) & 3u;
+                const V4<T> u = uprow[f][gg];
+                v0 = fn == 0u ? u.y : u.x;
+                v1 = fn <= 1u ? u.z : u.y;
+                v2 = fn <= 2u ? u.w : u.z;
+            } else if (A.psi_in) {
+                const int4 tv = __ldg(A.tets + c);
+                const int vi[4] = {tv.x, tv.y, tv.z, tv.w};
+                v0 = __ldg(A.psi_in + (size_t)vi[f == 0 ? 1 : 0] * A.G + gg);
+                v1 = __ldg(A.psi_in + (size_t)vi[f <= 1 ? 2 : 1] * A.G + gg);
+                v2 = __ldg(A.psi_in + (size_t)vi[f <= 2 ? 3 : 2] * A.G + gg);
+            } else {
+                continue;
+            }
+            const T U = v0 + v1 + v2;
+            b[f == 0 ? 1 : 0] += t[f] * (v0 + U);
+            b[f <= 1 ? 2 : 1] += t[f] * (v1 + U);
+            b[f <= 2 ? 3 : 2] += t[f] * (v2 + U);
+        }
+        T a[4][4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) a[i][j] = P[j] + (i == j ? T(2) * (tt - t[i] + sv) : (tt - t[i] - t[j]) + sv);
+        T x[4];
+        solve4(a, b, x);
+        V4<T> o;
+        o.x = x[0];
+        o.y = x[1];
+        o.z = x[2];
+        o.w = x[3];
+        st_psi(out + gg, o);
+    }
+}
+
+// One task through the staged pipeline.  Stage of cell k = k mod 3; for each
+// stage two mbarriers (geometry+source, upwind rows) whose phase parities are
+// kept in `ph` (bit s: geometry barrier of stage s, bit 3+s: upwind barrier).
+// Returns false if a wait ran out (error word set).
+template <class T>
+__device__ __forceinline__ bool run_task_staged(const SweepArgs<T> &A, uint4 ti, int lane, T ox, T oy, T oz,
+                                                size_t psi_dir, unsigned char *wsm, uint32_t &ph)
+{
+    const unsigned FULL = 0xffffffffu;
+    const uint32_t ncell = ti.y & 0xffffu;
+    const StageLayout<T> L(A.G);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(wsm + 3 * L.stage);
+    const uint32_t e_lo = lane < (int)ncell ? __ldg(A.cells + ti.x + lane) : 0u;
+    const uint32_t e_hi = lane + 32 < (int)ncell ? __ldg(A.cells + ti.x + 32 + lane) : 0u;
+    auto entry = [&](uint32_t k) { return __shfl_sync(FULL, k < 32 ? e_lo : e_hi, k & 31); };
+    // psi rows written by other warps (generic proxy, acquired through the
+    // queue) are read here by the async proxy
+    if (lane == 0) fence_proxy_async_global();
+    const uint32_t e0 = entry(0);
+    const uint32_t e1 = ncell > 1 ? entry(1) : 0u;
+    if (lane == 0) {
+        issue_geoq(A, wsm, &bars[0], e0 >> 4, L);
+        if (ncell > 1) issue_geoq(A, wsm + L.stage, &bars[1], e1 >> 4, L);
+    }
+    if (!mbar_wait(&bars[0], ph & 1u, A.wait_limit_ns, &A.ctrl->error)) return false;
+    ph ^= 1u;
+    if (lane == 0) issue_up(A, wsm, &bars[3], e0 & 15u, psi_dir, L);
+    for (uint32_t k = 0; k < ncell; ++k) {
+        const uint32_t s = k % 3u;
+        const uint32_t ek = entry(k);
+        if (k + 1 < ncell) {
+            const uint32_t s1 = (k + 1) % 3u, en = entry(k + 1);
+            if (!mbar_wait(&bars[s1], (ph >> s1) & 1u, A.wait_limit_ns, &A.ctrl->error)) return false;
+            ph ^= 1u << s1;
+            if (lane == 0) issue_up(A, wsm + s1 * L.stage, &bars[3 + s1], en & 15u, psi_dir, L);
+        }
+        if (k + 2 < ncell) {
+            const uint32_t s2 = (k + 2) % 3u, en2 = entry(k + 2);
+            if (lane == 0) {
+                fence_proxy_async_shared();  // generic reads of this stage (cell k-1) before the async writes
+                issue_geoq(A, wsm + s2 * L.stage, &bars[s2], en2 >> 4, L);
+            }
+        }
+        if (!mbar_wait(&bars[3 + s], (ph >> (3 + s)) & 1u, A.wait_limit_ns, &A.ctrl->error)) return false;
+        ph ^= 1u << (3 + s);
+        solve_staged_cell(A, wsm + s * L.stage, ek, lane, ox, oy, oz, psi_dir, L);
+        __syncwarp();
+    }
+    return true;
+}
+
 __device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
 
 // Persistent sweep: every warp repeatedly claims a ticket (the next queue
@@ -419,12 +654,25 @@ __device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_re
 // latency overlaps the task.  Termination: exactly n_tasks slots get filled,
 // so a warp whose ticket is >= n_tasks exits.  Every wait is bounded by
 // wait_limit_ns.
-template <class T> __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 3) sweep_kernel(const SweepArgs<T> A)
+// MODE: 0 = any group count (registers), 1 = G a multiple of 32 (registers),
+// 2 = G a multiple of 32 with the rows staged in shared memory.
+template <class T, int MODE>
+__global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 3) sweep_kernel(const SweepArgs<T> A)
 {
     const int lane = threadIdx.x & 31;
     const unsigned FULL = 0xffffffffu;
     const unsigned epoch = *(const volatile unsigned *)&A.ctrl->epoch;
-    const bool wide = (A.G % 32) == 0 && A.max_cells <= 64;
+    extern __shared__ __align__(128) unsigned char dsm[];
+    unsigned char *wsm = dsm + (size_t)(threadIdx.x >> 5) * A.warp_smem;
+    uint32_t ph = 0;  // mbarrier phase parities of this warp's stages
+    if constexpr (MODE == 2) {
+        if (lane == 0) {
+            uint64_t *bars = reinterpret_cast<uint64_t *>(wsm + 3 * StageLayout<T>(A.G).stage);
+            for (int b = 0; b < 6; ++b) mbar_init(&bars[b], 1);
+            fence_proxy_async_shared();
+        }
+        __syncwarp();
+    }
     // per-warp counters live in shared memory (lane 0 updates them) to spare registers
     __shared__ unsigned long long wstat[8][6];  // polls, wait_ns, busy_ns, done, depth, pops
     unsigned long long *ws = wstat[threadIdx.x >> 5];
@@ -484,10 +732,13 @@ template <class T> __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 3
         const uint32_t dir = ti.y >> 16;
         const V4<T> om = ld_ro(A.omega + dir);
         const size_t psi_dir = (size_t)(dir - (uint32_t)A.dir_begin) * (size_t)A.C;
-        if (wide)
+        if constexpr (MODE == 2) {
+            if (!run_task_staged(A, ti, lane, om.x, om.y, om.z, psi_dir, wsm, ph)) break;
+        } else if constexpr (MODE == 1) {
             run_task_wide(A, ti, lane, om.x, om.y, om.z, psi_dir);
-        else
+        } else {
             run_task_generic(A, ti, lane, om.x, om.y, om.z, psi_dir);
+        }
         // release: every lane's psi stores are ordered before any counter decrement
         fence_acq_rel_gpu();
         __syncwarp();
@@ -852,6 +1103,9 @@ struct DeviceState {
     std::vector<int64_t> chunk_seed_begin;  // [n_chunks + 1]
     int64_t max_chunk_tasks = 0;
     int grid = 0, wpc = 0;
+    bool staged = false;
+    int mode = 0;  // sweep kernel variant (see sweep_kernel)
+    uint32_t warp_smem = 0;
     int stats_blocks = 0;
     int last_chunk = -1;
     std::vector<void *> allocs;
@@ -1127,10 +1381,21 @@ tf_status device_create(Problem &p, const int32_t *cell_material, const double *
     if ((s = dmalloc(d, &d.psi, per_dir * Dc)) != TF_OK) return s;
     // persistent grid: resident CTAs per SM x SMs
     d.wpc = p.opt.warps_per_cta > 0 ? std::min(p.opt.warps_per_cta, 4) : 4;  // launch bounds: 128 threads
+    {
+        const size_t wb = d.fp64 ? staged_warp_bytes<double>(d.G) : staged_warp_bytes<float>(d.G);
+        const size_t wb128 = (wb + 127) / 128 * 128;
+        d.staged = p.opt.staging == 0 && d.G % 32 == 0 && g.cells_per_task <= 64 && wb128 * d.wpc <= 227 * 1024;
+        d.warp_smem = d.staged ? (uint32_t)wb128 : 0u;
+    }
+    d.mode = d.staged ? 2 : (d.G % 32 == 0 && g.cells_per_task <= 64 ? 1 : 0);
+    const int dyn = (int)(d.warp_smem * d.wpc);
+    const void *kfn = d.fp64 ? (d.mode == 2 ? (const void *)sweep_kernel<double, 2>
+                                            : d.mode == 1 ? (const void *)sweep_kernel<double, 1> : (const void *)sweep_kernel<double, 0>)
+                             : (d.mode == 2 ? (const void *)sweep_kernel<float, 2>
+                                            : d.mode == 1 ? (const void *)sweep_kernel<float, 1> : (const void *)sweep_kernel<float, 0>);
+    if (dyn > 0) TF_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn));
     int per_sm = 0;
-    cudaError_t e = d.fp64 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_kernel<double>, 32 * d.wpc, 0)
-                           : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_kernel<float>, 32 * d.wpc, 0);
-    if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
+    TF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, 32 * d.wpc, dyn));
     if (p.opt.ctas_per_sm > 0) per_sm = std::min(per_sm, p.opt.ctas_per_sm);
     d.grid = std::max(1, per_sm) * d.sm_count;
     d.ev_start.resize(1 + 2 * d.n_chunks);
@@ -1225,8 +1490,15 @@ template <class T> tf_status launch_step(Problem &p, const double *phi_in, doubl
         A.n_tasks = (unsigned long long)(t1 - t0);
         A.wait_limit_ns = (unsigned long long)(p.opt.wait_limit_s * 1e9);
         A.max_cells = p.graph.cells_per_task;
+        A.warp_smem = d.warp_smem;
         TF_CUDA(cudaEventRecord(d.ev_start[1 + 2 * k], st));
-        sweep_kernel<T><<<d.grid, 32 * d.wpc, 0, st>>>(A);
+        const size_t dyn = (size_t)d.warp_smem * d.wpc;
+        if (d.mode == 2)
+            sweep_kernel<T, 2><<<d.grid, 32 * d.wpc, dyn, st>>>(A);
+        else if (d.mode == 1)
+            sweep_kernel<T, 1><<<d.grid, 32 * d.wpc, 0, st>>>(A);
+        else
+            sweep_kernel<T, 0><<<d.grid, 32 * d.wpc, 0, st>>>(A);
         TF_CUDA(cudaGetLastError());
         TF_CUDA(cudaEventRecord(d.ev_stop[1 + 2 * k], st));
         end_kernel<<<1, 1, 0, st>>>(d.ctrl);
