@@ -199,7 +199,8 @@ def run_ours(args):
     prec = tf.TF_FP64 if args.precision == "fp64" else tf.TF_FP32
     t_setup = time.perf_counter()
     prob = tf.Problem.from_config(cfg, precision=prec, device=local, cells_per_task=args.cells_per_task,
-                                  warps_per_cta=args.warps_per_cta)
+                                  warps_per_cta=args.warps_per_cta, octant_window=args.octant_window,
+                                  staging=args.staging)
     t_setup = time.perf_counter() - t_setup
     C, G, D = prob.n_cells, prob.n_groups, prob.n_dirs
     units = prob.n_units
@@ -253,7 +254,7 @@ def run_ours(args):
                            "max_level": st1["max_level"], "grid_ctas": st1["grid_ctas"],
                            "warps_per_cta": st1["warps_per_cta"], "mean_ready": st1["mean_ready"],
                            "wait_frac": st1["wait_seconds"] / max(st1["wait_seconds"] + st1["busy_seconds"], 1e-30),
-                           "n_chunks": st1["n_chunks"]},
+                           "n_chunks": st1["n_chunks"], "octant_window": args.octant_window or 2},
             "gpu_launches": int((st1["launches_per_step"] + 3) * args.steps),
             "clocks": clk}
     # end to end: tf_sweep with pinned host buffers (H2D of phi_in, D2H of phi_out inside)
@@ -313,6 +314,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-compare", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--octant-window", type=int, default=0, help="octants active at once (0 = library default)")
+    ap.add_argument("--staging", type=int, default=0, help="1 = no shared-memory staging")
     ap.add_argument("--n", type=int, default=0, help="hexes per box edge (default: the workload's)")
     ap.add_argument("--groups", type=int, default=0)
     ap.add_argument("--polar", type=int, default=0)

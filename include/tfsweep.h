@@ -78,7 +78,10 @@ typedef struct {
     int32_t staging;         /* 0 = automatic: stage each cell's rows in shared memory with bulk
                               * asynchronous copies when n_groups is a multiple of 32 and they fit;
                               * 1 = never (registers only) */
-    int32_t reserved_i[6];
+    int32_t octant_window;   /* directions are admitted one octant at a time; this many octants are
+                              * active at once (the next one enters when the oldest is half done);
+                              * 0 = automatic (2), 8 = every direction from the start */
+    int32_t reserved_i[5];
     double residual_floor;   /* stopping-test denominator floor, as a fraction of the group's max |phi|:
                               * 1 (the default; 0 also means 1) = per-group max-norm relative change,
                               * 1e-10 = pointwise relative change (unreachable in FP32 where DG

@@ -71,6 +71,7 @@ struct Ctrl {
     unsigned long long pops;
     unsigned long long residual_bits;  // max residual as ordered bits of a non-negative double
     unsigned long long kernel_ns;      // summed over chunks
+    int next_group;                    // next direction group to admit
 };
 
 // ============================================================== PTX helpers
@@ -181,6 +182,14 @@ template <class T> struct SweepArgs {
     unsigned long long wait_limit_ns;
     int32_t max_cells;           // largest task (cells)
     uint32_t warp_smem;          // dynamic shared memory per warp (staged path)
+    // admission of direction groups (octants): the seeds of group g + window are
+    // released when group g is half done
+    const int32_t *dir_group;    // [D] group index of each direction within its chunk
+    int32_t *group_rem;          // [n_groups] tasks not yet finished (this launch)
+    const int32_t *group_admit;  // [n_groups] remaining count that admits the next group
+    const uint32_t *gseed;       // [n_groups + 1] seed ranges (offsets into seeds)
+    const uint32_t *seeds;
+    int32_t n_groups, window;
 };
 
 // Solve one 4x4 system by Gaussian elimination without pivoting: the
@@ -752,6 +761,31 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 3) sweep_kernel(cons
                     atomicCAS(&A.ctrl->error, 0, (int)TF_ERR_DEVICE);
             }
         }
+        // admission: the task that brings its group to the threshold releases the next group's seeds
+        if (A.window < A.n_groups) {
+            int ng = -1;
+            if (lane == 0) {
+                const int grp = __ldg(A.dir_group + dir);
+                const int left = atomicSub(A.group_rem + grp, 1) - 1;
+                if (left == __ldg(A.group_admit + grp)) {
+                    ng = atomicAdd(&A.ctrl->next_group, 1);
+                    if (ng >= A.n_groups) ng = -1;
+                }
+            }
+            ng = __shfl_sync(FULL, ng, 0);
+            if (ng >= 0) {
+                const uint32_t s0 = __ldg(A.gseed + ng), n = __ldg(A.gseed + ng + 1) - s0;
+                unsigned long long base = 0;
+                if (lane == 0) base = atomicAdd(&A.ctrl->tail, (unsigned long long)n);
+                base = __shfl_sync(FULL, base, 0);
+                if (base + n > A.n_tasks) {
+                    if (lane == 0) atomicCAS(&A.ctrl->error, 0, (int)TF_ERR_DEVICE);
+                } else {
+                    for (uint32_t i = lane; i < n; i += 32)
+                        st_release(A.slots + base + i, ((unsigned long long)epoch << 32) | __ldg(A.seeds + s0 + i));
+                }
+            }
+        }
         __syncwarp();
         if (lane == 0) {
             ws[2] += globaltimer() - tb;
@@ -774,9 +808,10 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 3) sweep_kernel(cons
 }
 
 // New launch: bump the epoch, empty the queue.
-__global__ void begin_kernel(Ctrl *ctrl, unsigned long long n_seeds, int reset_stats)
+__global__ void begin_kernel(Ctrl *ctrl, unsigned long long n_seeds, int reset_stats, int first_group)
 {
     ctrl->epoch = ctrl->epoch + 1u;
+    ctrl->next_group = first_group;
     ctrl->head = 0;
     ctrl->tail = n_seeds;
     if (reset_stats) {
@@ -788,11 +823,15 @@ __global__ void begin_kernel(Ctrl *ctrl, unsigned long long n_seeds, int reset_s
     ctrl->t_last = 0;
 }
 
-// Counters of the chunk's tasks <- in-degrees; the first n_seeds slots <- seeds.
+// Counters of the chunk's tasks <- in-degrees; group counters <- group sizes;
+// the first n_seeds slots <- the seeds of the initially admitted groups.
 __global__ void fill_kernel(Ctrl *ctrl, int *counters, const int *indeg, uint32_t task_begin, uint32_t n_tasks,
-                            unsigned long long *slots, const uint32_t *seeds, uint32_t n_seeds, int inject_stall)
+                            unsigned long long *slots, const uint32_t *seeds, uint32_t n_seeds, int inject_stall,
+                            int *group_rem, const int *group_total, int n_groups)
 {
     const unsigned epoch = ctrl->epoch;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_groups; i += gridDim.x * blockDim.x)
+        group_rem[i] = group_total[i];
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n_tasks; i += gridDim.x * blockDim.x)
         counters[task_begin + i] = indeg[task_begin + i];
     if (inject_stall) return;
@@ -1101,6 +1140,12 @@ struct DeviceState {
     int Dc = 0, n_chunks = 0;
     std::vector<int64_t> chunk_task_begin;  // [n_chunks + 1]
     std::vector<int64_t> chunk_seed_begin;  // [n_chunks + 1]
+    std::vector<int32_t> chunk_group_begin;  // [n_chunks + 1] into the group arrays
+    std::vector<uint32_t> gseed_host;        // [n_groups_total + n_chunks] seed offsets
+    int32_t *dir_group = nullptr;
+    int32_t *group_rem = nullptr, *group_total = nullptr, *group_admit = nullptr;
+    uint32_t *gseed = nullptr;
+    int window = 0;
     int64_t max_chunk_tasks = 0;
     int grid = 0, wpc = 0;
     bool staged = false;
@@ -1358,23 +1403,60 @@ tf_status device_create(Problem &p, const int32_t *cell_material, const double *
     if (Dc < 1) return fail(TF_ERR_NOMEM, "not enough device memory for one direction of angular flux");
     d.Dc = Dc;
     d.n_chunks = (d.D + Dc - 1) / Dc;
-    // seeds per chunk, longest remaining critical path first
+    // Seeds per chunk.  Directions are grouped by octant (sign pattern of Omega,
+    // Sec. 2: the angles of an octant share a sweep orientation); a chunk's
+    // groups are admitted `window` at a time so that the active wavefronts stay
+    // close and their source and face data stay in L2.  Within a group the
+    // seeds with the longest remaining critical path come first.
     std::vector<uint32_t> seeds;
+    std::vector<int32_t> dir_group(d.D, 0), group_total, group_admit;
     d.chunk_task_begin.assign(d.n_chunks + 1, 0);
     d.chunk_seed_begin.assign(d.n_chunks + 1, 0);
+    d.chunk_group_begin.assign(d.n_chunks + 1, 0);
+    d.gseed_host.clear();
+    auto octant = [&](int a) {
+        const double *o = &p.quad->omega[3 * a];
+        return (o[0] < 0.0 ? 1 : 0) | (o[1] < 0.0 ? 2 : 0) | (o[2] < 0.0 ? 4 : 0);
+    };
     for (int k = 0; k < d.n_chunks; ++k) {
         const int a0 = k * Dc, a1 = std::min(d.D, a0 + Dc);
         const int64_t t0 = g.dir_task_begin[a0], t1 = g.dir_task_begin[a1];
         d.chunk_task_begin[k] = t0;
         d.chunk_task_begin[k + 1] = t1;
         d.max_chunk_tasks = std::max(d.max_chunk_tasks, t1 - t0);
-        const size_t sb = seeds.size();
-        for (int64_t t = t0; t < t1; ++t)
-            if (g.task_indeg[t] == 0) seeds.push_back((uint32_t)t);
-        std::stable_sort(seeds.begin() + sb, seeds.end(),
-                         [&](uint32_t x, uint32_t y) { return g.task_blevel[x] > g.task_blevel[y]; });
+        int present[8] = {0}, local[8];
+        for (int a = a0; a < a1; ++a) present[octant(a)] = 1;
+        int ngrp = 0;
+        for (int o = 0; o < 8; ++o) local[o] = present[o] ? ngrp++ : -1;
+        for (int a = a0; a < a1; ++a) dir_group[a] = local[octant(a)];
+        d.chunk_group_begin[k] = (int32_t)group_total.size();
+        std::vector<int64_t> tot(ngrp, 0);
+        for (int a = a0; a < a1; ++a) tot[dir_group[a]] += g.dir_task_begin[a + 1] - g.dir_task_begin[a];
+        for (int j = 0; j < ngrp; ++j) {
+            group_total.push_back((int32_t)tot[j]);
+            group_admit.push_back((int32_t)(tot[j] / 2));
+        }
+        for (int j = 0; j < ngrp; ++j) {
+            d.gseed_host.push_back((uint32_t)seeds.size());
+            const size_t sb = seeds.size();
+            for (int a = a0; a < a1; ++a) {
+                if (dir_group[a] != j) continue;
+                for (int64_t t = g.dir_task_begin[a]; t < g.dir_task_begin[a + 1]; ++t)
+                    if (g.task_indeg[t] == 0) seeds.push_back((uint32_t)t);
+            }
+            std::stable_sort(seeds.begin() + sb, seeds.end(),
+                             [&](uint32_t x, uint32_t y) { return g.task_blevel[x] > g.task_blevel[y]; });
+        }
+        d.gseed_host.push_back((uint32_t)seeds.size());
         d.chunk_seed_begin[k + 1] = (int64_t)seeds.size();
     }
+    d.chunk_group_begin[d.n_chunks] = (int32_t)group_total.size();
+    d.window = p.opt.octant_window > 0 ? p.opt.octant_window : 2;
+    if ((s = upload(d, &d.dir_group, dir_group.data(), dir_group.size() * 4)) != TF_OK) return s;
+    if ((s = upload(d, &d.group_total, group_total.data(), group_total.size() * 4)) != TF_OK) return s;
+    if ((s = upload(d, &d.group_admit, group_admit.data(), group_admit.size() * 4)) != TF_OK) return s;
+    if ((s = dmalloc(d, &d.group_rem, group_total.size() * 4)) != TF_OK) return s;
+    if ((s = upload(d, &d.gseed, d.gseed_host.data(), d.gseed_host.size() * 4)) != TF_OK) return s;
     if ((s = upload(d, &d.seeds, seeds.data(), seeds.size() * 4)) != TF_OK) return s;
     if ((s = dmalloc(d, &d.slots, (size_t)d.max_chunk_tasks * 8)) != TF_OK) return s;
     TF_CUDA(cudaMemset(d.slots, 0, (size_t)d.max_chunk_tasks * 8));
@@ -1461,12 +1543,17 @@ template <class T> tf_status launch_step(Problem &p, const double *phi_in, doubl
     }
     for (int k = 0; k < d.n_chunks; ++k) {
         const int64_t t0 = d.chunk_task_begin[k], t1 = d.chunk_task_begin[k + 1];
-        const int64_t s0 = d.chunk_seed_begin[k], s1 = d.chunk_seed_begin[k + 1];
         const int a0 = k * d.Dc, a1 = std::min(d.D, a0 + d.Dc);
-        begin_kernel<<<1, 1, 0, st>>>(d.ctrl, (unsigned long long)(s1 - s0), k == 0);
+        const int gb = d.chunk_group_begin[k], ng = d.chunk_group_begin[k + 1] - gb;
+        const int win = std::min(d.window, ng);
+        // gseed_host of this chunk: ng + 1 offsets starting at index gb + k
+        const uint32_t *gs = d.gseed_host.data() + gb + k;
+        const uint32_t s0 = gs[0], s_init = gs[win];
+        begin_kernel<<<1, 1, 0, st>>>(d.ctrl, (unsigned long long)(s_init - s0), k == 0, win);
         const int fb = (int)std::min<int64_t>(std::max<int64_t>(1, (t1 - t0 + 255) / 256), (int64_t)d.sm_count * 8);
         fill_kernel<<<fb, 256, 0, st>>>(d.ctrl, d.counters, d.indeg, (uint32_t)t0, (uint32_t)(t1 - t0), d.slots,
-                                        d.seeds + s0, (uint32_t)(s1 - s0), p.opt.inject_stall);
+                                        d.seeds + s0, s_init - s0, p.opt.inject_stall, d.group_rem + gb,
+                                        d.group_total + gb, ng);
         SweepArgs<T> A;
         A.geo = (const CellGeo<T> *)d.geo;
         A.cells = d.cells;
@@ -1491,6 +1578,13 @@ template <class T> tf_status launch_step(Problem &p, const double *phi_in, doubl
         A.wait_limit_ns = (unsigned long long)(p.opt.wait_limit_s * 1e9);
         A.max_cells = p.graph.cells_per_task;
         A.warp_smem = d.warp_smem;
+        A.dir_group = d.dir_group;
+        A.group_rem = d.group_rem + gb;
+        A.group_admit = d.group_admit + gb;
+        A.gseed = d.gseed + gb + k;
+        A.seeds = d.seeds;
+        A.n_groups = ng;
+        A.window = win;
         TF_CUDA(cudaEventRecord(d.ev_start[1 + 2 * k], st));
         const size_t dyn = (size_t)d.warp_smem * d.wpc;
         if (d.mode == 2)
