@@ -190,6 +190,7 @@ template <class T> struct SweepArgs {
     const uint32_t *gseed;       // [n_groups + 1] seed ranges (offsets into seeds)
     const uint32_t *seeds;
     int32_t n_groups, window;
+    int32_t lpc_shift, ppl;      // paired path: log2 lanes per cell, group pairs per lane
 };
 
 // Solve one 4x4 system by Gaussian elimination without pivoting: the
@@ -652,6 +653,222 @@ __device__ __forceinline__ bool run_task_staged(const SweepArgs<T> &A, uint4 ti,
     return true;
 }
 
+// ------------------------------------------------------------------ packed pairs
+// FP32 mode, even G: a lane solves two groups of one cell at once.  Both
+// groups' values of a quantity share one 64-bit register and Blackwell's
+// packed FP32 instructions (add/sub/mul/fma .f32x2) operate on both halves.
+// The source and psi rows are stored pair-interleaved, [cell][G/2][node][2],
+// so one 32-byte load yields the four packed nodal values of a group pair.
+struct f2 {
+    unsigned long long v;
+};
+__device__ __forceinline__ f2 pk(float a, float b)
+{
+    f2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r.v) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void upk(f2 a, float &x, float &y) { asm("mov.b64 {%0, %1}, %2;" : "=f"(x), "=f"(y) : "l"(a.v)); }
+__device__ __forceinline__ f2 operator+(f2 a, f2 b)
+{
+    f2 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d.v) : "l"(a.v), "l"(b.v));
+    return d;
+}
+__device__ __forceinline__ f2 operator*(f2 a, f2 b)
+{
+    f2 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d.v) : "l"(a.v), "l"(b.v));
+    return d;
+}
+__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c)
+{
+    f2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d.v) : "l"(a.v), "l"(b.v), "l"(c.v));
+    return d;
+}
+__device__ __forceinline__ f2 sel2(bool p, f2 a, f2 b)
+{
+    f2 r;
+    r.v = p ? a.v : b.v;
+    return r;
+}
+// -1 / a, halfwise (one MUFU reciprocal each)
+__device__ __forceinline__ f2 nrcp2(f2 a)
+{
+    float x, y;
+    upk(a, x, y);
+    return pk(rcp<float>(-x), rcp<float>(-y));
+}
+struct P4 {
+    f2 x, y, z, w;  // node 0..3, each packed (group 2p, group 2p+1)
+};
+__device__ __forceinline__ P4 ld_pair_ro(const float *p)
+{
+    const ulonglong2 a = __ldg(reinterpret_cast<const ulonglong2 *>(p)), b = __ldg(reinterpret_cast<const ulonglong2 *>(p) + 1);
+    return {{a.x}, {a.y}, {b.x}, {b.y}};
+}
+__device__ __forceinline__ P4 ld_pair_l2(const float *p)
+{
+    const ulonglong2 a = __ldcg(reinterpret_cast<const ulonglong2 *>(p)), b = __ldcg(reinterpret_cast<const ulonglong2 *>(p) + 1);
+    return {{a.x}, {a.y}, {b.x}, {b.y}};
+}
+__device__ __forceinline__ void st_pair(float *p, const P4 &v)
+{
+    reinterpret_cast<ulonglong2 *>(p)[0] = make_ulonglong2(v.x.v, v.y.v);
+    reinterpret_cast<ulonglong2 *>(p)[1] = make_ulonglong2(v.z.v, v.w.v);
+}
+
+// Per-lane cell data of the paired path: the group-independent matrix part
+// W (A = W + sigma (V/20)(1 + delta_ij)), the face weights t_f and V/20, all
+// broadcast into both halves.
+struct PCell {
+    f2 W[4][4];
+    f2 t[4];
+    f2 mv;
+    uint32_t c, mask, code;
+    int32_t nbr[4];
+    int32_t mat;
+};
+
+__device__ __forceinline__ void pcell_setup(const SweepArgs<float> &A, uint32_t entry, float ox, float oy, float oz,
+                                            PCell &s)
+{
+    s.c = entry >> 4;
+    s.mask = entry & 15u;
+    union {
+        CellGeo<float> g;
+        uint4 u[sizeof(CellGeo<float>) / 16];
+    } U;
+    const uint4 *src = reinterpret_cast<const uint4 *>(A.geo + s.c);
+#pragma unroll
+    for (int k = 0; k < (int)(sizeof(CellGeo<float>) / 16); ++k) U.u[k] = __ldg(src + k);
+    const CellGeo<float> &g = U.g;
+    float P[4], t[4], tt = 0.f;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) P[j] = ox * g.gx[j] + oy * g.gy[j] + oz * g.gz[j];
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+        const float sf = ox * g.nx[f] + oy * g.ny[f] + oz * g.nz[f];
+        t[f] = ((s.mask >> f) & 1u) ? fabsf(sf) * (1.f / 12.f) : 0.f;
+        tt += t[f];
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const float w = P[j] + (i == j ? 2.f * (tt - t[i]) : tt - t[i] - t[j]);
+            s.W[i][j] = pk(w, w);
+        }
+#pragma unroll
+    for (int f = 0; f < 4; ++f) s.t[f] = pk(t[f], t[f]);
+    s.mv = pk(g.mv, g.mv);
+    s.code = g.code;
+    s.mat = g.mat;
+#pragma unroll
+    for (int f = 0; f < 4; ++f) s.nbr[f] = g.nbr[f];
+}
+
+// Groups 2p and 2p+1 of one cell: assemble, solve (Gaussian elimination
+// without pivoting, negated multipliers so every update is one packed FMA),
+// store psi (sorted node order, pair-interleaved).
+__device__ __forceinline__ void pair_solve(const SweepArgs<float> &A, const PCell &s, int p, size_t psi_dir, float ox,
+                                           float oy, float oz)
+{
+    const int P = A.G >> 1;
+    const f2 sig = *reinterpret_cast<const f2 *>(A.sigma_t + (size_t)s.mat * A.G + 2 * p);
+    const f2 sv = sig * s.mv;
+    const P4 q = ld_pair_ro(reinterpret_cast<const float *>(A.q) + ((size_t)s.c * P + p) * 8);
+    const f2 qs = (q.x + q.y) + (q.z + q.w);
+    f2 b[4] = {s.mv * (q.x + qs), s.mv * (q.y + qs), s.mv * (q.z + qs), s.mv * (q.w + qs)};
+    if (A.S1) {
+        const float4 s0 = __ldg(A.S1 + (size_t)s.c * A.G + 2 * p), s1 = __ldg(A.S1 + (size_t)s.c * A.G + 2 * p + 1);
+        float mv, mv1;
+        upk(s.mv, mv, mv1);
+        const f2 os = pk(5.f * mv * (ox * s0.x + oy * s0.y + oz * s0.z), 5.f * mv * (ox * s1.x + oy * s1.y + oz * s1.z));
+#pragma unroll
+        for (int i = 0; i < 4; ++i) b[i] = b[i] + os;
+    }
+    const f2 zero = {0ull};
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+        const bool inflow = (s.mask >> f) & 1u;
+        const bool interior = inflow && s.nbr[f] >= 0;
+        P4 u = {zero, zero, zero, zero};
+        if (interior) u = ld_pair_l2(reinterpret_cast<const float *>(A.psi) + ((psi_dir + (size_t)s.nbr[f]) * P + p) * 8);
+        const uint32_t fn = (s.code >> (2 * f)) & 3u;
+        f2 v0 = sel2(fn == 0u, u.y, u.x), v1 = sel2(fn <= 1u, u.z, u.y), v2 = sel2(fn <= 2u, u.w, u.z);
+        if (A.psi_in && inflow && s.nbr[f] < 0) {
+            const int4 tv = __ldg(A.tets + s.c);
+            const int vi[4] = {tv.x, tv.y, tv.z, tv.w};
+            const float *pi = reinterpret_cast<const float *>(A.psi_in);
+            v0 = *reinterpret_cast<const f2 *>(pi + (size_t)vi[f == 0 ? 1 : 0] * A.G + 2 * p);
+            v1 = *reinterpret_cast<const f2 *>(pi + (size_t)vi[f <= 1 ? 2 : 1] * A.G + 2 * p);
+            v2 = *reinterpret_cast<const f2 *>(pi + (size_t)vi[f <= 2 ? 3 : 2] * A.G + 2 * p);
+        }
+        const f2 Uf = (v0 + v1) + v2;
+        const int i0 = f == 0 ? 1 : 0, i1 = f <= 1 ? 2 : 1, i2 = f <= 2 ? 3 : 2;
+        b[i0] = fma2(s.t[f], v0 + Uf, b[i0]);
+        b[i1] = fma2(s.t[f], v1 + Uf, b[i1]);
+        b[i2] = fma2(s.t[f], v2 + Uf, b[i2]);
+    }
+    const f2 two = pk(2.f, 2.f);
+    f2 a[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) a[i][j] = i == j ? fma2(two, sv, s.W[i][i]) : s.W[i][j] + sv;
+    // elimination with n_ik = -a_ik / a_kk
+    const f2 nr0 = nrcp2(a[0][0]);
+    const f2 n10 = a[1][0] * nr0, n20 = a[2][0] * nr0, n30 = a[3][0] * nr0;
+    const f2 a11 = fma2(n10, a[0][1], a[1][1]), a12 = fma2(n10, a[0][2], a[1][2]), a13 = fma2(n10, a[0][3], a[1][3]);
+    const f2 a21 = fma2(n20, a[0][1], a[2][1]), a22 = fma2(n20, a[0][2], a[2][2]), a23 = fma2(n20, a[0][3], a[2][3]);
+    const f2 a31 = fma2(n30, a[0][1], a[3][1]), a32 = fma2(n30, a[0][2], a[3][2]), a33 = fma2(n30, a[0][3], a[3][3]);
+    const f2 b1 = fma2(n10, b[0], b[1]), b2 = fma2(n20, b[0], b[2]), b3 = fma2(n30, b[0], b[3]);
+    const f2 nr1 = nrcp2(a11);
+    const f2 n21 = a21 * nr1, n31 = a31 * nr1;
+    const f2 c22 = fma2(n21, a12, a22), c23 = fma2(n21, a13, a23), c32 = fma2(n31, a12, a32), c33 = fma2(n31, a13, a33);
+    const f2 d2 = fma2(n21, b1, b2), d3 = fma2(n31, b1, b3);
+    const f2 nr2 = nrcp2(c22);
+    const f2 n32 = c32 * nr2;
+    const f2 e33 = fma2(n32, c23, c33), e3 = fma2(n32, d2, d3);
+    // back substitution on y = -x:  y_k = (b_k + sum_{j>k} a_kj y_j) * (-1/a_kk)
+    const f2 y3 = e3 * nrcp2(e33);
+    const f2 y2 = fma2(c23, y3, d2) * nr2;
+    const f2 y1 = fma2(a13, y3, fma2(a12, y2, b1)) * nr1;
+    const f2 y0 = fma2(a[0][3], y3, fma2(a[0][2], y2, fma2(a[0][1], y1, b[0]))) * nr0;
+    const f2 m1 = pk(-1.f, -1.f);
+    P4 o;
+    o.x = y0 * m1;
+    o.y = y1 * m1;
+    o.z = y2 * m1;
+    o.w = y3 * m1;
+    st_pair(reinterpret_cast<float *>(A.psi) + ((psi_dir + (size_t)s.c) * P + p) * 8, o);
+}
+
+// One task on the paired path: lpc lanes share a cell (32 / lpc cells per
+// warp iteration) and each lane solves ppl group pairs of its cell, so one
+// lane's cell setup serves 2 ppl units.
+__device__ __forceinline__ void run_task_paired(const SweepArgs<float> &A, uint4 ti, int lane, float ox, float oy,
+                                                float oz, size_t psi_dir)
+{
+    const uint32_t ncell = ti.y & 0xffffu;
+    const int sh = A.lpc_shift, lpc = 1 << sh, cpi = 32 >> sh;
+    const int sub = lane & (lpc - 1), slot = lane >> sh;
+    for (uint32_t k0 = 0; k0 < ncell; k0 += cpi) {
+        const uint32_t k = k0 + slot;
+        if (k < ncell) {
+            PCell s;
+            pcell_setup(A, __ldg(A.cells + ti.x + k), ox, oy, oz, s);
+            if (k + cpi < ncell && sub == 0) {
+                const uint32_t en = __ldg(A.cells + ti.x + k + cpi);
+                prefetch_l1(A.geo + (en >> 4));
+            }
+            for (int j = 0; j < A.ppl; ++j) pair_solve(A, s, sub + (j << sh), psi_dir, ox, oy, oz);
+        }
+    }
+}
+
 __device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
 
 // Persistent sweep: every warp repeatedly claims a ticket (the next queue
@@ -664,7 +881,8 @@ __device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_re
 // so a warp whose ticket is >= n_tasks exits.  Every wait is bounded by
 // wait_limit_ns.
 // MODE: 0 = any group count (registers), 1 = G a multiple of 32 (registers),
-// 2 = G a multiple of 32 with the rows staged in shared memory.
+// 2 = G a multiple of 32 with the rows staged in shared memory, 3 = FP32 and
+// G even: packed group pairs (pair-interleaved source and psi rows).
 template <class T, int MODE>
 __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 3) sweep_kernel(const SweepArgs<T> A)
 {
@@ -741,7 +959,9 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 3) sweep_kernel(cons
         const uint32_t dir = ti.y >> 16;
         const V4<T> om = ld_ro(A.omega + dir);
         const size_t psi_dir = (size_t)(dir - (uint32_t)A.dir_begin) * (size_t)A.C;
-        if constexpr (MODE == 2) {
+        if constexpr (MODE == 3) {
+            run_task_paired(A, ti, lane, om.x, om.y, om.z, psi_dir);
+        } else if constexpr (MODE == 2) {
             if (!run_task_staged(A, ti, lane, om.x, om.y, om.z, psi_dir, wsm, ph)) break;
         } else if constexpr (MODE == 1) {
             run_task_wide(A, ti, lane, om.x, om.y, om.z, psi_dir);
@@ -853,7 +1073,8 @@ __global__ void end_kernel(Ctrl *ctrl)
 template <class T>
 __global__ void __launch_bounds__(256) source_kernel(const double *__restrict__ phi, const V4<T> *__restrict__ Qext,
                                                      const T *__restrict__ sigma_s, const CellGeo<T> *__restrict__ geo,
-                                                     V4<T> *__restrict__ q, int64_t C, int G, int cells_per_cta)
+                                                     V4<T> *__restrict__ q, int64_t C, int G, int cells_per_cta,
+                                                     int paired)
 {
     extern __shared__ unsigned char smem_raw[];
     T *ph = reinterpret_cast<T *>(smem_raw);  // [cells_per_cta][G][4]
@@ -878,13 +1099,22 @@ __global__ void __launch_bounds__(256) source_kernel(const double *__restrict__ 
                 a[2] += s * p[4 * h + 2];
                 a[3] += s * p[4 * h + 3];
             }
-            const V4<T> Qv = ld_ro(Qext + (size_t)c * G + g);
-            V4<T> o;
-            o.x = (Qv.x + pick4(a, (code >> 8) & 3u)) * inv4pi;
-            o.y = (Qv.y + pick4(a, (code >> 10) & 3u)) * inv4pi;
-            o.z = (Qv.z + pick4(a, (code >> 12) & 3u)) * inv4pi;
-            o.w = (Qv.w + pick4(a, (code >> 14) & 3u)) * inv4pi;
-            q[(size_t)c * G + g] = o;
+            if (paired) {
+                // [c][G/2][node][2]: node j of group g at ((c G/2 + g/2) 4 + j) 2 + (g & 1)
+                const size_t base = ((size_t)c * (G >> 1) + (g >> 1)) * 8 + (g & 1);
+                const T *Qf = reinterpret_cast<const T *>(Qext) + base;
+                T *qf = reinterpret_cast<T *>(q) + base;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) qf[2 * j] = (__ldg(Qf + 2 * j) + pick4(a, (code >> (8 + 2 * j)) & 3u)) * inv4pi;
+            } else {
+                const V4<T> Qv = ld_ro(Qext + (size_t)c * G + g);
+                V4<T> o;
+                o.x = (Qv.x + pick4(a, (code >> 8) & 3u)) * inv4pi;
+                o.y = (Qv.y + pick4(a, (code >> 10) & 3u)) * inv4pi;
+                o.z = (Qv.z + pick4(a, (code >> 12) & 3u)) * inv4pi;
+                o.w = (Qv.w + pick4(a, (code >> 14) & 3u)) * inv4pi;
+                q[(size_t)c * G + g] = o;
+            }
         }
     }
 }
@@ -989,6 +1219,88 @@ __global__ void __launch_bounds__(256) phi_kernel(const V4<T> *__restrict__ psi,
         }
         out[0] = make_double2(o[0], o[1]);
         out[1] = make_double2(o[2], o[3]);
+    }
+}
+
+// Paired layout (FP32, even G): thread per (cell, group pair); per direction
+// one 32-byte load of the pair's 8 nodal values, the same accumulation rules.
+template <bool PAIR>
+__global__ void __launch_bounds__(256) phi_pair_kernel(const float *__restrict__ psi, const WeightPair *__restrict__ wts,
+                                                       int Dc, size_t CP, int G, const CellGeo<float> *__restrict__ geo,
+                                                       double *__restrict__ phi, int accumulate)
+{
+    const int P = G >> 1;
+    for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < CP; idx += (size_t)gridDim.x * blockDim.x) {
+        double r[8];  // [node j][half h] at 2 j + h, sorted node order
+        if constexpr (PAIR) {
+            float hi[8], lo[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) hi[i] = lo[i] = 0.f;
+            for (int a = 0; a < Dc; ++a) {
+                const float4 *src = reinterpret_cast<const float4 *>(psi + ((size_t)a * CP + idx) * 8);
+                const float4 u = __ldcs(src), v = __ldcs(src + 1);
+                const float x[8] = {u.x, u.y, u.z, u.w, v.x, v.y, v.z, v.w};
+                const WeightPair w = wts[a];
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const float pp = w.hi * x[i];
+                    const float e = fmaf(w.hi, x[i], -pp) + w.lo * x[i];
+                    two_sum_acc(hi[i], lo[i], pp, e);
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < 8; ++i) r[i] = (double)hi[i] + (double)lo[i];
+        } else {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) r[i] = 0.0;
+            for (int a = 0; a < Dc; ++a) {
+                const float4 *src = reinterpret_cast<const float4 *>(psi + ((size_t)a * CP + idx) * 8);
+                const float4 u = __ldcs(src), v = __ldcs(src + 1);
+                const float x[8] = {u.x, u.y, u.z, u.w, v.x, v.y, v.z, v.w};
+                const double w = wts[a].d;
+#pragma unroll
+                for (int i = 0; i < 8; ++i) r[i] = fma(w, (double)x[i], r[i]);
+            }
+        }
+        const size_t c = idx / (size_t)P;
+        const int p = (int)(idx - c * (size_t)P);
+        const uint32_t code = __ldg(&geo[c].code);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const double rs[4] = {r[h], r[2 + h], r[4 + h], r[6 + h]};
+            double o[4];
+            scatter4(rs, code, o);
+            double2 *out = reinterpret_cast<double2 *>(phi + ((size_t)c * G + 2 * p + h) * 4);
+            if (accumulate) {
+                const double2 o0 = out[0], o1 = out[1];
+                o[0] += o0.x;
+                o[1] += o0.y;
+                o[2] += o1.x;
+                o[3] += o1.y;
+            }
+            out[0] = make_double2(o[0], o[1]);
+            out[1] = make_double2(o[2], o[3]);
+        }
+    }
+}
+
+// psi of one direction, paired layout -> [C][G][4] in the caller's node order.
+__global__ void psi_unpair_kernel(const float *__restrict__ src, float4 *__restrict__ dst, size_t CP, int G,
+                                  const CellGeo<float> *__restrict__ geo)
+{
+    const int P = G >> 1;
+    for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < CP; idx += (size_t)gridDim.x * blockDim.x) {
+        const size_t c = idx / (size_t)P;
+        const int p = (int)(idx - c * (size_t)P);
+        const uint32_t code = __ldg(&geo[c].code);
+        const float *s8 = src + idx * 8;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const float r[4] = {s8[h], s8[2 + h], s8[4 + h], s8[6 + h]};
+            float o[4];
+            scatter4(r, code, o);
+            dst[(size_t)c * G + 2 * p + h] = make_float4(o[0], o[1], o[2], o[3]);
+        }
     }
 }
 
@@ -1149,6 +1461,8 @@ struct DeviceState {
     int64_t max_chunk_tasks = 0;
     int grid = 0, wpc = 0;
     bool staged = false;
+    bool paired = false;  // FP32, even G: packed group pairs, pair-interleaved q and psi
+    int lpc_shift = 0, ppl = 0;
     int mode = 0;  // sweep kernel variant (see sweep_kernel)
     uint32_t warp_smem = 0;
     int stats_blocks = 0;
@@ -1282,8 +1596,11 @@ template <class T> tf_status create_typed(Problem &p, DeviceState &d, const int3
             int s2u[4];
             sorted_order(&m.tets[4 * c], s2u);
             for (int gq = 0; gq < d.G; ++gq)
-                for (int j = 0; j < 4; ++j)
-                    Qs[((size_t)c * d.G + gq) * 4 + j] = Q[((size_t)c * d.G + gq) * 4 + s2u[j]];
+                for (int j = 0; j < 4; ++j) {
+                    const size_t at = d.paired ? (((size_t)c * (d.G / 2) + gq / 2) * 4 + j) * 2 + (gq & 1)
+                                               : ((size_t)c * d.G + gq) * 4 + j;
+                    Qs[at] = Q[((size_t)c * d.G + gq) * 4 + s2u[j]];
+                }
         }
         if ((s = upload_typed<T>(d, &d.Q, Qs.data(), Qs.size())) != TF_OK) return s;
     }
@@ -1327,6 +1644,16 @@ tf_status device_create(Problem &p, const int32_t *cell_material, const double *
     d.D = p.quad->D;
     d.M = p.M;
     d.fp64 = p.opt.precision == TF_FP64;
+    d.paired = !d.fp64 && d.G % 2 == 0 && p.opt.pairing == 0;
+    if (d.paired) {
+        // lanes per cell: the largest power of two <= (G/2)/4 that divides G/2 (at most 32)
+        const int P = d.G / 2;
+        int lpc = 1;
+        while (lpc * 2 <= 32 && lpc * 2 * 4 <= P && P % (lpc * 2) == 0) lpc *= 2;
+        d.ppl = P / lpc;
+        d.lpc_shift = 0;
+        while ((1 << d.lpc_shift) < lpc) ++d.lpc_shift;
+    }
     d.tsize = d.fp64 ? 8 : 4;
     const int64_t T = g.T();
     if ((uint64_t)g.down_list.size() >= (1ull << 32)) return fail(TF_ERR_ARG, "graph too large: 2^32 downwind edges");
@@ -1469,12 +1796,18 @@ tf_status device_create(Problem &p, const int32_t *cell_material, const double *
         d.staged = p.opt.staging == 0 && d.G % 32 == 0 && g.cells_per_task <= 64 && wb128 * d.wpc <= 227 * 1024;
         d.warp_smem = d.staged ? (uint32_t)wb128 : 0u;
     }
-    d.mode = d.staged ? 2 : (d.G % 32 == 0 && g.cells_per_task <= 64 ? 1 : 0);
-    const int dyn = (int)(d.warp_smem * d.wpc);
+    d.mode = d.paired ? 3 : d.staged ? 2 : (d.G % 32 == 0 && g.cells_per_task <= 64 ? 1 : 0);
+    if (d.paired) {
+        d.staged = false;
+        d.warp_smem = 0;
+    }
+    const int dyn = d.paired ? 0 : (int)(d.warp_smem * d.wpc);
     const void *kfn = d.fp64 ? (d.mode == 2 ? (const void *)sweep_kernel<double, 2>
                                             : d.mode == 1 ? (const void *)sweep_kernel<double, 1> : (const void *)sweep_kernel<double, 0>)
-                             : (d.mode == 2 ? (const void *)sweep_kernel<float, 2>
-                                            : d.mode == 1 ? (const void *)sweep_kernel<float, 1> : (const void *)sweep_kernel<float, 0>);
+                             : (d.mode == 3   ? (const void *)sweep_kernel<float, 3>
+                                : d.mode == 2 ? (const void *)sweep_kernel<float, 2>
+                                : d.mode == 1 ? (const void *)sweep_kernel<float, 1>
+                                              : (const void *)sweep_kernel<float, 0>);
     if (dyn > 0) TF_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn));
     int per_sm = 0;
     TF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, 32 * d.wpc, dyn));
@@ -1537,7 +1870,8 @@ template <class T> tf_status launch_step(Problem &p, const double *phi_in, doubl
         const int blocks = (int)std::min<int64_t>((d.C + cpc - 1) / cpc, (int64_t)d.sm_count * 16);
         TF_CUDA(cudaEventRecord(d.ev_start[0], st));
         source_kernel<T><<<blocks, 256, smem, st>>>(phi_in, (const V4<T> *)d.Q, (const T *)d.sigma_s,
-                                                    (const CellGeo<T> *)d.geo, (V4<T> *)d.q, d.C, d.G, cpc);
+                                                    (const CellGeo<T> *)d.geo, (V4<T> *)d.q, d.C, d.G, cpc,
+                                                    d.paired ? 1 : 0);
         TF_CUDA(cudaGetLastError());
         TF_CUDA(cudaEventRecord(d.ev_stop[0], st));
     }
@@ -1585,9 +1919,15 @@ template <class T> tf_status launch_step(Problem &p, const double *phi_in, doubl
         A.seeds = d.seeds;
         A.n_groups = ng;
         A.window = win;
+        A.lpc_shift = d.lpc_shift;
+        A.ppl = d.ppl;
         TF_CUDA(cudaEventRecord(d.ev_start[1 + 2 * k], st));
         const size_t dyn = (size_t)d.warp_smem * d.wpc;
-        if (d.mode == 2)
+        if constexpr (sizeof(T) == 4) {
+            if (d.mode == 3) sweep_kernel<T, 3><<<d.grid, 32 * d.wpc, 0, st>>>(A);
+        }
+        if (d.mode == 3) {
+        } else if (d.mode == 2)
             sweep_kernel<T, 2><<<d.grid, 32 * d.wpc, dyn, st>>>(A);
         else if (d.mode == 1)
             sweep_kernel<T, 1><<<d.grid, 32 * d.wpc, 0, st>>>(A);
@@ -1598,7 +1938,16 @@ template <class T> tf_status launch_step(Problem &p, const double *phi_in, doubl
         end_kernel<<<1, 1, 0, st>>>(d.ctrl);
         const int pb = (int)std::min<size_t>((CG + 255) / 256, (size_t)d.sm_count * 32);
         TF_CUDA(cudaEventRecord(d.ev_start[2 + 2 * k], st));
-        if (!d.fp64 && p.opt.phi_accumulate == TF_PHI_PAIR)
+        if (d.paired) {
+            const size_t CP = CG / 2;
+            const int pb2 = (int)std::min<size_t>((CP + 255) / 256, (size_t)d.sm_count * 32);
+            if (p.opt.phi_accumulate == TF_PHI_PAIR)
+                phi_pair_kernel<true><<<pb2, 256, 0, st>>>((const float *)d.psi, d.wts + a0, a1 - a0, CP, d.G,
+                                                           (const CellGeo<float> *)d.geo, phi_out, k > 0);
+            else
+                phi_pair_kernel<false><<<pb2, 256, 0, st>>>((const float *)d.psi, d.wts + a0, a1 - a0, CP, d.G,
+                                                            (const CellGeo<float> *)d.geo, phi_out, k > 0);
+        } else if (!d.fp64 && p.opt.phi_accumulate == TF_PHI_PAIR)
             phi_kernel<T, true><<<pb, 256, 0, st>>>((const V4<T> *)d.psi, d.wts + a0, a1 - a0, CG, d.G,
                                                     (const CellGeo<T> *)d.geo, phi_out, k > 0);
         else
@@ -1754,7 +2103,10 @@ tf_status device_psi(Problem &p, int32_t dir, void *out, void *stream)
     const size_t CG = (size_t)d.C * d.G;
     cudaStream_t st = (cudaStream_t)stream;
     const int blocks = (int)std::min<size_t>((CG + 255) / 256, (size_t)d.sm_count * 16);
-    if (d.fp64)
+    if (d.paired)
+        psi_unpair_kernel<<<blocks, 256, 0, st>>>((const float *)d.psi + (size_t)(dir - a0) * CG * 4, (float4 *)out,
+                                                  CG / 2, d.G, (const CellGeo<float> *)d.geo);
+    else if (d.fp64)
         psi_unsort_kernel<double><<<blocks, 256, 0, st>>>((const V4<double> *)d.psi + (size_t)(dir - a0) * CG,
                                                           (V4<double> *)out, CG, d.G, (const CellGeo<double> *)d.geo);
     else

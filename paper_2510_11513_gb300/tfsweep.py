@@ -36,7 +36,7 @@ class tf_options(C.Structure):
         ("warps_per_cta", C.c_int32), ("ctas_per_sm", C.c_int32), ("wait_limit_s", C.c_double),
         ("phi_accumulate", C.c_int32), ("inject_stall", C.c_int32), ("psi_budget_gb", C.c_double),
         ("task_order", C.c_int32), ("staging", C.c_int32), ("octant_window", C.c_int32),
-        ("reserved_i", C.c_int32 * 5),
+        ("pairing", C.c_int32), ("reserved_i", C.c_int32 * 4),
         ("residual_floor", C.c_double),
         ("reserved_d", C.c_double * 3),
     ]

@@ -47,6 +47,30 @@ def test_one_sweep_matches_oracle(precision, G, cells_per_task, dir_chunk):
     assert st["tasks_executed"] == st["n_tasks"]
 
 
+# FP32 kernel variants: packed group pairs (even G, default), shared-memory
+# staging (G multiple of 32, pairing off), registers only (staging off), and
+# the any-G path; G and cells_per_task chosen to leave ragged tails.
+@pytest.mark.parametrize("G,opts", [
+    (2, {}), (6, {}), (12, dict(cells_per_task=5)), (24, {}), (40, {}), (64, {}), (64, dict(cells_per_task=7)),
+    (128, {}), (32, dict(pairing=1)), (64, dict(pairing=1)), (64, dict(pairing=1, staging=1)),
+    (32, dict(pairing=1, staging=1, cells_per_task=9)), (8, dict(pairing=1)), (64, dict(octant_window=8)),
+    (64, dict(octant_window=1, dir_chunk=7)),
+])
+def test_fp32_variants_match_oracle(G, opts):
+    cfg = W.two_material_box(n=4, G=G, n_polar=4, n_az=8)
+    P = oracle.Problem(cfg)
+    phi_in = _seeded_phi(P.C, G, seed=G)
+    ref = P.transport_step(phi_in, threads=8)
+    prob = tf.Problem.from_config(cfg, precision=tf.TF_FP32, **opts)
+    out = torch.zeros_like(_dev(phi_in))
+    prob.sweep(_dev(phi_in), out)
+    assert _rel(out.cpu().numpy(), ref) < 2e-5
+    buf = torch.empty((P.C, G, 4), dtype=torch.float32, device="cuda")
+    q = P.source(phi_in)
+    for a in (0, P.D - 1):
+        assert _rel(prob.psi(a, buf).double().cpu().numpy(), P.sweep_direction(a, q)) < 2e-5
+
+
 @pytest.mark.parametrize("precision", [tf.TF_FP64, tf.TF_FP32])
 def test_psi_of_every_direction_matches_oracle(precision):
     cfg = W.two_material_box(n=6, G=8, n_polar=2, n_az=8)
