@@ -719,28 +719,32 @@ __device__ __forceinline__ void st_pair(float *p, const P4 &v)
     reinterpret_cast<ulonglong2 *>(p)[1] = make_ulonglong2(v.z.v, v.w.v);
 }
 
-// Per-lane cell data of the paired path: the group-independent matrix part
-// W (A = W + sigma (V/20)(1 + delta_ij)), the face weights t_f and V/20, all
-// broadcast into both halves.
-struct PCell {
+// Cell table of the paired path: one 256-byte row per task cell, written once
+// per task by the lane that owns the cell (lane-parallel setup) and read by
+// every lane that solves one of the cell's group pairs.  W is the
+// group-independent matrix part (A = W + sigma (V/20)(1 + delta_ij)), t the
+// inflow face weights, mv = V/20, all broadcast into both halves.
+struct TabRow {
     f2 W[4][4];
     f2 t[4];
     f2 mv;
     uint32_t c, mask, code;
-    int32_t nbr[4];
     int32_t mat;
+    int32_t nbr[4];
+    uint32_t upmask;  // interior inflow faces (their psi rows are staged, in face order)
+    uint32_t pad[13];
 };
+static_assert(sizeof(TabRow) == 256, "table row must be 256 bytes");
 
-__device__ __forceinline__ void pcell_setup(const SweepArgs<float> &A, uint32_t entry, float ox, float oy, float oz,
-                                            PCell &s)
+__device__ __forceinline__ void tab_setup(const SweepArgs<float> &A, uint32_t entry, float ox, float oy, float oz,
+                                          TabRow &r)
 {
-    s.c = entry >> 4;
-    s.mask = entry & 15u;
+    const uint32_t c = entry >> 4, mask = entry & 15u;
     union {
         CellGeo<float> g;
         uint4 u[sizeof(CellGeo<float>) / 16];
     } U;
-    const uint4 *src = reinterpret_cast<const uint4 *>(A.geo + s.c);
+    const uint4 *src = reinterpret_cast<const uint4 *>(A.geo + c);
 #pragma unroll
     for (int k = 0; k < (int)(sizeof(CellGeo<float>) / 16); ++k) U.u[k] = __ldg(src + k);
     const CellGeo<float> &g = U.g;
@@ -750,7 +754,7 @@ __device__ __forceinline__ void pcell_setup(const SweepArgs<float> &A, uint32_t 
 #pragma unroll
     for (int f = 0; f < 4; ++f) {
         const float sf = ox * g.nx[f] + oy * g.ny[f] + oz * g.nz[f];
-        t[f] = ((s.mask >> f) & 1u) ? fabsf(sf) * (1.f / 12.f) : 0.f;
+        t[f] = ((mask >> f) & 1u) ? fabsf(sf) * (1.f / 12.f) : 0.f;
         tt += t[f];
     }
 #pragma unroll
@@ -758,59 +762,78 @@ __device__ __forceinline__ void pcell_setup(const SweepArgs<float> &A, uint32_t 
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             const float w = P[j] + (i == j ? 2.f * (tt - t[i]) : tt - t[i] - t[j]);
-            s.W[i][j] = pk(w, w);
+            r.W[i][j] = pk(w, w);
         }
+    uint32_t up = 0;
 #pragma unroll
-    for (int f = 0; f < 4; ++f) s.t[f] = pk(t[f], t[f]);
-    s.mv = pk(g.mv, g.mv);
-    s.code = g.code;
-    s.mat = g.mat;
-#pragma unroll
-    for (int f = 0; f < 4; ++f) s.nbr[f] = g.nbr[f];
+    for (int f = 0; f < 4; ++f) {
+        r.t[f] = pk(t[f], t[f]);
+        r.nbr[f] = g.nbr[f];
+        up |= (((mask >> f) & 1u) && g.nbr[f] >= 0) ? (1u << f) : 0u;
+    }
+    r.mv = pk(g.mv, g.mv);
+    r.c = c;
+    r.mask = mask;
+    r.code = g.code;
+    r.mat = g.mat;
+    r.upmask = up;
 }
 
-// Groups 2p and 2p+1 of one cell: assemble, solve (Gaussian elimination
+// Groups 2p and 2p+1 of one staged cell: assemble, solve (Gaussian elimination
 // without pivoting, negated multipliers so every update is one packed FMA),
-// store psi (sorted node order, pair-interleaved).
-__device__ __forceinline__ void pair_solve(const SweepArgs<float> &A, const PCell &s, int p, size_t psi_dir, float ox,
-                                           float oy, float oz)
+// store psi (sorted node order, pair-interleaved).  qrow: the cell's staged
+// source row; ups: its staged upwind rows, one per interior inflow face in
+// face order; row = G/2 pairs x 32 bytes.
+__device__ __forceinline__ void pair_solve(const SweepArgs<float> &A, const TabRow &s, const unsigned char *qrow,
+                                           uint32_t row, int p, size_t psi_dir, float ox, float oy, float oz)
 {
     const int P = A.G >> 1;
     const f2 sig = *reinterpret_cast<const f2 *>(A.sigma_t + (size_t)s.mat * A.G + 2 * p);
-    const f2 sv = sig * s.mv;
-    const P4 q = ld_pair_ro(reinterpret_cast<const float *>(A.q) + ((size_t)s.c * P + p) * 8);
-    const f2 qs = (q.x + q.y) + (q.z + q.w);
-    f2 b[4] = {s.mv * (q.x + qs), s.mv * (q.y + qs), s.mv * (q.z + qs), s.mv * (q.w + qs)};
+    const f2 mv = s.mv;
+    const f2 sv = sig * mv;
+    const ulonglong2 *qp = reinterpret_cast<const ulonglong2 *>(qrow + (size_t)p * 32);
+    const ulonglong2 q01 = qp[0], q23 = qp[1];
+    const f2 qx = {q01.x}, qy = {q01.y}, qz = {q23.x}, qw = {q23.y};
+    const f2 qs = (qx + qy) + (qz + qw);
+    f2 b[4] = {mv * (qx + qs), mv * (qy + qs), mv * (qz + qs), mv * (qw + qs)};
+    const uint32_t c = s.c, code = s.code, upmask = s.upmask, mask = s.mask;
     if (A.S1) {
-        const float4 s0 = __ldg(A.S1 + (size_t)s.c * A.G + 2 * p), s1 = __ldg(A.S1 + (size_t)s.c * A.G + 2 * p + 1);
-        float mv, mv1;
-        upk(s.mv, mv, mv1);
-        const f2 os = pk(5.f * mv * (ox * s0.x + oy * s0.y + oz * s0.z), 5.f * mv * (ox * s1.x + oy * s1.y + oz * s1.z));
+        const float4 s0 = __ldg(A.S1 + (size_t)c * A.G + 2 * p), s1 = __ldg(A.S1 + (size_t)c * A.G + 2 * p + 1);
+        float m0, m1;
+        upk(mv, m0, m1);
+        const f2 os = pk(5.f * m0 * (ox * s0.x + oy * s0.y + oz * s0.z), 5.f * m1 * (ox * s1.x + oy * s1.y + oz * s1.z));
 #pragma unroll
         for (int i = 0; i < 4; ++i) b[i] = b[i] + os;
     }
-    const f2 zero = {0ull};
 #pragma unroll
     for (int f = 0; f < 4; ++f) {
-        const bool inflow = (s.mask >> f) & 1u;
-        const bool interior = inflow && s.nbr[f] >= 0;
-        P4 u = {zero, zero, zero, zero};
-        if (interior) u = ld_pair_l2(reinterpret_cast<const float *>(A.psi) + ((psi_dir + (size_t)s.nbr[f]) * P + p) * 8);
-        const uint32_t fn = (s.code >> (2 * f)) & 3u;
-        f2 v0 = sel2(fn == 0u, u.y, u.x), v1 = sel2(fn <= 1u, u.z, u.y), v2 = sel2(fn <= 2u, u.w, u.z);
-        if (A.psi_in && inflow && s.nbr[f] < 0) {
-            const int4 tv = __ldg(A.tets + s.c);
+        if (!((mask >> f) & 1u)) continue;
+        f2 v0, v1, v2;
+        if ((upmask >> f) & 1u) {
+            const uint32_t slot = __popc(upmask & ((1u << f) - 1u));
+            const ulonglong2 *up = reinterpret_cast<const ulonglong2 *>(qrow + (size_t)(1 + slot) * row + (size_t)p * 32);
+            const ulonglong2 u01 = up[0], u23 = up[1];
+            const f2 ux = {u01.x}, uy = {u01.y}, uz = {u23.x}, uw = {u23.y};
+            const uint32_t fn = (code >> (2 * f)) & 3u;
+            v0 = sel2(fn == 0u, uy, ux);
+            v1 = sel2(fn <= 1u, uz, uy);
+            v2 = sel2(fn <= 2u, uw, uz);
+        } else if (A.psi_in) {
+            const int4 tv = __ldg(A.tets + c);
             const int vi[4] = {tv.x, tv.y, tv.z, tv.w};
-            const float *pi = reinterpret_cast<const float *>(A.psi_in);
+            const float *pi = A.psi_in;
             v0 = *reinterpret_cast<const f2 *>(pi + (size_t)vi[f == 0 ? 1 : 0] * A.G + 2 * p);
             v1 = *reinterpret_cast<const f2 *>(pi + (size_t)vi[f <= 1 ? 2 : 1] * A.G + 2 * p);
             v2 = *reinterpret_cast<const f2 *>(pi + (size_t)vi[f <= 2 ? 3 : 2] * A.G + 2 * p);
+        } else {
+            continue;  // vacuum
         }
         const f2 Uf = (v0 + v1) + v2;
+        const f2 tf = s.t[f];
         const int i0 = f == 0 ? 1 : 0, i1 = f <= 1 ? 2 : 1, i2 = f <= 2 ? 3 : 2;
-        b[i0] = fma2(s.t[f], v0 + Uf, b[i0]);
-        b[i1] = fma2(s.t[f], v1 + Uf, b[i1]);
-        b[i2] = fma2(s.t[f], v2 + Uf, b[i2]);
+        b[i0] = fma2(tf, v0 + Uf, b[i0]);
+        b[i1] = fma2(tf, v1 + Uf, b[i1]);
+        b[i2] = fma2(tf, v2 + Uf, b[i2]);
     }
     const f2 two = pk(2.f, 2.f);
     f2 a[4][4];
@@ -843,30 +866,96 @@ __device__ __forceinline__ void pair_solve(const SweepArgs<float> &A, const PCel
     o.y = y1 * m1;
     o.z = y2 * m1;
     o.w = y3 * m1;
-    st_pair(reinterpret_cast<float *>(A.psi) + ((psi_dir + (size_t)s.c) * P + p) * 8, o);
+    st_pair(reinterpret_cast<float *>(A.psi) + ((psi_dir + (size_t)c) * P + p) * 8, o);
 }
 
-// One task on the paired path: lpc lanes share a cell (32 / lpc cells per
-// warp iteration) and each lane solves ppl group pairs of its cell, so one
-// lane's cell setup serves 2 ppl units.
-__device__ __forceinline__ void run_task_paired(const SweepArgs<float> &A, uint4 ti, int lane, float ox, float oy,
-                                                float oz, size_t psi_dir)
-{
-    const uint32_t ncell = ti.y & 0xffffu;
-    const int sh = A.lpc_shift, lpc = 1 << sh, cpi = 32 >> sh;
-    const int sub = lane & (lpc - 1), slot = lane >> sh;
-    for (uint32_t k0 = 0; k0 < ncell; k0 += cpi) {
-        const uint32_t k = k0 + slot;
-        if (k < ncell) {
-            PCell s;
-            pcell_setup(A, __ldg(A.cells + ti.x + k), ox, oy, oz, s);
-            if (k + cpi < ncell && sub == 0) {
-                const uint32_t en = __ldg(A.cells + ti.x + k + cpi);
-                prefetch_l1(A.geo + (en >> 4));
-            }
-            for (int j = 0; j < A.ppl; ++j) pair_solve(A, s, sub + (j << sh), psi_dir, ox, oy, oz);
-        }
+// Shared memory of one warp on the paired path: the cell table, three stage
+// buffers (each: cps cells x [source row, 3 upwind rows]) and their mbarriers.
+struct PairLayout {
+    uint32_t P, row, cps, lpc_shift, ppl, stage, table;
+    __device__ __host__ PairLayout(int G, int max_cells)
+    {
+        P = (uint32_t)G / 2;
+        row = P * 32u;
+        lpc_shift = 0;  // lanes per cell: the smallest power of two >= min(P, 32)
+        while ((1u << lpc_shift) < (P >= 32u ? 32u : P)) ++lpc_shift;
+        cps = 32u >> lpc_shift;        // cells per stage
+        ppl = (P + 31u) / 32u;         // pair slots per lane
+        stage = cps * 4u * row;
+        table = (uint32_t)max_cells * (uint32_t)sizeof(TabRow);
     }
+    __device__ __host__ uint32_t bytes() const { return table + 3u * stage + 3u * 8u; }
+};
+
+// One task on the paired path.  Lanes first build the task's cell table in
+// parallel (lane j: cell j), then the stages (cps cells each) stream through
+// a three-buffer ring of bulk asynchronous copies while lanes solve pairs:
+// lane l takes cell l >> lpc_shift of the stage and pairs (l mod lpc) + 32 m.
+// Returns false if a wait ran out (error word set).
+__device__ __forceinline__ bool run_task_pairs(const SweepArgs<float> &A, uint4 ti, int lane, float ox, float oy,
+                                               float oz, size_t psi_dir, unsigned char *wsm, uint32_t &ph)
+{
+    const unsigned FULL = 0xffffffffu;
+    const uint32_t ncell = ti.y & 0xffffu;
+    const PairLayout L(A.G, A.max_cells);
+    TabRow *tab = reinterpret_cast<TabRow *>(wsm);
+    unsigned char *stages = wsm + L.table;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(stages + 3 * L.stage);
+    for (uint32_t j = lane; j < ncell; j += 32) tab_setup(A, __ldg(A.cells + ti.x + j), ox, oy, oz, tab[j]);
+    __syncwarp();
+    const uint32_t nst = (ncell + L.cps - 1) / L.cps;
+    // psi rows written by other warps (generic proxy, acquired through the queue)
+    // are read below by the async proxy
+    fence_proxy_async_global();
+    auto issue = [&](uint32_t st) {
+        const uint32_t b = st % 3u, k0 = st * L.cps;
+        const uint32_t k = k0 + (uint32_t)lane;
+        const bool mine = (uint32_t)lane < L.cps && k < ncell;
+        uint32_t upm = mine ? tab[k].upmask : 0u;
+        if (__popc(upm) > 3) {  // a closed tetrahedron has at most three inflow faces
+            atomicCAS(&A.ctrl->error, 0, (int)TF_ERR_DEVICE);
+            upm = 0u;
+        }
+        const uint32_t rows = mine ? 1u + __popc(upm) : 0u;
+        const uint32_t bytes = __reduce_add_sync(FULL, rows) * L.row;
+        if (lane == 0) {
+            fence_proxy_async_shared();  // earlier generic reads of this buffer come first
+            mbar_arrive_expect_tx(&bars[b], bytes);
+        }
+        __syncwarp();
+        if (mine) {
+            unsigned char *dst = stages + b * L.stage + (size_t)lane * 4u * L.row;
+            const TabRow &r = tab[k];
+            bulk_g2s(dst, reinterpret_cast<const float *>(A.q) + (size_t)r.c * L.P * 8, L.row, &bars[b]);
+            uint32_t slot = 1;
+#pragma unroll
+            for (int f = 0; f < 4; ++f)
+                if ((upm >> f) & 1u) {
+                    bulk_g2s(dst + slot * L.row, reinterpret_cast<const float *>(A.psi) + (psi_dir + (size_t)r.nbr[f]) * L.P * 8,
+                             L.row, &bars[b]);
+                    ++slot;
+                }
+        }
+    };
+    issue(0);
+    if (nst > 1) issue(1);
+    for (uint32_t st = 0; st < nst; ++st) {
+        if (st + 2 < nst) issue(st + 2);
+        const uint32_t b = st % 3u;
+        if (!mbar_wait(&bars[b], (ph >> b) & 1u, A.wait_limit_ns, &A.ctrl->error)) return false;
+        ph ^= 1u << b;
+        const uint32_t j = (uint32_t)lane >> L.lpc_shift, k = st * L.cps + j;
+        if (k < ncell) {
+            const unsigned char *qrow = stages + b * L.stage + (size_t)j * 4u * L.row;
+            const uint32_t p0 = (uint32_t)lane & ((1u << L.lpc_shift) - 1u);
+            for (uint32_t m = 0; m < L.ppl; ++m) {
+                const uint32_t pp = p0 + 32u * m;
+                if (pp < L.P) pair_solve(A, tab[k], qrow, L.row, (int)pp, psi_dir, ox, oy, oz);
+            }
+        }
+        __syncwarp();
+    }
+    return true;
 }
 
 __device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
@@ -896,6 +985,15 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 3) sweep_kernel(cons
         if (lane == 0) {
             uint64_t *bars = reinterpret_cast<uint64_t *>(wsm + 3 * StageLayout<T>(A.G).stage);
             for (int b = 0; b < 6; ++b) mbar_init(&bars[b], 1);
+            fence_proxy_async_shared();
+        }
+        __syncwarp();
+    }
+    if constexpr (MODE == 3) {
+        if (lane == 0) {
+            const PairLayout L(A.G, A.max_cells);
+            uint64_t *bars = reinterpret_cast<uint64_t *>(wsm + L.table + 3 * L.stage);
+            for (int b = 0; b < 3; ++b) mbar_init(&bars[b], 1);
             fence_proxy_async_shared();
         }
         __syncwarp();
@@ -960,7 +1058,7 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 3) sweep_kernel(cons
         const V4<T> om = ld_ro(A.omega + dir);
         const size_t psi_dir = (size_t)(dir - (uint32_t)A.dir_begin) * (size_t)A.C;
         if constexpr (MODE == 3) {
-            run_task_paired(A, ti, lane, om.x, om.y, om.z, psi_dir);
+            if (!run_task_pairs(A, ti, lane, om.x, om.y, om.z, psi_dir, wsm, ph)) break;
         } else if constexpr (MODE == 2) {
             if (!run_task_staged(A, ti, lane, om.x, om.y, om.z, psi_dir, wsm, ph)) break;
         } else if constexpr (MODE == 1) {
@@ -1644,16 +1742,8 @@ tf_status device_create(Problem &p, const int32_t *cell_material, const double *
     d.D = p.quad->D;
     d.M = p.M;
     d.fp64 = p.opt.precision == TF_FP64;
-    d.paired = !d.fp64 && d.G % 2 == 0 && p.opt.pairing == 0;
-    if (d.paired) {
-        // lanes per cell: the largest power of two <= (G/2)/4 that divides G/2 (at most 32)
-        const int P = d.G / 2;
-        int lpc = 1;
-        while (lpc * 2 <= 32 && lpc * 2 * 4 <= P && P % (lpc * 2) == 0) lpc *= 2;
-        d.ppl = P / lpc;
-        d.lpc_shift = 0;
-        while ((1 << d.lpc_shift) < lpc) ++d.lpc_shift;
-    }
+    d.paired = !d.fp64 && d.G % 2 == 0 && p.opt.pairing == 0 && g.cells_per_task <= 32 &&
+               PairLayout(d.G, g.cells_per_task).bytes() <= 227u * 1024u;
     d.tsize = d.fp64 ? 8 : 4;
     const int64_t T = g.T();
     if ((uint64_t)g.down_list.size() >= (1ull << 32)) return fail(TF_ERR_ARG, "graph too large: 2^32 downwind edges");
@@ -1799,9 +1889,14 @@ tf_status device_create(Problem &p, const int32_t *cell_material, const double *
     d.mode = d.paired ? 3 : d.staged ? 2 : (d.G % 32 == 0 && g.cells_per_task <= 64 ? 1 : 0);
     if (d.paired) {
         d.staged = false;
-        d.warp_smem = 0;
+        const uint32_t wb = (PairLayout(d.G, g.cells_per_task).bytes() + 127u) / 128u * 128u;
+        while (d.wpc > 1 && wb * d.wpc > 227u * 1024u) d.wpc /= 2;
+        d.warp_smem = wb;
+        const PairLayout L(d.G, g.cells_per_task);
+        d.lpc_shift = (int)L.lpc_shift;
+        d.ppl = (int)L.ppl;
     }
-    const int dyn = d.paired ? 0 : (int)(d.warp_smem * d.wpc);
+    const int dyn = (int)(d.warp_smem * d.wpc);
     const void *kfn = d.fp64 ? (d.mode == 2 ? (const void *)sweep_kernel<double, 2>
                                             : d.mode == 1 ? (const void *)sweep_kernel<double, 1> : (const void *)sweep_kernel<double, 0>)
                              : (d.mode == 3   ? (const void *)sweep_kernel<float, 3>
@@ -1924,7 +2019,7 @@ template <class T> tf_status launch_step(Problem &p, const double *phi_in, doubl
         TF_CUDA(cudaEventRecord(d.ev_start[1 + 2 * k], st));
         const size_t dyn = (size_t)d.warp_smem * d.wpc;
         if constexpr (sizeof(T) == 4) {
-            if (d.mode == 3) sweep_kernel<T, 3><<<d.grid, 32 * d.wpc, 0, st>>>(A);
+            if (d.mode == 3) sweep_kernel<T, 3><<<d.grid, 32 * d.wpc, dyn, st>>>(A);
         }
         if (d.mode == 3) {
         } else if (d.mode == 2)
