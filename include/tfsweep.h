@@ -81,8 +81,9 @@ typedef struct {
     int32_t octant_window;   /* directions are admitted one octant at a time; this many octants are
                               * active at once (the next one enters when the oldest is half done);
                               * 0 = automatic (2), 8 = every direction from the start */
-    int32_t pairing;         /* FP32 with an even group count: 0 = solve two groups per lane with packed
-                              * FP32x2 arithmetic (default), 1 = one group per lane */
+    int32_t pairing;         /* FP32, even group count: solve two groups per lane with packed FP32x2
+                              * arithmetic.  0 = automatic (when n_groups is not a multiple of 32),
+                              * 1 = never, 2 = whenever n_groups is even */
     int32_t reserved_i[4];
     double residual_floor;   /* stopping-test denominator floor, as a fraction of the group's max |phi|:
                               * 1 (the default; 0 also means 1) = per-group max-norm relative change,

@@ -178,7 +178,8 @@ tf_status tf_problem_create(tf_handle mesh, tf_handle quad, int32_t n_groups, in
     int32_t B = p->opt.cells_per_task;
     if (B <= 0) {
         // about 1024 units per task; at most 32 cells when the FP32 paired path will run
-        const bool paired = p->opt.precision == TF_FP32 && n_groups % 2 == 0 && p->opt.pairing == 0;
+        const bool paired = p->opt.precision == TF_FP32 && n_groups % 2 == 0 &&
+                            (p->opt.pairing == 2 || (p->opt.pairing == 0 && n_groups % 32 != 0));
         B = std::max(2, std::min(paired ? 32 : 64, 1024 / n_groups));
     }
     tf_status s = build_task_graph(*m, *q, B, p->graph);

@@ -1742,7 +1742,10 @@ tf_status device_create(Problem &p, const int32_t *cell_material, const double *
     d.D = p.quad->D;
     d.M = p.M;
     d.fp64 = p.opt.precision == TF_FP64;
-    d.paired = !d.fp64 && d.G % 2 == 0 && p.opt.pairing == 0 && g.cells_per_task <= 32 &&
+    // pairing 0 = automatic: packed pairs unless G is a multiple of 32 (there the
+    // shared-memory staged path is faster); 2 = packed pairs whenever G is even
+    d.paired = !d.fp64 && d.G % 2 == 0 && (p.opt.pairing == 2 || (p.opt.pairing == 0 && d.G % 32 != 0)) &&
+               g.cells_per_task <= 32 &&
                PairLayout(d.G, g.cells_per_task).bytes() <= 227u * 1024u;
     d.tsize = d.fp64 ? 8 : 4;
     const int64_t T = g.T();

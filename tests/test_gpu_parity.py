@@ -52,7 +52,8 @@ def test_one_sweep_matches_oracle(precision, G, cells_per_task, dir_chunk):
 # the any-G path; G and cells_per_task chosen to leave ragged tails.
 @pytest.mark.parametrize("G,opts", [
     (2, {}), (6, {}), (12, dict(cells_per_task=5)), (24, {}), (40, {}), (64, {}), (64, dict(cells_per_task=7)),
-    (128, {}), (32, dict(pairing=1)), (64, dict(pairing=1)), (64, dict(pairing=1, staging=1)),
+    (128, {}), (64, dict(pairing=2)), (32, dict(pairing=2, cells_per_task=3)), (128, dict(pairing=2)),
+    (32, dict(pairing=1)), (64, dict(pairing=1)), (64, dict(pairing=1, staging=1)),
     (32, dict(pairing=1, staging=1, cells_per_task=9)), (8, dict(pairing=1)), (64, dict(octant_window=8)),
     (64, dict(octant_window=1, dir_chunk=7)),
 ])
