@@ -221,6 +221,27 @@ tf_status tf_problem_psi(tf_handle problem, int32_t dir, void *out, void *stream
 /* Scheduling statistics of the problem's last sweep. */
 tf_status tf_problem_stats(tf_handle problem, tf_stats *out);
 
+/* Per-group statistics of a scalar-flux array, computed without allocating any
+ * device memory.  The paper has no counterpart: this exists for callers that
+ * cannot allocate device memory, such as a host program whose device memory
+ * is owned entirely by another runtime's pool, or a latency-critical loop that
+ * must not pay cudaMalloc's implicit device synchronisation.
+ *   phi    device [n_cells][n_groups][4] FP64 nodal scalar flux;
+ *   volume device [n_cells] FP64 cell volumes;
+ *   out    device [n_groups][3] FP64: max |phi|, the integral over space
+ *          sum_c (V_c/4) sum_i phi (Eq. (3) with volume weights), and the
+ *          plain nodal sum sum_c sum_i phi.
+ * Runs on the current device, asynchronously on `stream`.  Its reduction
+ * scratch is one fixed 8 MiB array per device (held by every GPU that loads
+ * the library until the process exits), shared by all calls: calls that
+ * overlap on the GPU race on it.  Each call overwrites the part it uses, so
+ * nothing carries over between calls.  The first call on a device looks the
+ * array up (cudaGetSymbolAddress); make that first call before any stream
+ * capture.  n_groups must be at most 1024 (TF_ERR_ARG otherwise).
+ * Errors: TF_ERR_ARG, TF_ERR_CUDA. */
+tf_status tf_integrated_flux_noalloc(const double *phi, const double *volume, int64_t n_cells, int32_t n_groups,
+                                     double *out, void *stream);
+
 /* Static description of a status code. */
 const char *tf_status_string(tf_status s);
 

@@ -26,7 +26,7 @@ TF_PHI_PAIR, TF_PHI_DADD = 0, 1
 SYMBOLS = (
     "tf_options_default", "tf_mesh_create", "tf_quadrature_create", "tf_problem_create", "tf_sweep",
     "tf_source_iterate", "tf_destroy", "tf_mesh_geometry", "tf_quadrature_get", "tf_graph_levels",
-    "tf_problem_psi", "tf_problem_stats", "tf_status_string", "tf_last_error",
+    "tf_problem_psi", "tf_problem_stats", "tf_status_string", "tf_last_error", "tf_integrated_flux_noalloc",
 )
 
 
@@ -101,6 +101,7 @@ def load(build_if_missing: bool = True):
     lib.tf_graph_levels.argtypes = [H, H, vp, vp]
     lib.tf_problem_psi.argtypes = [H, i32, vp, vp]
     lib.tf_problem_stats.argtypes = [H, C.POINTER(tf_stats)]
+    lib.tf_integrated_flux_noalloc.argtypes = [vp, vp, i64, i32, vp, vp]
     lib.tf_status_string.argtypes = [i32]
     lib.tf_status_string.restype = C.c_char_p
     lib.tf_last_error.argtypes = []
@@ -242,6 +243,13 @@ def tf_graph_levels(mesh, quad, n_cells, n_dirs):
 
 def tf_problem_psi(problem, direction, out, stream=None):
     return _check(load().tf_problem_psi(problem, int(direction), _ptr(out), _stream_handle(stream)), "tf_problem_psi")
+
+
+def tf_integrated_flux_noalloc(phi, volume, n_cells, n_groups, out, stream=None):
+    """Per-group (max |phi|, integral, nodal sum) into `out` [n_groups, 3] (device),
+    with no device allocation (see include/tfsweep.h)."""
+    return _check(load().tf_integrated_flux_noalloc(_ptr(phi), _ptr(volume), int(n_cells), int(n_groups), _ptr(out),
+                                                     _stream_handle(stream)), "tf_integrated_flux_noalloc")
 
 
 def tf_problem_stats(problem):
