@@ -200,7 +200,7 @@ def run_ours(args):
     t_setup = time.perf_counter()
     prob = tf.Problem.from_config(cfg, precision=prec, device=local, cells_per_task=args.cells_per_task,
                                   warps_per_cta=args.warps_per_cta, octant_window=args.octant_window,
-                                  staging=args.staging)
+                                  staging=args.staging, pairing=args.pairing)
     t_setup = time.perf_counter() - t_setup
     C, G, D = prob.n_cells, prob.n_groups, prob.n_dirs
     units = prob.n_units
@@ -316,6 +316,7 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--octant-window", type=int, default=0, help="octants active at once (0 = library default)")
     ap.add_argument("--staging", type=int, default=0, help="1 = no shared-memory staging")
+    ap.add_argument("--pairing", type=int, default=0, help="0 auto, 1 off, 2 packed group pairs when G is even")
     ap.add_argument("--n", type=int, default=0, help="hexes per box edge (default: the workload's)")
     ap.add_argument("--groups", type=int, default=0)
     ap.add_argument("--polar", type=int, default=0)
