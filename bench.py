@@ -276,7 +276,7 @@ def run_ours(args):
         line["e2e"] = {"value": e2e_ms * 1e6 / units / world, "unit": UNIT, "h2d_bytes_per_step": nbytes,
                        "d2h_bytes_per_step": nbytes, "ms_per_step": e2e_ms,
                        "call": "tf_sweep(host pinned phi_in, host pinned phi_out)"}
-    if args.fp64_compare and prec == tf.TF_FP32:
+    if not args.no_fp64_compare and prec == tf.TF_FP32:
         del prob
         torch.cuda.synchronize(dev)
         p64 = tf.Problem.from_config(cfg, precision=tf.TF_FP64, device=local)
@@ -291,6 +291,26 @@ def run_ours(args):
         line["fp64_plain_gpu"] = {"ms_per_step": ms64, "grind": ms64 * 1e6 / units, "unit": UNIT,
                                   "fp32_speedup": ms64 / ms_per_step, "n_chunks": p64.stats()["n_chunks"]}
         del p64
+    if not args.no_time_to_tol:
+        # time to the stopping test 1e-6 on the two-material box (196,608 tets, 128 directions,
+        # 32 groups): FP32 sweep with FP64 phi/residual against the plain FP64 GPU sweep
+        tcfg = W.two_material_box()
+        out = {"workload": tcfg["name"], "tol": tcfg["tol"]}
+        for name, pr in (("fp32", tf.TF_FP32), ("fp64", tf.TF_FP64)):
+            pt = tf.Problem.from_config(tcfg, precision=pr, device=local)
+            ph = torch.zeros((pt.n_cells, pt.n_groups, 4), dtype=torch.float64, device=dev)
+            pt.source_iterate(ph, 0.0, 1, stream=stream)  # warm-up sweep
+            ph.zero_()
+            torch.cuda.synchronize(dev)
+            e0.record(stream)
+            r = pt.source_iterate(ph, tcfg["tol"], 2000, stream=stream)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            out[name] = {"seconds": e0.elapsed_time(e1) / 1e3, "iterations": r["iterations"],
+                         "converged": r["converged"], "residual": r["residual"]}
+            del pt, ph
+        out["fp64_over_fp32"] = out["fp64"]["seconds"] / out["fp32"]["seconds"]
+        line["time_to_tol"] = out
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_oracle_sample(cfg)
     if rank == 0:
@@ -312,7 +332,8 @@ def main():
     ap.add_argument("--warps-per-cta", type=int, default=0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--fp64-compare", action="store_true")
+    ap.add_argument("--no-fp64-compare", action="store_true", help="skip the plain FP64 GPU sweep comparison")
+    ap.add_argument("--no-time-to-tol", action="store_true", help="skip the time-to-1e-6 comparison")
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--octant-window", type=int, default=0, help="octants active at once (0 = library default)")
     ap.add_argument("--staging", type=int, default=0, help="1 = no shared-memory staging")
