@@ -37,6 +37,27 @@ UNIT = "ns/(cell·dir·group)"
 L2_BYTES = 129 * 1024 * 1024
 
 
+def _traffic(workload, precision, kernel_label):
+    """DRAM bytes per sweep-kernel launch from the committed ncu record, if it was taken on
+    this workload with the current kernel source; else None."""
+    import glob
+    import hashlib
+    src = os.path.join(ROOT, "paper_2510_11513_gb300", "csrc", "sweep_kernel.cuh")
+    try:
+        sha = hashlib.sha1(open(src, "rb").read()).hexdigest()
+    except OSError:
+        return None
+    for f in glob.glob(os.path.join(ROOT, "profiles", "traffic_*.json")):
+        try:
+            rec = json.load(open(f))
+        except (OSError, ValueError):
+            continue
+        if (rec.get("workload") == workload and rec.get("precision") == precision
+                and rec.get("kernel_source_sha1") == sha and rec.get("kernel") == kernel_label):
+            return rec["dram_bytes_read"] + rec["dram_bytes_write"]
+    return None
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -232,6 +253,7 @@ def run_ours(args):
     phi_s = (st1["cum_phi_event_seconds"] - st0["cum_phi_event_seconds"]) / args.steps
     src_s = (st1["cum_source_event_seconds"] - st0["cum_source_event_seconds"]) / args.steps
     s = 4 if prec == tf.TF_FP32 else 8
+    mode = st1["kernel_mode"]
     # algorithmic bytes of the sweep kernel per unit: q (4 s), psi store (4 s), and the
     # cell record + cell-list entry once per (cell, direction), amortised over G
     geo = 128 if prec == tf.TF_FP32 else 256
@@ -246,8 +268,11 @@ def run_ours(args):
                        "l2": "inputs larger than L2 (psi store %.1f GB)" % (units * 4 * s / 1e9),
                        "parallelism": f"replicas{world}", "setup_s": round(t_setup, 2)},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None, "kernel": "sweep_kernel",
-                         "bytes_per_unit": b_unit, "peak_kind": peak_kind},
+                         "frac": achieved / peak,
+                         "traffic": _traffic(cfg["name"], args.precision, f"sweep_kernel<{'float' if s == 4 else 'double'}, {mode}>"),
+                         "kernel": f"sweep_kernel<{'float' if s == 4 else 'double'}, {mode}>",
+                         "bytes_per_unit": b_unit, "peak_kind": peak_kind,
+                         "algorithmic_bytes_per_launch": b_unit * units},
             "breakdown_ms": {"source": src_s * 1e3, "sweep": sweep_s * 1e3, "phi": phi_s * 1e3,
                              "other": ms_per_step - (src_s + sweep_s + phi_s) * 1e3},
             "scheduling": {"n_tasks": st1["n_tasks"], "cells_per_task": st1["cells_per_task"],
@@ -255,7 +280,7 @@ def run_ours(args):
                            "warps_per_cta": st1["warps_per_cta"], "mean_ready": st1["mean_ready"],
                            "wait_frac": st1["wait_seconds"] / max(st1["wait_seconds"] + st1["busy_seconds"], 1e-30),
                            "n_chunks": st1["n_chunks"], "octant_window": args.octant_window or 2},
-            "gpu_launches": int((st1["launches_per_step"] + 3) * args.steps),
+            "gpu_launches": int((st1["launches_per_step"] + 2) * args.steps),
             "clocks": clk}
     # end to end: tf_sweep with pinned host buffers (H2D of phi_in, D2H of phi_out inside)
     if not args.no_e2e:

@@ -127,7 +127,9 @@ typedef struct {
     double cum_source_event_seconds, cum_sweep_event_seconds, cum_phi_event_seconds;
     int64_t cum_steps;
     int64_t launches_per_step;  /* kernels this library launches per transport step */
-    int32_t reserved_i[6];
+    int32_t kernel_mode;        /* sweep kernel variant: 0 any G, 1 G%32==0 (registers), 2 G%32==0 staged
+                                 * in shared memory, 3 packed group pairs (FP32, even G) */
+    int32_t reserved_i[5];
     double reserved_d[6];
 } tf_stats;
 

@@ -59,7 +59,8 @@ class tf_stats(C.Structure):
         ("mean_ready", C.c_double), ("source_event_seconds", C.c_double), ("sweep_event_seconds", C.c_double),
         ("phi_event_seconds", C.c_double), ("cum_source_event_seconds", C.c_double),
         ("cum_sweep_event_seconds", C.c_double), ("cum_phi_event_seconds", C.c_double), ("cum_steps", C.c_int64),
-        ("launches_per_step", C.c_int64), ("reserved_i", C.c_int32 * 6), ("reserved_d", C.c_double * 6),
+        ("launches_per_step", C.c_int64), ("kernel_mode", C.c_int32), ("reserved_i", C.c_int32 * 5),
+        ("reserved_d", C.c_double * 6),
     ]
 
 
