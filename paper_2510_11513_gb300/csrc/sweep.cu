@@ -949,12 +949,12 @@ template <class T> tf_status launch_step(Problem &p, const double *phi_in, doubl
         const int cpc = std::max(1, 256 / d.G);
         const size_t smem = (size_t)cpc * d.G * 4 * sizeof(T);
         const int blocks = (int)std::min<int64_t>((d.C + cpc - 1) / cpc, (int64_t)d.sm_count * 16);
-        TF_CUDA(cudaEventRecord(d.ev_start[0], st));
+        TF_CUDA(cudaEventRecordWithFlags(d.ev_start[0], st, cudaEventRecordExternal));
         source_kernel<T><<<blocks, 256, smem, st>>>(phi_in, (const V4<T> *)d.Q, (const T *)d.sigma_s,
                                                     (const CellGeo<T> *)d.geo, (V4<T> *)d.q, d.C, d.G, cpc,
                                                     d.paired ? 1 : 0);
         TF_CUDA(cudaGetLastError());
-        TF_CUDA(cudaEventRecord(d.ev_stop[0], st));
+        TF_CUDA(cudaEventRecordWithFlags(d.ev_stop[0], st, cudaEventRecordExternal));
     }
     for (int k = 0; k < d.n_chunks; ++k) {
         const int64_t t0 = d.chunk_task_begin[k], t1 = d.chunk_task_begin[k + 1];
@@ -1002,7 +1002,7 @@ template <class T> tf_status launch_step(Problem &p, const double *phi_in, doubl
         A.window = win;
         A.lpc_shift = d.lpc_shift;
         A.ppl = d.ppl;
-        TF_CUDA(cudaEventRecord(d.ev_start[1 + 2 * k], st));
+        TF_CUDA(cudaEventRecordWithFlags(d.ev_start[1 + 2 * k], st, cudaEventRecordExternal));
         const size_t dyn = (size_t)d.warp_smem * d.wpc;
         if constexpr (sizeof(T) == 4) {
             if (d.mode == 3) sweep_kernel<T, 3><<<d.grid, 32 * d.wpc, dyn, st>>>(A);
@@ -1015,10 +1015,10 @@ template <class T> tf_status launch_step(Problem &p, const double *phi_in, doubl
         else
             sweep_kernel<T, 0><<<d.grid, 32 * d.wpc, 0, st>>>(A);
         TF_CUDA(cudaGetLastError());
-        TF_CUDA(cudaEventRecord(d.ev_stop[1 + 2 * k], st));
+        TF_CUDA(cudaEventRecordWithFlags(d.ev_stop[1 + 2 * k], st, cudaEventRecordExternal));
         end_kernel<<<1, 1, 0, st>>>(d.ctrl);
         const int pb = (int)std::min<size_t>((CG + 255) / 256, (size_t)d.sm_count * 32);
-        TF_CUDA(cudaEventRecord(d.ev_start[2 + 2 * k], st));
+        TF_CUDA(cudaEventRecordWithFlags(d.ev_start[2 + 2 * k], st, cudaEventRecordExternal));
         if (d.paired) {
             const size_t CP = CG / 2;
             const int pb2 = (int)std::min<size_t>((CP + 255) / 256, (size_t)d.sm_count * 32);
@@ -1035,7 +1035,7 @@ template <class T> tf_status launch_step(Problem &p, const double *phi_in, doubl
             phi_kernel<T, false><<<pb, 256, 0, st>>>((const V4<T> *)d.psi, d.wts + a0, a1 - a0, CG, d.G,
                                                      (const CellGeo<T> *)d.geo, phi_out, k > 0);
         TF_CUDA(cudaGetLastError());
-        TF_CUDA(cudaEventRecord(d.ev_stop[2 + 2 * k], st));
+        TF_CUDA(cudaEventRecordWithFlags(d.ev_stop[2 + 2 * k], st, cudaEventRecordExternal));
         d.last_chunk = k;
     }
     return TF_OK;
@@ -1061,23 +1061,29 @@ tf_status collect(Problem &p, cudaStream_t st, bool copied = false)
     s.kernel_seconds = c.kernel_ns * 1e-9;
     s.mean_ready = c.pops ? (double)c.depth_sum / (double)c.pops : 0.0;
     {
+        // CUDA-event times of the step's kernels (events recorded as external
+        // nodes when the step runs inside a captured graph)
         float ms = 0.f;
         double src = 0.0, sw = 0.0, ph = 0.0;
-        TF_CUDA(cudaEventElapsedTime(&ms, d.ev_start[0], d.ev_stop[0]));
+        bool ok = cudaEventElapsedTime(&ms, d.ev_start[0], d.ev_stop[0]) == cudaSuccess;
         src = ms * 1e-3;
-        for (int k = 0; k < d.n_chunks; ++k) {
-            TF_CUDA(cudaEventElapsedTime(&ms, d.ev_start[1 + 2 * k], d.ev_stop[1 + 2 * k]));
+        for (int k = 0; ok && k < d.n_chunks; ++k) {
+            ok = cudaEventElapsedTime(&ms, d.ev_start[1 + 2 * k], d.ev_stop[1 + 2 * k]) == cudaSuccess;
             sw += ms * 1e-3;
-            TF_CUDA(cudaEventElapsedTime(&ms, d.ev_start[2 + 2 * k], d.ev_stop[2 + 2 * k]));
+            ok = ok && cudaEventElapsedTime(&ms, d.ev_start[2 + 2 * k], d.ev_stop[2 + 2 * k]) == cudaSuccess;
             ph += ms * 1e-3;
         }
-        s.source_event_seconds = src;
-        s.sweep_event_seconds = sw;
-        s.phi_event_seconds = ph;
-        s.cum_source_event_seconds += src;
-        s.cum_sweep_event_seconds += sw;
-        s.cum_phi_event_seconds += ph;
-        s.cum_steps += 1;
+        if (ok) {
+            s.source_event_seconds = src;
+            s.sweep_event_seconds = sw;
+            s.phi_event_seconds = ph;
+            s.cum_source_event_seconds += src;
+            s.cum_sweep_event_seconds += sw;
+            s.cum_phi_event_seconds += ph;
+            s.cum_steps += 1;
+        } else {
+            cudaGetLastError();
+        }
     }
     if (c.error) {
         const int err = c.error;
