@@ -546,6 +546,17 @@ struct DeviceState {
 
 namespace {
 
+// Records a timing event; inside a stream capture it becomes an external event
+// node of the graph, so replays record it too.
+cudaError_t record_event(cudaEvent_t ev, cudaStream_t st)
+{
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    const cudaError_t e = cudaStreamIsCapturing(st, &cs);
+    if (e != cudaSuccess) return e;
+    return cs == cudaStreamCaptureStatusActive ? cudaEventRecordWithFlags(ev, st, cudaEventRecordExternal)
+                                               : cudaEventRecord(ev, st);
+}
+
 tf_status cuda_fail(cudaError_t e, const char *what)
 {
     return fail(e == cudaErrorMemoryAllocation ? TF_ERR_NOMEM : TF_ERR_CUDA,
@@ -949,12 +960,12 @@ template <class T> tf_status launch_step(Problem &p, const double *phi_in, doubl
         const int cpc = std::max(1, 256 / d.G);
         const size_t smem = (size_t)cpc * d.G * 4 * sizeof(T);
         const int blocks = (int)std::min<int64_t>((d.C + cpc - 1) / cpc, (int64_t)d.sm_count * 16);
-        TF_CUDA(cudaEventRecordWithFlags(d.ev_start[0], st, cudaEventRecordExternal));
+        TF_CUDA(record_event(d.ev_start[0], st));
         source_kernel<T><<<blocks, 256, smem, st>>>(phi_in, (const V4<T> *)d.Q, (const T *)d.sigma_s,
                                                     (const CellGeo<T> *)d.geo, (V4<T> *)d.q, d.C, d.G, cpc,
                                                     d.paired ? 1 : 0);
         TF_CUDA(cudaGetLastError());
-        TF_CUDA(cudaEventRecordWithFlags(d.ev_stop[0], st, cudaEventRecordExternal));
+        TF_CUDA(record_event(d.ev_stop[0], st));
     }
     for (int k = 0; k < d.n_chunks; ++k) {
         const int64_t t0 = d.chunk_task_begin[k], t1 = d.chunk_task_begin[k + 1];
@@ -1002,7 +1013,7 @@ template <class T> tf_status launch_step(Problem &p, const double *phi_in, doubl
         A.window = win;
         A.lpc_shift = d.lpc_shift;
         A.ppl = d.ppl;
-        TF_CUDA(cudaEventRecordWithFlags(d.ev_start[1 + 2 * k], st, cudaEventRecordExternal));
+        TF_CUDA(record_event(d.ev_start[1 + 2 * k], st));
         const size_t dyn = (size_t)d.warp_smem * d.wpc;
         if constexpr (sizeof(T) == 4) {
             if (d.mode == 3) sweep_kernel<T, 3><<<d.grid, 32 * d.wpc, dyn, st>>>(A);
@@ -1015,10 +1026,10 @@ template <class T> tf_status launch_step(Problem &p, const double *phi_in, doubl
         else
             sweep_kernel<T, 0><<<d.grid, 32 * d.wpc, 0, st>>>(A);
         TF_CUDA(cudaGetLastError());
-        TF_CUDA(cudaEventRecordWithFlags(d.ev_stop[1 + 2 * k], st, cudaEventRecordExternal));
+        TF_CUDA(record_event(d.ev_stop[1 + 2 * k], st));
         end_kernel<<<1, 1, 0, st>>>(d.ctrl);
         const int pb = (int)std::min<size_t>((CG + 255) / 256, (size_t)d.sm_count * 32);
-        TF_CUDA(cudaEventRecordWithFlags(d.ev_start[2 + 2 * k], st, cudaEventRecordExternal));
+        TF_CUDA(record_event(d.ev_start[2 + 2 * k], st));
         if (d.paired) {
             const size_t CP = CG / 2;
             const int pb2 = (int)std::min<size_t>((CP + 255) / 256, (size_t)d.sm_count * 32);
@@ -1035,7 +1046,7 @@ template <class T> tf_status launch_step(Problem &p, const double *phi_in, doubl
             phi_kernel<T, false><<<pb, 256, 0, st>>>((const V4<T> *)d.psi, d.wts + a0, a1 - a0, CG, d.G,
                                                      (const CellGeo<T> *)d.geo, phi_out, k > 0);
         TF_CUDA(cudaGetLastError());
-        TF_CUDA(cudaEventRecordWithFlags(d.ev_stop[2 + 2 * k], st, cudaEventRecordExternal));
+        TF_CUDA(record_event(d.ev_stop[2 + 2 * k], st));
         d.last_chunk = k;
     }
     return TF_OK;
