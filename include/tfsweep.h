@@ -80,7 +80,7 @@ typedef struct {
                               * 1 = never (registers only) */
     int32_t octant_window;   /* directions are admitted one octant at a time; this many octants are
                               * active at once (the next one enters when the oldest is half done);
-                              * 0 = automatic (2), 8 = every direction from the start */
+                              * 0 = automatic (8: every direction from the start) */
     int32_t pairing;         /* FP32, even group count: solve two groups per lane with packed FP32x2
                               * arithmetic.  0 = automatic (when n_groups is not a multiple of 32),
                               * 1 = never, 2 = whenever n_groups is even */

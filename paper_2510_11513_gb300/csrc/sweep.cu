@@ -856,7 +856,7 @@ tf_status device_create(Problem &p, const int32_t *cell_material, const double *
         d.chunk_seed_begin[k + 1] = (int64_t)seeds.size();
     }
     d.chunk_group_begin[d.n_chunks] = (int32_t)group_total.size();
-    d.window = p.opt.octant_window > 0 ? p.opt.octant_window : 2;
+    d.window = p.opt.octant_window > 0 ? p.opt.octant_window : 8;
     if ((s = upload(d, &d.dir_group, dir_group.data(), dir_group.size() * 4)) != TF_OK) return s;
     if ((s = upload(d, &d.group_total, group_total.data(), group_total.size() * 4)) != TF_OK) return s;
     if ((s = upload(d, &d.group_admit, group_admit.data(), group_admit.size() * 4)) != TF_OK) return s;

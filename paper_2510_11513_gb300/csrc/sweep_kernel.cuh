@@ -993,10 +993,10 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 3) sweep_kernel(cons
             const unsigned long long t0 = globaltimer();
             unsigned long long v = ld_acquire(A.slots + ticket);
             if ((unsigned)(v >> 32) != epoch) {
-                unsigned ns = 64;
+                unsigned ns = 32;
                 for (;;) {
                     __nanosleep(ns);
-                    if (ns < 2048) ns <<= 1;
+                    if (ns < 256) ns <<= 1;
                     ++ws[0];
                     v = ld_acquire(A.slots + ticket);
                     if ((unsigned)(v >> 32) == epoch) break;
