@@ -103,6 +103,8 @@ typedef struct {
     double integrated_total;   /* Eq. (3): sum over groups of the integrated flux of the final phi */
     double *integrated_flux;   /* caller host array [n_groups] or NULL: per-group integral of phi over space */
     double *residual_history;  /* caller host array [max_iters] or NULL: residual after each sweep */
+    double seconds;            /* batched calls: wall time from the call's start to this problem's
+                                * convergence (or to the end) */
 } tf_iter_info;
 
 /* Scheduling statistics of the last sweep of a problem (for measurement). */

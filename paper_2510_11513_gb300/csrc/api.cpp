@@ -200,11 +200,8 @@ tf_status tf_sweep(const tf_handle *problems, int32_t n, const double *const *ph
         Problem *p = as<Problem>(problems[k], Kind::Problem);
         if (!p || !phi_in[k] || !phi_out[k]) return fail(TF_ERR_ARG, "tf_sweep: bad problem handle or phi pointer");
     }
-    for (int32_t k = 0; k < n; ++k) {
-        tf_status s = device_sweep(*as<Problem>(problems[k], Kind::Problem), phi_in[k], phi_out[k], stream);
-        if (s != TF_OK) return s;
-    }
-    return TF_OK;
+    if (n > 1) return device_batch_iterate(problems, n, 0.0, 1, phi_out, nullptr, true, phi_in, stream);
+    return device_sweep(*as<Problem>(problems[0], Kind::Problem), phi_in[0], phi_out[0], stream);
 }
 
 tf_status tf_source_iterate(const tf_handle *problems, int32_t n, double tol, int32_t max_iters,
@@ -216,6 +213,7 @@ tf_status tf_source_iterate(const tf_handle *problems, int32_t n, double tol, in
         if (!as<Problem>(problems[k], Kind::Problem) || !phi[k])
             return fail(TF_ERR_ARG, "tf_source_iterate: bad problem handle or NULL phi buffer");
     }
+    if (n > 1) return device_batch_iterate(problems, n, tol, max_iters, phi, info, false, nullptr, stream);
     tf_status worst = TF_OK;
     for (int32_t k = 0; k < n; ++k) {
         tf_status s = device_iterate(*as<Problem>(problems[k], Kind::Problem), tol, max_iters, phi[k],

@@ -14,6 +14,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -521,6 +522,7 @@ struct DeviceState {
     std::vector<int64_t> chunk_seed_begin;  // [n_chunks + 1]
     std::vector<int32_t> chunk_group_begin;  // [n_chunks + 1] into the group arrays
     std::vector<uint32_t> gseed_host;        // [n_groups_total + n_chunks] seed offsets
+    std::vector<uint32_t> seeds_host;        // seed task ids, grouped as gseed_host says
     int32_t *dir_group = nullptr;
     int32_t *group_rem = nullptr, *group_total = nullptr, *group_admit = nullptr;
     uint32_t *gseed = nullptr;
@@ -863,6 +865,7 @@ tf_status device_create(Problem &p, const int32_t *cell_material, const double *
     if ((s = dmalloc(d, &d.group_rem, group_total.size() * 4)) != TF_OK) return s;
     if ((s = upload(d, &d.gseed, d.gseed_host.data(), d.gseed_host.size() * 4)) != TF_OK) return s;
     if ((s = upload(d, &d.seeds, seeds.data(), seeds.size() * 4)) != TF_OK) return s;
+    d.seeds_host = seeds;
     if ((s = dmalloc(d, &d.slots, (size_t)d.max_chunk_tasks * 8)) != TF_OK) return s;
     TF_CUDA(cudaMemset(d.slots, 0, (size_t)d.max_chunk_tasks * 8));
     if ((s = dmalloc(d, &d.psi, per_dir * Dc)) != TF_OK) return s;
@@ -870,14 +873,14 @@ tf_status device_create(Problem &p, const int32_t *cell_material, const double *
     d.wpc = p.opt.warps_per_cta > 0 ? std::min(p.opt.warps_per_cta, 4) : 4;  // launch bounds: 128 threads
     {
         const size_t wb = d.fp64 ? staged_warp_bytes<double>(d.G) : staged_warp_bytes<float>(d.G);
-        const size_t wb128 = (wb + 127) / 128 * 128;
+        const size_t wb128 = (wb + 48 + 127) / 128 * 128;  // + the six mbarriers at the end
         d.staged = p.opt.staging == 0 && d.G % 32 == 0 && g.cells_per_task <= 64 && wb128 * d.wpc <= 227 * 1024;
         d.warp_smem = d.staged ? (uint32_t)wb128 : 0u;
     }
     d.mode = d.paired ? 3 : d.staged ? 2 : (d.G % 32 == 0 && g.cells_per_task <= 64 ? 1 : 0);
     if (d.paired) {
         d.staged = false;
-        const uint32_t wb = (PairLayout(d.G, g.cells_per_task).bytes() + 127u) / 128u * 128u;
+        const uint32_t wb = (PairLayout(d.G, g.cells_per_task).bytes() + 48u + 127u) / 128u * 128u;
         while (d.wpc > 1 && wb * d.wpc > 227u * 1024u) d.wpc /= 2;
         d.warp_smem = wb;
         const PairLayout L(d.G, g.cells_per_task);
@@ -951,25 +954,97 @@ bool is_device_pointer(const void *ptr)
     return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
-template <class T> tf_status launch_step(Problem &p, const double *phi_in, double *phi_out, cudaStream_t st)
+// q <- source(phi_in), for one problem.
+template <class T> void launch_source(Problem &p, const double *phi_in, cudaStream_t st)
+{
+    DeviceState &d = *p.dev;
+    const int cpc = std::max(1, 256 / d.G);
+    const size_t smem = (size_t)cpc * d.G * 4 * sizeof(T);
+    const int blocks = (int)std::min<int64_t>((d.C + cpc - 1) / cpc, (int64_t)d.sm_count * 16);
+    source_kernel<T><<<blocks, 256, smem, st>>>(phi_in, (const V4<T> *)d.Q, (const T *)d.sigma_s,
+                                                (const CellGeo<T> *)d.geo, (V4<T> *)d.q, d.C, d.G, cpc,
+                                                d.paired ? 1 : 0);
+}
+
+// Sweep arguments of direction chunk k of one problem (queue fields for a launch of its own).
+template <class T> SweepArgs<T> make_args(Problem &p, int k)
+{
+    DeviceState &d = *p.dev;
+    const int64_t t0 = d.chunk_task_begin[k], t1 = d.chunk_task_begin[k + 1];
+    const int a0 = k * d.Dc;
+    const int gb = d.chunk_group_begin[k], ng = d.chunk_group_begin[k + 1] - gb;
+    SweepArgs<T> A;
+    std::memset(&A, 0, sizeof(A));
+    A.geo = (const CellGeo<T> *)d.geo;
+    A.cells = d.cells;
+    A.task = d.task;
+    A.down = d.down;
+    A.counters = d.counters;
+    A.slots = d.slots;
+    A.ctrl = d.ctrl;
+    A.q = (const V4<T> *)d.q;
+    A.psi = (V4<T> *)d.psi;
+    A.sigma_t = (const T *)d.sigma_t;
+    A.omega = (const V4<T> *)d.omega;
+    A.S1 = (const V4<T> *)d.S1;
+    A.psi_in = (const T *)d.psi_in;
+    A.tets = d.tets;
+    A.C = d.C;
+    A.G = d.G;
+    A.dir_begin = a0;
+    A.task_begin = (uint32_t)t0;
+    A.task_end = (uint32_t)t1;
+    A.n_tasks = (unsigned long long)(t1 - t0);
+    A.wait_limit_ns = (unsigned long long)(p.opt.wait_limit_s * 1e9);
+    A.max_cells = p.graph.cells_per_task;
+    A.warp_smem = d.warp_smem;
+    A.dir_group = d.dir_group;
+    A.group_rem = d.group_rem + gb;
+    A.group_admit = d.group_admit + gb;
+    A.gseed = d.gseed + gb + k;
+    A.seeds = d.seeds;
+    A.n_groups = ng;
+    A.window = std::min(d.window, ng);
+    A.lpc_shift = d.lpc_shift;
+    A.ppl = d.ppl;
+    A.mode = d.mode;
+    return A;
+}
+
+// phi_out (+)= sum over chunk k's directions of w_a psi_a, for one problem.
+template <class T> void launch_phi(Problem &p, int k, double *phi_out, cudaStream_t st)
 {
     DeviceState &d = *p.dev;
     const size_t CG = (size_t)d.C * d.G;
-    // source update
-    {
-        const int cpc = std::max(1, 256 / d.G);
-        const size_t smem = (size_t)cpc * d.G * 4 * sizeof(T);
-        const int blocks = (int)std::min<int64_t>((d.C + cpc - 1) / cpc, (int64_t)d.sm_count * 16);
-        TF_CUDA(record_event(d.ev_start[0], st));
-        source_kernel<T><<<blocks, 256, smem, st>>>(phi_in, (const V4<T> *)d.Q, (const T *)d.sigma_s,
-                                                    (const CellGeo<T> *)d.geo, (V4<T> *)d.q, d.C, d.G, cpc,
-                                                    d.paired ? 1 : 0);
-        TF_CUDA(cudaGetLastError());
-        TF_CUDA(record_event(d.ev_stop[0], st));
+    const int a0 = k * d.Dc, a1 = std::min(d.D, a0 + d.Dc);
+    const int pb = (int)std::min<size_t>((CG + 255) / 256, (size_t)d.sm_count * 32);
+    if (d.paired) {
+        const size_t CP = CG / 2;
+        const int pb2 = (int)std::min<size_t>((CP + 255) / 256, (size_t)d.sm_count * 32);
+        if (p.opt.phi_accumulate == TF_PHI_PAIR)
+            phi_pair_kernel<true><<<pb2, 256, 0, st>>>((const float *)d.psi, d.wts + a0, a1 - a0, CP, d.G,
+                                                       (const CellGeo<float> *)d.geo, phi_out, k > 0);
+        else
+            phi_pair_kernel<false><<<pb2, 256, 0, st>>>((const float *)d.psi, d.wts + a0, a1 - a0, CP, d.G,
+                                                        (const CellGeo<float> *)d.geo, phi_out, k > 0);
+    } else if (!d.fp64 && p.opt.phi_accumulate == TF_PHI_PAIR) {
+        phi_kernel<T, true><<<pb, 256, 0, st>>>((const V4<T> *)d.psi, d.wts + a0, a1 - a0, CG, d.G,
+                                                (const CellGeo<T> *)d.geo, phi_out, k > 0);
+    } else {
+        phi_kernel<T, false><<<pb, 256, 0, st>>>((const V4<T> *)d.psi, d.wts + a0, a1 - a0, CG, d.G,
+                                                 (const CellGeo<T> *)d.geo, phi_out, k > 0);
     }
+}
+
+template <class T> tf_status launch_step(Problem &p, const double *phi_in, double *phi_out, cudaStream_t st)
+{
+    DeviceState &d = *p.dev;
+    TF_CUDA(record_event(d.ev_start[0], st));
+    launch_source<T>(p, phi_in, st);
+    TF_CUDA(cudaGetLastError());
+    TF_CUDA(record_event(d.ev_stop[0], st));
     for (int k = 0; k < d.n_chunks; ++k) {
         const int64_t t0 = d.chunk_task_begin[k], t1 = d.chunk_task_begin[k + 1];
-        const int a0 = k * d.Dc, a1 = std::min(d.D, a0 + d.Dc);
         const int gb = d.chunk_group_begin[k], ng = d.chunk_group_begin[k + 1] - gb;
         const int win = std::min(d.window, ng);
         // gseed_host of this chunk: ng + 1 offsets starting at index gb + k
@@ -980,39 +1055,7 @@ template <class T> tf_status launch_step(Problem &p, const double *phi_in, doubl
         fill_kernel<<<fb, 256, 0, st>>>(d.ctrl, d.counters, d.indeg, (uint32_t)t0, (uint32_t)(t1 - t0), d.slots,
                                         d.seeds + s0, s_init - s0, p.opt.inject_stall, d.group_rem + gb,
                                         d.group_total + gb, ng);
-        SweepArgs<T> A;
-        A.geo = (const CellGeo<T> *)d.geo;
-        A.cells = d.cells;
-        A.task = d.task;
-        A.down = d.down;
-        A.counters = d.counters;
-        A.slots = d.slots;
-        A.ctrl = d.ctrl;
-        A.q = (const V4<T> *)d.q;
-        A.psi = (V4<T> *)d.psi;
-        A.sigma_t = (const T *)d.sigma_t;
-        A.omega = (const V4<T> *)d.omega;
-        A.S1 = (const V4<T> *)d.S1;
-        A.psi_in = (const T *)d.psi_in;
-        A.tets = d.tets;
-        A.C = d.C;
-        A.G = d.G;
-        A.dir_begin = a0;
-        A.task_begin = (uint32_t)t0;
-        A.task_end = (uint32_t)t1;
-        A.n_tasks = (unsigned long long)(t1 - t0);
-        A.wait_limit_ns = (unsigned long long)(p.opt.wait_limit_s * 1e9);
-        A.max_cells = p.graph.cells_per_task;
-        A.warp_smem = d.warp_smem;
-        A.dir_group = d.dir_group;
-        A.group_rem = d.group_rem + gb;
-        A.group_admit = d.group_admit + gb;
-        A.gseed = d.gseed + gb + k;
-        A.seeds = d.seeds;
-        A.n_groups = ng;
-        A.window = win;
-        A.lpc_shift = d.lpc_shift;
-        A.ppl = d.ppl;
+        const SweepArgs<T> A = make_args<T>(p, k);
         TF_CUDA(record_event(d.ev_start[1 + 2 * k], st));
         const size_t dyn = (size_t)d.warp_smem * d.wpc;
         if constexpr (sizeof(T) == 4) {
@@ -1028,23 +1071,8 @@ template <class T> tf_status launch_step(Problem &p, const double *phi_in, doubl
         TF_CUDA(cudaGetLastError());
         TF_CUDA(record_event(d.ev_stop[1 + 2 * k], st));
         end_kernel<<<1, 1, 0, st>>>(d.ctrl);
-        const int pb = (int)std::min<size_t>((CG + 255) / 256, (size_t)d.sm_count * 32);
         TF_CUDA(record_event(d.ev_start[2 + 2 * k], st));
-        if (d.paired) {
-            const size_t CP = CG / 2;
-            const int pb2 = (int)std::min<size_t>((CP + 255) / 256, (size_t)d.sm_count * 32);
-            if (p.opt.phi_accumulate == TF_PHI_PAIR)
-                phi_pair_kernel<true><<<pb2, 256, 0, st>>>((const float *)d.psi, d.wts + a0, a1 - a0, CP, d.G,
-                                                           (const CellGeo<float> *)d.geo, phi_out, k > 0);
-            else
-                phi_pair_kernel<false><<<pb2, 256, 0, st>>>((const float *)d.psi, d.wts + a0, a1 - a0, CP, d.G,
-                                                            (const CellGeo<float> *)d.geo, phi_out, k > 0);
-        } else if (!d.fp64 && p.opt.phi_accumulate == TF_PHI_PAIR)
-            phi_kernel<T, true><<<pb, 256, 0, st>>>((const V4<T> *)d.psi, d.wts + a0, a1 - a0, CG, d.G,
-                                                    (const CellGeo<T> *)d.geo, phi_out, k > 0);
-        else
-            phi_kernel<T, false><<<pb, 256, 0, st>>>((const V4<T> *)d.psi, d.wts + a0, a1 - a0, CG, d.G,
-                                                     (const CellGeo<T> *)d.geo, phi_out, k > 0);
+        launch_phi<T>(p, k, phi_out, st);
         TF_CUDA(cudaGetLastError());
         TF_CUDA(record_event(d.ev_stop[2 + 2 * k], st));
         d.last_chunk = k;
@@ -1251,6 +1279,363 @@ tf_status device_iterate(Problem &p, double tol, int32_t max_iters, double *phi,
         info->integrated_total = tot;
     }
     return conv ? TF_OK : fail(TF_ERR_NOT_CONVERGED, "source iteration reached max_iters");
+}
+
+
+// ================================================================ batched problems
+// Independent problems (meshes, direction sets, group counts of their own, one
+// precision) swept together: for each direction-chunk index c, one persistent
+// launch of sweep_batch_kernel runs the chunk-c tasks of every problem through
+// one shared ticket queue.  Source updates, phi reductions and statistics stay
+// per problem.  Each source iteration is a captured CUDA graph (one per
+// ping-pong parity) for the current set of unconverged problems; the graphs
+// are captured again when a problem converges and leaves the set.
+namespace {
+
+__global__ void batch_seed_kernel(const Ctrl *ctrl, unsigned long long *slots, const uint32_t *seeds, uint32_t n)
+{
+    const unsigned epoch = ctrl->epoch;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        slots[i] = ((unsigned long long)epoch << 32) | seeds[i];
+}
+
+struct BatchRun {
+    std::vector<Problem *> P;
+    int device = 0, n = 0, max_chunks = 0, sm_count = 0;
+    bool fp64 = false;
+    Ctrl *ctrl = nullptr, *ctrl_host = nullptr;
+    unsigned long long *slots = nullptr;
+    void *args = nullptr;          // [max_chunks][n] SweepArgs<T>
+    uint32_t *offsets = nullptr;   // [max_chunks][n + 1]
+    uint32_t *seeds = nullptr;     // [max_chunks][seed_cap]
+    size_t seed_cap = 0, task_cap = 0;
+    std::vector<std::vector<int>> part;  // per chunk: participating problems of the active set
+    std::vector<uint64_t> n_tasks, n_seeds;
+    int grid = 0, wpc = 4;
+    uint32_t warp_smem = 48;
+    cudaStream_t st = nullptr;
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+    ~BatchRun()
+    {
+        for (auto &g : gexec)
+            if (g) cudaGraphExecDestroy(g);
+        if (st) cudaStreamSynchronize(st);
+        cudaFree(ctrl);
+        cudaFree(slots);
+        cudaFree(args);
+        cudaFree(offsets);
+        cudaFree(seeds);
+        if (ctrl_host) cudaFreeHost(ctrl_host);
+        if (st) cudaStreamDestroy(st);
+    }
+};
+
+template <class T> const void *batch_kernel_fn() { return (const void *)sweep_batch_kernel<T>; }
+
+tf_status batch_setup(BatchRun &B, const tf_handle *problems, int32_t n)
+{
+    B.n = n;
+    for (int k = 0; k < n; ++k) B.P.push_back(static_cast<Problem *>(reinterpret_cast<Object *>(problems[k])));
+    B.device = B.P[0]->dev->device;
+    B.fp64 = B.P[0]->dev->fp64;
+    for (Problem *p : B.P) {
+        if (p->dev->device != B.device || p->dev->fp64 != B.fp64)
+            return fail(TF_ERR_ARG, "batched problems must share one device and one precision");
+        if (p->opt.inject_stall) return fail(TF_ERR_ARG, "inject_stall is not supported in batched launches");
+        B.max_chunks = std::max(B.max_chunks, p->dev->n_chunks);
+        B.warp_smem = std::max(B.warp_smem, p->dev->warp_smem);
+    }
+    TF_CUDA(cudaSetDevice(B.device));
+    TF_CUDA(cudaDeviceGetAttribute(&B.sm_count, cudaDevAttrMultiProcessorCount, B.device));
+    for (int c = 0; c < B.max_chunks; ++c) {
+        size_t t = 0, s = 0;
+        for (Problem *p : B.P) {
+            DeviceState &d = *p->dev;
+            if (c >= d.n_chunks) continue;
+            t += (size_t)(d.chunk_task_begin[c + 1] - d.chunk_task_begin[c]);
+            s += (size_t)(d.chunk_seed_begin[c + 1] - d.chunk_seed_begin[c]);
+        }
+        B.task_cap = std::max(B.task_cap, t);
+        B.seed_cap = std::max(B.seed_cap, s);
+    }
+    if (B.task_cap >= (size_t(1) << 32)) return fail(TF_ERR_ARG, "batched launch of more than 2^32 tasks");
+    const size_t argsz = B.fp64 ? sizeof(SweepArgs<double>) : sizeof(SweepArgs<float>);
+    TF_CUDA(cudaMalloc(&B.ctrl, sizeof(Ctrl)));
+    TF_CUDA(cudaMemset(B.ctrl, 0, sizeof(Ctrl)));
+    TF_CUDA(cudaMallocHost(&B.ctrl_host, sizeof(Ctrl)));
+    TF_CUDA(cudaMalloc(&B.slots, std::max<size_t>(B.task_cap, 1) * 8));
+    TF_CUDA(cudaMemset(B.slots, 0, std::max<size_t>(B.task_cap, 1) * 8));
+    TF_CUDA(cudaMalloc(&B.args, argsz * B.max_chunks * n));
+    TF_CUDA(cudaMalloc(&B.offsets, 4 * (size_t)B.max_chunks * (n + 1)));
+    TF_CUDA(cudaMalloc(&B.seeds, 4 * std::max<size_t>(B.seed_cap, 1) * B.max_chunks));
+    TF_CUDA(cudaStreamCreateWithFlags(&B.st, cudaStreamNonBlocking));
+    while (B.wpc > 1 && (size_t)B.warp_smem * B.wpc > 227 * 1024) B.wpc /= 2;
+    const int dyn = (int)(B.warp_smem * B.wpc);
+    const void *kfn = B.fp64 ? batch_kernel_fn<double>() : batch_kernel_fn<float>();
+    TF_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn));
+    int per_sm = 0;
+    TF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, 32 * B.wpc, dyn));
+    B.grid = std::max(1, per_sm) * B.sm_count;
+    return TF_OK;
+}
+
+// Per-chunk participant lists, global offsets, arguments and seeds of the active set.
+template <class T> tf_status batch_build(BatchRun &B, const std::vector<char> &active)
+{
+    B.part.assign(B.max_chunks, {});
+    B.n_tasks.assign(B.max_chunks, 0);
+    B.n_seeds.assign(B.max_chunks, 0);
+    std::vector<SweepArgs<T>> args((size_t)B.max_chunks * B.n);
+    std::vector<uint32_t> offs((size_t)B.max_chunks * (B.n + 1), 0), seeds(std::max<size_t>(B.seed_cap, 1) * B.max_chunks);
+    for (int c = 0; c < B.max_chunks; ++c) {
+        uint32_t off = 0;
+        size_t ns = 0;
+        for (int k = 0; k < B.n; ++k) {
+            Problem &p = *B.P[k];
+            DeviceState &d = *p.dev;
+            if (!active[k] || c >= d.n_chunks) continue;
+            const int j = (int)B.part[c].size();
+            B.part[c].push_back(k);
+            SweepArgs<T> A = make_args<T>(p, c);
+            A.ctrl = B.ctrl;  // waits report their errors to the batch's control block
+            A.slots = B.slots;
+            args[(size_t)c * B.n + j] = A;
+            offs[(size_t)c * (B.n + 1) + j] = off;
+            const int64_t s0 = d.chunk_seed_begin[c], s1 = d.chunk_seed_begin[c + 1];
+            for (int64_t i = s0; i < s1; ++i)
+                seeds[(size_t)c * B.seed_cap + ns++] = d.seeds_host[i] - (uint32_t)d.chunk_task_begin[c] + off;
+            off += (uint32_t)(d.chunk_task_begin[c + 1] - d.chunk_task_begin[c]);
+        }
+        offs[(size_t)c * (B.n + 1) + B.part[c].size()] = off;
+        B.n_tasks[c] = off;
+        B.n_seeds[c] = ns;
+    }
+    TF_CUDA(cudaMemcpy(B.args, args.data(), sizeof(SweepArgs<T>) * args.size(), cudaMemcpyHostToDevice));
+    TF_CUDA(cudaMemcpy(B.offsets, offs.data(), 4 * offs.size(), cudaMemcpyHostToDevice));
+    TF_CUDA(cudaMemcpy(B.seeds, seeds.data(), 4 * seeds.size(), cudaMemcpyHostToDevice));
+    return TF_OK;
+}
+
+// One source iteration of every active problem: phi_buf[k] -> phi_buf[1 - k].
+template <class T>
+tf_status batch_enqueue(BatchRun &B, const std::vector<char> &active, int k, bool with_stats, cudaStream_t st)
+{
+    for (int i = 0; i < B.n; ++i)
+        if (active[i]) launch_source<T>(*B.P[i], B.P[i]->dev->phi_buf[k], st);
+    for (int c = 0; c < B.max_chunks; ++c) {
+        if (B.part[c].empty()) continue;
+        begin_kernel<<<1, 1, 0, st>>>(B.ctrl, (unsigned long long)B.n_seeds[c], c == 0, 0);
+        for (int i : B.part[c]) {
+            DeviceState &d = *B.P[i]->dev;
+            const int64_t t0 = d.chunk_task_begin[c], t1 = d.chunk_task_begin[c + 1];
+            const int gb = d.chunk_group_begin[c], ng = d.chunk_group_begin[c + 1] - gb;
+            const int fb = (int)std::min<int64_t>(std::max<int64_t>(1, (t1 - t0 + 255) / 256), (int64_t)d.sm_count * 8);
+            fill_kernel<<<fb, 256, 0, st>>>(d.ctrl, d.counters, d.indeg, (uint32_t)t0, (uint32_t)(t1 - t0), d.slots,
+                                            d.seeds, 0u, 0, d.group_rem + gb, d.group_total + gb, ng);
+        }
+        const int sb = (int)std::min<uint64_t>(std::max<uint64_t>(1, (B.n_seeds[c] + 255) / 256), (uint64_t)B.sm_count * 4);
+        batch_seed_kernel<<<sb, 256, 0, st>>>(B.ctrl, B.slots, B.seeds + (size_t)c * B.seed_cap, (uint32_t)B.n_seeds[c]);
+        BatchArgs<T> BA;
+        BA.probs = reinterpret_cast<const SweepArgs<T> *>(B.args) + (size_t)c * B.n;
+        BA.offsets = B.offsets + (size_t)c * (B.n + 1);
+        BA.n = (int32_t)B.part[c].size();
+        BA.ctrl = B.ctrl;
+        BA.slots = B.slots;
+        BA.n_tasks = B.n_tasks[c];
+        BA.wait_limit_ns = (unsigned long long)(B.P[0]->opt.wait_limit_s * 1e9);
+        BA.warp_smem = B.warp_smem;
+        sweep_batch_kernel<T><<<B.grid, 32 * B.wpc, (size_t)B.warp_smem * B.wpc, st>>>(BA);
+        TF_CUDA(cudaGetLastError());
+        end_kernel<<<1, 1, 0, st>>>(B.ctrl);
+        for (int i : B.part[c]) launch_phi<T>(*B.P[i], c, B.P[i]->dev->phi_buf[1 - k], st);
+    }
+    if (with_stats) {
+        for (int i = 0; i < B.n; ++i) {
+            if (!active[i]) continue;
+            Problem &p = *B.P[i];
+            DeviceState &d = *p.dev;
+            double *cur = d.phi_buf[k], *nxt = d.phi_buf[1 - k];
+            TF_CUDA(cudaMemsetAsync(&d.ctrl->residual_bits, 0, 8, st));
+            if (p.opt.residual_floor >= 1.0) {
+                stats_res_kernel<<<d.stats_blocks, dim3(32, 8), 0, st>>>(nxt, cur, d.vol4, d.C, d.G, d.part);
+                finish_stats_res_kernel<<<(d.G + 127) / 128, 128, 0, st>>>(d.part, d.stats_blocks, d.G, d.gstats, d.ctrl);
+            } else {
+                stats_kernel<<<d.stats_blocks, dim3(32, 8), 0, st>>>(nxt, d.vol4, d.C, d.G, d.part);
+                finish_stats_kernel<<<(d.G + 127) / 128, 128, 0, st>>>(d.part, d.stats_blocks, d.G, d.gstats);
+                residual_kernel<<<d.stats_blocks, dim3(32, 8), 0, st>>>(nxt, cur, d.gstats, d.C, d.G,
+                                                                        p.opt.residual_floor, d.ctrl);
+            }
+            TF_CUDA(cudaMemcpyAsync(d.ctrl_host, d.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
+        }
+    }
+    TF_CUDA(cudaGetLastError());
+    TF_CUDA(cudaMemcpyAsync(B.ctrl_host, B.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
+    return TF_OK;
+}
+
+template <class T> tf_status batch_capture(BatchRun &B, const std::vector<char> &active)
+{
+    for (auto &g : B.gexec)
+        if (g) {
+            cudaGraphExecDestroy(g);
+            g = nullptr;
+        }
+    for (int k = 0; k < 2; ++k) {
+        if (cudaStreamBeginCapture(B.st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) break;
+        const tf_status s = batch_enqueue<T>(B, active, k, true, B.st);
+        cudaGraph_t g = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(B.st, &g);
+        if (s != TF_OK || e != cudaSuccess || !g) {
+            if (g) cudaGraphDestroy(g);
+            break;
+        }
+        const cudaError_t ei = cudaGraphInstantiate(&B.gexec[k], g, 0);
+        cudaGraphDestroy(g);
+        if (ei != cudaSuccess) B.gexec[k] = nullptr;
+    }
+    if (!B.gexec[0] || !B.gexec[1]) {
+        for (auto &g : B.gexec)
+            if (g) {
+                cudaGraphExecDestroy(g);
+                g = nullptr;
+            }
+        cudaGetLastError();
+    }
+    return TF_OK;
+}
+
+tf_status batch_check(BatchRun &B, const std::vector<char> &active)
+{
+    const Ctrl &c = *B.ctrl_host;
+    if (c.error) {
+        const int err = c.error;
+        cudaMemsetAsync(&B.ctrl->error, 0, sizeof(int), B.st);
+        cudaStreamSynchronize(B.st);
+        return fail((tf_status)err, "batched sweep: device error");
+    }
+    // task counts accumulate over the chunk launches of one iteration
+    uint64_t expect = 0;
+    for (int ch = 0; ch < B.max_chunks; ++ch) expect += B.n_tasks[ch];
+    (void)active;
+    if (c.tasks_done != expect)
+        return fail(TF_ERR_DEVICE, "batched sweep: executed " + std::to_string(c.tasks_done) + " of " +
+                                       std::to_string(expect) + " tasks");
+    return TF_OK;
+}
+
+tf_status copy_in(Problem &p, const double *src, double *dst, cudaStream_t st)
+{
+    const size_t bytes = (size_t)p.dev->C * p.dev->G * 4 * 8;
+    if (!src) {
+        TF_CUDA(cudaMemsetAsync(dst, 0, bytes, st));
+        return TF_OK;
+    }
+    TF_CUDA(cudaMemcpyAsync(dst, src, bytes, is_device_pointer(src) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+    return TF_OK;
+}
+
+tf_status copy_out(Problem &p, const double *src, double *dst, cudaStream_t st)
+{
+    const size_t bytes = (size_t)p.dev->C * p.dev->G * 4 * 8;
+    TF_CUDA(cudaMemcpyAsync(dst, src, bytes, is_device_pointer(dst) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+    return TF_OK;
+}
+
+}  // namespace
+
+tf_status device_batch_iterate(const tf_handle *problems, int32_t n, double tol, int32_t max_iters, double *const *phi,
+                               tf_iter_info *info, bool stats_only_sweep, const double *const *phi_in, void *stream)
+{
+    BatchRun B;
+    tf_status s = batch_setup(B, problems, n);
+    if (s != TF_OK) return s;
+    cudaStream_t user = (cudaStream_t)stream;
+    cudaEvent_t ev = nullptr;
+    TF_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    TF_CUDA(cudaEventRecord(ev, user));
+    TF_CUDA(cudaStreamWaitEvent(B.st, ev, 0));
+    for (int i = 0; i < n; ++i) {
+        const double *src = stats_only_sweep ? phi_in[i] : phi[i];
+        if ((s = copy_in(*B.P[i], src, B.P[i]->dev->phi_buf[0], B.st)) != TF_OK) return s;
+    }
+    std::vector<char> active(n, 1), built;
+    std::vector<int> iters(n, 0), final_buf(n, 0);
+    std::vector<double> res(n, INFINITY), secs(n, 0.0);
+    std::vector<char> conv(n, 0);
+    const bool timing = !stats_only_sweep;
+    int k = 0;
+    const auto t0 = std::chrono::steady_clock::now();
+    const int iterations = stats_only_sweep ? 1 : max_iters;
+    for (int it = 1; it <= iterations; ++it) {
+        if (active != built) {
+            s = B.fp64 ? batch_build<double>(B, active) : batch_build<float>(B, active);
+            if (s != TF_OK) return s;
+            if (timing) {
+                s = B.fp64 ? batch_capture<double>(B, active) : batch_capture<float>(B, active);
+                if (s != TF_OK) return s;
+            }
+            built = active;
+        }
+        if (timing && B.gexec[k]) {
+            TF_CUDA(cudaGraphLaunch(B.gexec[k], B.st));
+        } else {
+            s = B.fp64 ? batch_enqueue<double>(B, active, k, !stats_only_sweep, B.st)
+                       : batch_enqueue<float>(B, active, k, !stats_only_sweep, B.st);
+            if (s != TF_OK) return s;
+        }
+        TF_CUDA(cudaStreamSynchronize(B.st));
+        if ((s = batch_check(B, active)) != TF_OK) return s;
+        const double now = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        bool any = false;
+        for (int i = 0; i < n; ++i) {
+            if (!active[i]) continue;
+            iters[i] = it;
+            final_buf[i] = 1 - k;
+            if (!stats_only_sweep) {
+                std::memcpy(&res[i], &B.P[i]->dev->ctrl_host->residual_bits, sizeof(double));
+                if (info && info[i].residual_history) info[i].residual_history[it - 1] = res[i];
+                if (res[i] < tol) {
+                    conv[i] = 1;
+                    active[i] = 0;
+                    secs[i] = now;
+                }
+            }
+            if (active[i]) any = true;
+        }
+        for (int i = 0; i < n; ++i)
+            if (!conv[i]) secs[i] = now;
+        k = 1 - k;
+        if (!any) break;
+    }
+    for (int i = 0; i < n; ++i) {
+        DeviceState &d = *B.P[i]->dev;
+        double *dst = stats_only_sweep ? const_cast<double *>(phi[i]) : phi[i];
+        if ((s = copy_out(*B.P[i], d.phi_buf[final_buf[i]], dst, B.st)) != TF_OK) return s;
+        if (!stats_only_sweep)
+            TF_CUDA(cudaMemcpyAsync(d.gstats_host, d.gstats, sizeof(double) * 4 * d.G, cudaMemcpyDeviceToHost, B.st));
+        d.last_chunk = d.n_chunks - 1;
+    }
+    TF_CUDA(cudaEventRecord(ev, B.st));
+    TF_CUDA(cudaStreamWaitEvent(user, ev, 0));
+    TF_CUDA(cudaStreamSynchronize(B.st));
+    cudaEventDestroy(ev);
+    bool all = true;
+    for (int i = 0; i < n; ++i) {
+        all = all && (conv[i] || stats_only_sweep);
+        if (!info || stats_only_sweep) continue;
+        DeviceState &d = *B.P[i]->dev;
+        info[i].iterations = iters[i];
+        info[i].converged = conv[i];
+        info[i].residual = res[i];
+        info[i].seconds = secs[i];
+        double tot = 0.0;
+        for (int g = 0; g < d.G; ++g) {
+            tot += d.gstats_host[4 * g + 1];
+            if (info[i].integrated_flux) info[i].integrated_flux[g] = d.gstats_host[4 * g + 1];
+        }
+        info[i].integrated_total = tot;
+    }
+    return all ? TF_OK : fail(TF_ERR_NOT_CONVERGED, "batched source iteration reached max_iters");
 }
 
 tf_status device_psi(Problem &p, int32_t dir, void *out, void *stream)

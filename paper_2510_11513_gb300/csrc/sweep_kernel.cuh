@@ -170,6 +170,7 @@ template <class T> struct SweepArgs {
     const uint32_t *seeds;
     int32_t n_groups, window;
     int32_t lpc_shift, ppl;      // paired path: log2 lanes per cell, group pairs per lane
+    int32_t mode;                // kernel variant of this problem (batched launches dispatch on it)
 };
 
 // Solve one 4x4 system by Gaussian elimination without pivoting: the
@@ -457,10 +458,10 @@ template <class T> struct StageLayout {
     }
 };
 
-// Bytes of shared memory one warp needs for the staged path (3 stages + 6 mbarriers).
+// Bytes of shared memory one warp needs for the staged path's 3 stages (the mbarriers come on top).
 template <class T> inline size_t staged_warp_bytes(int G)
 {
-    return 3 * (sizeof(CellGeo<T>) + 4 * (size_t)G * sizeof(V4<T>)) + 6 * 8;
+    return 3 * (sizeof(CellGeo<T>) + 4 * (size_t)G * sizeof(V4<T>));
 }
 
 // Lane 0: geometry record and source row of cell c into stage s.
@@ -587,12 +588,11 @@ __device__ __forceinline__ void solve_staged_cell(const SweepArgs<T> &A, const u
 // Returns false if a wait ran out (error word set).
 template <class T>
 __device__ __forceinline__ bool run_task_staged(const SweepArgs<T> &A, uint4 ti, int lane, T ox, T oy, T oz,
-                                                size_t psi_dir, unsigned char *wsm, uint32_t &ph)
+                                                size_t psi_dir, unsigned char *wsm, uint64_t *bars, uint32_t &ph)
 {
     const unsigned FULL = 0xffffffffu;
     const uint32_t ncell = ti.y & 0xffffu;
     const StageLayout<T> L(A.G);
-    uint64_t *bars = reinterpret_cast<uint64_t *>(wsm + 3 * L.stage);
     const uint32_t e_lo = lane < (int)ncell ? __ldg(A.cells + ti.x + lane) : 0u;
     const uint32_t e_hi = lane + 32 < (int)ncell ? __ldg(A.cells + ti.x + 32 + lane) : 0u;
     auto entry = [&](uint32_t k) { return __shfl_sync(FULL, k < 32 ? e_lo : e_hi, k & 31); };
@@ -848,8 +848,8 @@ __device__ __forceinline__ void pair_solve(const SweepArgs<float> &A, const TabR
     st_pair(reinterpret_cast<float *>(A.psi) + ((psi_dir + (size_t)c) * P + p) * 8, o);
 }
 
-// Shared memory of one warp on the paired path: the cell table, three stage
-// buffers (each: cps cells x [source row, 3 upwind rows]) and their mbarriers.
+// Shared memory of one warp on the paired path: the cell table and three stage
+// buffers (each: cps cells x [source row, 3 upwind rows]); the mbarriers come on top.
 struct PairLayout {
     uint32_t P, row, cps, lpc_shift, ppl, stage, table;
     __device__ __host__ PairLayout(int G, int max_cells)
@@ -863,7 +863,7 @@ struct PairLayout {
         stage = cps * 4u * row;
         table = (uint32_t)max_cells * (uint32_t)sizeof(TabRow);
     }
-    __device__ __host__ uint32_t bytes() const { return table + 3u * stage + 3u * 8u; }
+    __device__ __host__ uint32_t bytes() const { return table + 3u * stage; }
 };
 
 // One task on the paired path.  Lanes first build the task's cell table in
@@ -872,14 +872,14 @@ struct PairLayout {
 // lane l takes cell l >> lpc_shift of the stage and pairs (l mod lpc) + 32 m.
 // Returns false if a wait ran out (error word set).
 __device__ __forceinline__ bool run_task_pairs(const SweepArgs<float> &A, uint4 ti, int lane, float ox, float oy,
-                                               float oz, size_t psi_dir, unsigned char *wsm, uint32_t &ph)
+                                               float oz, size_t psi_dir, unsigned char *wsm, uint64_t *bars,
+                                               uint32_t &ph)
 {
     const unsigned FULL = 0xffffffffu;
     const uint32_t ncell = ti.y & 0xffffu;
     const PairLayout L(A.G, A.max_cells);
     TabRow *tab = reinterpret_cast<TabRow *>(wsm);
     unsigned char *stages = wsm + L.table;
-    uint64_t *bars = reinterpret_cast<uint64_t *>(stages + 3 * L.stage);
     for (uint32_t j = lane; j < ncell; j += 32) tab_setup(A, __ldg(A.cells + ti.x + j), ox, oy, oz, tab[j]);
     __syncwarp();
     const uint32_t nst = (ncell + L.cps - 1) / L.cps;
@@ -960,19 +960,11 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 3) sweep_kernel(cons
     extern __shared__ __align__(128) unsigned char dsm[];
     unsigned char *wsm = dsm + (size_t)(threadIdx.x >> 5) * A.warp_smem;
     uint32_t ph = 0;  // mbarrier phase parities of this warp's stages
-    if constexpr (MODE == 2) {
+    // the six mbarriers of the staged paths sit in the last 48 bytes of the warp's region
+    uint64_t *bars = reinterpret_cast<uint64_t *>(wsm + A.warp_smem - 48);
+    if constexpr (MODE == 2 || MODE == 3) {
         if (lane == 0) {
-            uint64_t *bars = reinterpret_cast<uint64_t *>(wsm + 3 * StageLayout<T>(A.G).stage);
             for (int b = 0; b < 6; ++b) mbar_init(&bars[b], 1);
-            fence_proxy_async_shared();
-        }
-        __syncwarp();
-    }
-    if constexpr (MODE == 3) {
-        if (lane == 0) {
-            const PairLayout L(A.G, A.max_cells);
-            uint64_t *bars = reinterpret_cast<uint64_t *>(wsm + L.table + 3 * L.stage);
-            for (int b = 0; b < 3; ++b) mbar_init(&bars[b], 1);
             fence_proxy_async_shared();
         }
         __syncwarp();
@@ -1037,9 +1029,9 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 3) sweep_kernel(cons
         const V4<T> om = ld_ro(A.omega + dir);
         const size_t psi_dir = (size_t)(dir - (uint32_t)A.dir_begin) * (size_t)A.C;
         if constexpr (MODE == 3) {
-            if (!run_task_pairs(A, ti, lane, om.x, om.y, om.z, psi_dir, wsm, ph)) break;
+            if (!run_task_pairs(A, ti, lane, om.x, om.y, om.z, psi_dir, wsm, bars, ph)) break;
         } else if constexpr (MODE == 2) {
-            if (!run_task_staged(A, ti, lane, om.x, om.y, om.z, psi_dir, wsm, ph)) break;
+            if (!run_task_staged(A, ti, lane, om.x, om.y, om.z, psi_dir, wsm, bars, ph)) break;
         } else if constexpr (MODE == 1) {
             run_task_wide(A, ti, lane, om.x, om.y, om.z, psi_dir);
         } else {
@@ -1104,3 +1096,136 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 3) sweep_kernel(cons
     }
 }
 
+// ------------------------------------------------------------------ batched launch
+// Several independent problems in one persistent launch: their tasks share one
+// ticket queue under global ids (problem k owns [offsets[k], offsets[k+1]));
+// each task runs with its own problem's arguments and kernel variant, and its
+// downwind releases are translated back to global ids.
+template <class T> struct BatchArgs {
+    const SweepArgs<T> *probs;  // [n] per-problem arguments (queue fields unused)
+    const uint32_t *offsets;    // [n + 1]
+    int32_t n;
+    Ctrl *ctrl;
+    unsigned long long *slots;
+    unsigned long long n_tasks;
+    unsigned long long wait_limit_ns;
+    uint32_t warp_smem;
+};
+
+template <class T>
+__global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 3) sweep_batch_kernel(const BatchArgs<T> B)
+{
+    const int lane = threadIdx.x & 31;
+    const unsigned FULL = 0xffffffffu;
+    const unsigned epoch = *(const volatile unsigned *)&B.ctrl->epoch;
+    extern __shared__ __align__(128) unsigned char dsm[];
+    unsigned char *wsm = dsm + (size_t)(threadIdx.x >> 5) * B.warp_smem;
+    uint32_t ph = 0;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(wsm + B.warp_smem - 48);
+    if (lane == 0) {
+        for (int b = 0; b < 6; ++b) mbar_init(&bars[b], 1);
+        fence_proxy_async_shared();
+    }
+    __shared__ unsigned long long wstat[8][6];
+    unsigned long long *ws = wstat[threadIdx.x >> 5];
+    if (lane < 6) ws[lane] = 0;
+    __syncwarp();
+    const unsigned long long t_start = globaltimer();
+    unsigned long long ticket = 0;
+    if (lane == 0) ticket = atomicAdd(&B.ctrl->head, 1ull);
+    ticket = __shfl_sync(FULL, ticket, 0);
+    while (ticket < B.n_tasks) {
+        unsigned gid = 0;
+        int stop = 0;
+        if (lane == 0) {
+            const unsigned long long t0 = globaltimer();
+            unsigned long long v = ld_acquire(B.slots + ticket);
+            if ((unsigned)(v >> 32) != epoch) {
+                unsigned ns = 32;
+                for (;;) {
+                    __nanosleep(ns);
+                    if (ns < 256) ns <<= 1;
+                    ++ws[0];
+                    v = ld_acquire(B.slots + ticket);
+                    if ((unsigned)(v >> 32) == epoch) break;
+                    if (ld_volatile(&B.ctrl->error)) {
+                        stop = 1;
+                        break;
+                    }
+                    if (globaltimer() - t0 > B.wait_limit_ns) {
+                        atomicCAS(&B.ctrl->error, 0, (int)TF_ERR_TIMEOUT);
+                        stop = 1;
+                        break;
+                    }
+                }
+            }
+            ws[1] += globaltimer() - t0;
+            ++ws[5];
+            gid = (unsigned)v;
+            if (!stop && gid >= B.n_tasks) {
+                atomicCAS(&B.ctrl->error, 0, (int)TF_ERR_DEVICE);
+                stop = 1;
+            }
+        }
+        __syncwarp();
+        stop = __shfl_sync(FULL, stop, 0);
+        if (stop) break;
+        gid = __shfl_sync(FULL, gid, 0);
+        unsigned long long tb = 0;
+        if (lane == 0) tb = globaltimer();
+        unsigned long long next = 0;
+        if (lane == 0) next = atomicAdd(&B.ctrl->head, 1ull);
+        // problem owning the global id: offsets ascend, n is small
+        int lo = 0, hi = B.n - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (__ldg(B.offsets + mid) <= gid) lo = mid; else hi = mid - 1;
+        }
+        const SweepArgs<T> &A = B.probs[lo];
+        const uint32_t base = __ldg(B.offsets + lo);
+        const uint32_t task = gid - base + A.task_begin;
+        const uint4 ti = __ldg(A.task + task);
+        const uint32_t dir = ti.y >> 16;
+        const V4<T> om = ld_ro(A.omega + dir);
+        const size_t psi_dir = (size_t)(dir - (uint32_t)A.dir_begin) * (size_t)A.C;
+        bool ok = true;
+        if constexpr (sizeof(T) == 4) {
+            if (A.mode == 3) ok = run_task_pairs(A, ti, lane, om.x, om.y, om.z, psi_dir, wsm, bars, ph);
+            else if (A.mode == 2) ok = run_task_staged(A, ti, lane, om.x, om.y, om.z, psi_dir, wsm, bars, ph);
+            else run_task_generic(A, ti, lane, om.x, om.y, om.z, psi_dir);
+        } else {
+            if (A.mode == 2) ok = run_task_staged(A, ti, lane, om.x, om.y, om.z, psi_dir, wsm, bars, ph);
+            else run_task_generic(A, ti, lane, om.x, om.y, om.z, psi_dir);
+        }
+        if (!ok) break;
+        fence_acq_rel_gpu();
+        __syncwarp();
+        for (uint32_t e = lane; e < ti.w; e += 32) {
+            const uint32_t d = __ldg(A.down + ti.z + e);
+            if (atom_add_acq_rel(A.counters + d, -1) == 1) {
+                const unsigned long long slot = atomicAdd(&B.ctrl->tail, 1ull);
+                if (slot < B.n_tasks)
+                    st_release(B.slots + slot, ((unsigned long long)epoch << 32) | (d - A.task_begin + base));
+                else
+                    atomicCAS(&B.ctrl->error, 0, (int)TF_ERR_DEVICE);
+            }
+        }
+        __syncwarp();
+        if (lane == 0) {
+            ws[2] += globaltimer() - tb;
+            ++ws[3];
+        }
+        ticket = __shfl_sync(FULL, next, 0);
+    }
+    const unsigned long long t_end = globaltimer();
+    __syncwarp();
+    if (lane == 0) {
+        atomicAdd(&B.ctrl->tasks_done, ws[3]);
+        atomicAdd(&B.ctrl->polls, ws[0]);
+        atomicAdd(&B.ctrl->wait_ns, ws[1]);
+        atomicAdd(&B.ctrl->busy_ns, ws[2]);
+        atomicAdd(&B.ctrl->pops, ws[5]);
+        atomicMin(&B.ctrl->t_first, t_start);
+        atomicMax(&B.ctrl->t_last, t_end);
+    }
+}

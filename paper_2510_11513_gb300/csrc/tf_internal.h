@@ -98,5 +98,9 @@ void device_destroy(Problem &p);
 tf_status device_sweep(Problem &p, const double *phi_in, double *phi_out, void *stream);
 tf_status device_iterate(Problem &p, double tol, int32_t max_iters, double *phi, tf_iter_info *info, void *stream);
 tf_status device_psi(Problem &p, int32_t dir, void *out, void *stream);
+// Batched problems in shared persistent launches (sweep.cu).  sweep_only: one
+// transport step phi_in -> phi (no statistics).
+tf_status device_batch_iterate(const tf_handle *problems, int32_t n, double tol, int32_t max_iters, double *const *phi,
+                               tf_iter_info *info, bool sweep_only, const double *const *phi_in, void *stream);
 
 }  // namespace tf

@@ -46,7 +46,7 @@ class tf_iter_info(C.Structure):
     _fields_ = [
         ("iterations", C.c_int32), ("converged", C.c_int32), ("residual", C.c_double),
         ("integrated_total", C.c_double), ("integrated_flux", C.POINTER(C.c_double)),
-        ("residual_history", C.POINTER(C.c_double)),
+        ("residual_history", C.POINTER(C.c_double)), ("seconds", C.c_double),
     ]
 
 
@@ -257,6 +257,37 @@ def tf_problem_stats(problem):
     s = tf_stats()
     _check(load().tf_problem_stats(problem, C.byref(s)), "tf_problem_stats")
     return {name: getattr(s, name) for name, _ in tf_stats._fields_ if not name.startswith("reserved")}
+
+
+def sweep_batch(problems, phi_in, phi_out, stream=None):
+    """One transport step of several problems in shared persistent launches."""
+    tf_sweep([p.h for p in problems], phi_in, phi_out, stream)
+    return phi_out
+
+
+def source_iterate_batch(problems, phis, tol, max_iters, stream=None, history=False):
+    """Source iteration of several problems in shared persistent launches; returns
+    (status, [info dict per problem]) with per-problem iterations, convergence,
+    residual, integrated flux and seconds to convergence."""
+    infos, keep = [], []
+    for p in problems:
+        ig = (C.c_double * p.n_groups)()
+        hist = (C.c_double * max_iters)() if history else None
+        i = tf_iter_info()
+        i.integrated_flux = C.cast(ig, C.POINTER(C.c_double))
+        if hist is not None:
+            i.residual_history = C.cast(hist, C.POINTER(C.c_double))
+        infos.append(i)
+        keep.append((ig, hist))
+    st, out = tf_source_iterate([p.h for p in problems], tol, max_iters, phis, infos, stream)
+    res = []
+    for i, (ig, hist) in zip(out, keep):
+        d = dict(iterations=i.iterations, converged=bool(i.converged), residual=i.residual, seconds=i.seconds,
+                 integrated_total=i.integrated_total, integrated_flux=np.array(ig[:]))
+        if hist is not None:
+            d["residual_history"] = np.array(hist[: i.iterations])
+        res.append(d)
+    return st, res
 
 
 # ------------------------------------------------------------- handle owners
