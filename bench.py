@@ -345,6 +345,51 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_batch(args):
+    """Many independent problems (uneven meshes, direction sets, group counts) iterated to the
+    stopping test together in shared persistent launches; aggregate grind time over the units
+    actually swept, and each problem's time to convergence."""
+    import torch
+
+    import paper_2510_11513_gb300 as tf
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    cfgs = W.batch_of_problems(count=args.batch_count)
+    psi = [len(c["tets"]) * c["n_polar"] * c["n_azimuthal"] * c["n_groups"] * 16 for c in cfgs]
+    free = torch.cuda.mem_get_info()[0]
+    budget = 0.6 * free
+    t0 = time.perf_counter()
+    probs = []
+    for c, pb in zip(cfgs, psi):
+        share = budget * pb / sum(psi) if sum(psi) > budget else 0.0
+        probs.append(tf.Problem.from_config(c, precision=tf.TF_FP32, psi_budget_gb=share / 1e9))
+    setup = time.perf_counter() - t0
+    phis = [torch.zeros((p.n_cells, p.n_groups, 4), dtype=torch.float64, device=dev) for p in probs]
+    tf.source_iterate_batch(probs, phis, 0.0, 1)  # warm-up iteration
+    for ph in phis:
+        ph.zero_()
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    st, infos = tf.source_iterate_batch(probs, phis, args.batch_tol, 2000)
+    e1.record()
+    torch.cuda.synchronize(dev)
+    sec = e0.elapsed_time(e1) / 1e3
+    swept = sum(p.n_units * i["iterations"] for p, i in zip(probs, infos))
+    line = {"metric": METRIC, "value": sec * 1e9 / swept, "unit": UNIT, "n_gpus": 1, "steps": 1, "warmup": 1,
+            "ms_per_step": sec * 1e3, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"batch_{len(cfgs)}_problems", "problems": len(cfgs),
+                       "units_per_sweep": sum(p.n_units for p in probs), "tol": args.batch_tol,
+                       "setup_s": round(setup, 1), "n_chunks": [p.stats()["n_chunks"] for p in probs]},
+            "all_converged": st == tf.TF_OK,
+            "per_problem": [{"cells": p.n_cells, "directions": p.n_dirs, "groups": p.n_groups,
+                             "iterations": i["iterations"], "seconds_to_tol": round(i["seconds"], 4),
+                             "converged": i["converged"]} for p, i in zip(probs, infos)]}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -363,6 +408,8 @@ def main():
     ap.add_argument("--octant-window", type=int, default=0, help="octants active at once (0 = library default)")
     ap.add_argument("--staging", type=int, default=0, help="1 = no shared-memory staging")
     ap.add_argument("--pairing", type=int, default=0, help="0 auto, 1 off, 2 packed group pairs when G is even")
+    ap.add_argument("--batch-count", type=int, default=64, help="--config batch: number of problems")
+    ap.add_argument("--batch-tol", type=float, default=1e-6)
     ap.add_argument("--n", type=int, default=0, help="hexes per box edge (default: the workload's)")
     ap.add_argument("--groups", type=int, default=0)
     ap.add_argument("--polar", type=int, default=0)
@@ -371,6 +418,8 @@ def main():
     args.warmup = max(3, args.warmup)  # at least 3 untimed warm-up steps
     if args.impl == "reference":
         run_reference(args)
+    elif args.config == "batch":
+        run_batch(args)
     else:
         run_ours(args)
 
