@@ -17,6 +17,8 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -559,16 +561,32 @@ cudaError_t record_event(cudaEvent_t ev, cudaStream_t st)
                                                : cudaEventRecord(ev, st);
 }
 
+// The dynamic shared-memory limit is an attribute of the kernel function, shared
+// by every problem and by captured graphs: it is only ever raised.
+cudaError_t ensure_dyn_smem(const void *kfn, int bytes)
+{
+    static std::mutex mu;
+    static std::map<const void *, int> cur;
+    std::lock_guard<std::mutex> lk(mu);
+    int &c = cur[kfn];
+    if (bytes <= c) return cudaSuccess;
+    const cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) c = bytes;
+    return e;
+}
+
 tf_status cuda_fail(cudaError_t e, const char *what)
 {
     return fail(e == cudaErrorMemoryAllocation ? TF_ERR_NOMEM : TF_ERR_CUDA,
                 std::string(what) + ": " + cudaGetErrorString(e));
 }
 
-#define TF_CUDA(call)                                       \
-    do {                                                    \
-        cudaError_t e_ = (call);                            \
-        if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+#define TF_STR2(x) #x
+#define TF_STR(x) TF_STR2(x)
+#define TF_CUDA(call)                                                                   \
+    do {                                                                                \
+        cudaError_t e_ = (call);                                                        \
+        if (e_ != cudaSuccess) return cuda_fail(e_, "sweep.cu:" TF_STR(__LINE__) " " #call); \
     } while (0)
 
 template <class P> tf_status dmalloc(DeviceState &d, P **p, size_t bytes)
@@ -894,7 +912,7 @@ tf_status device_create(Problem &p, const int32_t *cell_material, const double *
                                 : d.mode == 2 ? (const void *)sweep_kernel<float, 2>
                                 : d.mode == 1 ? (const void *)sweep_kernel<float, 1>
                                               : (const void *)sweep_kernel<float, 0>);
-    if (dyn > 0) TF_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn));
+    if (dyn > 0) TF_CUDA(ensure_dyn_smem(kfn, dyn));
     int per_sm = 0;
     TF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, 32 * d.wpc, dyn));
     if (p.opt.ctas_per_sm > 0) per_sm = std::min(per_sm, p.opt.ctas_per_sm);
@@ -1372,7 +1390,7 @@ tf_status batch_setup(BatchRun &B, const tf_handle *problems, int32_t n)
     while (B.wpc > 1 && (size_t)B.warp_smem * B.wpc > 227 * 1024) B.wpc /= 2;
     const int dyn = (int)(B.warp_smem * B.wpc);
     const void *kfn = B.fp64 ? batch_kernel_fn<double>() : batch_kernel_fn<float>();
-    TF_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn));
+    TF_CUDA(ensure_dyn_smem(kfn, dyn));
     int per_sm = 0;
     TF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, 32 * B.wpc, dyn));
     B.grid = std::max(1, per_sm) * B.sm_count;

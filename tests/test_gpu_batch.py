@@ -27,7 +27,11 @@ MIX = [  # (n, G, n_polar, n_az, extra options)
 def _problems(precision, mix=MIX):
     cfgs, probs = [], []
     for j, (n, G, npol, naz, opts) in enumerate(mix):
-        cfg = W.two_material_box(n=n, G=G, n_polar=npol, n_az=naz, seed=W.BASE_SEED + 100 + j)
+        seed = W.BASE_SEED + 100 + j
+        cfg = W.two_material_box(n=n, G=G, n_polar=npol, n_az=naz, seed=seed)
+        while cfg["Q"].sum() == 0.0:  # small boxes can draw only the source-free material
+            seed += 1000
+            cfg = W.two_material_box(n=n, G=G, n_polar=npol, n_az=naz, seed=seed)
         cfgs.append(cfg)
         probs.append(tf.Problem.from_config(cfg, precision=precision, **opts))
     return cfgs, probs
