@@ -363,7 +363,8 @@ def run_batch(args):
     probs = []
     for c, pb in zip(cfgs, psi):
         share = budget * pb / sum(psi) if sum(psi) > budget else 0.0
-        probs.append(tf.Problem.from_config(c, precision=tf.TF_FP32, psi_budget_gb=share / 1e9))
+        probs.append(tf.Problem.from_config(c, precision=tf.TF_FP32, psi_budget_gb=share / 1e9,
+                                            cells_per_task=-1 if args.autotune else 0))
     setup = time.perf_counter() - t0
     phis = [torch.zeros((p.n_cells, p.n_groups, 4), dtype=torch.float64, device=dev) for p in probs]
     tf.source_iterate_batch(probs, phis, 0.0, 1)  # warm-up iteration
@@ -382,9 +383,11 @@ def run_batch(args):
             "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"batch_{len(cfgs)}_problems", "problems": len(cfgs),
                        "units_per_sweep": sum(p.n_units for p in probs), "tol": args.batch_tol,
-                       "setup_s": round(setup, 1), "n_chunks": [p.stats()["n_chunks"] for p in probs]},
+                       "setup_s": round(setup, 1), "n_chunks": [p.stats()["n_chunks"] for p in probs],
+                       "autotune": bool(args.autotune)},
             "all_converged": st == tf.TF_OK,
             "per_problem": [{"cells": p.n_cells, "directions": p.n_dirs, "groups": p.n_groups,
+                             "cells_per_task": p.stats()["cells_per_task"], "kernel_mode": p.stats()["kernel_mode"],
                              "iterations": i["iterations"], "seconds_to_tol": round(i["seconds"], 4),
                              "converged": i["converged"]} for p, i in zip(probs, infos)]}
     print(json.dumps(line), flush=True)
@@ -410,6 +413,7 @@ def main():
     ap.add_argument("--pairing", type=int, default=0, help="0 auto, 1 off, 2 packed group pairs when G is even")
     ap.add_argument("--batch-count", type=int, default=64, help="--config batch: number of problems")
     ap.add_argument("--batch-tol", type=float, default=1e-6)
+    ap.add_argument("--autotune", type=int, default=1, help="--config batch: autotuned task grain (1) or default (0)")
     ap.add_argument("--n", type=int, default=0, help="hexes per box edge (default: the workload's)")
     ap.add_argument("--groups", type=int, default=0)
     ap.add_argument("--polar", type=int, default=0)

@@ -66,7 +66,9 @@ typedef enum {
 typedef struct {
     int32_t precision;       /* tf_precision: arithmetic of local solves and psi storage (default TF_FP32) */
     int32_t device;          /* CUDA device ordinal (default 0) */
-    int32_t cells_per_task;  /* cells of one t-level grouped into one task; 0 = automatic */
+    int32_t cells_per_task;  /* cells of one t-level grouped into one task; 0 = automatic (about 1024 units),
+                              * < 0 = autotuned: timed trial sweeps over a direction sample, cached per
+                              * (precision, groups, directions, log2 cells) */
     int32_t dir_chunk;       /* directions swept per persistent launch; 0 = as many as the memory budget allows */
     int32_t warps_per_cta;   /* persistent kernel CTA size in warps; 0 = automatic */
     int32_t ctas_per_sm;     /* persistent CTAs per SM; 0 = as many as are resident */
@@ -131,6 +133,12 @@ typedef struct {
     int64_t launches_per_step;  /* kernels this library launches per transport step */
     int32_t kernel_mode;        /* sweep kernel variant: 0 any G, 1 G%32==0 (registers), 2 G%32==0 staged
                                  * in shared memory, 3 packed group pairs (FP32, even G) */
+    /* task-grain autotuning (cells_per_task < 0 at creation): candidate grains and the time
+     * of one trial sweep over a direction sample for each; tuned_cached = 1 if the choice
+     * came from an earlier problem of the same class */
+    int32_t tuned_n, tuned_cached;
+    int32_t tuned_candidates[8];
+    double tuned_seconds[8];
     int32_t reserved_i[5];
     double reserved_d[6];
 } tf_stats;

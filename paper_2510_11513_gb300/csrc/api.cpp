@@ -176,7 +176,15 @@ tf_status tf_problem_create(tf_handle mesh, tf_handle quad, int32_t n_groups, in
     p->has_S1 = S1 != nullptr;
     p->has_inflow = psi_inflow != nullptr;
     int32_t B = p->opt.cells_per_task;
-    if (B <= 0) {
+    if (B < 0) {
+        tf_status st = autotune_cells_per_task(*m, *q, n_groups, n_materials, cell_material, sigma_t, sigma_s, Q, p->opt,
+                                               &B, &p->tune);
+        if (st != TF_OK) {
+            release(p);
+            return st;
+        }
+    }
+    if (B == 0) {
         // about 1024 units per task; at most 32 cells when the FP32 paired path will run
         const bool paired = p->opt.precision == TF_FP32 && n_groups % 2 == 0 &&
                             (p->opt.pairing == 2 || (p->opt.pairing == 0 && n_groups % 32 != 0));
@@ -282,6 +290,12 @@ tf_status tf_problem_stats(tf_handle problem, tf_stats *out)
     Problem *p = as<Problem>(problem, Kind::Problem);
     if (!p || !out) return fail(TF_ERR_ARG, "tf_problem_stats: bad handle or NULL output");
     *out = p->stats;
+    out->tuned_n = p->tune.n_candidates;
+    out->tuned_cached = p->tune.cached;
+    for (int k = 0; k < 8; ++k) {
+        out->tuned_candidates[k] = p->tune.candidates[k];
+        out->tuned_seconds[k] = p->tune.seconds[k];
+    }
     return TF_OK;
 }
 

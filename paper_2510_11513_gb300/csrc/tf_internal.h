@@ -75,6 +75,12 @@ tf_status build_task_graph(const Mesh &m, const Quad &q, int32_t cells_per_task,
 
 struct DeviceState;  // defined in the CUDA part
 
+struct tf_autotune_report {
+    int32_t n_candidates = 0, chosen = 0, cached = 0, sample_directions = 0;
+    int32_t candidates[8] = {0};
+    double seconds[8] = {0};
+};
+
 struct Problem : Object {
     Problem() : Object(Kind::Problem) {}
     ~Problem() override;
@@ -86,7 +92,13 @@ struct Problem : Object {
     TaskGraph graph;
     DeviceState *dev = nullptr;
     tf_stats stats{};
+    tf_autotune_report tune;
 };
+
+// Picks cells_per_task by timed trial sweeps over a direction sample (autotune.cpp).
+tf_status autotune_cells_per_task(const Mesh &m, const Quad &q, int32_t G, int32_t M, const int32_t *cell_material,
+                                  const double *sigma_t, const double *sigma_s, const double *Q, const tf_options &opt,
+                                  int32_t *out, tf_autotune_report *rep);
 
 void retain(Object *o);
 void release(Object *o);

@@ -59,8 +59,9 @@ class tf_stats(C.Structure):
         ("mean_ready", C.c_double), ("source_event_seconds", C.c_double), ("sweep_event_seconds", C.c_double),
         ("phi_event_seconds", C.c_double), ("cum_source_event_seconds", C.c_double),
         ("cum_sweep_event_seconds", C.c_double), ("cum_phi_event_seconds", C.c_double), ("cum_steps", C.c_int64),
-        ("launches_per_step", C.c_int64), ("kernel_mode", C.c_int32), ("reserved_i", C.c_int32 * 5),
-        ("reserved_d", C.c_double * 6),
+        ("launches_per_step", C.c_int64), ("kernel_mode", C.c_int32), ("tuned_n", C.c_int32),
+        ("tuned_cached", C.c_int32), ("tuned_candidates", C.c_int32 * 8), ("tuned_seconds", C.c_double * 8),
+        ("reserved_i", C.c_int32 * 5), ("reserved_d", C.c_double * 6),
     ]
 
 
@@ -256,7 +257,10 @@ def tf_integrated_flux_noalloc(phi, volume, n_cells, n_groups, out, stream=None)
 def tf_problem_stats(problem):
     s = tf_stats()
     _check(load().tf_problem_stats(problem, C.byref(s)), "tf_problem_stats")
-    return {name: getattr(s, name) for name, _ in tf_stats._fields_ if not name.startswith("reserved")}
+    out = {name: getattr(s, name) for name, _ in tf_stats._fields_ if not name.startswith("reserved")}
+    out["tuned_candidates"] = list(s.tuned_candidates[: s.tuned_n])
+    out["tuned_seconds"] = list(s.tuned_seconds[: s.tuned_n])
+    return out
 
 
 def sweep_batch(problems, phi_in, phi_out, stream=None):

@@ -72,3 +72,22 @@ def test_batched_source_iteration_matches_single_runs():
     order = np.argsort([i["iterations"] for i in infos])
     secs = [infos[k]["seconds"] for k in order]
     assert all(a <= b + 1e-9 for a, b in zip(secs, secs[1:]))
+
+
+def test_autotuned_task_grain():
+    cfg = W.two_material_box(n=6, G=16, n_polar=4, n_az=8, seed=W.BASE_SEED + 77)
+    p = tf.Problem.from_config(cfg, precision=tf.TF_FP32, cells_per_task=-1)
+    st = p.stats()
+    assert st["tuned_n"] >= 2 and not st["tuned_cached"]
+    assert st["cells_per_task"] in st["tuned_candidates"]
+    best = st["tuned_candidates"][int(np.argmin(st["tuned_seconds"]))]
+    assert st["cells_per_task"] == best
+    rng = np.random.default_rng(1)
+    x = rng.uniform(0, 1, (p.n_cells, 16, 4))
+    out = torch.zeros((p.n_cells, 16, 4), dtype=torch.float64, device="cuda")
+    p.sweep(torch.from_numpy(x).cuda(), out)
+    assert _rel(out.cpu().numpy(), oracle.Problem(cfg).transport_step(x, threads=8)) < 2e-5
+    # same class (precision, groups, directions, size): the cached choice is reused
+    q = tf.Problem.from_config(W.two_material_box(n=6, G=16, n_polar=4, n_az=8, seed=W.BASE_SEED + 78),
+                               precision=tf.TF_FP32, cells_per_task=-1)
+    assert q.stats()["tuned_cached"] == 1 and q.stats()["cells_per_task"] == st["cells_per_task"]
