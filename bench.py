@@ -364,7 +364,7 @@ def run_batch(args):
     for c, pb in zip(cfgs, psi):
         share = budget * pb / sum(psi) if sum(psi) > budget else 0.0
         probs.append(tf.Problem.from_config(c, precision=tf.TF_FP32, psi_budget_gb=share / 1e9,
-                                            cells_per_task=-1 if args.autotune else 0))
+                                            cells_per_task=-2 if args.autotune else 0))
     setup = time.perf_counter() - t0
     phis = [torch.zeros((p.n_cells, p.n_groups, 4), dtype=torch.float64, device=dev) for p in probs]
     tf.source_iterate_batch(probs, phis, 0.0, 1)  # warm-up iteration

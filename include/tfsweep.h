@@ -67,8 +67,9 @@ typedef struct {
     int32_t precision;       /* tf_precision: arithmetic of local solves and psi storage (default TF_FP32) */
     int32_t device;          /* CUDA device ordinal (default 0) */
     int32_t cells_per_task;  /* cells of one t-level grouped into one task; 0 = automatic (about 1024 units),
-                              * < 0 = autotuned: timed trial sweeps over a direction sample, cached per
-                              * (precision, groups, directions, log2 cells) */
+                              * -1 = autotuned for use on its own (wall time of trial sweeps over a
+                              * direction sample), -2 = autotuned for batched use (busy time of the
+                              * warps); choices cached per (precision, groups, directions, log2 cells) */
     int32_t dir_chunk;       /* directions swept per persistent launch; 0 = as many as the memory budget allows */
     int32_t warps_per_cta;   /* persistent kernel CTA size in warps; 0 = automatic */
     int32_t ctas_per_sm;     /* persistent CTAs per SM; 0 = as many as are resident */

@@ -1,7 +1,10 @@
 // Task-grain autotuner: picks cells_per_task for a problem by timing trial
 // sweeps of the same mesh, groups and cross sections over a sample of its
 // directions, one candidate grain at a time; the choice is cached per
-// (precision, groups, directions, log2 cells).
+// (precision, criterion, groups, directions, log2 cells).  Criterion: the wall
+// time of the trial sweep (cells_per_task = -1, a problem swept on its own) or
+// the summed busy time of the warps (-2, a problem swept in a batch, where the
+// other problems keep the GPU busy).
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -28,7 +31,7 @@ tf_status autotune_cells_per_task(const Mesh &m, const Quad &q, int32_t G, int32
                                   int32_t *out, tf_autotune_report *rep)
 {
     const int lc = (int)std::lround(std::log2((double)std::max<int64_t>(m.nc, 1)));
-    const auto key = std::make_tuple(opt.precision, G, q.D, lc);
+    const auto key = std::make_tuple(opt.precision * 4 + (opt.cells_per_task == -2 ? 1 : 0), G, q.D, lc);
     {
         std::lock_guard<std::mutex> lk(g_mu);
         auto it = g_cache.find(key);
@@ -81,13 +84,16 @@ tf_status autotune_cells_per_task(const Mesh &m, const Quad &q, int32_t G, int32
         if (s == TF_OK) s = device_create(*p, cell_material, sigma_t, sigma_s, Q, nullptr, nullptr);
         double t = 1e300;
         if (s == TF_OK) {
-            // one warm-up sweep, then the best of two timed sweeps
+            // one warm-up sweep, then the best of two timed sweeps.  For use on its own the
+            // wall time counts; for batched use (other problems supply the parallelism) the
+            // warps' busy time, i.e. the cost of the units when the GPU is saturated.
             s = device_sweep(*p, dphi, dphi, nullptr);
             for (int r = 0; r < 2 && s == TF_OK; ++r) {
                 cudaDeviceSynchronize();
                 const auto t0 = std::chrono::steady_clock::now();
                 s = device_sweep(*p, dphi, dphi, nullptr);
-                t = std::min(t, std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count());
+                const double wall = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+                t = std::min(t, opt.cells_per_task == -2 ? p->stats.busy_seconds : wall);
             }
         }
         if (rep && tried < 8) {
