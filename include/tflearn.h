@@ -1,0 +1,112 @@
+/*
+ * tflearn — learned initial flux for source iteration (part of libtfsweep.so).
+ *
+ * The paper has no counterpart of this part: its source iteration (the inner
+ * and outer iterations of the benchmarks, Sec. 3 and Sec. 5) starts from a
+ * given scalar flux.  These calls train and run a small per-cell network that
+ * proposes that starting flux; tf_source_iterate then runs unchanged from it,
+ * with the same stopping test, so a zero start remains the plain method and
+ * the converged answer does not depend on the network.
+ *
+ * Network: inputs (I) -> H -> H -> outputs (O), tanh on the two hidden layers,
+ * identity output.  Master parameters are FP32, flat, in this order:
+ *   W1 [H][I], b1 [H], W2 [H][H], b2 [H], W3 [O][H], b3 [O]
+ * (layer l computes z = W_l a + b_l).  The forward and backward kernels read
+ * the weights W1, W2, W3 rounded to BF16 (round to nearest even) and
+ * accumulate in FP32; biases stay FP32.  A handle also keeps a target
+ * standardisation (mu, sd): the network output y predicts (t - mu) / sd.
+ *
+ * Per-cell features (tf_mlp_features), I = G^2 + 4 G for G groups, cell c of
+ * material m:
+ *   x[g]                  = log sigma_t[m][g]
+ *   x[G + g' G + g]       = sigma_s[m][g'][g] / sigma_t[m][g']
+ *   x[G + G^2 + g]        = qbar[c][g], the mean of the 4 nodal Q[c][g][i]
+ *   x[2G + G^2 + g]       = mean of log sigma_t[g] over the face neighbours
+ *   x[3G + G^2 + g]       = mean of qbar[g] over the face neighbours
+ * (a cell with no neighbour takes its own values in the last two blocks).
+ * Targets (tf_mlp_targets): t[c][g] = log(max(mean_i phi[c][g][i], 0) + 1e-6),
+ * the log of the cell-average scalar flux; tf_mlp_predict_phi inverts that map.
+ *
+ * Loss over n samples: L = (1 / (n O)) sum_s sum_o (y_so - (t_so - mu)/sd)^2.
+ * Optimiser: Adam with b1 = 0.9, b2 = 0.999, eps = 1e-8 and bias correction,
+ * on the FP32 master parameters; the BF16 copy is refreshed after each step.
+ *
+ * Conventions: X, T, Y, phi and the feature inputs are device pointers
+ * (cudaMalloc or torch CUDA tensors), row-major as stated; host pointers are
+ * marked "host".  `stream` is a cudaStream_t (NULL = legacy default stream).
+ * Every call returns a tf_status; the handle is destroyed with tf_destroy.
+ */
+#ifndef TFLEARN_H
+#define TFLEARN_H
+
+#include <stdint.h>
+
+#include "tfsweep.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* New network on the current CUDA device.  n_hidden in {8, 16, 32, 64},
+ * 1 <= n_out <= 64, n_in >= 1.  Weights Glorot-uniform from a Mersenne twister
+ * seeded with `seed`, biases zero, (mu, sd) = (0, 1).  TF_ERR_ARG on bad sizes,
+ * TF_ERR_NOMEM / TF_ERR_CUDA on device failures. */
+tf_status tf_mlp_create(int32_t n_in, int32_t n_hidden, int32_t n_out, uint64_t seed, tf_handle *out);
+
+/* Copies the FP32 master parameters out to `get` (host, n_params floats) and/or
+ * replaces them from `set` (host; also resets the Adam moments and step count).
+ * Either may be NULL; *n_params (if non-NULL) receives the count. */
+tf_status tf_mlp_params(tf_handle net, float *get, const float *set, int64_t *n_params);
+
+/* Reads (mu_get, sd_get, host) and/or sets (mu_set, sd_set, host; sd > 0) the
+ * target standardisation.  Any pointer may be NULL. */
+tf_status tf_mlp_scale(tf_handle net, float *mu_get, float *sd_get, const float *mu_set, const float *sd_set);
+
+/* Sets (mu, sd) to the mean and the population standard deviation of the
+ * n_values targets T (FP64 sums).  Synchronises `stream`. */
+tf_status tf_mlp_fit_scale(tf_handle net, const float *T, int64_t n_values, void *stream);
+
+/* Features of every cell into X [n_cells][G^2 + 4G] (FP32).  Inputs (device):
+ * cell_material [n_cells], sigma_t [M][G], sigma_s [M][G][G] (element
+ * [m][g_from][g_to]), Q [n_cells][G][4], nbr [n_cells][4] (neighbour across the
+ * face opposite local vertex f, -1 on the boundary; tf_mesh_geometry gives it).
+ * Asynchronous on `stream`. */
+tf_status tf_mlp_features(int64_t n_cells, int32_t n_groups, const int32_t *cell_material, const double *sigma_t,
+                          const double *sigma_s, const double *Q, const int32_t *nbr, float *X, void *stream);
+
+/* Targets T [n_cells][G] from a scalar flux phi [n_cells][G][4] (FP64).  Asynchronous. */
+tf_status tf_mlp_targets(int64_t n_cells, int32_t n_groups, const double *phi, float *T, void *stream);
+
+/* Network outputs Y [n][O] for inputs X [n][I].  Asynchronous on `stream`. */
+tf_status tf_mlp_forward(tf_handle net, const float *X, int64_t n, float *Y, void *stream);
+
+/* Loss and gradient of L over the n samples (X [n][I], T [n][O]) at the current
+ * parameters; the gradient (parameter order above) is kept for tf_mlp_adam_step
+ * and copied to `grad` (host, n_params floats) and the loss to `loss` (host)
+ * when those are non-NULL.  Synchronises `stream`. */
+tf_status tf_mlp_gradients(tf_handle net, const float *X, const float *T, int64_t n, float *grad, float *loss,
+                           void *stream);
+
+/* One Adam step with learning rate lr > 0 from the last computed gradient.
+ * Synchronises `stream`. */
+tf_status tf_mlp_adam_step(tf_handle net, float lr, void *stream);
+
+/* Minibatch training: `epochs` passes over the n samples, each pass over a
+ * fresh shuffle (Mersenne twister seeded with `seed`) cut into consecutive
+ * minibatches of `batch` samples (the last may be shorter), one Adam step per
+ * minibatch.  loss_history (host, `epochs` floats, may be NULL) receives each
+ * epoch's mean loss over its minibatches' samples.  Allocates its own
+ * minibatch scratch; synchronises `stream`. */
+tf_status tf_mlp_train(tf_handle net, const float *X, const float *T, int64_t n, int32_t epochs, int32_t batch,
+                       float lr, uint64_t seed, float *loss_history, void *stream);
+
+/* Initial flux for source iteration: phi [n_cells][O][4] (FP64, O = groups) set
+ * at every node to max(exp(mu + sd y) - 1e-6, 0), y the network output for the
+ * cell's features X [n_cells][I].  Synchronises `stream`. */
+tf_status tf_mlp_predict_phi(tf_handle net, const float *X, int64_t n_cells, double *phi, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif

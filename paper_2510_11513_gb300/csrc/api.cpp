@@ -239,7 +239,7 @@ tf_status tf_destroy(tf_handle h)
 {
     auto *o = reinterpret_cast<Object *>(h);
     if (!o) return TF_OK;
-    if (o->kind != Kind::Mesh && o->kind != Kind::Quad && o->kind != Kind::Problem)
+    if (o->kind != Kind::Mesh && o->kind != Kind::Quad && o->kind != Kind::Problem && o->kind != Kind::Mlp)
         return fail(TF_ERR_ARG, "tf_destroy: not a tfsweep handle");
     release(o);
     return TF_OK;

@@ -16,7 +16,7 @@ void set_error(const std::string &msg);
 tf_status fail(tf_status s, const std::string &msg);
 
 // ------------------------------------------------------------------ objects
-enum class Kind : int32_t { Mesh = 1, Quad = 2, Problem = 3 };
+enum class Kind : int32_t { Mesh = 1, Quad = 2, Problem = 3, Mlp = 4 };
 
 struct Object {
     explicit Object(Kind k) : kind(k) {}

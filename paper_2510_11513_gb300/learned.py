@@ -1,0 +1,105 @@
+"""Learned initial flux for source iteration (include/tflearn.h).
+
+The paper's source iteration starts from a given scalar flux; a per-cell
+network trained on converged fluxes proposes that start, and the iteration
+then runs unchanged with the same stopping test, so a zero start remains the
+plain method and the answer does not depend on the network.
+
+This module only moves arrays and orders calls: features, targets, training,
+prediction and the solves all run in libtfsweep.so's kernels.  Device arrays
+are torch CUDA tensors.
+"""
+from __future__ import annotations
+
+import time
+
+import numpy as np
+import torch
+
+from . import tfsweep as tf
+
+
+def n_features(n_groups: int) -> int:
+    """Inputs per cell: log sigma_t (G), scattering probabilities (G^2), cell-average
+    source (G) and the face-neighbour means of log sigma_t and of the source (2G)."""
+    return n_groups * n_groups + 4 * n_groups
+
+
+def cell_features(mesh: tf.Mesh, cfg: dict, device="cuda", stream=None) -> torch.Tensor:
+    """Features [n_cells][G^2 + 4G] (FP32, device) of a problem given by its mesh
+    and its material / source arrays (cfg keys cell_material, sigma_t, sigma_s, Q)."""
+    G = int(cfg["n_groups"])
+    C = mesh.n_cells
+    nbr = torch.from_numpy(np.ascontiguousarray(mesh.geometry()["nbr"], dtype=np.int32)).to(device)
+    mat = torch.from_numpy(np.ascontiguousarray(cfg["cell_material"], dtype=np.int32)).to(device)
+    st = torch.from_numpy(np.ascontiguousarray(cfg["sigma_t"], dtype=np.float64)).to(device)
+    ss = torch.from_numpy(np.ascontiguousarray(cfg["sigma_s"], dtype=np.float64)).to(device)
+    Q = torch.from_numpy(np.ascontiguousarray(cfg["Q"], dtype=np.float64)).to(device)
+    X = torch.empty((C, n_features(G)), dtype=torch.float32, device=device)
+    tf.tf_mlp_features(C, G, mat, st, ss, Q, nbr, X, stream)
+    return X
+
+
+def flux_targets(phi: torch.Tensor, n_groups: int, stream=None) -> torch.Tensor:
+    """Targets [n_cells][G] (FP32): log(max(cell-average phi, 0) + 1e-6)."""
+    C = phi.shape[0]
+    T = torch.empty((C, n_groups), dtype=torch.float32, device=phi.device)
+    tf.tf_mlp_targets(C, n_groups, phi, T, stream)
+    return T
+
+
+def generate(cfgs, tol=1e-6, max_iters=5000, device="cuda", **solver_opts):
+    """Training data from the plain solver: for each problem configuration, its
+    features and the targets of its converged zero-start solution.  Returns
+    (X [sum C][I], T [sum C][G], per-problem info dicts with iterations and seconds)."""
+    Xs, Ts, infos = [], [], []
+    for cfg in cfgs:
+        t0 = time.perf_counter()
+        prob = tf.Problem.from_config(cfg, **solver_opts)
+        t_setup = time.perf_counter() - t0
+        X = cell_features(prob.mesh, cfg, device)
+        phi = torch.zeros((prob.n_cells, prob.n_groups, 4), dtype=torch.float64, device=device)
+        t0 = time.perf_counter()
+        r = prob.source_iterate(phi, tol, max_iters)
+        torch.cuda.synchronize()
+        r["solve_seconds"] = time.perf_counter() - t0
+        r["setup_seconds"] = t_setup
+        r["name"] = cfg.get("name", "")
+        Xs.append(X)
+        Ts.append(flux_targets(phi, prob.n_groups))
+        infos.append(r)
+        prob.close()
+    return torch.cat(Xs), torch.cat(Ts), infos
+
+
+class LearnedStart:
+    """A network mapping cell features to the initial scalar flux."""
+
+    def __init__(self, n_groups: int, hidden: int = 64, seed: int = 0):
+        self.n_groups = int(n_groups)
+        self.net = tf.Mlp(n_features(self.n_groups), hidden, self.n_groups, seed)
+
+    def fit(self, X: torch.Tensor, T: torch.Tensor, epochs: int = 20, batch: int = 1024, lr: float = 1e-3,
+            seed: int = 0, stream=None) -> np.ndarray:
+        """Standardises the targets (mean / standard deviation over T) and trains
+        with Adam; returns the per-epoch mean loss."""
+        if X.shape[0] != T.shape[0] or T.shape[1] != self.n_groups:
+            raise ValueError("X and T disagree in samples or groups")
+        tf.tf_mlp_fit_scale(self.net.h, T, T.numel(), stream)
+        return tf.tf_mlp_train(self.net.h, X, T, X.shape[0], epochs, batch, lr, seed, stream)
+
+    def initial_flux(self, X: torch.Tensor, stream=None) -> torch.Tensor:
+        """phi0 [n_cells][G][4] (FP64, device) for the cells whose features are X."""
+        phi = torch.empty((X.shape[0], self.n_groups, 4), dtype=torch.float64, device=X.device)
+        tf.tf_mlp_predict_phi(self.net.h, X, X.shape[0], phi, stream)
+        return phi
+
+    def solve(self, problem: tf.Problem, X: torch.Tensor, tol: float, max_iters: int, stream=None):
+        """Source iteration of `problem` from the learned start; returns (phi, info),
+        info with the network's time as predict_seconds."""
+        t0 = time.perf_counter()
+        phi = self.initial_flux(X, stream)
+        t_pred = time.perf_counter() - t0
+        r = problem.source_iterate(phi, tol, max_iters, stream)
+        r["predict_seconds"] = t_pred
+        return phi, r

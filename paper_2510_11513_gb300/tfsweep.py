@@ -27,6 +27,9 @@ SYMBOLS = (
     "tf_options_default", "tf_mesh_create", "tf_quadrature_create", "tf_problem_create", "tf_sweep",
     "tf_source_iterate", "tf_destroy", "tf_mesh_geometry", "tf_quadrature_get", "tf_graph_levels",
     "tf_problem_psi", "tf_problem_stats", "tf_status_string", "tf_last_error", "tf_integrated_flux_noalloc",
+    # include/tflearn.h
+    "tf_mlp_create", "tf_mlp_params", "tf_mlp_scale", "tf_mlp_fit_scale", "tf_mlp_features", "tf_mlp_targets",
+    "tf_mlp_forward", "tf_mlp_gradients", "tf_mlp_adam_step", "tf_mlp_train", "tf_mlp_predict_phi",
 )
 
 
@@ -104,6 +107,18 @@ def load(build_if_missing: bool = True):
     lib.tf_problem_psi.argtypes = [H, i32, vp, vp]
     lib.tf_problem_stats.argtypes = [H, C.POINTER(tf_stats)]
     lib.tf_integrated_flux_noalloc.argtypes = [vp, vp, i64, i32, vp, vp]
+    f32, u64, fp = C.c_float, C.c_uint64, C.POINTER(C.c_float)
+    lib.tf_mlp_create.argtypes = [i32, i32, i32, u64, C.POINTER(H)]
+    lib.tf_mlp_params.argtypes = [H, vp, vp, C.POINTER(i64)]
+    lib.tf_mlp_scale.argtypes = [H, fp, fp, fp, fp]
+    lib.tf_mlp_fit_scale.argtypes = [H, vp, i64, vp]
+    lib.tf_mlp_features.argtypes = [i64, i32, vp, vp, vp, vp, vp, vp, vp]
+    lib.tf_mlp_targets.argtypes = [i64, i32, vp, vp, vp]
+    lib.tf_mlp_forward.argtypes = [H, vp, i64, vp, vp]
+    lib.tf_mlp_gradients.argtypes = [H, vp, vp, i64, vp, fp, vp]
+    lib.tf_mlp_adam_step.argtypes = [H, f32, vp]
+    lib.tf_mlp_train.argtypes = [H, vp, vp, i64, i32, i32, f32, u64, vp, vp]
+    lib.tf_mlp_predict_phi.argtypes = [H, vp, i64, vp, vp]
     lib.tf_status_string.argtypes = [i32]
     lib.tf_status_string.restype = C.c_char_p
     lib.tf_last_error.argtypes = []
@@ -294,6 +309,69 @@ def source_iterate_batch(problems, phis, tol, max_iters, stream=None, history=Fa
     return st, res
 
 
+# ------------------------------------------------------- learned start calls
+def tf_mlp_create(n_in, n_hidden, n_out, seed=0):
+    h = C.c_void_p()
+    _check(load().tf_mlp_create(int(n_in), int(n_hidden), int(n_out), int(seed), C.byref(h)), "tf_mlp_create")
+    return h
+
+
+def tf_mlp_params(net, get=None, set=None):
+    n = C.c_int64()
+    _check(load().tf_mlp_params(net, _ptr(get), _ptr(set), C.byref(n)), "tf_mlp_params")
+    return n.value
+
+
+def tf_mlp_scale(net, mu=None, sd=None):
+    mu_g, sd_g = C.c_float(), C.c_float()
+    mu_s = None if mu is None else C.byref(C.c_float(mu))
+    sd_s = None if sd is None else C.byref(C.c_float(sd))
+    _check(load().tf_mlp_scale(net, C.byref(mu_g), C.byref(sd_g), mu_s, sd_s), "tf_mlp_scale")
+    return mu_g.value, sd_g.value
+
+
+def tf_mlp_fit_scale(net, T, n_values, stream=None):
+    return _check(load().tf_mlp_fit_scale(net, _ptr(T), int(n_values), _stream_handle(stream)), "tf_mlp_fit_scale")
+
+
+def tf_mlp_features(n_cells, n_groups, cell_material, sigma_t, sigma_s, Q, nbr, X, stream=None):
+    return _check(load().tf_mlp_features(int(n_cells), int(n_groups), _ptr(cell_material), _ptr(sigma_t),
+                                         _ptr(sigma_s), _ptr(Q), _ptr(nbr), _ptr(X), _stream_handle(stream)),
+                  "tf_mlp_features")
+
+
+def tf_mlp_targets(n_cells, n_groups, phi, T, stream=None):
+    return _check(load().tf_mlp_targets(int(n_cells), int(n_groups), _ptr(phi), _ptr(T), _stream_handle(stream)),
+                  "tf_mlp_targets")
+
+
+def tf_mlp_forward(net, X, n, Y, stream=None):
+    return _check(load().tf_mlp_forward(net, _ptr(X), int(n), _ptr(Y), _stream_handle(stream)), "tf_mlp_forward")
+
+
+def tf_mlp_gradients(net, X, T, n, grad=None, stream=None):
+    loss = C.c_float()
+    _check(load().tf_mlp_gradients(net, _ptr(X), _ptr(T), int(n), _ptr(grad), C.byref(loss), _stream_handle(stream)),
+           "tf_mlp_gradients")
+    return loss.value
+
+
+def tf_mlp_adam_step(net, lr, stream=None):
+    return _check(load().tf_mlp_adam_step(net, float(lr), _stream_handle(stream)), "tf_mlp_adam_step")
+
+
+def tf_mlp_train(net, X, T, n, epochs, batch, lr, seed=0, stream=None):
+    hist = np.zeros(int(epochs), np.float32)
+    _check(load().tf_mlp_train(net, _ptr(X), _ptr(T), int(n), int(epochs), int(batch), float(lr), int(seed),
+                               _ptr(hist), _stream_handle(stream)), "tf_mlp_train")
+    return hist
+
+
+def tf_mlp_predict_phi(net, X, n_cells, phi, stream=None):
+    return _check(load().tf_mlp_predict_phi(net, _ptr(X), int(n_cells), _ptr(phi), _stream_handle(stream)),
+                  "tf_mlp_predict_phi")
+
+
 # ------------------------------------------------------------- handle owners
 class _Handle:
     h = None
@@ -308,6 +386,24 @@ class _Handle:
             self.close()
         except Exception:
             pass
+
+
+class Mlp(_Handle):
+    """A per-cell network on the device (include/tflearn.h)."""
+
+    def __init__(self, n_in, n_hidden, n_out, seed=0):
+        self.h = tf_mlp_create(n_in, n_hidden, n_out, seed)
+        self.n_in, self.n_hidden, self.n_out = int(n_in), int(n_hidden), int(n_out)
+        self.n_params = tf_mlp_params(self.h)
+
+    def params(self, set=None):
+        """The FP32 master parameters (host); replaces them first when `set` is given."""
+        out = np.zeros(self.n_params, np.float32)
+        tf_mlp_params(self.h, get=out, set=None if set is None else np.ascontiguousarray(set, dtype=np.float32))
+        return out
+
+    def scale(self, mu=None, sd=None):
+        return tf_mlp_scale(self.h, mu, sd)
 
 
 class Mesh(_Handle):

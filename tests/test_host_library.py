@@ -15,10 +15,15 @@ from paper_2510_11513_gb300 import build as tfbuild
 def test_library_exports_every_declared_symbol():
     import ctypes
     import os
-    header = open(os.path.join(os.path.dirname(tfbuild.HERE), "include", "tfsweep.h")).read()
-    declared = set(re.findall(r"^\s*(?:tf_status|void|const char \*)\s*(tf_\w+)\s*\(", header, re.M))
+    inc = os.path.join(os.path.dirname(tfbuild.HERE), "include")
+    headers = sorted(f for f in os.listdir(inc) if f.endswith(".h"))
+    assert {"tfsweep.h", "tflearn.h"} <= set(headers)
+    declared = set()
+    for h in headers:
+        text = open(os.path.join(inc, h)).read()
+        declared |= set(re.findall(r"^\s*(?:tf_status|void|const char \*)\s*(tf_\w+)\s*\(", text, re.M))
     assert {"tf_mesh_create", "tf_quadrature_create", "tf_problem_create", "tf_sweep", "tf_source_iterate",
-            "tf_destroy"} <= declared
+            "tf_destroy", "tf_mlp_create", "tf_mlp_train", "tf_mlp_predict_phi"} <= declared
     lib = ctypes.CDLL(tf.load().__dict__["_name"])
     for name in sorted(declared):
         assert hasattr(lib, name), name
