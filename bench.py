@@ -409,16 +409,17 @@ def run_learned(args):
     tol = args.batch_tol
     t0 = time.perf_counter()
     train = [W.random_layout(layout=k, **kw) for k in range(args.train_layouts)]
-    X, T, gen = L.generate(train, tol=tol, max_iters=5000, device=dev, precision=tf.TF_FP32)
+    floor = args.weight_floor if args.weight_floor >= 0 else None
+    X, T, Wt, gen = L.generate(train, tol=tol, max_iters=5000, device=dev, weight_floor=floor, precision=tf.TF_FP32)
     t_gen = time.perf_counter() - t0
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
     ls = L.LearnedStart(kw["G"], hidden=64, seed=args.seed)
-    hist = ls.fit(X, T, epochs=args.epochs, batch=args.train_batch, lr=args.lr, seed=args.seed)
+    hist = ls.fit(X, T, Wt, epochs=args.epochs, batch=args.train_batch, lr=args.lr, seed=args.seed)
     torch.cuda.synchronize(dev)
     t_train = time.perf_counter() - t0
     samples = X.shape[0]
-    del X, T
+    del X, T, Wt
     rows = []
     for k in range(args.eval_layouts):
         cfg = W.random_layout(layout=10000 + k, **kw)
@@ -458,7 +459,8 @@ def run_learned(args):
             "data": "synthetic",
             "config": {"workload": f"learned_start_layouts_{kw['n']}^3_D{kw['n_polar'] * kw['n_az']}_G{kw['G']}",
                        "train_layouts": args.train_layouts, "eval_layouts": args.eval_layouts, "samples": samples,
-                       "epochs": args.epochs, "batch": args.train_batch, "lr": args.lr, "tol": tol},
+                       "epochs": args.epochs, "batch": args.train_batch, "lr": args.lr, "tol": tol,
+                       "weight_floor": floor},
             "zero_start_s": sz / len(rows), "iterations_zero": iz, "iterations_learned": il,
             "iteration_ratio": il / max(iz, 1), "generate_s": round(t_gen, 1),
             "generate_solve_s": round(sum(g["solve_seconds"] for g in gen), 2),
@@ -499,6 +501,8 @@ def main():
     ap.add_argument("--train-batch", type=int, default=1024)
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--weight-floor", type=float, default=1e-3,
+                    help="--config layout: loss weights (phi/max)^2 + floor; negative = unweighted")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)  # at least 3 untimed warm-up steps
     if args.impl == "reference":

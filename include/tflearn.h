@@ -27,7 +27,11 @@
  * Targets (tf_mlp_targets): t[c][g] = log(max(mean_i phi[c][g][i], 0) + 1e-6),
  * the log of the cell-average scalar flux; tf_mlp_predict_phi inverts that map.
  *
- * Loss over n samples: L = (1 / (n O)) sum_s sum_o (y_so - (t_so - mu)/sd)^2.
+ * Loss over n samples: L = (1 / (n O)) sum_s sum_o w_so (y_so - (t_so - mu)/sd)^2,
+ * with per-target weights w (all 1 when no weight array is given).  The
+ * weights of tf_mlp_weights, w = (phi / max phi)^2 + floor per group, make a
+ * log-space error count as the absolute flux error it causes relative to the
+ * group's largest flux, the scale of the source-iteration stopping test.
  * Optimiser: Adam with b1 = 0.9, b2 = 0.999, eps = 1e-8 and bias correction,
  * on the FP32 master parameters; the BF16 copy is refreshed after each step.
  *
@@ -77,28 +81,34 @@ tf_status tf_mlp_features(int64_t n_cells, int32_t n_groups, const int32_t *cell
 /* Targets T [n_cells][G] from a scalar flux phi [n_cells][G][4] (FP64).  Asynchronous. */
 tf_status tf_mlp_targets(int64_t n_cells, int32_t n_groups, const double *phi, float *T, void *stream);
 
+/* Weights W [n_cells][G] for the loss: w[c][g] = (pbar[c][g] / max_c pbar[c][g])^2 + floor,
+ * pbar = max(mean_i phi[c][g][i], 0) (floor alone where a group's maximum is 0);
+ * floor >= 0.  Allocates G words of scratch; synchronises `stream`. */
+tf_status tf_mlp_weights(int64_t n_cells, int32_t n_groups, const double *phi, float floor_w, float *W, void *stream);
+
 /* Network outputs Y [n][O] for inputs X [n][I].  Asynchronous on `stream`. */
 tf_status tf_mlp_forward(tf_handle net, const float *X, int64_t n, float *Y, void *stream);
 
-/* Loss and gradient of L over the n samples (X [n][I], T [n][O]) at the current
- * parameters; the gradient (parameter order above) is kept for tf_mlp_adam_step
+/* Loss and gradient of L over the n samples (X [n][I], T [n][O], weights W [n][O]
+ * or NULL) at the current parameters; the gradient (parameter order above) is kept for tf_mlp_adam_step
  * and copied to `grad` (host, n_params floats) and the loss to `loss` (host)
  * when those are non-NULL.  Synchronises `stream`. */
-tf_status tf_mlp_gradients(tf_handle net, const float *X, const float *T, int64_t n, float *grad, float *loss,
-                           void *stream);
+tf_status tf_mlp_gradients(tf_handle net, const float *X, const float *T, const float *W, int64_t n, float *grad,
+                           float *loss, void *stream);
 
 /* One Adam step with learning rate lr > 0 from the last computed gradient.
  * Synchronises `stream`. */
 tf_status tf_mlp_adam_step(tf_handle net, float lr, void *stream);
 
-/* Minibatch training: `epochs` passes over the n samples, each pass over a
+/* Minibatch training: `epochs` passes over the n samples (X, T and the optional
+ * weights W as for tf_mlp_gradients), each pass over a
  * fresh shuffle (Mersenne twister seeded with `seed`) cut into consecutive
  * minibatches of `batch` samples (the last may be shorter), one Adam step per
  * minibatch.  loss_history (host, `epochs` floats, may be NULL) receives each
  * epoch's mean loss over its minibatches' samples.  Allocates its own
  * minibatch scratch; synchronises `stream`. */
-tf_status tf_mlp_train(tf_handle net, const float *X, const float *T, int64_t n, int32_t epochs, int32_t batch,
-                       float lr, uint64_t seed, float *loss_history, void *stream);
+tf_status tf_mlp_train(tf_handle net, const float *X, const float *T, const float *W, int64_t n, int32_t epochs,
+                       int32_t batch, float lr, uint64_t seed, float *loss_history, void *stream);
 
 /* Initial flux for source iteration: phi [n_cells][O][4] (FP64, O = groups) set
  * at every node to max(exp(mu + sd y) - 1e-6, 0), y the network output for the

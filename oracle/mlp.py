@@ -12,9 +12,10 @@ computes, so that the kernels can be checked against it:
              probabilities, cell-average source and the averages of log sigma_t
              and of the source over the face neighbours);
   targets    log(max(cell-average phi, 0) + 1e-6);
+  weights    (cell-average phi / its group maximum)^2 + floor, per target;
   forward    tanh MLP, inputs -> H -> H -> outputs, z = W a + b per layer;
-  gradient   backpropagation of the mean squared error of the standardised
-             targets;
+  gradient   backpropagation of the (optionally weighted) mean squared error
+             of the standardised targets;
   adam       Adam with bias correction (b1 = 0.9, b2 = 0.999, eps = 1e-8);
   predict    the inverse of the target map, copied to the 4 nodes.
 
@@ -106,6 +107,15 @@ def targets(phi):
     return np.log(np.maximum(cell_average(phi), 0.0) + EPS_T)
 
 
+def weights(phi, floor):
+    """w[c][g] = (pbar[c][g] / max_c pbar[c][g])^2 + floor with pbar the clamped
+    cell average; floor alone in a group whose maximum is 0."""
+    pbar = np.maximum(cell_average(phi), 0.0)
+    m = pbar.max(axis=0)
+    r = np.divide(pbar, m, out=np.zeros_like(pbar), where=m > 0)
+    return r * r + floor
+
+
 def predict_phi(y, mu, sd):
     """Inverse of the standardised target map at every node: [C][G][4]."""
     v = np.maximum(np.exp(mu + sd * np.asarray(y, dtype=np.float64)) - EPS_T, 0.0)
@@ -137,23 +147,25 @@ def forward(p, X, I, H, O, bf16=False):
     return y, (a1, a2)
 
 
-def loss(p, X, T, I, H, O, mu=0.0, sd=1.0, bf16=False):
+def loss(p, X, T, I, H, O, mu=0.0, sd=1.0, bf16=False, W=None):
     y, _ = forward(p, X, I, H, O, bf16)
     r = y - (np.asarray(T, dtype=np.float64) - mu) / sd
-    return float(np.mean(r * r))
+    w = 1.0 if W is None else np.asarray(W, dtype=np.float64)
+    return float(np.mean(w * r * r))
 
 
-def gradient(p, X, T, I, H, O, mu=0.0, sd=1.0, bf16=False):
+def gradient(p, X, T, I, H, O, mu=0.0, sd=1.0, bf16=False, W=None):
     """Loss and its gradient (flat, parameter order) by backpropagation:
-    dL/dy = 2 r / (n O); through z3 = W3 a2 + b3, a2 = tanh(z2), z2 = W2 a1 + b2,
+    dL/dy = 2 w r / (n O) (w = 1 without weights); through z3 = W3 a2 + b3, a2 = tanh(z2), z2 = W2 a1 + b2,
     a1 = tanh(z1), z1 = W1 x + b1, with tanh' = 1 - tanh^2."""
     W1, b1, W2, b2, W3, b3 = _weights(p, I, H, O, bf16)
     X = np.asarray(X, dtype=np.float64)
     n = X.shape[0]
     y, (a1, a2) = forward(p, X, I, H, O, bf16)
     r = y - (np.asarray(T, dtype=np.float64) - mu) / sd
-    L = float(np.mean(r * r))
-    dy = 2.0 * r / (n * O)                 # dL/dz3   [n][O]
+    w = 1.0 if W is None else np.asarray(W, dtype=np.float64)
+    L = float(np.mean(w * r * r))
+    dy = 2.0 * w * r / (n * O)             # dL/dz3   [n][O]
     gW3 = dy.T @ a2
     gb3 = dy.sum(axis=0)
     d2 = (dy @ W3) * (1.0 - a2 * a2)       # dL/dz2   [n][H]
@@ -175,13 +187,15 @@ def adam(p, m, v, g, t, lr, b1=0.9, b2=0.999, eps=1e-8):
 
 
 def train_steps(p, batches, I, H, O, lr, mu=0.0, sd=1.0, bf16=False):
-    """Adam over the given list of (X, T) minibatches in order; returns the
-    parameters and the loss of each minibatch before its step."""
+    """Adam over the given list of (X, T) or (X, T, W) minibatches in order;
+    returns the parameters and the loss of each minibatch before its step."""
     m = np.zeros_like(p)
     v = np.zeros_like(p)
     losses = []
-    for t, (X, T) in enumerate(batches, start=1):
-        L, g = gradient(p, X, T, I, H, O, mu, sd, bf16)
+    for t, b in enumerate(batches, start=1):
+        X, T = b[0], b[1]
+        W = b[2] if len(b) > 2 else None
+        L, g = gradient(p, X, T, I, H, O, mu, sd, bf16, W)
         losses.append(L)
         p, m, v = adam(p, m, v, g, t, lr)
     return p, losses

@@ -9,8 +9,9 @@
 // Master parameters, flat FP32: W1 [H][I], b1 [H], W2 [H][H], b2 [H],
 // W3 [O][H], b3 [O].  The BF16 copy used by the kernels holds W1^T [I][H],
 // W2^T [H][H] and W3 [O][H] (the orders the per-sample loops read).
-// Loss over n samples: (1/(n O)) sum_s sum_o (y_so - (t_so - mu)/sd)^2, with
-// (mu, sd) the target standardisation kept in the handle.
+// Loss over n samples: (1/(n O)) sum_s sum_o w_so (y_so - (t_so - mu)/sd)^2, with
+// (mu, sd) the target standardisation kept in the handle and w optional
+// per-target weights (1 without them).
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -144,6 +145,31 @@ __global__ void targets_kernel(int64_t CG, const double *__restrict__ phi, float
     }
 }
 
+// Per-group maximum of the clamped cell-average flux (FP64 bit patterns of non-negative
+// values order like the values, so an unsigned atomicMax finds the maximum).
+__global__ void group_max_kernel(int64_t C, int G, const double *__restrict__ phi, unsigned long long *__restrict__ gmax)
+{
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < C * G; e += (int64_t)gridDim.x * blockDim.x) {
+        const double *f = phi + (size_t)e * 4;
+        const double avg = fmax(0.25 * (((f[0] + f[1]) + f[2]) + f[3]), 0.0);
+        atomicMax(gmax + (e % G), (unsigned long long)__double_as_longlong(avg));
+    }
+}
+
+// w[c][g] = (phi_cg / max_c phi_cg)^2 + floor, phi the clamped cell average (floor alone
+// where the group's maximum is 0).
+__global__ void weights_kernel(int64_t C, int G, const double *__restrict__ phi,
+                               const unsigned long long *__restrict__ gmax, float floor_w, float *__restrict__ W)
+{
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < C * G; e += (int64_t)gridDim.x * blockDim.x) {
+        const double *f = phi + (size_t)e * 4;
+        const double avg = fmax(0.25 * (((f[0] + f[1]) + f[2]) + f[3]), 0.0);
+        const double m = __longlong_as_double((long long)gmax[e % G]);
+        const double r = m > 0.0 ? avg / m : 0.0;
+        W[e] = (float)(r * r + (double)floor_w);
+    }
+}
+
 // sum of (t - shift)^2 (square = 1) or of t - shift (square = 0) over n values into acc (FP64)
 __global__ void moment_kernel(int64_t n, const float *__restrict__ T, double shift, int square, double *__restrict__ acc)
 {
@@ -244,13 +270,14 @@ __global__ void __launch_bounds__(128) forward_kernel(int64_t n, int I, int O, c
 }
 
 // ---------------------------------------------------------------- backward
-// Per sample: dy_o = 2 (y_o - (t_o - mu)/sd) / (n O);  d2 = (W3^T dy) (1 - a2^2);
-// d1 = (W2^T d2) (1 - a1^2), with the BF16 weights of the forward pass.
-// loss[0] += minibatch loss; loss[1] += squared error / (n_epoch O) when n_epoch > 0.
+// Per sample: dy_o = 2 w_o (y_o - (t_o - mu)/sd) / (n O) (w = 1 without weights);
+// d2 = (W3^T dy) (1 - a2^2); d1 = (W2^T d2) (1 - a1^2), with the BF16 weights of the forward pass.
+// loss[0] += minibatch loss; loss[1] += weighted squared error / (n_epoch O) when n_epoch > 0.
 template <int H>
 __global__ void __launch_bounds__(128) backward_kernel(int64_t n, int I, int O, const __nv_bfloat16 *__restrict__ wb,
                                                        const float *__restrict__ Y, const float *__restrict__ T,
-                                                       float mu, float inv_sd, const float *__restrict__ A1,
+                                                       const float *__restrict__ Wt, float mu, float inv_sd,
+                                                       const float *__restrict__ A1,
                                                        const float *__restrict__ A2, float *__restrict__ DY,
                                                        float *__restrict__ D1, float *__restrict__ D2,
                                                        float *__restrict__ loss, int64_t n_epoch)
@@ -270,8 +297,9 @@ __global__ void __launch_bounds__(128) backward_kernel(int64_t n, int I, int O, 
         for (int k = 0; k < H; ++k) d2[k] = 0.f;
         for (int o = 0; o < O; ++o) {
             const float r = Y[(size_t)s * O + o] - (T[(size_t)s * O + o] - mu) * inv_sd;
-            lsum = fmaf(r, r, lsum);
-            const float dy = scale * r;
+            const float w = Wt ? Wt[(size_t)s * O + o] : 1.f;
+            lsum = fmaf(w * r, r, lsum);
+            const float dy = scale * w * r;
             DY[(size_t)s * O + o] = dy;
             const float4 *wr = reinterpret_cast<const float4 *>(w3 + o * H);
 #pragma unroll
@@ -419,9 +447,10 @@ __global__ void pack_bf16_kernel(int I, int H, int O, const float *__restrict__ 
     }
 }
 
-// Xb[i] = X[perm[i]], Tb[i] = T[perm[i]] for i < nn.
+// Xb[i] = X[perm[i]], Tb[i] = T[perm[i]] (and Wb[i] = Wt[perm[i]] with weights) for i < nn.
 __global__ void gather_kernel(int64_t nn, int I, int O, const int64_t *__restrict__ perm, const float *__restrict__ X,
-                              const float *__restrict__ T, float *__restrict__ Xb, float *__restrict__ Tb)
+                              const float *__restrict__ T, const float *__restrict__ Wt, float *__restrict__ Xb,
+                              float *__restrict__ Tb, float *__restrict__ Wb)
 {
     const int64_t tot = nn * (I + O);
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
@@ -431,6 +460,7 @@ __global__ void gather_kernel(int64_t nn, int I, int O, const int64_t *__restric
         } else {
             const int64_t f = e - nn * I, i = f / O, k = f - i * O;
             Tb[f] = T[(size_t)perm[i] * O + k];
+            if (Wt) Wb[f] = Wt[(size_t)perm[i] * O + k];
         }
     }
 }
@@ -475,14 +505,15 @@ void launch_forward(const Mlp &m, int64_t n, const float *X, float *Y, float *A1
     }
 }
 
-void launch_backward(const Mlp &m, int64_t n, const float *Y, const float *T, const float *A1, const float *A2,
-                     float *DY, float *D1, float *D2, int64_t n_epoch, cudaStream_t st)
+void launch_backward(const Mlp &m, int64_t n, const float *Y, const float *T, const float *Wt, const float *A1,
+                     const float *A2, float *DY, float *D1, float *D2, int64_t n_epoch, cudaStream_t st)
 {
     const int blocks = (int)((n + 127) / 128);
     const size_t sm = bwd_smem(m);
     const float is = 1.f / m.sd;
 #define TF_BWD(HH) \
-    backward_kernel<HH><<<blocks, 128, sm, st>>>(n, m.I, m.O, m.wb, Y, T, m.mu, is, A1, A2, DY, D1, D2, m.loss, n_epoch)
+    backward_kernel<HH><<<blocks, 128, sm, st>>>(n, m.I, m.O, m.wb, Y, T, Wt, m.mu, is, A1, A2, DY, D1, D2, m.loss, \
+                                                 n_epoch)
     switch (m.H) {
     case 8: TF_BWD(8); break;
     case 16: TF_BWD(16); break;
@@ -529,7 +560,8 @@ tf_status ensure_scratch(Mlp &m, int64_t n)
 }
 
 // Forward and backward over n samples: the gradient into m.g and the loss into m.loss[0].
-tf_status gradients(Mlp &m, const float *X, const float *T, int64_t n, int64_t n_epoch, cudaStream_t st)
+tf_status gradients(Mlp &m, const float *X, const float *T, const float *Wt, int64_t n, int64_t n_epoch,
+                    cudaStream_t st)
 {
     tf_status s = ensure_scratch(m, n);
     if (s != TF_OK) return s;
@@ -537,7 +569,7 @@ tf_status gradients(Mlp &m, const float *X, const float *T, int64_t n, int64_t n
     float *Y = D2 + (size_t)n * m.H, *DY = Y + (size_t)n * m.O;
     launch_forward(m, n, X, Y, A1, A2, st);
     MLP_CUDA(cudaMemsetAsync(m.loss, 0, sizeof(float), st));
-    launch_backward(m, n, Y, T, A1, A2, DY, D1, D2, n_epoch, st);
+    launch_backward(m, n, Y, T, Wt, A1, A2, DY, D1, D2, n_epoch, st);
     launch_wgrad(m, n, m.H, m.I, D1, X, m.g, m.g + m.off_b1(), st);
     launch_wgrad(m, n, m.H, m.H, D2, A1, m.g + m.off_W2(), m.g + m.off_b2(), st);
     launch_wgrad(m, n, m.O, m.H, DY, A2, m.g + m.off_W3(), m.g + m.off_b3(), st);
@@ -695,6 +727,26 @@ tf_status tf_mlp_targets(int64_t n_cells, int32_t n_groups, const double *phi, f
     return TF_OK;
 }
 
+tf_status tf_mlp_weights(int64_t n_cells, int32_t n_groups, const double *phi, float floor_w, float *W, void *stream)
+{
+    if (n_cells < 1 || n_groups < 1 || !phi || !W || !(floor_w >= 0.f))
+        return fail(TF_ERR_ARG, "tf_mlp_weights: bad arguments");
+    cudaStream_t st = (cudaStream_t)stream;
+    unsigned long long *gmax = nullptr;
+    MLP_CUDA(cudaMalloc(&gmax, sizeof(unsigned long long) * (size_t)n_groups));
+    const int64_t CG = n_cells * n_groups;
+    cudaError_t e = cudaMemsetAsync(gmax, 0, sizeof(unsigned long long) * (size_t)n_groups, st);
+    if (e == cudaSuccess) {
+        group_max_kernel<<<grid_for(CG, 256, 8 * 152), 256, 0, st>>>(n_cells, n_groups, phi, gmax);
+        weights_kernel<<<grid_for(CG, 256, 8 * 152), 256, 0, st>>>(n_cells, n_groups, phi, gmax, floor_w, W);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(gmax);
+    if (e != cudaSuccess) return fail(TF_ERR_CUDA, std::string("tf_mlp_weights: ") + cudaGetErrorString(e));
+    return TF_OK;
+}
+
 tf_status tf_mlp_forward(tf_handle h, const float *X, int64_t n, float *Y, void *stream)
 {
     Mlp *m = as_mlp(h);
@@ -705,14 +757,14 @@ tf_status tf_mlp_forward(tf_handle h, const float *X, int64_t n, float *Y, void 
     return TF_OK;
 }
 
-tf_status tf_mlp_gradients(tf_handle h, const float *X, const float *T, int64_t n, float *grad, float *loss,
-                           void *stream)
+tf_status tf_mlp_gradients(tf_handle h, const float *X, const float *T, const float *W, int64_t n, float *grad,
+                           float *loss, void *stream)
 {
     Mlp *m = as_mlp(h);
     if (!m || !X || !T || n < 1) return fail(TF_ERR_ARG, "tf_mlp_gradients: bad arguments");
     MLP_CUDA(cudaSetDevice(m->device));
     cudaStream_t st = (cudaStream_t)stream;
-    tf_status s = gradients(*m, X, T, n, 0, st);
+    tf_status s = gradients(*m, X, T, W, n, 0, st);
     if (s != TF_OK) return s;
     if (grad) MLP_CUDA(cudaMemcpyAsync(grad, m->g, sizeof(float) * m->np, cudaMemcpyDeviceToHost, st));
     if (loss) MLP_CUDA(cudaMemcpyAsync(loss, m->loss, sizeof(float), cudaMemcpyDeviceToHost, st));
@@ -731,8 +783,8 @@ tf_status tf_mlp_adam_step(tf_handle h, float lr, void *stream)
     return TF_OK;
 }
 
-tf_status tf_mlp_train(tf_handle h, const float *X, const float *T, int64_t n, int32_t epochs, int32_t batch, float lr,
-                       uint64_t seed, float *loss_history, void *stream)
+tf_status tf_mlp_train(tf_handle h, const float *X, const float *T, const float *W, int64_t n, int32_t epochs,
+                       int32_t batch, float lr, uint64_t seed, float *loss_history, void *stream)
 {
     Mlp *m = as_mlp(h);
     if (!m || !X || !T || n < 1 || epochs < 1 || batch < 1 || !(lr > 0.f))
@@ -740,15 +792,17 @@ tf_status tf_mlp_train(tf_handle h, const float *X, const float *T, int64_t n, i
     MLP_CUDA(cudaSetDevice(m->device));
     cudaStream_t st = (cudaStream_t)stream;
     const int64_t B = std::min<int64_t>(batch, n);
-    float *Xb = nullptr, *Tb = nullptr;
+    float *Xb = nullptr, *Tb = nullptr, *Wb = nullptr;
     int64_t *perm_d = nullptr;
     auto cleanup = [&]() {
         cudaFree(Xb);
         cudaFree(Tb);
+        cudaFree(Wb);
         cudaFree(perm_d);
     };
     cudaError_t e = cudaMalloc(&Xb, sizeof(float) * (size_t)B * m->I);
     if (e == cudaSuccess) e = cudaMalloc(&Tb, sizeof(float) * (size_t)B * m->O);
+    if (e == cudaSuccess && W) e = cudaMalloc(&Wb, sizeof(float) * (size_t)B * m->O);
     if (e == cudaSuccess) e = cudaMalloc(&perm_d, sizeof(int64_t) * (size_t)n);
     if (e != cudaSuccess) {
         cleanup();
@@ -766,8 +820,8 @@ tf_status tf_mlp_train(tf_handle h, const float *X, const float *T, int64_t n, i
         for (int64_t b0 = 0; b0 < n && s == TF_OK && e == cudaSuccess; b0 += B) {
             const int64_t nn = std::min<int64_t>(B, n - b0);
             gather_kernel<<<grid_for(nn * (m->I + m->O), 256, 8 * 152), 256, 0, st>>>(nn, m->I, m->O, perm_d + b0, X, T,
-                                                                                      Xb, Tb);
-            s = gradients(*m, Xb, Tb, nn, n, st);
+                                                                                      W, Xb, Tb, Wb);
+            s = gradients(*m, Xb, Tb, Wb, nn, n, st);
             if (s == TF_OK) s = adam(*m, lr, st);
         }
         float l = 0.f;

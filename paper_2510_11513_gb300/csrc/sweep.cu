@@ -35,6 +35,7 @@ __global__ void begin_kernel(Ctrl *ctrl, unsigned long long n_seeds, int reset_s
     ctrl->next_group = first_group;
     ctrl->head = 0;
     ctrl->tail = n_seeds;
+    ctrl->complete = 0;
     if (reset_stats) {
         ctrl->tasks_done = ctrl->polls = ctrl->wait_ns = ctrl->busy_ns = 0;
         ctrl->depth_sum = ctrl->pops = 0;

@@ -38,6 +38,8 @@ struct Ctrl {
     unsigned long long pad0[15];
     unsigned long long tail;  // next slot to fill
     unsigned long long pad1[15];
+    unsigned long long complete;  // tasks finished in this launch (releases done)
+    unsigned long long pad2[15];
     unsigned int epoch;       // tag of the slots filled in the current launch
     int error;                // first device error (TF_ERR_*), 0 if none
     unsigned long long tasks_done;
@@ -939,15 +941,14 @@ __device__ __forceinline__ bool run_task_pairs(const SweepArgs<float> &A, uint4 
 
 __device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
 
-// Persistent sweep: every warp repeatedly claims a ticket (the next queue
-// slot), waits until that slot holds a ready task, executes it with lanes
-// spanning (cell, group) units, then decrements the counters of the task's
-// downwind blocks; the decrement that reaches zero enqueues that block
-// (work-first generation, Algorithm 1; atomic counters, Sec. 3.5).
-// A warp claims its next ticket as soon as it starts a task, so the claim's
-// latency overlaps the task.  Termination: exactly n_tasks slots get filled,
-// so a warp whose ticket is >= n_tasks exits.  Every wait is bounded by
-// wait_limit_ns.
+// Persistent sweep: a warp claims a ticket (the next queue slot), waits until
+// that slot holds a ready task, executes it with lanes spanning (cell, group)
+// units, then decrements the counters of the task's downwind blocks; a
+// decrement that reaches zero makes that block ready (work-first generation,
+// Algorithm 1; atomic counters, Sec. 3.5).  The warp keeps the first block it
+// made ready and runs it next, without the queue; it enqueues the others.
+// Termination: a warp whose ticket is >= n_tasks, or that waits while all
+// n_tasks tasks are complete, exits.  Every wait is bounded by wait_limit_ns.
 // MODE: 0 = any group count (registers), 1 = G a multiple of 32 (registers),
 // 2 = G a multiple of 32 with the rows staged in shared memory, 3 = FP32 and
 // G even: packed group pairs (pair-interleaved source and psi rows).
@@ -975,54 +976,68 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 3) sweep_kernel(cons
     if (lane < 6) ws[lane] = 0;
     __syncwarp();
     const unsigned long long t_start = globaltimer();
-    unsigned long long ticket = 0;
-    if (lane == 0) ticket = atomicAdd(&A.ctrl->head, 1ull);
-    ticket = __shfl_sync(FULL, ticket, 0);
-    while (ticket < A.n_tasks) {
-        unsigned task = 0;
-        int stop = 0;
-        if (lane == 0) {
-            const unsigned long long t0 = globaltimer();
-            unsigned long long v = ld_acquire(A.slots + ticket);
-            if ((unsigned)(v >> 32) != epoch) {
-                unsigned ns = 32;
-                for (;;) {
-                    __nanosleep(ns);
-                    if (ns < 256) ns <<= 1;
-                    ++ws[0];
+    // A warp that releases downwind tasks keeps one of them and runs it next
+    // (its upwind rows were just written and are still in L2); it claims a
+    // queue ticket only when it keeps nothing.  Fewer than n_tasks slots are
+    // then filled, so a waiting warp also stops once every task is complete.
+    unsigned keep = 0xffffffffu;
+    for (;;) {
+        unsigned task = keep;
+        if (keep == 0xffffffffu) {
+            int stop = 0;
+            if (lane == 0) {
+                const unsigned long long ticket = atomicAdd(&A.ctrl->head, 1ull);
+                const unsigned long long t0 = globaltimer();
+                unsigned long long v = 0;
+                if (ticket >= A.n_tasks) {
+                    stop = 2;
+                } else {
                     v = ld_acquire(A.slots + ticket);
-                    if ((unsigned)(v >> 32) == epoch) break;
-                    if (ld_volatile(&A.ctrl->error)) {
-                        stop = 1;
-                        break;
+                    if ((unsigned)(v >> 32) != epoch) {
+                        unsigned ns = 32;
+                        for (;;) {
+                            __nanosleep(ns);
+                            if (ns < 256) ns <<= 1;
+                            ++ws[0];
+                            v = ld_acquire(A.slots + ticket);
+                            if ((unsigned)(v >> 32) == epoch) break;
+                            if (ld_volatile(&A.ctrl->complete) >= A.n_tasks) {
+                                stop = 2;
+                                break;
+                            }
+                            if (ld_volatile(&A.ctrl->error)) {
+                                stop = 1;
+                                break;
+                            }
+                            if (globaltimer() - t0 > A.wait_limit_ns) {
+                                atomicCAS(&A.ctrl->error, 0, (int)TF_ERR_TIMEOUT);
+                                stop = 1;
+                                break;
+                            }
+                        }
                     }
-                    if (globaltimer() - t0 > A.wait_limit_ns) {
-                        atomicCAS(&A.ctrl->error, 0, (int)TF_ERR_TIMEOUT);
+                }
+                const unsigned long long t1 = globaltimer();
+                ws[1] += t1 - t0;
+                if (!stop) {
+                    const long long dq = (long long)(ld_volatile(&A.ctrl->tail) - ticket);
+                    ws[4] += dq > 0 ? (unsigned long long)dq : 0ull;
+                    ++ws[5];
+                    task = (unsigned)v;
+                    if (task < A.task_begin || task >= A.task_end) {
+                        atomicCAS(&A.ctrl->error, 0, (int)TF_ERR_DEVICE);
                         stop = 1;
-                        break;
                     }
                 }
             }
-            const unsigned long long t1 = globaltimer();
-            ws[1] += t1 - t0;
-            const long long dq = (long long)(ld_volatile(&A.ctrl->tail) - ticket);
-            ws[4] += dq > 0 ? (unsigned long long)dq : 0ull;
-            ++ws[5];
-            task = (unsigned)v;
-            if (!stop && (task < A.task_begin || task >= A.task_end)) {
-                atomicCAS(&A.ctrl->error, 0, (int)TF_ERR_DEVICE);
-                stop = 1;
-            }
+            __syncwarp();
+            stop = __shfl_sync(FULL, stop, 0);
+            if (stop) break;
+            task = __shfl_sync(FULL, task, 0);
         }
-        __syncwarp();
-        stop = __shfl_sync(FULL, stop, 0);
-        if (stop) break;
-        task = __shfl_sync(FULL, task, 0);
+        keep = 0xffffffffu;
         unsigned long long tb = 0;
         if (lane == 0) tb = globaltimer();
-        // claim the next ticket now; its latency overlaps this task
-        unsigned long long next = 0;
-        if (lane == 0) next = atomicAdd(&A.ctrl->head, 1ull);
 
         const uint4 ti = __ldg(A.task + task);
         const uint32_t dir = ti.y >> 16;
@@ -1040,9 +1055,18 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 3) sweep_kernel(cons
         // release: every lane's psi stores are ordered before any counter decrement
         fence_acq_rel_gpu();
         __syncwarp();
-        for (uint32_t e = lane; e < ti.w; e += 32) {
-            const uint32_t d = __ldg(A.down + ti.z + e);
-            if (atom_add_acq_rel(A.counters + d, -1) == 1) {
+        for (uint32_t e0 = 0; e0 < ti.w; e0 += 32) {
+            const uint32_t e = e0 + lane;
+            uint32_t d = 0;
+            bool ready = false;
+            if (e < ti.w) {
+                d = __ldg(A.down + ti.z + e);
+                ready = atom_add_acq_rel(A.counters + d, -1) == 1;
+            }
+            const unsigned rb = __ballot_sync(FULL, ready);
+            const int kl = (e0 == 0 && rb) ? __ffs(rb) - 1 : -1;  // the warp keeps this lane's task
+            if (kl >= 0) keep = __shfl_sync(FULL, d, kl);
+            if (ready && (int)lane != kl) {
                 const unsigned long long slot = atomicAdd(&A.ctrl->tail, 1ull);
                 if (slot < A.n_tasks)
                     st_release(A.slots + slot, ((unsigned long long)epoch << 32) | d);
@@ -1077,10 +1101,10 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 3) sweep_kernel(cons
         }
         __syncwarp();
         if (lane == 0) {
+            atomicAdd(&A.ctrl->complete, 1ull);
             ws[2] += globaltimer() - tb;
             ++ws[3];
         }
-        ticket = __shfl_sync(FULL, next, 0);
     }
     const unsigned long long t_end = globaltimer();
     __syncwarp();
@@ -1131,50 +1155,61 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 3) sweep_batch_kerne
     if (lane < 6) ws[lane] = 0;
     __syncwarp();
     const unsigned long long t_start = globaltimer();
-    unsigned long long ticket = 0;
-    if (lane == 0) ticket = atomicAdd(&B.ctrl->head, 1ull);
-    ticket = __shfl_sync(FULL, ticket, 0);
-    while (ticket < B.n_tasks) {
-        unsigned gid = 0;
-        int stop = 0;
-        if (lane == 0) {
-            const unsigned long long t0 = globaltimer();
-            unsigned long long v = ld_acquire(B.slots + ticket);
-            if ((unsigned)(v >> 32) != epoch) {
-                unsigned ns = 32;
-                for (;;) {
-                    __nanosleep(ns);
-                    if (ns < 256) ns <<= 1;
-                    ++ws[0];
+    unsigned keep = 0xffffffffu;  // a block this warp made ready and runs next (global id)
+    for (;;) {
+        unsigned gid = keep;
+        if (keep == 0xffffffffu) {
+            int stop = 0;
+            if (lane == 0) {
+                const unsigned long long ticket = atomicAdd(&B.ctrl->head, 1ull);
+                const unsigned long long t0 = globaltimer();
+                unsigned long long v = 0;
+                if (ticket >= B.n_tasks) {
+                    stop = 2;
+                } else {
                     v = ld_acquire(B.slots + ticket);
-                    if ((unsigned)(v >> 32) == epoch) break;
-                    if (ld_volatile(&B.ctrl->error)) {
-                        stop = 1;
-                        break;
+                    if ((unsigned)(v >> 32) != epoch) {
+                        unsigned ns = 32;
+                        for (;;) {
+                            __nanosleep(ns);
+                            if (ns < 256) ns <<= 1;
+                            ++ws[0];
+                            v = ld_acquire(B.slots + ticket);
+                            if ((unsigned)(v >> 32) == epoch) break;
+                            if (ld_volatile(&B.ctrl->complete) >= B.n_tasks) {
+                                stop = 2;
+                                break;
+                            }
+                            if (ld_volatile(&B.ctrl->error)) {
+                                stop = 1;
+                                break;
+                            }
+                            if (globaltimer() - t0 > B.wait_limit_ns) {
+                                atomicCAS(&B.ctrl->error, 0, (int)TF_ERR_TIMEOUT);
+                                stop = 1;
+                                break;
+                            }
+                        }
                     }
-                    if (globaltimer() - t0 > B.wait_limit_ns) {
-                        atomicCAS(&B.ctrl->error, 0, (int)TF_ERR_TIMEOUT);
+                }
+                ws[1] += globaltimer() - t0;
+                if (!stop) {
+                    ++ws[5];
+                    gid = (unsigned)v;
+                    if (gid >= B.n_tasks) {
+                        atomicCAS(&B.ctrl->error, 0, (int)TF_ERR_DEVICE);
                         stop = 1;
-                        break;
                     }
                 }
             }
-            ws[1] += globaltimer() - t0;
-            ++ws[5];
-            gid = (unsigned)v;
-            if (!stop && gid >= B.n_tasks) {
-                atomicCAS(&B.ctrl->error, 0, (int)TF_ERR_DEVICE);
-                stop = 1;
-            }
+            __syncwarp();
+            stop = __shfl_sync(FULL, stop, 0);
+            if (stop) break;
+            gid = __shfl_sync(FULL, gid, 0);
         }
-        __syncwarp();
-        stop = __shfl_sync(FULL, stop, 0);
-        if (stop) break;
-        gid = __shfl_sync(FULL, gid, 0);
+        keep = 0xffffffffu;
         unsigned long long tb = 0;
         if (lane == 0) tb = globaltimer();
-        unsigned long long next = 0;
-        if (lane == 0) next = atomicAdd(&B.ctrl->head, 1ull);
         // problem owning the global id: offsets ascend, n is small
         int lo = 0, hi = B.n - 1;
         while (lo < hi) {
@@ -1200,9 +1235,18 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 3) sweep_batch_kerne
         if (!ok) break;
         fence_acq_rel_gpu();
         __syncwarp();
-        for (uint32_t e = lane; e < ti.w; e += 32) {
-            const uint32_t d = __ldg(A.down + ti.z + e);
-            if (atom_add_acq_rel(A.counters + d, -1) == 1) {
+        for (uint32_t e0 = 0; e0 < ti.w; e0 += 32) {
+            const uint32_t e = e0 + lane;
+            uint32_t d = 0;
+            bool ready = false;
+            if (e < ti.w) {
+                d = __ldg(A.down + ti.z + e);
+                ready = atom_add_acq_rel(A.counters + d, -1) == 1;
+            }
+            const unsigned rb = __ballot_sync(FULL, ready);
+            const int kl = (e0 == 0 && rb) ? __ffs(rb) - 1 : -1;
+            if (kl >= 0) keep = __shfl_sync(FULL, d - A.task_begin + base, kl);
+            if (ready && (int)lane != kl) {
                 const unsigned long long slot = atomicAdd(&B.ctrl->tail, 1ull);
                 if (slot < B.n_tasks)
                     st_release(B.slots + slot, ((unsigned long long)epoch << 32) | (d - A.task_begin + base));
@@ -1212,10 +1256,10 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 3) sweep_batch_kerne
         }
         __syncwarp();
         if (lane == 0) {
+            atomicAdd(&B.ctrl->complete, 1ull);
             ws[2] += globaltimer() - tb;
             ++ws[3];
         }
-        ticket = __shfl_sync(FULL, next, 0);
     }
     const unsigned long long t_end = globaltimer();
     __syncwarp();

@@ -48,11 +48,20 @@ def flux_targets(phi: torch.Tensor, n_groups: int, stream=None) -> torch.Tensor:
     return T
 
 
-def generate(cfgs, tol=1e-6, max_iters=5000, device="cuda", **solver_opts):
+def flux_weights(phi: torch.Tensor, n_groups: int, floor: float, stream=None) -> torch.Tensor:
+    """Loss weights [n_cells][G] (FP32): (cell-average phi / group maximum)^2 + floor."""
+    C = phi.shape[0]
+    W = torch.empty((C, n_groups), dtype=torch.float32, device=phi.device)
+    tf.tf_mlp_weights(C, n_groups, phi, floor, W, stream)
+    return W
+
+
+def generate(cfgs, tol=1e-6, max_iters=5000, device="cuda", weight_floor=None, **solver_opts):
     """Training data from the plain solver: for each problem configuration, its
-    features and the targets of its converged zero-start solution.  Returns
-    (X [sum C][I], T [sum C][G], per-problem info dicts with iterations and seconds)."""
-    Xs, Ts, infos = [], [], []
+    features and the targets of its converged zero-start solution, and with
+    `weight_floor` the loss weights of each problem's flux.  Returns
+    (X [sum C][I], T [sum C][G], W [sum C][G] or None, per-problem info dicts)."""
+    Xs, Ts, Ws, infos = [], [], [], []
     for cfg in cfgs:
         t0 = time.perf_counter()
         prob = tf.Problem.from_config(cfg, **solver_opts)
@@ -67,9 +76,11 @@ def generate(cfgs, tol=1e-6, max_iters=5000, device="cuda", **solver_opts):
         r["name"] = cfg.get("name", "")
         Xs.append(X)
         Ts.append(flux_targets(phi, prob.n_groups))
+        if weight_floor is not None:
+            Ws.append(flux_weights(phi, prob.n_groups, weight_floor))
         infos.append(r)
         prob.close()
-    return torch.cat(Xs), torch.cat(Ts), infos
+    return torch.cat(Xs), torch.cat(Ts), (torch.cat(Ws) if Ws else None), infos
 
 
 class LearnedStart:
@@ -79,14 +90,23 @@ class LearnedStart:
         self.n_groups = int(n_groups)
         self.net = tf.Mlp(n_features(self.n_groups), hidden, self.n_groups, seed)
 
-    def fit(self, X: torch.Tensor, T: torch.Tensor, epochs: int = 20, batch: int = 1024, lr: float = 1e-3,
-            seed: int = 0, stream=None) -> np.ndarray:
+    def fit(self, X: torch.Tensor, T: torch.Tensor, W: torch.Tensor | None = None, epochs: int = 20,
+            batch: int = 1024, lr: float = 1e-3, seed: int = 0, decay: int = 3, stream=None) -> np.ndarray:
         """Standardises the targets (mean / standard deviation over T) and trains
-        with Adam; returns the per-epoch mean loss."""
+        with Adam, optionally weighted by W; the epochs are split into `decay`
+        phases whose learning rate drops by 3x each.  Returns the per-epoch mean loss."""
         if X.shape[0] != T.shape[0] or T.shape[1] != self.n_groups:
             raise ValueError("X and T disagree in samples or groups")
+        if W is not None and W.shape != T.shape:
+            raise ValueError("W and T disagree in shape")
         tf.tf_mlp_fit_scale(self.net.h, T, T.numel(), stream)
-        return tf.tf_mlp_train(self.net.h, X, T, X.shape[0], epochs, batch, lr, seed, stream)
+        phases = max(1, min(int(decay), int(epochs)))
+        hist = []
+        for k in range(phases):
+            ep = epochs // phases + (1 if k < epochs % phases else 0)
+            hist.append(tf.tf_mlp_train(self.net.h, X, T, X.shape[0], ep, batch, lr / 3.0 ** k, seed + k, W=W,
+                                        stream=stream))
+        return np.concatenate(hist)
 
     def initial_flux(self, X: torch.Tensor, stream=None) -> torch.Tensor:
         """phi0 [n_cells][G][4] (FP64, device) for the cells whose features are X."""

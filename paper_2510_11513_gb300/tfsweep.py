@@ -29,7 +29,7 @@ SYMBOLS = (
     "tf_problem_psi", "tf_problem_stats", "tf_status_string", "tf_last_error", "tf_integrated_flux_noalloc",
     # include/tflearn.h
     "tf_mlp_create", "tf_mlp_params", "tf_mlp_scale", "tf_mlp_fit_scale", "tf_mlp_features", "tf_mlp_targets",
-    "tf_mlp_forward", "tf_mlp_gradients", "tf_mlp_adam_step", "tf_mlp_train", "tf_mlp_predict_phi",
+    "tf_mlp_weights", "tf_mlp_forward", "tf_mlp_gradients", "tf_mlp_adam_step", "tf_mlp_train", "tf_mlp_predict_phi",
 )
 
 
@@ -115,9 +115,10 @@ def load(build_if_missing: bool = True):
     lib.tf_mlp_features.argtypes = [i64, i32, vp, vp, vp, vp, vp, vp, vp]
     lib.tf_mlp_targets.argtypes = [i64, i32, vp, vp, vp]
     lib.tf_mlp_forward.argtypes = [H, vp, i64, vp, vp]
-    lib.tf_mlp_gradients.argtypes = [H, vp, vp, i64, vp, fp, vp]
+    lib.tf_mlp_weights.argtypes = [i64, i32, vp, f32, vp, vp]
+    lib.tf_mlp_gradients.argtypes = [H, vp, vp, vp, i64, vp, fp, vp]
     lib.tf_mlp_adam_step.argtypes = [H, f32, vp]
-    lib.tf_mlp_train.argtypes = [H, vp, vp, i64, i32, i32, f32, u64, vp, vp]
+    lib.tf_mlp_train.argtypes = [H, vp, vp, vp, i64, i32, i32, f32, u64, vp, vp]
     lib.tf_mlp_predict_phi.argtypes = [H, vp, i64, vp, vp]
     lib.tf_status_string.argtypes = [i32]
     lib.tf_status_string.restype = C.c_char_p
@@ -345,14 +346,19 @@ def tf_mlp_targets(n_cells, n_groups, phi, T, stream=None):
                   "tf_mlp_targets")
 
 
+def tf_mlp_weights(n_cells, n_groups, phi, floor, W, stream=None):
+    return _check(load().tf_mlp_weights(int(n_cells), int(n_groups), _ptr(phi), float(floor), _ptr(W),
+                                        _stream_handle(stream)), "tf_mlp_weights")
+
+
 def tf_mlp_forward(net, X, n, Y, stream=None):
     return _check(load().tf_mlp_forward(net, _ptr(X), int(n), _ptr(Y), _stream_handle(stream)), "tf_mlp_forward")
 
 
-def tf_mlp_gradients(net, X, T, n, grad=None, stream=None):
+def tf_mlp_gradients(net, X, T, n, grad=None, W=None, stream=None):
     loss = C.c_float()
-    _check(load().tf_mlp_gradients(net, _ptr(X), _ptr(T), int(n), _ptr(grad), C.byref(loss), _stream_handle(stream)),
-           "tf_mlp_gradients")
+    _check(load().tf_mlp_gradients(net, _ptr(X), _ptr(T), _ptr(W), int(n), _ptr(grad), C.byref(loss),
+                                   _stream_handle(stream)), "tf_mlp_gradients")
     return loss.value
 
 
@@ -360,9 +366,9 @@ def tf_mlp_adam_step(net, lr, stream=None):
     return _check(load().tf_mlp_adam_step(net, float(lr), _stream_handle(stream)), "tf_mlp_adam_step")
 
 
-def tf_mlp_train(net, X, T, n, epochs, batch, lr, seed=0, stream=None):
+def tf_mlp_train(net, X, T, n, epochs, batch, lr, seed=0, W=None, stream=None):
     hist = np.zeros(int(epochs), np.float32)
-    _check(load().tf_mlp_train(net, _ptr(X), _ptr(T), int(n), int(epochs), int(batch), float(lr), int(seed),
+    _check(load().tf_mlp_train(net, _ptr(X), _ptr(T), _ptr(W), int(n), int(epochs), int(batch), float(lr), int(seed),
                                _ptr(hist), _stream_handle(stream)), "tf_mlp_train")
     return hist
 

@@ -76,6 +76,27 @@ def test_gradients_match_oracle(I, H, O, n):
         k += sz
 
 
+def test_weighted_gradients_and_weights_match_oracle():
+    I, H, O, n = 320, 64, 16, 513
+    p, X, T = _net_and_data(I, H, O, n, seed=31)
+    rng = np.random.default_rng(32)
+    phi = rng.uniform(-0.05, 1.0, (n, O, 4)) ** 3
+    Wd = L.flux_weights(torch.from_numpy(phi).to(DEV), O, 1e-3)
+    Wref = om.weights(phi, 1e-3)
+    np.testing.assert_allclose(Wd.cpu().numpy(), Wref, rtol=1e-6, atol=1e-9)
+    net = _gpu_net(I, H, O, p)
+    g = np.zeros(net.n_params, np.float32)
+    loss = tf.tf_mlp_gradients(net.h, torch.from_numpy(X).to(DEV), torch.from_numpy(T).to(DEV), n, grad=g, W=Wd)
+    W32 = Wd.cpu().numpy().astype(np.float64)
+    L_ref, g_ref = om.gradient(p, X, T, I, H, O, bf16=True, W=W32)
+    assert loss == pytest.approx(L_ref, rel=2e-5)
+    k = 0
+    for sz in [H * I, H, H * H, H, O * H, O]:
+        a, b = g[k:k + sz].astype(np.float64), g_ref[k:k + sz]
+        assert np.abs(a - b).max() <= 1e-4 * np.abs(b).max() + 1e-12, (k, sz)
+        k += sz
+
+
 def test_adam_step_matches_oracle():
     I, H, O, n = 64, 32, 8, 500
     p, X, T = _net_and_data(I, H, O, n, seed=5)
@@ -171,10 +192,10 @@ def test_learned_start_fewer_iterations_same_answer():
     within the FP32 tolerance of the tightly converged FP64 solution."""
     torch.manual_seed(0)
     train = [_layout(k) for k in range(24)]
-    X, T, infos = L.generate(train, tol=1e-6, max_iters=3000, precision=tf.TF_FP32)
+    X, T, Wt, infos = L.generate(train, tol=1e-6, max_iters=3000, weight_floor=1e-3, precision=tf.TF_FP32)
     assert all(i["converged"] for i in infos)
     ls = L.LearnedStart(4, hidden=64, seed=3)
-    hist = ls.fit(X, T, epochs=30, batch=1024, lr=2e-3, seed=5)
+    hist = ls.fit(X, T, Wt, epochs=30, batch=1024, lr=2e-3, seed=5)
     assert hist[-1] < 0.5 * hist[0]
     it_zero = it_learned = 0
     for k in range(100, 104):
@@ -202,7 +223,7 @@ def test_learned_start_oracle_check_one_layout():
     """One held-out layout: the learned-start FP64 solve against the oracle's own
     source iteration converged tightly on the CPU."""
     train = [_layout(k, n=6) for k in range(12)]
-    X, T, _ = L.generate(train, tol=1e-6, max_iters=3000, precision=tf.TF_FP32)
+    X, T, _, _ = L.generate(train, tol=1e-6, max_iters=3000, precision=tf.TF_FP32)
     ls = L.LearnedStart(4, hidden=32, seed=7)
     ls.fit(X, T, epochs=20, batch=512, lr=2e-3, seed=1)
     cfg = _layout(200, n=6)

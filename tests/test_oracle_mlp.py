@@ -261,3 +261,37 @@ def test_mesh_neighbours_from_jittered_mesh_are_symmetric():
         for n in nbr[c]:
             if n >= 0:
                 assert c in nbr[n]
+
+
+def test_weighted_gradient_matches_central_differences():
+    I, H, O, n = 6, 8, 3, 5
+    rng = np.random.default_rng(21)
+    p = _rand_net(I, H, O, 22)
+    X = rng.normal(size=(n, I))
+    T = rng.normal(size=(n, O))
+    Wt = rng.uniform(0.0, 2.0, size=(n, O))
+    _, g = om.gradient(p, X, T, I, H, O, 0.5, 1.5, W=Wt)
+    h = 1e-6
+    fd = np.array([(om.loss(p + h * e, X, T, I, H, O, 0.5, 1.5, W=Wt) - om.loss(p - h * e, X, T, I, H, O, 0.5, 1.5,
+                                                                               W=Wt)) / (2 * h)
+                   for e in np.eye(p.size)])
+    assert np.abs(g - fd).max() <= 1e-7 * np.abs(g).max()
+
+
+def test_weights_are_squared_fraction_of_group_max():
+    phi = np.zeros((3, 2, 4))
+    phi[0, 0] = 2.0       # group 0 max
+    phi[1, 0] = 1.0       # half of it
+    phi[2, 0] = -1.0      # clamps to 0
+    phi[:, 1] = 0.0       # a group without flux
+    W = om.weights(phi, 0.01)
+    np.testing.assert_allclose(W[:, 0], [1.01, 0.26, 0.01], rtol=1e-15)
+    np.testing.assert_allclose(W[:, 1], [0.01, 0.01, 0.01], rtol=1e-15)
+    # unit weights reproduce the unweighted loss and gradient
+    I, H, O = 4, 8, 2
+    p = _rand_net(I, H, O, 23)
+    X = np.random.default_rng(24).normal(size=(3, I))
+    T = np.random.default_rng(25).normal(size=(3, O))
+    L1, g1 = om.gradient(p, X, T, I, H, O)
+    L2, g2 = om.gradient(p, X, T, I, H, O, W=np.ones((3, O)))
+    assert L1 == L2 and np.array_equal(g1, g2)
