@@ -414,7 +414,7 @@ def run_learned(args):
     t_gen = time.perf_counter() - t0
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
-    ls = L.LearnedStart(kw["G"], hidden=64, seed=args.seed)
+    ls = L.LearnedStart(kw["G"], hidden=64, seed=args.seed, overshoot_weight=args.overshoot_weight)
     hist = ls.fit(X, T, Wt, epochs=args.epochs, batch=args.train_batch, lr=args.lr, seed=args.seed)
     torch.cuda.synchronize(dev)
     t_train = time.perf_counter() - t0
@@ -460,7 +460,7 @@ def run_learned(args):
             "config": {"workload": f"learned_start_layouts_{kw['n']}^3_D{kw['n_polar'] * kw['n_az']}_G{kw['G']}",
                        "train_layouts": args.train_layouts, "eval_layouts": args.eval_layouts, "samples": samples,
                        "epochs": args.epochs, "batch": args.train_batch, "lr": args.lr, "tol": tol,
-                       "weight_floor": floor},
+                       "weight_floor": floor, "overshoot_weight": args.overshoot_weight},
             "zero_start_s": sz / len(rows), "iterations_zero": iz, "iterations_learned": il,
             "iteration_ratio": il / max(iz, 1), "generate_s": round(t_gen, 1),
             "generate_solve_s": round(sum(g["solve_seconds"] for g in gen), 2),
@@ -501,8 +501,10 @@ def main():
     ap.add_argument("--train-batch", type=int, default=1024)
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--seed", type=int, default=0)
-    ap.add_argument("--weight-floor", type=float, default=1e-3,
+    ap.add_argument("--weight-floor", type=float, default=-1.0,
                     help="--config layout: loss weights (phi/max)^2 + floor; negative = unweighted")
+    ap.add_argument("--overshoot-weight", type=float, default=1.0,
+                    help="--config layout: loss weight of overshooting outputs (1 = plain squared error)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)  # at least 3 untimed warm-up steps
     if args.impl == "reference":

@@ -14,7 +14,10 @@
  * (layer l computes z = W_l a + b_l).  The forward and backward kernels read
  * the weights W1, W2, W3 rounded to BF16 (round to nearest even) and
  * accumulate in FP32; biases stay FP32.  A handle also keeps a target
- * standardisation (mu, sd): the network output y predicts (t - mu) / sd.
+ * standardisation (mu, sd): the network output y predicts (t - mu) / sd, and
+ * an upper cap on the predicted target (tf_mlp_fit_scale sets it to the
+ * largest training target, so a prediction never exceeds the largest flux
+ * seen in training).
  *
  * Per-cell features (tf_mlp_features), I = G^2 + 4 G for G groups, cell c of
  * material m:
@@ -27,8 +30,10 @@
  * Targets (tf_mlp_targets): t[c][g] = log(max(mean_i phi[c][g][i], 0) + 1e-6),
  * the log of the cell-average scalar flux; tf_mlp_predict_phi inverts that map.
  *
- * Loss over n samples: L = (1 / (n O)) sum_s sum_o w_so (y_so - (t_so - mu)/sd)^2,
- * with per-target weights w (all 1 when no weight array is given).  The
+ * Loss over n samples: L = (1 / (n O)) sum_s sum_o w_so k_so (y_so - (t_so - mu)/sd)^2,
+ * with per-target weights w (all 1 when no weight array is given) and
+ * k_so = kappa where the output overshoots (y_so > (t_so - mu)/sd), else 1
+ * (an asymmetric least-squares loss: kappa > 1 makes the network err low).  The
  * weights of tf_mlp_weights, w = (phi / max phi)^2 + floor per group, make a
  * log-space error count as the absolute flux error it causes relative to the
  * group's largest flux, the scale of the source-iteration stopping test.
@@ -66,8 +71,14 @@ tf_status tf_mlp_params(tf_handle net, float *get, const float *set, int64_t *n_
  * target standardisation.  Any pointer may be NULL. */
 tf_status tf_mlp_scale(tf_handle net, float *mu_get, float *sd_get, const float *mu_set, const float *sd_set);
 
+/* Reads and/or sets (host pointers, any may be NULL) the overshoot weight kappa
+ * (> 0, default 1: symmetric loss) and the cap on the predicted target
+ * (default +infinity). */
+tf_status tf_mlp_limits(tf_handle net, float *kappa_get, float *cap_get, const float *kappa_set, const float *cap_set);
+
 /* Sets (mu, sd) to the mean and the population standard deviation of the
- * n_values targets T (FP64 sums).  Synchronises `stream`. */
+ * n_values targets T (FP64 sums) and the prediction cap to their maximum.
+ * Synchronises `stream`. */
 tf_status tf_mlp_fit_scale(tf_handle net, const float *T, int64_t n_values, void *stream);
 
 /* Features of every cell into X [n_cells][G^2 + 4G] (FP32).  Inputs (device):
@@ -111,8 +122,8 @@ tf_status tf_mlp_train(tf_handle net, const float *X, const float *T, const floa
                        int32_t batch, float lr, uint64_t seed, float *loss_history, void *stream);
 
 /* Initial flux for source iteration: phi [n_cells][O][4] (FP64, O = groups) set
- * at every node to max(exp(mu + sd y) - 1e-6, 0), y the network output for the
- * cell's features X [n_cells][I].  Synchronises `stream`. */
+ * at every node to max(exp(min(mu + sd y, cap)) - 1e-6, 0), y the network output
+ * for the cell's features X [n_cells][I].  Synchronises `stream`. */
 tf_status tf_mlp_predict_phi(tf_handle net, const float *X, int64_t n_cells, double *phi, void *stream);
 
 #ifdef __cplusplus

@@ -11,11 +11,13 @@ computes, so that the kernels can be checked against it:
   features   per-cell inputs read from the problem (cross sections, scattering
              probabilities, cell-average source and the averages of log sigma_t
              and of the source over the face neighbours);
-  targets    log(max(cell-average phi, 0) + 1e-6);
+  targets    log(max(cell-average phi, 0) + 1e-6), standardised by their mean
+             and deviation, predictions capped at the largest target;
   weights    (cell-average phi / its group maximum)^2 + floor, per target;
   forward    tanh MLP, inputs -> H -> H -> outputs, z = W a + b per layer;
-  gradient   backpropagation of the (optionally weighted) mean squared error
-             of the standardised targets;
+  gradient   backpropagation of the (optionally weighted, optionally
+             asymmetric: kappa on overshoots) mean squared error of the
+             standardised targets;
   adam       Adam with bias correction (b1 = 0.9, b2 = 0.999, eps = 1e-8);
   predict    the inverse of the target map, copied to the 4 nodes.
 
@@ -116,9 +118,10 @@ def weights(phi, floor):
     return r * r + floor
 
 
-def predict_phi(y, mu, sd):
-    """Inverse of the standardised target map at every node: [C][G][4]."""
-    v = np.maximum(np.exp(mu + sd * np.asarray(y, dtype=np.float64)) - EPS_T, 0.0)
+def predict_phi(y, mu, sd, cap=np.inf):
+    """Inverse of the standardised target map at every node, the target capped
+    at `cap` (the largest training target): [C][G][4]."""
+    v = np.maximum(np.exp(np.minimum(mu + sd * np.asarray(y, dtype=np.float64), cap)) - EPS_T, 0.0)
     return np.repeat(v[:, :, None], 4, axis=2)
 
 
@@ -147,23 +150,29 @@ def forward(p, X, I, H, O, bf16=False):
     return y, (a1, a2)
 
 
-def loss(p, X, T, I, H, O, mu=0.0, sd=1.0, bf16=False, W=None):
+def _loss_weights(r, W, kappa):
+    """Per-target weight: the given one (1 without) times kappa where the output overshoots."""
+    w = np.ones_like(r) if W is None else np.asarray(W, dtype=np.float64)
+    return w * np.where(r > 0.0, kappa, 1.0)
+
+
+def loss(p, X, T, I, H, O, mu=0.0, sd=1.0, bf16=False, W=None, kappa=1.0):
     y, _ = forward(p, X, I, H, O, bf16)
     r = y - (np.asarray(T, dtype=np.float64) - mu) / sd
-    w = 1.0 if W is None else np.asarray(W, dtype=np.float64)
-    return float(np.mean(w * r * r))
+    return float(np.mean(_loss_weights(r, W, kappa) * r * r))
 
 
-def gradient(p, X, T, I, H, O, mu=0.0, sd=1.0, bf16=False, W=None):
+def gradient(p, X, T, I, H, O, mu=0.0, sd=1.0, bf16=False, W=None, kappa=1.0):
     """Loss and its gradient (flat, parameter order) by backpropagation:
-    dL/dy = 2 w r / (n O) (w = 1 without weights); through z3 = W3 a2 + b3, a2 = tanh(z2), z2 = W2 a1 + b2,
+    dL/dy = 2 w r / (n O) (w the given weight, 1 without, times kappa where r > 0;
+    the loss is continuously differentiable at r = 0); through z3 = W3 a2 + b3, a2 = tanh(z2), z2 = W2 a1 + b2,
     a1 = tanh(z1), z1 = W1 x + b1, with tanh' = 1 - tanh^2."""
     W1, b1, W2, b2, W3, b3 = _weights(p, I, H, O, bf16)
     X = np.asarray(X, dtype=np.float64)
     n = X.shape[0]
     y, (a1, a2) = forward(p, X, I, H, O, bf16)
     r = y - (np.asarray(T, dtype=np.float64) - mu) / sd
-    w = 1.0 if W is None else np.asarray(W, dtype=np.float64)
+    w = _loss_weights(r, W, kappa)
     L = float(np.mean(w * r * r))
     dy = 2.0 * w * r / (n * O)             # dL/dz3   [n][O]
     gW3 = dy.T @ a2

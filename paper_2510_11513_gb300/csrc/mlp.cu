@@ -11,12 +11,13 @@
 // W2^T [H][H] and W3 [O][H] (the orders the per-sample loops read).
 // Loss over n samples: (1/(n O)) sum_s sum_o w_so (y_so - (t_so - mu)/sd)^2, with
 // (mu, sd) the target standardisation kept in the handle and w optional
-// per-target weights (1 without them).
+// per-target weights (1 without them) times kappa on overshooting outputs.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <new>
 #include <numeric>
 #include <random>
@@ -52,6 +53,8 @@ struct Mlp : Object {
     float *loss = nullptr;     // [0] last minibatch loss, [1] epoch accumulator
     double *red = nullptr;     // reduction scratch (2 doubles)
     float mu = 0.f, sd = 1.f;
+    float kappa = 1.f;             // loss weight multiplier of overshooting outputs
+    float t_cap = INFINITY;        // predictions are capped at this target value
     int64_t step = 0;
     size_t off_b1() const { return (size_t)H * I; }
     size_t off_W2() const { return off_b1() + H; }
@@ -182,6 +185,21 @@ __global__ void moment_kernel(int64_t n, const float *__restrict__ T, double shi
     if ((threadIdx.x & 31) == 0) atomicAdd(acc, s);
 }
 
+// Largest of n values into *acc as an order-preserving unsigned key of the float.
+__device__ __forceinline__ unsigned float_key(float f)
+{
+    const unsigned b = __float_as_uint(f);
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+__global__ void max_key_kernel(int64_t n, const float *__restrict__ T, unsigned *__restrict__ acc)
+{
+    unsigned k = 0u;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+        k = max(k, float_key(T[e]));
+    for (int o = 16; o > 0; o >>= 1) k = max(k, __shfl_xor_sync(0xffffffffu, k, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(acc, k);
+}
+
 // ---------------------------------------------------------------- forward
 // One thread per sample; the BF16 weights are widened to FP32 in shared memory
 // (W1^T in chunks of kKC rows) and read as float4 broadcasts.
@@ -270,13 +288,14 @@ __global__ void __launch_bounds__(128) forward_kernel(int64_t n, int I, int O, c
 }
 
 // ---------------------------------------------------------------- backward
-// Per sample: dy_o = 2 w_o (y_o - (t_o - mu)/sd) / (n O) (w = 1 without weights);
+// Per sample, r_o = y_o - (t_o - mu)/sd: dy_o = 2 w_o r_o / (n O), with w_o the given weight
+// (1 without weights) times kappa where r_o > 0 (an overshooting output);
 // d2 = (W3^T dy) (1 - a2^2); d1 = (W2^T d2) (1 - a1^2), with the BF16 weights of the forward pass.
 // loss[0] += minibatch loss; loss[1] += weighted squared error / (n_epoch O) when n_epoch > 0.
 template <int H>
 __global__ void __launch_bounds__(128) backward_kernel(int64_t n, int I, int O, const __nv_bfloat16 *__restrict__ wb,
                                                        const float *__restrict__ Y, const float *__restrict__ T,
-                                                       const float *__restrict__ Wt, float mu, float inv_sd,
+                                                       const float *__restrict__ Wt, float mu, float inv_sd, float kappa,
                                                        const float *__restrict__ A1,
                                                        const float *__restrict__ A2, float *__restrict__ DY,
                                                        float *__restrict__ D1, float *__restrict__ D2,
@@ -297,7 +316,7 @@ __global__ void __launch_bounds__(128) backward_kernel(int64_t n, int I, int O, 
         for (int k = 0; k < H; ++k) d2[k] = 0.f;
         for (int o = 0; o < O; ++o) {
             const float r = Y[(size_t)s * O + o] - (T[(size_t)s * O + o] - mu) * inv_sd;
-            const float w = Wt ? Wt[(size_t)s * O + o] : 1.f;
+            const float w = (Wt ? Wt[(size_t)s * O + o] : 1.f) * (r > 0.f ? kappa : 1.f);
             lsum = fmaf(w * r, r, lsum);
             const float dy = scale * w * r;
             DY[(size_t)s * O + o] = dy;
@@ -465,11 +484,14 @@ __global__ void gather_kernel(int64_t nn, int I, int O, const int64_t *__restric
     }
 }
 
-// phi0[c][g][i] = max(exp(mu + sd y[c][g]) - 1e-6, 0) at the 4 nodes (inverse of the target map).
-__global__ void predict_phi_kernel(int64_t CG, const float *__restrict__ Y, float mu, float sd, double *__restrict__ phi)
+// phi0[c][g][i] = max(exp(min(mu + sd y[c][g], t_cap)) - 1e-6, 0) at the 4 nodes (inverse of the
+// target map, capped at the largest training target).
+__global__ void predict_phi_kernel(int64_t CG, const float *__restrict__ Y, float mu, float sd, float t_cap,
+                                   double *__restrict__ phi)
 {
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < CG; e += (int64_t)gridDim.x * blockDim.x) {
-        const double v = fmax(exp((double)mu + (double)sd * (double)Y[e]) - 1e-6, 0.0);
+        const double t = fmin((double)mu + (double)sd * (double)Y[e], (double)t_cap);
+        const double v = fmax(exp(t) - 1e-6, 0.0);
         double2 *o = reinterpret_cast<double2 *>(phi + (size_t)e * 4);
         o[0] = make_double2(v, v);
         o[1] = make_double2(v, v);
@@ -512,7 +534,7 @@ void launch_backward(const Mlp &m, int64_t n, const float *Y, const float *T, co
     const size_t sm = bwd_smem(m);
     const float is = 1.f / m.sd;
 #define TF_BWD(HH) \
-    backward_kernel<HH><<<blocks, 128, sm, st>>>(n, m.I, m.O, m.wb, Y, T, Wt, m.mu, is, A1, A2, DY, D1, D2, m.loss, \
+    backward_kernel<HH><<<blocks, 128, sm, st>>>(n, m.I, m.O, m.wb, Y, T, Wt, m.mu, is, m.kappa, A1, A2, DY, D1, D2, m.loss, \
                                                  n_epoch)
     switch (m.H) {
     case 8: TF_BWD(8); break;
@@ -685,6 +707,19 @@ tf_status tf_mlp_scale(tf_handle h, float *mu_get, float *sd_get, const float *m
     return TF_OK;
 }
 
+tf_status tf_mlp_limits(tf_handle h, float *kappa_get, float *cap_get, const float *kappa_set, const float *cap_set)
+{
+    Mlp *m = as_mlp(h);
+    if (!m) return fail(TF_ERR_ARG, "tf_mlp_limits: not a network handle");
+    if (kappa_set && !(*kappa_set > 0.f)) return fail(TF_ERR_ARG, "tf_mlp_limits: overshoot weight must be > 0");
+    if (cap_set && std::isnan(*cap_set)) return fail(TF_ERR_ARG, "tf_mlp_limits: cap is NaN");
+    if (kappa_set) m->kappa = *kappa_set;
+    if (cap_set) m->t_cap = *cap_set;
+    if (kappa_get) *kappa_get = m->kappa;
+    if (cap_get) *cap_get = m->t_cap;
+    return TF_OK;
+}
+
 tf_status tf_mlp_fit_scale(tf_handle h, const float *T, int64_t n_values, void *stream)
 {
     Mlp *m = as_mlp(h);
@@ -702,8 +737,18 @@ tf_status tf_mlp_fit_scale(tf_handle h, const float *T, int64_t n_values, void *
     MLP_CUDA(cudaMemcpyAsync(acc + 1, m->red + 1, sizeof(double), cudaMemcpyDeviceToHost, st));
     MLP_CUDA(cudaStreamSynchronize(st));
     const double sd = std::sqrt(acc[1] / (double)n_values);
+    unsigned key = 0u;
+    unsigned *kd = reinterpret_cast<unsigned *>(m->red);
+    MLP_CUDA(cudaMemsetAsync(kd, 0, sizeof(unsigned), st));
+    max_key_kernel<<<grid, 256, 0, st>>>(n_values, T, kd);
+    MLP_CUDA(cudaMemcpyAsync(&key, kd, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+    MLP_CUDA(cudaStreamSynchronize(st));
+    const unsigned bits = (key & 0x80000000u) ? (key & 0x7fffffffu) : ~key;
+    float tmax;
+    std::memcpy(&tmax, &bits, sizeof(float));
     m->mu = (float)mu;
     m->sd = sd > 0.0 ? (float)sd : 1.f;
+    m->t_cap = tmax;
     return TF_OK;
 }
 
@@ -844,7 +889,7 @@ tf_status tf_mlp_predict_phi(tf_handle h, const float *X, int64_t n_cells, doubl
     MLP_CUDA(cudaMalloc(&Y, sizeof(float) * (size_t)n_cells * m->O));
     launch_forward(*m, n_cells, X, Y, nullptr, nullptr, st);
     const int64_t CG = n_cells * m->O;
-    predict_phi_kernel<<<grid_for(CG, 256, 8 * 152), 256, 0, st>>>(CG, Y, m->mu, m->sd, phi);
+    predict_phi_kernel<<<grid_for(CG, 256, 8 * 152), 256, 0, st>>>(CG, Y, m->mu, m->sd, m->t_cap, phi);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     cudaFree(Y);

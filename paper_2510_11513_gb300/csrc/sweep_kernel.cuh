@@ -24,13 +24,15 @@ template <class T> using V4 = typename Vec4<T>::type;
 template <class T> struct alignas(16) CellGeo {
     T gx[4], gy[4], gz[4];
     T nx[4], ny[4], nz[4];
+    int32_t nbr[4];  // 16-byte aligned: read as one int4 ahead of the record
     T mv;
     int32_t mat;
     uint32_t code;
-    int32_t nbr[4];
 };
 static_assert(sizeof(CellGeo<float>) == 128, "float cell record must be one 128-byte line");
 static_assert(sizeof(CellGeo<double>) % 16 == 0, "double cell record must be 16-byte aligned");
+static_assert(offsetof(CellGeo<float>, nbr) % 16 == 0 && offsetof(CellGeo<double>, nbr) % 16 == 0,
+              "neighbour list must be 16-byte aligned");
 
 // Queue control block.  head/tail live on their own 128-byte lines.
 struct Ctrl {
@@ -477,19 +479,15 @@ __device__ __forceinline__ void issue_geoq(const SweepArgs<T> &A, unsigned char 
 }
 
 // Lane 0: psi rows of the interior inflow neighbours (mask from the task list,
-// neighbours from the staged record) into the stage's upwind slots, in face order.
+// neighbours nb read ahead of the record) into the stage's upwind slots, in face order.
 template <class T>
 __device__ __forceinline__ void issue_up(const SweepArgs<T> &A, unsigned char *st_base, uint64_t *bar, uint32_t mask,
-                                         size_t psi_dir, const StageLayout<T> &L)
+                                         int4 nb4, size_t psi_dir, const StageLayout<T> &L)
 {
-    const CellGeo<T> *g = reinterpret_cast<const CellGeo<T> *>(st_base);
+    const int32_t nb[4] = {nb4.x, nb4.y, nb4.z, nb4.w};
     uint32_t n_up = 0;
-    int32_t nb[4];
 #pragma unroll
-    for (int f = 0; f < 4; ++f) {
-        nb[f] = g->nbr[f];
-        n_up += (((mask >> f) & 1u) && nb[f] >= 0) ? 1u : 0u;
-    }
+    for (int f = 0; f < 4; ++f) n_up += (((mask >> f) & 1u) && nb[f] >= 0) ? 1u : 0u;
     mbar_arrive_expect_tx(bar, n_up * L.row);
     uint32_t slot = 0;
 #pragma unroll
@@ -587,7 +585,10 @@ __device__ __forceinline__ void solve_staged_cell(const SweepArgs<T> &A, const u
 // One task through the staged pipeline.  Stage of cell k = k mod 3; for each
 // stage two mbarriers (geometry+source, upwind rows) whose phase parities are
 // kept in `ph` (bit s: geometry barrier of stage s, bit 3+s: upwind barrier).
-// Returns false if a wait ran out (error word set).
+// Each lane first reads the neighbour list of its cell(s) straight from the
+// records, so every copy of cell k (record, source row, upwind rows) is issued
+// together, two cells ahead of the solve.  Returns false if a wait ran out
+// (error word set).
 template <class T>
 __device__ __forceinline__ bool run_task_staged(const SweepArgs<T> &A, uint4 ti, int lane, T ox, T oy, T oz,
                                                 size_t psi_dir, unsigned char *wsm, uint64_t *bars, uint32_t &ph)
@@ -597,35 +598,37 @@ __device__ __forceinline__ bool run_task_staged(const SweepArgs<T> &A, uint4 ti,
     const StageLayout<T> L(A.G);
     const uint32_t e_lo = lane < (int)ncell ? __ldg(A.cells + ti.x + lane) : 0u;
     const uint32_t e_hi = lane + 32 < (int)ncell ? __ldg(A.cells + ti.x + 32 + lane) : 0u;
-    auto entry = [&](uint32_t k) { return __shfl_sync(FULL, k < 32 ? e_lo : e_hi, k & 31); };
+    int4 n_lo = make_int4(-1, -1, -1, -1), n_hi = n_lo;
+    if (lane < (int)ncell) n_lo = __ldg(reinterpret_cast<const int4 *>(A.geo[e_lo >> 4].nbr));
+    if (lane + 32 < (int)ncell) n_hi = __ldg(reinterpret_cast<const int4 *>(A.geo[e_hi >> 4].nbr));
     // psi rows written by other warps (generic proxy, acquired through the
     // queue) are read here by the async proxy
     if (lane == 0) fence_proxy_async_global();
-    const uint32_t e0 = entry(0);
-    const uint32_t e1 = ncell > 1 ? entry(1) : 0u;
-    if (lane == 0) {
-        issue_geoq(A, wsm, &bars[0], e0 >> 4, L);
-        if (ncell > 1) issue_geoq(A, wsm + L.stage, &bars[1], e1 >> 4, L);
-    }
-    if (!mbar_wait(&bars[0], ph & 1u, A.wait_limit_ns, &A.ctrl->error)) return false;
-    ph ^= 1u;
-    if (lane == 0) issue_up(A, wsm, &bars[3], e0 & 15u, psi_dir, L);
+    auto issue = [&](uint32_t k) {
+        const int src = (int)(k & 31u);
+        const bool hi = k >= 32u;
+        const uint32_t ek = __shfl_sync(FULL, hi ? e_hi : e_lo, src);
+        int4 nb;
+        nb.x = __shfl_sync(FULL, hi ? n_hi.x : n_lo.x, src);
+        nb.y = __shfl_sync(FULL, hi ? n_hi.y : n_lo.y, src);
+        nb.z = __shfl_sync(FULL, hi ? n_hi.z : n_lo.z, src);
+        nb.w = __shfl_sync(FULL, hi ? n_hi.w : n_lo.w, src);
+        if (lane == 0) {
+            const uint32_t s = k % 3u;
+            unsigned char *st = wsm + s * L.stage;
+            fence_proxy_async_shared();  // generic reads of this stage (cell k - 3) before the async writes
+            issue_geoq(A, st, &bars[s], ek >> 4, L);
+            issue_up(A, st, &bars[3 + s], ek & 15u, nb, psi_dir, L);
+        }
+    };
+    issue(0);
+    if (ncell > 1) issue(1);
     for (uint32_t k = 0; k < ncell; ++k) {
         const uint32_t s = k % 3u;
-        const uint32_t ek = entry(k);
-        if (k + 1 < ncell) {
-            const uint32_t s1 = (k + 1) % 3u, en = entry(k + 1);
-            if (!mbar_wait(&bars[s1], (ph >> s1) & 1u, A.wait_limit_ns, &A.ctrl->error)) return false;
-            ph ^= 1u << s1;
-            if (lane == 0) issue_up(A, wsm + s1 * L.stage, &bars[3 + s1], en & 15u, psi_dir, L);
-        }
-        if (k + 2 < ncell) {
-            const uint32_t s2 = (k + 2) % 3u, en2 = entry(k + 2);
-            if (lane == 0) {
-                fence_proxy_async_shared();  // generic reads of this stage (cell k-1) before the async writes
-                issue_geoq(A, wsm + s2 * L.stage, &bars[s2], en2 >> 4, L);
-            }
-        }
+        const uint32_t ek = __shfl_sync(FULL, k < 32 ? e_lo : e_hi, k & 31);
+        if (k + 2 < ncell) issue(k + 2);
+        if (!mbar_wait(&bars[s], (ph >> s) & 1u, A.wait_limit_ns, &A.ctrl->error)) return false;
+        ph ^= 1u << s;
         if (!mbar_wait(&bars[3 + s], (ph >> (3 + s)) & 1u, A.wait_limit_ns, &A.ctrl->error)) return false;
         ph ^= 1u << (3 + s);
         solve_staged_cell(A, wsm + s * L.stage, ek, lane, ox, oy, oz, psi_dir, L);

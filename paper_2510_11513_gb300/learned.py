@@ -86,14 +86,17 @@ def generate(cfgs, tol=1e-6, max_iters=5000, device="cuda", weight_floor=None, *
 class LearnedStart:
     """A network mapping cell features to the initial scalar flux."""
 
-    def __init__(self, n_groups: int, hidden: int = 64, seed: int = 0):
+    def __init__(self, n_groups: int, hidden: int = 64, seed: int = 0, overshoot_weight: float = 1.0):
+        """overshoot_weight > 1 weights overshooting outputs more in the loss, so the
+        network errs low (a start below the answer cannot raise the first change)."""
         self.n_groups = int(n_groups)
         self.net = tf.Mlp(n_features(self.n_groups), hidden, self.n_groups, seed)
+        tf.tf_mlp_limits(self.net.h, kappa=overshoot_weight)
 
     def fit(self, X: torch.Tensor, T: torch.Tensor, W: torch.Tensor | None = None, epochs: int = 20,
             batch: int = 1024, lr: float = 1e-3, seed: int = 0, decay: int = 3, stream=None) -> np.ndarray:
-        """Standardises the targets (mean / standard deviation over T) and trains
-        with Adam, optionally weighted by W; the epochs are split into `decay`
+        """Standardises the targets (mean / standard deviation over T; predictions
+        are capped at the largest target) and trains with Adam, optionally weighted by W; the epochs are split into `decay`
         phases whose learning rate drops by 3x each.  Returns the per-epoch mean loss."""
         if X.shape[0] != T.shape[0] or T.shape[1] != self.n_groups:
             raise ValueError("X and T disagree in samples or groups")

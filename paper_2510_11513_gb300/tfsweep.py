@@ -28,7 +28,7 @@ SYMBOLS = (
     "tf_source_iterate", "tf_destroy", "tf_mesh_geometry", "tf_quadrature_get", "tf_graph_levels",
     "tf_problem_psi", "tf_problem_stats", "tf_status_string", "tf_last_error", "tf_integrated_flux_noalloc",
     # include/tflearn.h
-    "tf_mlp_create", "tf_mlp_params", "tf_mlp_scale", "tf_mlp_fit_scale", "tf_mlp_features", "tf_mlp_targets",
+    "tf_mlp_create", "tf_mlp_params", "tf_mlp_scale", "tf_mlp_limits", "tf_mlp_fit_scale", "tf_mlp_features", "tf_mlp_targets",
     "tf_mlp_weights", "tf_mlp_forward", "tf_mlp_gradients", "tf_mlp_adam_step", "tf_mlp_train", "tf_mlp_predict_phi",
 )
 
@@ -111,6 +111,7 @@ def load(build_if_missing: bool = True):
     lib.tf_mlp_create.argtypes = [i32, i32, i32, u64, C.POINTER(H)]
     lib.tf_mlp_params.argtypes = [H, vp, vp, C.POINTER(i64)]
     lib.tf_mlp_scale.argtypes = [H, fp, fp, fp, fp]
+    lib.tf_mlp_limits.argtypes = [H, fp, fp, fp, fp]
     lib.tf_mlp_fit_scale.argtypes = [H, vp, i64, vp]
     lib.tf_mlp_features.argtypes = [i64, i32, vp, vp, vp, vp, vp, vp, vp]
     lib.tf_mlp_targets.argtypes = [i64, i32, vp, vp, vp]
@@ -329,6 +330,14 @@ def tf_mlp_scale(net, mu=None, sd=None):
     sd_s = None if sd is None else C.byref(C.c_float(sd))
     _check(load().tf_mlp_scale(net, C.byref(mu_g), C.byref(sd_g), mu_s, sd_s), "tf_mlp_scale")
     return mu_g.value, sd_g.value
+
+
+def tf_mlp_limits(net, kappa=None, cap=None):
+    kg, cg = C.c_float(), C.c_float()
+    ks = None if kappa is None else C.byref(C.c_float(kappa))
+    cs = None if cap is None else C.byref(C.c_float(cap))
+    _check(load().tf_mlp_limits(net, C.byref(kg), C.byref(cg), ks, cs), "tf_mlp_limits")
+    return kg.value, cg.value
 
 
 def tf_mlp_fit_scale(net, T, n_values, stream=None):

@@ -97,6 +97,39 @@ def test_weighted_gradients_and_weights_match_oracle():
         k += sz
 
 
+def test_asymmetric_gradients_and_cap_match_oracle():
+    I, H, O, n = 96, 32, 8, 300
+    p, X, T = _net_and_data(I, H, O, n, seed=41)
+    net = _gpu_net(I, H, O, p)
+    mu, sd = -3.0, 2.0
+    net.scale(mu, sd)
+    tf.tf_mlp_limits(net.h, kappa=6.0)
+    g = np.zeros(net.n_params, np.float32)
+    loss = tf.tf_mlp_gradients(net.h, torch.from_numpy(X).to(DEV), torch.from_numpy(T).to(DEV), n, grad=g)
+    L_ref, g_ref = om.gradient(p, X, T, I, H, O, mu, sd, bf16=True, kappa=6.0)
+    assert loss == pytest.approx(L_ref, rel=2e-5)
+    k = 0
+    for sz in [H * I, H, H * H, H, O * H, O]:
+        a, b = g[k:k + sz].astype(np.float64), g_ref[k:k + sz]
+        assert np.abs(a - b).max() <= 1e-4 * np.abs(b).max() + 1e-12, (k, sz)
+        k += sz
+    # fit_scale: mean, deviation and the cap at the largest target
+    Td = torch.from_numpy(T).to(DEV)
+    tf.tf_mlp_fit_scale(net.h, Td, Td.numel())
+    mu2, sd2 = net.scale()
+    kappa, cap = tf.tf_mlp_limits(net.h)
+    m_ref, s_ref = om.fit_scale(T.astype(np.float64))
+    assert mu2 == pytest.approx(m_ref, rel=1e-6) and sd2 == pytest.approx(s_ref, rel=1e-6)
+    assert kappa == 6.0 and cap == float(T.max())
+    phi = torch.empty((n, O, 4), dtype=torch.float64, device=DEV)
+    tf.tf_mlp_predict_phi(net.h, torch.from_numpy(X).to(DEV), n, phi)
+    y, _ = om.forward(p, X, I, H, O, bf16=True)
+    ref = om.predict_phi(y, mu2, sd2, cap=cap)
+    got = phi.cpu().numpy()
+    assert np.all(np.abs(got - ref) <= 2e-5 * np.abs(y).max() * sd2 * (ref + 1e-6) * 1.5 + 1e-300)
+    assert got.max() <= np.exp(cap)
+
+
 def test_adam_step_matches_oracle():
     I, H, O, n = 64, 32, 8, 500
     p, X, T = _net_and_data(I, H, O, n, seed=5)

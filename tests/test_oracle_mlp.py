@@ -295,3 +295,41 @@ def test_weights_are_squared_fraction_of_group_max():
     L1, g1 = om.gradient(p, X, T, I, H, O)
     L2, g2 = om.gradient(p, X, T, I, H, O, W=np.ones((3, O)))
     assert L1 == L2 and np.array_equal(g1, g2)
+
+
+def test_asymmetric_loss_gradient_and_limit():
+    """kappa weights overshoots: central differences still pin the gradient (the
+    loss is C^1 at r = 0), kappa = 1 is the symmetric loss, and a constant fitted
+    to two targets by the asymmetric loss is the kappa-weighted mean (expectile)."""
+    I, H, O, n = 5, 8, 2, 6
+    rng = np.random.default_rng(26)
+    p = _rand_net(I, H, O, 27)
+    X = rng.normal(size=(n, I))
+    T = rng.normal(size=(n, O))
+    _, g = om.gradient(p, X, T, I, H, O, kappa=7.0)
+    h = 1e-6
+    fd = np.array([(om.loss(p + h * e, X, T, I, H, O, kappa=7.0) - om.loss(p - h * e, X, T, I, H, O, kappa=7.0)) / (2 * h)
+                   for e in np.eye(p.size)])
+    assert np.abs(g - fd).max() <= 1e-7 * np.abs(g).max()
+    L1, g1 = om.gradient(p, X, T, I, H, O)
+    L2, g2 = om.gradient(p, X, T, I, H, O, kappa=1.0)
+    assert L1 == L2 and np.array_equal(g1, g2)
+    # a network whose output is its bias b3 (zero W3): minimise over b3 with targets {0, 1}
+    W1, b1, W2, b2, _, _ = om.unpack(p, I, H, O)
+    Xs = np.zeros((2, I))
+    Ts = np.array([[0.0, 0.0], [1.0, 1.0]])
+    kappa = 4.0
+    best = None
+    for c in np.linspace(0.0, 1.0, 10001):
+        q = om.pack(W1, b1, W2, b2, np.zeros((O, H)), np.full(O, c))
+        L = om.loss(q, Xs, Ts, I, H, O, kappa=kappa)
+        if best is None or L < best[0]:
+            best = (L, c)
+    # stationary point: kappa c = (1 - c)  =>  c = 1 / (1 + kappa)
+    assert abs(best[1] - 1.0 / (1.0 + kappa)) < 2e-4
+
+
+def test_prediction_cap():
+    y = np.array([[0.0, 10.0]])
+    out = om.predict_phi(y, 0.0, 1.0, cap=np.log(2.0))
+    np.testing.assert_allclose(out[0, :, 0], [1.0 - 1e-6, 2.0 - 1e-6], rtol=1e-15)
