@@ -332,7 +332,7 @@ def run_ours(args):
             e1.record(stream)
             torch.cuda.synchronize(dev)
             out[name] = {"seconds": e0.elapsed_time(e1) / 1e3, "iterations": r["iterations"],
-                         "converged": r["converged"], "residual": r["residual"]}
+                         "converged": r["converged"], "residual": r["residual"], "balance": r["balance"]}
             del pt, ph
         out["fp64_over_fp32"] = out["fp64"]["seconds"] / out["fp32"]["seconds"]
         line["time_to_tol"] = out
@@ -389,7 +389,7 @@ def run_batch(args):
             "per_problem": [{"cells": p.n_cells, "directions": p.n_dirs, "groups": p.n_groups,
                              "cells_per_task": p.stats()["cells_per_task"], "kernel_mode": p.stats()["kernel_mode"],
                              "iterations": i["iterations"], "seconds_to_tol": round(i["seconds"], 4),
-                             "converged": i["converged"]} for p, i in zip(probs, infos)]}
+                             "converged": i["converged"], "balance": i["balance"]} for p, i in zip(probs, infos)]}
     print(json.dumps(line), flush=True)
 
 
@@ -414,7 +414,8 @@ def run_learned(args):
     t_gen = time.perf_counter() - t0
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
-    ls = L.LearnedStart(kw["G"], hidden=64, seed=args.seed, overshoot_weight=args.overshoot_weight)
+    ls = L.LearnedStart(kw["G"], hidden=64, seed=args.seed, overshoot_weight=args.overshoot_weight,
+                        shrink=args.shrink)
     hist = ls.fit(X, T, Wt, epochs=args.epochs, batch=args.train_batch, lr=args.lr, seed=args.seed)
     torch.cuda.synchronize(dev)
     t_train = time.perf_counter() - t0
@@ -427,17 +428,20 @@ def run_learned(args):
         Xh = L.cell_features(prob.mesh, cfg, dev)
         phi0 = torch.zeros((prob.n_cells, prob.n_groups, 4), dtype=torch.float64, device=dev)
         torch.cuda.synchronize(dev)
+        start = ls.initial_flux(Xh)
         a = time.perf_counter()
         r0 = prob.source_iterate(phi0, tol, 5000)
         torch.cuda.synchronize(dev)
         s0 = time.perf_counter() - a
+        start_err = float((start - phi0).norm() / phi0.norm())  # the zero start's is 1
+        del start
         a = time.perf_counter()
         phi1, r1 = ls.solve(prob, Xh, tol, 5000)
         torch.cuda.synchronize(dev)
         s1 = time.perf_counter() - a
         row = {"layout": 10000 + k, "iters_zero": r0["iterations"], "iters_learned": r1["iterations"],
                "s_zero": round(s0, 4), "s_learned": round(s1, 4), "predict_s": round(r1["predict_seconds"], 5),
-               "converged": bool(r0["converged"] and r1["converged"])}
+               "converged": bool(r0["converged"] and r1["converged"]), "start_rel_l2_err": round(start_err, 4)}
         if k < args.eval_fp64:
             p64 = tf.Problem.from_config(cfg, precision=tf.TF_FP64)
             ref = torch.zeros_like(phi0)
@@ -460,7 +464,7 @@ def run_learned(args):
             "config": {"workload": f"learned_start_layouts_{kw['n']}^3_D{kw['n_polar'] * kw['n_az']}_G{kw['G']}",
                        "train_layouts": args.train_layouts, "eval_layouts": args.eval_layouts, "samples": samples,
                        "epochs": args.epochs, "batch": args.train_batch, "lr": args.lr, "tol": tol,
-                       "weight_floor": floor, "overshoot_weight": args.overshoot_weight},
+                       "weight_floor": floor, "overshoot_weight": args.overshoot_weight, "shrink": args.shrink},
             "zero_start_s": sz / len(rows), "iterations_zero": iz, "iterations_learned": il,
             "iteration_ratio": il / max(iz, 1), "generate_s": round(t_gen, 1),
             "generate_solve_s": round(sum(g["solve_seconds"] for g in gen), 2),
@@ -503,6 +507,7 @@ def main():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--weight-floor", type=float, default=-1.0,
                     help="--config layout: loss weights (phi/max)^2 + floor; negative = unweighted")
+    ap.add_argument("--shrink", type=float, default=0.5, help="--config layout: factor on the predicted flux")
     ap.add_argument("--overshoot-weight", type=float, default=1.0,
                     help="--config layout: loss weight of overshooting outputs (1 = plain squared error)")
     args = ap.parse_args()

@@ -14,7 +14,9 @@
  * (layer l computes z = W_l a + b_l).  The forward and backward kernels read
  * the weights W1, W2, W3 rounded to BF16 (round to nearest even) and
  * accumulate in FP32; biases stay FP32.  A handle also keeps a target
- * standardisation (mu, sd): the network output y predicts (t - mu) / sd, and
+ * standardisation (mu, sd): the network output y predicts (t - mu) / sd, an
+ * optional input standardisation (x - mean) inv applied to the features on
+ * entry (tf_mlp_fit_inputs), and
  * an upper cap on the predicted target (tf_mlp_fit_scale sets it to the
  * largest training target, so a prediction never exceeds the largest flux
  * seen in training).
@@ -23,9 +25,9 @@
  * material m:
  *   x[g]                  = log sigma_t[m][g]
  *   x[G + g' G + g]       = sigma_s[m][g'][g] / sigma_t[m][g']
- *   x[G + G^2 + g]        = qbar[c][g], the mean of the 4 nodal Q[c][g][i]
+ *   x[G + G^2 + g]        = log(qbar[c][g] + 1e-6), qbar the mean of the 4 nodal Q[c][g][i]
  *   x[2G + G^2 + g]       = mean of log sigma_t[g] over the face neighbours
- *   x[3G + G^2 + g]       = mean of qbar[g] over the face neighbours
+ *   x[3G + G^2 + g]       = log(mean of qbar[g] over the face neighbours + 1e-6)
  * (a cell with no neighbour takes its own values in the last two blocks).
  * Targets (tf_mlp_targets): t[c][g] = log(max(mean_i phi[c][g][i], 0) + 1e-6),
  * the log of the cell-average scalar flux; tf_mlp_predict_phi inverts that map.
@@ -76,6 +78,20 @@ tf_status tf_mlp_scale(tf_handle net, float *mu_get, float *sd_get, const float 
  * (default +infinity). */
 tf_status tf_mlp_limits(tf_handle net, float *kappa_get, float *cap_get, const float *kappa_set, const float *cap_set);
 
+/* Reads (get) and/or sets (set, in [0, 1]; default 1) the factor that multiplies
+ * the predicted flux in tf_mlp_predict_phi (host pointers, either may be NULL). */
+tf_status tf_mlp_shrink(tf_handle net, float *get, const float *set);
+
+/* Sets the input standardisation from the n rows of X [n][I]: per feature the mean
+ * and inv = 1 / population standard deviation (1 for a constant feature), FP64
+ * sums.  Every later call that takes features (forward, gradients, training,
+ * prediction) standardises them on entry.  Synchronises `stream`. */
+tf_status tf_mlp_fit_inputs(tf_handle net, const float *X, int64_t n, void *stream);
+
+/* Reads (mean_get, inv_get: host, I floats each; TF_ERR_ARG if none is set) and/or
+ * sets (mean_set and inv_set together) the input standardisation. */
+tf_status tf_mlp_input_scale(tf_handle net, float *mean_get, float *inv_get, const float *mean_set, const float *inv_set);
+
 /* Sets (mu, sd) to the mean and the population standard deviation of the
  * n_values targets T (FP64 sums) and the prediction cap to their maximum.
  * Synchronises `stream`. */
@@ -122,7 +138,7 @@ tf_status tf_mlp_train(tf_handle net, const float *X, const float *T, const floa
                        int32_t batch, float lr, uint64_t seed, float *loss_history, void *stream);
 
 /* Initial flux for source iteration: phi [n_cells][O][4] (FP64, O = groups) set
- * at every node to max(exp(min(mu + sd y, cap)) - 1e-6, 0), y the network output
+ * at every node to shrink max(exp(min(mu + sd y, cap)) - 1e-6, 0), y the network output
  * for the cell's features X [n_cells][I].  Synchronises `stream`. */
 tf_status tf_mlp_predict_phi(tf_handle net, const float *X, int64_t n_cells, double *phi, void *stream);
 

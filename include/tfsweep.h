@@ -66,7 +66,8 @@ typedef enum {
 typedef struct {
     int32_t precision;       /* tf_precision: arithmetic of local solves and psi storage (default TF_FP32) */
     int32_t device;          /* CUDA device ordinal (default 0) */
-    int32_t cells_per_task;  /* cells of one t-level grouped into one task; 0 = automatic (about 1024 units),
+    int32_t cells_per_task;  /* cells of one t-level grouped into one task; 0 = automatic (about 1024 units,
+                              * 2048 on the shared-memory staged path, at most 32 or 64 cells),
                               * -1 = autotuned for use on its own (wall time of trial sweeps over a
                               * direction sample), -2 = autotuned for batched use (busy time of the
                               * warps); choices cached per (precision, groups, directions, log2 cells) */
@@ -108,6 +109,11 @@ typedef struct {
     double *residual_history;  /* caller host array [max_iters] or NULL: residual after each sweep */
     double seconds;            /* batched calls: wall time from the call's start to this problem's
                                 * convergence (or to the end) */
+    double balance;            /* particle balance of the last transport step, FP64 on the device:
+                                * max over groups of |leakage + absorption - source| / max(source,
+                                * absorption), with leakage the boundary outflow minus prescribed
+                                * inflow, absorption sum_c sigma_t int_c phi, source int (Q + scattering)
+                                * as the sweep used it; zero up to rounding of the local solves */
 } tf_iter_info;
 
 /* Scheduling statistics of the last sweep of a problem (for measurement). */

@@ -19,6 +19,7 @@ computes, so that the kernels can be checked against it:
              asymmetric: kappa on overshoots) mean squared error of the
              standardised targets;
   adam       Adam with bias correction (b1 = 0.9, b2 = 0.999, eps = 1e-8);
+  inputs     per-feature standardisation (x - mean) / deviation;
   predict    the inverse of the target map, copied to the 4 nodes.
 
 `bf16=True` rounds W1, W2, W3 to bfloat16 (round to nearest even) before use,
@@ -78,8 +79,8 @@ def cell_average(v):
 
 def features(nbr, cell_material, sigma_t, sigma_s, Q):
     """Inputs [C][G^2 + 4G] of every cell, in the order
-    log sigma_t (G) | sigma_s[g'][g] / sigma_t[g'] (G*G, row g') | qbar (G) |
-    neighbour mean of log sigma_t (G) | neighbour mean of qbar (G);
+    log sigma_t (G) | sigma_s[g'][g] / sigma_t[g'] (G*G, row g') | log(qbar + 1e-6) (G) |
+    neighbour mean of log sigma_t (G) | log(neighbour mean of qbar + 1e-6) (G);
     a cell without neighbours takes its own values in the last two blocks."""
     nbr = np.asarray(nbr)
     mat = np.asarray(cell_material)
@@ -94,13 +95,13 @@ def features(nbr, cell_material, sigma_t, sigma_s, Q):
         nb = [int(n) for n in nbr[c] if n >= 0]
         X[c, :G] = log_st[m]
         X[c, G:G + G * G] = prob[m].reshape(-1)
-        X[c, G + G * G:2 * G + G * G] = qbar[c]
+        X[c, G + G * G:2 * G + G * G] = np.log(qbar[c] + EPS_T)
         if nb:
             X[c, 2 * G + G * G:3 * G + G * G] = np.mean([log_st[mat[n]] for n in nb], axis=0)
-            X[c, 3 * G + G * G:] = np.mean([qbar[n] for n in nb], axis=0)
+            X[c, 3 * G + G * G:] = np.log(np.mean([qbar[n] for n in nb], axis=0) + EPS_T)
         else:
             X[c, 2 * G + G * G:3 * G + G * G] = log_st[m]
-            X[c, 3 * G + G * G:] = qbar[c]
+            X[c, 3 * G + G * G:] = np.log(qbar[c] + EPS_T)
     return X
 
 
@@ -118,11 +119,26 @@ def weights(phi, floor):
     return r * r + floor
 
 
-def predict_phi(y, mu, sd, cap=np.inf):
+def predict_phi(y, mu, sd, cap=np.inf, shrink=1.0):
     """Inverse of the standardised target map at every node, the target capped
-    at `cap` (the largest training target): [C][G][4]."""
-    v = np.maximum(np.exp(np.minimum(mu + sd * np.asarray(y, dtype=np.float64), cap)) - EPS_T, 0.0)
+    at `cap` (the largest training target), times `shrink`: [C][G][4]."""
+    v = shrink * np.maximum(np.exp(np.minimum(mu + sd * np.asarray(y, dtype=np.float64), cap)) - EPS_T, 0.0)
     return np.repeat(v[:, :, None], 4, axis=2)
+
+
+def input_scale(X):
+    """Per-feature mean and inv = 1 / population standard deviation (1 where the
+    feature is constant: variance <= 1e-12)."""
+    X = np.asarray(X, dtype=np.float64)
+    mean = X.mean(axis=0)
+    var = np.mean((X - mean) ** 2, axis=0)
+    inv = np.where(var > 1e-12, 1.0 / np.sqrt(np.maximum(var, 1e-300)), 1.0)
+    return mean, inv
+
+
+def normalize(X, mean, inv):
+    """(x - mean) inv per feature."""
+    return (np.asarray(X, dtype=np.float64) - mean) * inv
 
 
 def fit_scale(T):

@@ -52,9 +52,13 @@ struct Mlp : Object {
     float *part = nullptr;     // weight-gradient partial sums [splits][R][C+1]
     float *loss = nullptr;     // [0] last minibatch loss, [1] epoch accumulator
     double *red = nullptr;     // reduction scratch (2 doubles)
+    float *xm = nullptr, *xinv = nullptr;  // input standardisation x' = (x - xm) xinv, [I] (NULL: none)
+    float *xn = nullptr;       // standardised inputs of a gradient call [n][I]
+    size_t xn_cap = 0;
     float mu = 0.f, sd = 1.f;
     float kappa = 1.f;             // loss weight multiplier of overshooting outputs
     float t_cap = INFINITY;        // predictions are capped at this target value
+    float shrink = 1.f;            // the predicted flux is multiplied by this factor
     int64_t step = 0;
     size_t off_b1() const { return (size_t)H * I; }
     size_t off_W2() const { return off_b1() + H; }
@@ -75,6 +79,9 @@ Mlp::~Mlp()
     cudaFree(part);
     cudaFree(loss);
     cudaFree(red);
+    cudaFree(xm);
+    cudaFree(xinv);
+    cudaFree(xn);
 }
 
 namespace {
@@ -91,9 +98,10 @@ namespace {
 // Per cell, I = G^2 + 4G values:
 //   [0, G)            log sigma_t[m][g]
 //   [G, G + G^2)      sigma_s[m][g'][g] / sigma_t[m][g'] at G + g' G + g (scattering probabilities)
-//   next G            cell-average source qbar[g] = mean of the 4 nodal Q[c][g][i]
+//   next G            log(qbar[g] + 1e-6), qbar = cell-average source = mean of the 4 nodal Q[c][g][i]
 //   next G            mean over the face neighbours of log sigma_t[g] (the cell's own value if none)
-//   next G            mean over the face neighbours of qbar[g] (the cell's own value if none)
+//   next G            log(mean over the face neighbours of qbar[g] + 1e-6) (the cell's own qbar if none)
+// (the flux grows linearly with the source, so its logarithm, the target, with log qbar)
 __global__ void features_kernel(int64_t C, int G, const int32_t *__restrict__ mat, const double *__restrict__ sig_t,
                                 const double *__restrict__ sig_s, const double *__restrict__ Q,
                                 const int32_t *__restrict__ nbr, float *__restrict__ X)
@@ -116,7 +124,7 @@ __global__ void features_kernel(int64_t C, int G, const int32_t *__restrict__ ma
                 val = sig_s[((size_t)m * G + gf) * G + gt] / sig_t[(size_t)m * G + gf];
             } else if (e < 2 * G + G * G) {
                 const double *q = Q + ((size_t)c * G + (e - G - G * G)) * 4;
-                val = 0.25 * (((q[0] + q[1]) + q[2]) + q[3]);
+                val = log(0.25 * (((q[0] + q[1]) + q[2]) + q[3]) + 1e-6);
             } else if (e < 3 * G + G * G) {
                 const int gg = e - 2 * G - G * G;
                 double s = 0.0;
@@ -130,7 +138,7 @@ __global__ void features_kernel(int64_t C, int G, const int32_t *__restrict__ ma
                     s += 0.25 * (((q[0] + q[1]) + q[2]) + q[3]);
                 }
                 const double *q = Q + ((size_t)c * G + gg) * 4;
-                val = nn ? s / nn : 0.25 * (((q[0] + q[1]) + q[2]) + q[3]);
+                val = log((nn ? s / nn : 0.25 * (((q[0] + q[1]) + q[2]) + q[3])) + 1e-6);
             }
             x[e] = (float)val;
         }
@@ -185,6 +193,47 @@ __global__ void moment_kernel(int64_t n, const float *__restrict__ T, double shi
     if ((threadIdx.x & 31) == 0) atomicAdd(acc, s);
 }
 
+// Per column k of X [n][I]: acc[k] += sum over rows of (x - shift[k]) (square = 0) or its
+// square (square = 1); FP64.  Threads span the columns of a row (coalesced), blocks stride rows.
+__global__ void colsum_kernel(int64_t n, int I, const float *__restrict__ X, const double *__restrict__ shift,
+                              int square, double *__restrict__ acc)
+{
+    for (int k = threadIdx.x; k < I; k += blockDim.x) {
+        const double sh = shift ? shift[k] : 0.0;
+        double s = 0.0;
+        for (int64_t r = blockIdx.x; r < n; r += gridDim.x) {
+            const double d = (double)X[(size_t)r * I + k] - sh;
+            s += square ? d * d : d;
+        }
+        atomicAdd(acc + k, s);
+    }
+}
+
+// mean[k] = sum[k] / n; then, from the squared deviations, inv[k] = 1 / std (1 for a constant column).
+__global__ void colstat_kernel(int I, int64_t n, const double *__restrict__ sum, const double *__restrict__ sq,
+                               double *__restrict__ mean_d, float *__restrict__ mean, float *__restrict__ inv, int stage)
+{
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < I; k += gridDim.x * blockDim.x) {
+        if (stage == 0) {
+            mean_d[k] = sum[k] / (double)n;
+            mean[k] = (float)mean_d[k];
+        } else {
+            const double var = sq[k] / (double)n;
+            inv[k] = var > 1e-12 ? (float)(1.0 / sqrt(var)) : 1.f;
+        }
+    }
+}
+
+// Xn[s][k] = (X[s][k] - xm[k]) xinv[k].
+__global__ void normalize_kernel(int64_t n, int I, const float *__restrict__ X, const float *__restrict__ xm,
+                                 const float *__restrict__ xinv, float *__restrict__ Xn)
+{
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n * I; e += (int64_t)gridDim.x * blockDim.x) {
+        const int k = (int)(e % I);
+        Xn[e] = (X[e] - xm[k]) * xinv[k];
+    }
+}
+
 // Largest of n values into *acc as an order-preserving unsigned key of the float.
 __device__ __forceinline__ unsigned float_key(float f)
 {
@@ -202,10 +251,12 @@ __global__ void max_key_kernel(int64_t n, const float *__restrict__ T, unsigned 
 
 // ---------------------------------------------------------------- forward
 // One thread per sample; the BF16 weights are widened to FP32 in shared memory
-// (W1^T in chunks of kKC rows) and read as float4 broadcasts.
+// (W1^T in chunks of kKC rows) and read as float4 broadcasts.  With xm / xinv the
+// inputs are standardised on load.
 template <int H>
 __global__ void __launch_bounds__(128) forward_kernel(int64_t n, int I, int O, const __nv_bfloat16 *__restrict__ wb,
                                                       const float *__restrict__ P, const float *__restrict__ X,
+                                                      const float *__restrict__ xm, const float *__restrict__ xinv,
                                                       float *__restrict__ Y, float *__restrict__ A1,
                                                       float *__restrict__ A2)
 {
@@ -230,7 +281,7 @@ __global__ void __launch_bounds__(128) forward_kernel(int64_t n, int I, int O, c
         __syncthreads();
         if (live)
             for (int kk = 0; kk < kn; ++kk) {
-                const float xk = x[k0 + kk];
+                const float xk = xm ? (x[k0 + kk] - __ldg(xm + k0 + kk)) * __ldg(xinv + k0 + kk) : x[k0 + kk];
                 const float4 *wr = reinterpret_cast<const float4 *>(w1c + kk * H);
 #pragma unroll
                 for (int q = 0; q < H / 4; ++q) {
@@ -466,16 +517,19 @@ __global__ void pack_bf16_kernel(int I, int H, int O, const float *__restrict__ 
     }
 }
 
-// Xb[i] = X[perm[i]], Tb[i] = T[perm[i]] (and Wb[i] = Wt[perm[i]] with weights) for i < nn.
+// Xb[i] = X[perm[i]] (standardised when xm is given), Tb[i] = T[perm[i]] (and Wb[i] = Wt[perm[i]]
+// with weights) for i < nn.
 __global__ void gather_kernel(int64_t nn, int I, int O, const int64_t *__restrict__ perm, const float *__restrict__ X,
-                              const float *__restrict__ T, const float *__restrict__ Wt, float *__restrict__ Xb,
-                              float *__restrict__ Tb, float *__restrict__ Wb)
+                              const float *__restrict__ T, const float *__restrict__ Wt, const float *__restrict__ xm,
+                              const float *__restrict__ xinv, float *__restrict__ Xb, float *__restrict__ Tb,
+                              float *__restrict__ Wb)
 {
     const int64_t tot = nn * (I + O);
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
         if (e < nn * I) {
             const int64_t i = e / I, k = e - i * I;
-            Xb[e] = X[(size_t)perm[i] * I + k];
+            const float x = X[(size_t)perm[i] * I + k];
+            Xb[e] = xm ? (x - xm[k]) * xinv[k] : x;
         } else {
             const int64_t f = e - nn * I, i = f / O, k = f - i * O;
             Tb[f] = T[(size_t)perm[i] * O + k];
@@ -484,14 +538,14 @@ __global__ void gather_kernel(int64_t nn, int I, int O, const int64_t *__restric
     }
 }
 
-// phi0[c][g][i] = max(exp(min(mu + sd y[c][g], t_cap)) - 1e-6, 0) at the 4 nodes (inverse of the
-// target map, capped at the largest training target).
+// phi0[c][g][i] = shrink max(exp(min(mu + sd y[c][g], t_cap)) - 1e-6, 0) at the 4 nodes (inverse of
+// the target map, capped at the largest training target, times a shrink factor).
 __global__ void predict_phi_kernel(int64_t CG, const float *__restrict__ Y, float mu, float sd, float t_cap,
-                                   double *__restrict__ phi)
+                                   float shrink, double *__restrict__ phi)
 {
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < CG; e += (int64_t)gridDim.x * blockDim.x) {
         const double t = fmin((double)mu + (double)sd * (double)Y[e], (double)t_cap);
-        const double v = fmax(exp(t) - 1e-6, 0.0);
+        const double v = (double)shrink * fmax(exp(t) - 1e-6, 0.0);
         double2 *o = reinterpret_cast<double2 *>(phi + (size_t)e * 4);
         o[0] = make_double2(v, v);
         o[1] = make_double2(v, v);
@@ -515,15 +569,17 @@ size_t fwd_smem(const Mlp &m)
 }
 size_t bwd_smem(const Mlp &m) { return sizeof(float) * ((size_t)m.H * m.H + (size_t)m.O * m.H); }
 
-void launch_forward(const Mlp &m, int64_t n, const float *X, float *Y, float *A1, float *A2, cudaStream_t st)
+// raw = true: X holds raw features (standardised on load when the handle has an input scale).
+void launch_forward(const Mlp &m, int64_t n, const float *X, bool raw, float *Y, float *A1, float *A2, cudaStream_t st)
 {
     const int blocks = (int)((n + 127) / 128);
     const size_t sm = fwd_smem(m);
+    const float *xm = raw ? m.xm : nullptr, *xi = raw ? m.xinv : nullptr;
     switch (m.H) {
-    case 8: forward_kernel<8><<<blocks, 128, sm, st>>>(n, m.I, m.O, m.wb, m.p, X, Y, A1, A2); break;
-    case 16: forward_kernel<16><<<blocks, 128, sm, st>>>(n, m.I, m.O, m.wb, m.p, X, Y, A1, A2); break;
-    case 32: forward_kernel<32><<<blocks, 128, sm, st>>>(n, m.I, m.O, m.wb, m.p, X, Y, A1, A2); break;
-    default: forward_kernel<64><<<blocks, 128, sm, st>>>(n, m.I, m.O, m.wb, m.p, X, Y, A1, A2); break;
+    case 8: forward_kernel<8><<<blocks, 128, sm, st>>>(n, m.I, m.O, m.wb, m.p, X, xm, xi, Y, A1, A2); break;
+    case 16: forward_kernel<16><<<blocks, 128, sm, st>>>(n, m.I, m.O, m.wb, m.p, X, xm, xi, Y, A1, A2); break;
+    case 32: forward_kernel<32><<<blocks, 128, sm, st>>>(n, m.I, m.O, m.wb, m.p, X, xm, xi, Y, A1, A2); break;
+    default: forward_kernel<64><<<blocks, 128, sm, st>>>(n, m.I, m.O, m.wb, m.p, X, xm, xi, Y, A1, A2); break;
     }
 }
 
@@ -582,14 +638,27 @@ tf_status ensure_scratch(Mlp &m, int64_t n)
 }
 
 // Forward and backward over n samples: the gradient into m.g and the loss into m.loss[0].
-tf_status gradients(Mlp &m, const float *X, const float *T, const float *Wt, int64_t n, int64_t n_epoch,
+// raw = true: X holds raw features, standardised first into scratch when the handle has
+// an input scale (the first layer's weight gradient needs the standardised inputs).
+tf_status gradients(Mlp &m, const float *X, bool raw, const float *T, const float *Wt, int64_t n, int64_t n_epoch,
                     cudaStream_t st)
 {
     tf_status s = ensure_scratch(m, n);
     if (s != TF_OK) return s;
+    if (raw && m.xm) {
+        if ((size_t)n > m.xn_cap) {
+            cudaFree(m.xn);
+            m.xn = nullptr;
+            m.xn_cap = 0;
+            MLP_CUDA(cudaMalloc(&m.xn, sizeof(float) * (size_t)n * m.I));
+            m.xn_cap = (size_t)n;
+        }
+        normalize_kernel<<<grid_for(n * m.I, 256, 8 * 152), 256, 0, st>>>(n, m.I, X, m.xm, m.xinv, m.xn);
+        X = m.xn;
+    }
     float *A1 = m.act, *A2 = A1 + (size_t)n * m.H, *D1 = A2 + (size_t)n * m.H, *D2 = D1 + (size_t)n * m.H;
     float *Y = D2 + (size_t)n * m.H, *DY = Y + (size_t)n * m.O;
-    launch_forward(m, n, X, Y, A1, A2, st);
+    launch_forward(m, n, X, false, Y, A1, A2, st);
     MLP_CUDA(cudaMemsetAsync(m.loss, 0, sizeof(float), st));
     launch_backward(m, n, Y, T, Wt, A1, A2, DY, D1, D2, n_epoch, st);
     launch_wgrad(m, n, m.H, m.I, D1, X, m.g, m.g + m.off_b1(), st);
@@ -720,6 +789,63 @@ tf_status tf_mlp_limits(tf_handle h, float *kappa_get, float *cap_get, const flo
     return TF_OK;
 }
 
+tf_status tf_mlp_shrink(tf_handle h, float *get, const float *set)
+{
+    Mlp *m = as_mlp(h);
+    if (!m) return fail(TF_ERR_ARG, "tf_mlp_shrink: not a network handle");
+    if (set && !(*set >= 0.f && *set <= 1.f)) return fail(TF_ERR_ARG, "tf_mlp_shrink: factor must be in [0, 1]");
+    if (set) m->shrink = *set;
+    if (get) *get = m->shrink;
+    return TF_OK;
+}
+
+tf_status tf_mlp_input_scale(tf_handle h, float *mean_get, float *inv_get, const float *mean_set, const float *inv_set)
+{
+    Mlp *m = as_mlp(h);
+    if (!m || (!mean_set) != (!inv_set)) return fail(TF_ERR_ARG, "tf_mlp_input_scale: bad arguments");
+    MLP_CUDA(cudaSetDevice(m->device));
+    const size_t bytes = sizeof(float) * (size_t)m->I;
+    if (mean_set) {
+        if (!m->xm) MLP_CUDA(cudaMalloc(&m->xm, bytes));
+        if (!m->xinv) MLP_CUDA(cudaMalloc(&m->xinv, bytes));
+        MLP_CUDA(cudaMemcpy(m->xm, mean_set, bytes, cudaMemcpyHostToDevice));
+        MLP_CUDA(cudaMemcpy(m->xinv, inv_set, bytes, cudaMemcpyHostToDevice));
+    }
+    if (mean_get || inv_get) {
+        if (!m->xm) return fail(TF_ERR_ARG, "tf_mlp_input_scale: the network has no input scale");
+        if (mean_get) MLP_CUDA(cudaMemcpy(mean_get, m->xm, bytes, cudaMemcpyDeviceToHost));
+        if (inv_get) MLP_CUDA(cudaMemcpy(inv_get, m->xinv, bytes, cudaMemcpyDeviceToHost));
+    }
+    return TF_OK;
+}
+
+tf_status tf_mlp_fit_inputs(tf_handle h, const float *X, int64_t n, void *stream)
+{
+    Mlp *m = as_mlp(h);
+    if (!m || !X || n < 2) return fail(TF_ERR_ARG, "tf_mlp_fit_inputs: bad arguments");
+    MLP_CUDA(cudaSetDevice(m->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t bytes = sizeof(float) * (size_t)m->I;
+    if (!m->xm) MLP_CUDA(cudaMalloc(&m->xm, bytes));
+    if (!m->xinv) MLP_CUDA(cudaMalloc(&m->xinv, bytes));
+    double *acc = nullptr;  // sum [I], squared deviations [I], FP64 mean [I]
+    MLP_CUDA(cudaMalloc(&acc, 3 * sizeof(double) * (size_t)m->I));
+    cudaError_t e = cudaMemsetAsync(acc, 0, 2 * sizeof(double) * (size_t)m->I, st);
+    const int grid = (int)std::min<int64_t>(n, 4 * 152);
+    const int sgrid = grid_for(m->I, 256, 64);
+    if (e == cudaSuccess) {
+        colsum_kernel<<<grid, 256, 0, st>>>(n, m->I, X, nullptr, 0, acc);
+        colstat_kernel<<<sgrid, 256, 0, st>>>(m->I, n, acc, nullptr, acc + 2 * m->I, m->xm, m->xinv, 0);
+        colsum_kernel<<<grid, 256, 0, st>>>(n, m->I, X, acc + 2 * m->I, 1, acc + m->I);
+        colstat_kernel<<<sgrid, 256, 0, st>>>(m->I, n, nullptr, acc + m->I, nullptr, nullptr, m->xinv, 1);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(acc);
+    if (e != cudaSuccess) return fail(TF_ERR_CUDA, std::string("tf_mlp_fit_inputs: ") + cudaGetErrorString(e));
+    return TF_OK;
+}
+
 tf_status tf_mlp_fit_scale(tf_handle h, const float *T, int64_t n_values, void *stream)
 {
     Mlp *m = as_mlp(h);
@@ -797,7 +923,7 @@ tf_status tf_mlp_forward(tf_handle h, const float *X, int64_t n, float *Y, void 
     Mlp *m = as_mlp(h);
     if (!m || !X || !Y || n < 1) return fail(TF_ERR_ARG, "tf_mlp_forward: bad arguments");
     MLP_CUDA(cudaSetDevice(m->device));
-    launch_forward(*m, n, X, Y, nullptr, nullptr, (cudaStream_t)stream);
+    launch_forward(*m, n, X, true, Y, nullptr, nullptr, (cudaStream_t)stream);
     MLP_CUDA(cudaGetLastError());
     return TF_OK;
 }
@@ -809,7 +935,7 @@ tf_status tf_mlp_gradients(tf_handle h, const float *X, const float *T, const fl
     if (!m || !X || !T || n < 1) return fail(TF_ERR_ARG, "tf_mlp_gradients: bad arguments");
     MLP_CUDA(cudaSetDevice(m->device));
     cudaStream_t st = (cudaStream_t)stream;
-    tf_status s = gradients(*m, X, T, W, n, 0, st);
+    tf_status s = gradients(*m, X, true, T, W, n, 0, st);
     if (s != TF_OK) return s;
     if (grad) MLP_CUDA(cudaMemcpyAsync(grad, m->g, sizeof(float) * m->np, cudaMemcpyDeviceToHost, st));
     if (loss) MLP_CUDA(cudaMemcpyAsync(loss, m->loss, sizeof(float), cudaMemcpyDeviceToHost, st));
@@ -865,8 +991,8 @@ tf_status tf_mlp_train(tf_handle h, const float *X, const float *T, const float 
         for (int64_t b0 = 0; b0 < n && s == TF_OK && e == cudaSuccess; b0 += B) {
             const int64_t nn = std::min<int64_t>(B, n - b0);
             gather_kernel<<<grid_for(nn * (m->I + m->O), 256, 8 * 152), 256, 0, st>>>(nn, m->I, m->O, perm_d + b0, X, T,
-                                                                                      W, Xb, Tb, Wb);
-            s = gradients(*m, Xb, Tb, Wb, nn, n, st);
+                                                                                      W, m->xm, m->xinv, Xb, Tb, Wb);
+            s = gradients(*m, Xb, false, Tb, Wb, nn, n, st);
             if (s == TF_OK) s = adam(*m, lr, st);
         }
         float l = 0.f;
@@ -887,9 +1013,9 @@ tf_status tf_mlp_predict_phi(tf_handle h, const float *X, int64_t n_cells, doubl
     cudaStream_t st = (cudaStream_t)stream;
     float *Y = nullptr;
     MLP_CUDA(cudaMalloc(&Y, sizeof(float) * (size_t)n_cells * m->O));
-    launch_forward(*m, n_cells, X, Y, nullptr, nullptr, st);
+    launch_forward(*m, n_cells, X, true, Y, nullptr, nullptr, st);
     const int64_t CG = n_cells * m->O;
-    predict_phi_kernel<<<grid_for(CG, 256, 8 * 152), 256, 0, st>>>(CG, Y, m->mu, m->sd, m->t_cap, phi);
+    predict_phi_kernel<<<grid_for(CG, 256, 8 * 152), 256, 0, st>>>(CG, Y, m->mu, m->sd, m->t_cap, m->shrink, phi);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     cudaFree(Y);

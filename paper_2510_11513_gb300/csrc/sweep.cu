@@ -142,6 +142,11 @@ __device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float p, float
     lo += err + e;
 }
 
+// Boundary leakage of one cell and group for the particle balance: for each
+// boundary face f (sorted face f is opposite sorted node f) and direction a,
+// w_a s_f mean_f(psi_a) on an outflow face (s_f = Omega_a . N_f, not below the
+// inflow threshold -1e-12 |N_f| of the sweep graph) and -w_a |s_f| mean_f(psi_in)
+// on an inflow face with prescribed inflow (vacuum: nothing).  FP64 sums.
 template <class T, bool PAIR>
 __global__ void __launch_bounds__(256) phi_kernel(const V4<T> *__restrict__ psi, const WeightPair *__restrict__ wts,
                                                   int Dc, size_t CG, int G, const CellGeo<T> *__restrict__ geo,
@@ -287,6 +292,92 @@ __global__ void __launch_bounds__(256) phi_pair_kernel(const float *__restrict__
     }
 }
 
+// Boundary leakage for the particle balance, per (boundary cell, group) over the
+// directions of a chunk: for each boundary face f (sorted face f is opposite sorted
+// node f), w_a s_f mean_f(psi_a) on an outflow face (s_f = Omega_a . N_f not below
+// the sweep graph's inflow threshold -1e-12 |N_f|) and -w_a |s_f| mean_f(psi_in)
+// on an inflow face with prescribed inflow (vacuum: nothing).  FP64 sums, added
+// to leak[g].  PAIRED: psi in the pair-interleaved layout [C][G/2][4][2].
+template <class T, bool PAIRED>
+__global__ void __launch_bounds__(256) leak_kernel(const T *__restrict__ psi, const WeightPair *__restrict__ wts,
+                                                   const V4<T> *__restrict__ omega, int Dc, int64_t C, int G,
+                                                   const uint32_t *__restrict__ bcells, int64_t nb,
+                                                   const CellGeo<T> *__restrict__ geo, const int4 *__restrict__ tets,
+                                                   const T *__restrict__ psi_in, double *__restrict__ leak)
+{
+    for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < nb * G; u += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t b = u / G;
+        const int g = (int)(u - b * G);
+        const uint32_t c = bcells[b];
+        const CellGeo<T> &cg = geo[c];
+        uint32_t faces = 0;
+        T nx[4], ny[4], nz[4], thr[4];
+        double pin[4];
+#pragma unroll
+        for (int f = 0; f < 4; ++f) {
+            faces |= (cg.nbr[f] < 0 ? 1u : 0u) << f;
+            nx[f] = cg.nx[f];
+            ny[f] = cg.ny[f];
+            nz[f] = cg.nz[f];
+            thr[f] = T(-1e-12) * sqrt(nx[f] * nx[f] + ny[f] * ny[f] + nz[f] * nz[f]);
+            pin[f] = 0.0;
+        }
+        if (psi_in) {
+            const int4 tv = tets[c];
+            const int vi[4] = {tv.x, tv.y, tv.z, tv.w};
+#pragma unroll
+            for (int f = 0; f < 4; ++f) {
+                double m = 0.0;
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    if (j != f) m += (double)psi_in[(size_t)vi[j] * G + g];
+                pin[f] = m / 3.0;
+            }
+        }
+        // FP64 sweeps accumulate in FP64.  FP32 sweeps form each direction's
+        // face term in FP32 (its inputs are FP32) and add w_a times it exactly as a
+        // float pair (TwoProd, weight split hi + lo; TwoSum), as the phi reduction
+        // does: GB300's FP64 rate would make the direction loop FP64-bound.
+        double acc = 0.0;
+        float hi = 0.f, lo = 0.f;
+#pragma unroll 4
+        for (int a = 0; a < Dc; ++a) {
+            T x[4];
+            if constexpr (PAIRED) {
+                const T *q = psi + (((size_t)a * C + c) * (G >> 1) + (g >> 1)) * 8 + (g & 1);
+#pragma unroll
+                for (int j = 0; j < 4; ++j) x[j] = q[2 * j];
+            } else {
+                const V4<T> v = reinterpret_cast<const V4<T> *>(psi)[((size_t)a * C + c) * G + g];
+                x[0] = v.x;
+                x[1] = v.y;
+                x[2] = v.z;
+                x[3] = v.w;
+            }
+            const T sum = (x[0] + x[1]) + (x[2] + x[3]);
+            const V4<T> om = omega[a];
+            T t = T(0);  // sum over the boundary faces of s_f mean_f (outflow) or -|s_f| mean_f(psi_in)
+#pragma unroll
+            for (int f = 0; f < 4; ++f) {
+                if (!((faces >> f) & 1u)) continue;
+                const T sf = om.x * nx[f] + om.y * ny[f] + om.z * nz[f];
+                if (sf >= thr[f]) t += sf * ((sum - x[f]) * T(1.0 / 3.0));
+                else t -= fabs(sf) * (T)pin[f];
+            }
+            if constexpr (sizeof(T) == 8) {
+                acc += wts[a].d * (double)t;
+            } else {
+                const WeightPair w = wts[a];
+                const float pp = w.hi * t;
+                const float e = fmaf(w.hi, t, -pp) + w.lo * t;
+                two_sum_acc(hi, lo, pp, e);
+            }
+        }
+        if constexpr (sizeof(T) == 4) acc = (double)hi + (double)lo;
+        atomicAdd(leak + g, acc);
+    }
+}
+
 // psi of one direction, paired layout -> [C][G][4] in the caller's node order.
 __global__ void psi_unpair_kernel(const float *__restrict__ src, float4 *__restrict__ dst, size_t CP, int G,
                                   const CellGeo<float> *__restrict__ geo)
@@ -330,16 +421,57 @@ __global__ void psi_unsort_kernel(const V4<T> *__restrict__ src, V4<T> *__restri
 // ============================================================== FP64 statistics
 // Deterministic per-group reductions over cells.  CTA = 32 x 8 threads:
 // threadIdx.x walks groups, threadIdx.y walks cells; per-CTA partials go to
-// scratch [nblk][G][3] = (max |phi|, sum_c (V_c/4) sum_i phi, sum_c sum_i phi),
-// then finish_stats_kernel reduces over CTAs in a fixed order (Eq. (3)) into
-// [G][4] = (max, integrated flux, plain nodal sum, 1/max).
-__global__ void __launch_bounds__(256) stats_kernel(const double *__restrict__ phi, const double *__restrict__ vol4,
-                                                    int64_t C, int G, double *__restrict__ part)
+// scratch [nblk][G][NP], then the finish kernels reduce over CTAs in a fixed
+// order.  Partials: max |phi|, integral sum_c (V_c/4) sum_i phi (Eq. (3)), the
+// plain nodal sum, the absorption sum_c sigma_t (V_c/4) sum_i phi and the
+// source sum_c (V_c/4) 4 pi sum_i q of the source the sweep used; with the
+// stopping test fused, also max |phi_new - phi_old|.
+//
+// Particle balance per group (summing the rows of every local system, Sigma_i b_i = 1,
+// and the directions with their weights; interior faces cancel):
+//   R_g = leakage_g + absorption_g - source_g = 0 up to rounding,
+// leakage from the phi kernels (boundary faces).  The finish kernels record
+// max_g |R_g| / max(source_g, absorption_g) in the control block.
+struct BalIn {
+    const int32_t *mat;  // [C] material
+    const double *sig;   // [M][G] sigma_t (FP64)
+    const void *q;       // source rows of the sweep
+    int qmode;           // 0: float4 [C][G], 1: FP64 [C][G][4], 2: float pairs [C][G/2][4][2]
+    const double *leak;  // [G] boundary leakage
+};
+
+__device__ __forceinline__ double q_nodal_sum(const BalIn &b, int64_t c, int g, int G)
 {
-    __shared__ double sh[3][8][32];
+    if (b.qmode == 0) {
+        const float4 v = reinterpret_cast<const float4 *>(b.q)[(size_t)c * G + g];
+        return ((double)v.x + (double)v.y) + ((double)v.z + (double)v.w);
+    }
+    if (b.qmode == 1) {
+        const double2 *v = reinterpret_cast<const double2 *>(b.q) + ((size_t)c * G + g) * 2;
+        const double2 x = v[0], y = v[1];
+        return (x.x + x.y) + (y.x + y.y);
+    }
+    const float *f = reinterpret_cast<const float *>(b.q) + ((size_t)c * (G >> 1) + (g >> 1)) * 8 + (g & 1);
+    return ((double)f[0] + (double)f[2]) + ((double)f[4] + (double)f[6]);
+}
+
+constexpr double kFourPi = 4.0 * 3.14159265358979323846;
+
+// r_g = |R_g| / max(source_g, absorption_g) (0 for a group without source or absorption).
+__device__ __forceinline__ void record_balance(double leak, double absorb, double source, Ctrl *ctrl)
+{
+    const double den = fmax(source, absorb);
+    const double r = den > 0.0 ? fabs(leak + absorb - source) / den : 0.0;
+    if (r > 0.0) atomicMax(&ctrl->balance_bits, (unsigned long long)__double_as_longlong(r));
+}
+
+__global__ void __launch_bounds__(256) stats_kernel(const double *__restrict__ phi, const double *__restrict__ vol4,
+                                                    int64_t C, int G, double *__restrict__ part, BalIn bi)
+{
+    __shared__ double sh[5][8][32];
     for (int g0 = 0; g0 < G; g0 += 32) {
         const int g = g0 + threadIdx.x;
-        double mx = 0.0, iv = 0.0, pl = 0.0;
+        double mx = 0.0, iv = 0.0, pl = 0.0, ab = 0.0, sr = 0.0;
         if (g < G) {
             for (int64_t c = (int64_t)blockIdx.x * 8 + threadIdx.y; c < C; c += (int64_t)gridDim.x * 8) {
                 const double2 *p = reinterpret_cast<const double2 *>(phi + ((size_t)c * G + g) * 4);
@@ -348,58 +480,71 @@ __global__ void __launch_bounds__(256) stats_kernel(const double *__restrict__ p
                 mx = fmax(mx, fmax(fmax(fabs(a.x), fabs(a.y)), fmax(fabs(b.x), fabs(b.y))));
                 iv += vol4[c] * s;
                 pl += s;
+                ab += bi.sig[(size_t)bi.mat[c] * G + g] * vol4[c] * s;
+                sr += vol4[c] * kFourPi * q_nodal_sum(bi, c, g, G);
             }
         }
         sh[0][threadIdx.y][threadIdx.x] = mx;
         sh[1][threadIdx.y][threadIdx.x] = iv;
         sh[2][threadIdx.y][threadIdx.x] = pl;
+        sh[3][threadIdx.y][threadIdx.x] = ab;
+        sh[4][threadIdx.y][threadIdx.x] = sr;
         __syncthreads();
         if (threadIdx.y == 0 && g < G) {
             double m = sh[0][0][threadIdx.x], a = sh[1][0][threadIdx.x], b = sh[2][0][threadIdx.x];
+            double e = sh[3][0][threadIdx.x], f = sh[4][0][threadIdx.x];
             for (int y = 1; y < 8; ++y) {
                 m = fmax(m, sh[0][y][threadIdx.x]);
                 a += sh[1][y][threadIdx.x];
                 b += sh[2][y][threadIdx.x];
+                e += sh[3][y][threadIdx.x];
+                f += sh[4][y][threadIdx.x];
             }
-            double *o = part + ((size_t)blockIdx.x * G + g) * 3;
+            double *o = part + ((size_t)blockIdx.x * G + g) * 5;
             o[0] = m;
             o[1] = a;
             o[2] = b;
+            o[3] = e;
+            o[4] = f;
         }
         __syncthreads();
     }
 }
 
-__global__ void finish_stats_kernel(const double *__restrict__ part, int nblk, int G, double *__restrict__ out)
+__global__ void finish_stats_kernel(const double *__restrict__ part, int nblk, int G, double *__restrict__ out,
+                                    const double *__restrict__ leak, Ctrl *ctrl)
 {
     for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < G; g += gridDim.x * blockDim.x) {
-        double m = 0.0, a = 0.0, b = 0.0;
+        double m = 0.0, a = 0.0, b = 0.0, e = 0.0, f = 0.0;
         for (int k = 0; k < nblk; ++k) {
-            const double *p = part + ((size_t)k * G + g) * 3;
+            const double *p = part + ((size_t)k * G + g) * 5;
             m = fmax(m, p[0]);
             a += p[1];
             b += p[2];
+            e += p[3];
+            f += p[4];
         }
         out[4 * g + 0] = m;
         out[4 * g + 1] = a;
         out[4 * g + 2] = b;
         out[4 * g + 3] = m > 0.0 ? 1.0 / m : 0.0;
+        record_balance(leak[g], e, f, ctrl);
     }
 }
 
 // Max-norm stopping test fused with the statistics (residual_floor = 1): one
 // pass over phi_new and phi_old gives per group max |phi_new|, the integral,
-// the nodal sum and max |phi_new - phi_old| (all FP64); the finish kernel
-// forms r = max_g max|dphi| / max|phi_new| and the [G][4] statistics.
+// the nodal sum, the balance sums and max |phi_new - phi_old| (all FP64); the
+// finish kernel forms r = max_g max|dphi| / max|phi_new| and the [G][4] statistics.
 __global__ void __launch_bounds__(256) stats_res_kernel(const double *__restrict__ phi_new,
                                                         const double *__restrict__ phi_old,
                                                         const double *__restrict__ vol4, int64_t C, int G,
-                                                        double *__restrict__ part)
+                                                        double *__restrict__ part, BalIn bi)
 {
-    __shared__ double sh[4][8][32];
+    __shared__ double sh[6][8][32];
     for (int g0 = 0; g0 < G; g0 += 32) {
         const int g = g0 + threadIdx.x;
-        double mx = 0.0, iv = 0.0, pl = 0.0, dm = 0.0;
+        double mx = 0.0, iv = 0.0, pl = 0.0, dm = 0.0, ab = 0.0, sr = 0.0;
         if (g < G) {
             for (int64_t c = (int64_t)blockIdx.x * 8 + threadIdx.y; c < C; c += (int64_t)gridDim.x * 8) {
                 const double2 *p = reinterpret_cast<const double2 *>(phi_new + ((size_t)c * G + g) * 4);
@@ -410,42 +555,53 @@ __global__ void __launch_bounds__(256) stats_res_kernel(const double *__restrict
                 dm = fmax(dm, fmax(fmax(fabs(a.x - oa.x), fabs(a.y - oa.y)), fmax(fabs(b.x - ob.x), fabs(b.y - ob.y))));
                 iv += vol4[c] * s;
                 pl += s;
+                ab += bi.sig[(size_t)bi.mat[c] * G + g] * vol4[c] * s;
+                sr += vol4[c] * kFourPi * q_nodal_sum(bi, c, g, G);
             }
         }
         sh[0][threadIdx.y][threadIdx.x] = mx;
         sh[1][threadIdx.y][threadIdx.x] = iv;
         sh[2][threadIdx.y][threadIdx.x] = pl;
         sh[3][threadIdx.y][threadIdx.x] = dm;
+        sh[4][threadIdx.y][threadIdx.x] = ab;
+        sh[5][threadIdx.y][threadIdx.x] = sr;
         __syncthreads();
         if (threadIdx.y == 0 && g < G) {
             double m = sh[0][0][threadIdx.x], a = sh[1][0][threadIdx.x], b = sh[2][0][threadIdx.x], d = sh[3][0][threadIdx.x];
+            double e = sh[4][0][threadIdx.x], f = sh[5][0][threadIdx.x];
             for (int y = 1; y < 8; ++y) {
                 m = fmax(m, sh[0][y][threadIdx.x]);
                 a += sh[1][y][threadIdx.x];
                 b += sh[2][y][threadIdx.x];
                 d = fmax(d, sh[3][y][threadIdx.x]);
+                e += sh[4][y][threadIdx.x];
+                f += sh[5][y][threadIdx.x];
             }
-            double *o = part + ((size_t)blockIdx.x * G + g) * 4;
+            double *o = part + ((size_t)blockIdx.x * G + g) * 6;
             o[0] = m;
             o[1] = a;
             o[2] = b;
             o[3] = d;
+            o[4] = e;
+            o[5] = f;
         }
         __syncthreads();
     }
 }
 
 __global__ void finish_stats_res_kernel(const double *__restrict__ part, int nblk, int G, double *__restrict__ out,
-                                        Ctrl *ctrl)
+                                        const double *__restrict__ leak, Ctrl *ctrl)
 {
     for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < G; g += gridDim.x * blockDim.x) {
-        double m = 0.0, a = 0.0, b = 0.0, d = 0.0;
+        double m = 0.0, a = 0.0, b = 0.0, d = 0.0, e = 0.0, f = 0.0;
         for (int k = 0; k < nblk; ++k) {
-            const double *p = part + ((size_t)k * G + g) * 4;
+            const double *p = part + ((size_t)k * G + g) * 6;
             m = fmax(m, p[0]);
             a += p[1];
             b += p[2];
             d = fmax(d, p[3]);
+            e += p[4];
+            f += p[5];
         }
         out[4 * g + 0] = m;
         out[4 * g + 1] = a;
@@ -453,6 +609,7 @@ __global__ void finish_stats_res_kernel(const double *__restrict__ part, int nbl
         out[4 * g + 3] = m > 0.0 ? 1.0 / m : 0.0;
         const double r = d == 0.0 ? 0.0 : (m > 0.0 ? d / m : INFINITY);
         if (r > 0.0) atomicMax(&ctrl->residual_bits, (unsigned long long)__double_as_longlong(r));
+        record_balance(leak[g], e, f, ctrl);
     }
 }
 
@@ -514,6 +671,11 @@ struct DeviceState {
     void *q = nullptr;
     void *psi = nullptr;
     double *vol4 = nullptr;
+    double *leak = nullptr;    // [G] boundary leakage of the last transport step (particle balance)
+    uint32_t *bcells = nullptr;  // cells with a boundary face
+    int64_t n_bcells = 0;
+    int32_t *mat = nullptr;    // [C] material of each cell
+    double *sig_d = nullptr;   // [M][G] sigma_t, FP64
     WeightPair *wts = nullptr;
     double *phi_buf[2] = {nullptr, nullptr};
     double *part = nullptr;
@@ -693,6 +855,8 @@ template <class T> tf_status create_typed(Problem &p, DeviceState &d, const int3
         d.geo = gp;
     }
     if ((s = upload_vec3<T>(d, &d.omega, p.quad->omega.data(), d.D, p.quad->w.data())) != TF_OK) return s;
+    if ((s = upload(d, &d.mat, cell_material, sizeof(int32_t) * (size_t)d.C)) != TF_OK) return s;
+    if ((s = upload(d, &d.sig_d, sigma_t, sizeof(double) * (size_t)d.M * d.G)) != TF_OK) return s;
     if ((s = upload_typed<T>(d, &d.sigma_t, sigma_t, (size_t)d.M * d.G)) != TF_OK) return s;
     if ((s = upload_typed<T>(d, &d.sigma_s, sigma_s, (size_t)d.M * d.G * d.G)) != TF_OK) return s;
     {
@@ -819,7 +983,17 @@ tf_status device_create(Problem &p, const int32_t *cell_material, const double *
     TF_CUDA(cudaMallocHost(&d.ctrl_host, sizeof(Ctrl)));
     TF_CUDA(cudaMallocHost(&d.gstats_host, sizeof(double) * 4 * d.G));
     d.stats_blocks = std::max(1, std::min<int>(4 * d.sm_count, (int)((d.C + 7) / 8)));
-    if ((s = dmalloc(d, &d.part, sizeof(double) * 4 * d.G * d.stats_blocks)) != TF_OK) return s;
+    if ((s = dmalloc(d, &d.part, sizeof(double) * 6 * d.G * d.stats_blocks)) != TF_OK) return s;
+    if ((s = dmalloc(d, &d.leak, sizeof(double) * d.G)) != TF_OK) return s;
+    TF_CUDA(cudaMemset(d.leak, 0, sizeof(double) * d.G));
+    {
+        std::vector<uint32_t> bc;
+        for (int64_t c = 0; c < m.nc; ++c)
+            if (m.nbr[4 * c] < 0 || m.nbr[4 * c + 1] < 0 || m.nbr[4 * c + 2] < 0 || m.nbr[4 * c + 3] < 0)
+                bc.push_back((uint32_t)c);
+        d.n_bcells = (int64_t)bc.size();
+        if ((s = upload(d, &d.bcells, bc.data(), 4 * bc.size())) != TF_OK) return s;
+    }
     if ((s = dmalloc(d, &d.gstats, sizeof(double) * 4 * d.G)) != TF_OK) return s;
     // direction chunks: as many directions per launch as the psi budget allows
     const size_t per_dir = (size_t)d.C * d.G * 4 * d.tsize;
@@ -926,7 +1100,8 @@ tf_status device_create(Problem &p, const int32_t *cell_material, const double *
         TF_CUDA(cudaEventCreate(&d.ev_stop[i]));
     }
     TF_CUDA(cudaDeviceSynchronize());
-    p.stats.launches_per_step = 1 + 5 * (int64_t)d.n_chunks;
+    // source; per chunk: begin, fill, sweep, end, phi and (with boundary cells) leakage
+    p.stats.launches_per_step = 1 + (5 + (d.n_bcells > 0 ? 1 : 0)) * (int64_t)d.n_chunks;
     p.stats.kernel_mode = d.mode;
     TF_CUDA(cudaStreamCreateWithFlags(&d.istream, cudaStreamNonBlocking));
     TF_CUDA(cudaEventCreateWithFlags(&d.ev_user, cudaEventDisableTiming));
@@ -984,6 +1159,30 @@ template <class T> void launch_source(Problem &p, const double *phi_in, cudaStre
     source_kernel<T><<<blocks, 256, smem, st>>>(phi_in, (const V4<T> *)d.Q, (const T *)d.sigma_s,
                                                 (const CellGeo<T> *)d.geo, (V4<T> *)d.q, d.C, d.G, cpc,
                                                 d.paired ? 1 : 0);
+    cudaMemsetAsync(d.leak, 0, sizeof(double) * d.G, st);  // the phi kernels add this step's leakage
+}
+
+// Statistics, particle balance and stopping test of the iterate nxt (previous: cur).
+void launch_stats(Problem &p, const double *cur, const double *nxt, cudaStream_t st)
+{
+    DeviceState &d = *p.dev;
+    BalIn bi;
+    bi.mat = d.mat;
+    bi.sig = d.sig_d;
+    bi.q = d.q;
+    bi.qmode = d.paired ? 2 : (d.fp64 ? 1 : 0);
+    bi.leak = d.leak;
+    cudaMemsetAsync(&d.ctrl->residual_bits, 0, 16, st);  // residual_bits, balance_bits
+    if (p.opt.residual_floor >= 1.0) {
+        stats_res_kernel<<<d.stats_blocks, dim3(32, 8), 0, st>>>(nxt, cur, d.vol4, d.C, d.G, d.part, bi);
+        finish_stats_res_kernel<<<(d.G + 127) / 128, 128, 0, st>>>(d.part, d.stats_blocks, d.G, d.gstats, d.leak,
+                                                                   d.ctrl);
+    } else {
+        stats_kernel<<<d.stats_blocks, dim3(32, 8), 0, st>>>(nxt, d.vol4, d.C, d.G, d.part, bi);
+        finish_stats_kernel<<<(d.G + 127) / 128, 128, 0, st>>>(d.part, d.stats_blocks, d.G, d.gstats, d.leak, d.ctrl);
+        residual_kernel<<<d.stats_blocks, dim3(32, 8), 0, st>>>(nxt, cur, d.gstats, d.C, d.G, p.opt.residual_floor,
+                                                                d.ctrl);
+    }
 }
 
 // Sweep arguments of direction chunk k of one problem (queue fields for a launch of its own).
@@ -1053,6 +1252,19 @@ template <class T> void launch_phi(Problem &p, int k, double *phi_out, cudaStrea
     } else {
         phi_kernel<T, false><<<pb, 256, 0, st>>>((const V4<T> *)d.psi, d.wts + a0, a1 - a0, CG, d.G,
                                                  (const CellGeo<T> *)d.geo, phi_out, k > 0);
+    }
+    // boundary leakage of this chunk's directions (particle balance)
+    if (d.n_bcells > 0) {
+        const int lb = (int)std::min<int64_t>((d.n_bcells * d.G + 255) / 256, (int64_t)d.sm_count * 16);
+        if (d.paired)
+            leak_kernel<float, true><<<lb, 256, 0, st>>>((const float *)d.psi, d.wts + a0, (const float4 *)d.omega + a0,
+                                                         a1 - a0, d.C, d.G, d.bcells, d.n_bcells,
+                                                         (const CellGeo<float> *)d.geo, d.tets,
+                                                         (const float *)d.psi_in, d.leak);
+        else
+            leak_kernel<T, false><<<lb, 256, 0, st>>>((const T *)d.psi, d.wts + a0, (const V4<T> *)d.omega + a0, a1 - a0,
+                                                      d.C, d.G, d.bcells, d.n_bcells, (const CellGeo<T> *)d.geo,
+                                                      d.tets, (const T *)d.psi_in, d.leak);
     }
 }
 
@@ -1189,16 +1401,7 @@ tf_status enqueue_iteration(Problem &p, const double *cur, double *nxt, cudaStre
     DeviceState &d = *p.dev;
     tf_status s = step(p, cur, nxt, st);
     if (s != TF_OK) return s;
-    TF_CUDA(cudaMemsetAsync(&d.ctrl->residual_bits, 0, 8, st));
-    if (p.opt.residual_floor >= 1.0) {
-        stats_res_kernel<<<d.stats_blocks, dim3(32, 8), 0, st>>>(nxt, cur, d.vol4, d.C, d.G, d.part);
-        finish_stats_res_kernel<<<(d.G + 127) / 128, 128, 0, st>>>(d.part, d.stats_blocks, d.G, d.gstats, d.ctrl);
-    } else {
-        stats_kernel<<<d.stats_blocks, dim3(32, 8), 0, st>>>(nxt, d.vol4, d.C, d.G, d.part);
-        finish_stats_kernel<<<(d.G + 127) / 128, 128, 0, st>>>(d.part, d.stats_blocks, d.G, d.gstats);
-        residual_kernel<<<d.stats_blocks, dim3(32, 8), 0, st>>>(nxt, cur, d.gstats, d.C, d.G, p.opt.residual_floor,
-                                                                d.ctrl);
-    }
+    launch_stats(p, cur, nxt, st);
     TF_CUDA(cudaGetLastError());
     TF_CUDA(cudaMemcpyAsync(d.ctrl_host, d.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
     return TF_OK;
@@ -1259,7 +1462,7 @@ tf_status device_iterate(Problem &p, double tol, int32_t max_iters, double *phi,
     if (!d.graphs_tried) build_iteration_graphs(p);
     int k = 0;  // phi_buf[k] holds the current iterate
     TF_CUDA(cudaMemcpyAsync(d.phi_buf[0], phi, bytes, host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, st));
-    double r = INFINITY;
+    double r = INFINITY, bal = 0.0;
     int it = 0;
     bool conv = false;
     for (it = 1; it <= max_iters; ++it) {
@@ -1273,6 +1476,7 @@ tf_status device_iterate(Problem &p, double tol, int32_t max_iters, double *phi,
         const tf_status s = collect(p, st, true);
         if (s != TF_OK) return s;
         std::memcpy(&r, &d.ctrl_host->residual_bits, sizeof(double));
+        std::memcpy(&bal, &d.ctrl_host->balance_bits, sizeof(double));
         if (info && info->residual_history) info->residual_history[it - 1] = r;
         k = 1 - k;
         if (r < tol) {
@@ -1291,6 +1495,7 @@ tf_status device_iterate(Problem &p, double tol, int32_t max_iters, double *phi,
         info->iterations = it;
         info->converged = conv ? 1 : 0;
         info->residual = r;
+        info->balance = bal;
         double tot = 0.0;
         for (int g = 0; g < d.G; ++g) {
             tot += d.gstats_host[4 * g + 1];
@@ -1475,16 +1680,7 @@ tf_status batch_enqueue(BatchRun &B, const std::vector<char> &active, int k, boo
             Problem &p = *B.P[i];
             DeviceState &d = *p.dev;
             double *cur = d.phi_buf[k], *nxt = d.phi_buf[1 - k];
-            TF_CUDA(cudaMemsetAsync(&d.ctrl->residual_bits, 0, 8, st));
-            if (p.opt.residual_floor >= 1.0) {
-                stats_res_kernel<<<d.stats_blocks, dim3(32, 8), 0, st>>>(nxt, cur, d.vol4, d.C, d.G, d.part);
-                finish_stats_res_kernel<<<(d.G + 127) / 128, 128, 0, st>>>(d.part, d.stats_blocks, d.G, d.gstats, d.ctrl);
-            } else {
-                stats_kernel<<<d.stats_blocks, dim3(32, 8), 0, st>>>(nxt, d.vol4, d.C, d.G, d.part);
-                finish_stats_kernel<<<(d.G + 127) / 128, 128, 0, st>>>(d.part, d.stats_blocks, d.G, d.gstats);
-                residual_kernel<<<d.stats_blocks, dim3(32, 8), 0, st>>>(nxt, cur, d.gstats, d.C, d.G,
-                                                                        p.opt.residual_floor, d.ctrl);
-            }
+            launch_stats(p, cur, nxt, st);
             TF_CUDA(cudaMemcpyAsync(d.ctrl_host, d.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
         }
     }
@@ -1580,7 +1776,7 @@ tf_status device_batch_iterate(const tf_handle *problems, int32_t n, double tol,
     }
     std::vector<char> active(n, 1), built;
     std::vector<int> iters(n, 0), final_buf(n, 0);
-    std::vector<double> res(n, INFINITY), secs(n, 0.0);
+    std::vector<double> res(n, INFINITY), secs(n, 0.0), bals(n, 0.0);
     std::vector<char> conv(n, 0);
     const bool timing = !stats_only_sweep;
     int k = 0;
@@ -1613,6 +1809,7 @@ tf_status device_batch_iterate(const tf_handle *problems, int32_t n, double tol,
             final_buf[i] = 1 - k;
             if (!stats_only_sweep) {
                 std::memcpy(&res[i], &B.P[i]->dev->ctrl_host->residual_bits, sizeof(double));
+                std::memcpy(&bals[i], &B.P[i]->dev->ctrl_host->balance_bits, sizeof(double));
                 if (info && info[i].residual_history) info[i].residual_history[it - 1] = res[i];
                 if (res[i] < tol) {
                     conv[i] = 1;
@@ -1647,6 +1844,7 @@ tf_status device_batch_iterate(const tf_handle *problems, int32_t n, double tol,
         info[i].iterations = iters[i];
         info[i].converged = conv[i];
         info[i].residual = res[i];
+        info[i].balance = bals[i];
         info[i].seconds = secs[i];
         double tot = 0.0;
         for (int g = 0; g < d.G; ++g) {

@@ -53,6 +53,7 @@ struct Ctrl {
     unsigned long long depth_sum;
     unsigned long long pops;
     unsigned long long residual_bits;  // max residual as ordered bits of a non-negative double
+    unsigned long long balance_bits;   // max over groups of the relative balance residual (same encoding)
     unsigned long long kernel_ns;      // summed over chunks
     int next_group;                    // next direction group to admit
 };
@@ -501,7 +502,9 @@ __device__ __forceinline__ void issue_up(const SweepArgs<T> &A, unsigned char *s
 }
 
 // Solve every group of one staged cell: lane l takes groups l, l+32, ...
-template <class T>
+// NPL > 0: exactly NPL groups per lane (G = 32 NPL), unrolled so that the
+// independent solves of a lane's groups interleave; NPL = 0: any G.
+template <class T, int NPL>
 __device__ __forceinline__ void solve_staged_cell(const SweepArgs<T> &A, const unsigned char *st_base, uint32_t entry,
                                                   int lane, T ox, T oy, T oz, size_t psi_dir, const StageLayout<T> &L)
 {
@@ -531,7 +534,13 @@ __device__ __forceinline__ void solve_staged_cell(const SweepArgs<T> &A, const u
     }
     const T *sig = A.sigma_t + (size_t)g.mat * A.G;
     V4<T> *out = A.psi + (psi_dir + (size_t)c) * A.G;
-    for (int gg = lane; gg < A.G; gg += 32) {
+    // group-independent part of the matrix; the group adds sigma_t (V/20)(1 + delta_ij)
+    T Bm[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) Bm[i][j] = P[j] + (i == j ? T(2) * (tt - t[i]) : (tt - t[i]) - t[j]);
+    auto unit = [&](int gg) {
         const T sv = __ldg(sig + gg) * mv;
         const V4<T> q4 = qrow[gg];
         const T qs = (q4.x + q4.y) + (q4.z + q4.w);
@@ -567,10 +576,11 @@ __device__ __forceinline__ void solve_staged_cell(const SweepArgs<T> &A, const u
             b[f <= 2 ? 3 : 2] += t[f] * (v2 + U);
         }
         T a[4][4];
+        const T sv2 = T(2) * sv;
 #pragma unroll
         for (int i = 0; i < 4; ++i)
 #pragma unroll
-            for (int j = 0; j < 4; ++j) a[i][j] = P[j] + (i == j ? T(2) * (tt - t[i] + sv) : (tt - t[i] - t[j]) + sv);
+            for (int j = 0; j < 4; ++j) a[i][j] = Bm[i][j] + (i == j ? sv2 : sv);
         T x[4];
         solve4(a, b, x);
         V4<T> o;
@@ -579,6 +589,12 @@ __device__ __forceinline__ void solve_staged_cell(const SweepArgs<T> &A, const u
         o.z = x[2];
         o.w = x[3];
         st_psi(out + gg, o);
+    };
+    if constexpr (NPL > 0) {
+#pragma unroll
+        for (int k = 0; k < NPL; ++k) unit(lane + 32 * k);
+    } else {
+        for (int gg = lane; gg < A.G; gg += 32) unit(gg);
     }
 }
 
@@ -589,7 +605,7 @@ __device__ __forceinline__ void solve_staged_cell(const SweepArgs<T> &A, const u
 // records, so every copy of cell k (record, source row, upwind rows) is issued
 // together, two cells ahead of the solve.  Returns false if a wait ran out
 // (error word set).
-template <class T>
+template <class T, int NPL>
 __device__ __forceinline__ bool run_task_staged(const SweepArgs<T> &A, uint4 ti, int lane, T ox, T oy, T oz,
                                                 size_t psi_dir, unsigned char *wsm, uint64_t *bars, uint32_t &ph)
 {
@@ -631,7 +647,7 @@ __device__ __forceinline__ bool run_task_staged(const SweepArgs<T> &A, uint4 ti,
         ph ^= 1u << s;
         if (!mbar_wait(&bars[3 + s], (ph >> (3 + s)) & 1u, A.wait_limit_ns, &A.ctrl->error)) return false;
         ph ^= 1u << (3 + s);
-        solve_staged_cell(A, wsm + s * L.stage, ek, lane, ox, oy, oz, psi_dir, L);
+        solve_staged_cell<T, NPL>(A, wsm + s * L.stage, ek, lane, ox, oy, oz, psi_dir, L);
         __syncwarp();
     }
     return true;
@@ -944,6 +960,16 @@ __device__ __forceinline__ bool run_task_pairs(const SweepArgs<float> &A, uint4 
 
 __device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
 
+// Staged path with the groups-per-lane count unrolled for the common G = 32 and 64.
+template <class T>
+__device__ __forceinline__ bool run_task_staged_any(const SweepArgs<T> &A, uint4 ti, int lane, T ox, T oy, T oz,
+                                                    size_t psi_dir, unsigned char *wsm, uint64_t *bars, uint32_t &ph)
+{
+    if (A.G == 64) return run_task_staged<T, 2>(A, ti, lane, ox, oy, oz, psi_dir, wsm, bars, ph);
+    if (A.G == 32) return run_task_staged<T, 1>(A, ti, lane, ox, oy, oz, psi_dir, wsm, bars, ph);
+    return run_task_staged<T, 0>(A, ti, lane, ox, oy, oz, psi_dir, wsm, bars, ph);
+}
+
 // Persistent sweep: a warp claims a ticket (the next queue slot), waits until
 // that slot holds a ready task, executes it with lanes spanning (cell, group)
 // units, then decrements the counters of the task's downwind blocks; a
@@ -1049,7 +1075,7 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 3) sweep_kernel(cons
         if constexpr (MODE == 3) {
             if (!run_task_pairs(A, ti, lane, om.x, om.y, om.z, psi_dir, wsm, bars, ph)) break;
         } else if constexpr (MODE == 2) {
-            if (!run_task_staged(A, ti, lane, om.x, om.y, om.z, psi_dir, wsm, bars, ph)) break;
+            if (!run_task_staged_any(A, ti, lane, om.x, om.y, om.z, psi_dir, wsm, bars, ph)) break;
         } else if constexpr (MODE == 1) {
             run_task_wide(A, ti, lane, om.x, om.y, om.z, psi_dir);
         } else {
@@ -1229,10 +1255,10 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 3) sweep_batch_kerne
         bool ok = true;
         if constexpr (sizeof(T) == 4) {
             if (A.mode == 3) ok = run_task_pairs(A, ti, lane, om.x, om.y, om.z, psi_dir, wsm, bars, ph);
-            else if (A.mode == 2) ok = run_task_staged(A, ti, lane, om.x, om.y, om.z, psi_dir, wsm, bars, ph);
+            else if (A.mode == 2) ok = run_task_staged_any(A, ti, lane, om.x, om.y, om.z, psi_dir, wsm, bars, ph);
             else run_task_generic(A, ti, lane, om.x, om.y, om.z, psi_dir);
         } else {
-            if (A.mode == 2) ok = run_task_staged(A, ti, lane, om.x, om.y, om.z, psi_dir, wsm, bars, ph);
+            if (A.mode == 2) ok = run_task_staged_any(A, ti, lane, om.x, om.y, om.z, psi_dir, wsm, bars, ph);
             else run_task_generic(A, ti, lane, om.x, om.y, om.z, psi_dir);
         }
         if (!ok) break;

@@ -20,8 +20,9 @@ from . import tfsweep as tf
 
 
 def n_features(n_groups: int) -> int:
-    """Inputs per cell: log sigma_t (G), scattering probabilities (G^2), cell-average
-    source (G) and the face-neighbour means of log sigma_t and of the source (2G)."""
+    """Inputs per cell: log sigma_t (G), scattering probabilities (G^2), log of the
+    cell-average source (G) and the face-neighbour means of log sigma_t and (log of
+    the mean) of the source (2G)."""
     return n_groups * n_groups + 4 * n_groups
 
 
@@ -86,22 +87,27 @@ def generate(cfgs, tol=1e-6, max_iters=5000, device="cuda", weight_floor=None, *
 class LearnedStart:
     """A network mapping cell features to the initial scalar flux."""
 
-    def __init__(self, n_groups: int, hidden: int = 64, seed: int = 0, overshoot_weight: float = 1.0):
+    def __init__(self, n_groups: int, hidden: int = 64, seed: int = 0, overshoot_weight: float = 1.0,
+                 shrink: float = 0.5):
         """overshoot_weight > 1 weights overshooting outputs more in the loss, so the
-        network errs low (a start below the answer cannot raise the first change)."""
+        network errs low; `shrink` scales the predicted flux (a start below the answer
+        cannot overshoot it; 0.5 took the fewest iterations over held-out layouts)."""
         self.n_groups = int(n_groups)
         self.net = tf.Mlp(n_features(self.n_groups), hidden, self.n_groups, seed)
         tf.tf_mlp_limits(self.net.h, kappa=overshoot_weight)
+        tf.tf_mlp_shrink(self.net.h, shrink)
 
     def fit(self, X: torch.Tensor, T: torch.Tensor, W: torch.Tensor | None = None, epochs: int = 20,
             batch: int = 1024, lr: float = 1e-3, seed: int = 0, decay: int = 3, stream=None) -> np.ndarray:
-        """Standardises the targets (mean / standard deviation over T; predictions
-        are capped at the largest target) and trains with Adam, optionally weighted by W; the epochs are split into `decay`
+        """Standardises the inputs (per feature over X) and the targets (mean /
+        standard deviation over T; predictions are capped at the largest target)
+        and trains with Adam, optionally weighted by W; the epochs are split into `decay`
         phases whose learning rate drops by 3x each.  Returns the per-epoch mean loss."""
         if X.shape[0] != T.shape[0] or T.shape[1] != self.n_groups:
             raise ValueError("X and T disagree in samples or groups")
         if W is not None and W.shape != T.shape:
             raise ValueError("W and T disagree in shape")
+        tf.tf_mlp_fit_inputs(self.net.h, X, X.shape[0], stream)
         tf.tf_mlp_fit_scale(self.net.h, T, T.numel(), stream)
         phases = max(1, min(int(decay), int(epochs)))
         hist = []

@@ -28,7 +28,8 @@ SYMBOLS = (
     "tf_source_iterate", "tf_destroy", "tf_mesh_geometry", "tf_quadrature_get", "tf_graph_levels",
     "tf_problem_psi", "tf_problem_stats", "tf_status_string", "tf_last_error", "tf_integrated_flux_noalloc",
     # include/tflearn.h
-    "tf_mlp_create", "tf_mlp_params", "tf_mlp_scale", "tf_mlp_limits", "tf_mlp_fit_scale", "tf_mlp_features", "tf_mlp_targets",
+    "tf_mlp_create", "tf_mlp_params", "tf_mlp_scale", "tf_mlp_limits", "tf_mlp_fit_inputs",
+    "tf_mlp_input_scale", "tf_mlp_shrink", "tf_mlp_fit_scale", "tf_mlp_features", "tf_mlp_targets",
     "tf_mlp_weights", "tf_mlp_forward", "tf_mlp_gradients", "tf_mlp_adam_step", "tf_mlp_train", "tf_mlp_predict_phi",
 )
 
@@ -49,7 +50,7 @@ class tf_iter_info(C.Structure):
     _fields_ = [
         ("iterations", C.c_int32), ("converged", C.c_int32), ("residual", C.c_double),
         ("integrated_total", C.c_double), ("integrated_flux", C.POINTER(C.c_double)),
-        ("residual_history", C.POINTER(C.c_double)), ("seconds", C.c_double),
+        ("residual_history", C.POINTER(C.c_double)), ("seconds", C.c_double), ("balance", C.c_double),
     ]
 
 
@@ -112,6 +113,9 @@ def load(build_if_missing: bool = True):
     lib.tf_mlp_params.argtypes = [H, vp, vp, C.POINTER(i64)]
     lib.tf_mlp_scale.argtypes = [H, fp, fp, fp, fp]
     lib.tf_mlp_limits.argtypes = [H, fp, fp, fp, fp]
+    lib.tf_mlp_fit_inputs.argtypes = [H, vp, i64, vp]
+    lib.tf_mlp_shrink.argtypes = [H, fp, fp]
+    lib.tf_mlp_input_scale.argtypes = [H, vp, vp, vp, vp]
     lib.tf_mlp_fit_scale.argtypes = [H, vp, i64, vp]
     lib.tf_mlp_features.argtypes = [i64, i32, vp, vp, vp, vp, vp, vp, vp]
     lib.tf_mlp_targets.argtypes = [i64, i32, vp, vp, vp]
@@ -304,7 +308,7 @@ def source_iterate_batch(problems, phis, tol, max_iters, stream=None, history=Fa
     res = []
     for i, (ig, hist) in zip(out, keep):
         d = dict(iterations=i.iterations, converged=bool(i.converged), residual=i.residual, seconds=i.seconds,
-                 integrated_total=i.integrated_total, integrated_flux=np.array(ig[:]))
+                 integrated_total=i.integrated_total, integrated_flux=np.array(ig[:]), balance=i.balance)
         if hist is not None:
             d["residual_history"] = np.array(hist[: i.iterations])
         res.append(d)
@@ -338,6 +342,26 @@ def tf_mlp_limits(net, kappa=None, cap=None):
     cs = None if cap is None else C.byref(C.c_float(cap))
     _check(load().tf_mlp_limits(net, C.byref(kg), C.byref(cg), ks, cs), "tf_mlp_limits")
     return kg.value, cg.value
+
+
+def tf_mlp_shrink(net, factor=None):
+    g = C.c_float()
+    _check(load().tf_mlp_shrink(net, C.byref(g), None if factor is None else C.byref(C.c_float(factor))),
+           "tf_mlp_shrink")
+    return g.value
+
+
+def tf_mlp_fit_inputs(net, X, n, stream=None):
+    return _check(load().tf_mlp_fit_inputs(net, _ptr(X), int(n), _stream_handle(stream)), "tf_mlp_fit_inputs")
+
+
+def tf_mlp_input_scale(net, n_in, mean=None, inv=None):
+    """Sets the input standardisation when mean and inv (host arrays) are given; returns (mean, inv)."""
+    ms = None if mean is None else np.ascontiguousarray(mean, dtype=np.float32)
+    iv = None if inv is None else np.ascontiguousarray(inv, dtype=np.float32)
+    mg, ig = np.zeros(int(n_in), np.float32), np.zeros(int(n_in), np.float32)
+    _check(load().tf_mlp_input_scale(net, _ptr(mg), _ptr(ig), _ptr(ms), _ptr(iv)), "tf_mlp_input_scale")
+    return mg, ig
 
 
 def tf_mlp_fit_scale(net, T, n_values, stream=None):
@@ -478,7 +502,7 @@ class Problem(_Handle):
         st, out = tf_source_iterate([self.h], tol, max_iters, [phi], [info], stream)
         i = out[0]
         res = dict(status=st, iterations=i.iterations, converged=bool(i.converged), residual=i.residual,
-                   integrated_total=i.integrated_total, integrated_flux=np.array(ig[:]))
+                   integrated_total=i.integrated_total, integrated_flux=np.array(ig[:]), balance=i.balance)
         if hist is not None:
             res["residual_history"] = np.array(hist[: i.iterations])
         return res

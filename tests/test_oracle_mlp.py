@@ -186,8 +186,9 @@ def test_features_two_cells_by_hand():
     Q[1, 0] = [2, 2, 2, 2]       # average 2
     X = om.features(geom["nbr"], np.array([0, 1]), sigma_t, sigma_s, Q)
     l = np.log
-    want0 = [l(1.0), l(2.0), 0.5, 0.25, 0.0, 0.5, 3.0, 1.0, l(4.0), l(0.5), 2.0, 0.0]
-    want1 = [l(4.0), l(0.5), 0.25, 0.5, 0.0, 0.5, 2.0, 0.0, l(1.0), l(2.0), 3.0, 1.0]
+    e = 1e-6
+    want0 = [l(1.0), l(2.0), 0.5, 0.25, 0.0, 0.5, l(3.0 + e), l(1.0 + e), l(4.0), l(0.5), l(2.0 + e), l(e)]
+    want1 = [l(4.0), l(0.5), 0.25, 0.5, 0.0, 0.5, l(2.0 + e), l(e), l(1.0), l(2.0), l(3.0 + e), l(1.0 + e)]
     np.testing.assert_allclose(X[0], want0, rtol=1e-15, atol=0)
     np.testing.assert_allclose(X[1], want1, rtol=1e-15, atol=0)
 
@@ -206,7 +207,7 @@ def test_features_neighbour_means_brute_force():
         nb = [d for d in range(C) if d != c and len(sets[c] & sets[d]) == 3]
         assert 1 <= len(nb) <= 4
         np.testing.assert_allclose(X[c, 2 * G + G * G:3 * G + G * G], lst[nb].mean(axis=0), rtol=1e-14)
-        np.testing.assert_allclose(X[c, 3 * G + G * G:], qbar[nb].mean(axis=0), rtol=1e-14, atol=1e-15)
+        np.testing.assert_allclose(X[c, 3 * G + G * G:], np.log(qbar[nb].mean(axis=0) + 1e-6), rtol=1e-14)
 
 
 def test_scattering_probabilities_sum_to_ratio_range():
@@ -333,3 +334,17 @@ def test_prediction_cap():
     y = np.array([[0.0, 10.0]])
     out = om.predict_phi(y, 0.0, 1.0, cap=np.log(2.0))
     np.testing.assert_allclose(out[0, :, 0], [1.0 - 1e-6, 2.0 - 1e-6], rtol=1e-15)
+
+
+def test_input_scale_standardises_columns():
+    rng = np.random.default_rng(28)
+    X = rng.normal(3.0, 2.0, size=(500, 4))
+    X[:, 2] = 7.5                     # a constant feature
+    mean, inv = om.input_scale(X)
+    Z = om.normalize(X, mean, inv)
+    np.testing.assert_allclose(Z[:, [0, 1, 3]].mean(axis=0), 0.0, atol=1e-12)
+    np.testing.assert_allclose(Z[:, [0, 1, 3]].std(axis=0), 1.0, rtol=1e-12)
+    assert inv[2] == 1.0 and np.all(Z[:, 2] == 0.0)
+    # closed form on two values
+    m2, i2 = om.input_scale(np.array([[1.0], [5.0]]))
+    assert m2[0] == 3.0 and i2[0] == 0.5
