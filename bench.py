@@ -279,6 +279,7 @@ def run_ours(args):
                            "max_level": st1["max_level"], "grid_ctas": st1["grid_ctas"],
                            "warps_per_cta": st1["warps_per_cta"], "mean_ready": st1["mean_ready"],
                            "wait_frac": st1["wait_seconds"] / max(st1["wait_seconds"] + st1["busy_seconds"], 1e-30),
+                           "data_wait_frac": st1["data_wait_seconds"] / max(st1["busy_seconds"], 1e-30),
                            "n_chunks": st1["n_chunks"], "octant_window": args.octant_window or 8},
             "gpu_launches": int((st1["launches_per_step"] + 2) * args.steps),
             "clocks": clk}

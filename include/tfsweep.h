@@ -147,7 +147,9 @@ typedef struct {
     int32_t tuned_candidates[8];
     double tuned_seconds[8];
     int32_t reserved_i[5];
-    double reserved_d[6];
+    double data_wait_seconds;  /* summed over warps: time waiting for rows staged by bulk copies
+                                * (SM cycles at the nominal SM clock) */
+    double reserved_d[5];
 } tf_stats;
 
 /* Mesh of tetrahedra.  xyz: host [n_vertices][3] FP64; tets: host [n_cells][4]

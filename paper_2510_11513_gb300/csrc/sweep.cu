@@ -40,6 +40,7 @@ __global__ void begin_kernel(Ctrl *ctrl, unsigned long long n_seeds, int reset_s
     if (reset_stats) {
         ctrl->tasks_done = ctrl->polls = ctrl->wait_ns = ctrl->busy_ns = 0;
         ctrl->depth_sum = ctrl->pops = 0;
+        ctrl->data_wait_cycles = 0;
         ctrl->kernel_ns = 0;
     }
     ctrl->t_first = ~0ull;
@@ -649,6 +650,7 @@ __global__ void __launch_bounds__(256) residual_kernel(const double *__restrict_
 // ============================================================== host side
 struct DeviceState {
     int device = 0, sm_count = 0;
+    int clock_khz = 0;  // SM clock (kHz), to turn device cycle counts into seconds
     int64_t C = 0, nv = 0;
     int32_t G = 0, D = 0, M = 0;
     bool fp64 = false;
@@ -907,6 +909,10 @@ tf_status device_create(Problem &p, const int32_t *cell_material, const double *
     if (d.device < 0 || d.device >= ndev) return fail(TF_ERR_ARG, "tf_problem_create: no such CUDA device");
     TF_CUDA(cudaSetDevice(d.device));
     TF_CUDA(cudaDeviceGetAttribute(&d.sm_count, cudaDevAttrMultiProcessorCount, d.device));
+    if (cudaDeviceGetAttribute(&d.clock_khz, cudaDevAttrClockRate, d.device) != cudaSuccess) {
+        d.clock_khz = 0;
+        cudaGetLastError();
+    }
     d.C = m.nc;
     d.nv = m.nv;
     d.G = p.G;
@@ -1331,6 +1337,7 @@ tf_status collect(Problem &p, cudaStream_t st, bool copied = false)
     s.busy_seconds = c.busy_ns * 1e-9;
     s.kernel_seconds = c.kernel_ns * 1e-9;
     s.mean_ready = c.pops ? (double)c.depth_sum / (double)c.pops : 0.0;
+    s.data_wait_seconds = d.clock_khz > 0 ? (double)c.data_wait_cycles / (1e3 * d.clock_khz) : 0.0;
     {
         // CUDA-event times of the step's kernels (events recorded as external
         // nodes when the step runs inside a captured graph)

@@ -52,6 +52,7 @@ struct Ctrl {
     unsigned long long t_last;   // latest warp end
     unsigned long long depth_sum;
     unsigned long long pops;
+    unsigned long long data_wait_cycles;  // summed over warps: SM cycles waiting for staged rows (bulk copies)
     unsigned long long residual_bits;  // max residual as ordered bits of a non-negative double
     unsigned long long balance_bits;   // max over groups of the relative balance residual (same encoding)
     unsigned long long kernel_ns;      // summed over chunks
@@ -441,16 +442,22 @@ __device__ __forceinline__ void fence_proxy_async_shared() { asm volatile("fence
 __device__ __forceinline__ void fence_proxy_async_global() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
 
 // Bounded wait on an mbarrier phase; false (and the error word set) after limit_ns.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, unsigned long long limit_ns, int *err)
+// Lane 0 adds the SM cycles it spent in the wait (try_wait may suspend the
+// thread inside the first attempt) to *acc, the warp's data-wait counter.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, unsigned long long limit_ns, int *err,
+                                          unsigned long long *acc)
 {
-    if (mbar_try_wait(bar, parity)) return true;
-    const unsigned long long t0 = globaltimer();
-    while (!mbar_try_wait(bar, parity)) {
-        if (globaltimer() - t0 > limit_ns) {
-            atomicCAS(err, 0, (int)TF_ERR_TIMEOUT);
-            return false;
+    const long long c0 = clock64();
+    if (!mbar_try_wait(bar, parity)) {
+        const unsigned long long t0 = globaltimer();
+        while (!mbar_try_wait(bar, parity)) {
+            if (globaltimer() - t0 > limit_ns) {
+                atomicCAS(err, 0, (int)TF_ERR_TIMEOUT);
+                return false;
+            }
         }
     }
+    if ((threadIdx.x & 31) == 0) *acc += (unsigned long long)(clock64() - c0);
     return true;
 }
 
@@ -469,36 +476,48 @@ template <class T> inline size_t staged_warp_bytes(int G)
     return 3 * (sizeof(CellGeo<T>) + 4 * (size_t)G * sizeof(V4<T>));
 }
 
-// Lane 0: geometry record and source row of cell c into stage s.
-template <class T>
-__device__ __forceinline__ void issue_geoq(const SweepArgs<T> &A, unsigned char *st_base, uint64_t *bar, uint32_t c,
-                                           const StageLayout<T> &L)
+// Packed FP32 pairs: both halves of a 64-bit register hold one group each and
+// Blackwell's add/mul/fma.rn.f32x2 operate on both.
+struct f2 {
+    unsigned long long v;
+};
+__device__ __forceinline__ f2 pk(float a, float b)
 {
-    mbar_arrive_expect_tx(bar, (uint32_t)sizeof(CellGeo<T>) + L.row);
-    bulk_g2s(st_base, A.geo + c, (uint32_t)sizeof(CellGeo<T>), bar);
-    bulk_g2s(st_base + sizeof(CellGeo<T>), A.q + (size_t)c * A.G, L.row, bar);
+    f2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r.v) : "f"(a), "f"(b));
+    return r;
 }
-
-// Lane 0: psi rows of the interior inflow neighbours (mask from the task list,
-// neighbours nb read ahead of the record) into the stage's upwind slots, in face order.
-template <class T>
-__device__ __forceinline__ void issue_up(const SweepArgs<T> &A, unsigned char *st_base, uint64_t *bar, uint32_t mask,
-                                         int4 nb4, size_t psi_dir, const StageLayout<T> &L)
+__device__ __forceinline__ void upk(f2 a, float &x, float &y) { asm("mov.b64 {%0, %1}, %2;" : "=f"(x), "=f"(y) : "l"(a.v)); }
+__device__ __forceinline__ f2 operator+(f2 a, f2 b)
 {
-    const int32_t nb[4] = {nb4.x, nb4.y, nb4.z, nb4.w};
-    uint32_t n_up = 0;
-#pragma unroll
-    for (int f = 0; f < 4; ++f) n_up += (((mask >> f) & 1u) && nb[f] >= 0) ? 1u : 0u;
-    mbar_arrive_expect_tx(bar, n_up * L.row);
-    uint32_t slot = 0;
-#pragma unroll
-    for (int f = 0; f < 4; ++f) {
-        if (((mask >> f) & 1u) && nb[f] >= 0) {
-            bulk_g2s(st_base + sizeof(CellGeo<T>) + (1 + slot) * L.row, A.psi + (psi_dir + (size_t)nb[f]) * A.G, L.row,
-                     bar);
-            ++slot;
-        }
-    }
+    f2 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d.v) : "l"(a.v), "l"(b.v));
+    return d;
+}
+__device__ __forceinline__ f2 operator*(f2 a, f2 b)
+{
+    f2 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d.v) : "l"(a.v), "l"(b.v));
+    return d;
+}
+__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c)
+{
+    f2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d.v) : "l"(a.v), "l"(b.v), "l"(c.v));
+    return d;
+}
+__device__ __forceinline__ f2 sel2(bool p, f2 a, f2 b)
+{
+    f2 r;
+    r.v = p ? a.v : b.v;
+    return r;
+}
+// -1 / a, halfwise (one MUFU reciprocal each)
+__device__ __forceinline__ f2 nrcp2(f2 a)
+{
+    float x, y;
+    upk(a, x, y);
+    return pk(rcp<float>(-x), rcp<float>(-y));
 }
 
 // Solve every group of one staged cell: lane l takes groups l, l+32, ...
@@ -590,9 +609,160 @@ __device__ __forceinline__ void solve_staged_cell(const SweepArgs<T> &A, const u
         o.w = x[3];
         st_psi(out + gg, o);
     };
-    if constexpr (NPL > 0) {
+    if constexpr (NPL == 2 && sizeof(T) == 4) {
+        // G = 64, FP32: the lane's two groups (lane, lane + 32) packed into f32x2 pairs,
+        // so the right-hand side, the matrix and the elimination take one packed
+        // instruction for both (the reciprocals stay one MUFU per half)
+        const float4 qa = reinterpret_cast<const float4 *>(qrow)[lane], qb = reinterpret_cast<const float4 *>(qrow)[lane + 32];
+        const f2 mvp = pk(mv, mv);
+        const f2 sv = pk(__ldg(sig + lane), __ldg(sig + lane + 32)) * mvp;
+        const f2 qx = pk(qa.x, qb.x), qy = pk(qa.y, qb.y), qz = pk(qa.z, qb.z), qw = pk(qa.w, qb.w);
+        const f2 qs = (qx + qy) + (qz + qw);
+        f2 b[4] = {mvp * (qx + qs), mvp * (qy + qs), mvp * (qz + qs), mvp * (qw + qs)};
+        if (A.S1) {
+            const float4 s0 = __ldg(reinterpret_cast<const float4 *>(A.S1) + (size_t)c * A.G + lane);
+            const float4 s1 = __ldg(reinterpret_cast<const float4 *>(A.S1) + (size_t)c * A.G + lane + 32);
+            const f2 os = pk(5.f * mv * (ox * s0.x + oy * s0.y + oz * s0.z), 5.f * mv * (ox * s1.x + oy * s1.y + oz * s1.z));
 #pragma unroll
-        for (int k = 0; k < NPL; ++k) unit(lane + 32 * k);
+            for (int i = 0; i < 4; ++i) b[i] = b[i] + os;
+        }
+#pragma unroll
+        for (int f = 0; f < 4; ++f) {
+            if (!((mask >> f) & 1u)) continue;
+            const int i0 = f == 0 ? 1 : 0, i1 = f <= 1 ? 2 : 1, i2 = f <= 2 ? 3 : 2;
+            f2 v0, v1, v2;
+            if (nb[f] >= 0) {
+                const uint32_t fn = (code >> (2 * f)) & 3u;  // upwind node opposite the face
+                const bool s0 = fn == 0u, s1 = fn <= 1u, s2 = fn <= 2u;
+                const float4 ua = reinterpret_cast<const float4 *>(uprow[f])[lane];
+                const float4 ub = reinterpret_cast<const float4 *>(uprow[f])[lane + 32];
+                v0 = pk(s0 ? ua.y : ua.x, s0 ? ub.y : ub.x);
+                v1 = pk(s1 ? ua.z : ua.y, s1 ? ub.z : ub.y);
+                v2 = pk(s2 ? ua.w : ua.z, s2 ? ub.w : ub.z);
+            } else if (A.psi_in) {
+                const int4 tv = __ldg(A.tets + c);
+                const int vi[4] = {tv.x, tv.y, tv.z, tv.w};
+                const float *pi = reinterpret_cast<const float *>(A.psi_in);
+                v0 = pk(__ldg(pi + (size_t)vi[i0] * A.G + lane), __ldg(pi + (size_t)vi[i0] * A.G + lane + 32));
+                v1 = pk(__ldg(pi + (size_t)vi[i1] * A.G + lane), __ldg(pi + (size_t)vi[i1] * A.G + lane + 32));
+                v2 = pk(__ldg(pi + (size_t)vi[i2] * A.G + lane), __ldg(pi + (size_t)vi[i2] * A.G + lane + 32));
+            } else {
+                continue;  // vacuum
+            }
+            const f2 tf = pk(t[f], t[f]);
+            const f2 Uf = (v0 + v1) + v2;
+            b[i0] = fma2(tf, v0 + Uf, b[i0]);
+            b[i1] = fma2(tf, v1 + Uf, b[i1]);
+            b[i2] = fma2(tf, v2 + Uf, b[i2]);
+        }
+        const f2 two = pk(2.f, 2.f);
+        f2 a[4][4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const f2 w = pk(Bm[i][j], Bm[i][j]);
+                a[i][j] = i == j ? fma2(two, sv, w) : w + sv;
+            }
+        // elimination with n_ik = -a_ik / a_kk, back substitution on y = -x
+        const f2 nr0 = nrcp2(a[0][0]);
+        const f2 n10 = a[1][0] * nr0, n20 = a[2][0] * nr0, n30 = a[3][0] * nr0;
+        const f2 a11 = fma2(n10, a[0][1], a[1][1]), a12 = fma2(n10, a[0][2], a[1][2]), a13 = fma2(n10, a[0][3], a[1][3]);
+        const f2 a21 = fma2(n20, a[0][1], a[2][1]), a22 = fma2(n20, a[0][2], a[2][2]), a23 = fma2(n20, a[0][3], a[2][3]);
+        const f2 a31 = fma2(n30, a[0][1], a[3][1]), a32 = fma2(n30, a[0][2], a[3][2]), a33 = fma2(n30, a[0][3], a[3][3]);
+        const f2 b1 = fma2(n10, b[0], b[1]), b2 = fma2(n20, b[0], b[2]), b3 = fma2(n30, b[0], b[3]);
+        const f2 nr1 = nrcp2(a11);
+        const f2 n21 = a21 * nr1, n31 = a31 * nr1;
+        const f2 c22 = fma2(n21, a12, a22), c23 = fma2(n21, a13, a23), c32 = fma2(n31, a12, a32), c33 = fma2(n31, a13, a33);
+        const f2 d2 = fma2(n21, b1, b2), d3 = fma2(n31, b1, b3);
+        const f2 nr2 = nrcp2(c22);
+        const f2 n32 = c32 * nr2;
+        const f2 e33 = fma2(n32, c23, c33), e3 = fma2(n32, d2, d3);
+        const f2 y3 = e3 * nrcp2(e33);
+        const f2 y2 = fma2(c23, y3, d2) * nr2;
+        const f2 y1 = fma2(a13, y3, fma2(a12, y2, b1)) * nr1;
+        const f2 y0 = fma2(a[0][3], y3, fma2(a[0][2], y2, fma2(a[0][1], y1, b[0]))) * nr0;
+        float x0a, x0b, x1a, x1b, x2a, x2b, x3a, x3b;
+        upk(y0, x0a, x0b);
+        upk(y1, x1a, x1b);
+        upk(y2, x2a, x2b);
+        upk(y3, x3a, x3b);
+        reinterpret_cast<float4 *>(out)[lane] = make_float4(-x0a, -x1a, -x2a, -x3a);
+        reinterpret_cast<float4 *>(out)[lane + 32] = make_float4(-x0b, -x1b, -x2b, -x3b);
+    } else if constexpr (NPL > 0) {
+        // the lane's NPL groups side by side: every face test and trace selection is made
+        // once per cell and the independent solves interleave
+        T sv[NPL], b[NPL][4];
+#pragma unroll
+        for (int k = 0; k < NPL; ++k) {
+            const int gg = lane + 32 * k;
+            sv[k] = __ldg(sig + gg) * mv;
+            const V4<T> q4 = qrow[gg];
+            const T qs = (q4.x + q4.y) + (q4.z + q4.w);
+            b[k][0] = mv * (q4.x + qs);
+            b[k][1] = mv * (q4.y + qs);
+            b[k][2] = mv * (q4.z + qs);
+            b[k][3] = mv * (q4.w + qs);
+        }
+        if (A.S1) {
+#pragma unroll
+            for (int k = 0; k < NPL; ++k) {
+                const V4<T> s1 = ld_ro(A.S1 + (size_t)c * A.G + lane + 32 * k);
+                const T os = T(5) * mv * (ox * s1.x + oy * s1.y + oz * s1.z);
+#pragma unroll
+                for (int i = 0; i < 4; ++i) b[k][i] += os;
+            }
+        }
+#pragma unroll
+        for (int f = 0; f < 4; ++f) {
+            if (!((mask >> f) & 1u)) continue;
+            // the face's nodes in sorted order are {0..3} \ {f}, ascending
+            const int i0 = f == 0 ? 1 : 0, i1 = f <= 1 ? 2 : 1, i2 = f <= 2 ? 3 : 2;
+            if (nb[f] >= 0) {
+                const uint32_t fn = (code >> (2 * f)) & 3u;  // upwind node opposite the face
+                const bool s0 = fn == 0u, s1 = fn <= 1u, s2 = fn <= 2u;
+#pragma unroll
+                for (int k = 0; k < NPL; ++k) {
+                    const V4<T> u = uprow[f][lane + 32 * k];
+                    const T v0 = s0 ? u.y : u.x, v1 = s1 ? u.z : u.y, v2 = s2 ? u.w : u.z;
+                    const T U = v0 + v1 + v2;
+                    b[k][i0] += t[f] * (v0 + U);
+                    b[k][i1] += t[f] * (v1 + U);
+                    b[k][i2] += t[f] * (v2 + U);
+                }
+            } else if (A.psi_in) {
+                const int4 tv = __ldg(A.tets + c);
+                const int vi[4] = {tv.x, tv.y, tv.z, tv.w};
+#pragma unroll
+                for (int k = 0; k < NPL; ++k) {
+                    const int gg = lane + 32 * k;
+                    const T v0 = __ldg(A.psi_in + (size_t)vi[i0] * A.G + gg);
+                    const T v1 = __ldg(A.psi_in + (size_t)vi[i1] * A.G + gg);
+                    const T v2 = __ldg(A.psi_in + (size_t)vi[i2] * A.G + gg);
+                    const T U = v0 + v1 + v2;
+                    b[k][i0] += t[f] * (v0 + U);
+                    b[k][i1] += t[f] * (v1 + U);
+                    b[k][i2] += t[f] * (v2 + U);
+                }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < NPL; ++k) {
+            T a[4][4];
+            const T sv2 = T(2) * sv[k];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) a[i][j] = Bm[i][j] + (i == j ? sv2 : sv[k]);
+            T x[4];
+            solve4(a, b[k], x);
+            V4<T> o;
+            o.x = x[0];
+            o.y = x[1];
+            o.z = x[2];
+            o.w = x[3];
+            st_psi(out + lane + 32 * k, o);
+        }
     } else {
         for (int gg = lane; gg < A.G; gg += 32) unit(gg);
     }
@@ -607,7 +777,8 @@ __device__ __forceinline__ void solve_staged_cell(const SweepArgs<T> &A, const u
 // (error word set).
 template <class T, int NPL>
 __device__ __forceinline__ bool run_task_staged(const SweepArgs<T> &A, uint4 ti, int lane, T ox, T oy, T oz,
-                                                size_t psi_dir, unsigned char *wsm, uint64_t *bars, uint32_t &ph)
+                                                size_t psi_dir, unsigned char *wsm, uint64_t *bars, uint32_t &ph,
+                                                unsigned long long *wacc)
 {
     const unsigned FULL = 0xffffffffu;
     const uint32_t ncell = ti.y & 0xffffu;
@@ -620,6 +791,8 @@ __device__ __forceinline__ bool run_task_staged(const SweepArgs<T> &A, uint4 ti,
     // psi rows written by other warps (generic proxy, acquired through the
     // queue) are read here by the async proxy
     if (lane == 0) fence_proxy_async_global();
+    // Copies of cell k into stage k mod 3, one per lane: lane 0 the record, lane 1 the
+    // source row, lanes 2.. the upwind rows (interior inflow faces in face order).
     auto issue = [&](uint32_t k) {
         const int src = (int)(k & 31u);
         const bool hi = k >= 32u;
@@ -629,12 +802,28 @@ __device__ __forceinline__ bool run_task_staged(const SweepArgs<T> &A, uint4 ti,
         nb.y = __shfl_sync(FULL, hi ? n_hi.y : n_lo.y, src);
         nb.z = __shfl_sync(FULL, hi ? n_hi.z : n_lo.z, src);
         nb.w = __shfl_sync(FULL, hi ? n_hi.w : n_lo.w, src);
+        const uint32_t s = k % 3u, mask = ek & 15u, c = ek >> 4;
+        const uint32_t upm = (((mask & 1u) && nb.x >= 0) ? 1u : 0u) | (((mask & 2u) && nb.y >= 0) ? 2u : 0u) |
+                             (((mask & 4u) && nb.z >= 0) ? 4u : 0u) | (((mask & 8u) && nb.w >= 0) ? 8u : 0u);
+        const uint32_t n_up = __popc(upm);
+        unsigned char *st = wsm + s * L.stage;
+        fence_proxy_async_shared();  // this lane's generic reads of the stage (cell k - 3) before async writes
         if (lane == 0) {
-            const uint32_t s = k % 3u;
-            unsigned char *st = wsm + s * L.stage;
-            fence_proxy_async_shared();  // generic reads of this stage (cell k - 3) before the async writes
-            issue_geoq(A, st, &bars[s], ek >> 4, L);
-            issue_up(A, st, &bars[3 + s], ek & 15u, nb, psi_dir, L);
+            mbar_arrive_expect_tx(&bars[s], (uint32_t)sizeof(CellGeo<T>) + L.row);
+            mbar_arrive_expect_tx(&bars[3 + s], n_up * L.row);
+        }
+        __syncwarp();
+        if (lane == 0) {
+            bulk_g2s(st, A.geo + c, (uint32_t)sizeof(CellGeo<T>), &bars[s]);
+        } else if (lane == 1) {
+            bulk_g2s(st + sizeof(CellGeo<T>), A.q + (size_t)c * A.G, L.row, &bars[s]);
+        } else if (lane < 2 + (int)n_up) {
+            uint32_t m = upm;
+            for (int r = 2; r < lane; ++r) m &= m - 1u;  // drop the faces of lanes 2 .. lane - 1
+            const int f = __ffs(m) - 1;
+            const int nbf = f == 0 ? nb.x : (f == 1 ? nb.y : (f == 2 ? nb.z : nb.w));
+            bulk_g2s(st + sizeof(CellGeo<T>) + (uint32_t)(lane - 1) * L.row, A.psi + (psi_dir + (size_t)nbf) * A.G,
+                     L.row, &bars[3 + s]);
         }
     };
     issue(0);
@@ -643,9 +832,9 @@ __device__ __forceinline__ bool run_task_staged(const SweepArgs<T> &A, uint4 ti,
         const uint32_t s = k % 3u;
         const uint32_t ek = __shfl_sync(FULL, k < 32 ? e_lo : e_hi, k & 31);
         if (k + 2 < ncell) issue(k + 2);
-        if (!mbar_wait(&bars[s], (ph >> s) & 1u, A.wait_limit_ns, &A.ctrl->error)) return false;
+        if (!mbar_wait(&bars[s], (ph >> s) & 1u, A.wait_limit_ns, &A.ctrl->error, wacc)) return false;
         ph ^= 1u << s;
-        if (!mbar_wait(&bars[3 + s], (ph >> (3 + s)) & 1u, A.wait_limit_ns, &A.ctrl->error)) return false;
+        if (!mbar_wait(&bars[3 + s], (ph >> (3 + s)) & 1u, A.wait_limit_ns, &A.ctrl->error, wacc)) return false;
         ph ^= 1u << (3 + s);
         solve_staged_cell<T, NPL>(A, wsm + s * L.stage, ek, lane, ox, oy, oz, psi_dir, L);
         __syncwarp();
@@ -659,47 +848,6 @@ __device__ __forceinline__ bool run_task_staged(const SweepArgs<T> &A, uint4 ti,
 // packed FP32 instructions (add/sub/mul/fma .f32x2) operate on both halves.
 // The source and psi rows are stored pair-interleaved, [cell][G/2][node][2],
 // so one 32-byte load yields the four packed nodal values of a group pair.
-struct f2 {
-    unsigned long long v;
-};
-__device__ __forceinline__ f2 pk(float a, float b)
-{
-    f2 r;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(r.v) : "f"(a), "f"(b));
-    return r;
-}
-__device__ __forceinline__ void upk(f2 a, float &x, float &y) { asm("mov.b64 {%0, %1}, %2;" : "=f"(x), "=f"(y) : "l"(a.v)); }
-__device__ __forceinline__ f2 operator+(f2 a, f2 b)
-{
-    f2 d;
-    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d.v) : "l"(a.v), "l"(b.v));
-    return d;
-}
-__device__ __forceinline__ f2 operator*(f2 a, f2 b)
-{
-    f2 d;
-    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d.v) : "l"(a.v), "l"(b.v));
-    return d;
-}
-__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c)
-{
-    f2 d;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d.v) : "l"(a.v), "l"(b.v), "l"(c.v));
-    return d;
-}
-__device__ __forceinline__ f2 sel2(bool p, f2 a, f2 b)
-{
-    f2 r;
-    r.v = p ? a.v : b.v;
-    return r;
-}
-// -1 / a, halfwise (one MUFU reciprocal each)
-__device__ __forceinline__ f2 nrcp2(f2 a)
-{
-    float x, y;
-    upk(a, x, y);
-    return pk(rcp<float>(-x), rcp<float>(-y));
-}
 struct P4 {
     f2 x, y, z, w;  // node 0..3, each packed (group 2p, group 2p+1)
 };
@@ -894,7 +1042,7 @@ struct PairLayout {
 // Returns false if a wait ran out (error word set).
 __device__ __forceinline__ bool run_task_pairs(const SweepArgs<float> &A, uint4 ti, int lane, float ox, float oy,
                                                float oz, size_t psi_dir, unsigned char *wsm, uint64_t *bars,
-                                               uint32_t &ph)
+                                               uint32_t &ph, unsigned long long *wacc)
 {
     const unsigned FULL = 0xffffffffu;
     const uint32_t ncell = ti.y & 0xffffu;
@@ -942,7 +1090,7 @@ __device__ __forceinline__ bool run_task_pairs(const SweepArgs<float> &A, uint4 
     for (uint32_t st = 0; st < nst; ++st) {
         if (st + 2 < nst) issue(st + 2);
         const uint32_t b = st % 3u;
-        if (!mbar_wait(&bars[b], (ph >> b) & 1u, A.wait_limit_ns, &A.ctrl->error)) return false;
+        if (!mbar_wait(&bars[b], (ph >> b) & 1u, A.wait_limit_ns, &A.ctrl->error, wacc)) return false;
         ph ^= 1u << b;
         const uint32_t j = (uint32_t)lane >> L.lpc_shift, k = st * L.cps + j;
         if (k < ncell) {
@@ -963,11 +1111,12 @@ __device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_re
 // Staged path with the groups-per-lane count unrolled for the common G = 32 and 64.
 template <class T>
 __device__ __forceinline__ bool run_task_staged_any(const SweepArgs<T> &A, uint4 ti, int lane, T ox, T oy, T oz,
-                                                    size_t psi_dir, unsigned char *wsm, uint64_t *bars, uint32_t &ph)
+                                                    size_t psi_dir, unsigned char *wsm, uint64_t *bars, uint32_t &ph,
+                                                    unsigned long long *wacc)
 {
-    if (A.G == 64) return run_task_staged<T, 2>(A, ti, lane, ox, oy, oz, psi_dir, wsm, bars, ph);
-    if (A.G == 32) return run_task_staged<T, 1>(A, ti, lane, ox, oy, oz, psi_dir, wsm, bars, ph);
-    return run_task_staged<T, 0>(A, ti, lane, ox, oy, oz, psi_dir, wsm, bars, ph);
+    if (A.G == 64) return run_task_staged<T, 2>(A, ti, lane, ox, oy, oz, psi_dir, wsm, bars, ph, wacc);
+    if (A.G == 32) return run_task_staged<T, 1>(A, ti, lane, ox, oy, oz, psi_dir, wsm, bars, ph, wacc);
+    return run_task_staged<T, 0>(A, ti, lane, ox, oy, oz, psi_dir, wsm, bars, ph, wacc);
 }
 
 // Persistent sweep: a warp claims a ticket (the next queue slot), waits until
@@ -1000,9 +1149,9 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 3) sweep_kernel(cons
         __syncwarp();
     }
     // per-warp counters live in shared memory (lane 0 updates them) to spare registers
-    __shared__ unsigned long long wstat[8][6];  // polls, wait_ns, busy_ns, done, depth, pops
+    __shared__ unsigned long long wstat[8][7];  // polls, wait_ns, busy_ns, done, depth, pops, data-wait cycles
     unsigned long long *ws = wstat[threadIdx.x >> 5];
-    if (lane < 6) ws[lane] = 0;
+    if (lane < 7) ws[lane] = 0;
     __syncwarp();
     const unsigned long long t_start = globaltimer();
     // A warp that releases downwind tasks keeps one of them and runs it next
@@ -1073,9 +1222,9 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 3) sweep_kernel(cons
         const V4<T> om = ld_ro(A.omega + dir);
         const size_t psi_dir = (size_t)(dir - (uint32_t)A.dir_begin) * (size_t)A.C;
         if constexpr (MODE == 3) {
-            if (!run_task_pairs(A, ti, lane, om.x, om.y, om.z, psi_dir, wsm, bars, ph)) break;
+            if (!run_task_pairs(A, ti, lane, om.x, om.y, om.z, psi_dir, wsm, bars, ph, ws + 6)) break;
         } else if constexpr (MODE == 2) {
-            if (!run_task_staged_any(A, ti, lane, om.x, om.y, om.z, psi_dir, wsm, bars, ph)) break;
+            if (!run_task_staged_any(A, ti, lane, om.x, om.y, om.z, psi_dir, wsm, bars, ph, ws + 6)) break;
         } else if constexpr (MODE == 1) {
             run_task_wide(A, ti, lane, om.x, om.y, om.z, psi_dir);
         } else {
@@ -1144,6 +1293,7 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 3) sweep_kernel(cons
         atomicAdd(&A.ctrl->busy_ns, ws[2]);
         atomicAdd(&A.ctrl->depth_sum, ws[4]);
         atomicAdd(&A.ctrl->pops, ws[5]);
+        atomicAdd(&A.ctrl->data_wait_cycles, ws[6]);
         atomicMin(&A.ctrl->t_first, t_start);
         atomicMax(&A.ctrl->t_last, t_end);
     }
@@ -1179,9 +1329,9 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 3) sweep_batch_kerne
         for (int b = 0; b < 6; ++b) mbar_init(&bars[b], 1);
         fence_proxy_async_shared();
     }
-    __shared__ unsigned long long wstat[8][6];
+    __shared__ unsigned long long wstat[8][7];
     unsigned long long *ws = wstat[threadIdx.x >> 5];
-    if (lane < 6) ws[lane] = 0;
+    if (lane < 7) ws[lane] = 0;
     __syncwarp();
     const unsigned long long t_start = globaltimer();
     unsigned keep = 0xffffffffu;  // a block this warp made ready and runs next (global id)
@@ -1254,11 +1404,11 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 3) sweep_batch_kerne
         const size_t psi_dir = (size_t)(dir - (uint32_t)A.dir_begin) * (size_t)A.C;
         bool ok = true;
         if constexpr (sizeof(T) == 4) {
-            if (A.mode == 3) ok = run_task_pairs(A, ti, lane, om.x, om.y, om.z, psi_dir, wsm, bars, ph);
-            else if (A.mode == 2) ok = run_task_staged_any(A, ti, lane, om.x, om.y, om.z, psi_dir, wsm, bars, ph);
+            if (A.mode == 3) ok = run_task_pairs(A, ti, lane, om.x, om.y, om.z, psi_dir, wsm, bars, ph, ws + 6);
+            else if (A.mode == 2) ok = run_task_staged_any(A, ti, lane, om.x, om.y, om.z, psi_dir, wsm, bars, ph, ws + 6);
             else run_task_generic(A, ti, lane, om.x, om.y, om.z, psi_dir);
         } else {
-            if (A.mode == 2) ok = run_task_staged_any(A, ti, lane, om.x, om.y, om.z, psi_dir, wsm, bars, ph);
+            if (A.mode == 2) ok = run_task_staged_any(A, ti, lane, om.x, om.y, om.z, psi_dir, wsm, bars, ph, ws + 6);
             else run_task_generic(A, ti, lane, om.x, om.y, om.z, psi_dir);
         }
         if (!ok) break;
@@ -1298,6 +1448,7 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 3) sweep_batch_kerne
         atomicAdd(&B.ctrl->wait_ns, ws[1]);
         atomicAdd(&B.ctrl->busy_ns, ws[2]);
         atomicAdd(&B.ctrl->pops, ws[5]);
+        atomicAdd(&B.ctrl->data_wait_cycles, ws[6]);
         atomicMin(&B.ctrl->t_first, t_start);
         atomicMax(&B.ctrl->t_last, t_end);
     }

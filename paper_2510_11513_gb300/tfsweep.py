@@ -65,7 +65,7 @@ class tf_stats(C.Structure):
         ("cum_sweep_event_seconds", C.c_double), ("cum_phi_event_seconds", C.c_double), ("cum_steps", C.c_int64),
         ("launches_per_step", C.c_int64), ("kernel_mode", C.c_int32), ("tuned_n", C.c_int32),
         ("tuned_cached", C.c_int32), ("tuned_candidates", C.c_int32 * 8), ("tuned_seconds", C.c_double * 8),
-        ("reserved_i", C.c_int32 * 5), ("reserved_d", C.c_double * 6),
+        ("reserved_i", C.c_int32 * 5), ("data_wait_seconds", C.c_double), ("reserved_d", C.c_double * 5),
     ]
 
 
