@@ -490,7 +490,7 @@ def main():
     ap.add_argument("--no-time-to-tol", action="store_true", help="skip the time-to-1e-6 comparison")
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--octant-window", type=int, default=0, help="octants active at once (0 = library default)")
-    ap.add_argument("--staging", type=int, default=0, help="1 = no shared-memory staging")
+    ap.add_argument("--staging", type=int, default=0, help="0 auto, 1 no shared-memory staging, 2 two stages, 3 three stages")
     ap.add_argument("--pairing", type=int, default=0, help="0 auto, 1 off, 2 packed group pairs when G is even")
     ap.add_argument("--batch-count", type=int, default=64, help="--config batch: number of problems")
     ap.add_argument("--batch-tol", type=float, default=1e-6)

@@ -80,8 +80,9 @@ typedef struct {
     double psi_budget_gb;    /* device memory allowed for the angular-flux store; 0 = 80 % of free memory */
     int32_t task_order;      /* 0 = FIFO ready queue, seeds longest-critical-path first */
     int32_t staging;         /* 0 = automatic: stage each cell's rows in shared memory with bulk
-                              * asynchronous copies when n_groups is a multiple of 32 and they fit;
-                              * 1 = never (registers only) */
+                              * asynchronous copies when n_groups is a multiple of 32 and they fit,
+                              * two cells ahead per warp with six CTAs per SM in FP32, three in FP64;
+                              * 1 = never (registers only); 2 = two stages (FP32); 3 = three stages */
     int32_t octant_window;   /* directions are admitted one octant at a time; this many octants are
                               * active at once (the next one enters when the oldest is half done);
                               * 0 = automatic (8: every direction from the start) */
@@ -139,7 +140,8 @@ typedef struct {
     int64_t cum_steps;
     int64_t launches_per_step;  /* kernels this library launches per transport step */
     int32_t kernel_mode;        /* sweep kernel variant: 0 any G, 1 G%32==0 (registers), 2 G%32==0 staged
-                                 * in shared memory, 3 packed group pairs (FP32, even G) */
+                                 * in shared memory (three stages), 3 packed group pairs (FP32, even G),
+                                 * 4 G%32==0 staged, two stages, six CTAs per SM (FP32) */
     /* task-grain autotuning (cells_per_task < 0 at creation): candidate grains and the time
      * of one trial sweep over a direction sample for each; tuned_cached = 1 if the choice
      * came from an earlier problem of the same class */

@@ -654,6 +654,7 @@ struct DeviceState {
     int64_t C = 0, nv = 0;
     int32_t G = 0, D = 0, M = 0;
     bool fp64 = false;
+    bool two_stage = false;  // staged path with two stages (mode 4)
     size_t tsize = 4;  // sizeof(T)
     void *geo = nullptr;
     uint32_t *cells = nullptr;
@@ -1072,12 +1073,15 @@ tf_status device_create(Problem &p, const int32_t *cell_material, const double *
     // persistent grid: resident CTAs per SM x SMs
     d.wpc = p.opt.warps_per_cta > 0 ? std::min(p.opt.warps_per_cta, 4) : 4;  // launch bounds: 128 threads
     {
-        const size_t wb = d.fp64 ? staged_warp_bytes<double>(d.G) : staged_warp_bytes<float>(d.G);
+        // FP32 stages two cells per warp (six CTAs fit per SM), FP64 three; staging 2 / 3 force it
+        const int ns = p.opt.staging == 3 ? 3 : p.opt.staging == 2 ? 2 : (d.fp64 ? 3 : 2);
+        const size_t wb = d.fp64 ? staged_warp_bytes<double>(d.G, ns) : staged_warp_bytes<float>(d.G, ns);
         const size_t wb128 = (wb + 48 + 127) / 128 * 128;  // + the six mbarriers at the end
-        d.staged = p.opt.staging == 0 && d.G % 32 == 0 && g.cells_per_task <= 64 && wb128 * d.wpc <= 227 * 1024;
+        d.staged = p.opt.staging != 1 && d.G % 32 == 0 && g.cells_per_task <= 64 && wb128 * d.wpc <= 227 * 1024;
         d.warp_smem = d.staged ? (uint32_t)wb128 : 0u;
+        d.two_stage = d.staged && ns == 2 && !d.fp64;
     }
-    d.mode = d.paired ? 3 : d.staged ? 2 : (d.G % 32 == 0 && g.cells_per_task <= 64 ? 1 : 0);
+    d.mode = d.paired ? 3 : d.staged ? (d.two_stage ? 4 : 2) : (d.G % 32 == 0 && g.cells_per_task <= 64 ? 1 : 0);
     if (d.paired) {
         d.staged = false;
         const uint32_t wb = (PairLayout(d.G, g.cells_per_task).bytes() + 48u + 127u) / 128u * 128u;
@@ -1091,6 +1095,7 @@ tf_status device_create(Problem &p, const int32_t *cell_material, const double *
     const void *kfn = d.fp64 ? (d.mode == 2 ? (const void *)sweep_kernel<double, 2>
                                             : d.mode == 1 ? (const void *)sweep_kernel<double, 1> : (const void *)sweep_kernel<double, 0>)
                              : (d.mode == 3   ? (const void *)sweep_kernel<float, 3>
+                                : d.mode == 4 ? (const void *)sweep_kernel<float, 4>
                                 : d.mode == 2 ? (const void *)sweep_kernel<float, 2>
                                 : d.mode == 1 ? (const void *)sweep_kernel<float, 1>
                                               : (const void *)sweep_kernel<float, 0>);
@@ -1298,8 +1303,9 @@ template <class T> tf_status launch_step(Problem &p, const double *phi_in, doubl
         const size_t dyn = (size_t)d.warp_smem * d.wpc;
         if constexpr (sizeof(T) == 4) {
             if (d.mode == 3) sweep_kernel<T, 3><<<d.grid, 32 * d.wpc, dyn, st>>>(A);
+            if (d.mode == 4) sweep_kernel<T, 4><<<d.grid, 32 * d.wpc, dyn, st>>>(A);
         }
-        if (d.mode == 3) {
+        if (d.mode == 3 || d.mode == 4) {
         } else if (d.mode == 2)
             sweep_kernel<T, 2><<<d.grid, 32 * d.wpc, dyn, st>>>(A);
         else if (d.mode == 1)

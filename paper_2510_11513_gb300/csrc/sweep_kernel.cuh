@@ -470,10 +470,10 @@ template <class T> struct StageLayout {
     }
 };
 
-// Bytes of shared memory one warp needs for the staged path's 3 stages (the mbarriers come on top).
-template <class T> inline size_t staged_warp_bytes(int G)
+// Bytes of shared memory one warp needs for the staged path's NS stages (the mbarriers come on top).
+template <class T> inline size_t staged_warp_bytes(int G, int NS = 3)
 {
-    return 3 * (sizeof(CellGeo<T>) + 4 * (size_t)G * sizeof(V4<T>));
+    return (size_t)NS * (sizeof(CellGeo<T>) + 4 * (size_t)G * sizeof(V4<T>));
 }
 
 // Packed FP32 pairs: both halves of a 64-bit register hold one group each and
@@ -775,11 +775,12 @@ __device__ __forceinline__ void solve_staged_cell(const SweepArgs<T> &A, const u
 // records, so every copy of cell k (record, source row, upwind rows) is issued
 // together, two cells ahead of the solve.  Returns false if a wait ran out
 // (error word set).
-template <class T, int NPL>
+template <class T, int NPL, int NS = 3>
 __device__ __forceinline__ bool run_task_staged(const SweepArgs<T> &A, uint4 ti, int lane, T ox, T oy, T oz,
                                                 size_t psi_dir, unsigned char *wsm, uint64_t *bars, uint32_t &ph,
                                                 unsigned long long *wacc)
 {
+    static_assert(NS == 2 || NS == 3, "two or three stages");
     const unsigned FULL = 0xffffffffu;
     const uint32_t ncell = ti.y & 0xffffu;
     const StageLayout<T> L(A.G);
@@ -802,7 +803,7 @@ __device__ __forceinline__ bool run_task_staged(const SweepArgs<T> &A, uint4 ti,
         nb.y = __shfl_sync(FULL, hi ? n_hi.y : n_lo.y, src);
         nb.z = __shfl_sync(FULL, hi ? n_hi.z : n_lo.z, src);
         nb.w = __shfl_sync(FULL, hi ? n_hi.w : n_lo.w, src);
-        const uint32_t s = k % 3u, mask = ek & 15u, c = ek >> 4;
+        const uint32_t s = k % (uint32_t)NS, mask = ek & 15u, c = ek >> 4;
         const uint32_t upm = (((mask & 1u) && nb.x >= 0) ? 1u : 0u) | (((mask & 2u) && nb.y >= 0) ? 2u : 0u) |
                              (((mask & 4u) && nb.z >= 0) ? 4u : 0u) | (((mask & 8u) && nb.w >= 0) ? 8u : 0u);
         const uint32_t n_up = __popc(upm);
@@ -827,11 +828,11 @@ __device__ __forceinline__ bool run_task_staged(const SweepArgs<T> &A, uint4 ti,
         }
     };
     issue(0);
-    if (ncell > 1) issue(1);
+    if (NS == 3 && ncell > 1) issue(1);
     for (uint32_t k = 0; k < ncell; ++k) {
-        const uint32_t s = k % 3u;
+        const uint32_t s = k % (uint32_t)NS;
         const uint32_t ek = __shfl_sync(FULL, k < 32 ? e_lo : e_hi, k & 31);
-        if (k + 2 < ncell) issue(k + 2);
+        if (k + NS - 1 < ncell) issue(k + NS - 1);
         if (!mbar_wait(&bars[s], (ph >> s) & 1u, A.wait_limit_ns, &A.ctrl->error, wacc)) return false;
         ph ^= 1u << s;
         if (!mbar_wait(&bars[3 + s], (ph >> (3 + s)) & 1u, A.wait_limit_ns, &A.ctrl->error, wacc)) return false;
@@ -1109,14 +1110,14 @@ __device__ __forceinline__ bool run_task_pairs(const SweepArgs<float> &A, uint4 
 __device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
 
 // Staged path with the groups-per-lane count unrolled for the common G = 32 and 64.
-template <class T>
+template <class T, int NS = 3>
 __device__ __forceinline__ bool run_task_staged_any(const SweepArgs<T> &A, uint4 ti, int lane, T ox, T oy, T oz,
                                                     size_t psi_dir, unsigned char *wsm, uint64_t *bars, uint32_t &ph,
                                                     unsigned long long *wacc)
 {
-    if (A.G == 64) return run_task_staged<T, 2>(A, ti, lane, ox, oy, oz, psi_dir, wsm, bars, ph, wacc);
-    if (A.G == 32) return run_task_staged<T, 1>(A, ti, lane, ox, oy, oz, psi_dir, wsm, bars, ph, wacc);
-    return run_task_staged<T, 0>(A, ti, lane, ox, oy, oz, psi_dir, wsm, bars, ph, wacc);
+    if (A.G == 64) return run_task_staged<T, 2, NS>(A, ti, lane, ox, oy, oz, psi_dir, wsm, bars, ph, wacc);
+    if (A.G == 32) return run_task_staged<T, 1, NS>(A, ti, lane, ox, oy, oz, psi_dir, wsm, bars, ph, wacc);
+    return run_task_staged<T, 0, NS>(A, ti, lane, ox, oy, oz, psi_dir, wsm, bars, ph, wacc);
 }
 
 // Persistent sweep: a warp claims a ticket (the next queue slot), waits until
@@ -1128,10 +1129,11 @@ __device__ __forceinline__ bool run_task_staged_any(const SweepArgs<T> &A, uint4
 // Termination: a warp whose ticket is >= n_tasks, or that waits while all
 // n_tasks tasks are complete, exits.  Every wait is bounded by wait_limit_ns.
 // MODE: 0 = any group count (registers), 1 = G a multiple of 32 (registers),
-// 2 = G a multiple of 32 with the rows staged in shared memory, 3 = FP32 and
-// G even: packed group pairs (pair-interleaved source and psi rows).
+// 2 = G a multiple of 32 with the rows staged in shared memory (three stages),
+// 3 = FP32 and G even: packed group pairs (pair-interleaved source and psi rows),
+// 4 = as 2 with two stages and six resident CTAs per SM (FP32).
 template <class T, int MODE>
-__global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 3) sweep_kernel(const SweepArgs<T> A)
+__global__ void __launch_bounds__(128, MODE == 4 ? 6 : (sizeof(T) == 4 ? 4 : 3)) sweep_kernel(const SweepArgs<T> A)
 {
     const int lane = threadIdx.x & 31;
     const unsigned FULL = 0xffffffffu;
@@ -1141,7 +1143,7 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 3) sweep_kernel(cons
     uint32_t ph = 0;  // mbarrier phase parities of this warp's stages
     // the six mbarriers of the staged paths sit in the last 48 bytes of the warp's region
     uint64_t *bars = reinterpret_cast<uint64_t *>(wsm + A.warp_smem - 48);
-    if constexpr (MODE == 2 || MODE == 3) {
+    if constexpr (MODE == 2 || MODE == 3 || MODE == 4) {
         if (lane == 0) {
             for (int b = 0; b < 6; ++b) mbar_init(&bars[b], 1);
             fence_proxy_async_shared();
@@ -1225,6 +1227,8 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 3) sweep_kernel(cons
             if (!run_task_pairs(A, ti, lane, om.x, om.y, om.z, psi_dir, wsm, bars, ph, ws + 6)) break;
         } else if constexpr (MODE == 2) {
             if (!run_task_staged_any(A, ti, lane, om.x, om.y, om.z, psi_dir, wsm, bars, ph, ws + 6)) break;
+        } else if constexpr (MODE == 4) {
+            if (!run_task_staged_any<T, 2>(A, ti, lane, om.x, om.y, om.z, psi_dir, wsm, bars, ph, ws + 6)) break;
         } else if constexpr (MODE == 1) {
             run_task_wide(A, ti, lane, om.x, om.y, om.z, psi_dir);
         } else {
@@ -1406,9 +1410,11 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 3) sweep_batch_kerne
         if constexpr (sizeof(T) == 4) {
             if (A.mode == 3) ok = run_task_pairs(A, ti, lane, om.x, om.y, om.z, psi_dir, wsm, bars, ph, ws + 6);
             else if (A.mode == 2) ok = run_task_staged_any(A, ti, lane, om.x, om.y, om.z, psi_dir, wsm, bars, ph, ws + 6);
+            else if (A.mode == 4) ok = run_task_staged_any<T, 2>(A, ti, lane, om.x, om.y, om.z, psi_dir, wsm, bars, ph, ws + 6);
             else run_task_generic(A, ti, lane, om.x, om.y, om.z, psi_dir);
         } else {
             if (A.mode == 2) ok = run_task_staged_any(A, ti, lane, om.x, om.y, om.z, psi_dir, wsm, bars, ph, ws + 6);
+            else if (A.mode == 4) ok = run_task_staged_any<T, 2>(A, ti, lane, om.x, om.y, om.z, psi_dir, wsm, bars, ph, ws + 6);
             else run_task_generic(A, ti, lane, om.x, om.y, om.z, psi_dir);
         }
         if (!ok) break;

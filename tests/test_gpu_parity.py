@@ -55,7 +55,8 @@ def test_one_sweep_matches_oracle(precision, G, cells_per_task, dir_chunk):
     (128, {}), (64, dict(pairing=2)), (32, dict(pairing=2, cells_per_task=3)), (128, dict(pairing=2)),
     (32, dict(pairing=1)), (64, dict(pairing=1)), (64, dict(pairing=1, staging=1)),
     (32, dict(pairing=1, staging=1, cells_per_task=9)), (8, dict(pairing=1)), (64, dict(octant_window=8)),
-    (64, dict(octant_window=1, dir_chunk=7)),
+    (64, dict(octant_window=1, dir_chunk=7)), (64, dict(staging=3)), (32, dict(staging=3, cells_per_task=5)),
+    (96, dict(staging=2, dir_chunk=11)), (64, dict(staging=2, cells_per_task=9)),
 ])
 def test_fp32_variants_match_oracle(G, opts):
     cfg = W.two_material_box(n=4, G=G, n_polar=4, n_az=8)
