@@ -67,7 +67,8 @@ typedef struct {
     int32_t precision;       /* tf_precision: arithmetic of local solves and psi storage (default TF_FP32) */
     int32_t device;          /* CUDA device ordinal (default 0) */
     int32_t cells_per_task;  /* cells of one t-level grouped into one task; 0 = automatic (about 1024 units,
-                              * 2048 on the shared-memory staged path, at most 32 or 64 cells),
+                              * 2048 on the shared-memory staged path with at most 32 cells, 256 on the
+                              * packed-pair path with 4 to 16 cells, otherwise at most 64 cells),
                               * -1 = autotuned for use on its own (wall time of trial sweeps over a
                               * direction sample), -2 = autotuned for batched use (busy time of the
                               * warps); choices cached per (precision, groups, directions, log2 cells) */

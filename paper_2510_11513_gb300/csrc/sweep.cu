@@ -655,6 +655,7 @@ struct DeviceState {
     int32_t G = 0, D = 0, M = 0;
     bool fp64 = false;
     bool two_stage = false;  // staged path with two stages (mode 4)
+    int pair_stages = 3;     // paired path: buffers in the ring of staged copies
     size_t tsize = 4;  // sizeof(T)
     void *geo = nullptr;
     uint32_t *cells = nullptr;
@@ -1084,10 +1085,26 @@ tf_status device_create(Problem &p, const int32_t *cell_material, const double *
     d.mode = d.paired ? 3 : d.staged ? (d.two_stage ? 4 : 2) : (d.G % 32 == 0 && g.cells_per_task <= 64 ? 1 : 0);
     if (d.paired) {
         d.staged = false;
-        const uint32_t wb = (PairLayout(d.G, g.cells_per_task).bytes() + 48u + 127u) / 128u * 128u;
-        while (d.wpc > 1 && wb * d.wpc > 227u * 1024u) d.wpc /= 2;
+        // three buffers unless two let more CTAs be resident per SM
+        auto warp_bytes = [&](int ns) { return (PairLayout(d.G, g.cells_per_task, ns).bytes() + 48u + 127u) / 128u * 128u; };
+        const uint32_t budget = 227u * 1024u;
+        auto resident = [&](int ns) {
+            const uint32_t w = warp_bytes(ns);
+            if (w * d.wpc > budget) return 0;
+            int n = 0;
+            const void *k3 = (const void *)sweep_kernel<float, 3>;
+            if (ensure_dyn_smem(k3, (int)(w * d.wpc)) != cudaSuccess ||
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k3, 32 * d.wpc, (size_t)w * d.wpc) != cudaSuccess) {
+                cudaGetLastError();
+                return 0;
+            }
+            return n;
+        };
+        d.pair_stages = resident(2) > resident(3) ? 2 : 3;
+        const uint32_t wb = warp_bytes(d.pair_stages);
+        while (d.wpc > 1 && wb * d.wpc > budget) d.wpc /= 2;
         d.warp_smem = wb;
-        const PairLayout L(d.G, g.cells_per_task);
+        const PairLayout L(d.G, g.cells_per_task, d.pair_stages);
         d.lpc_shift = (int)L.lpc_shift;
         d.ppl = (int)L.ppl;
     }
@@ -1237,6 +1254,7 @@ template <class T> SweepArgs<T> make_args(Problem &p, int k)
     A.window = std::min(d.window, ng);
     A.lpc_shift = d.lpc_shift;
     A.ppl = d.ppl;
+    A.stages = d.pair_stages;
     A.mode = d.mode;
     return A;
 }

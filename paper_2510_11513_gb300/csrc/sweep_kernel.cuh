@@ -176,6 +176,7 @@ template <class T> struct SweepArgs {
     const uint32_t *seeds;
     int32_t n_groups, window;
     int32_t lpc_shift, ppl;      // paired path: log2 lanes per cell, group pairs per lane
+    int32_t stages;              // paired path: buffers in the ring of staged copies (2 or 3)
     int32_t mode;                // kernel variant of this problem (batched launches dispatch on it)
 };
 
@@ -1021,8 +1022,8 @@ __device__ __forceinline__ void pair_solve(const SweepArgs<float> &A, const TabR
 // Shared memory of one warp on the paired path: the cell table and three stage
 // buffers (each: cps cells x [source row, 3 upwind rows]); the mbarriers come on top.
 struct PairLayout {
-    uint32_t P, row, cps, lpc_shift, ppl, stage, table;
-    __device__ __host__ PairLayout(int G, int max_cells)
+    uint32_t P, row, cps, lpc_shift, ppl, stage, table, ns;
+    __device__ __host__ PairLayout(int G, int max_cells, int stages = 3) : ns((uint32_t)stages)
     {
         P = (uint32_t)G / 2;
         row = P * 32u;
@@ -1033,12 +1034,12 @@ struct PairLayout {
         stage = cps * 4u * row;
         table = (uint32_t)max_cells * (uint32_t)sizeof(TabRow);
     }
-    __device__ __host__ uint32_t bytes() const { return table + 3u * stage; }
+    __device__ __host__ uint32_t bytes() const { return table + ns * stage; }
 };
 
 // One task on the paired path.  Lanes first build the task's cell table in
 // parallel (lane j: cell j), then the stages (cps cells each) stream through
-// a three-buffer ring of bulk asynchronous copies while lanes solve pairs:
+// a ring of A.stages (2 or 3) buffers of bulk asynchronous copies while lanes solve pairs:
 // lane l takes cell l >> lpc_shift of the stage and pairs (l mod lpc) + 32 m.
 // Returns false if a wait ran out (error word set).
 __device__ __forceinline__ bool run_task_pairs(const SweepArgs<float> &A, uint4 ti, int lane, float ox, float oy,
@@ -1047,7 +1048,7 @@ __device__ __forceinline__ bool run_task_pairs(const SweepArgs<float> &A, uint4 
 {
     const unsigned FULL = 0xffffffffu;
     const uint32_t ncell = ti.y & 0xffffu;
-    const PairLayout L(A.G, A.max_cells);
+    const PairLayout L(A.G, A.max_cells, A.stages);
     TabRow *tab = reinterpret_cast<TabRow *>(wsm);
     unsigned char *stages = wsm + L.table;
     for (uint32_t j = lane; j < ncell; j += 32) tab_setup(A, __ldg(A.cells + ti.x + j), ox, oy, oz, tab[j]);
@@ -1057,7 +1058,7 @@ __device__ __forceinline__ bool run_task_pairs(const SweepArgs<float> &A, uint4 
     // are read below by the async proxy
     fence_proxy_async_global();
     auto issue = [&](uint32_t st) {
-        const uint32_t b = st % 3u, k0 = st * L.cps;
+        const uint32_t b = st % L.ns, k0 = st * L.cps;
         const uint32_t k = k0 + (uint32_t)lane;
         const bool mine = (uint32_t)lane < L.cps && k < ncell;
         uint32_t upm = mine ? tab[k].upmask : 0u;
@@ -1087,10 +1088,10 @@ __device__ __forceinline__ bool run_task_pairs(const SweepArgs<float> &A, uint4 
         }
     };
     issue(0);
-    if (nst > 1) issue(1);
+    if (L.ns == 3u && nst > 1) issue(1);
     for (uint32_t st = 0; st < nst; ++st) {
-        if (st + 2 < nst) issue(st + 2);
-        const uint32_t b = st % 3u;
+        if (st + L.ns - 1u < nst) issue(st + L.ns - 1u);
+        const uint32_t b = st % L.ns;
         if (!mbar_wait(&bars[b], (ph >> b) & 1u, A.wait_limit_ns, &A.ctrl->error, wacc)) return false;
         ph ^= 1u << b;
         const uint32_t j = (uint32_t)lane >> L.lpc_shift, k = st * L.cps + j;
