@@ -23,8 +23,10 @@
  *   - creation inputs are host arrays; they are copied, the caller keeps them;
  *   - phi arrays passed to tf_sweep / tf_source_iterate are caller-owned,
  *     FP64, layout [n_cells][n_groups][4] (node i of cell c is local vertex i
- *     of tets[c]); they may live in device memory or in host memory (host
- *     buffers are copied in and out inside the call);
+ *     of tets[c]); they may live in device memory or in host memory (page-locked
+ *     host buffers mapped into the device address space, as cudaHostAlloc and
+ *     torch's pin_memory give, are read and written by the kernels directly
+ *     in tf_sweep; other host buffers are copied in and out inside the call);
  *   - `stream` is a cudaStream_t (NULL = the legacy default stream).
  * Device-side failures (a device wait that ran out, a bounds flag) are read
  * back when the call synchronises and returned as its status; the handle
@@ -66,9 +68,8 @@ typedef enum {
 typedef struct {
     int32_t precision;       /* tf_precision: arithmetic of local solves and psi storage (default TF_FP32) */
     int32_t device;          /* CUDA device ordinal (default 0) */
-    int32_t cells_per_task;  /* cells of one t-level grouped into one task; 0 = automatic (about 1024 units,
-                              * 2048 on the shared-memory staged path with at most 32 cells, 256 on the
-                              * packed-pair path with 4 to 16 cells, otherwise at most 64 cells),
+    int32_t cells_per_task;  /* cells of one t-level grouped into one task; 0 = automatic (about 1024 units
+                              * and at most 64 cells; 256 units and 4 to 16 cells on the packed-pair path),
                               * -1 = autotuned for use on its own (wall time of trial sweeps over a
                               * direction sample), -2 = autotuned for batched use (busy time of the
                               * warps); choices cached per (precision, groups, directions, log2 cells) */

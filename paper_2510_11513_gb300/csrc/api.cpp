@@ -185,14 +185,11 @@ tf_status tf_problem_create(tf_handle mesh, tf_handle quad, int32_t n_groups, in
         }
     }
     if (B == 0) {
-        // about 1024 units per task (2048 on the staged path, G a multiple of 32, whose
-        // per-task cost is higher; 256 and 4 to 16 cells on the FP32 paired path, whose
-        // per-task cell table sets how many CTAs fit per SM)
+        // about 1024 units per task (at most 64 cells); 256 units and 4 to 16 cells on the
+        // FP32 paired path, whose per-task cell table sets how many CTAs fit per SM
         const bool paired = p->opt.precision == TF_FP32 && n_groups % 2 == 0 &&
                             (p->opt.pairing == 2 || (p->opt.pairing == 0 && n_groups % 32 != 0));
-        const bool staged = !paired && n_groups % 32 == 0 && p->opt.staging != 1;
-        B = staged ? std::max(2, std::min(32, 2048 / n_groups))
-                   : paired ? std::max(4, std::min(16, 256 / n_groups)) : std::max(2, std::min(64, 1024 / n_groups));
+        B = paired ? std::max(4, std::min(16, 256 / n_groups)) : std::max(2, std::min(64, 1024 / n_groups));
     }
     tf_status s = build_task_graph(*m, *q, B, p->graph);
     if (s == TF_OK) s = device_create(*p, cell_material, sigma_t, sigma_s, Q, S1, psi_inflow);

@@ -1177,6 +1177,18 @@ bool is_device_pointer(const void *ptr)
     return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
+// Device address of page-locked host memory mapped into the device's address space
+// (cudaHostAlloc / torch pin_memory); NULL for anything else.
+void *mapped_host_pointer(const void *ptr)
+{
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, ptr) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
+}
+
 // q <- source(phi_in), for one problem.
 template <class T> void launch_source(Problem &p, const double *phi_in, cudaStream_t st)
 {
@@ -1411,15 +1423,24 @@ tf_status device_sweep(Problem &p, const double *phi_in, double *phi_out, void *
     const size_t bytes = (size_t)d.C * d.G * 4 * 8;
     const double *in = phi_in;
     double *out = phi_out;
+    // Pinned, mapped host buffers are read by the source kernel and written by the phi
+    // kernel directly (over the host link, overlapped with their work); other host
+    // memory goes through copies to and from device buffers.
     const bool host_in = !is_device_pointer(phi_in), host_out = !is_device_pointer(phi_out);
+    const double *map_in = host_in ? (const double *)mapped_host_pointer(phi_in) : nullptr;
+    double *map_out = host_out ? (double *)mapped_host_pointer(phi_out) : nullptr;
     if (host_in) {
-        TF_CUDA(cudaMemcpyAsync(d.phi_buf[0], phi_in, bytes, cudaMemcpyHostToDevice, st));
-        in = d.phi_buf[0];
+        if (map_in) {
+            in = map_in;
+        } else {
+            TF_CUDA(cudaMemcpyAsync(d.phi_buf[0], phi_in, bytes, cudaMemcpyHostToDevice, st));
+            in = d.phi_buf[0];
+        }
     }
-    if (host_out) out = d.phi_buf[1];
+    if (host_out) out = map_out ? map_out : d.phi_buf[1];
     tf_status s = step(p, in, out, st);
     if (s != TF_OK) return s;
-    if (host_out) TF_CUDA(cudaMemcpyAsync(phi_out, out, bytes, cudaMemcpyDeviceToHost, st));
+    if (host_out && !map_out) TF_CUDA(cudaMemcpyAsync(phi_out, out, bytes, cudaMemcpyDeviceToHost, st));
     return collect(p, st);
 }
 

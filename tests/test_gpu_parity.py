@@ -192,8 +192,16 @@ def test_host_buffers_match_device_buffers():
     assert np.array_equal(out_h, out_d.cpu().numpy())
     pinned = torch.from_numpy(phi_in).pin_memory()
     out_p = torch.zeros((C, 6, 4), dtype=torch.float64).pin_memory()
-    prob.sweep(pinned, out_p)
+    prob.sweep(pinned, out_p)  # mapped pinned memory: the kernels read and write it directly
     assert np.array_equal(out_p.numpy(), out_h)
+    # several direction chunks: the phi kernel accumulates into the mapped host buffer
+    chunked = tf.Problem.from_config(cfg, precision=tf.TF_FP64, dir_chunk=5)
+    out_c = torch.full((C, 6, 4), -1.0, dtype=torch.float64).pin_memory()
+    chunked.sweep(pinned, out_c)
+    assert _rel(out_c.numpy(), out_h) < 1e-13
+    out_cd = torch.zeros((C, 6, 4), dtype=torch.float64, device="cuda")
+    chunked.sweep(_dev(phi_in), out_cd)
+    assert np.array_equal(out_c.numpy(), out_cd.cpu().numpy())
 
 
 def test_device_wait_limit_returns_timeout_and_handle_stays_usable():
