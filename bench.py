@@ -205,6 +205,52 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+SCHEDULES = {"amt": 0, "bsp": 1, "bsp_launch": 2}
+
+
+def _schedule_leg(tf, cfg, prec, local, stream, steps, schedule, torch):
+    """One schedule on one workload: warm-up sweep, then `steps` source iterations
+    timed with CUDA events; returns ms per step, sweep-kernel ms and warp-time split."""
+    dev = torch.device("cuda", local)
+    pr = tf.Problem.from_config(cfg, precision=prec, device=local, schedule=SCHEDULES[schedule])
+    ph = torch.zeros((pr.n_cells, pr.n_groups, 4), dtype=torch.float64, device=dev)
+    pr.source_iterate(ph, 0.0, 1, stream=stream)
+    st0 = pr.stats()
+    torch.cuda.synchronize(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    r = pr.source_iterate(ph, 0.0, steps, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    st = pr.stats()
+    ms = e0.elapsed_time(e1) / steps
+    sweep_ms = (st["cum_sweep_event_seconds"] - st0["cum_sweep_event_seconds"]) / steps * 1e3
+    out = {"ms_per_step": ms, "sweep_ms": sweep_ms, "grind": ms * 1e6 / pr.n_units,
+           "warp_wait_frac": st["wait_seconds"] / max(st["wait_seconds"] + st["busy_seconds"], 1e-30),
+           "n_buckets": st["n_buckets"], "launches_per_step": st["launches_per_step"],
+           "grid_ctas": st["grid_ctas"], "cells_per_task": st["cells_per_task"], "iterations": r["iterations"]}
+    pr.close()
+    del pr, ph
+    torch.cuda.synchronize(dev)
+    return out
+
+
+def schedule_ablation(tf, cfg, prec, local, stream, steps, torch, amt=None):
+    """Many-task (AMT) against bulk-synchronous (BSP: grid barrier after every
+    (octant, t-level) bucket; BSP_LAUNCH: one launch per bucket) on one workload.
+    `amt` reuses a measurement of the AMT schedule made elsewhere."""
+    res = {"workload": cfg["name"], "steps": steps}
+    for name in ("amt", "bsp", "bsp_launch"):
+        if name == "amt" and amt is not None:
+            res[name] = amt
+            continue
+        res[name] = _schedule_leg(tf, cfg, prec, local, stream, steps, name, torch)
+    for name in ("bsp", "bsp_launch"):
+        res[f"amt_speedup_over_{name}"] = res[name]["ms_per_step"] / res["amt"]["ms_per_step"]
+    return res
+
+
 def run_ours(args):
     import torch
 
@@ -221,7 +267,7 @@ def run_ours(args):
     t_setup = time.perf_counter()
     prob = tf.Problem.from_config(cfg, precision=prec, device=local, cells_per_task=args.cells_per_task,
                                   warps_per_cta=args.warps_per_cta, octant_window=args.octant_window,
-                                  staging=args.staging, pairing=args.pairing)
+                                  staging=args.staging, pairing=args.pairing, schedule=SCHEDULES[args.schedule])
     t_setup = time.perf_counter() - t_setup
     C, G, D = prob.n_cells, prob.n_groups, prob.n_dirs
     units = prob.n_units
@@ -260,17 +306,20 @@ def run_ours(args):
     b_unit = 8 * s + (geo + 4) / G
     peak, peak_kind = _peaks()
     achieved = b_unit * units / sweep_s / 1e9
+    klabel = ("sweep_kernel" if args.schedule == "amt" else "bsp_sweep_kernel") + \
+        f"<{'float' if s == 4 else 'double'}, {mode}>"
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32" if prec == tf.TF_FP32 else "f64", "data": "synthetic",
             "config": {"workload": cfg["name"], "cells": C, "directions": D, "groups": G,
                        "units_per_step": units, "precision": args.precision, "phi_accumulate": "fp32-pair->fp64",
                        "l2": "inputs larger than L2 (psi store %.1f GB)" % (units * 4 * s / 1e9),
-                       "parallelism": f"replicas{world}", "setup_s": round(t_setup, 2)},
+                       "parallelism": f"replicas{world}", "setup_s": round(t_setup, 2),
+                       "schedule": args.schedule},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak,
-                         "traffic": _traffic(cfg["name"], args.precision, f"sweep_kernel<{'float' if s == 4 else 'double'}, {mode}>"),
-                         "kernel": f"sweep_kernel<{'float' if s == 4 else 'double'}, {mode}>",
+                         "traffic": _traffic(cfg["name"], args.precision, klabel),
+                         "kernel": klabel,
                          "bytes_per_unit": b_unit, "peak_kind": peak_kind,
                          "algorithmic_bytes_per_launch": b_unit * units},
             "breakdown_ms": {"source": src_s * 1e3, "sweep": sweep_s * 1e3, "phi": phi_s * 1e3,
@@ -302,9 +351,22 @@ def run_ours(args):
         line["e2e"] = {"value": e2e_ms * 1e6 / units / world, "unit": UNIT, "h2d_bytes_per_step": nbytes,
                        "d2h_bytes_per_step": nbytes, "ms_per_step": e2e_ms,
                        "call": "tf_sweep(host pinned phi_in, host pinned phi_out)"}
+    amt_main = None
+    if args.schedule == "amt":
+        amt_main = {"ms_per_step": ms_per_step, "sweep_ms": sweep_s * 1e3, "grind": grind,
+                    "warp_wait_frac": line["scheduling"]["wait_frac"], "n_buckets": 0,
+                    "launches_per_step": st1["launches_per_step"], "grid_ctas": st1["grid_ctas"],
+                    "cells_per_task": st1["cells_per_task"], "iterations": args.steps}
+    prob.close()
+    del prob
+    torch.cuda.synchronize(dev)
+    if not args.no_bsp_compare and world == 1:
+        # the paper's comparison (Sec. 5): many-task against level-synchronous buckets,
+        # on this workload and on the 16^3-hex one nearest the paper's own
+        abl = [schedule_ablation(tf, cfg, prec, local, stream, args.bsp_steps, torch, amt_main)]
+        abl.append(schedule_ablation(tf, W.paper_context_box(), prec, local, stream, 5, torch))
+        line["schedule_ablation"] = abl
     if not args.no_fp64_compare and prec == tf.TF_FP32:
-        del prob
-        torch.cuda.synchronize(dev)
         p64 = tf.Problem.from_config(cfg, precision=tf.TF_FP64, device=local)
         phi64 = torch.zeros((C, G, 4), dtype=torch.float64, device=dev)
         p64.source_iterate(phi64, 0.0, 1, stream=stream)
@@ -489,6 +551,10 @@ def main():
     ap.add_argument("--no-fp64-compare", action="store_true", help="skip the plain FP64 GPU sweep comparison")
     ap.add_argument("--no-time-to-tol", action="store_true", help="skip the time-to-1e-6 comparison")
     ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--schedule", default="amt", choices=sorted(SCHEDULES),
+                    help="task schedule of the timed sweep: many-task (amt) or bulk-synchronous")
+    ap.add_argument("--no-bsp-compare", action="store_true", help="skip the many-task vs bulk-synchronous legs")
+    ap.add_argument("--bsp-steps", type=int, default=2, help="timed steps of each schedule in the comparison")
     ap.add_argument("--octant-window", type=int, default=0, help="octants active at once (0 = library default)")
     ap.add_argument("--staging", type=int, default=0, help="0 auto, 1 no shared-memory staging, 2 two stages, 3 three stages")
     ap.add_argument("--pairing", type=int, default=0, help="0 auto, 1 off, 2 packed group pairs when G is even")

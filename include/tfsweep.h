@@ -65,20 +65,40 @@ typedef enum {
     TF_PHI_DADD = 1   /* one FP64 multiply-add per direction and node */
 } tf_phi_accumulate;
 
+/* Task schedule of the sweep.  All run (cell block, direction) tasks with the same local solves, and
+ * a solve reads only finished upwind rows, so all give bit-identical psi and phi: only the order of
+ * the work (and the default task grain, see cells_per_task) differs.
+ *   TF_SCHED_AMT         asynchronous many-task (Sec. 3, Algorithm 1): one persistent launch per
+ *                        direction chunk; a task runs as soon as its upwind tasks are done
+ *                        (dependency counters, device ready queue).
+ *   TF_SCHED_BSP         bulk-synchronous (Sec. 2.1): per direction chunk, buckets of (octant,
+ *                        t-level) with the buckets of an octant's directions merged (simultaneous
+ *                        angles); octants in sequence, levels in order, the tasks of a bucket in
+ *                        parallel, a device-wide barrier after every bucket; one cooperative
+ *                        persistent launch per chunk.
+ *   TF_SCHED_BSP_LAUNCH  the same buckets with one kernel launch per bucket (the launch boundary
+ *                        is the barrier).
+ * Batched calls (n > 1) run only TF_SCHED_AMT problems. */
+typedef enum { TF_SCHED_AMT = 0, TF_SCHED_BSP = 1, TF_SCHED_BSP_LAUNCH = 2 } tf_schedule;
+
 typedef struct {
     int32_t precision;       /* tf_precision: arithmetic of local solves and psi storage (default TF_FP32) */
     int32_t device;          /* CUDA device ordinal (default 0) */
     int32_t cells_per_task;  /* cells of one t-level grouped into one task; 0 = automatic (about 1024 units
-                              * and at most 64 cells; 256 units and 4 to 16 cells on the packed-pair path),
+                              * and at most 64 cells; 256 units and 4 to 16 cells on the packed-pair path;
+                              * a quarter of that, at least 2, with a bulk-synchronous schedule),
                               * -1 = autotuned for use on its own (wall time of trial sweeps over a
                               * direction sample), -2 = autotuned for batched use (busy time of the
-                              * warps); choices cached per (precision, groups, directions, log2 cells) */
+                              * warps); choices cached per (precision, schedule, groups, directions,
+                              * log2 cells) */
     int32_t dir_chunk;       /* directions swept per persistent launch; 0 = as many as the memory budget allows */
     int32_t warps_per_cta;   /* persistent kernel CTA size in warps; 0 = automatic */
     int32_t ctas_per_sm;     /* persistent CTAs per SM; 0 = as many as are resident */
     double wait_limit_s;     /* a device wait gives up after this many seconds (default 10) */
     int32_t phi_accumulate;  /* tf_phi_accumulate (default TF_PHI_PAIR) */
-    int32_t inject_stall;    /* fault injection for tests: 1 = seed no task, so every device wait runs out */
+    int32_t inject_stall;    /* fault injection for tests: 1 = every device wait runs out (TF_SCHED_AMT:
+                              * no task is seeded; TF_SCHED_BSP: each barrier waits for one CTA more
+                              * than the grid holds); not allowed with TF_SCHED_BSP_LAUNCH */
     double psi_budget_gb;    /* device memory allowed for the angular-flux store; 0 = 80 % of free memory */
     int32_t task_order;      /* 0 = FIFO ready queue, seeds longest-critical-path first */
     int32_t staging;         /* 0 = automatic: stage each cell's rows in shared memory with bulk
@@ -91,7 +111,8 @@ typedef struct {
     int32_t pairing;         /* FP32, even group count: solve two groups per lane with packed FP32x2
                               * arithmetic.  0 = automatic (when n_groups is not a multiple of 32),
                               * 1 = never, 2 = whenever n_groups is even */
-    int32_t reserved_i[4];
+    int32_t schedule;        /* tf_schedule: how the sweep orders its tasks (default TF_SCHED_AMT) */
+    int32_t reserved_i[3];
     double residual_floor;   /* stopping-test denominator floor, as a fraction of the group's max |phi|:
                               * 1 (the default; 0 also means 1) = per-group max-norm relative change,
                               * 1e-10 = pointwise relative change (unreachable in FP32 where DG
@@ -131,7 +152,8 @@ typedef struct {
     int32_t cells_per_task;
     int64_t tasks_executed;    /* counted on the device in the last sweep */
     int64_t wait_polls;        /* device polls of an empty queue slot in the last sweep */
-    double wait_seconds;       /* summed over warps: time spent waiting for a ready task */
+    double wait_seconds;       /* summed over warps: time spent waiting for a ready task (TF_SCHED_AMT)
+                                * or at the barriers between buckets (TF_SCHED_BSP) */
     double busy_seconds;       /* summed over warps: time spent executing tasks */
     double kernel_seconds;     /* first warp start to last warp end, summed over launches */
     double mean_ready;         /* mean ready-queue depth sampled at pops */
@@ -150,7 +172,9 @@ typedef struct {
     int32_t tuned_n, tuned_cached;
     int32_t tuned_candidates[8];
     double tuned_seconds[8];
-    int32_t reserved_i[5];
+    int32_t n_buckets;          /* bulk-synchronous schedules: (octant, t-level) buckets per sweep,
+                                 * summed over direction chunks (barriers + chunks); 0 for TF_SCHED_AMT */
+    int32_t reserved_i[4];
     double data_wait_seconds;  /* summed over warps: time waiting for rows staged by bulk copies
                                 * (SM cycles at the nominal SM clock) */
     double reserved_d[5];

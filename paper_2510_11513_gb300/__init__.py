@@ -8,6 +8,7 @@ library cannot be built or loaded, `load()` raises.
 """
 from .tfsweep import (TF_ERR_ARG, TF_ERR_CUDA, TF_ERR_CYCLE, TF_ERR_DEVICE, TF_ERR_MESH, TF_ERR_NOMEM,  # noqa: F401
                       TF_ERR_NOT_CONVERGED, TF_ERR_TIMEOUT, TF_FP32, TF_FP64, TF_OK, TF_PHI_DADD, TF_PHI_PAIR,
+                      TF_SCHED_AMT, TF_SCHED_BSP, TF_SCHED_BSP_LAUNCH,
                       Mesh, Mlp, Problem, Quadrature, TfError, library_path, load, options, source_iterate_batch,
                       sweep_batch, tf_destroy, tf_mlp_adam_step, tf_mlp_create, tf_mlp_features, tf_mlp_fit_scale,
                       tf_mlp_fit_inputs, tf_mlp_forward, tf_mlp_gradients, tf_mlp_input_scale, tf_mlp_limits, tf_mlp_params, tf_mlp_predict_phi, tf_mlp_scale, tf_mlp_shrink,

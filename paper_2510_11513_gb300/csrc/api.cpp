@@ -165,6 +165,12 @@ tf_status tf_problem_create(tf_handle mesh, tf_handle quad, int32_t n_groups, in
         delete p;
         return fail(TF_ERR_ARG, "tf_problem_create: precision must be TF_FP32 or TF_FP64");
     }
+    if (p->opt.schedule < TF_SCHED_AMT || p->opt.schedule > TF_SCHED_BSP_LAUNCH ||
+        (p->opt.inject_stall && p->opt.schedule == TF_SCHED_BSP_LAUNCH)) {
+        delete p;
+        return fail(TF_ERR_ARG, "tf_problem_create: schedule must be a tf_schedule (inject_stall: not with "
+                                "TF_SCHED_BSP_LAUNCH, which has no device wait)");
+    }
     if (!(p->opt.wait_limit_s > 0.0)) p->opt.wait_limit_s = 10.0;
     if (!(p->opt.residual_floor > 0.0) || p->opt.residual_floor > 1.0) p->opt.residual_floor = 1.0;
     p->mesh = m;
@@ -190,6 +196,11 @@ tf_status tf_problem_create(tf_handle mesh, tf_handle quad, int32_t n_groups, in
         const bool paired = p->opt.precision == TF_FP32 && n_groups % 2 == 0 &&
                             (p->opt.pairing == 2 || (p->opt.pairing == 0 && n_groups % 32 != 0));
         B = paired ? std::max(4, std::min(16, 256 / n_groups)) : std::max(2, std::min(64, 1024 / n_groups));
+        // Bulk-synchronous schedules: a bucket's tasks must cover the resident warps, and
+        // most buckets hold fewer cells than the many-task grain assumes; a quarter of it
+        // (at least 2 cells) took the least time over grains 1..64 on the 16^3-hex,
+        // 128-direction, 16-group and the 48^3-hex, 192-direction, 64-group boxes.
+        if (p->opt.schedule != TF_SCHED_AMT) B = std::max(2, B / 4);
     }
     tf_status s = build_task_graph(*m, *q, B, p->graph);
     if (s == TF_OK) s = device_create(*p, cell_material, sigma_t, sigma_s, Q, S1, psi_inflow);

@@ -4,7 +4,8 @@
 // (precision, criterion, groups, directions, log2 cells).  Criterion: the wall
 // time of the trial sweep (cells_per_task = -1, a problem swept on its own) or
 // the summed busy time of the warps (-2, a problem swept in a batch, where the
-// other problems keep the GPU busy).
+// other problems keep the GPU busy).  The trial sweeps use the problem's own
+// schedule (many-task or bulk-synchronous), which is part of the cache key.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -31,7 +32,8 @@ tf_status autotune_cells_per_task(const Mesh &m, const Quad &q, int32_t G, int32
                                   int32_t *out, tf_autotune_report *rep)
 {
     const int lc = (int)std::lround(std::log2((double)std::max<int64_t>(m.nc, 1)));
-    const auto key = std::make_tuple(opt.precision * 4 + (opt.cells_per_task == -2 ? 1 : 0), G, q.D, lc);
+    const auto key =
+        std::make_tuple(opt.precision * 16 + opt.schedule * 4 + (opt.cells_per_task == -2 ? 1 : 0), G, q.D, lc);
     {
         std::lock_guard<std::mutex> lk(g_mu);
         auto it = g_cache.find(key);
@@ -53,8 +55,8 @@ tf_status autotune_cells_per_task(const Mesh &m, const Quad &q, int32_t G, int32
     const bool paired = opt.precision == TF_FP32 && G % 2 == 0 && (opt.pairing == 2 || (opt.pairing == 0 && G % 32 != 0));
     const int cap = paired ? 32 : 64;
     std::vector<int32_t> cand;
-    for (int32_t b : {4, 8, 16, 32, 64})
-        if (b <= cap && (int64_t)b * G <= 4096) cand.push_back(b);
+    for (int32_t b : {2, 4, 8, 16, 32, 64})
+        if ((b > 2 || opt.schedule != TF_SCHED_AMT) && b <= cap && (int64_t)b * G <= 4096) cand.push_back(b);
     if (cand.empty()) cand.push_back(std::max(2, std::min(cap, 1024 / G)));
     std::vector<double> phi((size_t)m.nc * G * 4, 0.0);
     for (size_t i = 0; i < phi.size(); ++i) phi[i] = 1.0;

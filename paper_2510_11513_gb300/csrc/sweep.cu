@@ -28,6 +28,7 @@
 namespace tf {
 
 #include "sweep_kernel.cuh"
+#include "bsp.h"
 
 // New launch: bump the epoch, empty the queue.
 __global__ void begin_kernel(Ctrl *ctrl, unsigned long long n_seeds, int reset_stats, int first_group)
@@ -704,6 +705,14 @@ struct DeviceState {
     int lpc_shift = 0, ppl = 0;
     int mode = 0;  // sweep kernel variant (see sweep_kernel)
     uint32_t warp_smem = 0;
+    // bulk-synchronous schedules: task ids grouped by (octant, t-level) bucket, per chunk
+    int schedule = TF_SCHED_AMT;
+    uint32_t *bsp_order = nullptr;
+    uint32_t *bsp_bucket = nullptr;          // [n_buckets + 1] offsets into bsp_order
+    unsigned int *bsp_bar = nullptr;         // grid-barrier arrival counter
+    std::vector<uint32_t> bsp_bucket_host;
+    std::vector<int32_t> chunk_bucket_begin;  // [n_chunks + 1]
+    int bsp_grid = 0;
     int stats_blocks = 0;
     int last_chunk = -1;
     std::vector<void *> allocs;
@@ -1060,6 +1069,47 @@ tf_status device_create(Problem &p, const int32_t *cell_material, const double *
         d.chunk_seed_begin[k + 1] = (int64_t)seeds.size();
     }
     d.chunk_group_begin[d.n_chunks] = (int32_t)group_total.size();
+    // Bulk-synchronous schedules: per chunk, one bucket per (octant group, t-level),
+    // groups in order and levels ascending within a group; a bucket lists the
+    // tasks of all the group's directions on that level (direction, then block order).
+    d.schedule = p.opt.schedule;
+    if (d.schedule != TF_SCHED_AMT) {
+        std::vector<uint32_t> order;
+        order.reserve((size_t)T);
+        d.bsp_bucket_host.clear();
+        d.chunk_bucket_begin.assign(d.n_chunks + 1, 0);
+        for (int k = 0; k < d.n_chunks; ++k) {
+            const int a0 = k * Dc, a1 = std::min(d.D, a0 + Dc);
+            const int ngrp = d.chunk_group_begin[k + 1] - d.chunk_group_begin[k];
+            d.chunk_bucket_begin[k] = (int32_t)d.bsp_bucket_host.size();
+            for (int j = 0; j < ngrp; ++j) {
+                int L = 0;
+                for (int a = a0; a < a1; ++a)
+                    if (dir_group[a] == j) L = std::max(L, g.dir_levels[a]);
+                std::vector<size_t> start(L + 1, 0);
+                for (int a = a0; a < a1; ++a)
+                    if (dir_group[a] == j)
+                        for (int64_t t = g.dir_task_begin[a]; t < g.dir_task_begin[a + 1]; ++t) ++start[g.task_level[t] + 1];
+                for (int l = 0; l < L; ++l) start[l + 1] += start[l];
+                const size_t base = order.size();
+                order.resize(base + start[L]);
+                std::vector<size_t> pos(start.begin(), start.end() - 1);
+                for (int a = a0; a < a1; ++a)
+                    if (dir_group[a] == j)
+                        for (int64_t t = g.dir_task_begin[a]; t < g.dir_task_begin[a + 1]; ++t)
+                            order[base + pos[g.task_level[t]]++] = (uint32_t)t;
+                for (int l = 0; l < L; ++l) d.bsp_bucket_host.push_back((uint32_t)(base + start[l]));
+            }
+        }
+        d.chunk_bucket_begin[d.n_chunks] = (int32_t)d.bsp_bucket_host.size();
+        d.bsp_bucket_host.push_back((uint32_t)order.size());
+        // the claim counters of the buckets reuse the task counters: a bucket holds at least one task
+        if ((int64_t)order.size() != T || (int64_t)d.bsp_bucket_host.size() - 1 > T)
+            return fail(TF_ERR_DEVICE, "bulk-synchronous schedule does not cover the task graph");
+        if ((s = upload(d, &d.bsp_order, order.data(), order.size() * 4)) != TF_OK) return s;
+        if ((s = upload(d, &d.bsp_bucket, d.bsp_bucket_host.data(), d.bsp_bucket_host.size() * 4)) != TF_OK) return s;
+        if ((s = dmalloc(d, &d.bsp_bar, sizeof(unsigned int))) != TF_OK) return s;
+    }
     d.window = p.opt.octant_window > 0 ? p.opt.octant_window : 8;
     if ((s = upload(d, &d.dir_group, dir_group.data(), dir_group.size() * 4)) != TF_OK) return s;
     if ((s = upload(d, &d.group_total, group_total.data(), group_total.size() * 4)) != TF_OK) return s;
@@ -1121,6 +1171,17 @@ tf_status device_create(Problem &p, const int32_t *cell_material, const double *
     TF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, 32 * d.wpc, dyn));
     if (p.opt.ctas_per_sm > 0) per_sm = std::min(per_sm, p.opt.ctas_per_sm);
     d.grid = std::max(1, per_sm) * d.sm_count;
+    if (d.schedule != TF_SCHED_AMT) {
+        // bulk-synchronous kernel of the same variant; its cooperative launch needs a co-resident grid
+        const void *bfn = d.fp64 ? bsp_kernel_fn<double>(d.mode) : bsp_kernel_fn<float>(d.mode);
+        if (dyn > 0) TF_CUDA(ensure_dyn_smem(bfn, dyn));
+        int bsm = 0;
+        TF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bsm, bfn, 32 * d.wpc, dyn));
+        if (p.opt.ctas_per_sm > 0) bsm = std::min(bsm, p.opt.ctas_per_sm);
+        if (bsm < 1) return fail(TF_ERR_CUDA, "bulk-synchronous sweep kernel cannot be resident");
+        d.bsp_grid = bsm * d.sm_count;
+        p.stats.n_buckets = d.chunk_bucket_begin[d.n_chunks];
+    }
     d.ev_start.resize(1 + 2 * d.n_chunks);
     d.ev_stop.resize(1 + 2 * d.n_chunks);
     for (size_t i = 0; i < d.ev_start.size(); ++i) {
@@ -1129,7 +1190,11 @@ tf_status device_create(Problem &p, const int32_t *cell_material, const double *
     }
     TF_CUDA(cudaDeviceSynchronize());
     // source; per chunk: begin, fill, sweep, end, phi and (with boundary cells) leakage
-    p.stats.launches_per_step = 1 + (5 + (d.n_bcells > 0 ? 1 : 0)) * (int64_t)d.n_chunks;
+    if (d.schedule == TF_SCHED_AMT)
+        p.stats.launches_per_step = 1 + (5 + (d.n_bcells > 0 ? 1 : 0)) * (int64_t)d.n_chunks;
+    else  // begin, sweep (one, or one per bucket), end, phi, leakage
+        p.stats.launches_per_step = 1 + (3 + (d.n_bcells > 0 ? 1 : 0)) * (int64_t)d.n_chunks +
+                                    (d.schedule == TF_SCHED_BSP ? (int64_t)d.n_chunks : (int64_t)p.stats.n_buckets);
     p.stats.kernel_mode = d.mode;
     TF_CUDA(cudaStreamCreateWithFlags(&d.istream, cudaStreamNonBlocking));
     TF_CUDA(cudaEventCreateWithFlags(&d.ev_user, cudaEventDisableTiming));
@@ -1139,7 +1204,7 @@ tf_status device_create(Problem &p, const int32_t *cell_material, const double *
     p.stats.n_dirs = d.D;
     p.stats.max_level = g.max_level;
     p.stats.n_chunks = d.n_chunks;
-    p.stats.grid_ctas = d.grid;
+    p.stats.grid_ctas = d.schedule == TF_SCHED_AMT ? d.grid : d.bsp_grid;
     p.stats.warps_per_cta = d.wpc;
     p.stats.cells_per_task = g.cells_per_task;
     return TF_OK;
@@ -1317,6 +1382,36 @@ template <class T> tf_status launch_step(Problem &p, const double *phi_in, doubl
     TF_CUDA(cudaGetLastError());
     TF_CUDA(record_event(d.ev_stop[0], st));
     for (int k = 0; k < d.n_chunks; ++k) {
+        if (d.schedule != TF_SCHED_AMT) {
+            // bulk-synchronous: the chunk's buckets in sequence, a barrier after each
+            begin_kernel<<<1, 1, 0, st>>>(d.ctrl, 0ull, k == 0, 0);
+            const int b0 = d.chunk_bucket_begin[k], b1 = d.chunk_bucket_begin[k + 1];
+            TF_CUDA(cudaMemsetAsync(d.counters + b0, 0, sizeof(int) * (size_t)(b1 - b0), st));
+            TF_CUDA(cudaMemsetAsync(d.bsp_bar, 0, sizeof(unsigned int), st));
+            const SweepArgs<T> A = make_args<T>(p, k);
+            BspArgs S{d.bsp_order, d.bsp_bucket, d.counters, d.bsp_bar, b0, b1, p.opt.inject_stall ? 1 : 0};
+            const size_t dyn = (size_t)d.warp_smem * d.wpc;
+            TF_CUDA(record_event(d.ev_start[1 + 2 * k], st));
+            if (d.schedule == TF_SCHED_BSP) {
+                TF_CUDA(launch_bsp<T>(A, S, d.mode, d.bsp_grid, 32 * d.wpc, dyn, true, st));
+            } else {
+                for (int b = b0; b < b1; ++b) {
+                    S.b_lo = b;
+                    S.b_hi = b + 1;
+                    const int64_t nt = (int64_t)d.bsp_bucket_host[b + 1] - (int64_t)d.bsp_bucket_host[b];
+                    const int gr = (int)std::min<int64_t>(d.bsp_grid, (nt + d.wpc - 1) / d.wpc);
+                    TF_CUDA(launch_bsp<T>(A, S, d.mode, gr, 32 * d.wpc, dyn, false, st));
+                }
+            }
+            TF_CUDA(record_event(d.ev_stop[1 + 2 * k], st));
+            end_kernel<<<1, 1, 0, st>>>(d.ctrl);
+            TF_CUDA(record_event(d.ev_start[2 + 2 * k], st));
+            launch_phi<T>(p, k, phi_out, st);
+            TF_CUDA(cudaGetLastError());
+            TF_CUDA(record_event(d.ev_stop[2 + 2 * k], st));
+            d.last_chunk = k;
+            continue;
+        }
         const int64_t t0 = d.chunk_task_begin[k], t1 = d.chunk_task_begin[k + 1];
         const int gb = d.chunk_group_begin[k], ng = d.chunk_group_begin[k + 1] - gb;
         const int win = std::min(d.window, ng);
@@ -1619,6 +1714,8 @@ tf_status batch_setup(BatchRun &B, const tf_handle *problems, int32_t n)
         if (p->dev->device != B.device || p->dev->fp64 != B.fp64)
             return fail(TF_ERR_ARG, "batched problems must share one device and one precision");
         if (p->opt.inject_stall) return fail(TF_ERR_ARG, "inject_stall is not supported in batched launches");
+        if (p->dev->schedule != TF_SCHED_AMT)
+            return fail(TF_ERR_ARG, "batched launches run only problems with the TF_SCHED_AMT schedule");
         B.max_chunks = std::max(B.max_chunks, p->dev->n_chunks);
         B.warp_smem = std::max(B.warp_smem, p->dev->warp_smem);
     }

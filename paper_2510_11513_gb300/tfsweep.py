@@ -22,6 +22,7 @@ TF_OK, TF_ERR_ARG, TF_ERR_MESH, TF_ERR_CYCLE, TF_ERR_CUDA, TF_ERR_NOMEM, TF_ERR_
     TF_ERR_NOT_CONVERGED, TF_ERR_DEVICE = range(9)
 TF_FP32, TF_FP64 = 0, 1
 TF_PHI_PAIR, TF_PHI_DADD = 0, 1
+TF_SCHED_AMT, TF_SCHED_BSP, TF_SCHED_BSP_LAUNCH = 0, 1, 2
 
 SYMBOLS = (
     "tf_options_default", "tf_mesh_create", "tf_quadrature_create", "tf_problem_create", "tf_sweep",
@@ -40,7 +41,7 @@ class tf_options(C.Structure):
         ("warps_per_cta", C.c_int32), ("ctas_per_sm", C.c_int32), ("wait_limit_s", C.c_double),
         ("phi_accumulate", C.c_int32), ("inject_stall", C.c_int32), ("psi_budget_gb", C.c_double),
         ("task_order", C.c_int32), ("staging", C.c_int32), ("octant_window", C.c_int32),
-        ("pairing", C.c_int32), ("reserved_i", C.c_int32 * 4),
+        ("pairing", C.c_int32), ("schedule", C.c_int32), ("reserved_i", C.c_int32 * 3),
         ("residual_floor", C.c_double),
         ("reserved_d", C.c_double * 3),
     ]
@@ -65,7 +66,8 @@ class tf_stats(C.Structure):
         ("cum_sweep_event_seconds", C.c_double), ("cum_phi_event_seconds", C.c_double), ("cum_steps", C.c_int64),
         ("launches_per_step", C.c_int64), ("kernel_mode", C.c_int32), ("tuned_n", C.c_int32),
         ("tuned_cached", C.c_int32), ("tuned_candidates", C.c_int32 * 8), ("tuned_seconds", C.c_double * 8),
-        ("reserved_i", C.c_int32 * 5), ("data_wait_seconds", C.c_double), ("reserved_d", C.c_double * 5),
+        ("n_buckets", C.c_int32), ("reserved_i", C.c_int32 * 4), ("data_wait_seconds", C.c_double),
+        ("reserved_d", C.c_double * 5),
     ]
 
 
