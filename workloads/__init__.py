@@ -271,6 +271,19 @@ def paper_context_box(n=16, G=16, n_polar=8, n_az=16, seed=BASE_SEED + 6):
     return p
 
 
+def order2(cfg):
+    """The same problem for the second-order (ten-node) element: Q at the four
+    vertices and, at the six edge midpoints (0,1) (0,2) (0,3) (1,2) (1,3) (2,3),
+    the mean of the edge's two vertex values (the same linear field per cell)."""
+    Q = np.asarray(cfg["Q"], dtype=np.float64)
+    mids = [0.5 * (Q[..., a] + Q[..., b]) for a, b in ((0, 1), (0, 2), (0, 3), (1, 2), (1, 3), (2, 3))]
+    out = dict(cfg)
+    out["Q"] = np.concatenate([Q, np.stack(mids, axis=-1)], axis=-1)
+    out["order"] = 2
+    out["name"] = cfg.get("name", "") + "_P2"
+    return out
+
+
 CONFIGS = {
     "small_box": small_box,
     "two_material": two_material_box,
