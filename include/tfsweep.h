@@ -112,7 +112,11 @@ typedef struct {
                               * arithmetic.  0 = automatic (when n_groups is not a multiple of 32),
                               * 1 = never, 2 = whenever n_groups is even */
     int32_t schedule;        /* tf_schedule: how the sweep orders its tasks (default TF_SCHED_AMT) */
-    int32_t reserved_i[3];
+    int32_t order;           /* finite-element order: 0 or 1 = linear (4 nodes per cell), 2 = quadratic
+                              * (10 nodes: the 4 vertices, then the midpoints of the local edges (0,1) (0,2)
+                              * (0,3) (1,2) (1,3) (2,3)); Q and every phi buffer are [n_cells][n_groups][nodes].
+                              * Order 2: vacuum boundaries and no S1 (both NULL), TF_SCHED_AMT, no batching */
+    int32_t reserved_i[2];
     double residual_floor;   /* stopping-test denominator floor, as a fraction of the group's max |phi|:
                               * 1 (the default; 0 also means 1) = per-group max-norm relative change,
                               * 1e-10 = pointwise relative change (unreachable in FP32 where DG

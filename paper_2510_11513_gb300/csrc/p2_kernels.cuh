@@ -1,0 +1,271 @@
+// Per-iteration kernels of the second-order (ten-node) element: source update,
+// phi reduction, boundary leakage, FP64 statistics and stopping test, psi
+// inspection.  Included by sweep.cu inside namespace tf, after the linear
+// element's kernels (it uses WeightPair, two_sum_acc, BalIn, record_balance).
+//
+// Layouts: caller phi and Q [C][G][10] (FP64); device Q, q [C][10][G] and psi
+// [Dc][C][10][G] in the sweep precision (node-major, so that lanes over groups
+// read and write whole lines).
+#pragma once
+
+// q[c][i][g] = (Q[c][i][g] + sum_h sigma_s[m][h][g] phi[c][h][i]) / 4 pi.  One CTA
+// stages the scalar flux of a few cells (in the sweep precision) in shared memory.
+template <class T>
+__global__ void __launch_bounds__(256) source_p2_kernel(const double *__restrict__ phi, const T *__restrict__ Qext,
+                                                        const T *__restrict__ sigma_s, const int32_t *__restrict__ mat,
+                                                        T *__restrict__ q, int64_t C, int G, int cells_per_cta)
+{
+    extern __shared__ unsigned char smem_raw[];
+    T *ph = reinterpret_cast<T *>(smem_raw);  // [cells_per_cta][G][10]
+    const T inv4pi = T(1.0 / (4.0 * 3.14159265358979323846));
+    for (int64_t c0 = (int64_t)blockIdx.x * cells_per_cta; c0 < C; c0 += (int64_t)gridDim.x * cells_per_cta) {
+        const int nc = (int)((C - c0) < (int64_t)cells_per_cta ? (C - c0) : (int64_t)cells_per_cta);
+        __syncthreads();
+        for (int e = threadIdx.x; e < nc * G * 10; e += blockDim.x) ph[e] = (T)phi[(size_t)c0 * G * 10 + e];
+        __syncthreads();
+        for (int u = threadIdx.x; u < nc * G; u += blockDim.x) {
+            const int lc = u / G, g = u - lc * G;
+            const int64_t c = c0 + lc;
+            const T *S = sigma_s + (size_t)__ldg(mat + c) * G * G + g;
+            const T *p = ph + (size_t)lc * G * 10;
+            T a[10];
+#pragma unroll
+            for (int i = 0; i < 10; ++i) a[i] = T(0);
+            for (int h = 0; h < G; ++h) {
+                const T s = __ldg(S + (size_t)h * G);
+#pragma unroll
+                for (int i = 0; i < 10; ++i) a[i] += s * p[10 * h + i];
+            }
+#pragma unroll
+            for (int i = 0; i < 10; ++i) {
+                const size_t at = ((size_t)c * 10 + i) * G + g;
+                q[at] = (__ldg(Qext + at) + a[i]) * inv4pi;
+            }
+        }
+    }
+}
+
+// phi[c][g][i] (+)= sum over the chunk's directions of w_a psi_a[c][i][g] (Eq. (2)).
+// Thread per (cell, group); FP32 psi with PAIR: exact float-pair products and sums
+// (as the linear element's phi_kernel), rounded once to FP64.
+template <class T, bool PAIR>
+__global__ void __launch_bounds__(256) phi_p2_kernel(const T *__restrict__ psi, const WeightPair *__restrict__ wts,
+                                                     int Dc, int64_t C, int G, double *__restrict__ phi, int accumulate)
+{
+    const size_t CG = (size_t)C * G;
+    for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < CG; idx += (size_t)gridDim.x * blockDim.x) {
+        const size_t c = idx / (size_t)G;
+        const int g = (int)(idx - c * (size_t)G);
+        const T *src = psi + c * 10 * (size_t)G + g;
+        double r[10];
+        if constexpr (PAIR) {
+            float hi[10], lo[10];
+#pragma unroll
+            for (int i = 0; i < 10; ++i) hi[i] = lo[i] = 0.f;
+            for (int a = 0; a < Dc; ++a) {
+                const T *s = src + (size_t)a * CG * 10;
+                const WeightPair w = wts[a];
+#pragma unroll
+                for (int i = 0; i < 10; ++i) {
+                    const float x = __ldcs(s + (size_t)i * G);
+                    const float pp = w.hi * x;
+                    const float e = fmaf(w.hi, x, -pp) + w.lo * x;
+                    two_sum_acc(hi[i], lo[i], pp, e);
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < 10; ++i) r[i] = (double)hi[i] + (double)lo[i];
+        } else {
+#pragma unroll
+            for (int i = 0; i < 10; ++i) r[i] = 0.0;
+            for (int a = 0; a < Dc; ++a) {
+                const T *s = src + (size_t)a * CG * 10;
+                const double w = wts[a].d;
+#pragma unroll
+                for (int i = 0; i < 10; ++i) r[i] = fma(w, (double)__ldcs(s + (size_t)i * G), r[i]);
+            }
+        }
+        double *out = phi + idx * 10;
+#pragma unroll
+        for (int i = 0; i < 10; ++i) out[i] = accumulate ? out[i] + r[i] : r[i];
+    }
+}
+
+// Boundary leakage (vacuum boundaries): per (boundary cell, group) over the chunk's
+// directions, w_a s_f <psi_a>_f on every boundary outflow face (s_f = Omega_a . N_f
+// not below the sweep graph's inflow threshold -1e-12 |N_f|).  The face average of
+// the quadratic field is the mean of its three edge nodes (int_f phi_vertex = 0,
+// int_f phi_edge = A_f / 3).  Accumulated as the linear element's leak_kernel does.
+template <class T>
+__global__ void __launch_bounds__(256) leak_p2_kernel(const T *__restrict__ psi, const WeightPair *__restrict__ wts,
+                                                      const V4<T> *__restrict__ omega, int Dc, int64_t C, int G,
+                                                      const uint32_t *__restrict__ bcells, int64_t nb,
+                                                      const P2Geo<T> *__restrict__ geo, double *__restrict__ leak)
+{
+    for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < nb * G; u += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t b = u / G;
+        const int g = (int)(u - b * G);
+        const uint32_t c = bcells[b];
+        const P2Geo<T> &cg = geo[c];
+        uint32_t faces = 0;
+        T nx[4], ny[4], nz[4], thr[4];
+#pragma unroll
+        for (int f = 0; f < 4; ++f) {
+            faces |= (cg.nbr[f] < 0 ? 1u : 0u) << f;
+            nx[f] = cg.nrm[3 * f];
+            ny[f] = cg.nrm[3 * f + 1];
+            nz[f] = cg.nrm[3 * f + 2];
+            thr[f] = T(-1e-12) * sqrt(nx[f] * nx[f] + ny[f] * ny[f] + nz[f] * nz[f]);
+        }
+        double acc = 0.0;
+        float hi = 0.f, lo = 0.f;
+        for (int a = 0; a < Dc; ++a) {
+            const T *s = psi + (((size_t)a * C + c) * 10) * G + g;
+            const V4<T> om = omega[a];
+            T t = T(0);
+#pragma unroll
+            for (int f = 0; f < 4; ++f) {
+                if (!((faces >> f) & 1u)) continue;
+                const T sf = om.x * nx[f] + om.y * ny[f] + om.z * nz[f];
+                if (sf < thr[f]) continue;  // inflow face of a vacuum boundary
+                const T avg = (s[(size_t)p2_face_node(f, 3) * G] + s[(size_t)p2_face_node(f, 4) * G] +
+                               s[(size_t)p2_face_node(f, 5) * G]) * T(1.0 / 3.0);
+                t += sf * avg;
+            }
+            if constexpr (sizeof(T) == 8) {
+                acc += wts[a].d * (double)t;
+            } else {
+                const WeightPair w = wts[a];
+                const float pp = w.hi * t;
+                const float e = fmaf(w.hi, t, -pp) + w.lo * t;
+                two_sum_acc(hi, lo, pp, e);
+            }
+        }
+        if constexpr (sizeof(T) == 4) acc = (double)hi + (double)lo;
+        atomicAdd(leak + g, acc);
+    }
+}
+
+// Per-cell sums of one (cell, group) of the quadratic field: max |phi_i|, the
+// plain nodal sum and sum_i p_i phi_i (int over the cell / V).
+__device__ __forceinline__ void p2_cell_sums(const double *v, double &mx, double &plain, double &wsum)
+{
+    mx = 0.0;
+    plain = 0.0;
+    wsum = 0.0;
+#pragma unroll
+    for (int i = 0; i < 10; ++i) {
+        mx = fmax(mx, fabs(v[i]));
+        plain += v[i];
+        wsum += p2_p(i) * v[i];
+    }
+}
+
+template <class T> __device__ __forceinline__ double p2_q_weighted(const T *q, int64_t c, int g, int G)
+{
+    double s = 0.0;
+#pragma unroll
+    for (int i = 0; i < 10; ++i) s += p2_p(i) * (double)q[((size_t)c * 10 + i) * G + g];
+    return s;
+}
+
+// The statistics of stats_kernel / stats_res_kernel for the quadratic field (same
+// partial layout, so the same finish kernels apply): integral sum_c V_c sum_i p_i phi_i
+// (Eq. (3)), plain nodal sum, absorption, source, max |phi| and (RES) max |dphi|.
+template <class T, bool RES>
+__global__ void __launch_bounds__(256) stats_p2_kernel(const double *__restrict__ phi_new,
+                                                       const double *__restrict__ phi_old,
+                                                       const double *__restrict__ vol, int64_t C, int G,
+                                                       double *__restrict__ part, BalIn bi)
+{
+    constexpr int NP = RES ? 6 : 5;
+    __shared__ double sh[NP][8][32];
+    for (int g0 = 0; g0 < G; g0 += 32) {
+        const int g = g0 + threadIdx.x;
+        double mx = 0.0, iv = 0.0, pl = 0.0, dm = 0.0, ab = 0.0, sr = 0.0;
+        if (g < G) {
+            for (int64_t c = (int64_t)blockIdx.x * 8 + threadIdx.y; c < C; c += (int64_t)gridDim.x * 8) {
+                const double *pn = phi_new + ((size_t)c * G + g) * 10;
+                double m, plain, ws;
+                p2_cell_sums(pn, m, plain, ws);
+                mx = fmax(mx, m);
+                if constexpr (RES) {
+                    const double *po = phi_old + ((size_t)c * G + g) * 10;
+#pragma unroll
+                    for (int i = 0; i < 10; ++i) dm = fmax(dm, fabs(pn[i] - po[i]));
+                }
+                iv += vol[c] * ws;
+                pl += plain;
+                ab += bi.sig[(size_t)bi.mat[c] * G + g] * vol[c] * ws;
+                sr += vol[c] * kFourPi * p2_q_weighted(reinterpret_cast<const T *>(bi.q), c, g, G);
+            }
+        }
+        const double vals[6] = {mx, iv, pl, RES ? dm : ab, RES ? ab : sr, sr};
+#pragma unroll
+        for (int k = 0; k < NP; ++k) sh[k][threadIdx.y][threadIdx.x] = vals[k];
+        __syncthreads();
+        if (threadIdx.y == 0 && g < G) {
+            double o[NP];
+#pragma unroll
+            for (int k = 0; k < NP; ++k) o[k] = sh[k][0][threadIdx.x];
+            for (int y = 1; y < 8; ++y) {
+                o[0] = fmax(o[0], sh[0][y][threadIdx.x]);
+                o[1] += sh[1][y][threadIdx.x];
+                o[2] += sh[2][y][threadIdx.x];
+                if constexpr (RES) {
+                    o[3] = fmax(o[3], sh[3][y][threadIdx.x]);
+                    o[4] += sh[4][y][threadIdx.x];
+                    o[5] += sh[5][y][threadIdx.x];
+                } else {
+                    o[3] += sh[3][y][threadIdx.x];
+                    o[4] += sh[4][y][threadIdx.x];
+                }
+            }
+            double *dst = part + ((size_t)blockIdx.x * G + g) * NP;
+#pragma unroll
+            for (int k = 0; k < NP; ++k) dst[k] = o[k];
+        }
+        __syncthreads();
+    }
+}
+
+// Pointwise stopping test (residual_floor < 1) for the quadratic field, as residual_kernel.
+__global__ void __launch_bounds__(256) residual_p2_kernel(const double *__restrict__ phi_new,
+                                                          const double *__restrict__ phi_old,
+                                                          const double *__restrict__ gstats, int64_t C, int G,
+                                                          double floor_frac, Ctrl *ctrl)
+{
+    float rmax = 0.f;
+    for (int g0 = 0; g0 < G; g0 += 32) {
+        const int g = g0 + threadIdx.x;
+        if (g >= G) continue;
+        const double gmax = gstats[4 * g], inv = gstats[4 * g + 3];
+        const double floor_ = floor_frac * gmax;
+        for (int64_t c = (int64_t)blockIdx.x * 8 + threadIdx.y; c < C; c += (int64_t)gridDim.x * 8) {
+            const double *pn = phi_new + ((size_t)c * G + g) * 10, *po = phi_old + ((size_t)c * G + g) * 10;
+#pragma unroll
+            for (int i = 0; i < 10; ++i) {
+                const double diff = fabs(pn[i] - po[i]);
+                if (diff == 0.0) continue;
+                const double den = fmax(fabs(pn[i]), floor_);
+                rmax = fmaxf(rmax, den > 0.0 ? __fdiv_rn((float)(diff * inv), (float)(den * inv)) : INFINITY);
+            }
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) rmax = fmaxf(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
+    if ((threadIdx.x & 31) == 0 && rmax > 0.f)
+        atomicMax(&ctrl->residual_bits, (unsigned long long)__double_as_longlong((double)rmax));
+}
+
+// psi of one direction, [C][10][G] -> the caller's [C][G][10] (inspection only).
+template <class T>
+__global__ void psi_p2_out_kernel(const T *__restrict__ src, T *__restrict__ dst, int64_t C, int G)
+{
+    const size_t n = (size_t)C * G * 10;
+    for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += (size_t)gridDim.x * blockDim.x) {
+        const size_t c = idx / ((size_t)G * 10);
+        const size_t r = idx - c * (size_t)G * 10;
+        const int g = (int)(r / 10), i = (int)(r - (size_t)g * 10);
+        dst[idx] = src[(c * 10 + i) * G + g];
+    }
+}

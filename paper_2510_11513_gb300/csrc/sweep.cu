@@ -648,6 +648,8 @@ __global__ void __launch_bounds__(256) residual_kernel(const double *__restrict_
         atomicMax(&ctrl->residual_bits, (unsigned long long)__double_as_longlong((double)rmax));
 }
 
+#include "p2_kernels.cuh"
+
 // ============================================================== host side
 struct DeviceState {
     int device = 0, sm_count = 0;
@@ -655,6 +657,10 @@ struct DeviceState {
     int64_t C = 0, nv = 0;
     int32_t G = 0, D = 0, M = 0;
     bool fp64 = false;
+    int order = 1;           // element order: 1 linear (4 nodes), 2 quadratic (10 nodes)
+    int nb = 4;              // nodes per cell
+    void *geo2 = nullptr;    // second order: P2Geo<T> [C]
+    double *vol = nullptr;   // second order: cell volumes (FP64)
     bool two_stage = false;  // staged path with two stages (mode 4)
     int pair_stages = 3;     // paired path: buffers in the ring of staged copies
     size_t tsize = 4;  // sizeof(T)
@@ -903,6 +909,67 @@ template <class T> tf_status create_typed(Problem &p, DeviceState &d, const int3
     return TF_OK;
 }
 
+// Second-order element: cell records (grad lambda, normals, volume, material,
+// neighbours, and for each face node the neighbour's local node of the same
+// global vertex or edge), cross sections, Q reordered node-major [C][10][G].
+template <class T> tf_status create_typed_p2(Problem &p, DeviceState &d, const int32_t *cell_material,
+                                             const double *sigma_t, const double *sigma_s, const double *Q)
+{
+    const Mesh &m = *p.mesh;
+    tf_status s;
+    {
+        auto key = [&](int64_t c, int i) -> std::pair<int32_t, int32_t> {
+            const int32_t *t = &m.tets[4 * c];
+            if (i < 4) return {t[i], -1};
+            const int32_t a = t[p2_edge_end(i - 4, 0)], b = t[p2_edge_end(i - 4, 1)];
+            return {std::min(a, b), std::max(a, b)};
+        };
+        std::vector<P2Geo<T>> geo(m.nc);
+        for (int64_t c = 0; c < m.nc; ++c) {
+            P2Geo<T> &g = geo[c];
+            std::memset(&g, 0, sizeof(g));
+            for (int k = 0; k < 12; ++k) {
+                g.gl[k] = (T)m.grad[12 * c + k];
+                g.nrm[k] = (T)m.normal[12 * c + k];
+            }
+            g.vol = (T)m.vol[c];
+            g.mat = cell_material[c];
+            for (int f = 0; f < 4; ++f) {
+                const int32_t n = m.nbr[4 * c + f];
+                g.nbr[f] = n;
+                if (n < 0) continue;
+                for (int b = 0; b < 6; ++b) {
+                    const auto k = key(c, p2_face_node(f, b));
+                    int mm = -1;
+                    for (int j = 0; j < 10; ++j)
+                        if (key(n, j) == k) mm = j;
+                    if (mm < 0) return fail(TF_ERR_MESH, "second-order face node without a match in the neighbour");
+                    const int bit = 24 * f + 4 * b;
+                    g.fmap[bit >> 5] |= (uint32_t)mm << (bit & 31);
+                }
+            }
+        }
+        P2Geo<T> *gp = nullptr;
+        if ((s = upload(d, &gp, geo.data(), geo.size() * sizeof(P2Geo<T>))) != TF_OK) return s;
+        d.geo2 = gp;
+    }
+    if ((s = upload_vec3<T>(d, &d.omega, p.quad->omega.data(), d.D, p.quad->w.data())) != TF_OK) return s;
+    if ((s = upload(d, &d.mat, cell_material, sizeof(int32_t) * (size_t)d.C)) != TF_OK) return s;
+    if ((s = upload(d, &d.sig_d, sigma_t, sizeof(double) * (size_t)d.M * d.G)) != TF_OK) return s;
+    if ((s = upload_typed<T>(d, &d.sigma_t, sigma_t, (size_t)d.M * d.G)) != TF_OK) return s;
+    if ((s = upload_typed<T>(d, &d.sigma_s, sigma_s, (size_t)d.M * d.G * d.G)) != TF_OK) return s;
+    if ((s = upload(d, &d.vol, m.vol.data(), sizeof(double) * (size_t)d.C)) != TF_OK) return s;
+    {
+        std::vector<double> Qs((size_t)d.C * d.G * 10);
+        for (int64_t c = 0; c < d.C; ++c)
+            for (int gq = 0; gq < d.G; ++gq)
+                for (int i = 0; i < 10; ++i)
+                    Qs[((size_t)c * 10 + i) * d.G + gq] = Q[((size_t)c * d.G + gq) * 10 + i];
+        if ((s = upload_typed<T>(d, &d.Q, Qs.data(), Qs.size())) != TF_OK) return s;
+    }
+    return TF_OK;
+}
+
 }  // namespace
 
 tf_status device_create(Problem &p, const int32_t *cell_material, const double *sigma_t, const double *sigma_s,
@@ -930,9 +997,11 @@ tf_status device_create(Problem &p, const int32_t *cell_material, const double *
     d.D = p.quad->D;
     d.M = p.M;
     d.fp64 = p.opt.precision == TF_FP64;
+    d.order = p.opt.order == 2 ? 2 : 1;
+    d.nb = d.order == 2 ? 10 : 4;
     // pairing 0 = automatic: packed pairs unless G is a multiple of 32 (there the
     // shared-memory staged path is faster); 2 = packed pairs whenever G is even
-    d.paired = !d.fp64 && d.G % 2 == 0 && (p.opt.pairing == 2 || (p.opt.pairing == 0 && d.G % 32 != 0)) &&
+    d.paired = d.order == 1 && !d.fp64 && d.G % 2 == 0 && (p.opt.pairing == 2 || (p.opt.pairing == 0 && d.G % 32 != 0)) &&
                g.cells_per_task <= 32 &&
                PairLayout(d.G, g.cells_per_task).bytes() <= 227u * 1024u;
     d.tsize = d.fp64 ? 8 : 4;
@@ -952,10 +1021,11 @@ tf_status device_create(Problem &p, const int32_t *cell_material, const double *
                 remap[16 * c + mk] = (uint8_t)r;
             }
         }
+        // (the second-order element keeps the caller's face order)
         std::vector<uint32_t> cl(g.cell_list.size());
         for (size_t i = 0; i < cl.size(); ++i) {
             const uint32_t e = g.cell_list[i], c = e >> 4;
-            cl[i] = (c << 4) | remap[16 * (size_t)c + (e & 15u)];
+            cl[i] = d.order == 2 ? e : (c << 4) | remap[16 * (size_t)c + (e & 15u)];
         }
         if ((s = upload(d, &d.cells, cl.data(), cl.size() * 4)) != TF_OK) return s;
     }
@@ -978,12 +1048,16 @@ tf_status device_create(Problem &p, const int32_t *cell_material, const double *
         for (int64_t c = 0; c < m.nc; ++c) v4[c] = 0.25 * m.vol[c];
         if ((s = upload(d, &d.vol4, v4.data(), v4.size() * 8)) != TF_OK) return s;
     }
-    s = d.fp64 ? create_typed<double>(p, d, cell_material, sigma_t, sigma_s, Q, S1, psi_in)
-               : create_typed<float>(p, d, cell_material, sigma_t, sigma_s, Q, S1, psi_in);
+    if (d.order == 2)
+        s = d.fp64 ? create_typed_p2<double>(p, d, cell_material, sigma_t, sigma_s, Q)
+                   : create_typed_p2<float>(p, d, cell_material, sigma_t, sigma_s, Q);
+    else
+        s = d.fp64 ? create_typed<double>(p, d, cell_material, sigma_t, sigma_s, Q, S1, psi_in)
+                   : create_typed<float>(p, d, cell_material, sigma_t, sigma_s, Q, S1, psi_in);
     if (s != TF_OK) return s;
-    if ((s = dmalloc(d, &d.q, (size_t)d.C * d.G * 4 * d.tsize)) != TF_OK) return s;
-    if ((s = dmalloc(d, &d.phi_buf[0], (size_t)d.C * d.G * 4 * 8)) != TF_OK) return s;
-    if ((s = dmalloc(d, &d.phi_buf[1], (size_t)d.C * d.G * 4 * 8)) != TF_OK) return s;
+    if ((s = dmalloc(d, &d.q, (size_t)d.C * d.G * d.nb * d.tsize)) != TF_OK) return s;
+    if ((s = dmalloc(d, &d.phi_buf[0], (size_t)d.C * d.G * d.nb * 8)) != TF_OK) return s;
+    if ((s = dmalloc(d, &d.phi_buf[1], (size_t)d.C * d.G * d.nb * 8)) != TF_OK) return s;
     // per-direction weights
     {
         std::vector<WeightPair> w(d.D);
@@ -1013,7 +1087,7 @@ tf_status device_create(Problem &p, const int32_t *cell_material, const double *
     }
     if ((s = dmalloc(d, &d.gstats, sizeof(double) * 4 * d.G)) != TF_OK) return s;
     // direction chunks: as many directions per launch as the psi budget allows
-    const size_t per_dir = (size_t)d.C * d.G * 4 * d.tsize;
+    const size_t per_dir = (size_t)d.C * d.G * d.nb * d.tsize;
     size_t free_b = 0, total_b = 0;
     TF_CUDA(cudaMemGetInfo(&free_b, &total_b));
     double budget = p.opt.psi_budget_gb > 0 ? p.opt.psi_budget_gb * 1e9 : 0.8 * (double)free_b;
@@ -1128,11 +1202,15 @@ tf_status device_create(Problem &p, const int32_t *cell_material, const double *
         const int ns = p.opt.staging == 3 ? 3 : p.opt.staging == 2 ? 2 : (d.fp64 ? 3 : 2);
         const size_t wb = d.fp64 ? staged_warp_bytes<double>(d.G, ns) : staged_warp_bytes<float>(d.G, ns);
         const size_t wb128 = (wb + 48 + 127) / 128 * 128;  // + the six mbarriers at the end
-        d.staged = p.opt.staging != 1 && d.G % 32 == 0 && g.cells_per_task <= 64 && wb128 * d.wpc <= 227 * 1024;
+        d.staged = d.order == 1 && p.opt.staging != 1 && d.G % 32 == 0 && g.cells_per_task <= 64 &&
+                   wb128 * d.wpc <= 227 * 1024;
         d.warp_smem = d.staged ? (uint32_t)wb128 : 0u;
         d.two_stage = d.staged && ns == 2 && !d.fp64;
     }
-    d.mode = d.paired ? 3 : d.staged ? (d.two_stage ? 4 : 2) : (d.G % 32 == 0 && g.cells_per_task <= 64 ? 1 : 0);
+    d.mode = d.order == 2 ? 5
+             : d.paired  ? 3
+             : d.staged  ? (d.two_stage ? 4 : 2)
+                         : (d.G % 32 == 0 && g.cells_per_task <= 64 ? 1 : 0);
     if (d.paired) {
         d.staged = false;
         // three buffers unless two let more CTAs be resident per SM
@@ -1159,7 +1237,8 @@ tf_status device_create(Problem &p, const int32_t *cell_material, const double *
         d.ppl = (int)L.ppl;
     }
     const int dyn = (int)(d.warp_smem * d.wpc);
-    const void *kfn = d.fp64 ? (d.mode == 2 ? (const void *)sweep_kernel<double, 2>
+    const void *kfn = d.mode == 5 ? (d.fp64 ? (const void *)sweep_kernel<double, 5> : (const void *)sweep_kernel<float, 5>)
+                      : d.fp64 ? (d.mode == 2 ? (const void *)sweep_kernel<double, 2>
                                             : d.mode == 1 ? (const void *)sweep_kernel<double, 1> : (const void *)sweep_kernel<double, 0>)
                              : (d.mode == 3   ? (const void *)sweep_kernel<float, 3>
                                 : d.mode == 4 ? (const void *)sweep_kernel<float, 4>
@@ -1258,6 +1337,15 @@ void *mapped_host_pointer(const void *ptr)
 template <class T> void launch_source(Problem &p, const double *phi_in, cudaStream_t st)
 {
     DeviceState &d = *p.dev;
+    if (d.order == 2) {
+        const int cpc2 = std::max(1, 256 / d.G);
+        const size_t smem2 = (size_t)cpc2 * d.G * 10 * sizeof(T);
+        const int blocks2 = (int)std::min<int64_t>((d.C + cpc2 - 1) / cpc2, (int64_t)d.sm_count * 16);
+        source_p2_kernel<T><<<blocks2, 256, smem2, st>>>(phi_in, (const T *)d.Q, (const T *)d.sigma_s, d.mat,
+                                                         (T *)d.q, d.C, d.G, cpc2);
+        cudaMemsetAsync(d.leak, 0, sizeof(double) * d.G, st);
+        return;
+    }
     const int cpc = std::max(1, 256 / d.G);
     const size_t smem = (size_t)cpc * d.G * 4 * sizeof(T);
     const int blocks = (int)std::min<int64_t>((d.C + cpc - 1) / cpc, (int64_t)d.sm_count * 16);
@@ -1278,6 +1366,25 @@ void launch_stats(Problem &p, const double *cur, const double *nxt, cudaStream_t
     bi.qmode = d.paired ? 2 : (d.fp64 ? 1 : 0);
     bi.leak = d.leak;
     cudaMemsetAsync(&d.ctrl->residual_bits, 0, 16, st);  // residual_bits, balance_bits
+    if (d.order == 2) {
+        const bool res = p.opt.residual_floor >= 1.0;
+        if (d.fp64) {
+            if (res) stats_p2_kernel<double, true><<<d.stats_blocks, dim3(32, 8), 0, st>>>(nxt, cur, d.vol, d.C, d.G, d.part, bi);
+            else stats_p2_kernel<double, false><<<d.stats_blocks, dim3(32, 8), 0, st>>>(nxt, cur, d.vol, d.C, d.G, d.part, bi);
+        } else {
+            if (res) stats_p2_kernel<float, true><<<d.stats_blocks, dim3(32, 8), 0, st>>>(nxt, cur, d.vol, d.C, d.G, d.part, bi);
+            else stats_p2_kernel<float, false><<<d.stats_blocks, dim3(32, 8), 0, st>>>(nxt, cur, d.vol, d.C, d.G, d.part, bi);
+        }
+        if (res) {
+            finish_stats_res_kernel<<<(d.G + 127) / 128, 128, 0, st>>>(d.part, d.stats_blocks, d.G, d.gstats, d.leak,
+                                                                       d.ctrl);
+        } else {
+            finish_stats_kernel<<<(d.G + 127) / 128, 128, 0, st>>>(d.part, d.stats_blocks, d.G, d.gstats, d.leak, d.ctrl);
+            residual_p2_kernel<<<d.stats_blocks, dim3(32, 8), 0, st>>>(nxt, cur, d.gstats, d.C, d.G,
+                                                                       p.opt.residual_floor, d.ctrl);
+        }
+        return;
+    }
     if (p.opt.residual_floor >= 1.0) {
         stats_res_kernel<<<d.stats_blocks, dim3(32, 8), 0, st>>>(nxt, cur, d.vol4, d.C, d.G, d.part, bi);
         finish_stats_res_kernel<<<(d.G + 127) / 128, 128, 0, st>>>(d.part, d.stats_blocks, d.G, d.gstats, d.leak,
@@ -1333,6 +1440,7 @@ template <class T> SweepArgs<T> make_args(Problem &p, int k)
     A.ppl = d.ppl;
     A.stages = d.pair_stages;
     A.mode = d.mode;
+    A.geo2 = d.geo2;
     return A;
 }
 
@@ -1343,6 +1451,18 @@ template <class T> void launch_phi(Problem &p, int k, double *phi_out, cudaStrea
     const size_t CG = (size_t)d.C * d.G;
     const int a0 = k * d.Dc, a1 = std::min(d.D, a0 + d.Dc);
     const int pb = (int)std::min<size_t>((CG + 255) / 256, (size_t)d.sm_count * 32);
+    if (d.order == 2) {
+        if (!d.fp64 && p.opt.phi_accumulate == TF_PHI_PAIR)
+            phi_p2_kernel<T, true><<<pb, 256, 0, st>>>((const T *)d.psi, d.wts + a0, a1 - a0, d.C, d.G, phi_out, k > 0);
+        else
+            phi_p2_kernel<T, false><<<pb, 256, 0, st>>>((const T *)d.psi, d.wts + a0, a1 - a0, d.C, d.G, phi_out, k > 0);
+        if (d.n_bcells > 0) {
+            const int lb = (int)std::min<int64_t>((d.n_bcells * d.G + 255) / 256, (int64_t)d.sm_count * 16);
+            leak_p2_kernel<T><<<lb, 256, 0, st>>>((const T *)d.psi, d.wts + a0, (const V4<T> *)d.omega + a0, a1 - a0,
+                                                  d.C, d.G, d.bcells, d.n_bcells, (const P2Geo<T> *)d.geo2, d.leak);
+        }
+        return;
+    }
     if (d.paired) {
         const size_t CP = CG / 2;
         const int pb2 = (int)std::min<size_t>((CP + 255) / 256, (size_t)d.sm_count * 32);
@@ -1431,7 +1551,9 @@ template <class T> tf_status launch_step(Problem &p, const double *phi_in, doubl
             if (d.mode == 4) sweep_kernel<T, 4><<<d.grid, 32 * d.wpc, dyn, st>>>(A);
         }
         if (d.mode == 3 || d.mode == 4) {
-        } else if (d.mode == 2)
+        } else if (d.mode == 5)
+            sweep_kernel<T, 5><<<d.grid, 32 * d.wpc, 0, st>>>(A);
+        else if (d.mode == 2)
             sweep_kernel<T, 2><<<d.grid, 32 * d.wpc, dyn, st>>>(A);
         else if (d.mode == 1)
             sweep_kernel<T, 1><<<d.grid, 32 * d.wpc, 0, st>>>(A);
@@ -1515,7 +1637,7 @@ tf_status device_sweep(Problem &p, const double *phi_in, double *phi_out, void *
     DeviceState &d = *p.dev;
     TF_CUDA(cudaSetDevice(d.device));
     cudaStream_t st = (cudaStream_t)stream;
-    const size_t bytes = (size_t)d.C * d.G * 4 * 8;
+    const size_t bytes = (size_t)d.C * d.G * d.nb * 8;
     const double *in = phi_in;
     double *out = phi_out;
     // Pinned, mapped host buffers are read by the source kernel and written by the phi
@@ -1602,7 +1724,7 @@ tf_status device_iterate(Problem &p, double tol, int32_t max_iters, double *phi,
     cudaStream_t user = (cudaStream_t)stream;
     cudaStream_t st = d.istream;
     const size_t CG = (size_t)d.C * d.G;
-    const size_t bytes = CG * 4 * 8;
+    const size_t bytes = CG * d.nb * 8;
     const bool host = !is_device_pointer(phi);
     TF_CUDA(cudaEventRecord(d.ev_user, user));
     TF_CUDA(cudaStreamWaitEvent(st, d.ev_user, 0));
@@ -1714,8 +1836,8 @@ tf_status batch_setup(BatchRun &B, const tf_handle *problems, int32_t n)
         if (p->dev->device != B.device || p->dev->fp64 != B.fp64)
             return fail(TF_ERR_ARG, "batched problems must share one device and one precision");
         if (p->opt.inject_stall) return fail(TF_ERR_ARG, "inject_stall is not supported in batched launches");
-        if (p->dev->schedule != TF_SCHED_AMT)
-            return fail(TF_ERR_ARG, "batched launches run only problems with the TF_SCHED_AMT schedule");
+        if (p->dev->schedule != TF_SCHED_AMT || p->dev->order != 1)
+            return fail(TF_ERR_ARG, "batched launches run only linear-element problems with the TF_SCHED_AMT schedule");
         B.max_chunks = std::max(B.max_chunks, p->dev->n_chunks);
         B.warp_smem = std::max(B.warp_smem, p->dev->warp_smem);
     }
@@ -1890,7 +2012,7 @@ tf_status batch_check(BatchRun &B, const std::vector<char> &active)
 
 tf_status copy_in(Problem &p, const double *src, double *dst, cudaStream_t st)
 {
-    const size_t bytes = (size_t)p.dev->C * p.dev->G * 4 * 8;
+    const size_t bytes = (size_t)p.dev->C * p.dev->G * p.dev->nb * 8;
     if (!src) {
         TF_CUDA(cudaMemsetAsync(dst, 0, bytes, st));
         return TF_OK;
@@ -1901,7 +2023,7 @@ tf_status copy_in(Problem &p, const double *src, double *dst, cudaStream_t st)
 
 tf_status copy_out(Problem &p, const double *src, double *dst, cudaStream_t st)
 {
-    const size_t bytes = (size_t)p.dev->C * p.dev->G * 4 * 8;
+    const size_t bytes = (size_t)p.dev->C * p.dev->G * p.dev->nb * 8;
     TF_CUDA(cudaMemcpyAsync(dst, src, bytes, is_device_pointer(dst) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
     return TF_OK;
 }
@@ -2017,7 +2139,14 @@ tf_status device_psi(Problem &p, int32_t dir, void *out, void *stream)
     const size_t CG = (size_t)d.C * d.G;
     cudaStream_t st = (cudaStream_t)stream;
     const int blocks = (int)std::min<size_t>((CG + 255) / 256, (size_t)d.sm_count * 16);
-    if (d.paired)
+    if (d.order == 2) {
+        if (d.fp64)
+            psi_p2_out_kernel<double><<<blocks, 256, 0, st>>>((const double *)d.psi + (size_t)(dir - a0) * CG * 10,
+                                                              (double *)out, d.C, d.G);
+        else
+            psi_p2_out_kernel<float><<<blocks, 256, 0, st>>>((const float *)d.psi + (size_t)(dir - a0) * CG * 10,
+                                                             (float *)out, d.C, d.G);
+    } else if (d.paired)
         psi_unpair_kernel<<<blocks, 256, 0, st>>>((const float *)d.psi + (size_t)(dir - a0) * CG * 4, (float4 *)out,
                                                   CG / 2, d.G, (const CellGeo<float> *)d.geo);
     else if (d.fp64)

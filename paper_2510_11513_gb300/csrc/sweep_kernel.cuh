@@ -178,7 +178,10 @@ template <class T> struct SweepArgs {
     int32_t lpc_shift, ppl;      // paired path: log2 lanes per cell, group pairs per lane
     int32_t stages;              // paired path: buffers in the ring of staged copies (2 or 3)
     int32_t mode;                // kernel variant of this problem (batched launches dispatch on it)
+    const void *geo2;            // second-order element: P2Geo<T> [C] cell records (mode 5)
 };
+
+#include "p2_solve.cuh"
 
 // Solve one 4x4 system by Gaussian elimination without pivoting: the
 // symmetric part of the upwind-DG matrix, (1/2) sum_f |Omega.N_f| M_f +
@@ -1132,9 +1135,11 @@ __device__ __forceinline__ bool run_task_staged_any(const SweepArgs<T> &A, uint4
 // MODE: 0 = any group count (registers), 1 = G a multiple of 32 (registers),
 // 2 = G a multiple of 32 with the rows staged in shared memory (three stages),
 // 3 = FP32 and G even: packed group pairs (pair-interleaved source and psi rows),
-// 4 = as 2 with two stages and six resident CTAs per SM (FP32).
+// 4 = as 2 with two stages and six resident CTAs per SM (FP32),
+// 5 = the second-order (ten-node) element, lanes over (cell, group) units.
 template <class T, int MODE>
-__global__ void __launch_bounds__(128, MODE == 4 ? 6 : (sizeof(T) == 4 ? 4 : 3)) sweep_kernel(const SweepArgs<T> A)
+__global__ void __launch_bounds__(128, MODE == 5 ? 2 : MODE == 4 ? 6 : (sizeof(T) == 4 ? 4 : 3))
+    sweep_kernel(const SweepArgs<T> A)
 {
     const int lane = threadIdx.x & 31;
     const unsigned FULL = 0xffffffffu;
@@ -1232,6 +1237,8 @@ __global__ void __launch_bounds__(128, MODE == 4 ? 6 : (sizeof(T) == 4 ? 4 : 3))
             if (!run_task_staged_any<T, 2>(A, ti, lane, om.x, om.y, om.z, psi_dir, wsm, bars, ph, ws + 6)) break;
         } else if constexpr (MODE == 1) {
             run_task_wide(A, ti, lane, om.x, om.y, om.z, psi_dir);
+        } else if constexpr (MODE == 5) {
+            run_task_p2(A, ti, lane, om.x, om.y, om.z, psi_dir);
         } else {
             run_task_generic(A, ti, lane, om.x, om.y, om.z, psi_dir);
         }

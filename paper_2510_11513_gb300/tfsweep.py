@@ -6,8 +6,9 @@ functions named tf_* mirror the C calls one to one; the small classes below
 
 Arrays: host inputs are numpy arrays (converted to the C types and made
 contiguous).  Scalar-flux buffers for tf_sweep / tf_source_iterate are
-torch tensors (device or host, float64, shape [n_cells, n_groups, 4]) or
-numpy arrays (host); their data pointers are passed through unchanged.
+torch tensors (device or host, float64, shape [n_cells, n_groups, nodes], nodes = 4
+for the linear element and 10 for the quadratic one) or numpy arrays (host); their
+data pointers are passed through unchanged.
 """
 from __future__ import annotations
 
@@ -41,7 +42,8 @@ class tf_options(C.Structure):
         ("warps_per_cta", C.c_int32), ("ctas_per_sm", C.c_int32), ("wait_limit_s", C.c_double),
         ("phi_accumulate", C.c_int32), ("inject_stall", C.c_int32), ("psi_budget_gb", C.c_double),
         ("task_order", C.c_int32), ("staging", C.c_int32), ("octant_window", C.c_int32),
-        ("pairing", C.c_int32), ("schedule", C.c_int32), ("reserved_i", C.c_int32 * 3),
+        ("pairing", C.c_int32), ("schedule", C.c_int32), ("order", C.c_int32),
+        ("reserved_i", C.c_int32 * 2),
         ("residual_floor", C.c_double),
         ("reserved_d", C.c_double * 3),
     ]
@@ -471,6 +473,9 @@ class Problem(_Handle):
                  S1=None, psi_inflow=None, **opts):
         self.mesh, self.quad = mesh, quad
         self.opt = options(**opts)
+        self.n_nodes = 10 if self.opt.order == 2 else 4
+        if int(n_groups) > 0 and np.size(Q) != mesh.n_cells * int(n_groups) * self.n_nodes:
+            raise ValueError(f"Q must be [n_cells][n_groups][{self.n_nodes}]")
         self.h = tf_problem_create(mesh.h, quad.h, n_groups, n_materials, cell_material, sigma_t, sigma_s, Q, S1,
                                    psi_inflow, self.opt)
         self.n_groups = int(n_groups)

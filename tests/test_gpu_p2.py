@@ -1,0 +1,118 @@
+"""Parity of the second-order (ten-node) CUDA sweep with the second-order oracle.
+
+Tolerances as for the linear element (relative to the oracle's max-norm):
+FP64 1e-11, FP32 2e-5.  Sizes span several tasks, ragged group counts and cell
+blocks, and several direction chunks.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import p2 as o2
+
+torch = pytest.importorskip("torch")
+import paper_2510_11513_gb300 as tf  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+TOL = {tf.TF_FP64: 1e-11, tf.TF_FP32: 2e-5}
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+
+
+def _rel(a, b):
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+def _box(n, G, seed=5, two_material=False):
+    if two_material:
+        return W.order2(W.two_material_box(n=n, G=G, n_polar=2, n_az=8, seed=seed))
+    return W.order2(W.small_box(n=n, G=G, n_polar=2, n_az=8, seed=seed))
+
+
+@pytest.mark.parametrize("precision", [tf.TF_FP64, tf.TF_FP32])
+@pytest.mark.parametrize("G,opts", [(1, {}), (4, {}), (5, dict(cells_per_task=3)), (32, {}),
+                                    (37, dict(cells_per_task=2, dir_chunk=5)), (12, dict(dir_chunk=7))])
+def test_one_sweep_matches_oracle(precision, G, opts):
+    cfg = _box(n=4 if G >= 32 else 5, G=G)
+    P = o2.Problem2(cfg)
+    phi_in = np.random.default_rng(11).uniform(0.0, 1.0, (P.C, G, 10))
+    ref = P.transport_step(phi_in, threads=8)
+    prob = tf.Problem.from_config(cfg, precision=precision, order=2, **opts)
+    out = torch.zeros_like(_dev(phi_in))
+    prob.sweep(_dev(phi_in), out)
+    assert _rel(out.cpu().numpy(), ref) < TOL[precision]
+    st = prob.stats()
+    assert st["tasks_executed"] == st["n_tasks"] and st["kernel_mode"] == 5
+
+
+@pytest.mark.parametrize("precision", [tf.TF_FP64, tf.TF_FP32])
+def test_psi_of_directions_matches_oracle(precision):
+    cfg = _box(n=4, G=6)
+    P = o2.Problem2(cfg)
+    phi_in = np.random.default_rng(2).uniform(0.0, 1.0, (P.C, 6, 10))
+    q = P.source(phi_in)
+    prob = tf.Problem.from_config(cfg, precision=precision, order=2)
+    prob.sweep(_dev(phi_in), torch.zeros_like(_dev(phi_in)))
+    dt = torch.float64 if precision == tf.TF_FP64 else torch.float32
+    for a in (0, 5, P.D - 1):
+        buf = torch.empty((P.C, 6, 10), dtype=dt, device="cuda")
+        got = prob.psi(a, buf).double().cpu().numpy()
+        assert _rel(got, P.sweep_direction(a, q)) < TOL[precision], a
+
+
+@pytest.mark.parametrize("precision", [tf.TF_FP64, tf.TF_FP32])
+def test_converged_source_iteration_matches_oracle(precision):
+    """Two materials, up- and downscatter: the device iteration stops at the same
+    test, with phi, the integrated flux (Eq. 3 with the quadratic field) and the
+    particle balance of the device against the oracle."""
+    cfg = _box(n=4, G=4, two_material=True)
+    P = o2.Problem2(cfg)
+    ref, it_ref, r_ref = P.source_iterate(1e-8, 500, threads=8)
+    prob = tf.Problem.from_config(cfg, precision=precision, order=2)
+    phi = torch.zeros((P.C, 4, 10), dtype=torch.float64, device="cuda")
+    tol = 1e-8 if precision == tf.TF_FP64 else 1e-6
+    res = prob.source_iterate(phi, tol, 500)
+    assert res["converged"]
+    if precision == tf.TF_FP64:
+        assert abs(res["iterations"] - it_ref) <= 1
+    assert _rel(phi.cpu().numpy(), ref) < (1e-7 if precision == tf.TF_FP64 else 2e-5)
+    ig, tot = P.integrated_flux(phi.cpu().numpy())
+    assert np.allclose(res["integrated_flux"], ig, rtol=1e-12, atol=0)
+    assert res["balance"] < (1e-12 if precision == tf.TF_FP64 else 1e-5), res["balance"]
+
+
+def test_host_buffers_and_aliasing():
+    cfg = _box(n=3, G=3)
+    P = o2.Problem2(cfg)
+    phi_in = np.random.default_rng(4).uniform(0.0, 1.0, (P.C, 3, 10))
+    ref = P.transport_step(phi_in)
+    prob = tf.Problem.from_config(cfg, precision=tf.TF_FP64, order=2)
+    hin = torch.from_numpy(phi_in.copy()).pin_memory()
+    hout = torch.zeros_like(hin).pin_memory()
+    prob.sweep(hin, hout)
+    assert _rel(hout.numpy(), ref) < 1e-11
+    buf = _dev(phi_in)
+    prob.sweep(buf, buf)
+    assert _rel(buf.cpu().numpy(), ref) < 1e-11
+
+
+def test_second_order_rejections():
+    cfg = _box(n=2, G=2)
+    with pytest.raises(tf.TfError) as e:
+        tf.Problem.from_config(cfg, order=2, schedule=tf.TF_SCHED_BSP)
+    assert e.value.status == tf.TF_ERR_ARG
+    with pytest.raises(tf.TfError) as e:
+        tf.Problem.from_config(cfg, order=2, psi_inflow=np.ones((cfg["xyz"].shape[0], 2)))
+    assert e.value.status == tf.TF_ERR_ARG
+    with pytest.raises(ValueError):
+        tf.Problem.from_config(W.small_box(n=2, G=2), order=2)  # a linear-element Q
+    a = tf.Problem.from_config(cfg, order=2)
+    b = tf.Problem.from_config(cfg, order=2)
+    C = len(cfg["tets"])
+    phis = [torch.zeros((C, 2, 10), dtype=torch.float64, device="cuda") for _ in range(2)]
+    with pytest.raises(tf.TfError) as e:
+        tf.sweep_batch([a, b], phis, phis)
+    assert e.value.status == tf.TF_ERR_ARG

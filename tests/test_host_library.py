@@ -1,6 +1,7 @@
 """Host-side tests of the native library (no GPU): it loads, exports every
 symbol the C header declares, and its host precompute (geometry, quadrature,
 face classification, t-levels) is bit-identical to the oracle's."""
+import os
 import re
 
 import numpy as np
@@ -10,6 +11,8 @@ import oracle
 import paper_2510_11513_gb300 as tf
 import workloads as W
 from paper_2510_11513_gb300 import build as tfbuild
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def test_library_exports_every_declared_symbol():
@@ -108,3 +111,52 @@ def test_status_strings():
     lib = tf.load()
     for s in range(9):
         assert lib.tf_status_string(s)
+
+
+def test_second_order_element_tables_exact(tmp_path):
+    """The exact rationals the second-order kernels use (csrc/p2_tables.h, compiled
+    here as host C++) against exact monomial integration of the basis polynomials."""
+    import subprocess
+
+    from fractions import Fraction
+
+    from p2_checks import _mul, basis_polys, face_nodes, integrate_cell, tables
+
+    src = tmp_path / "t.cpp"
+    src.write_text(
+        '#include <cstdio>\n#include "p2_tables.h"\nint main() {\n'
+        '  for (int i = 0; i < 10; ++i) std::printf("%.17g\\n", p2_p(i));\n'
+        '  for (int i = 0; i < 10; ++i) for (int m = 0; m < 4; ++m) std::printf("%.17g\\n", p2_P(i, m));\n'
+        '  for (int i = 0; i < 10; ++i) for (int j = 0; j < 10; ++j) std::printf("%.17g\\n", p2_M(i, j));\n'
+        '  for (int b = 0; b < 6; ++b) for (int c = 0; c < 6; ++c) std::printf("%.17g\\n", p2_F(b, c));\n'
+        '  for (int f = 0; f < 4; ++f) for (int b = 0; b < 6; ++b) std::printf("%d\\n", p2_face_node(f, b));\n'
+        '  return 0; }\n')
+    exe = tmp_path / "t"
+    inc = os.path.join(ROOT, "paper_2510_11513_gb300", "csrc")
+    subprocess.check_call(["g++", "-std=c++17", f"-I{inc}", str(src), "-o", str(exe)])
+    vals = [float(x) for x in subprocess.check_output([str(exe)]).split()]
+    p, M, Dk, F = tables()
+    got_p, got_P = np.array(vals[:10]), np.array(vals[10:50]).reshape(10, 4)
+    got_M, got_F = np.array(vals[50:150]).reshape(10, 10), np.array(vals[150:186]).reshape(6, 6)
+    got_fn = np.array(vals[186:210], dtype=int).reshape(4, 6)
+    assert np.allclose(got_p, p, rtol=0, atol=1e-16)
+    assert np.allclose(got_M, M, rtol=0, atol=1e-16)
+    B = basis_polys()
+    lam = [{tuple(int(j == k) for j in range(4)): Fraction(1)} for k in range(4)]
+    P = np.array([[float(integrate_cell(_mul(B[i], lam[m]))) for m in range(4)] for i in range(10)])
+    assert np.allclose(got_P, P, rtol=0, atol=1e-16)
+    # the streaming matrix the kernel forms from P and p equals int phi_i d phi_j / d lambda_k exactly
+    E = ((0, 1), (0, 2), (0, 3), (1, 2), (1, 3), (2, 3))
+    for k in range(4):
+        for i in range(10):
+            for j in range(10):
+                if j < 4:
+                    v = (4 * got_P[i, j] - got_p[i]) if j == k else 0.0
+                else:
+                    a, b = E[j - 4]
+                    v = 4 * got_P[i, b] if k == a else (4 * got_P[i, a] if k == b else 0.0)
+                assert abs(v - Dk[k][i][j]) < 1e-15, (k, i, j)
+    for f in range(4):
+        assert list(got_fn[f]) == face_nodes(f)
+        sub = F[f][np.ix_(face_nodes(f), face_nodes(f))]
+        assert np.allclose(got_F, sub, rtol=0, atol=1e-16)
