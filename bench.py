@@ -251,6 +251,57 @@ def schedule_ablation(tf, cfg, prec, local, stream, steps, torch, amt=None):
     return res
 
 
+# FP32 peak of the CUDA cores: 152 SMs x 128 FP32 lanes x 2 flops (FMA) x 2.07 GHz (maximum SM clock).
+FP32_ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
+def p2_flops_per_unit(prob, tf):
+    """Algorithmic flops of one second-order unit (an FMA counts 2): streaming matrix 160,
+    A = V (sigma_t M + K) 300, b = V M q 210, the 10 x 10 elimination and back substitution
+    815, and 156 per interior inflow face (face matrix into A, face term into b); the mean
+    number of interior inflow faces per (cell, direction) comes from the sweep graph."""
+    inflow, _ = tf.tf_graph_levels(prob.mesh.h, prob.quad.h, prob.n_cells, prob.n_dirs)
+    nbr = prob.mesh.geometry()["nbr"]
+    interior = (nbr >= 0).astype(np.uint8)  # [C][4]
+    n_in = sum(float((((inflow >> f) & 1) * interior[None, :, f]).mean()) for f in range(4))
+    return 1485.0 + 156.0 * n_in, n_in
+
+
+def second_order_leg(tf, cfg, prec, local, stream, steps, torch):
+    """The second-order (ten-node) element on one workload: grind time of a source
+    iteration and the sweep kernel's ALU roofline (it is bound by FP32 arithmetic:
+    about 1,800 flops against 80-160 bytes per unit)."""
+    dev = torch.device("cuda", local)
+    pr = tf.Problem.from_config(cfg, precision=prec, device=local, order=2)
+    ph = torch.zeros((pr.n_cells, pr.n_groups, 10), dtype=torch.float64, device=dev)
+    pr.source_iterate(ph, 0.0, 1, stream=stream)
+    st0 = pr.stats()
+    torch.cuda.synchronize(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    r = pr.source_iterate(ph, 0.0, steps, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    st = pr.stats()
+    ms = e0.elapsed_time(e1) / steps
+    sweep_s = (st["cum_sweep_event_seconds"] - st0["cum_sweep_event_seconds"]) / steps
+    flops, n_in = p2_flops_per_unit(pr, tf)
+    achieved = flops * pr.n_units / sweep_s / 1e12
+    out = {"workload": cfg["name"], "units_per_step": pr.n_units, "ms_per_step": ms,
+           "grind": ms * 1e6 / pr.n_units, "unit": UNIT, "sweep_ms": sweep_s * 1e3,
+           "phi_ms": (st["cum_phi_event_seconds"] - st0["cum_phi_event_seconds"]) / steps * 1e3,
+           "cells_per_task": st["cells_per_task"], "balance": r["balance"],
+           "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
+                        "frac": achieved / FP32_ALU_PEAK_TFLOPS, "flops_per_unit": flops,
+                        "mean_interior_inflow_faces": n_in, "kernel": "sweep_kernel<float, 5>",
+                        "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"}}
+    pr.close()
+    del pr, ph
+    torch.cuda.synchronize(dev)
+    return out
+
+
 def run_ours(args):
     import torch
 
@@ -366,6 +417,9 @@ def run_ours(args):
         abl = [schedule_ablation(tf, cfg, prec, local, stream, args.bsp_steps, torch, amt_main)]
         abl.append(schedule_ablation(tf, W.paper_context_box(), prec, local, stream, 5, torch))
         line["schedule_ablation"] = abl
+    if not args.no_second_order and world == 1 and prec == tf.TF_FP32:
+        # the paper's second-order element, on the two-material box (805 M units per step)
+        line["second_order"] = second_order_leg(tf, W.order2(W.two_material_box()), prec, local, stream, 3, torch)
     if not args.no_fp64_compare and prec == tf.TF_FP32:
         p64 = tf.Problem.from_config(cfg, precision=tf.TF_FP64, device=local)
         phi64 = torch.zeros((C, G, 4), dtype=torch.float64, device=dev)
@@ -554,6 +608,7 @@ def main():
     ap.add_argument("--schedule", default="amt", choices=sorted(SCHEDULES),
                     help="task schedule of the timed sweep: many-task (amt) or bulk-synchronous")
     ap.add_argument("--no-bsp-compare", action="store_true", help="skip the many-task vs bulk-synchronous legs")
+    ap.add_argument("--no-second-order", action="store_true", help="skip the second-order element leg")
     ap.add_argument("--bsp-steps", type=int, default=2, help="timed steps of each schedule in the comparison")
     ap.add_argument("--octant-window", type=int, default=0, help="octants active at once (0 = library default)")
     ap.add_argument("--staging", type=int, default=0, help="0 auto, 1 no shared-memory staging, 2 two stages, 3 three stages")

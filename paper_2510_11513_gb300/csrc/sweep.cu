@@ -1207,7 +1207,11 @@ tf_status device_create(Problem &p, const int32_t *cell_material, const double *
         d.warp_smem = d.staged ? (uint32_t)wb128 : 0u;
         d.two_stage = d.staged && ns == 2 && !d.fp64;
     }
-    d.mode = d.order == 2 ? 5
+    // second order: staged in shared memory (FP32, G a multiple of 32, tasks of at most 32 cells)
+    const bool p2_staged = d.order == 2 && !d.fp64 && d.G % 32 == 0 && g.cells_per_task <= 32 && p.opt.staging != 1 &&
+                           ((p2_stage_bytes(d.G) * 2 + 48 + 127) / 128 * 128) * d.wpc <= 227 * 1024;
+    if (p2_staged) d.warp_smem = (p2_stage_bytes(d.G) * 2 + 48 + 127) / 128 * 128;
+    d.mode = d.order == 2 ? (p2_staged ? 6 : 5)
              : d.paired  ? 3
              : d.staged  ? (d.two_stage ? 4 : 2)
                          : (d.G % 32 == 0 && g.cells_per_task <= 64 ? 1 : 0);
@@ -1237,7 +1241,8 @@ tf_status device_create(Problem &p, const int32_t *cell_material, const double *
         d.ppl = (int)L.ppl;
     }
     const int dyn = (int)(d.warp_smem * d.wpc);
-    const void *kfn = d.mode == 5 ? (d.fp64 ? (const void *)sweep_kernel<double, 5> : (const void *)sweep_kernel<float, 5>)
+    const void *kfn = d.mode == 6   ? (const void *)sweep_kernel<float, 6>
+                      : d.mode == 5 ? (d.fp64 ? (const void *)sweep_kernel<double, 5> : (const void *)sweep_kernel<float, 5>)
                       : d.fp64 ? (d.mode == 2 ? (const void *)sweep_kernel<double, 2>
                                             : d.mode == 1 ? (const void *)sweep_kernel<double, 1> : (const void *)sweep_kernel<double, 0>)
                              : (d.mode == 3   ? (const void *)sweep_kernel<float, 3>
@@ -1549,8 +1554,9 @@ template <class T> tf_status launch_step(Problem &p, const double *phi_in, doubl
         if constexpr (sizeof(T) == 4) {
             if (d.mode == 3) sweep_kernel<T, 3><<<d.grid, 32 * d.wpc, dyn, st>>>(A);
             if (d.mode == 4) sweep_kernel<T, 4><<<d.grid, 32 * d.wpc, dyn, st>>>(A);
+            if (d.mode == 6) sweep_kernel<T, 6><<<d.grid, 32 * d.wpc, dyn, st>>>(A);
         }
-        if (d.mode == 3 || d.mode == 4) {
+        if (d.mode == 3 || d.mode == 4 || d.mode == 6) {
         } else if (d.mode == 5)
             sweep_kernel<T, 5><<<d.grid, 32 * d.wpc, 0, st>>>(A);
         else if (d.mode == 2)

@@ -181,8 +181,6 @@ template <class T> struct SweepArgs {
     const void *geo2;            // second-order element: P2Geo<T> [C] cell records (mode 5)
 };
 
-#include "p2_solve.cuh"
-
 // Solve one 4x4 system by Gaussian elimination without pivoting: the
 // symmetric part of the upwind-DG matrix, (1/2) sum_f |Omega.N_f| M_f +
 // sigma_t M, is positive definite, so every pivot is positive.
@@ -1124,6 +1122,8 @@ __device__ __forceinline__ bool run_task_staged_any(const SweepArgs<T> &A, uint4
     return run_task_staged<T, 0, NS>(A, ti, lane, ox, oy, oz, psi_dir, wsm, bars, ph, wacc);
 }
 
+#include "p2_solve.cuh"
+
 // Persistent sweep: a warp claims a ticket (the next queue slot), waits until
 // that slot holds a ready task, executes it with lanes spanning (cell, group)
 // units, then decrements the counters of the task's downwind blocks; a
@@ -1136,9 +1136,10 @@ __device__ __forceinline__ bool run_task_staged_any(const SweepArgs<T> &A, uint4
 // 2 = G a multiple of 32 with the rows staged in shared memory (three stages),
 // 3 = FP32 and G even: packed group pairs (pair-interleaved source and psi rows),
 // 4 = as 2 with two stages and six resident CTAs per SM (FP32),
-// 5 = the second-order (ten-node) element, lanes over (cell, group) units.
+// 5 = the second-order (ten-node) element, lanes over (cell, group) units,
+// 6 = the second-order element staged in shared memory (FP32, G a multiple of 32).
 template <class T, int MODE>
-__global__ void __launch_bounds__(128, MODE == 5 ? 2 : MODE == 4 ? 6 : (sizeof(T) == 4 ? 4 : 3))
+__global__ void __launch_bounds__(128, MODE == 5 ? 2 : MODE == 6 ? 3 : MODE == 4 ? 6 : (sizeof(T) == 4 ? 4 : 3))
     sweep_kernel(const SweepArgs<T> A)
 {
     const int lane = threadIdx.x & 31;
@@ -1149,7 +1150,7 @@ __global__ void __launch_bounds__(128, MODE == 5 ? 2 : MODE == 4 ? 6 : (sizeof(T
     uint32_t ph = 0;  // mbarrier phase parities of this warp's stages
     // the six mbarriers of the staged paths sit in the last 48 bytes of the warp's region
     uint64_t *bars = reinterpret_cast<uint64_t *>(wsm + A.warp_smem - 48);
-    if constexpr (MODE == 2 || MODE == 3 || MODE == 4) {
+    if constexpr (MODE == 2 || MODE == 3 || MODE == 4 || MODE == 6) {
         if (lane == 0) {
             for (int b = 0; b < 6; ++b) mbar_init(&bars[b], 1);
             fence_proxy_async_shared();
@@ -1239,6 +1240,8 @@ __global__ void __launch_bounds__(128, MODE == 5 ? 2 : MODE == 4 ? 6 : (sizeof(T
             run_task_wide(A, ti, lane, om.x, om.y, om.z, psi_dir);
         } else if constexpr (MODE == 5) {
             run_task_p2(A, ti, lane, om.x, om.y, om.z, psi_dir);
+        } else if constexpr (MODE == 6) {
+            if (!run_task_p2_staged(A, ti, lane, om.x, om.y, om.z, psi_dir, wsm, bars, ph, ws + 6)) break;
         } else {
             run_task_generic(A, ti, lane, om.x, om.y, om.z, psi_dir);
         }

@@ -34,7 +34,9 @@ def _box(n, G, seed=5, two_material=False):
 
 @pytest.mark.parametrize("precision", [tf.TF_FP64, tf.TF_FP32])
 @pytest.mark.parametrize("G,opts", [(1, {}), (4, {}), (5, dict(cells_per_task=3)), (32, {}),
-                                    (37, dict(cells_per_task=2, dir_chunk=5)), (12, dict(dir_chunk=7))])
+                                    (37, dict(cells_per_task=2, dir_chunk=5)), (12, dict(dir_chunk=7)),
+                                    (64, dict(cells_per_task=5, dir_chunk=9)), (32, dict(staging=1)),
+                                    (96, dict(cells_per_task=3))])
 def test_one_sweep_matches_oracle(precision, G, opts):
     cfg = _box(n=4 if G >= 32 else 5, G=G)
     P = o2.Problem2(cfg)
@@ -45,34 +47,35 @@ def test_one_sweep_matches_oracle(precision, G, opts):
     prob.sweep(_dev(phi_in), out)
     assert _rel(out.cpu().numpy(), ref) < TOL[precision]
     st = prob.stats()
-    assert st["tasks_executed"] == st["n_tasks"] and st["kernel_mode"] == 5
+    staged = precision == tf.TF_FP32 and G % 32 == 0 and opts.get("staging", 0) != 1
+    assert st["tasks_executed"] == st["n_tasks"] and st["kernel_mode"] == (6 if staged else 5)
 
 
-@pytest.mark.parametrize("precision", [tf.TF_FP64, tf.TF_FP32])
-def test_psi_of_directions_matches_oracle(precision):
-    cfg = _box(n=4, G=6)
+@pytest.mark.parametrize("precision,G", [(tf.TF_FP64, 6), (tf.TF_FP32, 6), (tf.TF_FP32, 32)])
+def test_psi_of_directions_matches_oracle(precision, G):
+    cfg = _box(n=4, G=G)
     P = o2.Problem2(cfg)
-    phi_in = np.random.default_rng(2).uniform(0.0, 1.0, (P.C, 6, 10))
+    phi_in = np.random.default_rng(2).uniform(0.0, 1.0, (P.C, G, 10))
     q = P.source(phi_in)
     prob = tf.Problem.from_config(cfg, precision=precision, order=2)
     prob.sweep(_dev(phi_in), torch.zeros_like(_dev(phi_in)))
     dt = torch.float64 if precision == tf.TF_FP64 else torch.float32
     for a in (0, 5, P.D - 1):
-        buf = torch.empty((P.C, 6, 10), dtype=dt, device="cuda")
+        buf = torch.empty((P.C, G, 10), dtype=dt, device="cuda")
         got = prob.psi(a, buf).double().cpu().numpy()
         assert _rel(got, P.sweep_direction(a, q)) < TOL[precision], a
 
 
-@pytest.mark.parametrize("precision", [tf.TF_FP64, tf.TF_FP32])
-def test_converged_source_iteration_matches_oracle(precision):
+@pytest.mark.parametrize("precision,G", [(tf.TF_FP64, 4), (tf.TF_FP32, 4), (tf.TF_FP32, 32)])
+def test_converged_source_iteration_matches_oracle(precision, G):
     """Two materials, up- and downscatter: the device iteration stops at the same
     test, with phi, the integrated flux (Eq. 3 with the quadratic field) and the
     particle balance of the device against the oracle."""
-    cfg = _box(n=4, G=4, two_material=True)
+    cfg = _box(n=4, G=G, two_material=True)
     P = o2.Problem2(cfg)
     ref, it_ref, r_ref = P.source_iterate(1e-8, 500, threads=8)
     prob = tf.Problem.from_config(cfg, precision=precision, order=2)
-    phi = torch.zeros((P.C, 4, 10), dtype=torch.float64, device="cuda")
+    phi = torch.zeros((P.C, G, 10), dtype=torch.float64, device="cuda")
     tol = 1e-8 if precision == tf.TF_FP64 else 1e-6
     res = prob.source_iterate(phi, tol, 500)
     assert res["converged"]
