@@ -151,8 +151,13 @@ def cpu_oracle_sample(cfg, n_dirs=None, threads=None):
     om, w = oracle.product_quadrature(cfg["n_polar"], cfg["n_azimuthal"])
     D = om.shape[0]
     idx = np.linspace(0, D - 1, n_dirs).round().astype(int)
-    P = oracle.Problem(cfg, omega=om[idx], w=w[idx])
-    phi = np.random.default_rng(0).uniform(0.0, 1.0, (P.C, P.G, 4))
+    if cfg.get("order", 1) == 2:
+        from oracle import p2 as o2
+        P = o2.Problem2(cfg, omega=om[idx], w=w[idx])
+    else:
+        P = oracle.Problem(cfg, omega=om[idx], w=w[idx])
+    nodes = 10 if cfg.get("order", 1) == 2 else 4
+    phi = np.random.default_rng(0).uniform(0.0, 1.0, (P.C, P.G, nodes))
     t0 = time.perf_counter()
     q = P.source(phi)
     _, _, used = P.sweep(q, threads=threads)
@@ -182,6 +187,8 @@ def run_reference(args):
     if rank != 0:
         return
     cfg = make_config(args)
+    if args.order == 2:
+        cfg = W.order2(cfg)
     threads = os.cpu_count() or 1
     # warm-up steps (untimed), then timed steps; each step is a bounded sample
     for _ in range(args.warmup):
@@ -314,16 +321,20 @@ def run_ours(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     cfg = make_config(args)
+    if args.order == 2:
+        cfg = W.order2(cfg)
     prec = tf.TF_FP64 if args.precision == "fp64" else tf.TF_FP32
     t_setup = time.perf_counter()
     prob = tf.Problem.from_config(cfg, precision=prec, device=local, cells_per_task=args.cells_per_task,
                                   warps_per_cta=args.warps_per_cta, octant_window=args.octant_window,
-                                  staging=args.staging, pairing=args.pairing, schedule=SCHEDULES[args.schedule])
+                                  staging=args.staging, pairing=args.pairing, schedule=SCHEDULES[args.schedule],
+                                  order=args.order)
     t_setup = time.perf_counter() - t_setup
     C, G, D = prob.n_cells, prob.n_groups, prob.n_dirs
     units = prob.n_units
     stream = torch.cuda.current_stream(dev)
-    phi = torch.zeros((C, G, 4), dtype=torch.float64, device=dev)
+    nodes = prob.n_nodes
+    phi = torch.zeros((C, G, nodes), dtype=torch.float64, device=dev)
     # warm-up: W source iterations from zero
     prob.source_iterate(phi, 0.0, args.warmup, stream=stream)
     st0 = prob.stats()
@@ -355,6 +366,8 @@ def run_ours(args):
     # cell record + cell-list entry once per (cell, direction), amortised over G
     geo = 128 if prec == tf.TF_FP32 else 256
     b_unit = 8 * s + (geo + 4) / G
+    if args.order == 2:  # source row and psi row of ten nodes, 144-byte record + list entry per (cell, direction)
+        b_unit = 20 * s + (144 + 4) / G
     peak, peak_kind = _peaks()
     achieved = b_unit * units / sweep_s / 1e9
     klabel = ("sweep_kernel" if args.schedule == "amt" else "bsp_sweep_kernel") + \
@@ -364,7 +377,8 @@ def run_ours(args):
             "vs_baseline": None, "dtype": "f32" if prec == tf.TF_FP32 else "f64", "data": "synthetic",
             "config": {"workload": cfg["name"], "cells": C, "directions": D, "groups": G,
                        "units_per_step": units, "precision": args.precision, "phi_accumulate": "fp32-pair->fp64",
-                       "l2": "inputs larger than L2 (psi store %.1f GB)" % (units * 4 * s / 1e9),
+                       "l2": "inputs larger than L2 (psi store %.1f GB)" % (units * nodes * s / 1e9),
+                       "element_order": args.order,
                        "parallelism": f"replicas{world}", "setup_s": round(t_setup, 2),
                        "schedule": args.schedule},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -383,9 +397,19 @@ def run_ours(args):
                            "n_chunks": st1["n_chunks"], "octant_window": args.octant_window or 8},
             "gpu_launches": int((st1["launches_per_step"] + 2) * args.steps),
             "clocks": clk}
+    if args.order == 2 and prec == tf.TF_FP32:
+        # the second-order kernel is bound by FP32 arithmetic, not by HBM
+        flops, n_in = p2_flops_per_unit(prob, tf)
+        ach = flops * units / sweep_s / 1e12
+        line["roofline"] = {"bound": "alu", "achieved": ach, "peak": FP32_ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
+                            "frac": ach / FP32_ALU_PEAK_TFLOPS,
+                            "traffic": _traffic(cfg["name"], args.precision, klabel), "kernel": klabel,
+                            "flops_per_unit": flops, "mean_interior_inflow_faces": n_in,
+                            "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
+                            "bytes_per_unit": b_unit, "hbm_achieved_gbs": achieved}
     # end to end: tf_sweep with pinned host buffers (H2D of phi_in, D2H of phi_out inside)
     if not args.no_e2e:
-        hin = torch.zeros((C, G, 4), dtype=torch.float64).pin_memory()
+        hin = torch.zeros((C, G, nodes), dtype=torch.float64).pin_memory()
         hin.copy_(phi.cpu())
         hout = torch.zeros_like(hin).pin_memory()
         prob.sweep(hin, hout, stream=stream)
@@ -398,7 +422,7 @@ def run_ours(args):
         torch.cuda.synchronize(dev)
         _barrier(world)
         e2e_ms = _max_over_ranks(world, (time.perf_counter() - t0) * 1e3) / args.steps
-        nbytes = C * G * 4 * 8
+        nbytes = C * G * nodes * 8
         line["e2e"] = {"value": e2e_ms * 1e6 / units / world, "unit": UNIT, "h2d_bytes_per_step": nbytes,
                        "d2h_bytes_per_step": nbytes, "ms_per_step": e2e_ms,
                        "call": "tf_sweep(host pinned phi_in, host pinned phi_out)"}
@@ -411,18 +435,18 @@ def run_ours(args):
     prob.close()
     del prob
     torch.cuda.synchronize(dev)
-    if not args.no_bsp_compare and world == 1:
+    if not args.no_bsp_compare and world == 1 and args.order == 1:
         # the paper's comparison (Sec. 5): many-task against level-synchronous buckets,
         # on this workload and on the 16^3-hex one nearest the paper's own
         abl = [schedule_ablation(tf, cfg, prec, local, stream, args.bsp_steps, torch, amt_main)]
         abl.append(schedule_ablation(tf, W.paper_context_box(), prec, local, stream, 5, torch))
         line["schedule_ablation"] = abl
-    if not args.no_second_order and world == 1 and prec == tf.TF_FP32:
+    if not args.no_second_order and world == 1 and prec == tf.TF_FP32 and args.order == 1:
         # the paper's second-order element, on the two-material box (805 M units per step)
         line["second_order"] = second_order_leg(tf, W.order2(W.two_material_box()), prec, local, stream, 3, torch)
     if not args.no_fp64_compare and prec == tf.TF_FP32:
-        p64 = tf.Problem.from_config(cfg, precision=tf.TF_FP64, device=local)
-        phi64 = torch.zeros((C, G, 4), dtype=torch.float64, device=dev)
+        p64 = tf.Problem.from_config(cfg, precision=tf.TF_FP64, device=local, order=args.order)
+        phi64 = torch.zeros((C, G, nodes), dtype=torch.float64, device=dev)
         p64.source_iterate(phi64, 0.0, 1, stream=stream)
         torch.cuda.synchronize(dev)
         e0.record(stream)
@@ -609,6 +633,8 @@ def main():
                     help="task schedule of the timed sweep: many-task (amt) or bulk-synchronous")
     ap.add_argument("--no-bsp-compare", action="store_true", help="skip the many-task vs bulk-synchronous legs")
     ap.add_argument("--no-second-order", action="store_true", help="skip the second-order element leg")
+    ap.add_argument("--order", type=int, default=1, choices=[1, 2],
+                    help="finite-element order of the timed sweep (2: the ten-node element)")
     ap.add_argument("--bsp-steps", type=int, default=2, help="timed steps of each schedule in the comparison")
     ap.add_argument("--octant-window", type=int, default=0, help="octants active at once (0 = library default)")
     ap.add_argument("--staging", type=int, default=0, help="0 auto, 1 no shared-memory staging, 2 two stages, 3 three stages")
