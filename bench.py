@@ -37,14 +37,25 @@ UNIT = "ns/(cell·dir·group)"
 L2_BYTES = 129 * 1024 * 1024
 
 
+KERNEL_SOURCES = ("sweep_kernel.cuh", "p2_solve.cuh", "p2_tables.h")
+
+
+def kernel_source_sha1():
+    """SHA-1 over the sweep kernel's device sources (concatenated in KERNEL_SOURCES order)."""
+    import hashlib
+    h = hashlib.sha1()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2510_11513_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
 def _traffic(workload, precision, kernel_label):
     """DRAM bytes per sweep-kernel launch from the committed ncu record, if it was taken on
     this workload with the current kernel source; else None."""
     import glob
-    import hashlib
-    src = os.path.join(ROOT, "paper_2510_11513_gb300", "csrc", "sweep_kernel.cuh")
     try:
-        sha = hashlib.sha1(open(src, "rb").read()).hexdigest()
+        sha = kernel_source_sha1()
     except OSError:
         return None
     for f in glob.glob(os.path.join(ROOT, "profiles", "traffic_*.json")):
@@ -295,13 +306,15 @@ def second_order_leg(tf, cfg, prec, local, stream, steps, torch):
     sweep_s = (st["cum_sweep_event_seconds"] - st0["cum_sweep_event_seconds"]) / steps
     flops, n_in = p2_flops_per_unit(pr, tf)
     achieved = flops * pr.n_units / sweep_s / 1e12
+    klabel = f"sweep_kernel<float, {st['kernel_mode']}>"
     out = {"workload": cfg["name"], "units_per_step": pr.n_units, "ms_per_step": ms,
            "grind": ms * 1e6 / pr.n_units, "unit": UNIT, "sweep_ms": sweep_s * 1e3,
            "phi_ms": (st["cum_phi_event_seconds"] - st0["cum_phi_event_seconds"]) / steps * 1e3,
            "cells_per_task": st["cells_per_task"], "balance": r["balance"],
            "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
                         "frac": achieved / FP32_ALU_PEAK_TFLOPS, "flops_per_unit": flops,
-                        "mean_interior_inflow_faces": n_in, "kernel": "sweep_kernel<float, 5>",
+                        "mean_interior_inflow_faces": n_in, "kernel": klabel,
+                        "traffic": _traffic(cfg["name"], "fp32", klabel),
                         "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"}}
     pr.close()
     del pr, ph
