@@ -340,6 +340,7 @@ def run_ours(args):
     t_setup = time.perf_counter()
     prob = tf.Problem.from_config(cfg, precision=prec, device=local, cells_per_task=args.cells_per_task,
                                   warps_per_cta=args.warps_per_cta, octant_window=args.octant_window,
+                                  keep_ready=args.keep_ready,
                                   staging=args.staging, pairing=args.pairing, schedule=SCHEDULES[args.schedule],
                                   order=args.order)
     t_setup = time.perf_counter() - t_setup
@@ -407,7 +408,8 @@ def run_ours(args):
                            "warps_per_cta": st1["warps_per_cta"], "mean_ready": st1["mean_ready"],
                            "wait_frac": st1["wait_seconds"] / max(st1["wait_seconds"] + st1["busy_seconds"], 1e-30),
                            "data_wait_frac": st1["data_wait_seconds"] / max(st1["busy_seconds"], 1e-30),
-                           "n_chunks": st1["n_chunks"], "octant_window": args.octant_window or 8},
+                           "n_chunks": st1["n_chunks"], "octant_window": args.octant_window or 8,
+                           "keep_ready": args.keep_ready or 1},
             "gpu_launches": int((st1["launches_per_step"] + 2) * args.steps),
             "clocks": clk}
     if args.order == 2 and prec == tf.TF_FP32:
@@ -650,6 +652,7 @@ def main():
                     help="finite-element order of the timed sweep (2: the ten-node element)")
     ap.add_argument("--bsp-steps", type=int, default=2, help="timed steps of each schedule in the comparison")
     ap.add_argument("--octant-window", type=int, default=0, help="octants active at once (0 = library default)")
+    ap.add_argument("--keep-ready", type=int, default=0, help="ready tasks a warp keeps and runs next (0 = library default)")
     ap.add_argument("--staging", type=int, default=0, help="0 auto, 1 no shared-memory staging, 2 two stages, 3 three stages")
     ap.add_argument("--pairing", type=int, default=0, help="0 auto, 1 off, 2 packed group pairs when G is even")
     ap.add_argument("--batch-count", type=int, default=64, help="--config batch: number of problems")

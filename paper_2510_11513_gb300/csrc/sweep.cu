@@ -1446,6 +1446,7 @@ template <class T> SweepArgs<T> make_args(Problem &p, int k)
     A.stages = d.pair_stages;
     A.mode = d.mode;
     A.geo2 = d.geo2;
+    A.keep_max = p.opt.keep_ready > 0 ? std::min(p.opt.keep_ready, 4) : 1;
     return A;
 }
 

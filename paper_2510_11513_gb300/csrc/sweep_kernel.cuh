@@ -179,6 +179,7 @@ template <class T> struct SweepArgs {
     int32_t stages;              // paired path: buffers in the ring of staged copies (2 or 3)
     int32_t mode;                // kernel variant of this problem (batched launches dispatch on it)
     const void *geo2;            // second-order element: P2Geo<T> [C] cell records (mode 5)
+    int32_t keep_max;            // ready tasks a warp keeps and runs next (1..4)
 };
 
 // Solve one 4x4 system by Gaussian elimination without pivoting: the
@@ -1128,8 +1129,9 @@ __device__ __forceinline__ bool run_task_staged_any(const SweepArgs<T> &A, uint4
 // that slot holds a ready task, executes it with lanes spanning (cell, group)
 // units, then decrements the counters of the task's downwind blocks; a
 // decrement that reaches zero makes that block ready (work-first generation,
-// Algorithm 1; atomic counters, Sec. 3.5).  The warp keeps the first block it
-// made ready and runs it next, without the queue; it enqueues the others.
+// Algorithm 1; atomic counters, Sec. 3.5).  The warp keeps up to keep_max of
+// the blocks it made ready and runs them next, without the queue; it enqueues
+// the others.
 // Termination: a warp whose ticket is >= n_tasks, or that waits while all
 // n_tasks tasks are complete, exits.  Every wait is bounded by wait_limit_ns.
 // MODE: 0 = any group count (registers), 1 = G a multiple of 32 (registers),
@@ -1163,14 +1165,19 @@ __global__ void __launch_bounds__(128, MODE == 5 ? 2 : MODE == 6 ? 3 : MODE == 4
     if (lane < 7) ws[lane] = 0;
     __syncwarp();
     const unsigned long long t_start = globaltimer();
-    // A warp that releases downwind tasks keeps one of them and runs it next
-    // (its upwind rows were just written and are still in L2); it claims a
-    // queue ticket only when it keeps nothing.  Fewer than n_tasks slots are
-    // then filled, so a waiting warp also stops once every task is complete.
-    unsigned keep = 0xffffffffu;
+    // A warp that releases downwind tasks keeps up to keep_max of them on a small
+    // private stack and runs them next, most recent first (their upwind rows were
+    // just written and are still in L2); it claims a queue ticket only when the
+    // stack is empty.  Fewer than n_tasks slots are then filled, so a waiting warp
+    // also stops once every task is complete.
+    __shared__ unsigned kstack[4][4];  // [warp][slot]
+    unsigned *ks = kstack[threadIdx.x >> 5];
+    int nk = 0;  // warp-uniform stack depth
     for (;;) {
-        unsigned task = keep;
-        if (keep == 0xffffffffu) {
+        unsigned task = 0;
+        if (nk > 0) {
+            task = ks[--nk];
+        } else {
             int stop = 0;
             if (lane == 0) {
                 const unsigned long long ticket = atomicAdd(&A.ctrl->head, 1ull);
@@ -1222,7 +1229,7 @@ __global__ void __launch_bounds__(128, MODE == 5 ? 2 : MODE == 6 ? 3 : MODE == 4
             if (stop) break;
             task = __shfl_sync(FULL, task, 0);
         }
-        keep = 0xffffffffu;
+        __syncwarp();  // every lane has read its task from the stack before kept tasks are written to it
         unsigned long long tb = 0;
         if (lane == 0) tb = globaltimer();
 
@@ -1257,9 +1264,13 @@ __global__ void __launch_bounds__(128, MODE == 5 ? 2 : MODE == 6 ? 3 : MODE == 4
                 ready = atom_add_acq_rel(A.counters + d, -1) == 1;
             }
             const unsigned rb = __ballot_sync(FULL, ready);
-            const int kl = (e0 == 0 && rb) ? __ffs(rb) - 1 : -1;  // the warp keeps this lane's task
-            if (kl >= 0) keep = __shfl_sync(FULL, d, kl);
-            if (ready && (int)lane != kl) {
+            // the first (keep_max - nk) ready lanes push their task on the warp's stack
+            const int room = A.keep_max - nk;
+            const int rank = __popc(rb & ((1u << lane) - 1u));
+            const bool kept = ready && rank < room;
+            if (kept) ks[nk + rank] = d;
+            nk += min(room, __popc(rb));
+            if (ready && !kept) {
                 const unsigned long long slot = atomicAdd(&A.ctrl->tail, 1ull);
                 if (slot < A.n_tasks)
                     st_release(A.slots + slot, ((unsigned long long)epoch << 32) | d);
@@ -1267,6 +1278,7 @@ __global__ void __launch_bounds__(128, MODE == 5 ? 2 : MODE == 6 ? 3 : MODE == 4
                     atomicCAS(&A.ctrl->error, 0, (int)TF_ERR_DEVICE);
             }
         }
+        __syncwarp();  // kept tasks visible to every lane of the warp
         // admission: the task that brings its group to the threshold releases the next group's seeds
         if (A.window < A.n_groups) {
             int ng = -1;

@@ -43,7 +43,7 @@ class tf_options(C.Structure):
         ("phi_accumulate", C.c_int32), ("inject_stall", C.c_int32), ("psi_budget_gb", C.c_double),
         ("task_order", C.c_int32), ("staging", C.c_int32), ("octant_window", C.c_int32),
         ("pairing", C.c_int32), ("schedule", C.c_int32), ("order", C.c_int32),
-        ("reserved_i", C.c_int32 * 2),
+        ("keep_ready", C.c_int32), ("reserved_i", C.c_int32 * 1),
         ("residual_floor", C.c_double),
         ("reserved_d", C.c_double * 3),
     ]

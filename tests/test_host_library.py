@@ -107,6 +107,19 @@ def test_argument_errors():
     assert e.value.status == tf.TF_ERR_ARG
 
 
+def test_empty_inputs_rejected():
+    xyz, tets = W.jittered_kuhn_mesh(1, 5)
+    with pytest.raises(tf.TfError) as e:
+        tf.Mesh(xyz, np.zeros((0, 4), dtype=np.int32))
+    assert e.value.status == tf.TF_ERR_ARG
+    with pytest.raises(tf.TfError) as e:
+        tf.Quadrature(omega=np.zeros((0, 3)), w=np.zeros(0))
+    assert e.value.status == tf.TF_ERR_ARG
+    with pytest.raises(tf.TfError) as e:
+        tf.Mesh(xyz[:3], tets[:1])  # fewer than four vertices
+    assert e.value.status == tf.TF_ERR_ARG
+
+
 def test_status_strings():
     lib = tf.load()
     for s in range(9):
