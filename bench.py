@@ -237,8 +237,9 @@ def _schedule_leg(tf, cfg, prec, local, stream, steps, schedule, torch):
     """One schedule on one workload: warm-up sweep, then `steps` source iterations
     timed with CUDA events; returns ms per step, sweep-kernel ms and warp-time split."""
     dev = torch.device("cuda", local)
-    pr = tf.Problem.from_config(cfg, precision=prec, device=local, schedule=SCHEDULES[schedule])
-    ph = torch.zeros((pr.n_cells, pr.n_groups, 4), dtype=torch.float64, device=dev)
+    pr = tf.Problem.from_config(cfg, precision=prec, device=local, schedule=SCHEDULES[schedule],
+                                order=cfg.get("order", 1))
+    ph = torch.zeros((pr.n_cells, pr.n_groups, pr.n_nodes), dtype=torch.float64, device=dev)
     pr.source_iterate(ph, 0.0, 1, stream=stream)
     st0 = pr.stats()
     torch.cuda.synchronize(dev)
@@ -462,6 +463,8 @@ def run_ours(args):
         # on this workload and on the 16^3-hex one nearest the paper's own
         abl = [schedule_ablation(tf, cfg, prec, local, stream, args.bsp_steps, torch, amt_main)]
         abl.append(schedule_ablation(tf, W.paper_context_box(), prec, local, stream, 5, torch))
+        # and with the second-order element, where each task carries about 20 x more arithmetic
+        abl.append(schedule_ablation(tf, W.order2(W.paper_context_box()), prec, local, stream, 5, torch))
         line["schedule_ablation"] = abl
     if not args.no_second_order and world == 1 and prec == tf.TF_FP32 and args.order == 1:
         # the paper's second-order element, on the two-material box (805 M units per step)

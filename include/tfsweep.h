@@ -115,7 +115,7 @@ typedef struct {
     int32_t order;           /* finite-element order: 0 or 1 = linear (4 nodes per cell), 2 = quadratic
                               * (10 nodes: the 4 vertices, then the midpoints of the local edges (0,1) (0,2)
                               * (0,3) (1,2) (1,3) (2,3)); Q and every phi buffer are [n_cells][n_groups][nodes].
-                              * Order 2: vacuum boundaries and no S1 (both NULL), TF_SCHED_AMT, no batching */
+                              * Order 2: vacuum boundaries and no S1 (both NULL), no batching */
     int32_t keep_ready;      /* ready tasks a warp keeps on a private stack and runs next (most recent
                               * first) instead of queueing them; 0 = automatic (1), at most 4 */
     int32_t reserved_i[1];

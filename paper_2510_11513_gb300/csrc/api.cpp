@@ -172,10 +172,9 @@ tf_status tf_problem_create(tf_handle mesh, tf_handle quad, int32_t n_groups, in
                                 "TF_SCHED_BSP_LAUNCH, which has no device wait)");
     }
     if (p->opt.order < 0 || p->opt.order > 2 ||
-        (p->opt.order == 2 && (S1 || psi_inflow || p->opt.schedule != TF_SCHED_AMT))) {
+        (p->opt.order == 2 && (S1 || psi_inflow))) {
         delete p;
-        return fail(TF_ERR_ARG, "tf_problem_create: order must be 0, 1 or 2 (order 2: S1 and psi_inflow NULL, "
-                                "TF_SCHED_AMT)");
+        return fail(TF_ERR_ARG, "tf_problem_create: order must be 0, 1 or 2 (order 2: S1 and psi_inflow NULL)");
     }
     if (!(p->opt.wait_limit_s > 0.0)) p->opt.wait_limit_s = 10.0;
     if (!(p->opt.residual_floor > 0.0) || p->opt.residual_floor > 1.0) p->opt.residual_floor = 1.0;

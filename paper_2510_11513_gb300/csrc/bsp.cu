@@ -78,6 +78,11 @@ __device__ __forceinline__ bool exec_task(const SweepArgs<T> &A, unsigned task, 
     } else if constexpr (MODE == 1) {
         run_task_wide(A, ti, lane, om.x, om.y, om.z, psi_dir);
         return true;
+    } else if constexpr (MODE == 5) {
+        run_task_p2(A, ti, lane, om.x, om.y, om.z, psi_dir);
+        return true;
+    } else if constexpr (MODE == 6) {
+        return run_task_p2_staged(A, ti, lane, om.x, om.y, om.z, psi_dir, wsm, bars, ph, wacc);
     } else {
         run_task_generic(A, ti, lane, om.x, om.y, om.z, psi_dir);
         return true;
@@ -90,7 +95,7 @@ __device__ __forceinline__ bool exec_task(const SweepArgs<T> &A, unsigned task, 
 // finished the bucket.  The time warps spend there is counted as wait time, the
 // time executing tasks as busy time.
 template <class T, int MODE>
-__global__ void __launch_bounds__(128, MODE == 4 ? 6 : (sizeof(T) == 4 ? 4 : 3))
+__global__ void __launch_bounds__(128, MODE == 5 ? 2 : MODE == 6 ? 3 : MODE == 4 ? 6 : (sizeof(T) == 4 ? 4 : 3))
     bsp_sweep_kernel(const SweepArgs<T> A, const BspArgs S)
 {
     const int lane = threadIdx.x & 31;
@@ -99,7 +104,7 @@ __global__ void __launch_bounds__(128, MODE == 4 ? 6 : (sizeof(T) == 4 ? 4 : 3))
     unsigned char *wsm = dsm + (size_t)(threadIdx.x >> 5) * A.warp_smem;
     uint32_t ph = 0;
     uint64_t *bars = reinterpret_cast<uint64_t *>(wsm + A.warp_smem - 48);
-    if constexpr (MODE == 2 || MODE == 3 || MODE == 4) {
+    if constexpr (MODE == 2 || MODE == 3 || MODE == 4 || MODE == 6) {
         if (lane == 0) {
             for (int b = 0; b < 6; ++b) mbar_init(&bars[b], 1);
             fence_proxy_async_shared();
@@ -181,6 +186,8 @@ cudaError_t launch_one(const SweepArgs<T> &A, const BspArgs &S, int grid, int bl
 template <> const void *bsp_kernel_fn<float>(int mode)
 {
     switch (mode) {
+    case 6: return (const void *)bsp_sweep_kernel<float, 6>;
+    case 5: return (const void *)bsp_sweep_kernel<float, 5>;
     case 4: return (const void *)bsp_sweep_kernel<float, 4>;
     case 3: return (const void *)bsp_sweep_kernel<float, 3>;
     case 2: return (const void *)bsp_sweep_kernel<float, 2>;
@@ -192,6 +199,7 @@ template <> const void *bsp_kernel_fn<float>(int mode)
 template <> const void *bsp_kernel_fn<double>(int mode)
 {
     switch (mode) {
+    case 5: return (const void *)bsp_sweep_kernel<double, 5>;
     case 2: return (const void *)bsp_sweep_kernel<double, 2>;
     case 1: return (const void *)bsp_sweep_kernel<double, 1>;
     default: return (const void *)bsp_sweep_kernel<double, 0>;
@@ -203,6 +211,8 @@ cudaError_t launch_bsp<float>(const SweepArgs<float> &A, const BspArgs &S, int m
                               bool cooperative, cudaStream_t st)
 {
     switch (mode) {
+    case 6: return launch_one<float, 6>(A, S, grid, block, dyn, cooperative, st);
+    case 5: return launch_one<float, 5>(A, S, grid, block, dyn, cooperative, st);
     case 4: return launch_one<float, 4>(A, S, grid, block, dyn, cooperative, st);
     case 3: return launch_one<float, 3>(A, S, grid, block, dyn, cooperative, st);
     case 2: return launch_one<float, 2>(A, S, grid, block, dyn, cooperative, st);
@@ -216,6 +226,7 @@ cudaError_t launch_bsp<double>(const SweepArgs<double> &A, const BspArgs &S, int
                                size_t dyn, bool cooperative, cudaStream_t st)
 {
     switch (mode) {
+    case 5: return launch_one<double, 5>(A, S, grid, block, dyn, cooperative, st);
     case 2: return launch_one<double, 2>(A, S, grid, block, dyn, cooperative, st);
     case 1: return launch_one<double, 1>(A, S, grid, block, dyn, cooperative, st);
     default: return launch_one<double, 0>(A, S, grid, block, dyn, cooperative, st);

@@ -102,11 +102,29 @@ def test_host_buffers_and_aliasing():
     assert _rel(buf.cpu().numpy(), ref) < 1e-11
 
 
+@pytest.mark.parametrize("schedule", [tf.TF_SCHED_BSP, tf.TF_SCHED_BSP_LAUNCH])
+@pytest.mark.parametrize("precision,G", [(tf.TF_FP64, 5), (tf.TF_FP32, 5), (tf.TF_FP32, 32)])
+def test_bulk_synchronous_schedules_same_result(schedule, precision, G):
+    """The level-synchronous schedules with the second-order element: bit-identical to
+    the many-task schedule, within tolerance of the oracle."""
+    cfg = _box(n=4, G=G)
+    P = o2.Problem2(cfg)
+    phi_in = np.random.default_rng(8).uniform(0.0, 1.0, (P.C, G, 10))
+    ref = P.transport_step(phi_in, threads=8)
+    a = tf.Problem.from_config(cfg, precision=precision, order=2)
+    b = tf.Problem.from_config(cfg, precision=precision, order=2, schedule=schedule)
+    out_a, out_b = torch.zeros_like(_dev(phi_in)), torch.zeros_like(_dev(phi_in))
+    a.sweep(_dev(phi_in), out_a)
+    b.sweep(_dev(phi_in), out_b)
+    assert torch.equal(out_a, out_b)
+    assert _rel(out_b.cpu().numpy(), ref) < TOL[precision]
+    st = b.stats()
+    assert st["tasks_executed"] == st["n_tasks"] and st["n_buckets"] > 0
+    assert st["kernel_mode"] == a.stats()["kernel_mode"]
+
+
 def test_second_order_rejections():
     cfg = _box(n=2, G=2)
-    with pytest.raises(tf.TfError) as e:
-        tf.Problem.from_config(cfg, order=2, schedule=tf.TF_SCHED_BSP)
-    assert e.value.status == tf.TF_ERR_ARG
     with pytest.raises(tf.TfError) as e:
         tf.Problem.from_config(cfg, order=2, psi_inflow=np.ones((cfg["xyz"].shape[0], 2)))
     assert e.value.status == tf.TF_ERR_ARG
