@@ -554,6 +554,7 @@ def run_batch(args):
             "all_converged": st == tf.TF_OK,
             "per_problem": [{"cells": p.n_cells, "directions": p.n_dirs, "groups": p.n_groups,
                              "cells_per_task": p.stats()["cells_per_task"], "kernel_mode": p.stats()["kernel_mode"],
+                             "octant_window": p.stats()["tuned_window"] or 8,
                              "iterations": i["iterations"], "seconds_to_tol": round(i["seconds"], 4),
                              "converged": i["converged"], "balance": i["balance"]} for p, i in zip(probs, infos)]}
     print(json.dumps(line), flush=True)

@@ -89,8 +89,10 @@ typedef struct {
                               * a quarter of that, at least 2, with a bulk-synchronous schedule),
                               * -1 = autotuned for use on its own (wall time of trial sweeps over a
                               * direction sample), -2 = autotuned for batched use (busy time of the
-                              * warps); choices cached per (precision, schedule, groups, directions,
-                              * log2 cells) */
+                              * warps); the tuner then also tries, at the chosen grain, the other
+                              * groups-per-lane variant (pairing), registers instead of staging and an
+                              * octant window of 2, for each of those options left at 0; choices cached
+                              * per (precision, order, schedule, groups, directions, log2 cells) */
     int32_t dir_chunk;       /* directions swept per persistent launch; 0 = as many as the memory budget allows */
     int32_t warps_per_cta;   /* persistent kernel CTA size in warps; 0 = automatic */
     int32_t ctas_per_sm;     /* persistent CTAs per SM; 0 = as many as are resident */
@@ -180,7 +182,10 @@ typedef struct {
     double tuned_seconds[8];
     int32_t n_buckets;          /* bulk-synchronous schedules: (octant, t-level) buckets per sweep,
                                  * summed over direction chunks (barriers + chunks); 0 for TF_SCHED_AMT */
-    int32_t reserved_i[4];
+    /* autotuning: the kernel-variant knobs in use after it (tf_options.pairing, staging,
+     * octant_window; 0 = automatic), tuned after the grain where the caller left them automatic */
+    int32_t tuned_pairing, tuned_staging, tuned_window;
+    int32_t reserved_i[1];
     double data_wait_seconds;  /* summed over warps: time waiting for rows staged by bulk copies
                                 * (SM cycles at the nominal SM clock) */
     double reserved_d[5];

@@ -194,6 +194,10 @@ tf_status tf_problem_create(tf_handle mesh, tf_handle quad, int32_t n_groups, in
             release(p);
             return st;
         }
+        // the tuned kernel-variant knobs (unchanged where the caller set them)
+        p->opt.pairing = p->tune.pairing;
+        p->opt.staging = p->tune.staging;
+        p->opt.octant_window = p->tune.window;
     }
     if (B == 0) {
         // about 1024 units per task (at most 64 cells); 256 units and 4 to 16 cells on the
@@ -311,6 +315,9 @@ tf_status tf_problem_stats(tf_handle problem, tf_stats *out)
     *out = p->stats;
     out->tuned_n = p->tune.n_candidates;
     out->tuned_cached = p->tune.cached;
+    out->tuned_pairing = p->tune.pairing;
+    out->tuned_staging = p->tune.staging;
+    out->tuned_window = p->tune.window;
     for (int k = 0; k < 8; ++k) {
         out->tuned_candidates[k] = p->tune.candidates[k];
         out->tuned_seconds[k] = p->tune.seconds[k];

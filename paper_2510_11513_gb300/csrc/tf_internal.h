@@ -79,6 +79,8 @@ struct tf_autotune_report {
     int32_t n_candidates = 0, chosen = 0, cached = 0, sample_directions = 0;
     int32_t candidates[8] = {0};
     double seconds[8] = {0};
+    // kernel-variant knobs tuned after the grain (only those the caller left automatic)
+    int32_t pairing = 0, staging = 0, window = 0, n_variants = 0;
 };
 
 struct Problem : Object {
@@ -95,7 +97,9 @@ struct Problem : Object {
     tf_autotune_report tune;
 };
 
-// Picks cells_per_task by timed trial sweeps over a direction sample (autotune.cpp).
+// Picks cells_per_task, then the kernel variant (groups per lane: pairing; shared-memory
+// staging) and the octant window, by timed trial sweeps over a direction sample
+// (autotune.cpp); the chosen knobs are returned in *rep and written to *opt_out.
 tf_status autotune_cells_per_task(const Mesh &m, const Quad &q, int32_t G, int32_t M, const int32_t *cell_material,
                                   const double *sigma_t, const double *sigma_s, const double *Q, const tf_options &opt,
                                   int32_t *out, tf_autotune_report *rep);

@@ -68,7 +68,8 @@ class tf_stats(C.Structure):
         ("cum_sweep_event_seconds", C.c_double), ("cum_phi_event_seconds", C.c_double), ("cum_steps", C.c_int64),
         ("launches_per_step", C.c_int64), ("kernel_mode", C.c_int32), ("tuned_n", C.c_int32),
         ("tuned_cached", C.c_int32), ("tuned_candidates", C.c_int32 * 8), ("tuned_seconds", C.c_double * 8),
-        ("n_buckets", C.c_int32), ("reserved_i", C.c_int32 * 4), ("data_wait_seconds", C.c_double),
+        ("n_buckets", C.c_int32), ("tuned_pairing", C.c_int32), ("tuned_staging", C.c_int32),
+        ("tuned_window", C.c_int32), ("reserved_i", C.c_int32 * 1), ("data_wait_seconds", C.c_double),
         ("reserved_d", C.c_double * 5),
     ]
 

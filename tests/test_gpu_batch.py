@@ -82,6 +82,12 @@ def test_autotuned_task_grain():
     assert st["cells_per_task"] in st["tuned_candidates"]
     best = st["tuned_candidates"][int(np.argmin(st["tuned_seconds"]))]
     assert st["cells_per_task"] == best
+    # phase 2 (kernel variant, octant window) leaves valid knobs, and the problem runs with them
+    assert st["tuned_pairing"] in (0, 1, 2) and st["tuned_staging"] in (0, 1) and st["tuned_window"] in (0, 2)
+    if st["tuned_pairing"] == 1:
+        assert st["kernel_mode"] != 3
+    if st["tuned_pairing"] == 0:
+        assert st["kernel_mode"] == 3  # 16 groups: packed pairs unless turned off
     rng = np.random.default_rng(1)
     x = rng.uniform(0, 1, (p.n_cells, 16, 4))
     out = torch.zeros((p.n_cells, 16, 4), dtype=torch.float64, device="cuda")
