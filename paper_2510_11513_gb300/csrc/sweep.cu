@@ -144,11 +144,8 @@ __device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float p, float
     lo += err + e;
 }
 
-// Boundary leakage of one cell and group for the particle balance: for each
-// boundary face f (sorted face f is opposite sorted node f) and direction a,
-// w_a s_f mean_f(psi_a) on an outflow face (s_f = Omega_a . N_f, not below the
-// inflow threshold -1e-12 |N_f| of the sweep graph) and -w_a |s_f| mean_f(psi_in)
-// on an inflow face with prescribed inflow (vacuum: nothing).  FP64 sums.
+// psi layout [Dc][C][G] of V4 rows in sorted node order; the result is written
+// (or added, for direction chunks after the first) in the caller's node order.
 template <class T, bool PAIR>
 __global__ void __launch_bounds__(256) phi_kernel(const V4<T> *__restrict__ psi, const WeightPair *__restrict__ wts,
                                                   int Dc, size_t CG, int G, const CellGeo<T> *__restrict__ geo,
