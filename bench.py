@@ -417,7 +417,12 @@ def run_ours(args):
                            "wait_frac": st1["wait_seconds"] / max(st1["wait_seconds"] + st1["busy_seconds"], 1e-30),
                            "data_wait_frac": st1["data_wait_seconds"] / max(st1["busy_seconds"], 1e-30),
                            "n_chunks": st1["n_chunks"], "octant_window": args.octant_window or 8,
-                           "keep_ready": args.keep_ready or 1},
+                           "keep_ready": args.keep_ready or 1,
+                           # mean task time of the last sweep and the critical-path bound
+                           # (longest chain of t-levels x that time)
+                           "mean_task_us": st1["busy_seconds"] * 1e6 / max(1, st1["tasks_executed"]),
+                           "critical_path_ms": (st1["max_level"] + 1) * st1["busy_seconds"] * 1e3 /
+                           max(1, st1["tasks_executed"])},
             "gpu_launches": int((st1["launches_per_step"] + 2) * args.steps),
             "clocks": clk}
     if args.order == 2 and prec == tf.TF_FP32:
