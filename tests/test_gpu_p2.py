@@ -137,3 +137,17 @@ def test_second_order_rejections():
     with pytest.raises(tf.TfError) as e:
         tf.sweep_batch([a, b], phis, phis)
     assert e.value.status == tf.TF_ERR_ARG
+
+
+def test_autotuned_second_order():
+    """The autotuner on a second-order problem (grain, staging, octant window), then parity."""
+    cfg = _box(n=4, G=32, seed=9)
+    P = o2.Problem2(cfg)
+    prob = tf.Problem.from_config(cfg, precision=tf.TF_FP32, order=2, cells_per_task=-1)
+    st = prob.stats()
+    assert st["tuned_n"] >= 2 and st["cells_per_task"] in st["tuned_candidates"]
+    assert st["kernel_mode"] == (5 if st["tuned_staging"] == 1 else 6)
+    phi_in = np.random.default_rng(12).uniform(0.0, 1.0, (P.C, 32, 10))
+    out = torch.zeros_like(_dev(phi_in))
+    prob.sweep(_dev(phi_in), out)
+    assert _rel(out.cpu().numpy(), P.transport_step(phi_in, threads=8)) < 2e-5
