@@ -173,3 +173,33 @@ def test_second_order_element_tables_exact(tmp_path):
         assert list(got_fn[f]) == face_nodes(f)
         sub = F[f][np.ix_(face_nodes(f), face_nodes(f))]
         assert np.allclose(got_F, sub, rtol=0, atol=1e-16)
+
+
+def test_python_structs_match_the_c_header(tmp_path):
+    """The ctypes mirrors of tf_options, tf_iter_info and tf_stats have the size and the
+    field offsets the C compiler gives the header's structs (the C ABI the binding uses)."""
+    import ctypes
+    import subprocess
+
+    from paper_2510_11513_gb300 import tfsweep as T
+
+    structs = [("tf_options", T.tf_options), ("tf_iter_info", T.tf_iter_info), ("tf_stats", T.tf_stats)]
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "tfsweep.h"', "int main(void) {"]
+    for cname, py in structs:
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for fname, _ in py._fields_:
+            lines.append(f'  printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "abi.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "abi"
+    subprocess.check_call(["gcc", "-std=c11", f"-I{os.path.join(ROOT, 'include')}", str(src), "-o", str(exe)])
+    got = {}
+    for line in subprocess.check_output([str(exe)]).decode().splitlines():
+        a, b, c = line.split()
+        got[(a, b)] = int(c)
+    for cname, py in structs:
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for fname, _ in py._fields_:
+            assert got[(cname, fname)] == getattr(py, fname).offset, (cname, fname)
+
