@@ -82,9 +82,19 @@ def node_coordinates(xyz, tets):
 class Problem2:
     """One second-order transport problem on the oracle."""
 
+    NB = NB
+
+    @staticmethod
+    def _load(src):
+        return load(src)
+
+    def _fn(self, name):
+        return getattr(self.lib, "ora2_" + name)
+
     def __init__(self, cfg, omega=None, w=None, S1=None, psi_bc=None, src=None):
+        NB = self.NB
         self.lib1 = load1()
-        self.lib = load(src)
+        self.lib = self._load(src)
         self.cfg = cfg
         self.geom = geometry(cfg["xyz"], cfg["tets"], self.lib1)
         if omega is None:
@@ -100,14 +110,15 @@ class Problem2:
         self.sigma_s = np.ascontiguousarray(cfg["sigma_s"], dtype=np.float64)
         self.Q = np.ascontiguousarray(cfg["Q"], dtype=np.float64)
         if self.Q.shape != (self.C, self.G, NB):
-            raise ValueError("second-order Q must be [C][G][10]")
+            raise ValueError(f"Q must be [C][G][{NB}]")
         self.S1 = None if S1 is None else np.ascontiguousarray(S1, dtype=np.float64)
         self.psi_bc = None if psi_bc is None else np.ascontiguousarray(psi_bc, dtype=np.float64)
         g = self.geom
         self._s = _Problem2(self.C, self.G, self.D, _p(g["xyz"]), _p(g["tets"]), _p(g["vol"]), _p(g["grad"]),
                             _p(g["normal"]), _p(g["nbr"]), _p(self.omega), _p(self.w), _p(self.inflow),
                             _p(self.level), _p(self.material), _p(self.sigma_t), _p(self.S1), _p(self.psi_bc))
-        self.p_int = basis_integrals(self.lib)
+        self.p_int = np.zeros(NB)
+        _check(self._fn("basis_integrals")(_p(self.p_int)), "basis_integrals")
 
     def source(self, phi):
         """q = (Q + sum_g' sigma_s[g'->g] phi_g') / (4 pi) at the ten nodes."""
@@ -119,19 +130,19 @@ class Problem2:
         return q / FOUR_PI
 
     def sweep_direction(self, a, q):
-        psi = np.zeros((self.C, self.G, NB))
+        psi = np.zeros((self.C, self.G, self.NB))
         q = np.ascontiguousarray(q, dtype=np.float64)
-        _check(self.lib.ora2_sweep_direction(C.byref(self._s), int(a), _p(q), _p(psi)), "sweep_direction")
+        _check(self._fn("sweep_direction")(C.byref(self._s), int(a), _p(q), _p(psi)), "sweep_direction")
         return psi
 
     def sweep(self, q, dirs=None, threads=1, keep_psi=False):
         q = np.ascontiguousarray(q, dtype=np.float64)
         dirs = np.arange(self.D, dtype=np.int32) if dirs is None else np.ascontiguousarray(dirs, dtype=np.int32)
-        phi = np.zeros((self.C, self.G, NB))
-        psi = np.zeros((len(dirs), self.C, self.G, NB)) if keep_psi else None
+        phi = np.zeros((self.C, self.G, self.NB))
+        psi = np.zeros((len(dirs), self.C, self.G, self.NB)) if keep_psi else None
         used = C.c_int(0)
-        _check(self.lib.ora2_sweep(C.byref(self._s), _p(q), len(dirs), _p(dirs), _p(phi), _p(psi), int(threads),
-                                   C.byref(used)), "sweep")
+        _check(self._fn("sweep")(C.byref(self._s), _p(q), len(dirs), _p(dirs), _p(phi), _p(psi), int(threads),
+                                 C.byref(used)), "sweep")
         return phi, psi, used.value
 
     def transport_step(self, phi, threads=1):
@@ -154,7 +165,7 @@ class Problem2:
         return ig, float(ig.sum())
 
     def source_iterate(self, tol, max_iters, phi0=None, threads=1):
-        phi = np.zeros((self.C, self.G, NB)) if phi0 is None else np.array(phi0, dtype=np.float64)
+        phi = np.zeros((self.C, self.G, self.NB)) if phi0 is None else np.array(phi0, dtype=np.float64)
         r = np.inf
         it = 0
         for it in range(1, max_iters + 1):

@@ -43,15 +43,32 @@ def _add(p, q, s=1):
     return {e: c for e, c in out.items() if c != 0}
 
 
-def basis_polys():
-    """The ten basis functions as polynomials in (lambda_0..lambda_3)."""
-    one = {(0, 0, 0, 0): Fraction(1)}
-    lam = [{_mono(k): Fraction(1)} for k in range(4)]
+def node_alphas(order):
+    """Lattice multi-indices of the nodes, in the element's node order: vertices; per edge
+    (a,b) its interior nodes from a towards b; (third order) the face centres, face f opposite vertex f."""
     out = []
     for v in range(4):
-        out.append(_mul(lam[v], _add({e: 2 * c for e, c in lam[v].items()}, one, -1)))
+        out.append(tuple(order if k == v else 0 for k in range(4)))
     for a, b in EDGES:
-        out.append({e: 4 * c for e, c in _mul(lam[a], lam[b]).items()})
+        for t in range(order - 1, 0, -1):  # lambda_a = t / order
+            out.append(tuple(t if k == a else (order - t if k == b else 0) for k in range(4)))
+    if order == 3:
+        for f in range(4):
+            out.append(tuple(0 if k == f else 1 for k in range(4)))
+    return out
+
+
+def basis_polys(order=2):
+    """The Lagrange basis on the equispaced lattice as polynomials in (lambda_0..lambda_3):
+    phi_alpha = prod_k prod_{m < alpha_k} (order lambda_k - m) / (m + 1)."""
+    out = []
+    for al in node_alphas(order):
+        p = {(0, 0, 0, 0): Fraction(1)}
+        for k in range(4):
+            for m in range(al[k]):
+                fac = {_mono(k): Fraction(order, m + 1), (0, 0, 0, 0): Fraction(-m, m + 1)}
+                p = _mul(p, {e: c for e, c in fac.items() if c != 0})
+        out.append(p)
     return out
 
 
@@ -84,10 +101,10 @@ def integrate_face(p, f):
     return s
 
 
-def reference_tables():
+def reference_tables(order=2):
     """Exact per-unit-volume / per-unit-area tables: p[i] = int phi_i / V, M[i][j] = int phi_i phi_j / V,
     Dk[k][i][j] = int phi_i d phi_j / d lambda_k / V, F[f][i][j] = int_F phi_i phi_j / A (float arrays)."""
-    B = basis_polys()
+    B = basis_polys(order)
     p = np.array([float(integrate_cell(b)) for b in B])
     M = np.array([[float(integrate_cell(_mul(bi, bj))) for bj in B] for bi in B])
     Dk = np.array([[[float(integrate_cell(_mul(bi, dpoly(bj, k)))) for bj in B] for bi in B] for k in range(4)])
@@ -95,68 +112,86 @@ def reference_tables():
     return p, M, Dk, F
 
 
-_TABLES = None
+_TABLES = {}
 
 
-def tables():
-    global _TABLES
-    if _TABLES is None:
-        _TABLES = reference_tables()
-    return _TABLES
+def tables(order=2):
+    if order not in _TABLES:
+        _TABLES[order] = reference_tables(order)
+    return _TABLES[order]
 
 
-def face_nodes(f):
-    """Local node indices on the face opposite vertex f (3 vertices, 3 edges)."""
-    return [i for i in range(4) if i != f] + [4 + e for e, (a, b) in enumerate(EDGES) if f not in (a, b)]
+def face_nodes(f, order=2):
+    """Local node indices on the face opposite vertex f (the nodes whose lambda_f is zero)."""
+    return [i for i, al in enumerate(node_alphas(order)) if al[f] == 0]
 
 
-def global_node_keys(tets):
-    """Per cell, the global identity of each of its ten nodes: ('v', vertex) or ('e', lo, hi)."""
+def global_node_keys(tets, order=2):
+    """Per cell, the global identity of each node: the multiset of global vertices its
+    lattice multi-index weights (vertex -> ((v, order),); edge node -> ((va, ta), (vb, tb)); ...)."""
     keys = []
+    als = node_alphas(order)
     for t in np.asarray(tets):
-        k = [("v", int(t[i])) for i in range(4)]
-        k += [("e",) + tuple(sorted((int(t[a]), int(t[b])))) for a, b in EDGES]
-        keys.append(k)
+        keys.append([tuple(sorted((int(t[k]), al[k]) for k in range(4) if al[k])) for al in als])
     return keys
 
 
 # ------------------------------------------------------------ dense global system
-def dense_direction_solve(geom, omega_a, sigma_t_c, q, inflow_mask):
-    """Single direction, single group: assemble the global 10C x 10C upwind-DG
+def dense_direction_solve(geom, omega_a, sigma_t_c, q, inflow_mask, order=2):
+    """Single direction, single group: assemble the global (NB C) x (NB C) upwind-DG
     system with the exact tables and dict-based coupling, solve it densely.
-    sigma_t_c [C], q [C][10] (per steradian), inflow_mask [C]; vacuum boundary."""
-    p, M, Dk, F = tables()
+    sigma_t_c [C], q [C][NB] (per steradian), inflow_mask [C]; vacuum boundary."""
+    p, M, Dk, F = tables(order)
+    nb = M.shape[0]
     tets = geom["tets"]
     Cn = tets.shape[0]
-    keys = global_node_keys(tets)
+    keys = global_node_keys(tets, order)
     where = {}
     for c in range(Cn):
         for i, k in enumerate(keys[c]):
             where.setdefault(k, []).append((c, i))
-    A = np.zeros((10 * Cn, 10 * Cn))
-    b = np.zeros(10 * Cn)
+    A = np.zeros((nb * Cn, nb * Cn))
+    b = np.zeros(nb * Cn)
     for c in range(Cn):
         V = geom["vol"][c]
         og = geom["grad"][c] @ omega_a
         K = V * np.einsum("k,kij->ij", og, Dk)
-        A[10 * c:10 * c + 10, 10 * c:10 * c + 10] += K + sigma_t_c[c] * V * M
-        b[10 * c:10 * c + 10] += V * M @ q[c]
+        rc = slice(nb * c, nb * c + nb)
+        A[rc, rc] += K + sigma_t_c[c] * V * M
+        b[rc] += V * M @ q[c]
         for f in range(4):
             if not (inflow_mask[c] >> f) & 1:
                 continue
             s = abs(float(geom["normal"][c, f] @ omega_a))
             Ff = s * F[f]
-            A[10 * c:10 * c + 10, 10 * c:10 * c + 10] += Ff
+            A[rc, rc] += Ff
             n = int(geom["nbr"][c, f])
             if n < 0:
                 continue
-            for j in face_nodes(f):
+            for j in face_nodes(f, order):
                 (nj,) = [i for (cc, i) in where[keys[c][j]] if cc == n]
-                A[10 * c:10 * c + 10, 10 * n + nj] -= Ff[:, j]
-    return np.linalg.solve(A, b).reshape(Cn, 10)
+                A[rc, nb * n + nj] -= Ff[:, j]
+    return np.linalg.solve(A, b).reshape(Cn, nb)
 
 
 # ------------------------------------------------------------ manufactured solution
+def cubic_field(rng, G):
+    """psi_g(x) = quadratic part + sum_d c_gd x_d^3 + e_g x y z per group; (value, gradient) callables."""
+    val2, grad2 = quadratic_field(rng, G)
+    c3 = rng.uniform(-0.3, 0.3, (G, 3))
+    e3 = rng.uniform(-0.3, 0.3, G)
+
+    def value(x):
+        return val2(x) + np.einsum("...d,gd->...g", x ** 3, c3) + e3 * (x[..., 0] * x[..., 1] * x[..., 2])[..., None]
+
+    def gradient(x):
+        g = grad2(x) + 3.0 * np.einsum("...d,gd->...gd", x ** 2, c3)
+        xyz = np.stack([x[..., 1] * x[..., 2], x[..., 0] * x[..., 2], x[..., 0] * x[..., 1]], axis=-1)
+        return g + e3[:, None] * xyz[..., None, :]
+
+    return value, gradient
+
+
 def quadratic_field(rng, G):
     """psi_g(x) = a_g + b_g . x + x^T S_g x per group (S symmetric); returns (value, gradient) callables."""
     a = rng.uniform(0.5, 1.5, G)
@@ -173,12 +208,13 @@ def quadratic_field(rng, G):
     return value, gradient
 
 
-def mms_inputs(cfg, node_xyz, rng):
-    """Q, S1, psi_bc and the exact nodal psi [C][G][10] of a quadratic manufactured solution
-    (direction independent, so phi = 4 pi psi): Q = 4 pi (sigma_t psi - sum_g' sigma_s[g'->g] psi_g'),
-    S1 = grad psi (the streaming term Omega . grad psi enters as the source Omega . S1)."""
+def mms_inputs(cfg, node_xyz, rng, field=None):
+    """Q, S1, psi_bc and the exact nodal psi [C][G][nodes] of a manufactured solution (quadratic
+    unless `field` is given; direction independent, so phi = 4 pi psi):
+    Q = 4 pi (sigma_t psi - sum_g' sigma_s[g'->g] psi_g'), S1 = grad psi (the streaming term
+    Omega . grad psi enters as the source Omega . S1)."""
     G = int(cfg["n_groups"])
-    value, gradient = quadratic_field(rng, G)
+    value, gradient = (field or quadratic_field)(rng, G)
     psi = value(node_xyz).transpose(0, 2, 1)  # [C][G][10]
     S1 = gradient(node_xyz).transpose(0, 2, 1, 3)  # [C][G][10][3]
     mat = np.asarray(cfg["cell_material"])

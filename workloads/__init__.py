@@ -284,6 +284,25 @@ def order2(cfg):
     return out
 
 
+def order3(cfg):
+    """The same problem for the third-order (twenty-node) element: Q at the vertices,
+    at the two nodes of each edge (0,1) (0,2) (0,3) (1,2) (1,3) (2,3) (at 1/3 and 2/3
+    from the edge's first vertex) and at the four face centres, each the value of the
+    cell's linear field through its four vertex values."""
+    Q = np.asarray(cfg["Q"], dtype=np.float64)
+    bary = [tuple(1.0 if k == v else 0.0 for k in range(4)) for v in range(4)]
+    for a, b in ((0, 1), (0, 2), (0, 3), (1, 2), (1, 3), (2, 3)):
+        for t in (2.0 / 3.0, 1.0 / 3.0):
+            bary.append(tuple(t if k == a else (1.0 - t if k == b else 0.0) for k in range(4)))
+    for f in range(4):
+        bary.append(tuple(0.0 if k == f else 1.0 / 3.0 for k in range(4)))
+    out = dict(cfg)
+    out["Q"] = np.einsum("cgk,ik->cgi", Q, np.array(bary))
+    out["order"] = 3
+    out["name"] = cfg.get("name", "") + "_P3"
+    return out
+
+
 CONFIGS = {
     "small_box": small_box,
     "two_material": two_material_box,
