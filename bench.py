@@ -169,12 +169,16 @@ def cpu_oracle_sample(cfg, n_dirs=None, threads=None):
     om, w = oracle.product_quadrature(cfg["n_polar"], cfg["n_azimuthal"])
     D = om.shape[0]
     idx = np.linspace(0, D - 1, n_dirs).round().astype(int)
-    if cfg.get("order", 1) == 2:
+    order = cfg.get("order", 1)
+    if order == 2:
         from oracle import p2 as o2
         P = o2.Problem2(cfg, omega=om[idx], w=w[idx])
+    elif order == 3:
+        from oracle import p3 as o3
+        P = o3.Problem3(cfg, omega=om[idx], w=w[idx])
     else:
         P = oracle.Problem(cfg, omega=om[idx], w=w[idx])
-    nodes = 10 if cfg.get("order", 1) == 2 else 4
+    nodes = {2: 10, 3: 20}.get(order, 4)
     phi = np.random.default_rng(0).uniform(0.0, 1.0, (P.C, P.G, nodes))
     t0 = time.perf_counter()
     q = P.source(phi)
@@ -205,8 +209,8 @@ def run_reference(args):
     if rank != 0:
         return
     cfg = make_config(args)
-    if args.order == 2:
-        cfg = W.order2(cfg)
+    if args.order >= 2:
+        cfg = (W.order2 if args.order == 2 else W.order3)(cfg)
     threads = os.cpu_count() or 1
     # warm-up steps (untimed), then timed steps; each step is a bounded sample
     for _ in range(args.warmup):
@@ -281,15 +285,19 @@ def schedule_ablation(tf, cfg, prec, local, stream, steps, torch, amt=None):
 FP32_ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
 
-def p2_flops_per_unit(prob, tf):
-    """Algorithmic flops of one second-order unit (an FMA counts 2): streaming matrix 160,
-    A = V (sigma_t M + K) 300, b = V M q 210, the 10 x 10 elimination and back substitution
-    815, and 156 per interior inflow face (face matrix into A, face term into b); the mean
-    number of interior inflow faces per (cell, direction) comes from the sweep graph."""
+def p2_flops_per_unit(prob, tf, order=2):
+    """Algorithmic flops of one higher-order unit (an FMA counts 2).  Second order: streaming
+    matrix 160, A = V (sigma_t M + K) 300, b = V M q 210, the 10 x 10 elimination and back
+    substitution 815, 156 per interior inflow face (face matrix into A, face term into b).
+    Third order: A = V (sigma_t M + sum_k w_k C_k) 4,400, b = V M q 800, the 20 x 20
+    elimination and back substitution 5,910, 420 per interior inflow face.  The mean number
+    of interior inflow faces per (cell, direction) comes from the sweep graph."""
     inflow, _ = tf.tf_graph_levels(prob.mesh.h, prob.quad.h, prob.n_cells, prob.n_dirs)
     nbr = prob.mesh.geometry()["nbr"]
     interior = (nbr >= 0).astype(np.uint8)  # [C][4]
     n_in = sum(float((((inflow >> f) & 1) * interior[None, :, f]).mean()) for f in range(4))
+    if order == 3:
+        return 11110.0 + 420.0 * n_in, n_in
     return 1485.0 + 156.0 * n_in, n_in
 
 
@@ -342,8 +350,8 @@ def run_ours(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     cfg = make_config(args)
-    if args.order == 2:
-        cfg = W.order2(cfg)
+    if args.order >= 2:
+        cfg = (W.order2 if args.order == 2 else W.order3)(cfg)
     prec = tf.TF_FP64 if args.precision == "fp64" else tf.TF_FP32
     t_setup = time.perf_counter()
     prob = tf.Problem.from_config(cfg, precision=prec, device=local, cells_per_task=args.cells_per_task,
@@ -388,8 +396,8 @@ def run_ours(args):
     # cell record + cell-list entry once per (cell, direction), amortised over G
     geo = 128 if prec == tf.TF_FP32 else 256
     b_unit = 8 * s + (geo + 4) / G
-    if args.order == 2:  # source row and psi row of ten nodes, 144-byte record + list entry per (cell, direction)
-        b_unit = 20 * s + (144 + 4) / G
+    if args.order >= 2:  # source and psi rows of NB nodes, the cell record + list entry per (cell, direction)
+        b_unit = 2 * nodes * s + ((144 if args.order == 2 else 160) + 4) / G
     peak, peak_kind = _peaks()
     achieved = b_unit * units / sweep_s / 1e9
     klabel = ("sweep_kernel" if args.schedule == "amt" else "bsp_sweep_kernel") + \
@@ -425,9 +433,9 @@ def run_ours(args):
                            max(1, st1["tasks_executed"])},
             "gpu_launches": int((st1["launches_per_step"] + 2) * args.steps),
             "clocks": clk}
-    if args.order == 2 and prec == tf.TF_FP32:
-        # the second-order kernel is bound by FP32 arithmetic, not by HBM
-        flops, n_in = p2_flops_per_unit(prob, tf)
+    if args.order >= 2 and prec == tf.TF_FP32:
+        # the higher-order kernels are bound by FP32 arithmetic, not by HBM
+        flops, n_in = p2_flops_per_unit(prob, tf, args.order)
         ach = flops * units / sweep_s / 1e12
         line["roofline"] = {"bound": "alu", "achieved": ach, "peak": FP32_ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
                             "frac": ach / FP32_ALU_PEAK_TFLOPS,
@@ -664,8 +672,8 @@ def main():
                     help="task schedule of the timed sweep: many-task (amt) or bulk-synchronous")
     ap.add_argument("--no-bsp-compare", action="store_true", help="skip the many-task vs bulk-synchronous legs")
     ap.add_argument("--no-second-order", action="store_true", help="skip the second-order element leg")
-    ap.add_argument("--order", type=int, default=1, choices=[1, 2],
-                    help="finite-element order of the timed sweep (2: the ten-node element)")
+    ap.add_argument("--order", type=int, default=1, choices=[1, 2, 3],
+                    help="finite-element order of the timed sweep (2: ten nodes, 3: twenty nodes)")
     ap.add_argument("--bsp-steps", type=int, default=2, help="timed steps of each schedule in the comparison")
     ap.add_argument("--octant-window", type=int, default=0, help="octants active at once (0 = library default)")
     ap.add_argument("--keep-ready", type=int, default=0, help="ready tasks a warp keeps and runs next (0 = library default)")

@@ -116,8 +116,11 @@ typedef struct {
     int32_t schedule;        /* tf_schedule: how the sweep orders its tasks (default TF_SCHED_AMT) */
     int32_t order;           /* finite-element order: 0 or 1 = linear (4 nodes per cell), 2 = quadratic
                               * (10 nodes: the 4 vertices, then the midpoints of the local edges (0,1) (0,2)
-                              * (0,3) (1,2) (1,3) (2,3)); Q and every phi buffer are [n_cells][n_groups][nodes].
-                              * Order 2: vacuum boundaries and no S1 (both NULL), no batching */
+                              * (0,3) (1,2) (1,3) (2,3)), 3 = cubic (20 nodes: the vertices, two per edge in
+                              * that edge order, first at (2/3, 1/3) along the edge, then the centres of the
+                              * faces opposite vertices 0..3); Q and every phi buffer are
+                              * [n_cells][n_groups][nodes].  Orders 2 and 3: vacuum boundaries and no S1
+                              * (both NULL), no batching */
     int32_t keep_ready;      /* ready tasks a warp keeps on a private stack and runs next (most recent
                               * first) instead of queueing them; 0 = automatic (1), at most 4 */
     int32_t reserved_i[1];

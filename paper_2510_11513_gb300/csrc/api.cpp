@@ -171,10 +171,10 @@ tf_status tf_problem_create(tf_handle mesh, tf_handle quad, int32_t n_groups, in
         return fail(TF_ERR_ARG, "tf_problem_create: schedule must be a tf_schedule (inject_stall: not with "
                                 "TF_SCHED_BSP_LAUNCH, which has no device wait)");
     }
-    if (p->opt.order < 0 || p->opt.order > 2 ||
-        (p->opt.order == 2 && (S1 || psi_inflow))) {
+    if (p->opt.order < 0 || p->opt.order > 3 ||
+        (p->opt.order >= 2 && (S1 || psi_inflow))) {
         delete p;
-        return fail(TF_ERR_ARG, "tf_problem_create: order must be 0, 1 or 2 (order 2: S1 and psi_inflow NULL)");
+        return fail(TF_ERR_ARG, "tf_problem_create: order must be 0 to 3 (orders 2 and 3: S1 and psi_inflow NULL)");
     }
     if (!(p->opt.wait_limit_s > 0.0)) p->opt.wait_limit_s = 10.0;
     if (!(p->opt.residual_floor > 0.0) || p->opt.residual_floor > 1.0) p->opt.residual_floor = 1.0;
@@ -207,6 +207,8 @@ tf_status tf_problem_create(tf_handle mesh, tf_handle quad, int32_t n_groups, in
         B = paired ? std::max(4, std::min(16, 256 / n_groups)) : std::max(2, std::min(64, 1024 / n_groups));
         // second order: a unit is a 10 x 10 solve, about 256 units per task
         if (p->opt.order == 2) B = std::max(2, std::min(32, 256 / n_groups));
+        // third order: a unit is a 20 x 20 solve, about 64 units per task
+        if (p->opt.order == 3) B = std::max(2, std::min(16, 64 / n_groups));
         // Bulk-synchronous schedules: a bucket's tasks must cover the resident warps, and
         // most buckets hold fewer cells than the many-task grain assumes; a quarter of it
         // (at least 2 cells) took the least time over grains 1..64 on the 16^3-hex,

@@ -72,7 +72,7 @@ tf_status autotune_cells_per_task(const Mesh &m, const Quad &q, int32_t G, int32
     for (int32_t b : {2, 4, 8, 16, 32, 64})
         if ((b > 2 || opt.schedule != TF_SCHED_AMT) && b <= cap && (int64_t)b * G <= 4096) cand.push_back(b);
     if (cand.empty()) cand.push_back(std::max(2, std::min(cap, 1024 / G)));
-    const int nb = order1 ? 4 : 10;
+    const int nb = order1 ? 4 : (opt.order == 3 ? 20 : 10);
     std::vector<double> phi((size_t)m.nc * G * nb, 1.0);
     double *dphi = nullptr;
     if (cudaMalloc(&dphi, phi.size() * 8) != cudaSuccess) {
@@ -133,7 +133,8 @@ tf_status autotune_cells_per_task(const Mesh &m, const Quad &q, int32_t G, int32
     std::vector<Choice> vars;
     if (opt.pairing == 0 && order1 && fp32 && G % 2 == 0 && best.cells <= 32)
         vars.push_back({best.cells, G % 32 == 0 ? 2 : 1, best.staging, best.window});
-    if (opt.staging == 0 && G % 32 == 0 && (order1 || fp32)) vars.push_back({best.cells, best.pairing, 1, best.window});
+    if (opt.staging == 0 && G % 32 == 0 && (order1 || (fp32 && opt.order == 2)))
+        vars.push_back({best.cells, best.pairing, 1, best.window});
     if (opt.octant_window == 0 && opt.schedule == TF_SCHED_AMT) vars.push_back({best.cells, best.pairing, best.staging, 2});
     int nvar = 0;
     for (const Choice &v : vars) {

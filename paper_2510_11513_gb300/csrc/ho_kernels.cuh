@@ -1,44 +1,53 @@
-// Per-iteration kernels of the second-order (ten-node) element: source update,
-// phi reduction, boundary leakage, FP64 statistics and stopping test, psi
-// inspection.  Included by sweep.cu inside namespace tf, after the linear
-// element's kernels (it uses WeightPair, two_sum_acc, BalIn, record_balance).
+// Per-iteration kernels of the higher-order elements (NB = 10 nodes: quadratic,
+// NB = 20: cubic): source update, phi reduction, boundary leakage, FP64 statistics
+// and stopping test, psi inspection.  Included by sweep.cu inside namespace tf,
+// after the linear element's kernels (it uses WeightPair, two_sum_acc, BalIn,
+// record_balance, kFourPi).
 //
-// Layouts: caller phi and Q [C][G][10] (FP64); device Q, q [C][10][G] and psi
-// [Dc][C][10][G] in the sweep precision (node-major, so that lanes over groups
-// read and write whole lines).
+// Layouts: caller phi and Q [C][G][NB] (FP64); device Q, q [C][NB][G] and psi
+// [Dc][C][NB][G] in the sweep precision (node-major, so that lanes over groups read
+// and write whole lines).  Element tables (exact, per order): pw[i] = int phi_i / V;
+// for the face opposite vertex f its NF nodes fn[f][.] and fav[.] = int_f phi / A
+// (the same in every face's node order).
 #pragma once
+
+struct HoTables {
+    const double *pw;      // [NB]
+    const int32_t *fn;     // [4][NF]
+    const double *fav;     // [NF]
+};
 
 // q[c][i][g] = (Q[c][i][g] + sum_h sigma_s[m][h][g] phi[c][h][i]) / 4 pi.  One CTA
 // stages the scalar flux of a few cells (in the sweep precision) in shared memory.
-template <class T>
-__global__ void __launch_bounds__(256) source_p2_kernel(const double *__restrict__ phi, const T *__restrict__ Qext,
+template <class T, int NB>
+__global__ void __launch_bounds__(256) source_ho_kernel(const double *__restrict__ phi, const T *__restrict__ Qext,
                                                         const T *__restrict__ sigma_s, const int32_t *__restrict__ mat,
                                                         T *__restrict__ q, int64_t C, int G, int cells_per_cta)
 {
     extern __shared__ unsigned char smem_raw[];
-    T *ph = reinterpret_cast<T *>(smem_raw);  // [cells_per_cta][G][10]
+    T *ph = reinterpret_cast<T *>(smem_raw);  // [cells_per_cta][G][NB]
     const T inv4pi = T(1.0 / (4.0 * 3.14159265358979323846));
     for (int64_t c0 = (int64_t)blockIdx.x * cells_per_cta; c0 < C; c0 += (int64_t)gridDim.x * cells_per_cta) {
         const int nc = (int)((C - c0) < (int64_t)cells_per_cta ? (C - c0) : (int64_t)cells_per_cta);
         __syncthreads();
-        for (int e = threadIdx.x; e < nc * G * 10; e += blockDim.x) ph[e] = (T)phi[(size_t)c0 * G * 10 + e];
+        for (int e = threadIdx.x; e < nc * G * NB; e += blockDim.x) ph[e] = (T)phi[(size_t)c0 * G * NB + e];
         __syncthreads();
         for (int u = threadIdx.x; u < nc * G; u += blockDim.x) {
             const int lc = u / G, g = u - lc * G;
             const int64_t c = c0 + lc;
             const T *S = sigma_s + (size_t)__ldg(mat + c) * G * G + g;
-            const T *p = ph + (size_t)lc * G * 10;
-            T a[10];
+            const T *p = ph + (size_t)lc * G * NB;
+            T a[NB];
 #pragma unroll
-            for (int i = 0; i < 10; ++i) a[i] = T(0);
+            for (int i = 0; i < NB; ++i) a[i] = T(0);
             for (int h = 0; h < G; ++h) {
                 const T s = __ldg(S + (size_t)h * G);
 #pragma unroll
-                for (int i = 0; i < 10; ++i) a[i] += s * p[10 * h + i];
+                for (int i = 0; i < NB; ++i) a[i] += s * p[NB * h + i];
             }
 #pragma unroll
-            for (int i = 0; i < 10; ++i) {
-                const size_t at = ((size_t)c * 10 + i) * G + g;
+            for (int i = 0; i < NB; ++i) {
+                const size_t at = ((size_t)c * NB + i) * G + g;
                 q[at] = (__ldg(Qext + at) + a[i]) * inv4pi;
             }
         }
@@ -48,25 +57,25 @@ __global__ void __launch_bounds__(256) source_p2_kernel(const double *__restrict
 // phi[c][g][i] (+)= sum over the chunk's directions of w_a psi_a[c][i][g] (Eq. (2)).
 // Thread per (cell, group); FP32 psi with PAIR: exact float-pair products and sums
 // (as the linear element's phi_kernel), rounded once to FP64.
-template <class T, bool PAIR>
-__global__ void __launch_bounds__(256) phi_p2_kernel(const T *__restrict__ psi, const WeightPair *__restrict__ wts,
+template <class T, bool PAIR, int NB>
+__global__ void __launch_bounds__(256) phi_ho_kernel(const T *__restrict__ psi, const WeightPair *__restrict__ wts,
                                                      int Dc, int64_t C, int G, double *__restrict__ phi, int accumulate)
 {
     const size_t CG = (size_t)C * G;
     for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < CG; idx += (size_t)gridDim.x * blockDim.x) {
         const size_t c = idx / (size_t)G;
         const int g = (int)(idx - c * (size_t)G);
-        const T *src = psi + c * 10 * (size_t)G + g;
-        double r[10];
+        const T *src = psi + c * NB * (size_t)G + g;
+        double r[NB];
         if constexpr (PAIR) {
-            float hi[10], lo[10];
+            float hi[NB], lo[NB];
 #pragma unroll
-            for (int i = 0; i < 10; ++i) hi[i] = lo[i] = 0.f;
+            for (int i = 0; i < NB; ++i) hi[i] = lo[i] = 0.f;
             for (int a = 0; a < Dc; ++a) {
-                const T *s = src + (size_t)a * CG * 10;
+                const T *s = src + (size_t)a * CG * NB;
                 const WeightPair w = wts[a];
 #pragma unroll
-                for (int i = 0; i < 10; ++i) {
+                for (int i = 0; i < NB; ++i) {
                     const float x = __ldcs(s + (size_t)i * G);
                     const float pp = w.hi * x;
                     const float e = fmaf(w.hi, x, -pp) + w.lo * x;
@@ -74,39 +83,38 @@ __global__ void __launch_bounds__(256) phi_p2_kernel(const T *__restrict__ psi, 
                 }
             }
 #pragma unroll
-            for (int i = 0; i < 10; ++i) r[i] = (double)hi[i] + (double)lo[i];
+            for (int i = 0; i < NB; ++i) r[i] = (double)hi[i] + (double)lo[i];
         } else {
 #pragma unroll
-            for (int i = 0; i < 10; ++i) r[i] = 0.0;
+            for (int i = 0; i < NB; ++i) r[i] = 0.0;
             for (int a = 0; a < Dc; ++a) {
-                const T *s = src + (size_t)a * CG * 10;
+                const T *s = src + (size_t)a * CG * NB;
                 const double w = wts[a].d;
 #pragma unroll
-                for (int i = 0; i < 10; ++i) r[i] = fma(w, (double)__ldcs(s + (size_t)i * G), r[i]);
+                for (int i = 0; i < NB; ++i) r[i] = fma(w, (double)__ldcs(s + (size_t)i * G), r[i]);
             }
         }
-        double *out = phi + idx * 10;
+        double *out = phi + idx * NB;
 #pragma unroll
-        for (int i = 0; i < 10; ++i) out[i] = accumulate ? out[i] + r[i] : r[i];
+        for (int i = 0; i < NB; ++i) out[i] = accumulate ? out[i] + r[i] : r[i];
     }
 }
 
 // Boundary leakage (vacuum boundaries): per (boundary cell, group) over the chunk's
 // directions, w_a s_f <psi_a>_f on every boundary outflow face (s_f = Omega_a . N_f
-// not below the sweep graph's inflow threshold -1e-12 |N_f|).  The face average of
-// the quadratic field is the mean of its three edge nodes (int_f phi_vertex = 0,
-// int_f phi_edge = A_f / 3).  Accumulated as the linear element's leak_kernel does.
-template <class T>
-__global__ void __launch_bounds__(256) leak_p2_kernel(const T *__restrict__ psi, const WeightPair *__restrict__ wts,
+// not below the sweep graph's inflow threshold -1e-12 |N_f|), with the face average
+// <psi>_f = sum_r fav[r] psi[fn[f][r]].  Accumulated as the linear element's leak_kernel.
+template <class T, int NB, int NF, class Geo>
+__global__ void __launch_bounds__(256) leak_ho_kernel(const T *__restrict__ psi, const WeightPair *__restrict__ wts,
                                                       const V4<T> *__restrict__ omega, int Dc, int64_t C, int G,
                                                       const uint32_t *__restrict__ bcells, int64_t nb,
-                                                      const P2Geo<T> *__restrict__ geo, double *__restrict__ leak)
+                                                      const Geo *__restrict__ geo, HoTables tb, double *__restrict__ leak)
 {
     for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < nb * G; u += (int64_t)gridDim.x * blockDim.x) {
         const int64_t b = u / G;
         const int g = (int)(u - b * G);
         const uint32_t c = bcells[b];
-        const P2Geo<T> &cg = geo[c];
+        const Geo &cg = geo[c];
         uint32_t faces = 0;
         T nx[4], ny[4], nz[4], thr[4];
 #pragma unroll
@@ -120,7 +128,7 @@ __global__ void __launch_bounds__(256) leak_p2_kernel(const T *__restrict__ psi,
         double acc = 0.0;
         float hi = 0.f, lo = 0.f;
         for (int a = 0; a < Dc; ++a) {
-            const T *s = psi + (((size_t)a * C + c) * 10) * G + g;
+            const T *s = psi + (((size_t)a * C + c) * NB) * G + g;
             const V4<T> om = omega[a];
             T t = T(0);
 #pragma unroll
@@ -128,8 +136,9 @@ __global__ void __launch_bounds__(256) leak_p2_kernel(const T *__restrict__ psi,
                 if (!((faces >> f) & 1u)) continue;
                 const T sf = om.x * nx[f] + om.y * ny[f] + om.z * nz[f];
                 if (sf < thr[f]) continue;  // inflow face of a vacuum boundary
-                const T avg = (s[(size_t)p2_face_node(f, 3) * G] + s[(size_t)p2_face_node(f, 4) * G] +
-                               s[(size_t)p2_face_node(f, 5) * G]) * T(1.0 / 3.0);
+                T avg = T(0);
+                for (int r = 0; r < NF; ++r)
+                    avg += T(__ldg(tb.fav + r)) * s[(size_t)__ldg(tb.fn + NF * f + r) * G];
                 t += sf * avg;
             }
             if constexpr (sizeof(T) == 8) {
@@ -146,37 +155,14 @@ __global__ void __launch_bounds__(256) leak_p2_kernel(const T *__restrict__ psi,
     }
 }
 
-// Per-cell sums of one (cell, group) of the quadratic field: max |phi_i|, the
-// plain nodal sum and sum_i p_i phi_i (int over the cell / V).
-__device__ __forceinline__ void p2_cell_sums(const double *v, double &mx, double &plain, double &wsum)
-{
-    mx = 0.0;
-    plain = 0.0;
-    wsum = 0.0;
-#pragma unroll
-    for (int i = 0; i < 10; ++i) {
-        mx = fmax(mx, fabs(v[i]));
-        plain += v[i];
-        wsum += p2_p(i) * v[i];
-    }
-}
-
-template <class T> __device__ __forceinline__ double p2_q_weighted(const T *q, int64_t c, int g, int G)
-{
-    double s = 0.0;
-#pragma unroll
-    for (int i = 0; i < 10; ++i) s += p2_p(i) * (double)q[((size_t)c * 10 + i) * G + g];
-    return s;
-}
-
-// The statistics of stats_kernel / stats_res_kernel for the quadratic field (same
-// partial layout, so the same finish kernels apply): integral sum_c V_c sum_i p_i phi_i
+// The statistics of stats_kernel / stats_res_kernel for a higher-order field (same
+// partial layout, so the same finish kernels apply): integral sum_c V_c sum_i pw_i phi_i
 // (Eq. (3)), plain nodal sum, absorption, source, max |phi| and (RES) max |dphi|.
-template <class T, bool RES>
-__global__ void __launch_bounds__(256) stats_p2_kernel(const double *__restrict__ phi_new,
+template <class T, bool RES, int NB>
+__global__ void __launch_bounds__(256) stats_ho_kernel(const double *__restrict__ phi_new,
                                                        const double *__restrict__ phi_old,
                                                        const double *__restrict__ vol, int64_t C, int G,
-                                                       double *__restrict__ part, BalIn bi)
+                                                       double *__restrict__ part, BalIn bi, const double *__restrict__ pw)
 {
     constexpr int NP = RES ? 6 : 5;
     __shared__ double sh[NP][8][32];
@@ -185,19 +171,26 @@ __global__ void __launch_bounds__(256) stats_p2_kernel(const double *__restrict_
         double mx = 0.0, iv = 0.0, pl = 0.0, dm = 0.0, ab = 0.0, sr = 0.0;
         if (g < G) {
             for (int64_t c = (int64_t)blockIdx.x * 8 + threadIdx.y; c < C; c += (int64_t)gridDim.x * 8) {
-                const double *pn = phi_new + ((size_t)c * G + g) * 10;
-                double m, plain, ws;
-                p2_cell_sums(pn, m, plain, ws);
-                mx = fmax(mx, m);
-                if constexpr (RES) {
-                    const double *po = phi_old + ((size_t)c * G + g) * 10;
+                const double *pn = phi_new + ((size_t)c * G + g) * NB;
+                double plain = 0.0, ws = 0.0, qs = 0.0;
+                const T *q = reinterpret_cast<const T *>(bi.q) + (size_t)c * NB * G + g;
 #pragma unroll
-                    for (int i = 0; i < 10; ++i) dm = fmax(dm, fabs(pn[i] - po[i]));
+                for (int i = 0; i < NB; ++i) {
+                    const double w = __ldg(pw + i);
+                    mx = fmax(mx, fabs(pn[i]));
+                    plain += pn[i];
+                    ws += w * pn[i];
+                    qs += w * (double)q[(size_t)i * G];
+                }
+                if constexpr (RES) {
+                    const double *po = phi_old + ((size_t)c * G + g) * NB;
+#pragma unroll
+                    for (int i = 0; i < NB; ++i) dm = fmax(dm, fabs(pn[i] - po[i]));
                 }
                 iv += vol[c] * ws;
                 pl += plain;
                 ab += bi.sig[(size_t)bi.mat[c] * G + g] * vol[c] * ws;
-                sr += vol[c] * kFourPi * p2_q_weighted(reinterpret_cast<const T *>(bi.q), c, g, G);
+                sr += vol[c] * kFourPi * qs;
             }
         }
         const double vals[6] = {mx, iv, pl, RES ? dm : ab, RES ? ab : sr, sr};
@@ -229,8 +222,9 @@ __global__ void __launch_bounds__(256) stats_p2_kernel(const double *__restrict_
     }
 }
 
-// Pointwise stopping test (residual_floor < 1) for the quadratic field, as residual_kernel.
-__global__ void __launch_bounds__(256) residual_p2_kernel(const double *__restrict__ phi_new,
+// Pointwise stopping test (residual_floor < 1) for a higher-order field, as residual_kernel.
+template <int NB>
+__global__ void __launch_bounds__(256) residual_ho_kernel(const double *__restrict__ phi_new,
                                                           const double *__restrict__ phi_old,
                                                           const double *__restrict__ gstats, int64_t C, int G,
                                                           double floor_frac, Ctrl *ctrl)
@@ -242,9 +236,9 @@ __global__ void __launch_bounds__(256) residual_p2_kernel(const double *__restri
         const double gmax = gstats[4 * g], inv = gstats[4 * g + 3];
         const double floor_ = floor_frac * gmax;
         for (int64_t c = (int64_t)blockIdx.x * 8 + threadIdx.y; c < C; c += (int64_t)gridDim.x * 8) {
-            const double *pn = phi_new + ((size_t)c * G + g) * 10, *po = phi_old + ((size_t)c * G + g) * 10;
+            const double *pn = phi_new + ((size_t)c * G + g) * NB, *po = phi_old + ((size_t)c * G + g) * NB;
 #pragma unroll
-            for (int i = 0; i < 10; ++i) {
+            for (int i = 0; i < NB; ++i) {
                 const double diff = fabs(pn[i] - po[i]);
                 if (diff == 0.0) continue;
                 const double den = fmax(fabs(pn[i]), floor_);
@@ -257,15 +251,15 @@ __global__ void __launch_bounds__(256) residual_p2_kernel(const double *__restri
         atomicMax(&ctrl->residual_bits, (unsigned long long)__double_as_longlong((double)rmax));
 }
 
-// psi of one direction, [C][10][G] -> the caller's [C][G][10] (inspection only).
-template <class T>
-__global__ void psi_p2_out_kernel(const T *__restrict__ src, T *__restrict__ dst, int64_t C, int G)
+// psi of one direction, [C][NB][G] -> the caller's [C][G][NB] (inspection only).
+template <class T, int NB>
+__global__ void psi_ho_out_kernel(const T *__restrict__ src, T *__restrict__ dst, int64_t C, int G)
 {
-    const size_t n = (size_t)C * G * 10;
+    const size_t n = (size_t)C * G * NB;
     for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += (size_t)gridDim.x * blockDim.x) {
-        const size_t c = idx / ((size_t)G * 10);
-        const size_t r = idx - c * (size_t)G * 10;
-        const int g = (int)(r / 10), i = (int)(r - (size_t)g * 10);
-        dst[idx] = src[(c * 10 + i) * G + g];
+        const size_t c = idx / ((size_t)G * NB);
+        const size_t r = idx - c * (size_t)G * NB;
+        const int g = (int)(r / NB), i = (int)(r - (size_t)g * NB);
+        dst[idx] = src[(c * NB + i) * G + g];
     }
 }

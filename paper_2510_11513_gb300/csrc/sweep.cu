@@ -14,6 +14,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <chrono>
 #include <cstddef>
 #include <cmath>
@@ -645,7 +646,7 @@ __global__ void __launch_bounds__(256) residual_kernel(const double *__restrict_
         atomicMax(&ctrl->residual_bits, (unsigned long long)__double_as_longlong((double)rmax));
 }
 
-#include "p2_kernels.cuh"
+#include "ho_kernels.cuh"
 
 // ============================================================== host side
 struct DeviceState {
@@ -656,8 +657,12 @@ struct DeviceState {
     bool fp64 = false;
     int order = 1;           // element order: 1 linear (4 nodes), 2 quadratic (10 nodes)
     int nb = 4;              // nodes per cell
-    void *geo2 = nullptr;    // second order: P2Geo<T> [C]
-    double *vol = nullptr;   // second order: cell volumes (FP64)
+    void *geo2 = nullptr;    // higher orders: P2Geo<T> / P3Geo<T> [C]
+    double *vol = nullptr;   // higher orders: cell volumes (FP64)
+    void *p3tab = nullptr;   // third order: P3Dev<T> element tables
+    double *ho_pw = nullptr;   // higher orders: int phi_i / V [nb]
+    int32_t *ho_fn = nullptr;  // higher orders: [4][nodes per face] face nodes
+    double *ho_fav = nullptr;  // higher orders: int_f phi / A_f on a face's nodes
     bool two_stage = false;  // staged path with two stages (mode 4)
     int pair_stages = 3;     // paired path: buffers in the ring of staged copies
     size_t tsize = 4;  // sizeof(T)
@@ -957,11 +962,107 @@ template <class T> tf_status create_typed_p2(Problem &p, DeviceState &d, const i
     if ((s = upload_typed<T>(d, &d.sigma_s, sigma_s, (size_t)d.M * d.G * d.G)) != TF_OK) return s;
     if ((s = upload(d, &d.vol, m.vol.data(), sizeof(double) * (size_t)d.C)) != TF_OK) return s;
     {
+        // statistics and leakage tables: p_i, the face nodes, and the face average (the mean of
+        // the three edge nodes: int_f phi_vertex = 0, int_f phi_edge = A_f / 3)
+        double pw[10], fav[6] = {0.0, 0.0, 0.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 3.0};
+        int32_t fn[24];
+        for (int i = 0; i < 10; ++i) pw[i] = p2_p(i);
+        for (int f = 0; f < 4; ++f)
+            for (int b = 0; b < 6; ++b) fn[6 * f + b] = p2_face_node(f, b);
+        if ((s = upload(d, &d.ho_pw, pw, sizeof(pw))) != TF_OK) return s;
+        if ((s = upload(d, &d.ho_fn, fn, sizeof(fn))) != TF_OK) return s;
+        if ((s = upload(d, &d.ho_fav, fav, sizeof(fav))) != TF_OK) return s;
+    }
+    {
         std::vector<double> Qs((size_t)d.C * d.G * 10);
         for (int64_t c = 0; c < d.C; ++c)
             for (int gq = 0; gq < d.G; ++gq)
                 for (int i = 0; i < 10; ++i)
                     Qs[((size_t)c * 10 + i) * d.G + gq] = Q[((size_t)c * d.G + gq) * 10 + i];
+        if ((s = upload_typed<T>(d, &d.Q, Qs.data(), Qs.size())) != TF_OK) return s;
+    }
+    return TF_OK;
+}
+
+// Third-order element: cell records (grad lambda, normals, volume, material, neighbours,
+// and for each of a face's ten nodes the neighbour's local node at the same place, matched
+// by the global vertices its lattice index weights), the exact element tables, cross
+// sections, Q reordered node-major [C][20][G].
+template <class T> tf_status create_typed_p3(Problem &p, DeviceState &d, const int32_t *cell_material,
+                                             const double *sigma_t, const double *sigma_s, const double *Q)
+{
+    const Mesh &m = *p.mesh;
+    tf_status s;
+    P3Tables tab;
+    p3_element_tables(tab);
+    {
+        // identity of node i of cell c: its four (global vertex, lattice weight) pairs, sorted
+        auto key = [&](int64_t c, int i) {
+            int al[4];
+            p3_node_alpha(i, al);
+            std::array<std::pair<int32_t, int>, 4> k;
+            for (int v = 0; v < 4; ++v) k[v] = {al[v] ? m.tets[4 * c + v] : -1, al[v]};
+            std::sort(k.begin(), k.end());
+            return k;
+        };
+        std::vector<P3Geo<T>> geo(m.nc);
+        for (int64_t c = 0; c < m.nc; ++c) {
+            P3Geo<T> &g = geo[c];
+            std::memset(&g, 0, sizeof(g));
+            for (int k = 0; k < 12; ++k) {
+                g.gl[k] = (T)m.grad[12 * c + k];
+                g.nrm[k] = (T)m.normal[12 * c + k];
+            }
+            g.vol = (T)m.vol[c];
+            g.mat = cell_material[c];
+            for (int f = 0; f < 4; ++f) {
+                const int32_t n = m.nbr[4 * c + f];
+                g.nbr[f] = n;
+                if (n < 0) continue;
+                for (int r = 0; r < 10; ++r) {
+                    const auto k = key(c, tab.fn[f][r]);
+                    int mm = -1;
+                    for (int j = 0; j < 20; ++j)
+                        if (key(n, j) == k) mm = j;
+                    if (mm < 0) return fail(TF_ERR_MESH, "third-order face node without a match in the neighbour");
+                    g.fmap[f] |= (unsigned long long)mm << (5 * r);
+                }
+            }
+        }
+        P3Geo<T> *gp = nullptr;
+        if ((s = upload(d, &gp, geo.data(), geo.size() * sizeof(P3Geo<T>))) != TF_OK) return s;
+        d.geo2 = gp;
+    }
+    {
+        P3Dev<T> dt;
+        for (int e = 0; e < 400; ++e) {
+            dt.M[e] = (T)tab.M[e];
+            for (int k = 0; k < 4; ++k) dt.C[k][e] = (T)tab.C[k][e];
+        }
+        for (int e = 0; e < 100; ++e) dt.F[e] = (T)tab.F[0][e];
+        for (int f = 0; f < 4; ++f)
+            for (int r = 0; r < 10; ++r) dt.fn[f][r] = tab.fn[f][r];
+        P3Dev<T> *tp = nullptr;
+        if ((s = upload(d, &tp, &dt, sizeof(dt))) != TF_OK) return s;
+        d.p3tab = tp;
+        int32_t fn[40];
+        for (int f = 0; f < 4; ++f)
+            for (int r = 0; r < 10; ++r) fn[10 * f + r] = tab.fn[f][r];
+        if ((s = upload(d, &d.ho_pw, tab.p, sizeof(tab.p))) != TF_OK) return s;
+        if ((s = upload(d, &d.ho_fn, fn, sizeof(fn))) != TF_OK) return s;
+        if ((s = upload(d, &d.ho_fav, tab.fav[0], sizeof(tab.fav[0]))) != TF_OK) return s;
+    }
+    if ((s = upload_vec3<T>(d, &d.omega, p.quad->omega.data(), d.D, p.quad->w.data())) != TF_OK) return s;
+    if ((s = upload(d, &d.mat, cell_material, sizeof(int32_t) * (size_t)d.C)) != TF_OK) return s;
+    if ((s = upload(d, &d.sig_d, sigma_t, sizeof(double) * (size_t)d.M * d.G)) != TF_OK) return s;
+    if ((s = upload_typed<T>(d, &d.sigma_t, sigma_t, (size_t)d.M * d.G)) != TF_OK) return s;
+    if ((s = upload_typed<T>(d, &d.sigma_s, sigma_s, (size_t)d.M * d.G * d.G)) != TF_OK) return s;
+    if ((s = upload(d, &d.vol, m.vol.data(), sizeof(double) * (size_t)d.C)) != TF_OK) return s;
+    {
+        std::vector<double> Qs((size_t)d.C * d.G * 20);
+        for (int64_t c = 0; c < d.C; ++c)
+            for (int gq = 0; gq < d.G; ++gq)
+                for (int i = 0; i < 20; ++i) Qs[((size_t)c * 20 + i) * d.G + gq] = Q[((size_t)c * d.G + gq) * 20 + i];
         if ((s = upload_typed<T>(d, &d.Q, Qs.data(), Qs.size())) != TF_OK) return s;
     }
     return TF_OK;
@@ -994,8 +1095,8 @@ tf_status device_create(Problem &p, const int32_t *cell_material, const double *
     d.D = p.quad->D;
     d.M = p.M;
     d.fp64 = p.opt.precision == TF_FP64;
-    d.order = p.opt.order == 2 ? 2 : 1;
-    d.nb = d.order == 2 ? 10 : 4;
+    d.order = p.opt.order >= 2 ? p.opt.order : 1;
+    d.nb = d.order == 3 ? 20 : d.order == 2 ? 10 : 4;
     // pairing 0 = automatic: packed pairs unless G is a multiple of 32 (there the
     // shared-memory staged path is faster); 2 = packed pairs whenever G is even
     d.paired = d.order == 1 && !d.fp64 && d.G % 2 == 0 && (p.opt.pairing == 2 || (p.opt.pairing == 0 && d.G % 32 != 0)) &&
@@ -1022,7 +1123,7 @@ tf_status device_create(Problem &p, const int32_t *cell_material, const double *
         std::vector<uint32_t> cl(g.cell_list.size());
         for (size_t i = 0; i < cl.size(); ++i) {
             const uint32_t e = g.cell_list[i], c = e >> 4;
-            cl[i] = d.order == 2 ? e : (c << 4) | remap[16 * (size_t)c + (e & 15u)];
+            cl[i] = d.order >= 2 ? e : (c << 4) | remap[16 * (size_t)c + (e & 15u)];
         }
         if ((s = upload(d, &d.cells, cl.data(), cl.size() * 4)) != TF_OK) return s;
     }
@@ -1045,7 +1146,10 @@ tf_status device_create(Problem &p, const int32_t *cell_material, const double *
         for (int64_t c = 0; c < m.nc; ++c) v4[c] = 0.25 * m.vol[c];
         if ((s = upload(d, &d.vol4, v4.data(), v4.size() * 8)) != TF_OK) return s;
     }
-    if (d.order == 2)
+    if (d.order == 3)
+        s = d.fp64 ? create_typed_p3<double>(p, d, cell_material, sigma_t, sigma_s, Q)
+                   : create_typed_p3<float>(p, d, cell_material, sigma_t, sigma_s, Q);
+    else if (d.order == 2)
         s = d.fp64 ? create_typed_p2<double>(p, d, cell_material, sigma_t, sigma_s, Q)
                    : create_typed_p2<float>(p, d, cell_material, sigma_t, sigma_s, Q);
     else
@@ -1208,7 +1312,12 @@ tf_status device_create(Problem &p, const int32_t *cell_material, const double *
     const bool p2_staged = d.order == 2 && !d.fp64 && d.G % 32 == 0 && g.cells_per_task <= 32 && p.opt.staging != 1 &&
                            ((p2_stage_bytes(d.G) * 2 + 48 + 127) / 128 * 128) * d.wpc <= 227 * 1024;
     if (p2_staged) d.warp_smem = (p2_stage_bytes(d.G) * 2 + 48 + 127) / 128 * 128;
-    d.mode = d.order == 2 ? (p2_staged ? 6 : 5)
+    if (d.order == 3) {  // one warp per CTA, its lanes' systems in shared memory
+        d.wpc = 1;
+        d.warp_smem = (uint32_t)(d.fp64 ? p3_warp_bytes<double>() : p3_warp_bytes<float>());
+    }
+    d.mode = d.order == 3 ? 7
+             : d.order == 2 ? (p2_staged ? 6 : 5)
              : d.paired  ? 3
              : d.staged  ? (d.two_stage ? 4 : 2)
                          : (d.G % 32 == 0 && g.cells_per_task <= 64 ? 1 : 0);
@@ -1238,7 +1347,8 @@ tf_status device_create(Problem &p, const int32_t *cell_material, const double *
         d.ppl = (int)L.ppl;
     }
     const int dyn = (int)(d.warp_smem * d.wpc);
-    const void *kfn = d.mode == 6   ? (const void *)sweep_kernel<float, 6>
+    const void *kfn = d.mode == 7   ? (d.fp64 ? (const void *)sweep_kernel<double, 7> : (const void *)sweep_kernel<float, 7>)
+                      : d.mode == 6 ? (const void *)sweep_kernel<float, 6>
                       : d.mode == 5 ? (d.fp64 ? (const void *)sweep_kernel<double, 5> : (const void *)sweep_kernel<float, 5>)
                       : d.fp64 ? (d.mode == 2 ? (const void *)sweep_kernel<double, 2>
                                             : d.mode == 1 ? (const void *)sweep_kernel<double, 1> : (const void *)sweep_kernel<double, 0>)
@@ -1339,12 +1449,16 @@ void *mapped_host_pointer(const void *ptr)
 template <class T> void launch_source(Problem &p, const double *phi_in, cudaStream_t st)
 {
     DeviceState &d = *p.dev;
-    if (d.order == 2) {
+    if (d.order >= 2) {
         const int cpc2 = std::max(1, 256 / d.G);
-        const size_t smem2 = (size_t)cpc2 * d.G * 10 * sizeof(T);
+        const size_t smem2 = (size_t)cpc2 * d.G * d.nb * sizeof(T);
         const int blocks2 = (int)std::min<int64_t>((d.C + cpc2 - 1) / cpc2, (int64_t)d.sm_count * 16);
-        source_p2_kernel<T><<<blocks2, 256, smem2, st>>>(phi_in, (const T *)d.Q, (const T *)d.sigma_s, d.mat,
-                                                         (T *)d.q, d.C, d.G, cpc2);
+        if (d.order == 3)
+            source_ho_kernel<T, 20><<<blocks2, 256, smem2, st>>>(phi_in, (const T *)d.Q, (const T *)d.sigma_s, d.mat,
+                                                                 (T *)d.q, d.C, d.G, cpc2);
+        else
+            source_ho_kernel<T, 10><<<blocks2, 256, smem2, st>>>(phi_in, (const T *)d.Q, (const T *)d.sigma_s, d.mat,
+                                                                 (T *)d.q, d.C, d.G, cpc2);
         cudaMemsetAsync(d.leak, 0, sizeof(double) * d.G, st);
         return;
     }
@@ -1355,6 +1469,27 @@ template <class T> void launch_source(Problem &p, const double *phi_in, cudaStre
                                                 (const CellGeo<T> *)d.geo, (V4<T> *)d.q, d.C, d.G, cpc,
                                                 d.paired ? 1 : 0);
     cudaMemsetAsync(d.leak, 0, sizeof(double) * d.G, st);  // the phi kernels add this step's leakage
+}
+
+// Statistics, balance and stopping test of a higher-order iterate (NB nodes per cell).
+template <int NB> void launch_stats_ho(Problem &p, const double *cur, const double *nxt, bool res, BalIn bi,
+                                       cudaStream_t st)
+{
+    DeviceState &d = *p.dev;
+    const dim3 blk(32, 8);
+    if (d.fp64) {
+        if (res) stats_ho_kernel<double, true, NB><<<d.stats_blocks, blk, 0, st>>>(nxt, cur, d.vol, d.C, d.G, d.part, bi, d.ho_pw);
+        else stats_ho_kernel<double, false, NB><<<d.stats_blocks, blk, 0, st>>>(nxt, cur, d.vol, d.C, d.G, d.part, bi, d.ho_pw);
+    } else {
+        if (res) stats_ho_kernel<float, true, NB><<<d.stats_blocks, blk, 0, st>>>(nxt, cur, d.vol, d.C, d.G, d.part, bi, d.ho_pw);
+        else stats_ho_kernel<float, false, NB><<<d.stats_blocks, blk, 0, st>>>(nxt, cur, d.vol, d.C, d.G, d.part, bi, d.ho_pw);
+    }
+    if (res) {
+        finish_stats_res_kernel<<<(d.G + 127) / 128, 128, 0, st>>>(d.part, d.stats_blocks, d.G, d.gstats, d.leak, d.ctrl);
+    } else {
+        finish_stats_kernel<<<(d.G + 127) / 128, 128, 0, st>>>(d.part, d.stats_blocks, d.G, d.gstats, d.leak, d.ctrl);
+        residual_ho_kernel<NB><<<d.stats_blocks, blk, 0, st>>>(nxt, cur, d.gstats, d.C, d.G, p.opt.residual_floor, d.ctrl);
+    }
 }
 
 // Statistics, particle balance and stopping test of the iterate nxt (previous: cur).
@@ -1368,23 +1503,10 @@ void launch_stats(Problem &p, const double *cur, const double *nxt, cudaStream_t
     bi.qmode = d.paired ? 2 : (d.fp64 ? 1 : 0);
     bi.leak = d.leak;
     cudaMemsetAsync(&d.ctrl->residual_bits, 0, 16, st);  // residual_bits, balance_bits
-    if (d.order == 2) {
+    if (d.order >= 2) {
         const bool res = p.opt.residual_floor >= 1.0;
-        if (d.fp64) {
-            if (res) stats_p2_kernel<double, true><<<d.stats_blocks, dim3(32, 8), 0, st>>>(nxt, cur, d.vol, d.C, d.G, d.part, bi);
-            else stats_p2_kernel<double, false><<<d.stats_blocks, dim3(32, 8), 0, st>>>(nxt, cur, d.vol, d.C, d.G, d.part, bi);
-        } else {
-            if (res) stats_p2_kernel<float, true><<<d.stats_blocks, dim3(32, 8), 0, st>>>(nxt, cur, d.vol, d.C, d.G, d.part, bi);
-            else stats_p2_kernel<float, false><<<d.stats_blocks, dim3(32, 8), 0, st>>>(nxt, cur, d.vol, d.C, d.G, d.part, bi);
-        }
-        if (res) {
-            finish_stats_res_kernel<<<(d.G + 127) / 128, 128, 0, st>>>(d.part, d.stats_blocks, d.G, d.gstats, d.leak,
-                                                                       d.ctrl);
-        } else {
-            finish_stats_kernel<<<(d.G + 127) / 128, 128, 0, st>>>(d.part, d.stats_blocks, d.G, d.gstats, d.leak, d.ctrl);
-            residual_p2_kernel<<<d.stats_blocks, dim3(32, 8), 0, st>>>(nxt, cur, d.gstats, d.C, d.G,
-                                                                       p.opt.residual_floor, d.ctrl);
-        }
+        if (d.order == 3) launch_stats_ho<20>(p, cur, nxt, res, bi, st);
+        else launch_stats_ho<10>(p, cur, nxt, res, bi, st);
         return;
     }
     if (p.opt.residual_floor >= 1.0) {
@@ -1443,6 +1565,7 @@ template <class T> SweepArgs<T> make_args(Problem &p, int k)
     A.stages = d.pair_stages;
     A.mode = d.mode;
     A.geo2 = d.geo2;
+    A.p3tab = d.p3tab;
     A.keep_max = p.opt.keep_ready > 0 ? std::min(p.opt.keep_ready, 4) : 1;
     return A;
 }
@@ -1454,15 +1577,26 @@ template <class T> void launch_phi(Problem &p, int k, double *phi_out, cudaStrea
     const size_t CG = (size_t)d.C * d.G;
     const int a0 = k * d.Dc, a1 = std::min(d.D, a0 + d.Dc);
     const int pb = (int)std::min<size_t>((CG + 255) / 256, (size_t)d.sm_count * 32);
-    if (d.order == 2) {
-        if (!d.fp64 && p.opt.phi_accumulate == TF_PHI_PAIR)
-            phi_p2_kernel<T, true><<<pb, 256, 0, st>>>((const T *)d.psi, d.wts + a0, a1 - a0, d.C, d.G, phi_out, k > 0);
-        else
-            phi_p2_kernel<T, false><<<pb, 256, 0, st>>>((const T *)d.psi, d.wts + a0, a1 - a0, d.C, d.G, phi_out, k > 0);
+    if (d.order >= 2) {
+        const bool pair = !d.fp64 && p.opt.phi_accumulate == TF_PHI_PAIR;
+        const T *ps = (const T *)d.psi;
+        if (d.order == 3) {
+            if (pair) phi_ho_kernel<T, true, 20><<<pb, 256, 0, st>>>(ps, d.wts + a0, a1 - a0, d.C, d.G, phi_out, k > 0);
+            else phi_ho_kernel<T, false, 20><<<pb, 256, 0, st>>>(ps, d.wts + a0, a1 - a0, d.C, d.G, phi_out, k > 0);
+        } else {
+            if (pair) phi_ho_kernel<T, true, 10><<<pb, 256, 0, st>>>(ps, d.wts + a0, a1 - a0, d.C, d.G, phi_out, k > 0);
+            else phi_ho_kernel<T, false, 10><<<pb, 256, 0, st>>>(ps, d.wts + a0, a1 - a0, d.C, d.G, phi_out, k > 0);
+        }
         if (d.n_bcells > 0) {
             const int lb = (int)std::min<int64_t>((d.n_bcells * d.G + 255) / 256, (int64_t)d.sm_count * 16);
-            leak_p2_kernel<T><<<lb, 256, 0, st>>>((const T *)d.psi, d.wts + a0, (const V4<T> *)d.omega + a0, a1 - a0,
-                                                  d.C, d.G, d.bcells, d.n_bcells, (const P2Geo<T> *)d.geo2, d.leak);
+            const HoTables tb{d.ho_pw, d.ho_fn, d.ho_fav};
+            const V4<T> *om = (const V4<T> *)d.omega + a0;
+            if (d.order == 3)
+                leak_ho_kernel<T, 20, 10, P3Geo<T>><<<lb, 256, 0, st>>>(ps, d.wts + a0, om, a1 - a0, d.C, d.G, d.bcells,
+                                                                        d.n_bcells, (const P3Geo<T> *)d.geo2, tb, d.leak);
+            else
+                leak_ho_kernel<T, 10, 6, P2Geo<T>><<<lb, 256, 0, st>>>(ps, d.wts + a0, om, a1 - a0, d.C, d.G, d.bcells,
+                                                                       d.n_bcells, (const P2Geo<T> *)d.geo2, tb, d.leak);
         }
         return;
     }
@@ -1555,7 +1689,9 @@ template <class T> tf_status launch_step(Problem &p, const double *phi_in, doubl
             if (d.mode == 6) sweep_kernel<T, 6><<<d.grid, 32 * d.wpc, dyn, st>>>(A);
         }
         if (d.mode == 3 || d.mode == 4 || d.mode == 6) {
-        } else if (d.mode == 5)
+        } else if (d.mode == 7)
+            sweep_kernel<T, 7><<<d.grid, 32 * d.wpc, dyn, st>>>(A);
+        else if (d.mode == 5)
             sweep_kernel<T, 5><<<d.grid, 32 * d.wpc, 0, st>>>(A);
         else if (d.mode == 2)
             sweep_kernel<T, 2><<<d.grid, 32 * d.wpc, dyn, st>>>(A);
@@ -2143,13 +2279,20 @@ tf_status device_psi(Problem &p, int32_t dir, void *out, void *stream)
     const size_t CG = (size_t)d.C * d.G;
     cudaStream_t st = (cudaStream_t)stream;
     const int blocks = (int)std::min<size_t>((CG + 255) / 256, (size_t)d.sm_count * 16);
-    if (d.order == 2) {
+    if (d.order == 3) {
         if (d.fp64)
-            psi_p2_out_kernel<double><<<blocks, 256, 0, st>>>((const double *)d.psi + (size_t)(dir - a0) * CG * 10,
-                                                              (double *)out, d.C, d.G);
+            psi_ho_out_kernel<double, 20><<<blocks, 256, 0, st>>>((const double *)d.psi + (size_t)(dir - a0) * CG * 20,
+                                                                  (double *)out, d.C, d.G);
         else
-            psi_p2_out_kernel<float><<<blocks, 256, 0, st>>>((const float *)d.psi + (size_t)(dir - a0) * CG * 10,
-                                                             (float *)out, d.C, d.G);
+            psi_ho_out_kernel<float, 20><<<blocks, 256, 0, st>>>((const float *)d.psi + (size_t)(dir - a0) * CG * 20,
+                                                                 (float *)out, d.C, d.G);
+    } else if (d.order == 2) {
+        if (d.fp64)
+            psi_ho_out_kernel<double, 10><<<blocks, 256, 0, st>>>((const double *)d.psi + (size_t)(dir - a0) * CG * 10,
+                                                                  (double *)out, d.C, d.G);
+        else
+            psi_ho_out_kernel<float, 10><<<blocks, 256, 0, st>>>((const float *)d.psi + (size_t)(dir - a0) * CG * 10,
+                                                                 (float *)out, d.C, d.G);
     } else if (d.paired)
         psi_unpair_kernel<<<blocks, 256, 0, st>>>((const float *)d.psi + (size_t)(dir - a0) * CG * 4, (float4 *)out,
                                                   CG / 2, d.G, (const CellGeo<float> *)d.geo);

@@ -180,6 +180,7 @@ template <class T> struct SweepArgs {
     int32_t mode;                // kernel variant of this problem (batched launches dispatch on it)
     const void *geo2;            // second-order element: P2Geo<T> [C] cell records (mode 5)
     int32_t keep_max;            // ready tasks a warp keeps and runs next (1..4)
+    const void *p3tab;           // third-order element: P3Dev<T> tables (mode 7)
 };
 
 // Solve one 4x4 system by Gaussian elimination without pivoting: the
@@ -1124,6 +1125,7 @@ __device__ __forceinline__ bool run_task_staged_any(const SweepArgs<T> &A, uint4
 }
 
 #include "p2_solve.cuh"
+#include "p3_solve.cuh"
 
 // Persistent sweep: a warp claims a ticket (the next queue slot), waits until
 // that slot holds a ready task, executes it with lanes spanning (cell, group)
@@ -1139,9 +1141,10 @@ __device__ __forceinline__ bool run_task_staged_any(const SweepArgs<T> &A, uint4
 // 3 = FP32 and G even: packed group pairs (pair-interleaved source and psi rows),
 // 4 = as 2 with two stages and six resident CTAs per SM (FP32),
 // 5 = the second-order (ten-node) element, lanes over (cell, group) units,
-// 6 = the second-order element staged in shared memory (FP32, G a multiple of 32).
+// 6 = the second-order element staged in shared memory (FP32, G a multiple of 32),
+// 7 = the third-order element, one system per lane in shared memory (one warp per CTA).
 template <class T, int MODE>
-__global__ void __launch_bounds__(128, MODE == 5 ? 2 : MODE == 6 ? 3 : MODE == 4 ? 6 : (sizeof(T) == 4 ? 4 : 3))
+__global__ void __launch_bounds__(128, MODE == 7 ? 1 : MODE == 5 ? 2 : MODE == 6 ? 3 : MODE == 4 ? 6 : (sizeof(T) == 4 ? 4 : 3))
     sweep_kernel(const SweepArgs<T> A)
 {
     const int lane = threadIdx.x & 31;
@@ -1249,6 +1252,8 @@ __global__ void __launch_bounds__(128, MODE == 5 ? 2 : MODE == 6 ? 3 : MODE == 4
             run_task_p2(A, ti, lane, om.x, om.y, om.z, psi_dir);
         } else if constexpr (MODE == 6) {
             if (!run_task_p2_staged(A, ti, lane, om.x, om.y, om.z, psi_dir, wsm, bars, ph, ws + 6)) break;
+        } else if constexpr (MODE == 7) {
+            run_task_p3(A, ti, lane, om.x, om.y, om.z, psi_dir, wsm);
         } else {
             run_task_generic(A, ti, lane, om.x, om.y, om.z, psi_dir);
         }

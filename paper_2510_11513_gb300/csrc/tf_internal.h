@@ -83,6 +83,21 @@ struct tf_autotune_report {
     int32_t pairing = 0, staging = 0, window = 0, n_variants = 0;
 };
 
+// Exact tables of the third-order (twenty-node) element (p3_tables.cpp), per unit
+// volume / area: p[i] = int phi_i, M = int phi_i phi_j, C[k] = int phi_i d phi_j / d lambda_k,
+// for the face opposite vertex f: fn[f] its ten nodes (node order), F[f] = int_f phi_r phi_c,
+// fav[f][r] = int_f phi_r.
+struct P3Tables {
+    double p[20];
+    double M[400];
+    double C[4][400];
+    int fn[4][10];
+    double F[4][100];
+    double fav[4][10];
+};
+void p3_element_tables(P3Tables &t);
+void p3_node_alpha(int i, int al[4]);
+
 struct Problem : Object {
     Problem() : Object(Kind::Problem) {}
     ~Problem() override;

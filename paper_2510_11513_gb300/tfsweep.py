@@ -474,7 +474,7 @@ class Problem(_Handle):
                  S1=None, psi_inflow=None, **opts):
         self.mesh, self.quad = mesh, quad
         self.opt = options(**opts)
-        self.n_nodes = 10 if self.opt.order == 2 else 4
+        self.n_nodes = {2: 10, 3: 20}.get(int(self.opt.order), 4)
         if int(n_groups) > 0 and np.size(Q) != mesh.n_cells * int(n_groups) * self.n_nodes:
             raise ValueError(f"Q must be [n_cells][n_groups][{self.n_nodes}]")
         self.h = tf_problem_create(mesh.h, quad.h, n_groups, n_materials, cell_material, sigma_t, sigma_s, Q, S1,
