@@ -37,7 +37,7 @@ UNIT = "ns/(cell·dir·group)"
 L2_BYTES = 129 * 1024 * 1024
 
 
-KERNEL_SOURCES = ("sweep_kernel.cuh", "p2_solve.cuh", "p2_tables.h")
+KERNEL_SOURCES = ("sweep_kernel.cuh", "p2_solve.cuh", "p2_tables.h", "p3_solve.cuh")
 
 
 def kernel_source_sha1():
@@ -301,13 +301,13 @@ def p2_flops_per_unit(prob, tf, order=2):
     return 1485.0 + 156.0 * n_in, n_in
 
 
-def second_order_leg(tf, cfg, prec, local, stream, steps, torch):
-    """The second-order (ten-node) element on one workload: grind time of a source
-    iteration and the sweep kernel's ALU roofline (it is bound by FP32 arithmetic:
-    about 1,800 flops against 80-160 bytes per unit)."""
+def second_order_leg(tf, cfg, prec, local, stream, steps, torch, order=2):
+    """A higher-order element (order 2: ten nodes, 3: twenty) on one workload: grind time
+    of a source iteration and the sweep kernel's ALU roofline (bound by FP32 arithmetic:
+    about 1,800 / 12,000 flops against 80-320 bytes per unit)."""
     dev = torch.device("cuda", local)
-    pr = tf.Problem.from_config(cfg, precision=prec, device=local, order=2)
-    ph = torch.zeros((pr.n_cells, pr.n_groups, 10), dtype=torch.float64, device=dev)
+    pr = tf.Problem.from_config(cfg, precision=prec, device=local, order=order)
+    ph = torch.zeros((pr.n_cells, pr.n_groups, pr.n_nodes), dtype=torch.float64, device=dev)
     pr.source_iterate(ph, 0.0, 1, stream=stream)
     st0 = pr.stats()
     torch.cuda.synchronize(dev)
@@ -320,7 +320,7 @@ def second_order_leg(tf, cfg, prec, local, stream, steps, torch):
     st = pr.stats()
     ms = e0.elapsed_time(e1) / steps
     sweep_s = (st["cum_sweep_event_seconds"] - st0["cum_sweep_event_seconds"]) / steps
-    flops, n_in = p2_flops_per_unit(pr, tf)
+    flops, n_in = p2_flops_per_unit(pr, tf, order)
     achieved = flops * pr.n_units / sweep_s / 1e12
     klabel = f"sweep_kernel<float, {st['kernel_mode']}>"
     out = {"workload": cfg["name"], "units_per_step": pr.n_units, "ms_per_step": ms,
@@ -482,6 +482,9 @@ def run_ours(args):
     if not args.no_second_order and world == 1 and prec == tf.TF_FP32 and args.order == 1:
         # the paper's second-order element, on the two-material box (805 M units per step)
         line["second_order"] = second_order_leg(tf, W.order2(W.two_material_box()), prec, local, stream, 3, torch)
+        # and the third-order element on the 16^3-hex workload (50 M units per step)
+        line["third_order"] = second_order_leg(tf, W.order3(W.paper_context_box()), prec, local, stream, 2, torch,
+                                               order=3)
     if not args.no_fp64_compare and prec == tf.TF_FP32:
         p64 = tf.Problem.from_config(cfg, precision=tf.TF_FP64, device=local, order=args.order)
         phi64 = torch.zeros((C, G, nodes), dtype=torch.float64, device=dev)
