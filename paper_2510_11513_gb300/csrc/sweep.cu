@@ -1312,10 +1312,7 @@ tf_status device_create(Problem &p, const int32_t *cell_material, const double *
     const bool p2_staged = d.order == 2 && !d.fp64 && d.G % 32 == 0 && g.cells_per_task <= 32 && p.opt.staging != 1 &&
                            ((p2_stage_bytes(d.G) * 2 + 48 + 127) / 128 * 128) * d.wpc <= 227 * 1024;
     if (p2_staged) d.warp_smem = (p2_stage_bytes(d.G) * 2 + 48 + 127) / 128 * 128;
-    if (d.order == 3) {  // one warp per CTA, its lanes' systems in shared memory
-        d.wpc = 1;
-        d.warp_smem = (uint32_t)(d.fp64 ? p3_warp_bytes<double>() : p3_warp_bytes<float>());
-    }
+    if (d.order == 3) d.warp_smem = 0;  // four lanes per unit, systems in registers
     d.mode = d.order == 3 ? 7
              : d.order == 2 ? (p2_staged ? 6 : 5)
              : d.paired  ? 3
