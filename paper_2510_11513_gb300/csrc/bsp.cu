@@ -98,7 +98,7 @@ __device__ __forceinline__ bool exec_task(const SweepArgs<T> &A, unsigned task, 
 // finished the bucket.  The time warps spend there is counted as wait time, the
 // time executing tasks as busy time.
 template <class T, int MODE>
-__global__ void __launch_bounds__(128, MODE == 7 ? 2 : MODE == 5 ? 2 : MODE == 6 ? 3 : MODE == 4 ? 6 : (sizeof(T) == 4 ? 4 : 3))
+__global__ void __launch_bounds__(128, MODE == 7 ? (sizeof(T) == 4 ? 3 : 2) : MODE == 5 ? 2 : MODE == 6 ? 3 : MODE == 4 ? 6 : (sizeof(T) == 4 ? 4 : 3))
     bsp_sweep_kernel(const SweepArgs<T> A, const BspArgs S)
 {
     const int lane = threadIdx.x & 31;

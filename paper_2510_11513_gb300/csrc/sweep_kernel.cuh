@@ -1144,7 +1144,7 @@ __device__ __forceinline__ bool run_task_staged_any(const SweepArgs<T> &A, uint4
 // 6 = the second-order element staged in shared memory (FP32, G a multiple of 32),
 // 7 = the third-order element, four lanes per unit with the system in registers.
 template <class T, int MODE>
-__global__ void __launch_bounds__(128, MODE == 7 ? 2 : MODE == 5 ? 2 : MODE == 6 ? 3 : MODE == 4 ? 6 : (sizeof(T) == 4 ? 4 : 3))
+__global__ void __launch_bounds__(128, MODE == 7 ? (sizeof(T) == 4 ? 3 : 2) : MODE == 5 ? 2 : MODE == 6 ? 3 : MODE == 4 ? 6 : (sizeof(T) == 4 ? 4 : 3))
     sweep_kernel(const SweepArgs<T> A)
 {
     const int lane = threadIdx.x & 31;
