@@ -37,14 +37,11 @@ UNIT = "ns/(cell·dir·group)"
 L2_BYTES = 129 * 1024 * 1024
 
 
-KERNEL_SOURCES = ("sweep_kernel.cuh", "p2_solve.cuh", "p2_tables.h", "p3_solve.cuh")
-
-
-def kernel_source_sha1():
-    """SHA-1 over the sweep kernel's device sources (concatenated in KERNEL_SOURCES order)."""
+def kernel_source_sha1(sources):
+    """SHA-1 over a kernel variant's device sources (files of csrc/, concatenated in order)."""
     import hashlib
     h = hashlib.sha1()
-    for f in KERNEL_SOURCES:
+    for f in sources:
         with open(os.path.join(ROOT, "paper_2510_11513_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()
@@ -52,16 +49,14 @@ def kernel_source_sha1():
 
 def _traffic(workload, precision, kernel_label):
     """DRAM bytes per sweep-kernel launch from the committed ncu record, if it was taken on
-    this workload with the current kernel source; else None."""
+    this workload with the current sources of that kernel variant (the files the record
+    lists); else None."""
     import glob
-    try:
-        sha = kernel_source_sha1()
-    except OSError:
-        return None
     for f in glob.glob(os.path.join(ROOT, "profiles", "traffic_*.json")):
         try:
             rec = json.load(open(f))
-        except (OSError, ValueError):
+            sha = kernel_source_sha1(rec["kernel_sources"])
+        except (OSError, ValueError, KeyError):
             continue
         if (rec.get("workload") == workload and rec.get("precision") == precision
                 and rec.get("kernel_source_sha1") == sha and rec.get("kernel") == kernel_label):
