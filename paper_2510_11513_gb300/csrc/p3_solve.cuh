@@ -30,6 +30,8 @@ template <class T> struct P3Dev {
     T C[4][400];        // int phi_i d phi_j / d lambda_k / V
     T F[100];           // int_f phi_r phi_c / A_f on a face's ten nodes (the same for every face)
     int32_t fn[4][10];  // the ten nodes of the face opposite vertex f
+    T FA[4][400];       // F of face f placed in the 20 x 20 matrix (zero off the face's nodes)
+    T FU[4][200];       // [f][i][c]: F(r, c) for the row i = fn[f][r] of the face, zero elsewhere
 };
 
 // lattice index of node i in coordinate k (compile-time structure of the element)
@@ -96,7 +98,9 @@ __device__ __forceinline__ void p3_unit4(const SweepArgs<T> &A, const P3Geo<T> *
         b[r] = V * bi;
     }
     T *psi = reinterpret_cast<T *>(A.psi);
-#pragma unroll
+    // inflow faces (one loop body for all four, to keep the kernel's code small): the face
+    // matrices come expanded to the lane's rows from the tables
+#pragma unroll 1
     for (int f = 0; f < 4; ++f) {
         if (!((mask >> f) & 1u)) continue;
         const T s = fabs(ox * cg.nrm[3 * f] + oy * cg.nrm[3 * f + 1] + oz * cg.nrm[3 * f + 2]);
@@ -112,17 +116,16 @@ __device__ __forceinline__ void p3_unit4(const SweepArgs<T> &A, const P3Geo<T> *
             for (int k = 0; k < 10; ++k) up[k] = T(0);  // vacuum boundary: no inflow
         }
 #pragma unroll
-        for (int rr = 0; rr < 10; ++rr) {
-            const int nr = p3_face_node(f, rr);
-            if ((nr & 3) != sub) continue;  // the row belongs to another lane of the four
+        for (int r = 0; r < 5; ++r) {
+            const int i = 4 * r + sub;
+            const T *fa = &tb->FA[f][20 * i];
+            const T *fu = &tb->FU[f][10 * i];
+#pragma unroll
+            for (int j = 0; j < 20; ++j) a[r][j] += s * __ldg(fa + j);
             T t = T(0);
 #pragma unroll
-            for (int cc = 0; cc < 10; ++cc) {
-                const T fv = __ldg(&tb->F[10 * rr + cc]);
-                a[nr >> 2][p3_face_node(f, cc)] += s * fv;
-                t += fv * up[cc];
-            }
-            b[nr >> 2] += s * t;
+            for (int cc = 0; cc < 10; ++cc) t += __ldg(fu + cc) * up[cc];
+            b[r] += s * t;
         }
     }
     // elimination: the pivot row k lives in lane (k & 3) of the four, local row k >> 2

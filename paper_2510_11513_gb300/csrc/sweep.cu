@@ -1034,7 +1034,8 @@ template <class T> tf_status create_typed_p3(Problem &p, DeviceState &d, const i
         d.geo2 = gp;
     }
     {
-        P3Dev<T> dt;
+        std::vector<P3Dev<T>> dtv(1);
+        P3Dev<T> &dt = dtv[0];
         for (int e = 0; e < 400; ++e) {
             dt.M[e] = (T)tab.M[e];
             for (int k = 0; k < 4; ++k) dt.C[k][e] = (T)tab.C[k][e];
@@ -1042,6 +1043,15 @@ template <class T> tf_status create_typed_p3(Problem &p, DeviceState &d, const i
         for (int e = 0; e < 100; ++e) dt.F[e] = (T)tab.F[0][e];
         for (int f = 0; f < 4; ++f)
             for (int r = 0; r < 10; ++r) dt.fn[f][r] = tab.fn[f][r];
+        for (int f = 0; f < 4; ++f) {
+            for (int e = 0; e < 400; ++e) dt.FA[f][e] = T(0);
+            for (int e = 0; e < 200; ++e) dt.FU[f][e] = T(0);
+            for (int r = 0; r < 10; ++r)
+                for (int c = 0; c < 10; ++c) {
+                    dt.FA[f][20 * tab.fn[f][r] + tab.fn[f][c]] = (T)tab.F[f][10 * r + c];
+                    dt.FU[f][10 * tab.fn[f][r] + c] = (T)tab.F[f][10 * r + c];
+                }
+        }
         P3Dev<T> *tp = nullptr;
         if ((s = upload(d, &tp, &dt, sizeof(dt))) != TF_OK) return s;
         d.p3tab = tp;
