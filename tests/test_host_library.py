@@ -203,3 +203,35 @@ def test_python_structs_match_the_c_header(tmp_path):
         for fname, _ in py._fields_:
             assert got[(cname, fname)] == getattr(py, fname).offset, (cname, fname)
 
+
+def test_third_order_element_tables_exact(tmp_path):
+    """The host-built tables of the third-order kernels (csrc/p3_tables.cpp) against exact
+    monomial integration in rational arithmetic: integrals, mass, streaming and face tables."""
+    import subprocess
+
+    from p2_checks import face_nodes, tables
+
+    src = tmp_path / "t.cpp"
+    src.write_text(
+        '#include <cstdio>\n#include "tf_internal.h"\nint main() {\n'
+        '  tf::P3Tables t; tf::p3_element_tables(t);\n'
+        '  for (int i = 0; i < 20; ++i) std::printf("%.17g\\n", t.p[i]);\n'
+        '  for (int i = 0; i < 400; ++i) std::printf("%.17g\\n", t.M[i]);\n'
+        '  for (int k = 0; k < 4; ++k) for (int i = 0; i < 400; ++i) std::printf("%.17g\\n", t.C[k][i]);\n'
+        '  for (int f = 0; f < 4; ++f) for (int r = 0; r < 10; ++r) std::printf("%d\\n", t.fn[f][r]);\n'
+        '  for (int f = 0; f < 4; ++f) for (int r = 0; r < 100; ++r) std::printf("%.17g\\n", t.F[f][r]);\n'
+        '  return 0; }\n')
+    exe = tmp_path / "t"
+    csrc = os.path.join(ROOT, "paper_2510_11513_gb300", "csrc")
+    subprocess.check_call(["g++", "-std=c++17", f"-I{csrc}", f"-I{os.path.join(ROOT, 'include')}", "-I/usr/local/cuda/include",
+                           str(src), os.path.join(csrc, "p3_tables.cpp"), "-o", str(exe)])
+    v = np.array([float(x) for x in subprocess.check_output([str(exe)]).split()])
+    p, M, Dk, F = tables(3)
+    assert np.allclose(v[:20], p, rtol=0, atol=1e-15)
+    assert np.allclose(v[20:420].reshape(20, 20), M, rtol=0, atol=1e-15)
+    assert np.allclose(v[420:2020].reshape(4, 20, 20), Dk, rtol=0, atol=1e-14)
+    fn = v[2020:2060].astype(int).reshape(4, 10)
+    Fg = v[2060:2460].reshape(4, 10, 10)
+    for f in range(4):
+        assert list(fn[f]) == face_nodes(f, 3)
+        assert np.allclose(Fg[f], F[f][np.ix_(face_nodes(f, 3), face_nodes(f, 3))], rtol=0, atol=1e-15)
