@@ -311,3 +311,49 @@ CONFIGS = {
     "layout": random_layout,
     "paper_context": paper_context_box,
 }
+
+
+# ------------------------------------------------------------------ hexahedra
+def twisted_hex_mesh(n: int, seed: int, jitter: float = 0.15, twist: float = 0.0):
+    """The n^3 hex box of `jittered_kuhn_mesh` (the same vertices and jitter draws) kept as
+    hexahedra and then twisted about the vertical line x = y = 1/2: a vertex at height z
+    turns by twist * z radians in the horizontal plane (twist = 0: no turn).
+
+    Returns (xyz [(n+1)^3, 3] float64, hexes [n^3, 8] int32).  Hex (i, j, k) has id
+    i + n*(j + n*k); its local vertex a + 2b + 4c (a, b, c in {0, 1}) is mesh vertex
+    (i + a, j + b, k + c).
+    """
+    xyz, _ = jittered_kuhn_mesh(n, seed, jitter)
+    if twist != 0.0:
+        t = twist * xyz[:, 2]
+        ct, sn = np.cos(t), np.sin(t)
+        x, y = xyz[:, 0] - 0.5, xyz[:, 1] - 0.5
+        xyz[:, 0] = 0.5 + (ct * x - sn * y)
+        xyz[:, 1] = 0.5 + (sn * x + ct * y)
+    n1 = n + 1
+    hk, hj, hi = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    v0 = (hi.ravel() + n1 * (hj.ravel() + n1 * hk.ravel())).astype(np.int64)
+    hexes = np.empty((n ** 3, 8), dtype=np.int64)
+    for v in range(8):
+        a, b, c = v & 1, (v >> 1) & 1, (v >> 2) & 1
+        hexes[:, v] = v0 + a + n1 * (b + n1 * c)
+    return xyz, hexes.astype(np.int32)
+
+
+def hex_problem(cfg, twist: float = 0.25):
+    """The same problem on trilinear hexahedra: the parent hexes of a tetrahedral
+    configuration above (same vertices before the twist, same material per hex, same
+    cross sections), twisted by `twist` radians over the box height.  Q becomes
+    [n^3][G][8]: every configuration here holds Q constant over a parent hex, and each
+    hex takes the mean of its six tetrahedra's nodal values."""
+    n = int(cfg["n"])
+    xyz, hexes = twisted_hex_mesh(n, int(cfg["seed"]), twist=twist)
+    G = int(cfg["n_groups"])
+    Qt = np.asarray(cfg["Q"], dtype=np.float64).reshape(n ** 3, 6, G, -1)
+    Q = np.repeat(Qt.mean(axis=(1, 3))[:, :, None], 8, axis=2)
+    out = dict(cfg)
+    out.update(xyz=xyz, hexes=hexes, element="hex", twist=twist,
+               cell_material=np.ascontiguousarray(np.asarray(cfg["cell_material"])[::6], dtype=np.int32),
+               Q=np.ascontiguousarray(Q), name=cfg.get("name", "") + f"_hex_twist{twist:g}")
+    out.pop("tets", None)
+    return out
