@@ -203,6 +203,31 @@ typedef struct {
 tf_status tf_mesh_create(int64_t n_vertices, const double *xyz, int64_t n_cells, const int32_t *tets,
                          tf_handle *out);
 
+/* Mesh of trilinear hexahedra (the element of the paper's twisted hex grids, Sec. 2).
+ * xyz: host [n_vertices][3] FP64; hexes: host [n_cells][8] vertex indices, local
+ * vertex a + 2b + 4c at the corner (a, b, c) of the reference cube [0,1]^3 (so
+ * 0-1, 0-2 and 0-4 are the edges at vertex 0).  The Jacobian determinant of the
+ * trilinear map must be positive at the 27 points of the {0, 1/2, 1}^3 lattice; a
+ * face (f = 2d + s, the reference face xi_d = s) is shared by at most two cells.
+ * Computes, exactly (polynomial integration, FP64): volumes; mass int b_i b_j;
+ * streaming int b_i d b_j / dx_d; face matrices int_f N_d b_k b_l over each face's
+ * four nodes (N the outward area-vector density, non-planar faces included); the
+ * integrated face area vectors (half the cross product of the face diagonals,
+ * outward), which classify faces (inflow iff Omega.Nbar_f < -1e-12 |Nbar_f|); face
+ * neighbours.  At most 2^26 - 1 cells.  Host-only: no CUDA call.
+ * Errors: TF_ERR_ARG, TF_ERR_MESH, TF_ERR_NOMEM.  Problems on such a mesh are not
+ * supported yet (tf_problem_create returns TF_ERR_ARG); tf_mesh_geometry,
+ * tf_mesh_hex_integrals and tf_graph_levels accept it. */
+tf_status tf_mesh_create_hex(int64_t n_vertices, const double *xyz, int64_t n_cells, const int32_t *hexes,
+                             tf_handle *out);
+
+/* Element integrals of a hexahedral mesh (host outputs; any may be NULL):
+ * mass [n_cells][8][8] = int b_i b_j; grad [n_cells][3][8][8] = int b_i d b_j / dx_d;
+ * face [n_cells][6][3][4][4] = int_f N_d b_k b_l, k and l the face-local nodes (the
+ * face's vertices in increasing local index).  Errors: TF_ERR_ARG (not a
+ * hexahedral mesh). */
+tf_status tf_mesh_hex_integrals(tf_handle mesh, double *mass, double *grad, double *face);
+
 /* Angular quadrature.  Either a product rule (omega == NULL): n_polar
  * Gauss-Legendre cosines times n_azimuthal azimuths (k + 1/2) 2 pi / n_azimuthal,
  * weights summing to 4 pi, direction index a = polar * n_azimuthal + azimuth;
@@ -263,7 +288,10 @@ tf_status tf_destroy(tf_handle h);
  * vol [n_cells]; normal [n_cells][4][3] area-weighted outward normal of the face
  * opposite local vertex f; nbr [n_cells][4] (-1 = boundary); nbr_node
  * [n_cells][4][4]: local index, in the neighbour across face f, of local vertex
- * i of the cell (-1 for i == f or a boundary face). */
+ * i of the cell (-1 for i == f or a boundary face).  For a hexahedral mesh
+ * (tf_mesh_create_hex): normal [n_cells][6][3] integrated outward area vectors;
+ * nbr [n_cells][6]; nbr_node [n_cells][6][4]: local index, in the neighbour, of
+ * face-local node k (-1 on the boundary). */
 tf_status tf_mesh_geometry(tf_handle mesh, int64_t *n_cells, int64_t *n_vertices, double *vol, double *normal,
                            int32_t *nbr, int32_t *nbr_node);
 
@@ -271,7 +299,7 @@ tf_status tf_mesh_geometry(tf_handle mesh, int64_t *n_cells, int64_t *n_vertices
 tf_status tf_quadrature_get(tf_handle quad, int32_t *n_dirs, double *omega, double *w);
 
 /* Host-only: face classification and t-levels for every direction (Sec. 2.1
- * buckets).  inflow [n_dirs][n_cells]: bit f set iff face f is inflow;
+ * buckets), tetrahedral or hexahedral mesh.  inflow [n_dirs][n_cells]: bit f set iff face f is inflow;
  * level [n_dirs][n_cells].  Either may be NULL.  Errors: TF_ERR_CYCLE. */
 tf_status tf_graph_levels(tf_handle mesh, tf_handle quad, uint8_t *inflow, int32_t *level);
 

@@ -104,6 +104,38 @@ tf_status tf_mesh_create(int64_t n_vertices, const double *xyz, int64_t n_cells,
     return TF_OK;
 }
 
+tf_status tf_mesh_create_hex(int64_t n_vertices, const double *xyz, int64_t n_cells, const int32_t *hexes,
+                             tf_handle *out)
+{
+    if (!out) return fail(TF_ERR_ARG, "tf_mesh_create_hex: out is NULL");
+    *out = nullptr;
+    if (n_vertices < 8 || n_cells < 1 || !xyz || !hexes)
+        return fail(TF_ERR_ARG, "tf_mesh_create_hex: empty mesh or NULL array");
+    if (n_vertices >= (int64_t(1) << 31) || n_cells >= (int64_t(1) << 26))
+        return fail(TF_ERR_ARG, "tf_mesh_create_hex: at most 2^31 - 1 vertices and 2^26 - 1 cells");
+    for (int64_t i = 0; i < 3 * n_vertices; ++i)
+        if (!std::isfinite(xyz[i])) return fail(TF_ERR_MESH, "tf_mesh_create_hex: non-finite coordinate");
+    Mesh *m = new (std::nothrow) Mesh();
+    if (!m) return fail(TF_ERR_NOMEM, "tf_mesh_create_hex: allocation failed");
+    tf_status s = build_hex_mesh(n_vertices, xyz, n_cells, hexes, *m);
+    if (s != TF_OK) {
+        delete m;
+        return s;
+    }
+    *out = reinterpret_cast<tf_handle>(static_cast<Object *>(m));
+    return TF_OK;
+}
+
+tf_status tf_mesh_hex_integrals(tf_handle mesh, double *mass, double *grad, double *face)
+{
+    Mesh *m = as<Mesh>(mesh, Kind::Mesh);
+    if (!m || m->nf != 6) return fail(TF_ERR_ARG, "tf_mesh_hex_integrals: not a hexahedral mesh handle");
+    if (mass) std::memcpy(mass, m->hmass.data(), sizeof(double) * 64 * m->nc);
+    if (grad) std::memcpy(grad, m->hgrad.data(), sizeof(double) * 192 * m->nc);
+    if (face) std::memcpy(face, m->hface.data(), sizeof(double) * 288 * m->nc);
+    return TF_OK;
+}
+
 tf_status tf_quadrature_create(int32_t n_polar, int32_t n_azimuthal, int32_t n_dirs, const double *omega,
                                const double *w, tf_handle *out)
 {
@@ -148,6 +180,9 @@ tf_status tf_problem_create(tf_handle mesh, tf_handle quad, int32_t n_groups, in
     Mesh *m = as<Mesh>(mesh, Kind::Mesh);
     Quad *q = as<Quad>(quad, Kind::Quad);
     if (!m || !q) return fail(TF_ERR_ARG, "tf_problem_create: mesh or quadrature handle invalid");
+    if (m->nf != 4)
+        return fail(TF_ERR_ARG, "tf_problem_create: hexahedral meshes have host geometry and sweep graphs "
+                                "(tf_mesh_hex_integrals, tf_graph_levels) but no device sweep");
     if (n_groups < 1 || n_groups > 1024 || n_materials < 1)
         return fail(TF_ERR_ARG, "tf_problem_create: need 1 <= n_groups <= 1024 and n_materials >= 1");
     if (!cell_material || !sigma_t || !sigma_s || !Q) return fail(TF_ERR_ARG, "tf_problem_create: NULL input array");
@@ -277,11 +312,12 @@ tf_status tf_mesh_geometry(tf_handle mesh, int64_t *n_cells, int64_t *n_vertices
     if (!m) return fail(TF_ERR_ARG, "tf_mesh_geometry: not a mesh handle");
     if (n_cells) *n_cells = m->nc;
     if (n_vertices) *n_vertices = m->nv;
+    const int64_t nf = m->nf;
     if (vol) std::memcpy(vol, m->vol.data(), sizeof(double) * m->nc);
-    if (normal) std::memcpy(normal, m->normal.data(), sizeof(double) * 12 * m->nc);
-    if (nbr) std::memcpy(nbr, m->nbr.data(), sizeof(int32_t) * 4 * m->nc);
+    if (normal) std::memcpy(normal, m->normal.data(), sizeof(double) * 3 * nf * m->nc);
+    if (nbr) std::memcpy(nbr, m->nbr.data(), sizeof(int32_t) * nf * m->nc);
     if (nbr_node)
-        for (int64_t i = 0; i < 16 * m->nc; ++i) nbr_node[i] = m->nbr_node[i];
+        for (int64_t i = 0; i < 4 * nf * m->nc; ++i) nbr_node[i] = m->nbr_node[i];
     return TF_OK;
 }
 

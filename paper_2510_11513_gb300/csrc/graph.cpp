@@ -19,11 +19,11 @@ namespace tf {
 namespace {
 
 // inflow iff Omega . N_f < -1e-12 |N_f|, dot product as ((Ox Nx + Oy Ny) + Oz Nz)
-inline uint8_t inflow_mask(const double *O, const double *N4)
+inline uint8_t inflow_mask(const double *O, const double *Nc, int nf)
 {
     uint8_t m = 0;
-    for (int f = 0; f < 4; ++f) {
-        const double *N = N4 + 3 * f;
+    for (int f = 0; f < nf; ++f) {
+        const double *N = Nc + 3 * f;
         const double s = (O[0] * N[0] + O[1] * N[1]) + O[2] * N[2];
         const double eps = 1e-12 * std::sqrt((N[0] * N[0] + N[1] * N[1]) + N[2] * N[2]);
         if (s < -eps) m |= (uint8_t)(1u << f);
@@ -36,22 +36,23 @@ bool levels_one(const Mesh &m, const uint8_t *mask, int32_t *level, std::vector<
                 std::vector<int32_t> &queue)
 {
     const int64_t nc = m.nc;
+    const int nf = m.nf;
     indeg.resize(nc);
     queue.resize(nc);
     int64_t tail = 0;
     for (int64_t c = 0; c < nc; ++c) {
         int d = 0;
-        for (int f = 0; f < 4; ++f) d += ((mask[c] >> f) & 1) && m.nbr[4 * c + f] >= 0;
+        for (int f = 0; f < nf; ++f) d += ((mask[c] >> f) & 1) && m.nbr[nf * c + f] >= 0;
         indeg[c] = d;
         level[c] = 0;
         if (d == 0) queue[tail++] = (int32_t)c;
     }
     for (int64_t head = 0; head < tail; ++head) {
         const int32_t c = queue[head];
-        for (int f = 0; f < 4; ++f) {
-            const int32_t n = m.nbr[4 * c + f];
+        for (int f = 0; f < nf; ++f) {
+            const int32_t n = m.nbr[nf * c + f];
             if (n < 0) continue;
-            if (!((mask[n] >> m.nbr_face[4 * c + f]) & 1)) continue;  // n is not downwind of c
+            if (!((mask[n] >> m.nbr_face[nf * c + f]) & 1)) continue;  // n is not downwind of c
             level[n] = std::max(level[n], level[c] + 1);
             if (--indeg[n] == 0) queue[tail++] = n;
         }
@@ -80,7 +81,7 @@ tf_status classify_and_level(const Mesh &m, const Quad &q, uint8_t *inflow, int3
     run_parallel(q.D, [&](int32_t a) {
         std::vector<uint8_t> mask(m.nc);
         std::vector<int32_t> lev(m.nc), indeg, queue;
-        for (int64_t c = 0; c < m.nc; ++c) mask[c] = inflow_mask(&q.omega[3 * a], &m.normal[12 * c]);
+        for (int64_t c = 0; c < m.nc; ++c) mask[c] = inflow_mask(&q.omega[3 * a], &m.normal[3 * m.nf * c], m.nf);
         if (!levels_one(m, mask.data(), lev.data(), indeg, queue)) cycle = true;
         if (inflow) std::copy(mask.begin(), mask.end(), inflow + (size_t)a * m.nc);
         if (level) std::copy(lev.begin(), lev.end(), level + (size_t)a * m.nc);
@@ -93,7 +94,7 @@ namespace {
 
 struct DirTasks {
     int32_t levels = 0;
-    std::vector<uint32_t> cells;       // (cell << 4) | mask, in task order
+    std::vector<uint32_t> cells;       // (cell << shift) | mask, in task order
     std::vector<uint32_t> cell_begin;  // per task, local into cells
     std::vector<uint16_t> ncell;
     std::vector<int32_t> level;
@@ -107,9 +108,10 @@ struct DirTasks {
 void build_direction(const Mesh &m, const double *O, int32_t B, DirTasks &out)
 {
     const int64_t nc = m.nc;
+    const int nf = m.nf, sh = nf == 6 ? 6 : 4;
     std::vector<uint8_t> mask(nc);
     std::vector<int32_t> lev(nc), indeg, queue;
-    for (int64_t c = 0; c < nc; ++c) mask[c] = inflow_mask(O, &m.normal[12 * c]);
+    for (int64_t c = 0; c < nc; ++c) mask[c] = inflow_mask(O, &m.normal[3 * nf * c], nf);
     if (!levels_one(m, mask.data(), lev.data(), indeg, queue)) {
         out.ok = false;
         return;
@@ -141,7 +143,7 @@ void build_direction(const Mesh &m, const double *O, int32_t B, DirTasks &out)
             for (int64_t i = s; i < e; ++i) {
                 const int32_t c = order[i];
                 block_of[c] = id;
-                out.cells[i] = ((uint32_t)c << 4) | mask[c];
+                out.cells[i] = ((uint32_t)c << sh) | mask[c];
             }
         }
     }
@@ -153,19 +155,19 @@ void build_direction(const Mesh &m, const double *O, int32_t B, DirTasks &out)
         // upwind blocks: neighbours across interior inflow faces
         tmp.clear();
         for (uint32_t i = out.cell_begin[b]; i < out.cell_begin[b] + out.ncell[b]; ++i) {
-            const int32_t c = (int32_t)(out.cells[i] >> 4);
-            for (int f = 0; f < 4; ++f)
-                if (((mask[c] >> f) & 1) && m.nbr[4 * c + f] >= 0) tmp.push_back(block_of[m.nbr[4 * c + f]]);
+            const int32_t c = (int32_t)(out.cells[i] >> sh);
+            for (int f = 0; f < nf; ++f)
+                if (((mask[c] >> f) & 1) && m.nbr[nf * c + f] >= 0) tmp.push_back(block_of[m.nbr[nf * c + f]]);
         }
         std::sort(tmp.begin(), tmp.end());
         out.indeg[b] = (int32_t)(std::unique(tmp.begin(), tmp.end()) - tmp.begin());
         // downwind blocks: neighbours whose matching face is inflow
         tmp.clear();
         for (uint32_t i = out.cell_begin[b]; i < out.cell_begin[b] + out.ncell[b]; ++i) {
-            const int32_t c = (int32_t)(out.cells[i] >> 4);
-            for (int f = 0; f < 4; ++f) {
-                const int32_t n = m.nbr[4 * c + f];
-                if (n >= 0 && ((mask[n] >> m.nbr_face[4 * c + f]) & 1)) tmp.push_back(block_of[n]);
+            const int32_t c = (int32_t)(out.cells[i] >> sh);
+            for (int f = 0; f < nf; ++f) {
+                const int32_t n = m.nbr[nf * c + f];
+                if (n >= 0 && ((mask[n] >> m.nbr_face[nf * c + f]) & 1)) tmp.push_back(block_of[n]);
             }
         }
         std::sort(tmp.begin(), tmp.end());
@@ -187,7 +189,9 @@ void build_direction(const Mesh &m, const double *O, int32_t B, DirTasks &out)
 tf_status build_task_graph(const Mesh &m, const Quad &q, int32_t B, TaskGraph &g)
 {
     if (B < 1 || B > 4096) return fail(TF_ERR_ARG, "cells_per_task must be in [1, 4096]");
-    if (m.nc >= (int64_t(1) << 28)) return fail(TF_ERR_ARG, "mesh too large: at most 2^28 - 1 cells");
+    const int sh = m.nf == 6 ? 6 : 4;
+    if (m.nc >= (int64_t(1) << (32 - sh)))
+        return fail(TF_ERR_ARG, "mesh too large: at most 2^" + std::to_string(32 - sh) + " - 1 cells");
     std::vector<DirTasks> per(q.D);
     try {
         run_parallel(q.D, [&](int32_t a) { build_direction(m, &q.omega[3 * a], B, per[a]); });
@@ -198,6 +202,7 @@ tf_status build_task_graph(const Mesh &m, const Quad &q, int32_t B, TaskGraph &g
         if (!d.ok) return fail(TF_ERR_CYCLE, "graph: a direction's dependency graph has a cycle");
     g.D = q.D;
     g.cells_per_task = B;
+    g.cell_shift = sh;
     g.dir_task_begin.assign(q.D + 1, 0);
     g.dir_levels.resize(q.D);
     int64_t T = 0, E = 0;

@@ -25,18 +25,27 @@ struct Object {
     std::atomic<int32_t> refs{1};
 };
 
-// Host geometry of a tetrahedral mesh (FP64).
+// Host geometry of a mesh of tetrahedra (nf = 4) or trilinear hexahedra (nf = 6), FP64.
 struct Mesh : Object {
     Mesh() : Object(Kind::Mesh) {}
     int64_t nc = 0, nv = 0;
+    int32_t nf = 4;                 // faces per cell
     std::vector<double> xyz;        // [nv][3]
-    std::vector<int32_t> tets;      // [nc][4]
+    std::vector<int32_t> tets;      // [nc][4]     (tetrahedra)
+    std::vector<int32_t> hexes;     // [nc][8]     (hexahedra; local vertex a + 2b + 4c at reference corner (a, b, c))
     std::vector<double> vol;        // [nc]
-    std::vector<double> grad;       // [nc][4][3]  gradient of basis b_j
-    std::vector<double> normal;     // [nc][4][3]  area-weighted outward normal of face f (opposite vertex f)
-    std::vector<int32_t> nbr;       // [nc][4]
-    std::vector<int8_t> nbr_face;   // [nc][4]     face index of this face inside the neighbour
-    std::vector<int8_t> nbr_node;   // [nc][4][4]  neighbour-local index of local vertex i on face f (-1 if none)
+    std::vector<double> grad;       // [nc][4][3]  gradient of basis b_j (tetrahedra)
+    std::vector<double> normal;     // [nc][nf][3] area-weighted outward normal of face f (tetrahedra: opposite
+                                    //             vertex f; hexahedra: integrated over the face xi_d = s, f = 2d + s)
+    std::vector<int32_t> nbr;       // [nc][nf]
+    std::vector<int8_t> nbr_face;   // [nc][nf]    face index of this face inside the neighbour
+    std::vector<int8_t> nbr_node;   // tetrahedra: [nc][4][4] neighbour-local index of local vertex i on face f
+                                    // (-1 if none); hexahedra: [nc][6][4] of face-local node k
+    // hexahedral element integrals (exact): M = int b_i b_j, G[d] = int b_i d b_j/dx_d,
+    // F[f][d][k][l] = int_f N_d b_k b_l over face-local nodes (N the outward area-vector density)
+    std::vector<double> hmass;      // [nc][8][8]
+    std::vector<double> hgrad;      // [nc][3][8][8]
+    std::vector<double> hface;      // [nc][6][3][4][4]
 };
 
 struct Quad : Object {
@@ -47,6 +56,9 @@ struct Quad : Object {
 };
 
 tf_status build_mesh(int64_t nv, const double *xyz, int64_t nc, const int32_t *tets, Mesh &m);
+tf_status build_hex_mesh(int64_t nv, const double *xyz, int64_t nc, const int32_t *hexes, Mesh &m);
+// local vertex of face-local node k (0..3) of hexahedral face f (0..5)
+int hex_face_node(int f, int k);
 tf_status build_quadrature(int32_t n_polar, int32_t n_az, Quad &q);
 
 // Per-direction sweep graph and cell-block tasks.
@@ -65,7 +77,8 @@ struct TaskGraph {
     std::vector<int32_t> task_blevel;      // [T]   longest path (in t-levels) from the task to a sink
     std::vector<uint64_t> down_begin;      // [T+1] into down_list
     std::vector<uint32_t> down_list;       // downwind task ids (global)
-    std::vector<uint32_t> cell_list;       // (cell << 4) | inflow mask, [D * nc]
+    std::vector<uint32_t> cell_list;       // (cell << cell_shift) | inflow mask, [D * nc]
+    int32_t cell_shift = 4;                // 4 for tetrahedra, 6 for hexahedra (one mask bit per face)
     int64_t T() const { return (int64_t)task_ncell.size(); }
 };
 

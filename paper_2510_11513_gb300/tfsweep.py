@@ -26,7 +26,7 @@ TF_PHI_PAIR, TF_PHI_DADD = 0, 1
 TF_SCHED_AMT, TF_SCHED_BSP, TF_SCHED_BSP_LAUNCH = 0, 1, 2
 
 SYMBOLS = (
-    "tf_options_default", "tf_mesh_create", "tf_quadrature_create", "tf_problem_create", "tf_sweep",
+    "tf_options_default", "tf_mesh_create", "tf_mesh_create_hex", "tf_mesh_hex_integrals", "tf_quadrature_create", "tf_problem_create", "tf_sweep",
     "tf_source_iterate", "tf_destroy", "tf_mesh_geometry", "tf_quadrature_get", "tf_graph_levels",
     "tf_problem_psi", "tf_problem_stats", "tf_status_string", "tf_last_error", "tf_integrated_flux_noalloc",
     # include/tflearn.h
@@ -102,6 +102,8 @@ def load(build_if_missing: bool = True):
     lib.tf_options_default.argtypes = [C.POINTER(tf_options)]
     lib.tf_options_default.restype = None
     lib.tf_mesh_create.argtypes = [i64, vp, i64, vp, C.POINTER(H)]
+    lib.tf_mesh_create_hex.argtypes = [i64, vp, i64, vp, C.POINTER(H)]
+    lib.tf_mesh_hex_integrals.argtypes = [H, vp, vp, vp]
     lib.tf_quadrature_create.argtypes = [i32, i32, i32, vp, vp, C.POINTER(H)]
     lib.tf_problem_create.argtypes = [H, H, i32, i32, vp, vp, vp, vp, vp, vp, C.POINTER(tf_options), C.POINTER(H)]
     lib.tf_sweep.argtypes = [C.POINTER(H), i32, C.POINTER(vp), C.POINTER(vp), vp]
@@ -192,6 +194,23 @@ def tf_mesh_create(xyz, tets):
     return h
 
 
+def tf_mesh_create_hex(xyz, hexes):
+    xyz = np.ascontiguousarray(xyz, dtype=np.float64)
+    hexes = np.ascontiguousarray(hexes, dtype=np.int32)
+    h = C.c_void_p()
+    _check(load().tf_mesh_create_hex(xyz.shape[0], _ptr(xyz), hexes.shape[0], _ptr(hexes), C.byref(h)),
+           "tf_mesh_create_hex")
+    return h
+
+
+def tf_mesh_hex_integrals(mesh, n_cells):
+    out = dict(mass=np.zeros((n_cells, 8, 8)), grad=np.zeros((n_cells, 3, 8, 8)),
+               face=np.zeros((n_cells, 6, 3, 4, 4)))
+    _check(load().tf_mesh_hex_integrals(mesh, _ptr(out["mass"]), _ptr(out["grad"]), _ptr(out["face"])),
+           "tf_mesh_hex_integrals")
+    return out
+
+
 def tf_quadrature_create(n_polar=0, n_azimuthal=0, omega=None, w=None):
     h = C.c_void_p()
     if omega is not None:
@@ -242,12 +261,13 @@ def tf_destroy(h):
     return _check(load().tf_destroy(h), "tf_destroy")
 
 
-def tf_mesh_geometry(mesh):
+def tf_mesh_geometry(mesh, n_faces=4):
+    """n_faces: 4 for a tetrahedral mesh, 6 for a hexahedral one."""
     nc, nv = C.c_int64(), C.c_int64()
     _check(load().tf_mesh_geometry(mesh, C.byref(nc), C.byref(nv), None, None, None, None), "tf_mesh_geometry")
-    C_ = nc.value
-    out = dict(vol=np.zeros(C_), normal=np.zeros((C_, 4, 3)), nbr=np.zeros((C_, 4), np.int32),
-               nbr_node=np.zeros((C_, 4, 4), np.int32))
+    C_, nf = nc.value, int(n_faces)
+    out = dict(vol=np.zeros(C_), normal=np.zeros((C_, nf, 3)), nbr=np.zeros((C_, nf), np.int32),
+               nbr_node=np.zeros((C_, nf, 4), np.int32))
     _check(load().tf_mesh_geometry(mesh, None, None, _ptr(out["vol"]), _ptr(out["normal"]), _ptr(out["nbr"]),
                                    _ptr(out["nbr_node"])), "tf_mesh_geometry")
     return out
@@ -458,6 +478,21 @@ class Mesh(_Handle):
 
     def geometry(self):
         return tf_mesh_geometry(self.h)
+
+
+class HexMesh(_Handle):
+    """Trilinear hexahedra (tf_mesh_create_hex): host geometry, element integrals and sweep graphs."""
+
+    def __init__(self, xyz, hexes):
+        self.h = tf_mesh_create_hex(xyz, hexes)
+        self.n_cells = int(np.asarray(hexes).shape[0])
+        self.n_vertices = int(np.asarray(xyz).shape[0])
+
+    def geometry(self):
+        return tf_mesh_geometry(self.h, 6)
+
+    def integrals(self):
+        return tf_mesh_hex_integrals(self.h, self.n_cells)
 
 
 class Quadrature(_Handle):
