@@ -5,7 +5,9 @@ code): reference values that later changes to the oracle or the library must kee
     source in the central hexes): source iteration to the max-norm test 1e-10, the
     iteration count and the integrated flux of Eq. (3) per group;
   * one transport step from a seeded flux for the second- and third-order elements on
-    a 2^3-hex box: the integrated flux per group and a nodal checksum.
+    a 2^3-hex box: the integrated flux per group and a nodal checksum;
+  * the same 8^3 box as trilinear hexahedra (orthogonal grid twisted by 0.25 rad):
+    source iteration to 1e-10, the iteration count and the integrated flux per group.
 
 Run from the repository root:  python tests/golden/make_golden.py
 """
@@ -22,6 +24,7 @@ import oracle  # noqa: E402
 import workloads as W  # noqa: E402
 from oracle import p2 as o2  # noqa: E402
 from oracle import p3 as o3  # noqa: E402
+from oracle import q1hex as oh  # noqa: E402
 
 
 def main():
@@ -41,6 +44,12 @@ def main():
         out[f"order{order}_step"] = {"seed": 2510115130 + order, "integrated_flux": ig.tolist(),
                                      "checksum": float(np.sum(step * np.arange(1, step.size + 1).reshape(step.shape)
                                                               / step.size))}
+    hcfg = W.hex_problem(W.small_box(), twist=0.25)
+    Ph = oh.ProblemHex(hcfg)
+    phi, it, r = Ph.source_iterate(1e-10, 1000, threads=8)
+    ig, tot = Ph.integrated_flux(phi)
+    out["hex_small_box"] = {"workload": hcfg["name"], "twist": 0.25, "tol": 1e-10, "iterations": it, "residual": r,
+                            "integrated_flux": ig.tolist(), "integrated_total": tot}
     path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "oracle_regression.json")
     with open(path, "w") as f:
         json.dump(out, f, indent=1)

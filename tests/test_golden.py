@@ -10,6 +10,7 @@ import oracle
 import workloads as W
 from oracle import p2 as o2
 from oracle import p3 as o3
+from oracle import q1hex as oh
 
 GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "oracle_regression.json")))
 
@@ -41,6 +42,15 @@ def test_oracle_reproduces_higher_order_step(order):
     assert np.allclose(ig, g["integrated_flux"], rtol=1e-12, atol=0)
     cs = float(np.sum(step * np.arange(1, step.size + 1).reshape(step.shape) / step.size))
     assert abs(cs - g["checksum"]) <= 1e-12 * abs(g["checksum"])
+
+
+def test_oracle_reproduces_hex_small_box():
+    g = GOLD["hex_small_box"]
+    P = oh.ProblemHex(W.hex_problem(W.small_box(), twist=g["twist"]))
+    phi, it, r = P.source_iterate(g["tol"], 1000, threads=4)
+    ig, _ = P.integrated_flux(phi)
+    assert it == g["iterations"]
+    assert np.allclose(ig, g["integrated_flux"], rtol=1e-12, atol=0)
 
 
 @pytest.mark.gpu
