@@ -155,12 +155,19 @@ def whole_job_grind(ms_per_step, units_per_rank, world):
     return ms_per_step * 1e6 / (units_per_rank * world)
 
 
-def cpu_oracle_sample(cfg, n_dirs=None, threads=None):
+def cpu_oracle_sample(cfg, n_dirs=None, threads=None, groups=16):
     """Oracle (plain FP64 CPU) grind time on a bounded sample: `n_dirs` directions of the
-    workload's quadrature (all cells, all groups), one source update + sweep."""
+    workload's quadrature and its first `groups` energy groups (all cells), one source
+    update + sweep.  Each oracle thread sweeps whole directions, so the wall time of a
+    sample is about one direction's sweep of the sampled groups."""
     import oracle
     threads = threads or os.cpu_count() or 1
     n_dirs = n_dirs or threads
+    G = int(cfg["n_groups"])
+    if groups and groups < G:
+        cfg = dict(cfg, n_groups=groups, sigma_t=np.ascontiguousarray(cfg["sigma_t"][:, :groups]),
+                   sigma_s=np.ascontiguousarray(cfg["sigma_s"][:, :groups, :groups]),
+                   Q=np.ascontiguousarray(cfg["Q"][:, :groups]))
     om, w = oracle.product_quadrature(cfg["n_polar"], cfg["n_azimuthal"])
     D = om.shape[0]
     idx = np.linspace(0, D - 1, n_dirs).round().astype(int)
@@ -181,7 +188,7 @@ def cpu_oracle_sample(cfg, n_dirs=None, threads=None):
     dt = time.perf_counter() - t0
     units = P.C * P.G * n_dirs
     return {"value": dt / units * 1e9, "unit": UNIT, "cores": used, "kind": "oracle",
-            "sample": f"{n_dirs} of {D} directions x {P.C} cells x {P.G} groups, one source update + sweep, "
+            "sample": f"{n_dirs} of {D} directions x {P.C} cells x {P.G} of {G} groups, one source update + sweep, "
                       f"{dt:.1f} s wall on {used} threads"}
 
 
@@ -209,7 +216,7 @@ def run_reference(args):
     threads = os.cpu_count() or 1
     # warm-up steps (untimed), then timed steps; each step is a bounded sample
     for _ in range(args.warmup):
-        cpu_oracle_sample(cfg, n_dirs=max(1, threads // 4), threads=threads)
+        cpu_oracle_sample(cfg, n_dirs=threads, threads=threads, groups=2)
     vals = []
     t0 = time.perf_counter()
     last = None
