@@ -1427,7 +1427,7 @@ tf_status device_create(Problem &p, const int32_t *cell_material, const double *
         d.ppl = (int)L.ppl;
     }
     if (d.nodemajor()) {
-        // the node-major source update stages min(256 / G, 1) cells' flux in shared memory:
+        // the node-major source update stages max(1, 256 / G) cells' flux in shared memory:
         // above 48 KB (large G) the kernel needs the opt-in limit
         const size_t smem2 = (size_t)std::max(1, 256 / d.G) * d.G * d.nb * d.tsize;
         const void *sfn = d.nb == 8    ? (d.fp64 ? (const void *)source_ho_kernel<double, 8> : (const void *)source_ho_kernel<float, 8>)
