@@ -143,3 +143,112 @@ __device__ __forceinline__ void run_task_hex(const SweepArgs<T> &A, uint4 ti, in
         hex_unit(A, geo, __ldg(A.cells + ti.x + k), g, ox, oy, oz, psi_dir);
     }
 }
+
+// Shared variant (G >= 8): per batch of 32 (cell, group) units the warp first forms, for
+// each of the at most HEX_NCB cells the batch touches, the group-independent parts once in
+// its shared memory -- the face matrices W_f = -Omega.F_f, the streaming-plus-inflow-face
+// matrix S = sum_d Omega_d G_d + sum_{f inflow} W_f and M -- then every lane adds sigma_t M,
+// forms its right-hand side and eliminates.  Per warp: HEX_NCB x (96 + 64 + 64) values.
+constexpr int HEX_NCB = 5;  // cells one batch of 32 units can touch when G >= 8
+__host__ __device__ constexpr uint32_t hex_stage_bytes(int tsize) { return (uint32_t)(HEX_NCB * 224 * tsize); }
+
+// face-local index of vertex v on face f (v on f)
+__device__ __forceinline__ int hex_local(int f, int v)
+{
+    const int d = f >> 1;
+    const int lo = d == 0 ? 1 : 0, hi = d == 2 ? 1 : 2;
+    return ((v >> lo) & 1) | (((v >> hi) & 1) << 1);
+}
+
+template <class T>
+__device__ __forceinline__ void run_task_hex_shared(const SweepArgs<T> &A, uint4 ti, int lane, T ox, T oy, T oz,
+                                                    size_t psi_dir, unsigned char *wsm)
+{
+    const HexGeo<T> *geo = reinterpret_cast<const HexGeo<T> *>(A.geo2);
+    T *Ws = reinterpret_cast<T *>(wsm);      // [HEX_NCB][6][16]
+    T *Ss = Ws + HEX_NCB * 96;               // [HEX_NCB][64]
+    T *Ms = Ss + HEX_NCB * 64;               // [HEX_NCB][64]
+    const int G = A.G;
+    const uint32_t ncell = ti.y & 0xffffu;
+    const uint32_t nu = ncell * (uint32_t)G;
+    T *psi = reinterpret_cast<T *>(A.psi);
+    for (uint32_t u0 = 0; u0 < nu; u0 += 32) {
+        const uint32_t k0 = u0 / (uint32_t)G;
+        const uint32_t k1 = min(ncell - 1u, (u0 + 31u) / (uint32_t)G);
+        const int nc = (int)(k1 - k0 + 1u);  // <= HEX_NCB for G >= 8 (the host picks this path only then)
+        if (nc > HEX_NCB) {
+            if (lane == 0) atomicCAS(&A.ctrl->error, 0, (int)TF_ERR_DEVICE);
+            return;
+        }
+        __syncwarp();  // the previous batch is done with the shared tables
+        for (int e = lane; e < nc * 96; e += 32) {
+            const int kk = e / 96, r = e - kk * 96;  // r = 16 f + 4 k + l
+            const HexGeo<T> *cg = geo + (__ldg(A.cells + ti.x + k0 + kk) >> 6);
+            const T *F = &cg->F[r >> 4][0][r & 15];
+            Ws[e] = -(ox * __ldg(F) + oy * __ldg(F + 16) + oz * __ldg(F + 32));
+        }
+        __syncwarp();
+        for (int e = lane; e < nc * 64; e += 32) {
+            const int kk = e >> 6, ij = e & 63, i = ij >> 3, j = ij & 7;
+            const uint32_t entry = __ldg(A.cells + ti.x + k0 + kk);
+            const HexGeo<T> *cg = geo + (entry >> 6);
+            const uint32_t mask = entry & 63u;
+            T s = ox * __ldg(&cg->Gd[0][ij]) + oy * __ldg(&cg->Gd[1][ij]) + oz * __ldg(&cg->Gd[2][ij]);
+            for (int f = 0; f < 6; ++f) {
+                const int d = f >> 1, sd = f & 1;
+                if (((mask >> f) & 1u) && ((i >> d) & 1) == sd && ((j >> d) & 1) == sd)
+                    s += Ws[kk * 96 + 16 * f + 4 * hex_local(f, i) + hex_local(f, j)];
+            }
+            Ss[e] = s;
+            Ms[e] = __ldg(&cg->M[ij]);
+        }
+        __syncwarp();
+        const uint32_t u = u0 + (uint32_t)lane;
+        if (u < nu) {
+            const uint32_t k = u / (uint32_t)G;
+            const int g = (int)(u - k * (uint32_t)G), kk = (int)(k - k0);
+            const uint32_t entry = __ldg(A.cells + ti.x + k);
+            const uint32_t c = entry >> 6, mask = entry & 63u;
+            const HexGeo<T> *cg = geo + c;
+            const T sig = __ldg(A.sigma_t + (size_t)__ldg(&cg->mat) * G + g);
+            const T *qc = reinterpret_cast<const T *>(A.q) + (size_t)c * 8 * G + g;
+            const T *S = Ss + kk * 64, *M = Ms + kk * 64, *W = Ws + kk * 96;
+            T a[8][8], b[8], x[8], qv[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) qv[j] = __ldg(qc + (size_t)j * G);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                T bi = T(0);
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const T m = M[8 * i + j];
+                    a[i][j] = S[8 * i + j] + sig * m;
+                    bi += m * qv[j];
+                }
+                b[i] = bi;
+            }
+#pragma unroll
+            for (int f = 0; f < 6; ++f) {
+                if (!((mask >> f) & 1u)) continue;
+                const int32_t n = __ldg(&cg->nbr[f]);
+                if (n < 0) continue;  // vacuum boundary: no inflow
+                const uint32_t nm = __ldg(&cg->nmap[f]);
+                const T *up = psi + (psi_dir + (size_t)n) * 8 * (size_t)G + g;
+                T uv[4];
+#pragma unroll
+                for (int l = 0; l < 4; ++l) uv[l] = __ldcg(up + (size_t)((nm >> (4 * l)) & 15u) * G);
+#pragma unroll
+                for (int kf = 0; kf < 4; ++kf) {
+                    T t = T(0);
+#pragma unroll
+                    for (int l = 0; l < 4; ++l) t += W[16 * f + 4 * kf + l] * uv[l];
+                    b[hex_node(f, kf)] += t;
+                }
+            }
+            hex_solve8(a, b, x);
+            T *out = psi + (psi_dir + c) * 8 * (size_t)G + g;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) out[(size_t)i * G] = x[i];
+        }
+    }
+}

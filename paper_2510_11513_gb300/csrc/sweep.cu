@@ -1395,7 +1395,11 @@ tf_status device_create(Problem &p, const int32_t *cell_material, const double *
                            ((p2_stage_bytes(d.G) * 2 + 48 + 127) / 128 * 128) * d.wpc <= 227 * 1024;
     if (p2_staged) d.warp_smem = (p2_stage_bytes(d.G) * 2 + 48 + 127) / 128 * 128;
     if (d.order == 3) d.warp_smem = 0;  // four lanes per unit, systems in registers
-    d.mode = d.hex ? 8
+    // hexahedra: the group-independent matrices in shared memory once per cell when a batch of
+    // 32 units touches at most five cells (G >= 8); staging = 1 keeps every lane on its own
+    const bool hex_shared = d.hex && d.G >= 8 && p.opt.staging != 1;
+    if (d.hex) d.warp_smem = hex_shared ? (hex_stage_bytes((int)d.tsize) + 127u) / 128u * 128u : 0u;
+    d.mode = d.hex ? (hex_shared ? 9 : 8)
              : d.order == 3 ? 7
              : d.order == 2 ? (p2_staged ? 6 : 5)
              : d.paired  ? 3
@@ -1436,7 +1440,8 @@ tf_status device_create(Problem &p, const int32_t *cell_material, const double *
         if (smem2 > 48 * 1024) TF_CUDA(ensure_dyn_smem(sfn, (int)smem2));
     }
     const int dyn = (int)(d.warp_smem * d.wpc);
-    const void *kfn = d.mode == 8   ? (d.fp64 ? (const void *)sweep_kernel<double, 8> : (const void *)sweep_kernel<float, 8>)
+    const void *kfn = d.mode == 9   ? (d.fp64 ? (const void *)sweep_kernel<double, 9> : (const void *)sweep_kernel<float, 9>)
+                      : d.mode == 8 ? (d.fp64 ? (const void *)sweep_kernel<double, 8> : (const void *)sweep_kernel<float, 8>)
                       : d.mode == 7 ? (d.fp64 ? (const void *)sweep_kernel<double, 7> : (const void *)sweep_kernel<float, 7>)
                       : d.mode == 6 ? (const void *)sweep_kernel<float, 6>
                       : d.mode == 5 ? (d.fp64 ? (const void *)sweep_kernel<double, 5> : (const void *)sweep_kernel<float, 5>)
@@ -1790,7 +1795,9 @@ template <class T> tf_status launch_step(Problem &p, const double *phi_in, doubl
             if (d.mode == 6) sweep_kernel<T, 6><<<d.grid, 32 * d.wpc, dyn, st>>>(A);
         }
         if (d.mode == 3 || d.mode == 4 || d.mode == 6) {
-        } else if (d.mode == 8)
+        } else if (d.mode == 9)
+            sweep_kernel<T, 9><<<d.grid, 32 * d.wpc, dyn, st>>>(A);
+        else if (d.mode == 8)
             sweep_kernel<T, 8><<<d.grid, 32 * d.wpc, 0, st>>>(A);
         else if (d.mode == 7)
             sweep_kernel<T, 7><<<d.grid, 32 * d.wpc, dyn, st>>>(A);

@@ -1144,9 +1144,10 @@ __device__ __forceinline__ bool run_task_staged_any(const SweepArgs<T> &A, uint4
 // 5 = the second-order (ten-node) element, lanes over (cell, group) units,
 // 6 = the second-order element staged in shared memory (FP32, G a multiple of 32),
 // 7 = the third-order element, four lanes per unit with the system in registers,
-// 8 = trilinear hexahedra, lanes over (cell, group) units.
+// 8 = trilinear hexahedra, lanes over (cell, group) units,
+// 9 = trilinear hexahedra with the group-independent matrices formed once per cell in shared memory (G >= 8).
 template <class T, int MODE>
-__global__ void __launch_bounds__(128, MODE == 7 ? (sizeof(T) == 4 ? 3 : 2) : MODE == 5 ? 2 : MODE == 6 ? 3 : MODE == 4 ? 6 : MODE == 8 ? (sizeof(T) == 4 ? 3 : 2) : (sizeof(T) == 4 ? 4 : 3))
+__global__ void __launch_bounds__(128, MODE == 7 ? (sizeof(T) == 4 ? 3 : 2) : MODE == 5 ? 2 : MODE == 6 ? 3 : MODE == 4 ? 6 : MODE == 9 ? (sizeof(T) == 4 ? 4 : 2) : MODE == 8 ? (sizeof(T) == 4 ? 3 : 2) : (sizeof(T) == 4 ? 4 : 3))
     sweep_kernel(const SweepArgs<T> A)
 {
     const int lane = threadIdx.x & 31;
@@ -1258,6 +1259,8 @@ __global__ void __launch_bounds__(128, MODE == 7 ? (sizeof(T) == 4 ? 3 : 2) : MO
             run_task_p3(A, ti, lane, om.x, om.y, om.z, psi_dir, wsm);
         } else if constexpr (MODE == 8) {
             run_task_hex(A, ti, lane, om.x, om.y, om.z, psi_dir);
+        } else if constexpr (MODE == 9) {
+            run_task_hex_shared(A, ti, lane, om.x, om.y, om.z, psi_dir, wsm);
         } else {
             run_task_generic(A, ti, lane, om.x, om.y, om.z, psi_dir);
         }
