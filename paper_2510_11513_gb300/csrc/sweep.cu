@@ -1353,6 +1353,14 @@ tf_status device_create(Problem &p, const int32_t *cell_material, const double *
         d.lpc_shift = (int)L.lpc_shift;
         d.ppl = (int)L.ppl;
     }
+    if (d.order >= 2) {
+        // the node-major source update stages max(1, 256 / G) cells' flux in shared memory:
+        // above 48 KB (large G) the kernel needs the opt-in limit
+        const size_t smem2 = (size_t)std::max(1, 256 / d.G) * d.G * d.nb * d.tsize;
+        const void *sfn = d.nb == 20 ? (d.fp64 ? (const void *)source_ho_kernel<double, 20> : (const void *)source_ho_kernel<float, 20>)
+                                     : (d.fp64 ? (const void *)source_ho_kernel<double, 10> : (const void *)source_ho_kernel<float, 10>);
+        if (smem2 > 48 * 1024) TF_CUDA(ensure_dyn_smem(sfn, (int)smem2));
+    }
     const int dyn = (int)(d.warp_smem * d.wpc);
     const void *kfn = d.mode == 7   ? (d.fp64 ? (const void *)sweep_kernel<double, 7> : (const void *)sweep_kernel<float, 7>)
                       : d.mode == 6 ? (const void *)sweep_kernel<float, 6>
