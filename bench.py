@@ -303,12 +303,25 @@ def p2_flops_per_unit(prob, tf, order=2):
     return 1485.0 + 156.0 * n_in, n_in
 
 
+def hex_flops_per_unit(prob, tf):
+    """Algorithmic flops of one trilinear-hexahedron unit (an FMA counts 2): A = sum_d Omega_d
+    G_d + sigma_t M 512, b = M q 128, the 8 x 8 elimination 364 and back substitution 72;
+    per interior inflow face 128 (the 4 x 4 matrix -Omega.F_f 80, added into A 16, its face
+    term into b 32), per boundary inflow face 96 (no face term under vacuum)."""
+    inflow, _ = tf.tf_graph_levels(prob.mesh.h, prob.quad.h, prob.n_cells, prob.n_dirs)
+    nbr = prob.mesh.geometry()["nbr"]
+    interior = (nbr >= 0).astype(np.uint8)  # [C][6]
+    n_in = sum(float((((inflow >> f) & 1) * interior[None, :, f]).mean()) for f in range(6))
+    n_bd = sum(float((((inflow >> f) & 1) * (1 - interior[None, :, f])).mean()) for f in range(6))
+    return 1076.0 + 128.0 * n_in + 96.0 * n_bd, n_in
+
+
 def second_order_leg(tf, cfg, prec, local, stream, steps, torch, order=2):
     """A higher-order element (order 2: ten nodes, 3: twenty) on one workload: grind time
     of a source iteration and the sweep kernel's ALU roofline (bound by FP32 arithmetic:
     about 1,800 / 12,000 flops against 80-320 bytes per unit)."""
     dev = torch.device("cuda", local)
-    pr = tf.Problem.from_config(cfg, precision=prec, device=local, order=order)
+    pr = tf.Problem.from_config(cfg, precision=prec, device=local, order=1 if order == "hex" else order)
     ph = torch.zeros((pr.n_cells, pr.n_groups, pr.n_nodes), dtype=torch.float64, device=dev)
     pr.source_iterate(ph, 0.0, 1, stream=stream)
     st0 = pr.stats()
@@ -322,7 +335,7 @@ def second_order_leg(tf, cfg, prec, local, stream, steps, torch, order=2):
     st = pr.stats()
     ms = e0.elapsed_time(e1) / steps
     sweep_s = (st["cum_sweep_event_seconds"] - st0["cum_sweep_event_seconds"]) / steps
-    flops, n_in = p2_flops_per_unit(pr, tf, order)
+    flops, n_in = hex_flops_per_unit(pr, tf) if order == "hex" else p2_flops_per_unit(pr, tf, order)
     achieved = flops * pr.n_units / sweep_s / 1e12
     klabel = f"sweep_kernel<float, {st['kernel_mode']}>"
     out = {"workload": cfg["name"], "units_per_step": pr.n_units, "ms_per_step": ms,
@@ -487,6 +500,11 @@ def run_ours(args):
         # and the third-order element on the 16^3-hex workload (50 M units per step)
         line["third_order"] = second_order_leg(tf, W.order3(W.paper_context_box()), prec, local, stream, 2, torch,
                                                order=3)
+        # trilinear hexahedra: the paper's own 16^3 workload (256 directions, 10 groups) and the
+        # two-material box as a twisted hex grid (134 M units per step)
+        line["hexahedra"] = [second_order_leg(tf, W.paper_hex_box(), prec, local, stream, 3, torch, order="hex"),
+                             second_order_leg(tf, W.hex_problem(W.two_material_box()), prec, local, stream, 3, torch,
+                                              order="hex")]
     if not args.no_fp64_compare and prec == tf.TF_FP32:
         p64 = tf.Problem.from_config(cfg, precision=tf.TF_FP64, device=local, order=args.order)
         phi64 = torch.zeros((C, G, nodes), dtype=torch.float64, device=dev)

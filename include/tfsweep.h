@@ -215,9 +215,9 @@ tf_status tf_mesh_create(int64_t n_vertices, const double *xyz, int64_t n_cells,
  * integrated face area vectors (half the cross product of the face diagonals,
  * outward), which classify faces (inflow iff Omega.Nbar_f < -1e-12 |Nbar_f|); face
  * neighbours.  At most 2^26 - 1 cells.  Host-only: no CUDA call.
- * Errors: TF_ERR_ARG, TF_ERR_MESH, TF_ERR_NOMEM.  Problems on such a mesh are not
- * supported yet (tf_problem_create returns TF_ERR_ARG); tf_mesh_geometry,
- * tf_mesh_hex_integrals and tf_graph_levels accept it. */
+ * Errors: TF_ERR_ARG, TF_ERR_MESH, TF_ERR_NOMEM.  Problems on such a mesh take the
+ * trilinear element (opt->order 0 or 1), vacuum boundaries and no S1; their Q, phi
+ * and psi hold the eight vertex values of every cell ([n_cells][n_groups][8]). */
 tf_status tf_mesh_create_hex(int64_t n_vertices, const double *xyz, int64_t n_cells, const int32_t *hexes,
                              tf_handle *out);
 

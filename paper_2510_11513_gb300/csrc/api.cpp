@@ -180,9 +180,9 @@ tf_status tf_problem_create(tf_handle mesh, tf_handle quad, int32_t n_groups, in
     Mesh *m = as<Mesh>(mesh, Kind::Mesh);
     Quad *q = as<Quad>(quad, Kind::Quad);
     if (!m || !q) return fail(TF_ERR_ARG, "tf_problem_create: mesh or quadrature handle invalid");
-    if (m->nf != 4)
-        return fail(TF_ERR_ARG, "tf_problem_create: hexahedral meshes have host geometry and sweep graphs "
-                                "(tf_mesh_hex_integrals, tf_graph_levels) but no device sweep");
+    if (m->nf == 6 && (S1 || psi_inflow || (opt && opt->order > 1)))
+        return fail(TF_ERR_ARG, "tf_problem_create: hexahedral meshes take the trilinear element (order 0 or 1) "
+                                "with vacuum boundaries and no S1");
     if (n_groups < 1 || n_groups > 1024 || n_materials < 1)
         return fail(TF_ERR_ARG, "tf_problem_create: need 1 <= n_groups <= 1024 and n_materials >= 1");
     if (!cell_material || !sigma_t || !sigma_s || !Q) return fail(TF_ERR_ARG, "tf_problem_create: NULL input array");
@@ -222,6 +222,7 @@ tf_status tf_problem_create(tf_handle mesh, tf_handle quad, int32_t n_groups, in
     p->has_S1 = S1 != nullptr;
     p->has_inflow = psi_inflow != nullptr;
     int32_t B = p->opt.cells_per_task;
+    if (B < 0 && m->nf == 6) B = 0;  // the task-grain autotuner covers tetrahedra only
     if (B < 0) {
         tf_status st = autotune_cells_per_task(*m, *q, n_groups, n_materials, cell_material, sigma_t, sigma_s, Q, p->opt,
                                                &B, &p->tune);
@@ -244,6 +245,8 @@ tf_status tf_problem_create(tf_handle mesh, tf_handle quad, int32_t n_groups, in
         if (p->opt.order == 2) B = std::max(2, std::min(32, 256 / n_groups));
         // third order: a unit is a 20 x 20 solve, about 64 units per task
         if (p->opt.order == 3) B = std::max(2, std::min(16, 64 / n_groups));
+        // trilinear hexahedra: an 8 x 8 solve, about 256 units per task as the second order
+        if (m->nf == 6) B = std::max(2, std::min(32, 256 / n_groups));
         // Bulk-synchronous schedules: a bucket's tasks must cover the resident warps, and
         // most buckets hold fewer cells than the many-task grain assumes; a quarter of it
         // (at least 2 cells) took the least time over grains 1..64 on the 16^3-hex,

@@ -86,6 +86,12 @@ __device__ __forceinline__ bool exec_task(const SweepArgs<T> &A, unsigned task, 
     } else if constexpr (MODE == 7) {
         run_task_p3(A, ti, lane, om.x, om.y, om.z, psi_dir, wsm);
         return true;
+    } else if constexpr (MODE == 8) {
+        run_task_hex(A, ti, lane, om.x, om.y, om.z, psi_dir);
+        return true;
+    } else if constexpr (MODE == 9) {
+        run_task_hex_shared(A, ti, lane, om.x, om.y, om.z, psi_dir, wsm);
+        return true;
     } else {
         run_task_generic(A, ti, lane, om.x, om.y, om.z, psi_dir);
         return true;
@@ -98,7 +104,7 @@ __device__ __forceinline__ bool exec_task(const SweepArgs<T> &A, unsigned task, 
 // finished the bucket.  The time warps spend there is counted as wait time, the
 // time executing tasks as busy time.
 template <class T, int MODE>
-__global__ void __launch_bounds__(128, MODE == 7 ? (sizeof(T) == 4 ? 3 : 2) : MODE == 5 ? 2 : MODE == 6 ? 3 : MODE == 4 ? 6 : (sizeof(T) == 4 ? 4 : 3))
+__global__ void __launch_bounds__(128, MODE == 7 ? (sizeof(T) == 4 ? 3 : 2) : MODE == 5 ? 2 : MODE == 6 ? 3 : MODE == 4 ? 6 : MODE == 9 ? (sizeof(T) == 4 ? 4 : 2) : MODE == 8 ? (sizeof(T) == 4 ? 3 : 2) : (sizeof(T) == 4 ? 4 : 3))
     bsp_sweep_kernel(const SweepArgs<T> A, const BspArgs S)
 {
     const int lane = threadIdx.x & 31;
@@ -189,6 +195,8 @@ cudaError_t launch_one(const SweepArgs<T> &A, const BspArgs &S, int grid, int bl
 template <> const void *bsp_kernel_fn<float>(int mode)
 {
     switch (mode) {
+    case 9: return (const void *)bsp_sweep_kernel<float, 9>;
+    case 8: return (const void *)bsp_sweep_kernel<float, 8>;
     case 7: return (const void *)bsp_sweep_kernel<float, 7>;
     case 6: return (const void *)bsp_sweep_kernel<float, 6>;
     case 5: return (const void *)bsp_sweep_kernel<float, 5>;
@@ -203,6 +211,8 @@ template <> const void *bsp_kernel_fn<float>(int mode)
 template <> const void *bsp_kernel_fn<double>(int mode)
 {
     switch (mode) {
+    case 9: return (const void *)bsp_sweep_kernel<double, 9>;
+    case 8: return (const void *)bsp_sweep_kernel<double, 8>;
     case 7: return (const void *)bsp_sweep_kernel<double, 7>;
     case 5: return (const void *)bsp_sweep_kernel<double, 5>;
     case 2: return (const void *)bsp_sweep_kernel<double, 2>;
@@ -216,6 +226,8 @@ cudaError_t launch_bsp<float>(const SweepArgs<float> &A, const BspArgs &S, int m
                               bool cooperative, cudaStream_t st)
 {
     switch (mode) {
+    case 9: return launch_one<float, 9>(A, S, grid, block, dyn, cooperative, st);
+    case 8: return launch_one<float, 8>(A, S, grid, block, dyn, cooperative, st);
     case 7: return launch_one<float, 7>(A, S, grid, block, dyn, cooperative, st);
     case 6: return launch_one<float, 6>(A, S, grid, block, dyn, cooperative, st);
     case 5: return launch_one<float, 5>(A, S, grid, block, dyn, cooperative, st);
@@ -232,6 +244,8 @@ cudaError_t launch_bsp<double>(const SweepArgs<double> &A, const BspArgs &S, int
                                size_t dyn, bool cooperative, cudaStream_t st)
 {
     switch (mode) {
+    case 9: return launch_one<double, 9>(A, S, grid, block, dyn, cooperative, st);
+    case 8: return launch_one<double, 8>(A, S, grid, block, dyn, cooperative, st);
     case 7: return launch_one<double, 7>(A, S, grid, block, dyn, cooperative, st);
     case 5: return launch_one<double, 5>(A, S, grid, block, dyn, cooperative, st);
     case 2: return launch_one<double, 2>(A, S, grid, block, dyn, cooperative, st);

@@ -155,14 +155,65 @@ __global__ void __launch_bounds__(256) leak_ho_kernel(const T *__restrict__ psi,
     }
 }
 
+// Boundary leakage of trilinear hexahedra (vacuum boundaries): per (boundary cell, group)
+// over the chunk's directions, w_a sum over the boundary outflow faces f (Omega_a . Nbar_f
+// not below the sweep graph's inflow threshold -1e-12 |Nbar_f|) of
+// int_f (Omega_a . N) psi_a = sum_k psi_k sum_d Omega_d sum_l F[f][d][l][k].
+template <class T>
+__global__ void __launch_bounds__(256) leak_hex_kernel(const T *__restrict__ psi, const WeightPair *__restrict__ wts,
+                                                       const V4<T> *__restrict__ omega, int Dc, int64_t C, int G,
+                                                       const uint32_t *__restrict__ bcells, int64_t nb,
+                                                       const HexGeo<T> *__restrict__ geo, double *__restrict__ leak)
+{
+    for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < nb * G; u += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t b = u / G;
+        const int g = (int)(u - b * G);
+        const uint32_t c = bcells[b];
+        const HexGeo<T> &cg = geo[c];
+        double acc = 0.0;
+        float hi = 0.f, lo = 0.f;
+        for (int a = 0; a < Dc; ++a) {
+            const T *s = psi + (((size_t)a * C + c) * 8) * G + g;
+            const V4<T> om = omega[a];
+            T t = T(0);
+            for (int f = 0; f < 6; ++f) {
+                if (cg.nbr[f] >= 0) continue;
+                const T nx = cg.nbar[f][0], ny = cg.nbar[f][1], nz = cg.nbar[f][2];
+                const T sf = om.x * nx + om.y * ny + om.z * nz;
+                if (sf < T(-1e-12) * sqrt(nx * nx + ny * ny + nz * nz)) continue;  // inflow face of a vacuum boundary
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    T col = T(0);
+#pragma unroll
+                    for (int l = 0; l < 4; ++l)
+                        col += om.x * cg.F[f][0][4 * l + k] + om.y * cg.F[f][1][4 * l + k] + om.z * cg.F[f][2][4 * l + k];
+                    t += col * s[(size_t)hex_node(f, k) * G];
+                }
+            }
+            if constexpr (sizeof(T) == 8) {
+                acc += wts[a].d * (double)t;
+            } else {
+                const WeightPair w = wts[a];
+                const float pp = w.hi * t;
+                const float e = fmaf(w.hi, t, -pp) + w.lo * t;
+                two_sum_acc(hi, lo, pp, e);
+            }
+        }
+        if constexpr (sizeof(T) == 4) acc = (double)hi + (double)lo;
+        atomicAdd(leak + g, acc);
+    }
+}
+
 // The statistics of stats_kernel / stats_res_kernel for a higher-order field (same
 // partial layout, so the same finish kernels apply): integral sum_c V_c sum_i pw_i phi_i
-// (Eq. (3)), plain nodal sum, absorption, source, max |phi| and (RES) max |dphi|.
+// (Eq. (3)), plain nodal sum, absorption, source, max |phi| and (RES) max |dphi|.  With
+// per-cell weights pwc [C][NB] (hexahedra: int b_i), the integral is sum_c sum_i pwc phi_i.
 template <class T, bool RES, int NB>
 __global__ void __launch_bounds__(256) stats_ho_kernel(const double *__restrict__ phi_new,
                                                        const double *__restrict__ phi_old,
                                                        const double *__restrict__ vol, int64_t C, int G,
-                                                       double *__restrict__ part, BalIn bi, const double *__restrict__ pw)
+                                                       double *__restrict__ part, BalIn bi, const double *__restrict__ pw,
+                                                       const double *__restrict__ pwc)
 {
     constexpr int NP = RES ? 6 : 5;
     __shared__ double sh[NP][8][32];
@@ -176,7 +227,7 @@ __global__ void __launch_bounds__(256) stats_ho_kernel(const double *__restrict_
                 const T *q = reinterpret_cast<const T *>(bi.q) + (size_t)c * NB * G + g;
 #pragma unroll
                 for (int i = 0; i < NB; ++i) {
-                    const double w = __ldg(pw + i);
+                    const double w = pwc ? __ldg(pwc + (size_t)c * NB + i) : __ldg(pw + i);
                     mx = fmax(mx, fabs(pn[i]));
                     plain += pn[i];
                     ws += w * pn[i];
@@ -187,10 +238,11 @@ __global__ void __launch_bounds__(256) stats_ho_kernel(const double *__restrict_
 #pragma unroll
                     for (int i = 0; i < NB; ++i) dm = fmax(dm, fabs(pn[i] - po[i]));
                 }
-                iv += vol[c] * ws;
+                const double vc = pwc ? 1.0 : vol[c];
+                iv += vc * ws;
                 pl += plain;
-                ab += bi.sig[(size_t)bi.mat[c] * G + g] * vol[c] * ws;
-                sr += vol[c] * kFourPi * qs;
+                ab += bi.sig[(size_t)bi.mat[c] * G + g] * vc * ws;
+                sr += vc * kFourPi * qs;
             }
         }
         const double vals[6] = {mx, iv, pl, RES ? dm : ab, RES ? ab : sr, sr};

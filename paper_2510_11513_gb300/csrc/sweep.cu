@@ -657,7 +657,10 @@ struct DeviceState {
     bool fp64 = false;
     int order = 1;           // element order: 1 linear (4 nodes), 2 quadratic (10 nodes)
     int nb = 4;              // nodes per cell
-    void *geo2 = nullptr;    // higher orders: P2Geo<T> / P3Geo<T> [C]
+    bool hex = false;        // trilinear hexahedra (8 nodes, node-major layouts as the higher orders)
+    bool nodemajor() const { return order >= 2 || hex; }
+    void *geo2 = nullptr;    // higher orders: P2Geo<T> / P3Geo<T> [C]; hexahedra: HexGeo<T> [C]
+    double *hex_pw = nullptr;  // hexahedra: int b_i per cell and node [C][8] (statistics)
     double *vol = nullptr;   // higher orders: cell volumes (FP64)
     void *p3tab = nullptr;   // third order: P3Dev<T> element tables
     double *ho_pw = nullptr;   // higher orders: int phi_i / V [nb]
@@ -984,6 +987,67 @@ template <class T> tf_status create_typed_p2(Problem &p, DeviceState &d, const i
     return TF_OK;
 }
 
+// Trilinear hexahedra: cell records (exact element integrals, integrated face normals,
+// material, neighbours and, per face, the neighbour's local vertex of each face node),
+// cross sections, the per-cell basis integrals int b_i (row sums of M) for the
+// statistics, Q reordered node-major [C][8][G].
+template <class T> tf_status create_typed_hex(Problem &p, DeviceState &d, const int32_t *cell_material,
+                                              const double *sigma_t, const double *sigma_s, const double *Q)
+{
+    const Mesh &m = *p.mesh;
+    tf_status s;
+    for (int f = 0; f < 6; ++f)
+        for (int k = 0; k < 4; ++k)
+            if (hex_node(f, k) != hex_face_node(f, k)) return fail(TF_ERR_MESH, "hexahedral face-node tables disagree");
+    {
+        std::vector<HexGeo<T>> geo(m.nc);
+        std::vector<double> pw(8 * (size_t)m.nc);
+        for (int64_t c = 0; c < m.nc; ++c) {
+            HexGeo<T> &g = geo[c];
+            std::memset(&g, 0, sizeof(g));
+            g.mat = cell_material[c];
+            for (int f = 0; f < 6; ++f) {
+                g.nbr[f] = m.nbr[6 * c + f];
+                if (g.nbr[f] >= 0)
+                    for (int k = 0; k < 4; ++k) {
+                        const int v = m.nbr_node[24 * c + 4 * f + k];
+                        if (v < 0 || v > 7) return fail(TF_ERR_MESH, "hexahedral face node without a match in the neighbour");
+                        g.nmap[f] |= (uint32_t)v << (4 * k);
+                    }
+                for (int r = 0; r < 3; ++r) g.nbar[f][r] = (T)m.normal[18 * c + 3 * f + r];
+                for (int dd = 0; dd < 3; ++dd)
+                    for (int k = 0; k < 16; ++k) g.F[f][dd][k] = (T)m.hface[288 * c + 48 * f + 16 * dd + k];
+            }
+            for (int i = 0; i < 64; ++i) g.M[i] = (T)m.hmass[64 * c + i];
+            for (int dd = 0; dd < 3; ++dd)
+                for (int i = 0; i < 64; ++i) g.Gd[dd][i] = (T)m.hgrad[192 * c + 64 * dd + i];
+            for (int i = 0; i < 8; ++i) {
+                double r = 0.0;
+                for (int j = 0; j < 8; ++j) r += m.hmass[64 * c + 8 * i + j];
+                pw[8 * c + i] = r;
+            }
+        }
+        HexGeo<T> *gp = nullptr;
+        if ((s = upload(d, &gp, geo.data(), geo.size() * sizeof(HexGeo<T>))) != TF_OK) return s;
+        d.geo2 = gp;
+        if ((s = upload(d, &d.hex_pw, pw.data(), pw.size() * sizeof(double))) != TF_OK) return s;
+    }
+    if ((s = upload_vec3<T>(d, &d.omega, p.quad->omega.data(), d.D, p.quad->w.data())) != TF_OK) return s;
+    if ((s = upload(d, &d.mat, cell_material, sizeof(int32_t) * (size_t)d.C)) != TF_OK) return s;
+    if ((s = upload(d, &d.sig_d, sigma_t, sizeof(double) * (size_t)d.M * d.G)) != TF_OK) return s;
+    if ((s = upload_typed<T>(d, &d.sigma_t, sigma_t, (size_t)d.M * d.G)) != TF_OK) return s;
+    if ((s = upload_typed<T>(d, &d.sigma_s, sigma_s, (size_t)d.M * d.G * d.G)) != TF_OK) return s;
+    if ((s = upload(d, &d.vol, m.vol.data(), sizeof(double) * (size_t)d.C)) != TF_OK) return s;
+    {
+        std::vector<double> Qs((size_t)d.C * d.G * 8);
+        for (int64_t c = 0; c < d.C; ++c)
+            for (int gq = 0; gq < d.G; ++gq)
+                for (int i = 0; i < 8; ++i) Qs[((size_t)c * 8 + i) * d.G + gq] = Q[((size_t)c * d.G + gq) * 8 + i];
+        if ((s = upload_typed<T>(d, &d.Q, Qs.data(), Qs.size())) != TF_OK) return s;
+    }
+    return TF_OK;
+}
+
 // Third-order element: cell records (grad lambda, normals, volume, material, neighbours,
 // and for each of a face's ten nodes the neighbour's local node at the same place, matched
 // by the global vertices its lattice index weights), the exact element tables, cross
@@ -1106,10 +1170,11 @@ tf_status device_create(Problem &p, const int32_t *cell_material, const double *
     d.M = p.M;
     d.fp64 = p.opt.precision == TF_FP64;
     d.order = p.opt.order >= 2 ? p.opt.order : 1;
-    d.nb = d.order == 3 ? 20 : d.order == 2 ? 10 : 4;
+    d.hex = m.nf == 6;
+    d.nb = d.hex ? 8 : d.order == 3 ? 20 : d.order == 2 ? 10 : 4;
     // pairing 0 = automatic: packed pairs unless G is a multiple of 32 (there the
     // shared-memory staged path is faster); 2 = packed pairs whenever G is even
-    d.paired = d.order == 1 && !d.fp64 && d.G % 2 == 0 && (p.opt.pairing == 2 || (p.opt.pairing == 0 && d.G % 32 != 0)) &&
+    d.paired = d.order == 1 && !d.hex && !d.fp64 && d.G % 2 == 0 && (p.opt.pairing == 2 || (p.opt.pairing == 0 && d.G % 32 != 0)) &&
                g.cells_per_task <= 32 &&
                PairLayout(d.G, g.cells_per_task).bytes() <= 227u * 1024u;
     d.tsize = d.fp64 ? 8 : 4;
@@ -1119,8 +1184,9 @@ tf_status device_create(Problem &p, const int32_t *cell_material, const double *
     // task graph
     {
         // inflow masks of the task cell lists, caller face order -> sorted face order
-        std::vector<uint8_t> remap((size_t)m.nc * 16);
-        for (int64_t c = 0; c < m.nc; ++c) {
+        // (linear tetrahedra only)
+        std::vector<uint8_t> remap(d.nodemajor() ? 0 : (size_t)m.nc * 16);
+        for (int64_t c = 0; c < (d.nodemajor() ? 0 : m.nc); ++c) {
             int s2u[4];
             sorted_order(&m.tets[4 * c], s2u);
             for (uint32_t mk = 0; mk < 16; ++mk) {
@@ -1129,11 +1195,11 @@ tf_status device_create(Problem &p, const int32_t *cell_material, const double *
                 remap[16 * c + mk] = (uint8_t)r;
             }
         }
-        // (the second-order element keeps the caller's face order)
+        // (the higher orders and hexahedra keep the caller's face order)
         std::vector<uint32_t> cl(g.cell_list.size());
         for (size_t i = 0; i < cl.size(); ++i) {
             const uint32_t e = g.cell_list[i], c = e >> 4;
-            cl[i] = d.order >= 2 ? e : (c << 4) | remap[16 * (size_t)c + (e & 15u)];
+            cl[i] = d.nodemajor() ? e : (c << 4) | remap[16 * (size_t)c + (e & 15u)];
         }
         if ((s = upload(d, &d.cells, cl.data(), cl.size() * 4)) != TF_OK) return s;
     }
@@ -1156,7 +1222,10 @@ tf_status device_create(Problem &p, const int32_t *cell_material, const double *
         for (int64_t c = 0; c < m.nc; ++c) v4[c] = 0.25 * m.vol[c];
         if ((s = upload(d, &d.vol4, v4.data(), v4.size() * 8)) != TF_OK) return s;
     }
-    if (d.order == 3)
+    if (d.hex)
+        s = d.fp64 ? create_typed_hex<double>(p, d, cell_material, sigma_t, sigma_s, Q)
+                   : create_typed_hex<float>(p, d, cell_material, sigma_t, sigma_s, Q);
+    else if (d.order == 3)
         s = d.fp64 ? create_typed_p3<double>(p, d, cell_material, sigma_t, sigma_s, Q)
                    : create_typed_p3<float>(p, d, cell_material, sigma_t, sigma_s, Q);
     else if (d.order == 2)
@@ -1191,8 +1260,11 @@ tf_status device_create(Problem &p, const int32_t *cell_material, const double *
     {
         std::vector<uint32_t> bc;
         for (int64_t c = 0; c < m.nc; ++c)
-            if (m.nbr[4 * c] < 0 || m.nbr[4 * c + 1] < 0 || m.nbr[4 * c + 2] < 0 || m.nbr[4 * c + 3] < 0)
-                bc.push_back((uint32_t)c);
+            for (int f = 0; f < m.nf; ++f)
+                if (m.nbr[(int64_t)m.nf * c + f] < 0) {
+                    bc.push_back((uint32_t)c);
+                    break;
+                }
         d.n_bcells = (int64_t)bc.size();
         if ((s = upload(d, &d.bcells, bc.data(), 4 * bc.size())) != TF_OK) return s;
     }
@@ -1313,7 +1385,7 @@ tf_status device_create(Problem &p, const int32_t *cell_material, const double *
         const int ns = p.opt.staging == 3 ? 3 : p.opt.staging == 2 ? 2 : (d.fp64 ? 3 : 2);
         const size_t wb = d.fp64 ? staged_warp_bytes<double>(d.G, ns) : staged_warp_bytes<float>(d.G, ns);
         const size_t wb128 = (wb + 48 + 127) / 128 * 128;  // + the six mbarriers at the end
-        d.staged = d.order == 1 && p.opt.staging != 1 && d.G % 32 == 0 && g.cells_per_task <= 64 &&
+        d.staged = d.order == 1 && !d.hex && p.opt.staging != 1 && d.G % 32 == 0 && g.cells_per_task <= 64 &&
                    wb128 * d.wpc <= 227 * 1024;
         d.warp_smem = d.staged ? (uint32_t)wb128 : 0u;
         d.two_stage = d.staged && ns == 2 && !d.fp64;
@@ -1323,7 +1395,12 @@ tf_status device_create(Problem &p, const int32_t *cell_material, const double *
                            ((p2_stage_bytes(d.G) * 2 + 48 + 127) / 128 * 128) * d.wpc <= 227 * 1024;
     if (p2_staged) d.warp_smem = (p2_stage_bytes(d.G) * 2 + 48 + 127) / 128 * 128;
     if (d.order == 3) d.warp_smem = 0;  // four lanes per unit, systems in registers
-    d.mode = d.order == 3 ? 7
+    // hexahedra: the group-independent matrices in shared memory once per cell when a batch of
+    // 32 units touches at most five cells (G >= 8); staging = 1 keeps every lane on its own
+    const bool hex_shared = d.hex && d.G >= 8 && p.opt.staging != 1;
+    if (d.hex) d.warp_smem = hex_shared ? (hex_stage_bytes((int)d.tsize) + 127u) / 128u * 128u : 0u;
+    d.mode = d.hex ? (hex_shared ? 9 : 8)
+             : d.order == 3 ? 7
              : d.order == 2 ? (p2_staged ? 6 : 5)
              : d.paired  ? 3
              : d.staged  ? (d.two_stage ? 4 : 2)
@@ -1353,16 +1430,19 @@ tf_status device_create(Problem &p, const int32_t *cell_material, const double *
         d.lpc_shift = (int)L.lpc_shift;
         d.ppl = (int)L.ppl;
     }
-    if (d.order >= 2) {
+    if (d.nodemajor()) {
         // the node-major source update stages max(1, 256 / G) cells' flux in shared memory:
         // above 48 KB (large G) the kernel needs the opt-in limit
         const size_t smem2 = (size_t)std::max(1, 256 / d.G) * d.G * d.nb * d.tsize;
-        const void *sfn = d.nb == 20 ? (d.fp64 ? (const void *)source_ho_kernel<double, 20> : (const void *)source_ho_kernel<float, 20>)
-                                     : (d.fp64 ? (const void *)source_ho_kernel<double, 10> : (const void *)source_ho_kernel<float, 10>);
+        const void *sfn = d.nb == 8    ? (d.fp64 ? (const void *)source_ho_kernel<double, 8> : (const void *)source_ho_kernel<float, 8>)
+                          : d.nb == 20 ? (d.fp64 ? (const void *)source_ho_kernel<double, 20> : (const void *)source_ho_kernel<float, 20>)
+                                       : (d.fp64 ? (const void *)source_ho_kernel<double, 10> : (const void *)source_ho_kernel<float, 10>);
         if (smem2 > 48 * 1024) TF_CUDA(ensure_dyn_smem(sfn, (int)smem2));
     }
     const int dyn = (int)(d.warp_smem * d.wpc);
-    const void *kfn = d.mode == 7   ? (d.fp64 ? (const void *)sweep_kernel<double, 7> : (const void *)sweep_kernel<float, 7>)
+    const void *kfn = d.mode == 9   ? (d.fp64 ? (const void *)sweep_kernel<double, 9> : (const void *)sweep_kernel<float, 9>)
+                      : d.mode == 8 ? (d.fp64 ? (const void *)sweep_kernel<double, 8> : (const void *)sweep_kernel<float, 8>)
+                      : d.mode == 7 ? (d.fp64 ? (const void *)sweep_kernel<double, 7> : (const void *)sweep_kernel<float, 7>)
                       : d.mode == 6 ? (const void *)sweep_kernel<float, 6>
                       : d.mode == 5 ? (d.fp64 ? (const void *)sweep_kernel<double, 5> : (const void *)sweep_kernel<float, 5>)
                       : d.fp64 ? (d.mode == 2 ? (const void *)sweep_kernel<double, 2>
@@ -1464,11 +1544,14 @@ void *mapped_host_pointer(const void *ptr)
 template <class T> void launch_source(Problem &p, const double *phi_in, cudaStream_t st)
 {
     DeviceState &d = *p.dev;
-    if (d.order >= 2) {
+    if (d.nodemajor()) {
         const int cpc2 = std::max(1, 256 / d.G);
         const size_t smem2 = (size_t)cpc2 * d.G * d.nb * sizeof(T);
         const int blocks2 = (int)std::min<int64_t>((d.C + cpc2 - 1) / cpc2, (int64_t)d.sm_count * 16);
-        if (d.order == 3)
+        if (d.hex)
+            source_ho_kernel<T, 8><<<blocks2, 256, smem2, st>>>(phi_in, (const T *)d.Q, (const T *)d.sigma_s, d.mat,
+                                                                (T *)d.q, d.C, d.G, cpc2);
+        else if (d.order == 3)
             source_ho_kernel<T, 20><<<blocks2, 256, smem2, st>>>(phi_in, (const T *)d.Q, (const T *)d.sigma_s, d.mat,
                                                                  (T *)d.q, d.C, d.G, cpc2);
         else
@@ -1492,12 +1575,13 @@ template <int NB> void launch_stats_ho(Problem &p, const double *cur, const doub
 {
     DeviceState &d = *p.dev;
     const dim3 blk(32, 8);
+    const double *pwc = d.hex_pw;  // hexahedra: per-cell weights; else V_c times the element's
     if (d.fp64) {
-        if (res) stats_ho_kernel<double, true, NB><<<d.stats_blocks, blk, 0, st>>>(nxt, cur, d.vol, d.C, d.G, d.part, bi, d.ho_pw);
-        else stats_ho_kernel<double, false, NB><<<d.stats_blocks, blk, 0, st>>>(nxt, cur, d.vol, d.C, d.G, d.part, bi, d.ho_pw);
+        if (res) stats_ho_kernel<double, true, NB><<<d.stats_blocks, blk, 0, st>>>(nxt, cur, d.vol, d.C, d.G, d.part, bi, d.ho_pw, pwc);
+        else stats_ho_kernel<double, false, NB><<<d.stats_blocks, blk, 0, st>>>(nxt, cur, d.vol, d.C, d.G, d.part, bi, d.ho_pw, pwc);
     } else {
-        if (res) stats_ho_kernel<float, true, NB><<<d.stats_blocks, blk, 0, st>>>(nxt, cur, d.vol, d.C, d.G, d.part, bi, d.ho_pw);
-        else stats_ho_kernel<float, false, NB><<<d.stats_blocks, blk, 0, st>>>(nxt, cur, d.vol, d.C, d.G, d.part, bi, d.ho_pw);
+        if (res) stats_ho_kernel<float, true, NB><<<d.stats_blocks, blk, 0, st>>>(nxt, cur, d.vol, d.C, d.G, d.part, bi, d.ho_pw, pwc);
+        else stats_ho_kernel<float, false, NB><<<d.stats_blocks, blk, 0, st>>>(nxt, cur, d.vol, d.C, d.G, d.part, bi, d.ho_pw, pwc);
     }
     if (res) {
         finish_stats_res_kernel<<<(d.G + 127) / 128, 128, 0, st>>>(d.part, d.stats_blocks, d.G, d.gstats, d.leak, d.ctrl);
@@ -1518,9 +1602,10 @@ void launch_stats(Problem &p, const double *cur, const double *nxt, cudaStream_t
     bi.qmode = d.paired ? 2 : (d.fp64 ? 1 : 0);
     bi.leak = d.leak;
     cudaMemsetAsync(&d.ctrl->residual_bits, 0, 16, st);  // residual_bits, balance_bits
-    if (d.order >= 2) {
+    if (d.nodemajor()) {
         const bool res = p.opt.residual_floor >= 1.0;
-        if (d.order == 3) launch_stats_ho<20>(p, cur, nxt, res, bi, st);
+        if (d.hex) launch_stats_ho<8>(p, cur, nxt, res, bi, st);
+        else if (d.order == 3) launch_stats_ho<20>(p, cur, nxt, res, bi, st);
         else launch_stats_ho<10>(p, cur, nxt, res, bi, st);
         return;
     }
@@ -1592,10 +1677,13 @@ template <class T> void launch_phi(Problem &p, int k, double *phi_out, cudaStrea
     const size_t CG = (size_t)d.C * d.G;
     const int a0 = k * d.Dc, a1 = std::min(d.D, a0 + d.Dc);
     const int pb = (int)std::min<size_t>((CG + 255) / 256, (size_t)d.sm_count * 32);
-    if (d.order >= 2) {
+    if (d.nodemajor()) {
         const bool pair = !d.fp64 && p.opt.phi_accumulate == TF_PHI_PAIR;
         const T *ps = (const T *)d.psi;
-        if (d.order == 3) {
+        if (d.hex) {
+            if (pair) phi_ho_kernel<T, true, 8><<<pb, 256, 0, st>>>(ps, d.wts + a0, a1 - a0, d.C, d.G, phi_out, k > 0);
+            else phi_ho_kernel<T, false, 8><<<pb, 256, 0, st>>>(ps, d.wts + a0, a1 - a0, d.C, d.G, phi_out, k > 0);
+        } else if (d.order == 3) {
             if (pair) phi_ho_kernel<T, true, 20><<<pb, 256, 0, st>>>(ps, d.wts + a0, a1 - a0, d.C, d.G, phi_out, k > 0);
             else phi_ho_kernel<T, false, 20><<<pb, 256, 0, st>>>(ps, d.wts + a0, a1 - a0, d.C, d.G, phi_out, k > 0);
         } else {
@@ -1606,7 +1694,10 @@ template <class T> void launch_phi(Problem &p, int k, double *phi_out, cudaStrea
             const int lb = (int)std::min<int64_t>((d.n_bcells * d.G + 255) / 256, (int64_t)d.sm_count * 16);
             const HoTables tb{d.ho_pw, d.ho_fn, d.ho_fav};
             const V4<T> *om = (const V4<T> *)d.omega + a0;
-            if (d.order == 3)
+            if (d.hex)
+                leak_hex_kernel<T><<<lb, 256, 0, st>>>(ps, d.wts + a0, om, a1 - a0, d.C, d.G, d.bcells, d.n_bcells,
+                                                       (const HexGeo<T> *)d.geo2, d.leak);
+            else if (d.order == 3)
                 leak_ho_kernel<T, 20, 10, P3Geo<T>><<<lb, 256, 0, st>>>(ps, d.wts + a0, om, a1 - a0, d.C, d.G, d.bcells,
                                                                         d.n_bcells, (const P3Geo<T> *)d.geo2, tb, d.leak);
             else
@@ -1704,7 +1795,11 @@ template <class T> tf_status launch_step(Problem &p, const double *phi_in, doubl
             if (d.mode == 6) sweep_kernel<T, 6><<<d.grid, 32 * d.wpc, dyn, st>>>(A);
         }
         if (d.mode == 3 || d.mode == 4 || d.mode == 6) {
-        } else if (d.mode == 7)
+        } else if (d.mode == 9)
+            sweep_kernel<T, 9><<<d.grid, 32 * d.wpc, dyn, st>>>(A);
+        else if (d.mode == 8)
+            sweep_kernel<T, 8><<<d.grid, 32 * d.wpc, 0, st>>>(A);
+        else if (d.mode == 7)
             sweep_kernel<T, 7><<<d.grid, 32 * d.wpc, dyn, st>>>(A);
         else if (d.mode == 5)
             sweep_kernel<T, 5><<<d.grid, 32 * d.wpc, 0, st>>>(A);
@@ -1991,7 +2086,7 @@ tf_status batch_setup(BatchRun &B, const tf_handle *problems, int32_t n)
         if (p->dev->device != B.device || p->dev->fp64 != B.fp64)
             return fail(TF_ERR_ARG, "batched problems must share one device and one precision");
         if (p->opt.inject_stall) return fail(TF_ERR_ARG, "inject_stall is not supported in batched launches");
-        if (p->dev->schedule != TF_SCHED_AMT || p->dev->order != 1)
+        if (p->dev->schedule != TF_SCHED_AMT || p->dev->order != 1 || p->dev->hex)
             return fail(TF_ERR_ARG, "batched launches run only linear-element problems with the TF_SCHED_AMT schedule");
         B.max_chunks = std::max(B.max_chunks, p->dev->n_chunks);
         B.warp_smem = std::max(B.warp_smem, p->dev->warp_smem);
@@ -2294,7 +2389,14 @@ tf_status device_psi(Problem &p, int32_t dir, void *out, void *stream)
     const size_t CG = (size_t)d.C * d.G;
     cudaStream_t st = (cudaStream_t)stream;
     const int blocks = (int)std::min<size_t>((CG + 255) / 256, (size_t)d.sm_count * 16);
-    if (d.order == 3) {
+    if (d.hex) {
+        if (d.fp64)
+            psi_ho_out_kernel<double, 8><<<blocks, 256, 0, st>>>((const double *)d.psi + (size_t)(dir - a0) * CG * 8,
+                                                                 (double *)out, d.C, d.G);
+        else
+            psi_ho_out_kernel<float, 8><<<blocks, 256, 0, st>>>((const float *)d.psi + (size_t)(dir - a0) * CG * 8,
+                                                                (float *)out, d.C, d.G);
+    } else if (d.order == 3) {
         if (d.fp64)
             psi_ho_out_kernel<double, 20><<<blocks, 256, 0, st>>>((const double *)d.psi + (size_t)(dir - a0) * CG * 20,
                                                                   (double *)out, d.C, d.G);

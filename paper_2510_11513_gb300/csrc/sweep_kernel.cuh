@@ -146,7 +146,7 @@ template <class T> __device__ __forceinline__ void scatter4(const T (&r)[4], uin
 // ============================================================== sweep kernel
 template <class T> struct SweepArgs {
     const CellGeo<T> *geo;
-    const uint32_t *cells;      // (cell << 4) | inflow mask
+    const uint32_t *cells;      // (cell << 4) | inflow mask; hexahedra: (cell << 6) | mask
     const uint4 *task;          // {cell_begin, ncell | dir << 16, down_begin, ndown}
     const uint32_t *down;       // downwind task ids
     int *counters;              // dependency counters
@@ -178,7 +178,7 @@ template <class T> struct SweepArgs {
     int32_t lpc_shift, ppl;      // paired path: log2 lanes per cell, group pairs per lane
     int32_t stages;              // paired path: buffers in the ring of staged copies (2 or 3)
     int32_t mode;                // kernel variant of this problem (batched launches dispatch on it)
-    const void *geo2;            // second-order element: P2Geo<T> [C] cell records (mode 5)
+    const void *geo2;            // second-order element: P2Geo<T> [C] cell records (modes 5, 6); P3Geo<T> (7); HexGeo<T> (8)
     int32_t keep_max;            // ready tasks a warp keeps and runs next (1..4)
     const void *p3tab;           // third-order element: P3Dev<T> tables (mode 7)
 };
@@ -1126,6 +1126,7 @@ __device__ __forceinline__ bool run_task_staged_any(const SweepArgs<T> &A, uint4
 
 #include "p2_solve.cuh"
 #include "p3_solve.cuh"
+#include "hex_solve.cuh"
 
 // Persistent sweep: a warp claims a ticket (the next queue slot), waits until
 // that slot holds a ready task, executes it with lanes spanning (cell, group)
@@ -1142,9 +1143,11 @@ __device__ __forceinline__ bool run_task_staged_any(const SweepArgs<T> &A, uint4
 // 4 = as 2 with two stages and six resident CTAs per SM (FP32),
 // 5 = the second-order (ten-node) element, lanes over (cell, group) units,
 // 6 = the second-order element staged in shared memory (FP32, G a multiple of 32),
-// 7 = the third-order element, four lanes per unit with the system in registers.
+// 7 = the third-order element, four lanes per unit with the system in registers,
+// 8 = trilinear hexahedra, lanes over (cell, group) units,
+// 9 = trilinear hexahedra with the group-independent matrices formed once per cell in shared memory (G >= 8).
 template <class T, int MODE>
-__global__ void __launch_bounds__(128, MODE == 7 ? (sizeof(T) == 4 ? 3 : 2) : MODE == 5 ? 2 : MODE == 6 ? 3 : MODE == 4 ? 6 : (sizeof(T) == 4 ? 4 : 3))
+__global__ void __launch_bounds__(128, MODE == 7 ? (sizeof(T) == 4 ? 3 : 2) : MODE == 5 ? 2 : MODE == 6 ? 3 : MODE == 4 ? 6 : MODE == 9 ? (sizeof(T) == 4 ? 4 : 2) : MODE == 8 ? (sizeof(T) == 4 ? 3 : 2) : (sizeof(T) == 4 ? 4 : 3))
     sweep_kernel(const SweepArgs<T> A)
 {
     const int lane = threadIdx.x & 31;
@@ -1254,6 +1257,10 @@ __global__ void __launch_bounds__(128, MODE == 7 ? (sizeof(T) == 4 ? 3 : 2) : MO
             if (!run_task_p2_staged(A, ti, lane, om.x, om.y, om.z, psi_dir, wsm, bars, ph, ws + 6)) break;
         } else if constexpr (MODE == 7) {
             run_task_p3(A, ti, lane, om.x, om.y, om.z, psi_dir, wsm);
+        } else if constexpr (MODE == 8) {
+            run_task_hex(A, ti, lane, om.x, om.y, om.z, psi_dir);
+        } else if constexpr (MODE == 9) {
+            run_task_hex_shared(A, ti, lane, om.x, om.y, om.z, psi_dir, wsm);
         } else {
             run_task_generic(A, ti, lane, om.x, om.y, om.z, psi_dir);
         }

@@ -509,7 +509,7 @@ class Problem(_Handle):
                  S1=None, psi_inflow=None, **opts):
         self.mesh, self.quad = mesh, quad
         self.opt = options(**opts)
-        self.n_nodes = {2: 10, 3: 20}.get(int(self.opt.order), 4)
+        self.n_nodes = 8 if isinstance(mesh, HexMesh) else {2: 10, 3: 20}.get(int(self.opt.order), 4)
         if int(n_groups) > 0 and np.size(Q) != mesh.n_cells * int(n_groups) * self.n_nodes:
             raise ValueError(f"Q must be [n_cells][n_groups][{self.n_nodes}]")
         self.h = tf_problem_create(mesh.h, quad.h, n_groups, n_materials, cell_material, sigma_t, sigma_s, Q, S1,
@@ -521,7 +521,7 @@ class Problem(_Handle):
 
     @classmethod
     def from_config(cls, cfg, S1=None, psi_inflow=None, omega=None, w=None, **opts):
-        mesh = Mesh(cfg["xyz"], cfg["tets"])
+        mesh = HexMesh(cfg["xyz"], cfg["hexes"]) if "hexes" in cfg else Mesh(cfg["xyz"], cfg["tets"])
         quad = Quadrature(omega=omega, w=w) if omega is not None else Quadrature(cfg["n_polar"], cfg["n_azimuthal"])
         return cls(mesh, quad, cfg["n_groups"], cfg["n_materials"], cfg["cell_material"], cfg["sigma_t"],
                    cfg["sigma_s"], cfg["Q"], S1=S1, psi_inflow=psi_inflow, **opts)

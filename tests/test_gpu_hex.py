@@ -1,0 +1,155 @@
+"""Parity of the trilinear-hexahedron CUDA sweep (sweep mode 8) with the hexahedral oracle.
+
+Tolerances as for the tetrahedra (relative to the oracle's max-norm): FP64 1e-11, FP32
+2e-5.  Twisted grids (0.25 rad over the height, no jitter: acyclic sweep graphs), sizes
+spanning several tasks, ragged group counts and cell blocks, several direction chunks.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import q1hex as oh
+
+torch = pytest.importorskip("torch")
+import paper_2510_11513_gb300 as tf  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+TOL = {tf.TF_FP64: 1e-11, tf.TF_FP32: 2e-5}
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+
+
+def _rel(a, b):
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+def _box(n, G, seed=5, two_material=False, twist=0.25):
+    maker = W.two_material_box if two_material else W.small_box
+    return W.hex_problem(maker(n=n, G=G, n_polar=2, n_az=8, seed=seed), twist=twist)
+
+
+@pytest.mark.parametrize("precision", [tf.TF_FP64, tf.TF_FP32])
+@pytest.mark.parametrize("G,opts", [(1, {}), (4, {}), (5, dict(cells_per_task=3)), (8, {}), (9, dict(cells_per_task=3)),
+                                    (32, {}), (32, dict(staging=1)), (37, dict(cells_per_task=2, dir_chunk=5)),
+                                    (12, dict(dir_chunk=7)), (64, dict(cells_per_task=5, dir_chunk=9))])
+def test_one_sweep_matches_oracle(precision, G, opts):
+    cfg = _box(n=4 if G >= 32 else 5, G=G)
+    P = oh.ProblemHex(cfg)
+    phi_in = np.random.default_rng(11).uniform(0.0, 1.0, (P.C, G, 8))
+    ref = P.transport_step(phi_in, threads=8)
+    prob = tf.Problem.from_config(cfg, precision=precision, **opts)
+    assert prob.n_nodes == 8
+    out = torch.zeros_like(_dev(phi_in))
+    prob.sweep(_dev(phi_in), out)
+    assert _rel(out.cpu().numpy(), ref) < TOL[precision]
+    st = prob.stats()
+    assert st["tasks_executed"] == st["n_tasks"]
+    assert st["kernel_mode"] == (9 if G >= 8 and opts.get("staging", 0) != 1 else 8)
+
+
+@pytest.mark.parametrize("precision,G", [(tf.TF_FP64, 6), (tf.TF_FP32, 6), (tf.TF_FP32, 32)])
+def test_psi_of_directions_matches_oracle(precision, G):
+    cfg = _box(n=4, G=G, twist=0.6)
+    P = oh.ProblemHex(cfg)
+    phi_in = np.random.default_rng(2).uniform(0.0, 1.0, (P.C, G, 8))
+    q = P.source(phi_in)
+    prob = tf.Problem.from_config(cfg, precision=precision)
+    prob.sweep(_dev(phi_in), torch.zeros_like(_dev(phi_in)))
+    dt = torch.float64 if precision == tf.TF_FP64 else torch.float32
+    for a in (0, 5, P.D - 1):
+        buf = torch.empty((P.C, G, 8), dtype=dt, device="cuda")
+        got = prob.psi(a, buf).double().cpu().numpy()
+        assert _rel(got, P.sweep_direction(a, q)) < TOL[precision], a
+
+
+@pytest.mark.parametrize("precision,G", [(tf.TF_FP64, 4), (tf.TF_FP32, 4), (tf.TF_FP32, 32)])
+def test_converged_source_iteration_matches_oracle(precision, G):
+    """Two materials, up- and downscatter: the device iteration stops at the same test, with
+    phi, the integrated flux (Eq. 3 with the trilinear field) and the particle balance of the
+    device against the oracle."""
+    cfg = _box(n=4, G=G, two_material=True)
+    P = oh.ProblemHex(cfg)
+    ref, it_ref, r_ref = P.source_iterate(1e-8, 500, threads=8)
+    prob = tf.Problem.from_config(cfg, precision=precision)
+    phi = torch.zeros((P.C, G, 8), dtype=torch.float64, device="cuda")
+    tol = 1e-8 if precision == tf.TF_FP64 else 1e-6
+    res = prob.source_iterate(phi, tol, 500)
+    assert res["converged"]
+    if precision == tf.TF_FP64:
+        assert abs(res["iterations"] - it_ref) <= 1
+    assert _rel(phi.cpu().numpy(), ref) < (1e-7 if precision == tf.TF_FP64 else 2e-5)
+    ig, tot = P.integrated_flux(phi.cpu().numpy())
+    assert np.allclose(res["integrated_flux"], ig, rtol=1e-12, atol=0)
+    assert res["balance"] < (1e-12 if precision == tf.TF_FP64 else 1e-5), res["balance"]
+
+
+def test_golden_hex_small_box():
+    """The 8^3 box as twisted hexahedra converged in FP64 against the oracle's stored values."""
+    import json
+    import os
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "oracle_regression.json")))["hex_small_box"]
+    cfg = W.hex_problem(W.small_box(), twist=g["twist"])
+    prob = tf.Problem.from_config(cfg, precision=tf.TF_FP64)
+    phi = torch.zeros((prob.n_cells, 4, 8), dtype=torch.float64, device="cuda")
+    res = prob.source_iterate(phi, g["tol"], 1000)
+    assert abs(res["iterations"] - g["iterations"]) <= 1
+    assert np.allclose(res["integrated_flux"], g["integrated_flux"], rtol=1e-10, atol=0)
+
+
+def test_host_buffers_and_aliasing():
+    cfg = _box(n=3, G=3)
+    P = oh.ProblemHex(cfg)
+    phi_in = np.random.default_rng(4).uniform(0.0, 1.0, (P.C, 3, 8))
+    ref = P.transport_step(phi_in)
+    prob = tf.Problem.from_config(cfg, precision=tf.TF_FP64)
+    hin = torch.from_numpy(phi_in.copy()).pin_memory()
+    hout = torch.zeros_like(hin).pin_memory()
+    prob.sweep(hin, hout)
+    assert _rel(hout.numpy(), ref) < 1e-11
+    buf = _dev(phi_in)
+    prob.sweep(buf, buf)
+    assert _rel(buf.cpu().numpy(), ref) < 1e-11
+
+
+@pytest.mark.parametrize("schedule", [tf.TF_SCHED_BSP, tf.TF_SCHED_BSP_LAUNCH])
+@pytest.mark.parametrize("precision,G", [(tf.TF_FP64, 5), (tf.TF_FP32, 5), (tf.TF_FP32, 32)])
+def test_bulk_synchronous_schedules_same_result(schedule, precision, G):
+    cfg = _box(n=4, G=G)
+    P = oh.ProblemHex(cfg)
+    phi_in = np.random.default_rng(8).uniform(0.0, 1.0, (P.C, G, 8))
+    ref = P.transport_step(phi_in, threads=8)
+    a = tf.Problem.from_config(cfg, precision=precision)
+    b = tf.Problem.from_config(cfg, precision=precision, schedule=schedule)
+    out_a, out_b = torch.zeros_like(_dev(phi_in)), torch.zeros_like(_dev(phi_in))
+    a.sweep(_dev(phi_in), out_a)
+    b.sweep(_dev(phi_in), out_b)
+    assert torch.equal(out_a, out_b)
+    assert _rel(out_b.cpu().numpy(), ref) < TOL[precision]
+    st = b.stats()
+    assert st["tasks_executed"] == st["n_tasks"] and st["n_buckets"] > 0
+    assert st["kernel_mode"] == a.stats()["kernel_mode"] == (9 if G >= 8 else 8)
+
+
+def test_hexahedral_rejections():
+    cfg = _box(n=2, G=2)
+    C = len(cfg["hexes"])
+    with pytest.raises(tf.TfError) as e:
+        tf.Problem.from_config(cfg, psi_inflow=np.ones((cfg["xyz"].shape[0], 2)))
+    assert e.value.status == tf.TF_ERR_ARG
+    with pytest.raises(tf.TfError) as e:
+        tf.Problem.from_config(cfg, S1=np.ones((C, 2, 3)))
+    assert e.value.status == tf.TF_ERR_ARG
+    with pytest.raises(tf.TfError) as e:
+        tf.Problem.from_config(cfg, order=2)
+    assert e.value.status == tf.TF_ERR_ARG
+    with pytest.raises(ValueError):
+        tf.Problem.from_config(dict(cfg, Q=np.zeros((C, 2, 4))))
+    a = tf.Problem.from_config(cfg)
+    b = tf.Problem.from_config(cfg)
+    phis = [torch.zeros((C, 2, 8), dtype=torch.float64, device="cuda") for _ in range(2)]
+    with pytest.raises(tf.TfError) as e:
+        tf.sweep_batch([a, b], phis, phis)
+    assert e.value.status == tf.TF_ERR_ARG

@@ -46,7 +46,7 @@ def test_graph_bit_exact(twist, jitter, n_polar, n_az):
     assert np.array_equal(level, level_ref)
 
 
-def test_errors_and_unsupported_problem():
+def test_errors():
     xyz, hexes = W.twisted_hex_mesh(2, 1)
     bad = hexes.copy()
     bad[0, [0, 1]] = bad[0, [1, 0]]  # mirrored cell
@@ -71,9 +71,9 @@ def test_errors_and_unsupported_problem():
     m = tf.HexMesh(xyz, hexes)
     q = tf.Quadrature(2, 4)
     C = len(hexes)
-    with pytest.raises(tf.TfError) as e:
+    with pytest.raises(tf.TfError) as e:  # hexahedra: no S1 (checked before any device work)
         tf.tf_problem_create(m.h, q.h, 1, 1, np.zeros(C, np.int32), np.ones((1, 1)), np.zeros((1, 1, 1)),
-                             np.zeros((C, 1, 8)))
+                             np.zeros((C, 1, 8)), S1=np.zeros((C, 1, 3)))
     assert e.value.status == tf.TF_ERR_ARG
 
 

@@ -303,6 +303,16 @@ def order3(cfg):
     return out
 
 
+def paper_hex_box(n=16, G=10, n_polar=8, n_az=32, seed=BASE_SEED + 7, twist=0.25):
+    """The paper's runtime-table workload as far as it is stated: 16^3 trilinear hexahedra
+    (the orthogonal grid twisted along one axis), 10 energy groups, 32 directions per octant
+    (8 polar x 32 azimuthal = 256); one material and the central box source as small_box."""
+    p = hex_problem(small_box(n=n, G=G, n_polar=n_polar, n_az=n_az, seed=seed, tol=1e-6, precision="f32"),
+                    twist=twist)
+    p["name"] = f"paper_hex_{n}^3_D{n_polar * n_az}_G{G}_twist{twist:g}"
+    return p
+
+
 CONFIGS = {
     "small_box": small_box,
     "two_material": two_material_box,
