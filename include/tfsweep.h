@@ -16,14 +16,18 @@
  *     in dependency order, every group inside one element visit, with the
  *     upwind face fluxes handed to downwind cells;
  *   - Eq. (3): the integrated flux per group and in total.
- * Spatial discretisation: upwind discontinuous Galerkin with linear basis
- * functions on tetrahedra (4 nodal unknowns per cell, group and direction).
+ * Spatial discretisation: upwind discontinuous Galerkin with nodal basis
+ * functions: linear, quadratic or cubic on tetrahedra (NB = 4, 10 or 20 unknowns
+ * per cell, group and direction; tf_options.order) or trilinear on hexahedra
+ * (NB = 8; tf_mesh_create_hex).
  *
  * Memory conventions:
  *   - creation inputs are host arrays; they are copied, the caller keeps them;
  *   - phi arrays passed to tf_sweep / tf_source_iterate are caller-owned,
- *     FP64, layout [n_cells][n_groups][4] (node i of cell c is local vertex i
- *     of tets[c]); they may live in device memory or in host memory (page-locked
+ *     FP64, layout [n_cells][n_groups][NB] (linear tetrahedra: node i of cell c
+ *     is local vertex i of tets[c]; the node orders of the other elements are
+ *     given with tf_options.order and tf_mesh_create_hex); they may live in
+ *     device memory or in host memory (page-locked
  *     host buffers mapped into the device address space, as cudaHostAlloc and
  *     torch's pin_memory give, are read and written by the kernels directly
  *     in tf_sweep; other host buffers are copied in and out inside the call);
@@ -242,7 +246,7 @@ tf_status tf_quadrature_create(int32_t n_polar, int32_t n_azimuthal, int32_t n_d
  *   cell_material [n_cells] in [0, n_materials);
  *   sigma_t [n_materials][n_groups] total cross section (> 0);
  *   sigma_s [n_materials][n_groups][n_groups], element [m][g_from][g_to];
- *   Q [n_cells][n_groups][4] total isotropic volumetric source at the nodes
+ *   Q [n_cells][n_groups][NB] total isotropic volumetric source at the nodes
  *     (the angular source per steradian is (Q + sum_g' sigma_s phi_g') / 4 pi);
  *   S1 [n_cells][n_groups][3] or NULL: adds the angular source Omega . S1
  *     (constant per cell; used by manufactured-solution tests);
@@ -261,7 +265,7 @@ tf_status tf_problem_create(tf_handle mesh, tf_handle quad, int32_t n_groups, in
  * a sweep of every direction (Algorithm 1: dependency counters released by
  * atomics, ready (cell block, direction) tasks pulled from a device queue),
  * and phi_out = sum_a w_a psi_a (Eq. 2).  phi_in / phi_out: [n] arrays of FP64
- * [n_cells][n_groups][4] buffers (device or host); phi_in[k] may equal
+ * [n_cells][n_groups][NB] buffers (device or host); phi_in[k] may equal
  * phi_out[k].  Synchronises `stream` before returning.
  * Errors: TF_ERR_ARG, TF_ERR_CUDA, TF_ERR_TIMEOUT, TF_ERR_DEVICE. */
 tf_status tf_sweep(const tf_handle *problems, int32_t n, const double *const *phi_in, double *const *phi_out,
@@ -304,7 +308,7 @@ tf_status tf_quadrature_get(tf_handle quad, int32_t *n_dirs, double *omega, doub
 tf_status tf_graph_levels(tf_handle mesh, tf_handle quad, uint8_t *inflow, int32_t *level);
 
 /* Copies the angular flux of direction `dir` from the last sweep of `problem`
- * into out (device memory, [n_cells][n_groups][4] in the problem precision:
+ * into out (device memory, [n_cells][n_groups][NB] in the problem precision:
  * float or double).  The direction must belong to the last direction chunk
  * swept (with one chunk: any direction).  Errors: TF_ERR_ARG, TF_ERR_CUDA. */
 tf_status tf_problem_psi(tf_handle problem, int32_t dir, void *out, void *stream);
