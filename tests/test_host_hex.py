@@ -91,3 +91,17 @@ def test_cycle_reported_like_the_oracle():
     with pytest.raises(tf.TfError) as e:
         tf.tf_graph_levels(m.h, q.h, m.n_cells, q.n_dirs)
     assert e.value.status == tf.TF_ERR_CYCLE
+
+
+def test_graph_bit_exact_paper_sized_workload():
+    """The paper's runtime-table size (16^3 twisted hexahedra, 256 directions): inflow masks and
+    t-levels of the library equal the oracle's."""
+    cfg = W.paper_hex_box()
+    geom = H.geometry(cfg["xyz"], cfg["hexes"])
+    om, _ = product_quadrature(cfg["n_polar"], cfg["n_azimuthal"])
+    inflow_ref, level_ref = H.graph(geom, om)
+    m = tf.HexMesh(cfg["xyz"], cfg["hexes"])
+    q = tf.Quadrature(cfg["n_polar"], cfg["n_azimuthal"])
+    inflow, level = tf.tf_graph_levels(m.h, q.h, m.n_cells, q.n_dirs)
+    assert np.array_equal(inflow, inflow_ref) and np.array_equal(level, level_ref)
+    assert level.max() + 1 == 61
