@@ -2,7 +2,7 @@
  * tflearn — learned initial flux for source iteration (part of libtfsweep.so).
  *
  * The paper has no counterpart of this part: its source iteration (the inner
- * and outer iterations of the benchmarks, Sec. 3 and Sec. 5) starts from a
+ * and outer iterations of the benchmarks, Sec. 3 and Sec. 3.6) starts from a
  * given scalar flux.  These calls train and run a small per-cell network that
  * proposes that starting flux; tf_source_iterate then runs unchanged from it,
  * with the same stopping test, so a zero start remains the plain method and

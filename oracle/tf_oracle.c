@@ -13,7 +13,7 @@
  * Algorithm for Unstructured S_N Transport on Shared Memory Systems"):
  *   - the steady multigroup transport problem of Eq. (1) with isotropic
  *     scattering, discretised by upwind discontinuous Galerkin on linear
- *     tetrahedra (the element-matrix ingredients of Table "tab:arrays":
+ *     tetrahedra (the element-matrix ingredients of Table 1:
  *     f_i df_j/dx det J, f_i f_j det J, face normals, face nodes, element
  *     neighbours), S_N directions from a product quadrature, energy groups;
  *   - the per-direction sweep in dependency (t-level) order, Sec. 2.1 and

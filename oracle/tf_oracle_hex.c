@@ -20,7 +20,7 @@
  * face-local nodes k = 0..3 are the vertices whose bit d equals s, in
  * increasing local index.
  *
- * Element integrals (the ingredients of Table "tab:arrays": f_i f_j det J,
+ * Element integrals (the ingredients of Table 1: f_i f_j det J,
  * f_i df_j/dx det J, face normals, face nodes, element neighbours):
  *     M[i][j]       = int_K b_i b_j dV
  *     Gd[d][i][j]   = int_K b_i (d b_j / d x_d) dV

@@ -7,7 +7,7 @@
  * Compiled with -ffp-contract=off.
  *
  * The paper runs first-, second- and third-order finite-element sweeps
- * (Sec. 5, the orders of Fig. fig:heatmap and Table tab:times); this file is
+ * (Sec. 3.6, the orders of Fig. 5 and Table 3); this file is
  * the second-order element on tetrahedra, written as the plain definition:
  *
  *   basis: quadratic Lagrange, ten nodes per cell, in this order:

@@ -1,5 +1,5 @@
 // Level-synchronous (bulk-synchronous) sweep schedule: the scheme the paper's
-// many-task sweep replaces (Sec. 2.1, Sec. 3; Fig. fig:schemes, centre).
+// many-task sweep replaces (Sec. 2.1, Sec. 3; Fig. 2, centre).
 // Included inside namespace tf after sweep_kernel.cuh (it needs SweepArgs).
 #pragma once
 

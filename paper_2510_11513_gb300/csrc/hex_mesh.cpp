@@ -5,7 +5,7 @@
 // x(xi) = sum_v x_v b_v(xi).  Face f = 2d + s is the reference face xi_d = s, its
 // face-local nodes the four vertices with bit d equal to s in increasing local index.
 //
-// The element integrals of Table tab:arrays (f_i f_j det J, f_i df_j/dx det J, face
+// The element integrals of Table 1 (f_i f_j det J, f_i df_j/dx det J, face
 // normals) are computed by exact polynomial algebra instead of quadrature: the map is
 // trilinear, so the tangents t_k = dx/dxi_k, the cofactor columns t_{k+1} x t_{k+2}
 // (the columns of det J times J^{-T}) and det J are polynomials of degree at most two per

@@ -29,7 +29,7 @@ inline void sorted3(int32_t a, int32_t b, int32_t c, int32_t out[3])
 // Basis function b_j of a linear tetrahedron has a constant gradient: rows of
 // the inverse of J = [x1-x0, x2-x0, x3-x0] for j = 1..3 and minus their sum
 // for j = 0 (these give the f_i df_j/dx det J element integrals of Table
-// tab:arrays as (V/4) d b_j / dx).  Face f is opposite local vertex f; its
+// Table 1 as (V/4) d b_j / dx).  Face f is opposite local vertex f; its
 // normal is (1/2)(xb - xa) x (xc - xa) over the face's global vertices in
 // increasing index order, flipped to point away from vertex f, so the two
 // cells sharing a face hold exactly opposite normals.
