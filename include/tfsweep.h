@@ -85,6 +85,21 @@ typedef enum {
  * Batched calls (n > 1) run only TF_SCHED_AMT problems. */
 typedef enum { TF_SCHED_AMT = 0, TF_SCHED_BSP = 1, TF_SCHED_BSP_LAUNCH = 2 } tf_schedule;
 
+/* Which cells form one task of a direction.  Both shapes solve the same units with the same
+ * arithmetic and give bit-identical psi and phi; they differ in the memory traffic and the
+ * parallelism of the sweep.
+ *   TF_TASK_LEVELS   up to cells_per_task cells of one t-level (cells that do not depend on each
+ *                    other: the buckets of Sec. 2.1 cut into blocks).
+ *   TF_TASK_PATCHES  spatial patches: the cells of one small box of space (patch_extent mean cell
+ *                    sizes on an edge) that can run together, listed in dependency order, at most
+ *                    cells_per_task (<= 64) of them.  A cell's upwind neighbour in the same patch
+ *                    was solved moments before by the same warp, so its face trace comes from
+ *                    the on-chip caches or registers instead of device memory.  Each direction's
+ *                    patch graph is acyclic by construction (a patch's round counts the region
+ *                    boundaries crossed on the longest upwind path).  Linear tetrahedra with
+ *                    n_groups a multiple of 32 and TF_SCHED_AMT only (else TF_ERR_ARG). */
+typedef enum { TF_TASK_AUTO = 0, TF_TASK_LEVELS = 1, TF_TASK_PATCHES = 2 } tf_task_shape;
+
 typedef struct {
     int32_t precision;       /* tf_precision: arithmetic of local solves and psi storage (default TF_FP32) */
     int32_t device;          /* CUDA device ordinal (default 0) */
@@ -127,12 +142,18 @@ typedef struct {
                               * (both NULL), no batching */
     int32_t keep_ready;      /* ready tasks a warp keeps on a private stack and runs next (most recent
                               * first) instead of queueing them; 0 = automatic (1), at most 4 */
-    int32_t reserved_i[1];
+    int32_t task_shape;      /* tf_task_shape: which cells form one task (the grain of Sec. 3.4).
+                              * 0 = automatic: spatial patches for linear tetrahedra with n_groups a
+                              * multiple of 32 (no packed group pairs) under TF_SCHED_AMT, whose
+                              * kernel variants solve a task's cells one after another; t-level
+                              * blocks otherwise */
     double residual_floor;   /* stopping-test denominator floor, as a fraction of the group's max |phi|:
                               * 1 (the default; 0 also means 1) = per-group max-norm relative change,
                               * 1e-10 = pointwise relative change (unreachable in FP32 where DG
                               * undershoots put |phi| near 0) */
-    double reserved_d[3];
+    double patch_extent;     /* spatial patches: edge of a patch region in mean cell sizes (the edge of
+                              * a cube of six tetrahedra of the mean volume); 0 = automatic (3) */
+    double reserved_d[2];
 } tf_options;
 
 /* Fills *opt with the defaults above. */
@@ -192,7 +213,7 @@ typedef struct {
     /* autotuning: the kernel-variant knobs in use after it (tf_options.pairing, staging,
      * octant_window; 0 = automatic), tuned after the grain where the caller left them automatic */
     int32_t tuned_pairing, tuned_staging, tuned_window;
-    int32_t reserved_i[1];
+    int32_t task_shape;        /* tf_task_shape in use: TF_TASK_LEVELS or TF_TASK_PATCHES */
     double data_wait_seconds;  /* summed over warps: time waiting for rows staged by bulk copies
                                 * (SM cycles at the nominal SM clock) */
     double reserved_d[5];
@@ -201,7 +222,7 @@ typedef struct {
 /* Mesh of tetrahedra.  xyz: host [n_vertices][3] FP64; tets: host [n_cells][4]
  * vertex indices.  Tetrahedra must be positively oriented (det of the edge
  * vectors x1-x0, x2-x0, x3-x0 > 0) and conforming (a face is shared by at most
- * two cells).  Computes volumes, basis gradients (Table tab:arrays' f_i df_j/dx
+ * two cells).  Computes volumes, basis gradients (Table 1's f_i df_j/dx
  * ingredients), area-weighted outward face normals and face neighbours.
  * Host-only: no CUDA call.  Errors: TF_ERR_ARG, TF_ERR_MESH, TF_ERR_NOMEM. */
 tf_status tf_mesh_create(int64_t n_vertices, const double *xyz, int64_t n_cells, const int32_t *tets,
@@ -307,6 +328,37 @@ tf_status tf_quadrature_get(tf_handle quad, int32_t *n_dirs, double *omega, doub
  * level [n_dirs][n_cells].  Either may be NULL.  Errors: TF_ERR_CYCLE. */
 tf_status tf_graph_levels(tf_handle mesh, tf_handle quad, uint8_t *inflow, int32_t *level);
 
+/* Host-only: the tasks a problem with options *opt (NULL = defaults) and n_groups groups on this
+ * mesh and quadrature would sweep (t-level blocks or spatial patches, tf_task_shape; the grain
+ * and shape chosen as tf_problem_create chooses them, without the autotuner: a negative
+ * cells_per_task is TF_ERR_ARG here).  *n_tasks: the number of tasks over all directions.
+ * task_of [n_dirs][n_cells]: the task (0 .. n_tasks - 1) that solves each cell in each direction;
+ * position [n_dirs][n_cells]: the cell's place in its task's list (a task solves its cells in
+ * that order); indeg [n_tasks]: the number of distinct other tasks holding an upwind cell of the
+ * task (its dependency counter's start).  Any array may be NULL (call once with all three NULL to
+ * learn n_tasks).  Errors: TF_ERR_ARG, TF_ERR_CYCLE, TF_ERR_NOMEM. */
+tf_status tf_graph_tasks(tf_handle mesh, tf_handle quad, const tf_options *opt, int32_t n_groups, int64_t *n_tasks,
+                         int32_t *task_of, int32_t *position, int32_t *indeg);
+
+/* Sum over the partners of a problem: replace buf[0 .. count) (device memory, FP64) by its
+ * elementwise sum over every partner's buffer of the same call (for example an allreduce across
+ * the processes that each sweep a share of the directions).  Called on the host thread of
+ * tf_sweep / tf_source_iterate with the stream their work runs on: the reduction must be
+ * enqueued on that stream (as an NCCL allreduce is) or finished before returning.  Return 0 on
+ * success; anything else ends the call with TF_ERR_CUDA. */
+typedef int32_t (*tf_reduce_fn)(void *user, double *buf, int64_t count, void *stream);
+
+/* Direction sharding.  A problem whose quadrature holds a share of a direction set (explicit
+ * omega and w in tf_quadrature_create) sweeps only those directions, so its phi = sum_a w_a psi_a
+ * (Eq. (2)) is a partial sum.  With a reduce function set, every transport step hands that
+ * partial phi ([n_cells][n_groups][NB] doubles) and this step's boundary leakage per group
+ * (n_groups doubles, for the particle balance) to `fn` right after the phi reduction and before
+ * the statistics, the stopping test and the next source update, so all partners iterate on the
+ * same full phi and take the same stopping decision.  fn = NULL removes it.  A problem with a
+ * reduce function runs its iterations without CUDA-graph capture and cannot be batched (n > 1:
+ * TF_ERR_ARG).  Errors: TF_ERR_ARG. */
+tf_status tf_problem_set_reduce(tf_handle problem, tf_reduce_fn fn, void *user);
+
 /* Copies the angular flux of direction `dir` from the last sweep of `problem`
  * into out (device memory, [n_cells][n_groups][NB] in the problem precision:
  * float or double).  The direction must belong to the last direction chunk
@@ -321,17 +373,21 @@ tf_status tf_problem_stats(tf_handle problem, tf_stats *out);
  * cannot allocate device memory, such as a host program whose device memory
  * is owned entirely by another runtime's pool, or a latency-critical loop that
  * must not pay cudaMalloc's implicit device synchronisation.
- *   phi    device [n_cells][n_groups][4] FP64 nodal scalar flux;
- *   volume device [n_cells] FP64 cell volumes;
- *   out    device [n_groups][3] FP64: max |phi|, the integral over space
- *          sum_c (V_c/4) sum_i phi (Eq. (3) with volume weights), and the
+ *   phi    [n_cells][n_groups][4] FP64 nodal scalar flux, 16-byte aligned;
+ *   volume [n_cells] FP64 cell volumes;
+ *   out    [n_groups][3] FP64: max |phi|, sum_c (V_c/4) sum_i phi, and the
  *          plain nodal sum sum_c sum_i phi.
+ * Each buffer must be memory the current device can reach: device memory of
+ * that device, managed memory, or page-locked host memory mapped into the
+ * device (cudaHostAlloc, torch's pin_memory); plain pageable host memory or a
+ * misaligned address is refused with TF_ERR_ARG before anything is launched.
  * Runs on the current device, asynchronously on `stream`.  Its reduction
  * scratch is one fixed 8 MiB array per device (held by every GPU that loads
  * the library until the process exits), shared by all calls: calls that
  * overlap on the GPU race on it.  Each call overwrites the part it uses, so
- * nothing carries over between calls.  The first call on a device looks the
- * array up (cudaGetSymbolAddress); make that first call before any stream
+ * nothing carries over between calls.  The first call on a device (and the
+ * first after the device's context changed, e.g. after cudaDeviceReset) looks
+ * the array up (cudaGetSymbolAddress); make that call before any stream
  * capture.  n_groups must be at most 1024 (TF_ERR_ARG otherwise).
  * Errors: TF_ERR_ARG, TF_ERR_CUDA. */
 tf_status tf_integrated_flux_noalloc(const double *phi, const double *volume, int64_t n_cells, int32_t n_groups,

@@ -51,9 +51,65 @@ T *as(tf_handle h, Kind k)
 
 }  // namespace tf
 
+namespace tf {
+// The kernel variants that solve a task's cells one after another (lanes over the groups of
+// one cell: n_groups a multiple of 32, FP32 without packed group pairs or FP64) accept tasks
+// whose cells depend on each other; the others, and the bulk-synchronous schedules (whose
+// buckets are t-levels), take t-level blocks.
+tf_status task_shape_of(const tf_options &o, const Mesh &m, int32_t G, bool *patches, TaskShape *shape)
+{
+    const bool paired = o.precision == TF_FP32 && G % 2 == 0 && (o.pairing == 2 || (o.pairing == 0 && G % 32 != 0));
+    const bool ok = m.nf == 4 && o.order <= 1 && o.schedule == TF_SCHED_AMT && G % 32 == 0 && !paired;
+    if (o.task_shape < TF_TASK_AUTO || o.task_shape > TF_TASK_PATCHES)
+        return fail(TF_ERR_ARG, "task_shape must be a tf_task_shape");
+    if (o.task_shape == TF_TASK_PATCHES && !ok)
+        return fail(TF_ERR_ARG, "spatial patches need linear tetrahedra, n_groups a multiple of 32, no packed "
+                                "group pairs and TF_SCHED_AMT");
+    if (!(o.patch_extent >= 0.0) || o.patch_extent > 64.0)
+        return fail(TF_ERR_ARG, "patch_extent must be in [0, 64]");
+    *patches = o.task_shape == TF_TASK_PATCHES || (o.task_shape == TF_TASK_AUTO && ok);
+    shape->extent = o.patch_extent > 0.0 ? o.patch_extent : 3.0;
+    // the staged kernels issue a cell's copies one cell ahead (two stages) or two (three stages)
+    const bool three = o.staging == 3 || (o.staging != 2 && o.precision == TF_FP64);
+    shape->gap = three ? 2 : 1;
+    return TF_OK;
+}
+// Cells per task (*B: the caller's value, or the default when it is 0) and the task shape.
+tf_status task_grain(const tf_options &o, const Mesh &m, int32_t n_groups, int32_t *B, bool *patches, TaskShape *shape)
+{
+    tf_status s = task_shape_of(o, m, n_groups, patches, shape);
+    if (s != TF_OK) return s;
+    int32_t b = *B;
+    if (b == 0 && *patches) {
+        b = 64;  // larger patches are cut into pieces of at most 64 cells (a warp's two entry registers)
+    } else if (b == 0) {
+        // about 1024 units per task (at most 64 cells); 256 units and 4 to 16 cells on the
+        // FP32 paired path, whose per-task cell table sets how many CTAs fit per SM
+        const bool paired = o.precision == TF_FP32 && n_groups % 2 == 0 &&
+                            (o.pairing == 2 || (o.pairing == 0 && n_groups % 32 != 0));
+        b = paired ? std::max(4, std::min(16, 256 / n_groups)) : std::max(2, std::min(64, 1024 / n_groups));
+        // second order: a unit is a 10 x 10 solve, about 256 units per task
+        if (o.order == 2) b = std::max(2, std::min(32, 256 / n_groups));
+        // third order: a unit is a 20 x 20 solve, about 64 units per task
+        if (o.order == 3) b = std::max(2, std::min(16, 64 / n_groups));
+        // trilinear hexahedra: an 8 x 8 solve, about 256 units per task as the second order
+        if (m.nf == 6) b = std::max(2, std::min(32, 256 / n_groups));
+        // Bulk-synchronous schedules: a bucket's tasks must cover the resident warps, and
+        // most buckets hold fewer cells than the many-task grain assumes; a quarter of it
+        // (at least 2 cells) took the least time over grains 1..64 on the 16^3-hex,
+        // 128-direction, 16-group and the 48^3-hex, 192-direction, 64-group boxes.
+        if (o.schedule != TF_SCHED_AMT) b = std::max(2, b / 4);
+    }
+    if (*patches && b > 64) return fail(TF_ERR_ARG, "spatial patches hold at most 64 cells");
+    *B = b;
+    return TF_OK;
+}
+}  // namespace tf
+
 using namespace tf;
 
 extern "C" {
+
 
 void tf_options_default(tf_options *opt)
 {
@@ -235,25 +291,10 @@ tf_status tf_problem_create(tf_handle mesh, tf_handle quad, int32_t n_groups, in
         p->opt.staging = p->tune.staging;
         p->opt.octant_window = p->tune.window;
     }
-    if (B == 0) {
-        // about 1024 units per task (at most 64 cells); 256 units and 4 to 16 cells on the
-        // FP32 paired path, whose per-task cell table sets how many CTAs fit per SM
-        const bool paired = p->opt.precision == TF_FP32 && n_groups % 2 == 0 &&
-                            (p->opt.pairing == 2 || (p->opt.pairing == 0 && n_groups % 32 != 0));
-        B = paired ? std::max(4, std::min(16, 256 / n_groups)) : std::max(2, std::min(64, 1024 / n_groups));
-        // second order: a unit is a 10 x 10 solve, about 256 units per task
-        if (p->opt.order == 2) B = std::max(2, std::min(32, 256 / n_groups));
-        // third order: a unit is a 20 x 20 solve, about 64 units per task
-        if (p->opt.order == 3) B = std::max(2, std::min(16, 64 / n_groups));
-        // trilinear hexahedra: an 8 x 8 solve, about 256 units per task as the second order
-        if (m->nf == 6) B = std::max(2, std::min(32, 256 / n_groups));
-        // Bulk-synchronous schedules: a bucket's tasks must cover the resident warps, and
-        // most buckets hold fewer cells than the many-task grain assumes; a quarter of it
-        // (at least 2 cells) took the least time over grains 1..64 on the 16^3-hex,
-        // 128-direction, 16-group and the 48^3-hex, 192-direction, 64-group boxes.
-        if (p->opt.schedule != TF_SCHED_AMT) B = std::max(2, B / 4);
-    }
-    tf_status s = build_task_graph(*m, *q, B, p->graph);
+    TaskShape shape;
+    bool patches = false;
+    tf_status s = task_grain(p->opt, *m, n_groups, &B, &patches, &shape);
+    if (s == TF_OK) s = build_task_graph(*m, *q, B, p->graph, patches ? &shape : nullptr);
     if (s == TF_OK) s = device_create(*p, cell_material, sigma_t, sigma_s, Q, S1, psi_inflow);
     if (s != TF_OK) {
         release(p);
@@ -340,6 +381,45 @@ tf_status tf_graph_levels(tf_handle mesh, tf_handle quad, uint8_t *inflow, int32
     Quad *q = as<Quad>(quad, Kind::Quad);
     if (!m || !q) return fail(TF_ERR_ARG, "tf_graph_levels: mesh or quadrature handle invalid");
     return classify_and_level(*m, *q, inflow, level);
+}
+
+tf_status tf_graph_tasks(tf_handle mesh, tf_handle quad, const tf_options *opt, int32_t n_groups, int64_t *n_tasks,
+                         int32_t *task_of, int32_t *position, int32_t *indeg)
+{
+    Mesh *m = as<Mesh>(mesh, Kind::Mesh);
+    Quad *q = as<Quad>(quad, Kind::Quad);
+    if (!m || !q || n_groups < 1 || n_groups > 1024) return fail(TF_ERR_ARG, "tf_graph_tasks: bad arguments");
+    tf_options o;
+    tf_options_default(&o);
+    if (opt) o = *opt;
+    if (o.cells_per_task < 0) return fail(TF_ERR_ARG, "tf_graph_tasks: the autotuned grain needs a device");
+    TaskShape shape;
+    bool patches = false;
+    int32_t B = o.cells_per_task;
+    tf_status s = task_grain(o, *m, n_groups, &B, &patches, &shape);
+    if (s != TF_OK) return s;
+    TaskGraph g;
+    if ((s = build_task_graph(*m, *q, B, g, patches ? &shape : nullptr)) != TF_OK) return s;
+    if (n_tasks) *n_tasks = g.T();
+    if (indeg) std::copy(g.task_indeg.begin(), g.task_indeg.end(), indeg);
+    for (int64_t t = 0; t < g.T(); ++t)
+        for (uint32_t i = 0; i < g.task_ncell[t]; ++i) {
+            const size_t e = (size_t)g.task_cell_begin[t] + i;
+            const int64_t c = g.cell_list[e] >> g.cell_shift;
+            const size_t at = (size_t)g.task_dir[t] * (size_t)m->nc + (size_t)c;
+            if (task_of) task_of[at] = (int32_t)t;
+            if (position) position[at] = (int32_t)i;
+        }
+    return TF_OK;
+}
+
+tf_status tf_problem_set_reduce(tf_handle problem, tf_reduce_fn fn, void *user)
+{
+    Problem *p = as<Problem>(problem, Kind::Problem);
+    if (!p) return fail(TF_ERR_ARG, "tf_problem_set_reduce: bad problem handle");
+    p->reduce = fn;
+    p->reduce_user = fn ? user : nullptr;
+    return TF_OK;
 }
 
 tf_status tf_problem_psi(tf_handle problem, int32_t dir, void *out, void *stream)

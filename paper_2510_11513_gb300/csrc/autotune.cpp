@@ -39,7 +39,7 @@ tf_status autotune_cells_per_task(const Mesh &m, const Quad &q, int32_t G, int32
                                   int32_t *out, tf_autotune_report *rep)
 {
     const int lc = (int)std::lround(std::log2((double)std::max<int64_t>(m.nc, 1)));
-    const auto key = std::make_tuple(opt.precision * 64 + opt.order * 16 + opt.schedule * 4 +
+    const auto key = std::make_tuple(opt.task_shape * 256 + opt.precision * 64 + opt.order * 16 + opt.schedule * 4 +
                                          (opt.cells_per_task == -2 ? 1 : 0),
                                      G, q.D, lc);
     {
@@ -94,7 +94,10 @@ tf_status autotune_cells_per_task(const Mesh &m, const Quad &q, int32_t G, int32
         retain(p->quad);
         p->G = G;
         p->M = M;
-        tf_status s = build_task_graph(m, *qs, o.cells_per_task, p->graph);
+        TaskShape shape;
+        bool patches = false;
+        tf_status s = task_shape_of(o, m, G, &patches, &shape);
+        if (s == TF_OK) s = build_task_graph(m, *qs, o.cells_per_task, p->graph, patches ? &shape : nullptr);
         if (s == TF_OK) s = device_create(*p, cell_material, sigma_t, sigma_s, Q, nullptr, nullptr);
         double t = 1e300;
         if (s == TF_OK) {

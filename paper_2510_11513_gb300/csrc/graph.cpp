@@ -2,10 +2,14 @@
 //
 // For every direction: classify faces (Sec. 2.1: the sweep's dependencies form
 // a DAG per angle), compute t-levels (the "buckets" of the schedule), group the
-// cells of one t-level into cell blocks, and derive the block-level dependency
-// graph: a block's in-degree counts its distinct upwind blocks (the atomic
-// counters of Sec. 3.5) and its downwind list names the blocks it releases
-// (Algorithm 1's "Downwind neighbours").
+// cells into tasks, and derive the task-level dependency graph: a task's
+// in-degree counts its distinct upwind tasks (the atomic counters of Sec. 3.5)
+// and its downwind list names the tasks it releases (Algorithm 1's "Downwind
+// neighbours").  Two task shapes (the granularity question of Sec. 3.4):
+//   - t-level blocks: up to B cells of one t-level (independent of each other);
+//   - spatial patches: cells of one small box of space, in an order that respects
+//     their dependencies, so that most upwind face traces a task's cells need are
+//     produced inside the same task and never leave the chip.
 #include <algorithm>
 #include <atomic>
 #include <cmath>
@@ -105,7 +109,104 @@ struct DirTasks {
     bool ok = true;
 };
 
-void build_direction(const Mesh &m, const double *O, int32_t B, DirTasks &out)
+// Spatial patches of one direction.  Every cell gets a round: 0 without interior
+// inflow faces, else the largest over its upwind cells u of round(u), plus one
+// when u lies in another region.  The cells of one (round, region) pair form a
+// patch (split into pieces of at most B cells).  Every edge between two patches
+// then goes from a lower round to a higher one, or between pieces of one patch in
+// their order, so the patch graph has no cycle, whatever the regions look like.
+// Inside a patch the cells are listed in an order that respects their
+// dependencies; a cell that depends on one of the `gap` cells listed just
+// before it is avoided when another is ready (the kernel stages a cell's inputs
+// `gap` cells ahead, and such a trace cannot be staged from memory).
+void patch_tasks(const Mesh &m, const uint8_t *mask, const int32_t *lev, const std::vector<int32_t> &order,
+                 const std::vector<int32_t> &region, int32_t B, int32_t gap, std::vector<int32_t> &task_of,
+                 DirTasks &out)
+{
+    const int64_t nc = m.nc;
+    const int nf = m.nf, sh = nf == 6 ? 6 : 4;
+    auto upwind = [&](int64_t c, int f) -> int32_t {
+        const int32_t n = m.nbr[nf * c + f];
+        return (((mask[c] >> f) & 1) && n >= 0) ? n : -1;
+    };
+    std::vector<int32_t> rnd(nc, 0);
+    for (int64_t i = 0; i < nc; ++i) {  // t-level order is a topological order
+        const int32_t c = order[i];
+        int32_t r = 0;
+        for (int f = 0; f < nf; ++f) {
+            const int32_t u = upwind(c, f);
+            if (u >= 0) r = std::max(r, rnd[u] + (region[u] != region[c] ? 1 : 0));
+        }
+        rnd[c] = r;
+    }
+    // cells grouped by (round, region), t-level order inside a group (stable sort of the level order)
+    std::vector<int32_t> by(order);
+    std::stable_sort(by.begin(), by.end(), [&](int32_t x, int32_t y) {
+        return rnd[x] != rnd[y] ? rnd[x] < rnd[y] : region[x] < region[y];
+    });
+    out.cells.resize(nc);
+    std::vector<int32_t> pos_in(nc, -1), indeg_in, picked;
+    std::vector<uint8_t> done;
+    int64_t w = 0;
+    for (int64_t g0 = 0; g0 < nc;) {
+        int64_t g1 = g0 + 1;
+        while (g1 < nc && rnd[by[g1]] == rnd[by[g0]] && region[by[g1]] == region[by[g0]]) ++g1;
+        const int64_t n = g1 - g0;
+        for (int64_t k = 0; k < n; ++k) pos_in[by[g0 + k]] = (int32_t)k;
+        indeg_in.assign(n, 0);
+        done.assign(n, 0);
+        for (int64_t k = 0; k < n; ++k)
+            for (int f = 0; f < nf; ++f) {
+                const int32_t u = upwind(by[g0 + k], f);
+                if (u >= 0 && pos_in[u] >= 0) ++indeg_in[k];
+            }
+        // list scheduling: the first ready cell in t-level order that does not depend on the
+        // last `gap` listed cells, else the first ready cell
+        picked.clear();
+        for (int64_t step = 0; step < n; ++step) {
+            int64_t pick = -1, first = -1;
+            for (int64_t k = 0; k < n && pick < 0; ++k) {
+                if (done[k] || indeg_in[k] != 0) continue;
+                if (first < 0) first = k;
+                bool near = false;
+                for (int f = 0; f < nf && !near; ++f) {
+                    const int32_t u = upwind(by[g0 + k], f);
+                    if (u < 0 || pos_in[u] < 0) continue;
+                    for (int64_t j = (int64_t)picked.size() - 1; j >= 0 && j >= (int64_t)picked.size() - gap; --j)
+                        if (picked[j] == pos_in[u]) near = true;
+                }
+                if (!near) pick = k;
+            }
+            if (pick < 0) pick = first;
+            done[pick] = 1;
+            picked.push_back((int32_t)pick);
+            const int32_t c = by[g0 + pick];
+            for (int f = 0; f < nf; ++f) {  // downwind cells of c inside the group
+                const int32_t d = m.nbr[nf * c + f];
+                if (d >= 0 && pos_in[d] >= 0 && ((mask[d] >> m.nbr_face[nf * c + f]) & 1)) --indeg_in[pos_in[d]];
+            }
+        }
+        // pieces of at most B cells, in the listed order
+        const int64_t np = (n + B - 1) / B;
+        for (int64_t k = 0; k < np; ++k) {
+            const int64_t s = (n * k) / np, e = (n * (k + 1)) / np;
+            const int32_t id = (int32_t)out.ncell.size();
+            out.cell_begin.push_back((uint32_t)(w));
+            out.ncell.push_back((uint16_t)(e - s));
+            out.level.push_back(rnd[by[g0]]);
+            for (int64_t i = s; i < e; ++i) {
+                const int32_t c = by[g0 + picked[i]];
+                task_of[c] = id;
+                out.cells[w++] = ((uint32_t)c << sh) | mask[c];
+            }
+        }
+        for (int64_t k = 0; k < n; ++k) pos_in[by[g0 + k]] = -1;
+        g0 = g1;
+    }
+}
+
+void build_direction(const Mesh &m, const double *O, int32_t B, const std::vector<int32_t> *region, int32_t gap,
+                     DirTasks &out)
 {
     const int64_t nc = m.nc;
     const int nf = m.nf, sh = nf == 6 ? 6 : 4;
@@ -128,22 +229,26 @@ void build_direction(const Mesh &m, const double *O, int32_t B, DirTasks &out)
         std::vector<int64_t> pos(lstart.begin(), lstart.end() - 1);
         for (int64_t c = 0; c < nc; ++c) order[pos[lev[c]]++] = (int32_t)c;
     }
-    // split every level into ceil(m / B) blocks of balanced size
     std::vector<int32_t> block_of(nc);
-    out.cells.resize(nc);
-    for (int32_t l = 0; l < L; ++l) {
-        const int64_t b0 = lstart[l], mcount = lstart[l + 1] - lstart[l];
-        const int64_t nb = (mcount + B - 1) / B;
-        for (int64_t k = 0; k < nb; ++k) {
-            const int64_t s = b0 + (mcount * k) / nb, e = b0 + (mcount * (k + 1)) / nb;
-            const int32_t id = (int32_t)out.ncell.size();
-            out.cell_begin.push_back((uint32_t)s);
-            out.ncell.push_back((uint16_t)(e - s));
-            out.level.push_back(l);
-            for (int64_t i = s; i < e; ++i) {
-                const int32_t c = order[i];
-                block_of[c] = id;
-                out.cells[i] = ((uint32_t)c << sh) | mask[c];
+    if (region) {
+        patch_tasks(m, mask.data(), lev.data(), order, *region, B, gap, block_of, out);
+    } else {
+        // split every level into ceil(m / B) blocks of balanced size
+        out.cells.resize(nc);
+        for (int32_t l = 0; l < L; ++l) {
+            const int64_t b0 = lstart[l], mcount = lstart[l + 1] - lstart[l];
+            const int64_t nb = (mcount + B - 1) / B;
+            for (int64_t k = 0; k < nb; ++k) {
+                const int64_t s = b0 + (mcount * k) / nb, e = b0 + (mcount * (k + 1)) / nb;
+                const int32_t id = (int32_t)out.ncell.size();
+                out.cell_begin.push_back((uint32_t)s);
+                out.ncell.push_back((uint16_t)(e - s));
+                out.level.push_back(l);
+                for (int64_t i = s; i < e; ++i) {
+                    const int32_t c = order[i];
+                    block_of[c] = id;
+                    out.cells[i] = ((uint32_t)c << sh) | mask[c];
+                }
             }
         }
     }
@@ -157,7 +262,8 @@ void build_direction(const Mesh &m, const double *O, int32_t B, DirTasks &out)
         for (uint32_t i = out.cell_begin[b]; i < out.cell_begin[b] + out.ncell[b]; ++i) {
             const int32_t c = (int32_t)(out.cells[i] >> sh);
             for (int f = 0; f < nf; ++f)
-                if (((mask[c] >> f) & 1) && m.nbr[nf * c + f] >= 0) tmp.push_back(block_of[m.nbr[nf * c + f]]);
+                if (((mask[c] >> f) & 1) && m.nbr[nf * c + f] >= 0 && block_of[m.nbr[nf * c + f]] != b)
+                    tmp.push_back(block_of[m.nbr[nf * c + f]]);
         }
         std::sort(tmp.begin(), tmp.end());
         out.indeg[b] = (int32_t)(std::unique(tmp.begin(), tmp.end()) - tmp.begin());
@@ -167,7 +273,7 @@ void build_direction(const Mesh &m, const double *O, int32_t B, DirTasks &out)
             const int32_t c = (int32_t)(out.cells[i] >> sh);
             for (int f = 0; f < nf; ++f) {
                 const int32_t n = m.nbr[nf * c + f];
-                if (n >= 0 && ((mask[n] >> m.nbr_face[nf * c + f]) & 1)) tmp.push_back(block_of[n]);
+                if (n >= 0 && ((mask[n] >> m.nbr_face[nf * c + f]) & 1) && block_of[n] != b) tmp.push_back(block_of[n]);
             }
         }
         std::sort(tmp.begin(), tmp.end());
@@ -175,7 +281,8 @@ void build_direction(const Mesh &m, const double *O, int32_t B, DirTasks &out)
         out.down.insert(out.down.end(), tmp.begin(), tmp.end());
         out.down_begin[b + 1] = (uint32_t)out.down.size();
     }
-    // b-level: longest chain of downwind blocks below each block (blocks are in level order)
+    // b-level: longest chain of downwind tasks below each task (tasks are in a topological
+    // order: t-level blocks by level, patches by round and, inside a patch, by piece)
     out.blevel.assign(T, 0);
     for (int32_t b = T - 1; b >= 0; --b) {
         int32_t v = 0;
@@ -186,18 +293,57 @@ void build_direction(const Mesh &m, const double *O, int32_t B, DirTasks &out)
 
 }  // namespace
 
-tf_status build_task_graph(const Mesh &m, const Quad &q, int32_t B, TaskGraph &g)
+// Regions of the spatial patches: boxes of edge `extent` times the mean cell size
+// (the edge of a cube holding six tetrahedra of the mean volume, or one hexahedron),
+// aligned with the mesh's bounding box; a cell belongs to the box holding its
+// vertex centroid.
+static void patch_regions(const Mesh &m, double extent, std::vector<int32_t> &region)
+{
+    const int nv_cell = m.nf == 6 ? 8 : 4;
+    const int32_t *cv = m.nf == 6 ? m.hexes.data() : m.tets.data();
+    double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300}, vol = 0.0;
+    for (int64_t v = 0; v < m.nv; ++v)
+        for (int d = 0; d < 3; ++d) {
+            lo[d] = std::min(lo[d], m.xyz[3 * v + d]);
+            hi[d] = std::max(hi[d], m.xyz[3 * v + d]);
+        }
+    for (int64_t c = 0; c < m.nc; ++c) vol += m.vol[c];
+    const double h = std::cbrt((m.nf == 6 ? 1.0 : 6.0) * vol / (double)std::max<int64_t>(1, m.nc));
+    const double edge = std::max(extent, 1e-3) * h;
+    int64_t nb[3];
+    for (int d = 0; d < 3; ++d) nb[d] = std::max<int64_t>(1, (int64_t)std::floor((hi[d] - lo[d]) / edge) + 1);
+    region.resize(m.nc);
+    for (int64_t c = 0; c < m.nc; ++c) {
+        int64_t b[3];
+        for (int d = 0; d < 3; ++d) {
+            double x = 0.0;
+            for (int k = 0; k < nv_cell; ++k) x += m.xyz[3 * (int64_t)cv[nv_cell * c + k] + d];
+            x /= nv_cell;
+            b[d] = std::min(nb[d] - 1, std::max<int64_t>(0, (int64_t)std::floor((x - lo[d]) / edge)));
+        }
+        region[c] = (int32_t)((b[0] + nb[0] * (b[1] + nb[1] * b[2])) % 2147483647);
+    }
+}
+
+tf_status build_task_graph(const Mesh &m, const Quad &q, int32_t B, TaskGraph &g, const TaskShape *shape)
 {
     if (B < 1 || B > 4096) return fail(TF_ERR_ARG, "cells_per_task must be in [1, 4096]");
     const int sh = m.nf == 6 ? 6 : 4;
     if (m.nc >= (int64_t(1) << (32 - sh)))
         return fail(TF_ERR_ARG, "mesh too large: at most 2^" + std::to_string(32 - sh) + " - 1 cells");
+    if (shape && (B > 64 || shape->gap < 0 || shape->gap > 8))
+        return fail(TF_ERR_ARG, "spatial patches: at most 64 cells per task");
     std::vector<DirTasks> per(q.D);
+    std::vector<int32_t> region;
     try {
-        run_parallel(q.D, [&](int32_t a) { build_direction(m, &q.omega[3 * a], B, per[a]); });
+        if (shape) patch_regions(m, shape->extent, region);
+        run_parallel(q.D, [&](int32_t a) {
+            build_direction(m, &q.omega[3 * a], B, shape ? &region : nullptr, shape ? shape->gap : 0, per[a]);
+        });
     } catch (const std::bad_alloc &) {
         return fail(TF_ERR_NOMEM, "graph: host allocation failed");
     }
+    g.patches = shape != nullptr;
     for (auto &d : per)
         if (!d.ok) return fail(TF_ERR_CYCLE, "graph: a direction's dependency graph has a cycle");
     g.D = q.D;

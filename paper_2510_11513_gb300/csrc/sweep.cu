@@ -667,6 +667,8 @@ struct DeviceState {
     int32_t *ho_fn = nullptr;  // higher orders: [4][nodes per face] face nodes
     double *ho_fav = nullptr;  // higher orders: int_f phi / A_f on a face's nodes
     bool two_stage = false;  // staged path with two stages (mode 4)
+    bool patches = false;    // spatial-patch tasks: a task's cells may depend on each other
+    uint8_t *cells_aux = nullptr;  // patches, staged variants: per cell entry, its in-task upwind handoffs
     int pair_stages = 3;     // paired path: buffers in the ring of staged copies
     size_t tsize = 4;  // sizeof(T)
     void *geo = nullptr;
@@ -1405,6 +1407,55 @@ tf_status device_create(Problem &p, const int32_t *cell_material, const double *
              : d.paired  ? 3
              : d.staged  ? (d.two_stage ? 4 : 2)
                          : (d.G % 32 == 0 && g.cells_per_task <= 64 ? 1 : 0);
+    // tasks whose cells depend on each other need a variant that solves a task's cells one
+    // after another with every lane on the groups of one cell (modes 1, 2, 4)
+    if (g.patches && !(d.mode == 1 || d.mode == 2 || d.mode == 4) )
+        return fail(TF_ERR_ARG, "spatial-patch tasks need a kernel variant with lanes over one cell's groups");
+    d.patches = g.patches;
+    if (d.patches && (d.mode == 2 || d.mode == 4)) {
+        // Per cell entry of a patch task, in the kernel's sorted face order (one byte):
+        //   bits 0-2  upwind slots (interior inflow faces by rank) that the lanes fill, because
+        //             the upwind cell is one of the task's NS - 1 cells listed just before: it is
+        //             not solved yet when this cell's copies are issued;
+        //   bit 3     the cell copies a row of an earlier cell of its own task (its lanes order
+        //             their stores of that row before the copy);
+        //   bits 4-5  slot + 1 of the next cell that takes this cell's solution (0: none);
+        //   bits 6-7  the same for the cell after next (three stages).
+        const int NS = d.mode == 4 ? 2 : 3;
+        std::vector<uint8_t> aux(g.cell_list.size(), 0);
+        std::vector<int32_t> pos_of;  // position in the current task, by cell (-1 outside)
+        pos_of.assign(m.nc, -1);
+        for (int64_t t = 0; t < T; ++t) {
+            const uint32_t b = g.task_cell_begin[t], n = g.task_ncell[t];
+            for (uint32_t i = 0; i < n; ++i) pos_of[g.cell_list[b + i] >> 4] = (int32_t)i;
+            for (uint32_t i = 0; i < n; ++i) {
+                const uint32_t e = g.cell_list[b + i], c = e >> 4, mk = e & 15u;
+                int s2u[4];
+                sorted_order(&m.tets[4 * (int64_t)c], s2u);
+                int r = 0;
+                for (int j = 0; j < 4; ++j) {
+                    const int u = s2u[j];
+                    const int32_t nb = m.nbr[4 * (int64_t)c + u];
+                    if (!((mk >> u) & 1u) || nb < 0) continue;
+                    const int32_t p = pos_of[nb];
+                    if (p >= 0 && p < (int32_t)i) {
+                        const int dist = (int)i - p;
+                        if (dist <= NS - 1) {
+                            aux[b + i] |= (uint8_t)(1u << r);
+                            aux[b + p] |= (uint8_t)((r + 1) << (dist == 1 ? 4 : 6));
+                        } else {
+                            aux[b + i] |= 8u;
+                        }
+                    } else if (p >= (int32_t)i) {
+                        return fail(TF_ERR_DEVICE, "patch task lists an upwind cell after its downwind cell");
+                    }
+                    ++r;
+                }
+            }
+            for (uint32_t i = 0; i < n; ++i) pos_of[g.cell_list[b + i] >> 4] = -1;
+        }
+        if ((s = upload(d, &d.cells_aux, aux.data(), aux.size())) != TF_OK) return s;
+    }
     if (d.paired) {
         d.staged = false;
         // three buffers unless two let more CTAs be resident per SM
@@ -1493,6 +1544,7 @@ tf_status device_create(Problem &p, const int32_t *cell_material, const double *
     p.stats.grid_ctas = d.schedule == TF_SCHED_AMT ? d.grid : d.bsp_grid;
     p.stats.warps_per_cta = d.wpc;
     p.stats.cells_per_task = g.cells_per_task;
+    p.stats.task_shape = g.patches ? TF_TASK_PATCHES : TF_TASK_LEVELS;
     return TF_OK;
 }
 
@@ -1652,6 +1704,8 @@ template <class T> SweepArgs<T> make_args(Problem &p, int k)
     A.n_tasks = (unsigned long long)(t1 - t0);
     A.wait_limit_ns = (unsigned long long)(p.opt.wait_limit_s * 1e9);
     A.max_cells = p.graph.cells_per_task;
+    A.intra = d.patches ? 1 : 0;
+    A.aux = d.cells_aux;
     A.warp_smem = d.warp_smem;
     A.dir_group = d.dir_group;
     A.group_rem = d.group_rem + gb;
@@ -1882,6 +1936,15 @@ tf_status collect(Problem &p, cudaStream_t st, bool copied = false)
 
 }  // namespace
 
+// Direction sharding: the partners' sum of a partial buffer (phi, or the leakage per group).
+static tf_status reduce_partial(Problem &p, double *buf, int64_t count, cudaStream_t st)
+{
+    const int32_t r = p.reduce(p.reduce_user, buf, count, (void *)st);
+    if (r != 0) return fail(TF_ERR_CUDA, "reduce callback returned " + std::to_string(r));
+    TF_CUDA(cudaGetLastError());
+    return TF_OK;
+}
+
 tf_status device_sweep(Problem &p, const double *phi_in, double *phi_out, void *stream)
 {
     DeviceState &d = *p.dev;
@@ -1904,9 +1967,11 @@ tf_status device_sweep(Problem &p, const double *phi_in, double *phi_out, void *
             in = d.phi_buf[0];
         }
     }
+    if (p.reduce) map_out = nullptr;  // the partners' sum works on a device buffer
     if (host_out) out = map_out ? map_out : d.phi_buf[1];
     tf_status s = step(p, in, out, st);
     if (s != TF_OK) return s;
+    if (p.reduce && (s = reduce_partial(p, out, (int64_t)(bytes / 8), st)) != TF_OK) return s;
     if (host_out && !map_out) TF_CUDA(cudaMemcpyAsync(phi_out, out, bytes, cudaMemcpyDeviceToHost, st));
     return collect(p, st);
 }
@@ -1920,6 +1985,10 @@ tf_status enqueue_iteration(Problem &p, const double *cur, double *nxt, cudaStre
     DeviceState &d = *p.dev;
     tf_status s = step(p, cur, nxt, st);
     if (s != TF_OK) return s;
+    if (p.reduce) {  // direction sharding: every partner continues from the full phi and leakage
+        if ((s = reduce_partial(p, nxt, (int64_t)d.C * d.G * d.nb, st)) != TF_OK) return s;
+        if ((s = reduce_partial(p, d.leak, d.G, st)) != TF_OK) return s;
+    }
     launch_stats(p, cur, nxt, st);
     TF_CUDA(cudaGetLastError());
     TF_CUDA(cudaMemcpyAsync(d.ctrl_host, d.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
@@ -1978,14 +2047,14 @@ tf_status device_iterate(Problem &p, double tol, int32_t max_iters, double *phi,
     const bool host = !is_device_pointer(phi);
     TF_CUDA(cudaEventRecord(d.ev_user, user));
     TF_CUDA(cudaStreamWaitEvent(st, d.ev_user, 0));
-    if (!d.graphs_tried) build_iteration_graphs(p);
+    if (!d.graphs_tried && !p.reduce) build_iteration_graphs(p);
     int k = 0;  // phi_buf[k] holds the current iterate
     TF_CUDA(cudaMemcpyAsync(d.phi_buf[0], phi, bytes, host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, st));
     double r = INFINITY, bal = 0.0;
     int it = 0;
     bool conv = false;
     for (it = 1; it <= max_iters; ++it) {
-        if (d.gexec[k]) {
+        if (d.gexec[k] && !p.reduce) {
             TF_CUDA(cudaGraphLaunch(d.gexec[k], st));
         } else {
             const tf_status s = enqueue_iteration(p, d.phi_buf[k], d.phi_buf[1 - k], st);
@@ -2086,6 +2155,7 @@ tf_status batch_setup(BatchRun &B, const tf_handle *problems, int32_t n)
         if (p->dev->device != B.device || p->dev->fp64 != B.fp64)
             return fail(TF_ERR_ARG, "batched problems must share one device and one precision");
         if (p->opt.inject_stall) return fail(TF_ERR_ARG, "inject_stall is not supported in batched launches");
+        if (p->reduce) return fail(TF_ERR_ARG, "a problem with a reduce function (direction sharding) cannot be batched");
         if (p->dev->schedule != TF_SCHED_AMT || p->dev->order != 1 || p->dev->hex)
             return fail(TF_ERR_ARG, "batched launches run only linear-element problems with the TF_SCHED_AMT schedule");
         B.max_chunks = std::max(B.max_chunks, p->dev->n_chunks);

@@ -180,6 +180,8 @@ template <class T> struct SweepArgs {
     int32_t mode;                // kernel variant of this problem (batched launches dispatch on it)
     const void *geo2;            // second-order element: P2Geo<T> [C] cell records (modes 5, 6); P3Geo<T> (7); HexGeo<T> (8)
     int32_t keep_max;            // ready tasks a warp keeps and runs next (1..4)
+    int32_t intra;               // 1: a task's cells may depend on each other (spatial patches)
+    const uint8_t *aux;          // patches, staged variants: per cell entry, its in-task upwind handoffs
     const void *p3tab;           // third-order element: P3Dev<T> tables (mode 7)
 };
 
@@ -527,9 +529,12 @@ __device__ __forceinline__ f2 nrcp2(f2 a)
 // Solve every group of one staged cell: lane l takes groups l, l+32, ...
 // NPL > 0: exactly NPL groups per lane (G = 32 NPL), unrolled so that the
 // independent solves of a lane's groups interleave; NPL = 0: any G.
+// fill0 / fill1: when not NULL, shared-memory upwind rows of later cells of the same task
+// (spatial patches) that take this cell's solution; each lane writes the entries it solves.
 template <class T, int NPL>
 __device__ __forceinline__ void solve_staged_cell(const SweepArgs<T> &A, const unsigned char *st_base, uint32_t entry,
-                                                  int lane, T ox, T oy, T oz, size_t psi_dir, const StageLayout<T> &L)
+                                                  int lane, T ox, T oy, T oz, size_t psi_dir, const StageLayout<T> &L,
+                                                  V4<T> *fill0, V4<T> *fill1)
 {
     const CellGeo<T> &g = *reinterpret_cast<const CellGeo<T> *>(st_base);
     const V4<T> *qrow = reinterpret_cast<const V4<T> *>(st_base + sizeof(CellGeo<T>));
@@ -612,6 +617,8 @@ __device__ __forceinline__ void solve_staged_cell(const SweepArgs<T> &A, const u
         o.z = x[2];
         o.w = x[3];
         st_psi(out + gg, o);
+        if (fill0) fill0[gg] = o;
+        if (fill1) fill1[gg] = o;
     };
     if constexpr (NPL == 2 && sizeof(T) == 4) {
         // G = 64, FP32: the lane's two groups (lane, lane + 32) packed into f32x2 pairs,
@@ -691,8 +698,17 @@ __device__ __forceinline__ void solve_staged_cell(const SweepArgs<T> &A, const u
         upk(y1, x1a, x1b);
         upk(y2, x2a, x2b);
         upk(y3, x3a, x3b);
-        reinterpret_cast<float4 *>(out)[lane] = make_float4(-x0a, -x1a, -x2a, -x3a);
-        reinterpret_cast<float4 *>(out)[lane + 32] = make_float4(-x0b, -x1b, -x2b, -x3b);
+        const float4 oa = make_float4(-x0a, -x1a, -x2a, -x3a), ob = make_float4(-x0b, -x1b, -x2b, -x3b);
+        reinterpret_cast<float4 *>(out)[lane] = oa;
+        reinterpret_cast<float4 *>(out)[lane + 32] = ob;
+        if (fill0) {
+            reinterpret_cast<float4 *>(fill0)[lane] = oa;
+            reinterpret_cast<float4 *>(fill0)[lane + 32] = ob;
+        }
+        if (fill1) {
+            reinterpret_cast<float4 *>(fill1)[lane] = oa;
+            reinterpret_cast<float4 *>(fill1)[lane + 32] = ob;
+        }
     } else if constexpr (NPL > 0) {
         // the lane's NPL groups side by side: every face test and trace selection is made
         // once per cell and the independent solves interleave
@@ -766,19 +782,28 @@ __device__ __forceinline__ void solve_staged_cell(const SweepArgs<T> &A, const u
             o.z = x[2];
             o.w = x[3];
             st_psi(out + lane + 32 * k, o);
+            if (fill0) fill0[lane + 32 * k] = o;
+            if (fill1) fill1[lane + 32 * k] = o;
         }
     } else {
         for (int gg = lane; gg < A.G; gg += 32) unit(gg);
     }
 }
 
-// One task through the staged pipeline.  Stage of cell k = k mod 3; for each
+// One task through the staged pipeline.  Stage of cell k = k mod NS; for each
 // stage two mbarriers (geometry+source, upwind rows) whose phase parities are
 // kept in `ph` (bit s: geometry barrier of stage s, bit 3+s: upwind barrier).
 // Each lane first reads the neighbour list of its cell(s) straight from the
 // records, so every copy of cell k (record, source row, upwind rows) is issued
-// together, two cells ahead of the solve.  Returns false if a wait ran out
+// together, NS - 1 cells ahead of the solve.  Returns false if a wait ran out
 // (error word set).
+// Spatial patches (A.intra): an upwind cell may be cell p < k of the same task;
+// the host marks each cell entry (A.aux, one byte).  If p was solved before
+// cell k's copies are issued (p <= k - NS), its row is copied like any other,
+// after every lane has ordered its own stores of that row before the copy (proxy
+// fence; the row is still in L2, so the copy costs no device-memory read);
+// otherwise the lanes write the entries of p's solution they computed into k's
+// upwind slot as they finish p (a lane reads back only what it wrote).
 template <class T, int NPL, int NS = 3>
 __device__ __forceinline__ bool run_task_staged(const SweepArgs<T> &A, uint4 ti, int lane, T ox, T oy, T oz,
                                                 size_t psi_dir, unsigned char *wsm, uint64_t *bars, uint32_t &ph,
@@ -790,18 +815,23 @@ __device__ __forceinline__ bool run_task_staged(const SweepArgs<T> &A, uint4 ti,
     const StageLayout<T> L(A.G);
     const uint32_t e_lo = lane < (int)ncell ? __ldg(A.cells + ti.x + lane) : 0u;
     const uint32_t e_hi = lane + 32 < (int)ncell ? __ldg(A.cells + ti.x + 32 + lane) : 0u;
+    const bool intra = A.intra != 0;
+    const uint32_t a_lo = intra && lane < (int)ncell ? (uint32_t)__ldg(A.aux + ti.x + lane) : 0u;
+    const uint32_t a_hi = intra && lane + 32 < (int)ncell ? (uint32_t)__ldg(A.aux + ti.x + 32 + lane) : 0u;
     int4 n_lo = make_int4(-1, -1, -1, -1), n_hi = n_lo;
     if (lane < (int)ncell) n_lo = __ldg(reinterpret_cast<const int4 *>(A.geo[e_lo >> 4].nbr));
     if (lane + 32 < (int)ncell) n_hi = __ldg(reinterpret_cast<const int4 *>(A.geo[e_hi >> 4].nbr));
     // psi rows written by other warps (generic proxy, acquired through the
     // queue) are read here by the async proxy
     if (lane == 0) fence_proxy_async_global();
-    // Copies of cell k into stage k mod 3, one per lane: lane 0 the record, lane 1 the
-    // source row, lanes 2.. the upwind rows (interior inflow faces in face order).
+    // Copies of cell k into stage k mod NS, one per lane: lane 0 the record, lane 1 the
+    // source row, lanes 2.. the upwind rows (interior inflow faces in face order) that
+    // are not filled by the lanes.
     auto issue = [&](uint32_t k) {
         const int src = (int)(k & 31u);
         const bool hi = k >= 32u;
         const uint32_t ek = __shfl_sync(FULL, hi ? e_hi : e_lo, src);
+        const uint32_t ak = intra ? __shfl_sync(FULL, hi ? a_hi : a_lo, src) : 0u;
         int4 nb;
         nb.x = __shfl_sync(FULL, hi ? n_hi.x : n_lo.x, src);
         nb.y = __shfl_sync(FULL, hi ? n_hi.y : n_lo.y, src);
@@ -811,18 +841,20 @@ __device__ __forceinline__ bool run_task_staged(const SweepArgs<T> &A, uint4 ti,
         const uint32_t upm = (((mask & 1u) && nb.x >= 0) ? 1u : 0u) | (((mask & 2u) && nb.y >= 0) ? 2u : 0u) |
                              (((mask & 4u) && nb.z >= 0) ? 4u : 0u) | (((mask & 8u) && nb.w >= 0) ? 8u : 0u);
         const uint32_t n_up = __popc(upm);
+        const uint32_t copied = ((1u << n_up) - 1u) & ~(ak & 7u);  // upwind slots filled by a copy
         unsigned char *st = wsm + s * L.stage;
-        fence_proxy_async_shared();  // this lane's generic reads of the stage (cell k - 3) before async writes
+        fence_proxy_async_shared();  // this lane's generic accesses of the stage (cell k - NS) before async writes
+        if (ak & 8u) fence_proxy_async_global();  // this lane's stores of the task's earlier rows before the copies
         if (lane == 0) {
             mbar_arrive_expect_tx(&bars[s], (uint32_t)sizeof(CellGeo<T>) + L.row);
-            mbar_arrive_expect_tx(&bars[3 + s], n_up * L.row);
+            mbar_arrive_expect_tx(&bars[3 + s], (uint32_t)__popc(copied) * L.row);
         }
         __syncwarp();
         if (lane == 0) {
             bulk_g2s(st, A.geo + c, (uint32_t)sizeof(CellGeo<T>), &bars[s]);
         } else if (lane == 1) {
             bulk_g2s(st + sizeof(CellGeo<T>), A.q + (size_t)c * A.G, L.row, &bars[s]);
-        } else if (lane < 2 + (int)n_up) {
+        } else if (lane < 2 + (int)n_up && ((copied >> (lane - 2)) & 1u)) {
             uint32_t m = upm;
             for (int r = 2; r < lane; ++r) m &= m - 1u;  // drop the faces of lanes 2 .. lane - 1
             const int f = __ffs(m) - 1;
@@ -836,12 +868,21 @@ __device__ __forceinline__ bool run_task_staged(const SweepArgs<T> &A, uint4 ti,
     for (uint32_t k = 0; k < ncell; ++k) {
         const uint32_t s = k % (uint32_t)NS;
         const uint32_t ek = __shfl_sync(FULL, k < 32 ? e_lo : e_hi, k & 31);
+        const uint32_t ak = intra ? __shfl_sync(FULL, k < 32 ? a_lo : a_hi, k & 31) : 0u;
         if (k + NS - 1 < ncell) issue(k + NS - 1);
         if (!mbar_wait(&bars[s], (ph >> s) & 1u, A.wait_limit_ns, &A.ctrl->error, wacc)) return false;
         ph ^= 1u << s;
         if (!mbar_wait(&bars[3 + s], (ph >> (3 + s)) & 1u, A.wait_limit_ns, &A.ctrl->error, wacc)) return false;
         ph ^= 1u << (3 + s);
-        solve_staged_cell<T, NPL>(A, wsm + s * L.stage, ek, lane, ox, oy, oz, psi_dir, L);
+        // the upwind slots of the next cells (already issued) that take this cell's solution
+        V4<T> *fill0 = nullptr, *fill1 = nullptr;
+        if (ak & 0x30u)
+            fill0 = reinterpret_cast<V4<T> *>(wsm + ((k + 1) % (uint32_t)NS) * L.stage + sizeof(CellGeo<T>) +
+                                              ((ak >> 4) & 3u) * L.row);
+        if (NS == 3 && (ak & 0xc0u))
+            fill1 = reinterpret_cast<V4<T> *>(wsm + ((k + 2) % (uint32_t)NS) * L.stage + sizeof(CellGeo<T>) +
+                                              ((ak >> 6) & 3u) * L.row);
+        solve_staged_cell<T, NPL>(A, wsm + s * L.stage, ek, lane, ox, oy, oz, psi_dir, L, fill0, fill1);
         __syncwarp();
     }
     return true;

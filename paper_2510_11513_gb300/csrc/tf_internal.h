@@ -79,12 +79,27 @@ struct TaskGraph {
     std::vector<uint32_t> down_list;       // downwind task ids (global)
     std::vector<uint32_t> cell_list;       // (cell << cell_shift) | inflow mask, [D * nc]
     int32_t cell_shift = 4;                // 4 for tetrahedra, 6 for hexahedra (one mask bit per face)
+    bool patches = false;                  // spatial patches: a task's cells may depend on each other
     int64_t T() const { return (int64_t)task_ncell.size(); }
 };
 
+// Spatial-patch tasks (graph.cpp): regions are boxes of `extent` mean cell sizes;
+// inside a patch, a cell that depends on one of the `gap` cells listed just before
+// it is avoided when possible.
+struct TaskShape {
+    double extent = 2.0;
+    int32_t gap = 1;
+};
+
+// Task shape a problem with options o on mesh m with G groups gets (api.cpp).
+tf_status task_shape_of(const tf_options &o, const Mesh &m, int32_t G, bool *patches, TaskShape *shape);
+// Cells per task (*B in: the caller's cells_per_task, >= 0; out: the grain) and shape (api.cpp).
+tf_status task_grain(const tf_options &o, const Mesh &m, int32_t G, int32_t *B, bool *patches, TaskShape *shape);
+
 // Face classification and levels only (no tasks); returns TF_ERR_CYCLE on a cycle.
 tf_status classify_and_level(const Mesh &m, const Quad &q, uint8_t *inflow, int32_t *level);
-tf_status build_task_graph(const Mesh &m, const Quad &q, int32_t cells_per_task, TaskGraph &g);
+tf_status build_task_graph(const Mesh &m, const Quad &q, int32_t cells_per_task, TaskGraph &g,
+                           const TaskShape *shape = nullptr);
 
 struct DeviceState;  // defined in the CUDA part
 
@@ -123,6 +138,8 @@ struct Problem : Object {
     DeviceState *dev = nullptr;
     tf_stats stats{};
     tf_autotune_report tune;
+    tf_reduce_fn reduce = nullptr;  // sum over partners (direction sharding), or NULL
+    void *reduce_user = nullptr;
 };
 
 // Picks cells_per_task, then the kernel variant (groups per lane: pairing; shared-memory

@@ -24,11 +24,12 @@ TF_OK, TF_ERR_ARG, TF_ERR_MESH, TF_ERR_CYCLE, TF_ERR_CUDA, TF_ERR_NOMEM, TF_ERR_
 TF_FP32, TF_FP64 = 0, 1
 TF_PHI_PAIR, TF_PHI_DADD = 0, 1
 TF_SCHED_AMT, TF_SCHED_BSP, TF_SCHED_BSP_LAUNCH = 0, 1, 2
+TF_TASK_AUTO, TF_TASK_LEVELS, TF_TASK_PATCHES = 0, 1, 2
 
 SYMBOLS = (
     "tf_options_default", "tf_mesh_create", "tf_mesh_create_hex", "tf_mesh_hex_integrals", "tf_quadrature_create", "tf_problem_create", "tf_sweep",
-    "tf_source_iterate", "tf_destroy", "tf_mesh_geometry", "tf_quadrature_get", "tf_graph_levels",
-    "tf_problem_psi", "tf_problem_stats", "tf_status_string", "tf_last_error", "tf_integrated_flux_noalloc",
+    "tf_source_iterate", "tf_destroy", "tf_mesh_geometry", "tf_quadrature_get", "tf_graph_levels", "tf_graph_tasks",
+    "tf_problem_psi", "tf_problem_set_reduce", "tf_problem_stats", "tf_status_string", "tf_last_error", "tf_integrated_flux_noalloc",
     # include/tflearn.h
     "tf_mlp_create", "tf_mlp_params", "tf_mlp_scale", "tf_mlp_limits", "tf_mlp_fit_inputs",
     "tf_mlp_input_scale", "tf_mlp_shrink", "tf_mlp_fit_scale", "tf_mlp_features", "tf_mlp_targets",
@@ -43,9 +44,9 @@ class tf_options(C.Structure):
         ("phi_accumulate", C.c_int32), ("inject_stall", C.c_int32), ("psi_budget_gb", C.c_double),
         ("task_order", C.c_int32), ("staging", C.c_int32), ("octant_window", C.c_int32),
         ("pairing", C.c_int32), ("schedule", C.c_int32), ("order", C.c_int32),
-        ("keep_ready", C.c_int32), ("reserved_i", C.c_int32 * 1),
-        ("residual_floor", C.c_double),
-        ("reserved_d", C.c_double * 3),
+        ("keep_ready", C.c_int32), ("task_shape", C.c_int32),
+        ("residual_floor", C.c_double), ("patch_extent", C.c_double),
+        ("reserved_d", C.c_double * 2),
     ]
 
 
@@ -69,9 +70,13 @@ class tf_stats(C.Structure):
         ("launches_per_step", C.c_int64), ("kernel_mode", C.c_int32), ("tuned_n", C.c_int32),
         ("tuned_cached", C.c_int32), ("tuned_candidates", C.c_int32 * 8), ("tuned_seconds", C.c_double * 8),
         ("n_buckets", C.c_int32), ("tuned_pairing", C.c_int32), ("tuned_staging", C.c_int32),
-        ("tuned_window", C.c_int32), ("reserved_i", C.c_int32 * 1), ("data_wait_seconds", C.c_double),
+        ("tuned_window", C.c_int32), ("task_shape", C.c_int32), ("data_wait_seconds", C.c_double),
         ("reserved_d", C.c_double * 5),
     ]
+
+
+# tf_reduce_fn: int32_t (*)(void *user, double *buf, int64_t count, void *stream)
+REDUCE_FN = C.CFUNCTYPE(C.c_int32, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p)
 
 
 class TfError(RuntimeError):
@@ -112,8 +117,10 @@ def load(build_if_missing: bool = True):
     lib.tf_mesh_geometry.argtypes = [H, C.POINTER(i64), C.POINTER(i64), vp, vp, vp, vp]
     lib.tf_quadrature_get.argtypes = [H, C.POINTER(i32), vp, vp]
     lib.tf_graph_levels.argtypes = [H, H, vp, vp]
+    lib.tf_graph_tasks.argtypes = [H, H, C.POINTER(tf_options), i32, C.POINTER(i64), vp, vp, vp]
     lib.tf_problem_psi.argtypes = [H, i32, vp, vp]
     lib.tf_problem_stats.argtypes = [H, C.POINTER(tf_stats)]
+    lib.tf_problem_set_reduce.argtypes = [H, REDUCE_FN, vp]
     lib.tf_integrated_flux_noalloc.argtypes = [vp, vp, i64, i32, vp, vp]
     f32, u64, fp = C.c_float, C.c_uint64, C.POINTER(C.c_float)
     lib.tf_mlp_create.argtypes = [i32, i32, i32, u64, C.POINTER(H)]
@@ -287,6 +294,28 @@ def tf_graph_levels(mesh, quad, n_cells, n_dirs):
     level = np.zeros((n_dirs, n_cells), np.int32)
     _check(load().tf_graph_levels(mesh, quad, _ptr(inflow), _ptr(level)), "tf_graph_levels")
     return inflow, level
+
+
+def tf_graph_tasks(mesh, quad, n_cells, n_dirs, n_groups, opts=None):
+    """(task_of [n_dirs][n_cells], position [n_dirs][n_cells], indeg [n_tasks]) of the tasks a
+    problem with these options would sweep (host only)."""
+    nt = C.c_int64()
+    o = opts if opts is not None else options()
+    _check(load().tf_graph_tasks(mesh, quad, C.byref(o), int(n_groups), C.byref(nt), None, None, None), "tf_graph_tasks")
+    task_of = np.zeros((n_dirs, n_cells), np.int32)
+    position = np.zeros((n_dirs, n_cells), np.int32)
+    indeg = np.zeros(nt.value, np.int32)
+    _check(load().tf_graph_tasks(mesh, quad, C.byref(o), int(n_groups), C.byref(nt), _ptr(task_of), _ptr(position),
+                                 _ptr(indeg)), "tf_graph_tasks")
+    return task_of, position, indeg
+
+
+def tf_problem_set_reduce(problem, fn):
+    """fn(ptr, count, stream) -> int, or None to remove; returns the ctypes callback object, which
+    the caller must keep alive while the problem may call it."""
+    cb = REDUCE_FN(lambda user, buf, count, stream: int(fn(buf, count, stream))) if fn is not None else REDUCE_FN()
+    _check(load().tf_problem_set_reduce(problem, cb, None), "tf_problem_set_reduce")
+    return cb
 
 
 def tf_problem_psi(problem, direction, out, stream=None):
@@ -549,6 +578,11 @@ class Problem(_Handle):
         if hist is not None:
             res["residual_history"] = np.array(hist[: i.iterations])
         return res
+
+    def set_reduce(self, fn):
+        """Sum of the partial phi over partners (direction sharding); fn(ptr, count, stream) -> 0 on
+        success.  None removes it."""
+        self._reduce_cb = tf_problem_set_reduce(self.h, fn)
 
     def psi(self, direction, out, stream=None):
         tf_problem_psi(self.h, direction, out, stream)
