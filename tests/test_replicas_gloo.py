@@ -1,6 +1,6 @@
-"""The multi-rank path of bench.py (independent replicas, no data-path collective),
-run as two gloo ranks on the CPU: barrier, max over ranks of the timed region,
-and the whole-job grind time over all ranks' units."""
+"""The multi-rank bookkeeping of bench.py, run as two gloo ranks on the CPU: barrier, max over
+ranks of the timed region, and the whole-job grind time over the job's units (replicas: every
+rank's problem; direction sharding: the one shared problem)."""
 import os
 import socket
 
@@ -28,7 +28,8 @@ def _rank_main(rank, world, port, out):
         bench._barrier(w)
         ms = 10.0 * (r + 1)  # rank 1 is the slower one
         mx = bench._max_over_ranks(w, ms)
-        out[r] = (w, r, local, mx, bench.whole_job_grind(mx, 1000, w))
+        out[r] = (w, r, local, mx, bench.whole_job_grind(mx, bench.job_units(1000, w, False)),
+                  bench.whole_job_grind(mx, bench.job_units(1000, w, True)))
         bench._barrier(w)
     finally:
         dist.destroy_process_group()
@@ -42,10 +43,11 @@ def test_two_gloo_ranks_max_and_whole_job_value():
     mp.start_processes(_rank_main, args=(world, port, out), nprocs=world, start_method="spawn", join=True)
     assert sorted(out.keys()) == [0, 1]
     for r in range(world):
-        w, rr, local, mx, value = out[r]
+        w, rr, local, mx, value, value_sharded = out[r]
         assert (w, rr, local) == (world, r, r)
         assert mx == 20.0  # max over ranks
-        assert abs(value - 20.0 * 1e6 / 2000) < 1e-9  # both ranks' units over the slowest time
+        assert abs(value - 20.0 * 1e6 / 2000) < 1e-9  # replicas: both ranks' units over the slowest time
+        assert abs(value_sharded - 20.0 * 1e6 / 1000) < 1e-9  # directions shared: the one problem's units
 
 
 def test_reference_arm_runs_on_rank_zero_only(monkeypatch, capsys):
