@@ -8,8 +8,10 @@
 // input and output buffers; the partial sums live in g_flux_scratch, which
 // every GPU that loads this library holds until the process exits.
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <cstdint>
 #include <mutex>
 #include <string>
 
@@ -30,6 +32,64 @@ static __device__ __align__(256) double g_flux_scratch[kScratchDoubles];
 std::mutex g_mu;
 double *g_scratch_addr[kMaxDevices] = {};  // device address of g_flux_scratch, per device
 int g_sm_count[kMaxDevices] = {};
+CUcontext g_scratch_ctx[kMaxDevices] = {};  // the context that address belongs to
+
+// cuCtxGetCurrent through the runtime's driver entry point (the library does not link libcuda)
+PFN_cuCtxGetCurrent_v4000 ctx_getter()
+{
+    static PFN_cuCtxGetCurrent_v4000 fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 4000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuCtxGetCurrent_v4000>(p);
+        else
+            cudaGetLastError();
+    }
+    return fn;
+}
+
+CUcontext current_ctx()
+{
+    CUcontext c = nullptr;
+    PFN_cuCtxGetCurrent_v4000 fn = ctx_getter();
+    if (fn && fn(&c) != CUDA_SUCCESS) c = nullptr;
+    return c;
+}
+
+// The address a kernel on device `dev` uses for caller buffer p (device, managed, or page-locked
+// host memory mapped into the device's address space); TF_ERR_ARG for memory the device cannot
+// reach (plain pageable host memory) or an address not aligned to `align` bytes.
+tf_status device_view(const void *p, size_t align, int dev, const char *name, const void **out)
+{
+    const std::string what = std::string("tf_integrated_flux_noalloc: ") + name;
+    if ((uintptr_t)p % align) return fail(TF_ERR_ARG, what + " is not " + std::to_string(align) + "-byte aligned");
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(TF_ERR_ARG, what + ": not memory the device can reach");
+    }
+    switch (at.type) {
+    case cudaMemoryTypeDevice:
+        if (at.device != dev) return fail(TF_ERR_ARG, what + " lives on another device");
+        *out = p;
+        break;
+    case cudaMemoryTypeManaged:
+        *out = p;
+        break;
+    case cudaMemoryTypeHost:
+        if (!at.devicePointer) return fail(TF_ERR_ARG, what + ": page-locked host memory not mapped into the device");
+        *out = at.devicePointer;
+        break;
+    default:
+        return fail(TF_ERR_ARG, what + ": pageable host memory (pass device, managed or mapped page-locked memory)");
+    }
+    if ((uintptr_t)*out % align) return fail(TF_ERR_ARG, what + " is not " + std::to_string(align) + "-byte aligned");
+    return TF_OK;
+}
 
 // Same reduction as the library's statistics kernel, with the cell volume
 // given directly (V/4 is formed here, exactly, as 0.25 V).
@@ -104,12 +164,20 @@ extern "C" tf_status tf_integrated_flux_noalloc(const double *phi, const double 
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return fail(TF_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
     if (dev < 0 || dev >= kMaxDevices) return fail(TF_ERR_ARG, "tf_integrated_flux_noalloc: device ordinal too large");
+    // the kernel reads phi as pairs of doubles (16 bytes), the volumes and the output as doubles
+    const void *phi_d = nullptr, *vol_d = nullptr, *out_d = nullptr;
+    tf_status s = device_view(phi, 16, dev, "phi", &phi_d);
+    if (s == TF_OK) s = device_view(volume, 8, dev, "volume", &vol_d);
+    if (s == TF_OK) s = device_view(out, 8, dev, "out", &out_d);
+    if (s != TF_OK) return s;
     double *scratch = nullptr;
     int sms = 0;
     {
-        // once per device, with that device current: the device address of the scratch array
+        // once per device and context, with that device current: the device address of the
+        // scratch array (looked up again when the device's context changed, e.g. after a reset)
         std::lock_guard<std::mutex> lk(g_mu);
-        if (!g_scratch_addr[dev]) {
+        const CUcontext ctx = current_ctx();
+        if (!g_scratch_addr[dev] || !ctx || ctx != g_scratch_ctx[dev]) {
             void *p = nullptr;
             e = cudaGetSymbolAddress(&p, g_flux_scratch);
             if (e != cudaSuccess) return fail(TF_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
@@ -118,6 +186,7 @@ extern "C" tf_status tf_integrated_flux_noalloc(const double *phi, const double 
             if (e != cudaSuccess) return fail(TF_ERR_CUDA, std::string("cudaDeviceGetAttribute: ") + cudaGetErrorString(e));
             g_scratch_addr[dev] = static_cast<double *>(p);
             g_sm_count[dev] = n;
+            g_scratch_ctx[dev] = current_ctx();  // the lookup made the device's context current
         }
         scratch = g_scratch_addr[dev];
         sms = g_sm_count[dev];
@@ -127,8 +196,11 @@ extern "C" tf_status tf_integrated_flux_noalloc(const double *phi, const double 
     if (nblk < 1) nblk = 1;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     // every block overwrites its own [n_groups][3] slice, so nothing has to start at zero
-    flux_stats_kernel<<<(unsigned)nblk, dim3(32, 8), 0, st>>>(phi, volume, n_cells, n_groups, scratch);
-    flux_finish_kernel<<<(n_groups + 127) / 128, 128, 0, st>>>(scratch, (int)nblk, n_groups, out);
+    flux_stats_kernel<<<(unsigned)nblk, dim3(32, 8), 0, st>>>(static_cast<const double *>(phi_d),
+                                                                static_cast<const double *>(vol_d), n_cells, n_groups,
+                                                                scratch);
+    flux_finish_kernel<<<(n_groups + 127) / 128, 128, 0, st>>>(scratch, (int)nblk, n_groups,
+                                                               const_cast<double *>(static_cast<const double *>(out_d)));
     e = cudaGetLastError();
     if (e != cudaSuccess) return fail(TF_ERR_CUDA, std::string("tf_integrated_flux_noalloc launch: ") + cudaGetErrorString(e));
     return TF_OK;

@@ -50,3 +50,44 @@ def test_noalloc_rejects_too_many_groups():
                                         ctypes.c_int64(1), ctypes.c_int32(1025), ctypes.c_void_p(buf.data_ptr()), None)
     assert st == tf.TF_ERR_ARG
     assert b"1024" in lib.tf_last_error()
+
+
+def _call(lib, phi_ptr, vol_ptr, C, G, out_ptr):
+    return lib.tf_integrated_flux_noalloc(ctypes.c_void_p(phi_ptr), ctypes.c_void_p(vol_ptr), ctypes.c_int64(C),
+                                          ctypes.c_int32(G), ctypes.c_void_p(out_ptr), None)
+
+
+def test_noalloc_refuses_unreachable_or_misaligned_buffers_before_launch():
+    """A plain (pageable) host buffer, or a phi address that is not 16-byte aligned, is refused
+    with TF_ERR_ARG on the host: nothing is launched, so no kernel can fault on it.  A
+    page-locked host buffer mapped into the device is accepted and gives the device result."""
+    lib = tf.load()
+    C, G = 50, 3
+    rng = np.random.default_rng(7)
+    phi_h = rng.uniform(0.0, 1.0, (C, G, 4))
+    vol_h = rng.uniform(0.5, 1.0, C)
+    phi = torch.from_numpy(phi_h).cuda()
+    vol = torch.from_numpy(vol_h).cuda()
+    out = torch.full((G, 3), -1.0, dtype=torch.float64, device="cuda")
+    # pageable host memory (numpy): refused
+    assert _call(lib, phi_h.ctypes.data, vol.data_ptr(), C, G, out.data_ptr()) == tf.TF_ERR_ARG
+    assert b"host" in lib.tf_last_error()
+    assert _call(lib, phi.data_ptr(), vol_h.ctypes.data, C, G, out.data_ptr()) == tf.TF_ERR_ARG
+    out_h = np.zeros((G, 3))
+    assert _call(lib, phi.data_ptr(), vol.data_ptr(), C, G, out_h.ctypes.data) == tf.TF_ERR_ARG
+    # phi one double into a device buffer: 8-byte but not 16-byte aligned: refused
+    big = torch.zeros(C * G * 4 + 1, dtype=torch.float64, device="cuda")
+    assert _call(lib, big.data_ptr() + 8, vol.data_ptr(), C, G, out.data_ptr()) == tf.TF_ERR_ARG
+    assert b"aligned" in lib.tf_last_error()
+    torch.cuda.synchronize()
+    assert np.all(out.cpu().numpy() == -1.0)  # nothing ran
+    # device buffers, then page-locked host phi: the same numbers
+    assert _call(lib, phi.data_ptr(), vol.data_ptr(), C, G, out.data_ptr()) == tf.TF_OK
+    torch.cuda.synchronize()
+    ref = out.cpu().numpy().copy()
+    phi_p = torch.from_numpy(phi_h).pin_memory()
+    out2 = torch.full((G, 3), -1.0, dtype=torch.float64, device="cuda")
+    assert _call(lib, phi_p.data_ptr(), vol.data_ptr(), C, G, out2.data_ptr()) == tf.TF_OK, lib.tf_last_error()
+    torch.cuda.synchronize()
+    assert np.array_equal(out2.cpu().numpy(), ref)
+    assert np.allclose(ref[:, 1], np.einsum("c,cgi->g", 0.25 * vol_h, phi_h), rtol=1e-13, atol=0)
