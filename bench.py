@@ -47,10 +47,12 @@ def kernel_source_sha1(sources):
     return h.hexdigest()
 
 
-def _traffic(workload, precision, kernel_label):
-    """DRAM bytes per sweep-kernel launch from the committed ncu record, if it was taken on
-    this workload with the current sources of that kernel variant (the files the record
-    lists); else None."""
+def _traffic(workload, precision, kernel_label, units):
+    """DRAM bytes (read + write) of one sweep-kernel launch of `units` units on `workload`, from
+    the committed one-pass ncu record of that kernel variant (profiles/traffic_*.json) whose
+    source files still hash to the recorded SHA-1: the record's bytes per unit, captured on the
+    workload itself or on a smaller case of it that the record names (scaled by the units of one
+    launch); None when no current record applies."""
     import glob
     for f in glob.glob(os.path.join(ROOT, "profiles", "traffic_*.json")):
         try:
@@ -58,9 +60,10 @@ def _traffic(workload, precision, kernel_label):
             sha = kernel_source_sha1(rec["kernel_sources"])
         except (OSError, ValueError, KeyError):
             continue
-        if (rec.get("workload") == workload and rec.get("precision") == precision
+        if (workload in rec.get("applies_to", []) and rec.get("precision") == precision
                 and rec.get("kernel_source_sha1") == sha and rec.get("kernel") == kernel_label):
-            return rec["dram_bytes_read"] + rec["dram_bytes_write"]
+            per_unit = (rec["dram_bytes_read"] + rec["dram_bytes_write"]) / rec["units_per_launch"]
+            return per_unit * units
     return None
 
 
@@ -148,11 +151,16 @@ def _max_over_ranks(world, x):
     return float(t.item())
 
 
-def whole_job_grind(ms_per_step, units_per_rank, world):
-    """Grind time of the whole job (ns per unit) from the slowest rank's time per step:
-    every rank processes units_per_rank units per step (replicas), so the job processes
-    world * units_per_rank units in ms_per_step."""
-    return ms_per_step * 1e6 / (units_per_rank * world)
+def job_units(units_per_rank, world, sharded):
+    """Units the whole job processes per step: with direction sharding the ranks share one
+    problem (each sweeps its directions), so the job's units are the sum of the ranks' shares;
+    replicas each solve the whole problem, world times the units."""
+    return units_per_rank * world if not sharded else units_per_rank
+
+
+def whole_job_grind(ms_per_step, units_job):
+    """Grind time of the whole job (ns per unit) from the slowest rank's time per step."""
+    return ms_per_step * 1e6 / units_job
 
 
 def cpu_oracle_sample(cfg, n_dirs=None, threads=None, groups=16):
@@ -192,6 +200,19 @@ def cpu_oracle_sample(cfg, n_dirs=None, threads=None, groups=16):
                       f"{dt:.1f} s wall on {used} threads"}
 
 
+def cpu_baseline(cfg, repeats=3):
+    """The oracle's grind time on this machine's cores: the median of `repeats` all-core samples
+    (their spread alongside) and one single-thread sample (one direction, the first 16 groups)."""
+    runs = [cpu_oracle_sample(cfg) for _ in range(repeats)]
+    vals = sorted(r["value"] for r in runs)
+    out = dict(runs[0])
+    out["value"] = statistics.median(vals)
+    out["spread"] = {"min": vals[0], "max": vals[-1], "samples": len(vals)}
+    one = cpu_oracle_sample(cfg, n_dirs=1, threads=1)
+    out["single_thread"] = {"value": one["value"], "unit": one["unit"], "cores": one["cores"], "sample": one["sample"]}
+    return out
+
+
 def make_config(args):
     """The named workload, optionally resized (--n, --groups, --polar, --azimuthal) for profiling runs."""
     kw = {}
@@ -224,14 +245,15 @@ def run_reference(args):
         last = cpu_oracle_sample(cfg, n_dirs=threads, threads=threads)
         vals.append(last["value"])
     wall = time.perf_counter() - t0
-    v = float(np.mean(vals))
+    v = float(np.median(vals))
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": wall / max(args.steps, 1) * 1e3,
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": cfg["name"], "cells": len(cfg["tets"]),
                        "directions": cfg["n_polar"] * cfg["n_azimuthal"], "groups": cfg["n_groups"]},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": last["cores"], "kind": "oracle",
-                             "sample": last["sample"]},
+                             "sample": last["sample"],
+                             "spread": {"min": float(min(vals)), "max": float(max(vals)), "samples": len(vals)}},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -287,33 +309,43 @@ def schedule_ablation(tf, cfg, prec, local, stream, steps, torch, amt=None):
 FP32_ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
 
-def p2_flops_per_unit(prob, tf, order=2):
-    """Algorithmic flops of one higher-order unit (an FMA counts 2).  Second order: streaming
-    matrix 160, A = V (sigma_t M + K) 300, b = V M q 210, the 10 x 10 elimination and back
-    substitution 815, 156 per interior inflow face (face matrix into A, face term into b).
-    Third order: A = V (sigma_t M + sum_k w_k C_k) 4,400, b = V M q 800, the 20 x 20
-    elimination and back substitution 5,910, 420 per interior inflow face.  The mean number
-    of interior inflow faces per (cell, direction) comes from the sweep graph."""
+def _inflow_faces(prob, tf, nf):
+    """Mean interior and boundary inflow faces per (cell, direction), from the sweep graph."""
     inflow, _ = tf.tf_graph_levels(prob.mesh.h, prob.quad.h, prob.n_cells, prob.n_dirs)
     nbr = prob.mesh.geometry()["nbr"]
-    interior = (nbr >= 0).astype(np.uint8)  # [C][4]
-    n_in = sum(float((((inflow >> f) & 1) * interior[None, :, f]).mean()) for f in range(4))
+    interior = (nbr >= 0).astype(np.uint8)  # [C][nf]
+    n_in = sum(float((((inflow >> f) & 1) * interior[None, :, f]).mean()) for f in range(nf))
+    n_bd = sum(float((((inflow >> f) & 1) * (1 - interior[None, :, f])).mean()) for f in range(nf))
+    return n_in, n_bd
+
+
+def p2_flops_per_unit(prob, tf, order=2):
+    """Algorithmic (minimum) flops of one higher-order unit, an FMA counting 2.  Work that depends
+    only on the cell and the direction (the streaming matrix V sum_k (Omega . grad lambda_k) C_k
+    and the inflow face matrices |Omega . N_f| F_f: the group-independent part W of the matrix)
+    is needed once per (cell, direction) and is divided by the group count G.  Per unit:
+    A_g = W + sigma_t,g (V M) (one FMA per entry), b = (V M) q (one FMA per entry plus the
+    scaling), the elimination without pivoting and the back substitution of an n x n system
+    (sum_{m<n} m (2 m + 3) + n^2 flops), and per interior inflow face the face term F_f psi_up.
+    Second order (n = 10): 200 + 210 + 815 per unit, 78 per face; 160 + 78 per face per
+    (cell, direction).  Third order (n = 20): 800 + 820 + 5,910 per unit, 220 per face;
+    3,624 + 200 per face per (cell, direction)."""
+    n_in, _ = _inflow_faces(prob, tf, 4)
+    G = prob.n_groups
     if order == 3:
-        return 11110.0 + 420.0 * n_in, n_in
-    return 1485.0 + 156.0 * n_in, n_in
+        return 7530.0 + 220.0 * n_in + (3624.0 + 200.0 * n_in) / G, n_in
+    return 1225.0 + 78.0 * n_in + (160.0 + 78.0 * n_in) / G, n_in
 
 
 def hex_flops_per_unit(prob, tf):
-    """Algorithmic flops of one trilinear-hexahedron unit (an FMA counts 2): A = sum_d Omega_d
-    G_d + sigma_t M 512, b = M q 128, the 8 x 8 elimination 364 and back substitution 72;
-    per interior inflow face 128 (the 4 x 4 matrix -Omega.F_f 80, added into A 16, its face
-    term into b 32), per boundary inflow face 96 (no face term under vacuum)."""
-    inflow, _ = tf.tf_graph_levels(prob.mesh.h, prob.quad.h, prob.n_cells, prob.n_dirs)
-    nbr = prob.mesh.geometry()["nbr"]
-    interior = (nbr >= 0).astype(np.uint8)  # [C][6]
-    n_in = sum(float((((inflow >> f) & 1) * interior[None, :, f]).mean()) for f in range(6))
-    n_bd = sum(float((((inflow >> f) & 1) * (1 - interior[None, :, f])).mean()) for f in range(6))
-    return 1076.0 + 128.0 * n_in + 96.0 * n_bd, n_in
+    """Algorithmic (minimum) flops of one trilinear-hexahedron unit, an FMA counting 2.  Per unit:
+    A_g = W + sigma_t,g M 128, b = M q 128, the 8 x 8 elimination 364 and back substitution 72,
+    per interior inflow face the face term into b 32.  Per (cell, direction), divided by the group
+    count G: the streaming matrix W = sum_d Omega_d G_d 384 and, per inflow face (interior or
+    boundary), the 4 x 4 face matrix -Omega . F_f (80) added into W (16)."""
+    n_in, n_bd = _inflow_faces(prob, tf, 6)
+    G = prob.n_groups
+    return 692.0 + 32.0 * n_in + (384.0 + 96.0 * (n_in + n_bd)) / G, n_in
 
 
 def second_order_leg(tf, cfg, prec, local, stream, steps, torch, order=2):
@@ -345,7 +377,7 @@ def second_order_leg(tf, cfg, prec, local, stream, steps, torch, order=2):
            "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
                         "frac": achieved / FP32_ALU_PEAK_TFLOPS, "flops_per_unit": flops,
                         "mean_interior_inflow_faces": n_in, "kernel": klabel,
-                        "traffic": _traffic(cfg["name"], "fp32", klabel),
+                        "traffic": _traffic(cfg["name"], "fp32", klabel, pr.n_units),
                         "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"}}
     pr.close()
     del pr, ph
@@ -369,14 +401,29 @@ def run_ours(args):
         cfg = (W.order2 if args.order == 2 else W.order3)(cfg)
     prec = tf.TF_FP64 if args.precision == "fp64" else tf.TF_FP32
     t_setup = time.perf_counter()
+    # N > 1: each rank sweeps a share of the directions and the partial scalar fluxes are summed
+    # over the ranks after every transport step (strong scaling), or (--shard replicas) each rank
+    # solves the whole problem on its own (weak scaling)
+    sharded = world > 1 and args.shard == "directions"
+    qopts = {}
+    if sharded:
+        from paper_2510_11513_gb300 import shard
+        om_all, w_all = tf.tf_quadrature_get(tf.Quadrature(cfg["n_polar"], cfg["n_azimuthal"]).h)
+        qopts["omega"], qopts["w"] = shard.shard_quadrature(om_all, w_all, rank, world)
     prob = tf.Problem.from_config(cfg, precision=prec, device=local, cells_per_task=args.cells_per_task,
                                   warps_per_cta=args.warps_per_cta, octant_window=args.octant_window,
                                   keep_ready=args.keep_ready,
                                   staging=args.staging, pairing=args.pairing, schedule=SCHEDULES[args.schedule],
-                                  order=args.order)
+                                  order=args.order, task_shape=args.task_shape, patch_extent=args.patch_extent,
+                                  **qopts)
+    if sharded:
+        prob.set_reduce(shard.TorchAllreduce())
     t_setup = time.perf_counter() - t_setup
     C, G, D = prob.n_cells, prob.n_groups, prob.n_dirs
-    units = prob.n_units
+    units = prob.n_units  # this rank's units per step
+    D_job = cfg["n_polar"] * cfg["n_azimuthal"]
+    # the whole job's units per step: all directions of the one problem (sharded), or every replica's
+    units_job = job_units(C * D_job * G if sharded else units, world, sharded)
     stream = torch.cuda.current_stream(dev)
     nodes = prob.n_nodes
     phi = torch.zeros((C, G, nodes), dtype=torch.float64, device=dev)
@@ -401,7 +448,7 @@ def run_ours(args):
     assert res["iterations"] == args.steps
     ms_per_step = ms / args.steps
     grind = ms_per_step * 1e6 / units  # ns per unit (per GPU)
-    value = whole_job_grind(ms_per_step, units, world)  # all ranks' units over the slowest rank's time
+    value = whole_job_grind(ms_per_step, units_job)  # all ranks' units over the slowest rank's time
     sweep_s = (st1["cum_sweep_event_seconds"] - st0["cum_sweep_event_seconds"]) / args.steps
     phi_s = (st1["cum_phi_event_seconds"] - st0["cum_phi_event_seconds"]) / args.steps
     src_s = (st1["cum_source_event_seconds"] - st0["cum_source_event_seconds"]) / args.steps
@@ -418,17 +465,19 @@ def run_ours(args):
     klabel = ("sweep_kernel" if args.schedule == "amt" else "bsp_sweep_kernel") + \
         f"<{'float' if s == 4 else 'double'}, {mode}>"
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": False, "scaling": "weak",
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": False,
+            "scaling": "strong" if sharded else "weak",
             "vs_baseline": None, "dtype": "f32" if prec == tf.TF_FP32 else "f64", "data": "synthetic",
-            "config": {"workload": cfg["name"], "cells": C, "directions": D, "groups": G,
-                       "units_per_step": units, "precision": args.precision, "phi_accumulate": "fp32-pair->fp64",
+            "config": {"workload": cfg["name"], "cells": C, "directions": D_job, "groups": G,
+                       "units_per_step": units_job, "precision": args.precision, "phi_accumulate": "fp32-pair->fp64",
                        "l2": "inputs larger than L2 (psi store %.1f GB)" % (units * nodes * s / 1e9),
                        "element_order": args.order,
-                       "parallelism": f"replicas{world}", "setup_s": round(t_setup, 2),
-                       "schedule": args.schedule},
+                       "parallelism": (f"directions{world}" if sharded else f"replicas{world}"),
+                       "setup_s": round(t_setup, 2), "schedule": args.schedule,
+                       "task_shape": "patches" if st1["task_shape"] == tf.TF_TASK_PATCHES else "t-level blocks"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak,
-                         "traffic": _traffic(cfg["name"], args.precision, klabel),
+                         "traffic": _traffic(cfg["name"], args.precision, klabel, units),
                          "kernel": klabel,
                          "bytes_per_unit": b_unit, "peak_kind": peak_kind,
                          "algorithmic_bytes_per_launch": b_unit * units},
@@ -454,7 +503,7 @@ def run_ours(args):
         ach = flops * units / sweep_s / 1e12
         line["roofline"] = {"bound": "alu", "achieved": ach, "peak": FP32_ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
                             "frac": ach / FP32_ALU_PEAK_TFLOPS,
-                            "traffic": _traffic(cfg["name"], args.precision, klabel), "kernel": klabel,
+                            "traffic": _traffic(cfg["name"], args.precision, klabel, units), "kernel": klabel,
                             "flops_per_unit": flops, "mean_interior_inflow_faces": n_in,
                             "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
                             "bytes_per_unit": b_unit, "hbm_achieved_gbs": achieved}
@@ -474,7 +523,7 @@ def run_ours(args):
         _barrier(world)
         e2e_ms = _max_over_ranks(world, (time.perf_counter() - t0) * 1e3) / args.steps
         nbytes = C * G * nodes * 8
-        line["e2e"] = {"value": whole_job_grind(e2e_ms, units, world), "unit": UNIT, "h2d_bytes_per_step": nbytes,
+        line["e2e"] = {"value": whole_job_grind(e2e_ms, units_job), "unit": UNIT, "h2d_bytes_per_step": nbytes,
                        "d2h_bytes_per_step": nbytes, "ms_per_step": e2e_ms,
                        "call": "tf_sweep(host pinned phi_in, host pinned phi_out)"}
     amt_main = None
@@ -487,7 +536,7 @@ def run_ours(args):
     del prob
     torch.cuda.synchronize(dev)
     if not args.no_bsp_compare and world == 1 and args.order == 1:
-        # the paper's comparison (Sec. 5): many-task against level-synchronous buckets,
+        # the paper's comparison (Sec. 3.6): many-task against level-synchronous buckets,
         # on this workload and on the 16^3-hex one nearest the paper's own
         abl = [schedule_ablation(tf, cfg, prec, local, stream, args.bsp_steps, torch, amt_main)]
         abl.append(schedule_ablation(tf, W.paper_context_box(), prec, local, stream, 5, torch))
@@ -543,8 +592,17 @@ def run_ours(args):
             del pt, ph
         out["fp64_over_fp32"] = out["fp64"]["seconds"] / out["fp32"]["seconds"]
         line["time_to_tol"] = out
+    if not args.no_batch and world == 1 and args.order == 1:
+        # batched problems (16 of the batch workload's uneven problems) at the default and the
+        # autotuned task grain, each to the 1e-6 stopping test
+        line["batch"] = {"default": batch_leg(tf, torch, 16, False, 1e-6),
+                         "autotuned": batch_leg(tf, torch, 16, True, 1e-6)}
+    if not args.no_learned and world == 1 and args.order == 1:
+        # the learned start: 16 training layouts, 4 held-out layouts from zero and from the network
+        lk = dict(n=24, G=16, n_polar=8, n_az=8)
+        line["learned"] = learned_leg(tf, torch, lk, 16, 4, 1, 20, 1024, 1e-3, 0, 1e-6)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_oracle_sample(cfg)
+        line["cpu_baseline"] = cpu_baseline(cfg)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -552,17 +610,14 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def run_batch(args):
-    """Many independent problems (uneven meshes, direction sets, group counts) iterated to the
-    stopping test together in shared persistent launches; aggregate grind time over the units
-    actually swept, and each problem's time to convergence."""
-    import torch
-
-    import paper_2510_11513_gb300 as tf
-
-    torch.cuda.set_device(0)
-    dev = torch.device("cuda", 0)
-    cfgs = W.batch_of_problems(count=args.batch_count)
+def batch_leg(tf, torch, count, autotune, tol, seed=None):
+    """`count` independent problems of the batch workload (uneven meshes, direction sets and
+    group counts) iterated to the stopping test together in shared persistent launches, with the
+    autotuned task grain (busy-time criterion) or the default one.  Returns the aggregate grind
+    time over the units actually swept, the setup time and each problem's time to tol."""
+    dev = torch.device("cuda", torch.cuda.current_device())
+    kw = {} if seed is None else {"seed": seed}
+    cfgs = W.batch_of_problems(count=count, **kw)
     psi = [len(c["tets"]) * c["n_polar"] * c["n_azimuthal"] * c["n_groups"] * 16 for c in cfgs]
     free = torch.cuda.mem_get_info()[0]
     budget = 0.6 * free
@@ -571,7 +626,7 @@ def run_batch(args):
     for c, pb in zip(cfgs, psi):
         share = budget * pb / sum(psi) if sum(psi) > budget else 0.0
         probs.append(tf.Problem.from_config(c, precision=tf.TF_FP32, psi_budget_gb=share / 1e9,
-                                            cells_per_task=-2 if args.autotune else 0))
+                                            cells_per_task=-2 if autotune else 0))
     setup = time.perf_counter() - t0
     phis = [torch.zeros((p.n_cells, p.n_groups, 4), dtype=torch.float64, device=dev) for p in probs]
     tf.source_iterate_batch(probs, phis, 0.0, 1)  # warm-up iteration
@@ -580,57 +635,68 @@ def run_batch(args):
     torch.cuda.synchronize(dev)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
-    st, infos = tf.source_iterate_batch(probs, phis, args.batch_tol, 2000)
+    st, infos = tf.source_iterate_batch(probs, phis, tol, 2000)
     e1.record()
     torch.cuda.synchronize(dev)
     sec = e0.elapsed_time(e1) / 1e3
     swept = sum(p.n_units * i["iterations"] for p, i in zip(probs, infos))
-    line = {"metric": METRIC, "value": sec * 1e9 / swept, "unit": UNIT, "n_gpus": 1, "steps": 1, "warmup": 1,
-            "ms_per_step": sec * 1e3, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"batch_{len(cfgs)}_problems", "problems": len(cfgs),
-                       "units_per_sweep": sum(p.n_units for p in probs), "tol": args.batch_tol,
-                       "setup_s": round(setup, 1), "n_chunks": [p.stats()["n_chunks"] for p in probs],
-                       "autotune": bool(args.autotune)},
-            "all_converged": st == tf.TF_OK,
-            "per_problem": [{"cells": p.n_cells, "directions": p.n_dirs, "groups": p.n_groups,
-                             "cells_per_task": p.stats()["cells_per_task"], "kernel_mode": p.stats()["kernel_mode"],
-                             "octant_window": p.stats()["tuned_window"] or 8,
-                             "iterations": i["iterations"], "seconds_to_tol": round(i["seconds"], 4),
-                             "converged": i["converged"], "balance": i["balance"]} for p, i in zip(probs, infos)]}
-    print(json.dumps(line), flush=True)
+    out = {"workload": f"batch_{len(cfgs)}_problems", "problems": len(cfgs), "autotune": bool(autotune),
+           "tol": tol, "seconds": sec, "grind": sec * 1e9 / swept, "unit": UNIT,
+           "units_per_sweep": sum(p.n_units for p in probs), "units_swept": swept, "setup_s": round(setup, 2),
+           "all_converged": st == tf.TF_OK,
+           "per_problem": [{"cells": p.n_cells, "directions": p.n_dirs, "groups": p.n_groups,
+                            "cells_per_task": p.stats()["cells_per_task"], "kernel_mode": p.stats()["kernel_mode"],
+                            "octant_window": p.stats()["tuned_window"] or 8,
+                            "iterations": i["iterations"], "seconds_to_tol": round(i["seconds"], 4),
+                            "converged": i["converged"], "balance": i["balance"]} for p, i in zip(probs, infos)]}
+    for p in probs:
+        p.close()
+    del probs, phis
+    torch.cuda.synchronize(dev)
+    return out
 
 
-def run_learned(args):
-    """Learned initial flux on the learned-start layouts (24^3 hexes, 82,944 tets,
-    64 directions, 16 groups): generate converged fluxes with the plain FP32 solver,
-    train the network with the library's kernels, then solve held-out layouts from
-    zero and from the learned start to the same stopping test."""
+def run_batch(args):
+    """The batch workload on its own (--config batch): one JSON line."""
     import torch
 
     import paper_2510_11513_gb300 as tf
-    from paper_2510_11513_gb300 import learned as L
 
     torch.cuda.set_device(0)
-    dev = torch.device("cuda", 0)
-    kw = dict(n=args.n or 24, G=args.groups or 16, n_polar=args.polar or 8, n_az=args.azimuthal or 8)
-    tol = args.batch_tol
+    b = batch_leg(tf, torch, args.batch_count, args.autotune, args.batch_tol)
+    line = {"metric": METRIC, "value": b["grind"], "unit": UNIT, "n_gpus": 1, "steps": 1, "warmup": 1,
+            "ms_per_step": b["seconds"] * 1e3, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": b["workload"], "problems": b["problems"], "units_per_sweep": b["units_per_sweep"],
+                       "tol": b["tol"], "setup_s": b["setup_s"], "autotune": b["autotune"]},
+            "all_converged": b["all_converged"], "per_problem": b["per_problem"]}
+    print(json.dumps(line), flush=True)
+
+
+def learned_leg(tf, torch, kw, train_layouts, eval_layouts, eval_fp64, epochs, batch, lr, seed, tol,
+                weight_floor=None, overshoot_weight=1.0, shrink=0.5):
+    """Learned initial flux on the learned-start layouts: converged fluxes of `train_layouts`
+    layouts from the plain FP32 solver, the network trained by the library's kernels, then
+    `eval_layouts` held-out layouts solved from zero and from the learned start to the same
+    stopping test (the first `eval_fp64` also against a tightly converged FP64 solve)."""
+    from paper_2510_11513_gb300 import learned as L
+
+    dev = torch.device("cuda", torch.cuda.current_device())
     t0 = time.perf_counter()
-    train = [W.random_layout(layout=k, **kw) for k in range(args.train_layouts)]
-    floor = args.weight_floor if args.weight_floor >= 0 else None
-    X, T, Wt, gen = L.generate(train, tol=tol, max_iters=5000, device=dev, weight_floor=floor, precision=tf.TF_FP32)
+    train = [W.random_layout(layout=k, **kw) for k in range(train_layouts)]
+    X, T, Wt, gen = L.generate(train, tol=tol, max_iters=5000, device=dev, weight_floor=weight_floor,
+                               precision=tf.TF_FP32)
     t_gen = time.perf_counter() - t0
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
-    ls = L.LearnedStart(kw["G"], hidden=64, seed=args.seed, overshoot_weight=args.overshoot_weight,
-                        shrink=args.shrink)
-    hist = ls.fit(X, T, Wt, epochs=args.epochs, batch=args.train_batch, lr=args.lr, seed=args.seed)
+    ls = L.LearnedStart(kw["G"], hidden=64, seed=seed, overshoot_weight=overshoot_weight, shrink=shrink)
+    hist = ls.fit(X, T, Wt, epochs=epochs, batch=batch, lr=lr, seed=seed)
     torch.cuda.synchronize(dev)
     t_train = time.perf_counter() - t0
     samples = X.shape[0]
     del X, T, Wt
     rows = []
-    for k in range(args.eval_layouts):
+    for k in range(eval_layouts):
         cfg = W.random_layout(layout=10000 + k, **kw)
         prob = tf.Problem.from_config(cfg, precision=tf.TF_FP32)
         Xh = L.cell_features(prob.mesh, cfg, dev)
@@ -650,7 +716,7 @@ def run_learned(args):
         row = {"layout": 10000 + k, "iters_zero": r0["iterations"], "iters_learned": r1["iterations"],
                "s_zero": round(s0, 4), "s_learned": round(s1, 4), "predict_s": round(r1["predict_seconds"], 5),
                "converged": bool(r0["converged"] and r1["converged"]), "start_rel_l2_err": round(start_err, 4)}
-        if k < args.eval_fp64:
+        if k < eval_fp64:
             p64 = tf.Problem.from_config(cfg, precision=tf.TF_FP64)
             ref = torch.zeros_like(phi0)
             r64 = p64.source_iterate(ref, 1e-10, 8000)
@@ -663,21 +729,38 @@ def run_learned(args):
         prob.close()
     iz = sum(r["iters_zero"] for r in rows)
     il = sum(r["iters_learned"] for r in rows)
-    sz = sum(r["s_zero"] for r in rows)
-    sl = sum(r["s_learned"] for r in rows)
-    line = {"metric": "time to 1e-6 per layout, learned start (zero-start alongside)", "value": sl / len(rows),
-            "unit": "s", "n_gpus": 1, "steps": len(rows), "warmup": 0, "ms_per_step": 1e3 * sl / len(rows),
-            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32+bf16",
-            "data": "synthetic",
-            "config": {"workload": f"learned_start_layouts_{kw['n']}^3_D{kw['n_polar'] * kw['n_az']}_G{kw['G']}",
-                       "train_layouts": args.train_layouts, "eval_layouts": args.eval_layouts, "samples": samples,
-                       "epochs": args.epochs, "batch": args.train_batch, "lr": args.lr, "tol": tol,
-                       "weight_floor": floor, "overshoot_weight": args.overshoot_weight, "shrink": args.shrink},
-            "zero_start_s": sz / len(rows), "iterations_zero": iz, "iterations_learned": il,
-            "iteration_ratio": il / max(iz, 1), "generate_s": round(t_gen, 1),
-            "generate_solve_s": round(sum(g["solve_seconds"] for g in gen), 2),
+    return {"workload": f"learned_start_layouts_{kw['n']}^3_D{kw['n_polar'] * kw['n_az']}_G{kw['G']}",
+            "train_layouts": train_layouts, "eval_layouts": eval_layouts, "samples": samples, "epochs": epochs,
+            "batch": batch, "lr": lr, "tol": tol, "weight_floor": weight_floor,
+            "overshoot_weight": overshoot_weight, "shrink": shrink,
+            "s_learned": sum(r["s_learned"] for r in rows) / len(rows),
+            "s_zero": sum(r["s_zero"] for r in rows) / len(rows),
+            "iterations_zero": iz, "iterations_learned": il, "iteration_ratio": il / max(iz, 1),
+            "generate_s": round(t_gen, 1), "generate_solve_s": round(sum(g["solve_seconds"] for g in gen), 2),
             "generate_iterations": [g["iterations"] for g in gen], "train_s": round(t_train, 2),
             "loss_history": [round(float(h), 5) for h in hist], "per_layout": rows}
+
+
+def run_learned(args):
+    """Learned initial flux (--config layout) on its own: one JSON line."""
+    import torch
+
+    import paper_2510_11513_gb300 as tf
+
+    torch.cuda.set_device(0)
+    kw = dict(n=args.n or 24, G=args.groups or 16, n_polar=args.polar or 8, n_az=args.azimuthal or 8)
+    floor = args.weight_floor if args.weight_floor >= 0 else None
+    r = learned_leg(tf, torch, kw, args.train_layouts, args.eval_layouts, args.eval_fp64, args.epochs,
+                    args.train_batch, args.lr, args.seed, args.batch_tol, floor, args.overshoot_weight, args.shrink)
+    line = {"metric": "time to 1e-6 per layout, learned start (zero-start alongside)", "value": r["s_learned"],
+            "unit": "s", "n_gpus": 1, "steps": r["eval_layouts"], "warmup": 0, "ms_per_step": 1e3 * r["s_learned"],
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32+bf16",
+            "data": "synthetic",
+            "config": {k: r[k] for k in ("workload", "train_layouts", "eval_layouts", "samples", "epochs", "batch",
+                                         "lr", "tol", "weight_floor", "overshoot_weight", "shrink")},
+            **{k: r[k] for k in ("iterations_zero", "iterations_learned", "iteration_ratio", "generate_s",
+                                 "generate_solve_s", "generate_iterations", "train_s", "loss_history", "per_layout")},
+            "zero_start_s": r["s_zero"]}
     print(json.dumps(line), flush=True)
 
 
@@ -700,6 +783,8 @@ def main():
                     help="task schedule of the timed sweep: many-task (amt) or bulk-synchronous")
     ap.add_argument("--no-bsp-compare", action="store_true", help="skip the many-task vs bulk-synchronous legs")
     ap.add_argument("--no-second-order", action="store_true", help="skip the second-order element leg")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched-problems leg")
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned-start leg")
     ap.add_argument("--order", type=int, default=1, choices=[1, 2, 3],
                     help="finite-element order of the timed sweep (2: ten nodes, 3: twenty nodes)")
     ap.add_argument("--bsp-steps", type=int, default=2, help="timed steps of each schedule in the comparison")
@@ -707,6 +792,10 @@ def main():
     ap.add_argument("--keep-ready", type=int, default=0, help="ready tasks a warp keeps and runs next (0 = library default)")
     ap.add_argument("--staging", type=int, default=0, help="0 auto, 1 no shared-memory staging, 2 two stages, 3 three stages")
     ap.add_argument("--pairing", type=int, default=0, help="0 auto, 1 off, 2 packed group pairs when G is even")
+    ap.add_argument("--task-shape", type=int, default=0, help="0 auto, 1 t-level blocks, 2 spatial patches")
+    ap.add_argument("--shard", default="directions", choices=["directions", "replicas"],
+                    help="N > 1: split the directions over the ranks (partial flux summed every step) or run replicas")
+    ap.add_argument("--patch-extent", type=float, default=0.0, help="spatial patches: region edge in cell sizes (0 = default)")
     ap.add_argument("--batch-count", type=int, default=64, help="--config batch: number of problems")
     ap.add_argument("--batch-tol", type=float, default=1e-6)
     ap.add_argument("--autotune", type=int, default=1, help="--config batch: autotuned task grain (1) or default (0)")

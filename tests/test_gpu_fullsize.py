@@ -2,8 +2,9 @@
 
 corner-source box (663,552 tets, 192 directions, 64 groups, FP32): one sweep
 from a seeded phi; the oracle solves sampled directions one by one (all
-cells, all groups) from the same source, and phi of sampled cells is checked
-against the FP64 quadrature sum of the device's own psi.
+cells, all groups) from the same source, phi of sampled cells is checked
+against the FP64 quadrature sum of the device's own psi, and phi of every cell
+in groups 0..7 against the oracle's transport step over all 192 directions.
 two-material box (196,608 tets, 128 directions, 32 groups, FP32): one full
 transport step compared with the oracle's, element by element.
 """
@@ -50,6 +51,30 @@ def test_corner_source_full_size_sampled():
         acc += w[a] * prob.psi(a, buf)[cells].double()
     got_phi = out[cells]
     assert _rel(got_phi.cpu().numpy(), acc.cpu().numpy()) < 1e-12
+
+
+def test_corner_source_full_size_phi_of_eight_groups_against_oracle():
+    """phi of the bench workload (all 663,552 cells, all 192 directions) after one transport step,
+    element by element against the oracle, for groups 0..7.  The workload scatters downward only,
+    so the source of groups 0..7 depends on phi of groups 0..7 alone: the oracle solves the problem
+    cut to its first eight groups (sigma_t, sigma_s and Q sliced), which is the full problem's first
+    eight groups exactly."""
+    import os
+
+    cfg = W.corner_source_box()
+    S = cfg["sigma_s"]
+    assert np.all(np.tril(S, -1) == 0.0)  # sigma_s[m][g_from][g_to] = 0 for g_to < g_from: no upscatter
+    prob = tf.Problem.from_config(cfg, precision=tf.TF_FP32)  # the bench's launch configuration
+    C, G = prob.n_cells, prob.n_groups
+    phi_in = np.random.default_rng(43).uniform(0.0, 1.0, (C, G, 4))
+    out = torch.zeros((C, G, 4), dtype=torch.float64, device="cuda")
+    prob.sweep(torch.from_numpy(phi_in).cuda(), out)
+    got = out[:, :8].cpu().numpy()
+    prob.close()
+    g8 = dict(cfg, n_groups=8, sigma_t=np.ascontiguousarray(cfg["sigma_t"][:, :8]),
+              sigma_s=np.ascontiguousarray(S[:, :8, :8]), Q=np.ascontiguousarray(cfg["Q"][:, :8]))
+    ref = oracle.Problem(g8).transport_step(np.ascontiguousarray(phi_in[:, :8]), threads=os.cpu_count() or 1)
+    assert _rel(got, ref) < 2e-5
 
 
 def test_two_material_full_size_one_step():

@@ -320,7 +320,7 @@ CONFIGS = {
     "batch": batch_of_problems,
     "layout": random_layout,
     "paper_context": paper_context_box,
-}
+}  # the hexahedral workloads join below, after their generators
 
 
 # ------------------------------------------------------------------ hexahedra
@@ -373,3 +373,12 @@ def hex_problem(cfg, twist: float = 0.25, jitter: float = 0.0):
                Q=np.ascontiguousarray(Q), name=cfg.get("name", "") + f"_hex_twist{twist:g}")
     out.pop("tets", None)
     return out
+
+
+def two_material_hex(**kw):
+    """The two-material box as a twisted hex grid (twist 0.25, no jitter)."""
+    return hex_problem(two_material_box(**kw))
+
+
+CONFIGS["paper_hex"] = paper_hex_box
+CONFIGS["two_material_hex"] = two_material_hex
