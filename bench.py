@@ -598,9 +598,9 @@ def run_ours(args):
         line["batch"] = {"default": batch_leg(tf, torch, 16, False, 1e-6),
                          "autotuned": batch_leg(tf, torch, 16, True, 1e-6)}
     if not args.no_learned and world == 1 and args.order == 1:
-        # the learned start: 16 training layouts, 4 held-out layouts from zero and from the network
+        # the learned start: 32 training layouts, 4 held-out layouts from zero and from the network
         lk = dict(n=24, G=16, n_polar=8, n_az=8)
-        line["learned"] = learned_leg(tf, torch, lk, 16, 4, 1, 20, 1024, 1e-3, 0, 1e-6)
+        line["learned"] = learned_leg(tf, torch, lk, 32, 4, 1, 20, 1024, 1e-3, 0, 1e-6)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(cfg)
     if rank == 0:
@@ -674,7 +674,7 @@ def run_batch(args):
 
 
 def learned_leg(tf, torch, kw, train_layouts, eval_layouts, eval_fp64, epochs, batch, lr, seed, tol,
-                weight_floor=None, overshoot_weight=1.0, shrink=0.5):
+                weight_floor=None, overshoot_weight=1.0, shrink=1.0, context=None, sample_cells=0):
     """Learned initial flux on the learned-start layouts: converged fluxes of `train_layouts`
     layouts from the plain FP32 solver, the network trained by the library's kernels, then
     `eval_layouts` held-out layouts solved from zero and from the learned start to the same
@@ -684,12 +684,14 @@ def learned_leg(tf, torch, kw, train_layouts, eval_layouts, eval_fp64, epochs, b
     dev = torch.device("cuda", torch.cuda.current_device())
     t0 = time.perf_counter()
     train = [W.random_layout(layout=k, **kw) for k in range(train_layouts)]
+    context = L.CONTEXT_STEPS if context is None else tuple(context)
     X, T, Wt, gen = L.generate(train, tol=tol, max_iters=5000, device=dev, weight_floor=weight_floor,
-                               precision=tf.TF_FP32)
+                               context=context, sample_cells=sample_cells, seed=seed, precision=tf.TF_FP32)
     t_gen = time.perf_counter() - t0
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
-    ls = L.LearnedStart(kw["G"], hidden=64, seed=seed, overshoot_weight=overshoot_weight, shrink=shrink)
+    ls = L.LearnedStart(kw["G"], hidden=64, seed=seed, overshoot_weight=overshoot_weight, shrink=shrink,
+                        context=context)
     hist = ls.fit(X, T, Wt, epochs=epochs, batch=batch, lr=lr, seed=seed)
     torch.cuda.synchronize(dev)
     t_train = time.perf_counter() - t0
@@ -699,7 +701,7 @@ def learned_leg(tf, torch, kw, train_layouts, eval_layouts, eval_fp64, epochs, b
     for k in range(eval_layouts):
         cfg = W.random_layout(layout=10000 + k, **kw)
         prob = tf.Problem.from_config(cfg, precision=tf.TF_FP32)
-        Xh = L.cell_features(prob.mesh, cfg, dev)
+        Xh = L.cell_features(prob.mesh, cfg, dev, context=ls.context)
         phi0 = torch.zeros((prob.n_cells, prob.n_groups, 4), dtype=torch.float64, device=dev)
         torch.cuda.synchronize(dev)
         start = ls.initial_flux(Xh)
@@ -731,6 +733,7 @@ def learned_leg(tf, torch, kw, train_layouts, eval_layouts, eval_fp64, epochs, b
     il = sum(r["iters_learned"] for r in rows)
     return {"workload": f"learned_start_layouts_{kw['n']}^3_D{kw['n_polar'] * kw['n_az']}_G{kw['G']}",
             "train_layouts": train_layouts, "eval_layouts": eval_layouts, "samples": samples, "epochs": epochs,
+            "context_steps": list(context), "sample_cells": sample_cells,
             "batch": batch, "lr": lr, "tol": tol, "weight_floor": weight_floor,
             "overshoot_weight": overshoot_weight, "shrink": shrink,
             "s_learned": sum(r["s_learned"] for r in rows) / len(rows),
@@ -750,14 +753,18 @@ def run_learned(args):
     torch.cuda.set_device(0)
     kw = dict(n=args.n or 24, G=args.groups or 16, n_polar=args.polar or 8, n_az=args.azimuthal or 8)
     floor = args.weight_floor if args.weight_floor >= 0 else None
+    ctx = () if args.context == "none" else (None if args.context == "default" else
+                                             tuple(int(x) for x in args.context.split(",")))
     r = learned_leg(tf, torch, kw, args.train_layouts, args.eval_layouts, args.eval_fp64, args.epochs,
-                    args.train_batch, args.lr, args.seed, args.batch_tol, floor, args.overshoot_weight, args.shrink)
+                    args.train_batch, args.lr, args.seed, args.batch_tol, floor, args.overshoot_weight, args.shrink,
+                    context=ctx, sample_cells=args.sample_cells)
     line = {"metric": "time to 1e-6 per layout, learned start (zero-start alongside)", "value": r["s_learned"],
             "unit": "s", "n_gpus": 1, "steps": r["eval_layouts"], "warmup": 0, "ms_per_step": 1e3 * r["s_learned"],
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32+bf16",
             "data": "synthetic",
             "config": {k: r[k] for k in ("workload", "train_layouts", "eval_layouts", "samples", "epochs", "batch",
-                                         "lr", "tol", "weight_floor", "overshoot_weight", "shrink")},
+                                         "lr", "tol", "weight_floor", "overshoot_weight", "shrink", "context_steps",
+                                         "sample_cells")},
             **{k: r[k] for k in ("iterations_zero", "iterations_learned", "iteration_ratio", "generate_s",
                                  "generate_solve_s", "generate_iterations", "train_s", "loss_history", "per_layout")},
             "zero_start_s": r["s_zero"]}
@@ -812,7 +819,10 @@ def main():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--weight-floor", type=float, default=-1.0,
                     help="--config layout: loss weights (phi/max)^2 + floor; negative = unweighted")
-    ap.add_argument("--shrink", type=float, default=0.5, help="--config layout: factor on the predicted flux")
+    ap.add_argument("--shrink", type=float, default=1.0, help="--config layout: factor on the predicted flux")
+    ap.add_argument("--context", default="default",
+                    help="--config layout: context steps of the inputs ('default', 'none' = one ring, or e.g. 4,16,64)")
+    ap.add_argument("--sample-cells", type=int, default=0, help="--config layout: training cells kept per layout (0 = all)")
     ap.add_argument("--overshoot-weight", type=float, default=1.0,
                     help="--config layout: loss weight of overshooting outputs (1 = plain squared error)")
     args = ap.parse_args()

@@ -105,6 +105,20 @@ tf_status tf_mlp_fit_scale(tf_handle net, const float *T, int64_t n_values, void
 tf_status tf_mlp_features(int64_t n_cells, int32_t n_groups, const int32_t *cell_material, const double *sigma_t,
                           const double *sigma_s, const double *Q, const int32_t *nbr, float *X, void *stream);
 
+/* Features with context: the G^2 + 4G features of tf_mlp_features, then, for each of the
+ * n_scales (<= 16) ascending counts t in steps (host array), the source and the total cross
+ * section seen over a neighbourhood of about sqrt(t) cells: starting from qbar (the cell-average
+ * source) and log sigma_t per (cell, group), t rounds of neighbour averaging (each round replaces
+ * a cell's value by the mean of its own and its face neighbours' values), written as
+ * log(averaged qbar + 1e-6) (G) and averaged log sigma_t (G).  X [n_cells][G^2 + 4G + 2G n_scales]
+ * (FP32, device).  One ring of neighbours cannot see a source more than one cell away, and the
+ * flux at a cell is set by the sources several mean free paths around it; the context widens
+ * that view.  Uses stream-ordered temporary device memory (4 n_cells G doubles).  Asynchronous on
+ * `stream`.  Errors: TF_ERR_ARG, TF_ERR_CUDA. */
+tf_status tf_mlp_features_context(int64_t n_cells, int32_t n_groups, const int32_t *cell_material,
+                                  const double *sigma_t, const double *sigma_s, const double *Q, const int32_t *nbr,
+                                  int32_t n_scales, const int32_t *steps, float *X, void *stream);
+
 /* Targets T [n_cells][G] from a scalar flux phi [n_cells][G][4] (FP64).  Asynchronous. */
 tf_status tf_mlp_targets(int64_t n_cells, int32_t n_groups, const double *phi, float *T, void *stream);
 

@@ -10,7 +10,9 @@ computes, so that the kernels can be checked against it:
 
   features   per-cell inputs read from the problem (cross sections, scattering
              probabilities, cell-average source and the averages of log sigma_t
-             and of the source over the face neighbours);
+             and of the source over the face neighbours), optionally followed by
+             context inputs: the source and log sigma_t averaged over wider
+             neighbourhoods (repeated neighbour averaging);
   targets    log(max(cell-average phi, 0) + 1e-6), standardised by their mean
              and deviation, predictions capped at the largest target;
   weights    (cell-average phi / its group maximum)^2 + floor, per target;
@@ -103,6 +105,35 @@ def features(nbr, cell_material, sigma_t, sigma_s, Q):
             X[c, 2 * G + G * G:3 * G + G * G] = log_st[m]
             X[c, 3 * G + G * G:] = np.log(qbar[c] + EPS_T)
     return X
+
+
+def smooth(nbr, v, steps):
+    """`steps` rounds of neighbour averaging of a per-cell field v [C][G]: each round replaces a
+    cell's value by the mean of its own and its face neighbours' values (a diffusion step on the
+    cell graph; after t rounds a value has spread over about sqrt(t) cells)."""
+    v = np.asarray(v, dtype=np.float64).copy()
+    for _ in range(int(steps)):
+        out = np.empty_like(v)
+        for c in range(v.shape[0]):
+            nb = [int(n) for n in nbr[c] if n >= 0]
+            out[c] = (v[c] + sum(v[n] for n in nb)) / (1 + len(nb))
+        v = out
+    return v
+
+
+def context_features(nbr, cell_material, sigma_t, Q, steps):
+    """Context inputs [C][2 G len(steps)]: for each t in `steps` (ascending), the source and the
+    total cross section seen over a neighbourhood of about sqrt(t) cells: log(smooth_t(qbar) + 1e-6)
+    (G), then smooth_t(log sigma_t) (G)."""
+    mat = np.asarray(cell_material)
+    qbar = cell_average(Q)
+    lst = np.log(sigma_t)[mat]
+    blocks, done, vq, vs = [], 0, qbar.copy(), lst.copy()
+    for t in steps:
+        vq, vs = smooth(nbr, vq, t - done), smooth(nbr, vs, t - done)
+        done = t
+        blocks += [np.log(vq + EPS_T), vs]
+    return np.concatenate(blocks, axis=1)
 
 
 def targets(phi):

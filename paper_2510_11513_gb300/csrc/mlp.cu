@@ -104,12 +104,12 @@ namespace {
 // (the flux grows linearly with the source, so its logarithm, the target, with log qbar)
 __global__ void features_kernel(int64_t C, int G, const int32_t *__restrict__ mat, const double *__restrict__ sig_t,
                                 const double *__restrict__ sig_s, const double *__restrict__ Q,
-                                const int32_t *__restrict__ nbr, float *__restrict__ X)
+                                const int32_t *__restrict__ nbr, float *__restrict__ X, int ld)
 {
     const int I = G * G + 4 * G;
     for (int64_t c = (int64_t)blockIdx.x * blockDim.y + threadIdx.y; c < C; c += (int64_t)gridDim.x * blockDim.y) {
         const int m = mat[c];
-        float *x = X + (size_t)c * I;
+        float *x = X + (size_t)c * ld;
         int nb[4], nn = 0;
         for (int f = 0; f < 4; ++f) {
             const int n = nbr[4 * c + f];
@@ -142,6 +142,57 @@ __global__ void features_kernel(int64_t C, int G, const int32_t *__restrict__ ma
             }
             x[e] = (float)val;
         }
+    }
+}
+
+// Context inputs: fields per (cell, group) averaged over wider neighbourhoods.  One round of
+// neighbour averaging replaces a cell's value by the mean of its own and its face neighbours'
+// values (a diffusion step on the cell graph: after t rounds a value has spread over about
+// sqrt(t) cells).
+__global__ void smooth_kernel(int64_t C, int G, const int32_t *__restrict__ nbr, const double *__restrict__ in,
+                              double *__restrict__ out)
+{
+    const int64_t CG = C * G;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < CG; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t c = i / G;
+        const int g = (int)(i - c * G);
+        double s = in[i];
+        int n = 1;
+        for (int f = 0; f < 4; ++f) {
+            const int32_t nb = nbr[4 * c + f];
+            if (nb >= 0) {
+                s += in[(size_t)nb * G + g];
+                ++n;
+            }
+        }
+        out[i] = s / n;
+    }
+}
+
+// The starting fields of the context: cell-average source qbar and log sigma_t per (cell, group).
+__global__ void context_init_kernel(int64_t C, int G, const int32_t *__restrict__ mat, const double *__restrict__ sig_t,
+                                    const double *__restrict__ Q, double *__restrict__ vq, double *__restrict__ vs)
+{
+    const int64_t CG = C * G;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < CG; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t c = i / G;
+        const int g = (int)(i - c * G);
+        const double *q = Q + (size_t)i * 4;
+        vq[i] = 0.25 * (((q[0] + q[1]) + q[2]) + q[3]);
+        vs[i] = log(sig_t[(size_t)mat[c] * G + g]);
+    }
+}
+
+// Columns [col, col + G) of X: log(vq + 1e-6); [col + G, col + 2G): vs.
+__global__ void context_write_kernel(int64_t C, int G, int ld, int col, const double *__restrict__ vq,
+                                     const double *__restrict__ vs, float *__restrict__ X)
+{
+    const int64_t CG = C * G;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < CG; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t c = i / G;
+        const int g = (int)(i - c * G);
+        X[(size_t)c * ld + col + g] = (float)log(vq[i] + 1e-6);
+        X[(size_t)c * ld + col + G + g] = (float)vs[i];
     }
 }
 
@@ -884,8 +935,47 @@ tf_status tf_mlp_features(int64_t n_cells, int32_t n_groups, const int32_t *cell
     if (n_cells < 1 || n_groups < 1 || !cell_material || !sigma_t || !sigma_s || !Q || !nbr || !X)
         return fail(TF_ERR_ARG, "tf_mlp_features: bad arguments");
     features_kernel<<<grid_for(n_cells, 4, 65535), dim3(32, 4), 0, (cudaStream_t)stream>>>(
-        n_cells, n_groups, cell_material, sigma_t, sigma_s, Q, nbr, X);
+        n_cells, n_groups, cell_material, sigma_t, sigma_s, Q, nbr, X, n_groups * n_groups + 4 * n_groups);
     MLP_CUDA(cudaGetLastError());
+    return TF_OK;
+}
+
+tf_status tf_mlp_features_context(int64_t n_cells, int32_t n_groups, const int32_t *cell_material,
+                                  const double *sigma_t, const double *sigma_s, const double *Q, const int32_t *nbr,
+                                  int32_t n_scales, const int32_t *steps, float *X, void *stream)
+{
+    if (n_cells < 1 || n_groups < 1 || !cell_material || !sigma_t || !sigma_s || !Q || !nbr || !X || n_scales < 0 ||
+        n_scales > 16 || (n_scales > 0 && !steps))
+        return fail(TF_ERR_ARG, "tf_mlp_features_context: bad arguments");
+    for (int k = 0; k < n_scales; ++k)
+        if (steps[k] < 0 || steps[k] > 100000 || (k > 0 && steps[k] < steps[k - 1]))
+            return fail(TF_ERR_ARG, "tf_mlp_features_context: steps must be ascending, in [0, 100000]");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int G = n_groups, base = G * G + 4 * G, ld = base + 2 * G * n_scales;
+    features_kernel<<<grid_for(n_cells, 4, 65535), dim3(32, 4), 0, st>>>(n_cells, G, cell_material, sigma_t, sigma_s,
+                                                                       Q, nbr, X, ld);
+    MLP_CUDA(cudaGetLastError());
+    if (n_scales == 0) return TF_OK;
+    const size_t CG = (size_t)n_cells * G;
+    double *buf = nullptr;  // vq, vs and their ping-pong copies
+    MLP_CUDA(cudaMallocAsync(&buf, 4 * CG * sizeof(double), st));
+    double *vq = buf, *vs = buf + CG, *tq = buf + 2 * CG, *ts = buf + 3 * CG;
+    const unsigned gb = (unsigned)grid_for((int64_t)CG, 256, 8 * 152);
+    context_init_kernel<<<gb, 256, 0, st>>>(n_cells, G, cell_material, sigma_t, Q, vq, vs);
+    int done = 0;
+    for (int k = 0; k < n_scales; ++k) {
+        for (; done < steps[k]; ++done) {
+            smooth_kernel<<<gb, 256, 0, st>>>(n_cells, G, nbr, vq, tq);
+            smooth_kernel<<<gb, 256, 0, st>>>(n_cells, G, nbr, vs, ts);
+            std::swap(vq, tq);
+            std::swap(vs, ts);
+        }
+        context_write_kernel<<<gb, 256, 0, st>>>(n_cells, G, ld, base + 2 * G * k, vq, vs, X);
+    }
+    cudaError_t e = cudaGetLastError();
+    const cudaError_t ef = cudaFreeAsync(buf, st);
+    if (e == cudaSuccess) e = ef;
+    MLP_CUDA(e);
     return TF_OK;
 }
 

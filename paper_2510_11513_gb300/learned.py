@@ -19,16 +19,22 @@ import torch
 from . import tfsweep as tf
 
 
-def n_features(n_groups: int) -> int:
+# Context radii of the default features: rounds of neighbour averaging (a value spreads over
+# about sqrt(t) cells), so the network sees the sources and cross sections up to about 32 cells away.
+CONTEXT_STEPS = (4, 16, 64, 256, 1024)
+
+
+def n_features(n_groups: int, context=()) -> int:
     """Inputs per cell: log sigma_t (G), scattering probabilities (G^2), log of the
     cell-average source (G) and the face-neighbour means of log sigma_t and (log of
-    the mean) of the source (2G)."""
-    return n_groups * n_groups + 4 * n_groups
+    the mean) of the source (2G); then 2G context inputs per entry of `context`."""
+    return n_groups * n_groups + 4 * n_groups + 2 * n_groups * len(context)
 
 
-def cell_features(mesh: tf.Mesh, cfg: dict, device="cuda", stream=None) -> torch.Tensor:
-    """Features [n_cells][G^2 + 4G] (FP32, device) of a problem given by its mesh
-    and its material / source arrays (cfg keys cell_material, sigma_t, sigma_s, Q)."""
+def cell_features(mesh: tf.Mesh, cfg: dict, device="cuda", stream=None, context=()) -> torch.Tensor:
+    """Features [n_cells][n_features(G, context)] (FP32, device) of a problem given by its mesh
+    and its material / source arrays (cfg keys cell_material, sigma_t, sigma_s, Q); `context`:
+    ascending rounds of neighbour averaging of the wider-neighbourhood inputs (none: one ring)."""
     G = int(cfg["n_groups"])
     C = mesh.n_cells
     nbr = torch.from_numpy(np.ascontiguousarray(mesh.geometry()["nbr"], dtype=np.int32)).to(device)
@@ -36,8 +42,11 @@ def cell_features(mesh: tf.Mesh, cfg: dict, device="cuda", stream=None) -> torch
     st = torch.from_numpy(np.ascontiguousarray(cfg["sigma_t"], dtype=np.float64)).to(device)
     ss = torch.from_numpy(np.ascontiguousarray(cfg["sigma_s"], dtype=np.float64)).to(device)
     Q = torch.from_numpy(np.ascontiguousarray(cfg["Q"], dtype=np.float64)).to(device)
-    X = torch.empty((C, n_features(G)), dtype=torch.float32, device=device)
-    tf.tf_mlp_features(C, G, mat, st, ss, Q, nbr, X, stream)
+    X = torch.empty((C, n_features(G, context)), dtype=torch.float32, device=device)
+    if context:
+        tf.tf_mlp_features_context(C, G, mat, st, ss, Q, nbr, list(context), X, stream)
+    else:
+        tf.tf_mlp_features(C, G, mat, st, ss, Q, nbr, X, stream)
     return X
 
 
@@ -57,17 +66,21 @@ def flux_weights(phi: torch.Tensor, n_groups: int, floor: float, stream=None) ->
     return W
 
 
-def generate(cfgs, tol=1e-6, max_iters=5000, device="cuda", weight_floor=None, **solver_opts):
+def generate(cfgs, tol=1e-6, max_iters=5000, device="cuda", weight_floor=None, context=CONTEXT_STEPS,
+             sample_cells=0, seed=0, **solver_opts):
     """Training data from the plain solver: for each problem configuration, its
     features and the targets of its converged zero-start solution, and with
-    `weight_floor` the loss weights of each problem's flux.  Returns
-    (X [sum C][I], T [sum C][G], W [sum C][G] or None, per-problem info dicts)."""
+    `weight_floor` the loss weights of each problem's flux.  sample_cells > 0 keeps a
+    seeded random subset of that many cells per problem (many layouts in bounded memory).
+    Returns (X [samples][I], T [samples][G], W [samples][G] or None, per-problem info dicts)."""
     Xs, Ts, Ws, infos = [], [], [], []
+    gen = torch.Generator(device="cpu")
+    gen.manual_seed(int(seed))
     for cfg in cfgs:
         t0 = time.perf_counter()
         prob = tf.Problem.from_config(cfg, **solver_opts)
         t_setup = time.perf_counter() - t0
-        X = cell_features(prob.mesh, cfg, device)
+        X = cell_features(prob.mesh, cfg, device, context=context)
         phi = torch.zeros((prob.n_cells, prob.n_groups, 4), dtype=torch.float64, device=device)
         t0 = time.perf_counter()
         r = prob.source_iterate(phi, tol, max_iters)
@@ -75,10 +88,16 @@ def generate(cfgs, tol=1e-6, max_iters=5000, device="cuda", weight_floor=None, *
         r["solve_seconds"] = time.perf_counter() - t0
         r["setup_seconds"] = t_setup
         r["name"] = cfg.get("name", "")
+        T = flux_targets(phi, prob.n_groups)
+        Wt = flux_weights(phi, prob.n_groups, weight_floor) if weight_floor is not None else None
+        if 0 < sample_cells < prob.n_cells:
+            keep = torch.randperm(prob.n_cells, generator=gen)[:sample_cells].to(device)
+            X, T = X[keep], T[keep]
+            Wt = Wt[keep] if Wt is not None else None
         Xs.append(X)
-        Ts.append(flux_targets(phi, prob.n_groups))
-        if weight_floor is not None:
-            Ws.append(flux_weights(phi, prob.n_groups, weight_floor))
+        Ts.append(T)
+        if Wt is not None:
+            Ws.append(Wt)
         infos.append(r)
         prob.close()
     return torch.cat(Xs), torch.cat(Ts), (torch.cat(Ws) if Ws else None), infos
@@ -88,12 +107,15 @@ class LearnedStart:
     """A network mapping cell features to the initial scalar flux."""
 
     def __init__(self, n_groups: int, hidden: int = 64, seed: int = 0, overshoot_weight: float = 1.0,
-                 shrink: float = 0.5):
+                 shrink: float = 1.0, context=CONTEXT_STEPS):
         """overshoot_weight > 1 weights overshooting outputs more in the loss, so the
-        network errs low; `shrink` scales the predicted flux (a start below the answer
-        cannot overshoot it; 0.5 took the fewest iterations over held-out layouts)."""
+        network errs low; `shrink` scales the predicted flux (a start uniformly too low by a
+        factor keeps that error in the slowest-decaying mode of source iteration, so the
+        default leaves the prediction as it is); `context`: the wider-neighbourhood inputs
+        (cell_features), () for one ring of neighbours only."""
         self.n_groups = int(n_groups)
-        self.net = tf.Mlp(n_features(self.n_groups), hidden, self.n_groups, seed)
+        self.context = tuple(context)
+        self.net = tf.Mlp(n_features(self.n_groups, self.context), hidden, self.n_groups, seed)
         tf.tf_mlp_limits(self.net.h, kappa=overshoot_weight)
         tf.tf_mlp_shrink(self.net.h, shrink)
 
@@ -105,6 +127,8 @@ class LearnedStart:
         phases whose learning rate drops by 3x each.  Returns the per-epoch mean loss."""
         if X.shape[0] != T.shape[0] or T.shape[1] != self.n_groups:
             raise ValueError("X and T disagree in samples or groups")
+        if X.shape[1] != n_features(self.n_groups, self.context):
+            raise ValueError("X does not have this network's inputs (one ring or context)")
         if W is not None and W.shape != T.shape:
             raise ValueError("W and T disagree in shape")
         tf.tf_mlp_fit_inputs(self.net.h, X, X.shape[0], stream)
@@ -118,7 +142,8 @@ class LearnedStart:
         return np.concatenate(hist)
 
     def initial_flux(self, X: torch.Tensor, stream=None) -> torch.Tensor:
-        """phi0 [n_cells][G][4] (FP64, device) for the cells whose features are X."""
+        """phi0 [n_cells][G][4] (FP64, device) for the cells whose features are X
+        (cell_features with this network's context)."""
         phi = torch.empty((X.shape[0], self.n_groups, 4), dtype=torch.float64, device=X.device)
         tf.tf_mlp_predict_phi(self.net.h, X, X.shape[0], phi, stream)
         return phi

@@ -32,7 +32,8 @@ SYMBOLS = (
     "tf_problem_psi", "tf_problem_set_reduce", "tf_problem_stats", "tf_status_string", "tf_last_error", "tf_integrated_flux_noalloc",
     # include/tflearn.h
     "tf_mlp_create", "tf_mlp_params", "tf_mlp_scale", "tf_mlp_limits", "tf_mlp_fit_inputs",
-    "tf_mlp_input_scale", "tf_mlp_shrink", "tf_mlp_fit_scale", "tf_mlp_features", "tf_mlp_targets",
+    "tf_mlp_input_scale", "tf_mlp_shrink", "tf_mlp_fit_scale", "tf_mlp_features", "tf_mlp_features_context",
+    "tf_mlp_targets",
     "tf_mlp_weights", "tf_mlp_forward", "tf_mlp_gradients", "tf_mlp_adam_step", "tf_mlp_train", "tf_mlp_predict_phi",
 )
 
@@ -132,6 +133,7 @@ def load(build_if_missing: bool = True):
     lib.tf_mlp_input_scale.argtypes = [H, vp, vp, vp, vp]
     lib.tf_mlp_fit_scale.argtypes = [H, vp, i64, vp]
     lib.tf_mlp_features.argtypes = [i64, i32, vp, vp, vp, vp, vp, vp, vp]
+    lib.tf_mlp_features_context.argtypes = [i64, i32, vp, vp, vp, vp, vp, i32, vp, vp, vp]
     lib.tf_mlp_targets.argtypes = [i64, i32, vp, vp, vp]
     lib.tf_mlp_forward.argtypes = [H, vp, i64, vp, vp]
     lib.tf_mlp_weights.argtypes = [i64, i32, vp, f32, vp, vp]
@@ -426,6 +428,13 @@ def tf_mlp_features(n_cells, n_groups, cell_material, sigma_t, sigma_s, Q, nbr, 
     return _check(load().tf_mlp_features(int(n_cells), int(n_groups), _ptr(cell_material), _ptr(sigma_t),
                                          _ptr(sigma_s), _ptr(Q), _ptr(nbr), _ptr(X), _stream_handle(stream)),
                   "tf_mlp_features")
+
+
+def tf_mlp_features_context(n_cells, n_groups, cell_material, sigma_t, sigma_s, Q, nbr, steps, X, stream=None):
+    st = (C.c_int32 * max(1, len(steps)))(*[int(t) for t in steps])
+    return _check(load().tf_mlp_features_context(int(n_cells), int(n_groups), _ptr(cell_material), _ptr(sigma_t),
+                                                 _ptr(sigma_s), _ptr(Q), _ptr(nbr), len(steps), st, _ptr(X),
+                                                 _stream_handle(stream)), "tf_mlp_features_context")
 
 
 def tf_mlp_targets(n_cells, n_groups, phi, T, stream=None):

@@ -348,3 +348,64 @@ def test_input_scale_standardises_columns():
     # closed form on two values
     m2, i2 = om.input_scale(np.array([[1.0], [5.0]]))
     assert m2[0] == 3.0 and i2[0] == 0.5
+
+
+# ------------------------------------------------------------------ context inputs
+def _chain_nbr(n):
+    """A chain of n cells: cell c touches c - 1 and c + 1 (neighbour lists padded with -1)."""
+    nbr = -np.ones((n, 4), dtype=np.int64)
+    for c in range(n):
+        k = 0
+        for d in (c - 1, c + 1):
+            if 0 <= d < n:
+                nbr[c, k] = d
+                k += 1
+    return nbr
+
+
+def test_smooth_chain_by_hand():
+    nbr = _chain_nbr(3)
+    v = np.array([[3.0], [0.0], [0.0]])
+    np.testing.assert_allclose(om.smooth(nbr, v, 1).ravel(), [1.5, 1.0, 0.0], rtol=0, atol=1e-15)
+    np.testing.assert_allclose(om.smooth(nbr, v, 2).ravel(), [1.25, 2.5 / 3.0, 0.5], rtol=0, atol=1e-15)
+    assert np.array_equal(om.smooth(nbr, v, 0), v)
+
+
+def test_smooth_is_the_power_of_the_averaging_matrix():
+    """t rounds of neighbour averaging = A^t v, A the row-stochastic averaging matrix of the
+    cell graph, built here independently from the mesh's face neighbours."""
+    xyz, tets = jittered_kuhn_mesh(2, 9)
+    nbr = geometry(xyz, tets)["nbr"]
+    C = len(tets)
+    A = np.zeros((C, C))
+    for c in range(C):
+        cells = [c] + [int(n) for n in nbr[c] if n >= 0]
+        A[c, cells] = 1.0 / len(cells)
+    v = np.random.default_rng(2).uniform(0.0, 1.0, (C, 3))
+    for t in (1, 5, 17):
+        np.testing.assert_allclose(om.smooth(nbr, v, t), np.linalg.matrix_power(A, t) @ v, rtol=1e-12, atol=1e-14)
+
+
+def test_smooth_constants_and_bounds():
+    xyz, tets = jittered_kuhn_mesh(2, 4)
+    nbr = geometry(xyz, tets)["nbr"]
+    C = len(tets)
+    c = np.full((C, 2), 7.25)
+    np.testing.assert_allclose(om.smooth(nbr, c, 9), c, rtol=1e-15)
+    v = np.random.default_rng(3).uniform(-2.0, 5.0, (C, 2))
+    s = om.smooth(nbr, v, 6)
+    assert np.all(s >= v.min(axis=0) - 1e-12) and np.all(s <= v.max(axis=0) + 1e-12)  # maximum principle
+
+
+def test_context_features_layout_and_zero_radius():
+    """Steps (0,): the context block is the cell's own log(qbar + 1e-6) and log sigma_t; later
+    blocks are the smoothings of the same starting fields, in the order the steps are given."""
+    cfg = random_layout(n=3, G=2, n_polar=2, n_az=4, layout=1)
+    nbr = geometry(cfg["xyz"], cfg["tets"])["nbr"]
+    ctx = om.context_features(nbr, cfg["cell_material"], cfg["sigma_t"], cfg["Q"], (0, 2))
+    qbar = om.cell_average(cfg["Q"])
+    lst = np.log(cfg["sigma_t"])[cfg["cell_material"]]
+    np.testing.assert_allclose(ctx[:, 0:2], np.log(qbar + om.EPS_T), rtol=1e-15)
+    np.testing.assert_allclose(ctx[:, 2:4], lst, rtol=1e-15)
+    np.testing.assert_allclose(ctx[:, 4:6], np.log(om.smooth(nbr, qbar, 2) + om.EPS_T), rtol=1e-15)
+    np.testing.assert_allclose(ctx[:, 6:8], om.smooth(nbr, lst, 2), rtol=1e-15)
