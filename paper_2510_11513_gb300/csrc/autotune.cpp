@@ -8,7 +8,8 @@
 // (cells_per_task = -1, a problem swept on its own) or the summed busy time of the
 // warps (-2, a problem swept in a batch, where the other problems keep the GPU busy).
 // The direction chunk is not tuned: the fewest chunks the memory allows is always
-// fastest (each chunk repeats the fill, the launch tail and the phi pass).
+// fastest (each chunk repeats the fill, the launch tail and the phi pass).  The default
+// choice is the incumbent; a candidate replaces it only when at least 5 % faster.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -68,10 +69,20 @@ tf_status autotune_cells_per_task(const Mesh &m, const Quad &q, int32_t G, int32
     const bool fp32 = opt.precision == TF_FP32, order1 = opt.order != 2;
     const bool paired = order1 && fp32 && G % 2 == 0 && (opt.pairing == 2 || (opt.pairing == 0 && G % 32 != 0));
     const int cap = (!order1 || paired) ? 32 : 64;
-    std::vector<int32_t> cand;
+    // the default grain is the incumbent: another candidate replaces it only when its trial is
+    // at least 5 % faster (trial sweeps over a direction sample are noisy at that level)
+    int32_t b_def = 0;
+    {
+        tf_options o = opt;
+        o.cells_per_task = 0;
+        bool pt = false;
+        TaskShape sh;
+        if (task_grain(o, m, G, &b_def, &pt, &sh) != TF_OK) b_def = std::max(2, std::min(cap, 1024 / G));
+    }
+    std::vector<int32_t> cand{b_def};
     for (int32_t b : {2, 4, 8, 16, 32, 64})
-        if ((b > 2 || opt.schedule != TF_SCHED_AMT) && b <= cap && (int64_t)b * G <= 4096) cand.push_back(b);
-    if (cand.empty()) cand.push_back(std::max(2, std::min(cap, 1024 / G)));
+        if (b != b_def && (b > 2 || opt.schedule != TF_SCHED_AMT) && b <= cap && (int64_t)b * G <= 4096)
+            cand.push_back(b);
     const int nb = order1 ? 4 : (opt.order == 3 ? 20 : 10);
     std::vector<double> phi((size_t)m.nc * G * nb, 1.0);
     double *dphi = nullptr;
@@ -126,7 +137,7 @@ tf_status autotune_cells_per_task(const Mesh &m, const Quad &q, int32_t G, int32
             rep->seconds[tried] = t;
         }
         ++tried;
-        if (t >= 0.0 && t < best_t) {
+        if (t >= 0.0 && t < (b == b_def ? best_t : 0.95 * best_t)) {
             best_t = t;
             best.cells = b;
         }
@@ -148,7 +159,7 @@ tf_status autotune_cells_per_task(const Mesh &m, const Quad &q, int32_t G, int32
         o.octant_window = v.window;
         const double t = trial(o);
         ++nvar;
-        if (t >= 0.0 && t < best_t) {
+        if (t >= 0.0 && t < 0.95 * best_t) {
             best_t = t;
             best = v;
         }

@@ -80,7 +80,14 @@ def test_autotuned_task_grain():
     st = p.stats()
     assert st["tuned_n"] >= 2 and not st["tuned_cached"]
     assert st["cells_per_task"] in st["tuned_candidates"]
-    best = st["tuned_candidates"][int(np.argmin(st["tuned_seconds"]))]
+    # the default grain is the first candidate (the incumbent); another grain replaces it only
+    # when its trial is at least 5 % faster than the best so far
+    n = st["tuned_n"]
+    cand, secs = list(st["tuned_candidates"][:n]), list(st["tuned_seconds"][:n])
+    best, best_t = cand[0], secs[0]
+    for b, t in zip(cand[1:], secs[1:]):
+        if 0.0 <= t < 0.95 * best_t:
+            best, best_t = b, t
     assert st["cells_per_task"] == best
     # phase 2 (kernel variant, octant window) leaves valid knobs, and the problem runs with them
     assert st["tuned_pairing"] in (0, 1, 2) and st["tuned_staging"] in (0, 1) and st["tuned_window"] in (0, 2)
