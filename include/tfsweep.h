@@ -121,7 +121,10 @@ typedef struct {
                               * no task is seeded; TF_SCHED_BSP: each barrier waits for one CTA more
                               * than the grid holds); not allowed with TF_SCHED_BSP_LAUNCH */
     double psi_budget_gb;    /* device memory allowed for the angular-flux store; 0 = 80 % of free memory */
-    int32_t task_order;      /* 0 = FIFO ready queue, seeds longest-critical-path first */
+    int32_t task_order;      /* 0 = FIFO ready queue, seeds longest-critical-path first, and of the tasks
+                              * a warp makes ready it runs next the one with the longest chain of
+                              * downwind tasks (a direction's critical path skips the queue);
+                              * 1 = the same, but the warp runs next the first task it made ready */
     int32_t staging;         /* 0 = automatic: stage each cell's rows in shared memory with bulk
                               * asynchronous copies when n_groups is a multiple of 32 and they fit,
                               * two cells ahead per warp with six CTAs per SM in FP32, three in FP64;
@@ -152,7 +155,7 @@ typedef struct {
                               * 1e-10 = pointwise relative change (unreachable in FP32 where DG
                               * undershoots put |phi| near 0) */
     double patch_extent;     /* spatial patches: edge of a patch region in mean cell sizes (the edge of
-                              * a cube of six tetrahedra of the mean volume); 0 = automatic (3) */
+                              * a cube of six tetrahedra of the mean volume); 0 = automatic (2) */
     double reserved_d[2];
 } tf_options;
 
@@ -241,8 +244,9 @@ tf_status tf_mesh_create(int64_t n_vertices, const double *xyz, int64_t n_cells,
  * outward), which classify faces (inflow iff Omega.Nbar_f < -1e-12 |Nbar_f|); face
  * neighbours.  At most 2^26 - 1 cells.  Host-only: no CUDA call.
  * Errors: TF_ERR_ARG, TF_ERR_MESH, TF_ERR_NOMEM.  Problems on such a mesh take the
- * trilinear element (opt->order 0 or 1), vacuum boundaries and no S1; their Q, phi
- * and psi hold the eight vertex values of every cell ([n_cells][n_groups][8]). */
+ * trilinear element (opt->order 0 or 1); their Q, phi and psi hold the eight vertex values
+ * of every cell ([n_cells][n_groups][8]); S1 adds (Omega.S1) int b_i per node, and
+ * psi_inflow is read at the vertices of boundary inflow faces. */
 tf_status tf_mesh_create_hex(int64_t n_vertices, const double *xyz, int64_t n_cells, const int32_t *hexes,
                              tf_handle *out);
 

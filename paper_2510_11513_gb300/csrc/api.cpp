@@ -68,7 +68,7 @@ tf_status task_shape_of(const tf_options &o, const Mesh &m, int32_t G, bool *pat
     if (!(o.patch_extent >= 0.0) || o.patch_extent > 64.0)
         return fail(TF_ERR_ARG, "patch_extent must be in [0, 64]");
     *patches = o.task_shape == TF_TASK_PATCHES || (o.task_shape == TF_TASK_AUTO && ok);
-    shape->extent = o.patch_extent > 0.0 ? o.patch_extent : 3.0;
+    shape->extent = o.patch_extent > 0.0 ? o.patch_extent : 2.0;
     // the staged kernels issue a cell's copies one cell ahead (two stages) or two (three stages)
     const bool three = o.staging == 3 || (o.staging != 2 && o.precision == TF_FP64);
     shape->gap = three ? 2 : 1;
@@ -236,9 +236,8 @@ tf_status tf_problem_create(tf_handle mesh, tf_handle quad, int32_t n_groups, in
     Mesh *m = as<Mesh>(mesh, Kind::Mesh);
     Quad *q = as<Quad>(quad, Kind::Quad);
     if (!m || !q) return fail(TF_ERR_ARG, "tf_problem_create: mesh or quadrature handle invalid");
-    if (m->nf == 6 && (S1 || psi_inflow || (opt && opt->order > 1)))
-        return fail(TF_ERR_ARG, "tf_problem_create: hexahedral meshes take the trilinear element (order 0 or 1) "
-                                "with vacuum boundaries and no S1");
+    if (m->nf == 6 && opt && opt->order > 1)
+        return fail(TF_ERR_ARG, "tf_problem_create: hexahedral meshes take the trilinear element (order 0 or 1)");
     if (n_groups < 1 || n_groups > 1024 || n_materials < 1)
         return fail(TF_ERR_ARG, "tf_problem_create: need 1 <= n_groups <= 1024 and n_materials >= 1");
     if (!cell_material || !sigma_t || !sigma_s || !Q) return fail(TF_ERR_ARG, "tf_problem_create: NULL input array");

@@ -6,10 +6,13 @@
 // is the reference face xi_d = s, its face-local nodes k = 0..3 the vertices whose bit
 // d equals s, in increasing local index.  Local system (weak form of Eq. (1)
 // integrated back by parts, upwind trace on the inflow faces):
-//   [ sum_d Omega_d G_d + sum_{f inflow} W_f + sigma_t M ] psi = M q + sum_{f inflow} W_f psi_up
+//   [ sum_d Omega_d G_d + sum_{f inflow} W_f + sigma_t M ] psi = M q + (Omega.S1) M 1 + sum_{f inflow} W_f psi_up
 // with M = int b_i b_j, G_d = int b_i d b_j / dx_d and, on face f's nodes,
 // W_f = -sum_d Omega_d F_{f,d}, F_{f,d} = int_f N_d b_k b_l (N the outward area-vector
-// density; on a planar face W_f = int_f |Omega.N| b_k b_l).  A face is inflow when the
+// density; on a planar face W_f = int_f |Omega.N| b_k b_l), psi_up the upwind cell's nodal
+// values on an interior face and the prescribed inflow at the face's vertices (zero under
+// vacuum) on a boundary face, and S1 an optional linear anisotropic source constant over the
+// cell (M 1: the row sums of M).  A face is inflow when the
 // sweep graph says so (the sign of Omega.Nbar_f, Nbar_f = int_f N).  The symmetric part
 // of the matrix, (1/2) sum_f |Omega.F_f| + sigma_t M, is positive definite on planar
 // faces and was at least 0.19 max|A| on the twisted grids, so elimination needs no
@@ -82,17 +85,23 @@ __device__ __forceinline__ void hex_unit(const SweepArgs<T> &A, const HexGeo<T> 
     T a[8][8], b[8], x[8], qv[8];
 #pragma unroll
     for (int j = 0; j < 8; ++j) qv[j] = __ldg(qc + (size_t)j * G);
+    T os = T(0);  // Omega.S1
+    if (A.S1) {
+        const V4<T> s1 = ld_ro(A.S1 + (size_t)c * G + g);
+        os = ox * s1.x + oy * s1.y + oz * s1.z;
+    }
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
-        T bi = T(0);
+        T bi = T(0), ri = T(0);
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
             const T m = __ldg(&cg->M[8 * i + j]);
             a[i][j] = ox * __ldg(&cg->Gd[0][8 * i + j]) + oy * __ldg(&cg->Gd[1][8 * i + j]) +
                       oz * __ldg(&cg->Gd[2][8 * i + j]) + sig * m;
             bi += m * qv[j];
+            ri += m;
         }
-        b[i] = bi;
+        b[i] = bi + os * ri;
     }
 #pragma unroll
     for (int f = 0; f < 6; ++f) {
@@ -109,12 +118,19 @@ __device__ __forceinline__ void hex_unit(const SweepArgs<T> &A, const HexGeo<T> 
 #pragma unroll
             for (int l = 0; l < 4; ++l) a[hex_node(f, k)][hex_node(f, l)] += w[k][l];
         const int32_t n = __ldg(&cg->nbr[f]);
-        if (n < 0) continue;  // vacuum boundary: no inflow
-        const uint32_t nm = __ldg(&cg->nmap[f]);
-        const T *up = psi + (psi_dir + (size_t)n) * 8 * (size_t)G + g;
         T u[4];
+        if (n >= 0) {
+            const uint32_t nm = __ldg(&cg->nmap[f]);
+            const T *up = psi + (psi_dir + (size_t)n) * 8 * (size_t)G + g;
 #pragma unroll
-        for (int l = 0; l < 4; ++l) u[l] = __ldcg(up + (size_t)((nm >> (4 * l)) & 15u) * G);
+            for (int l = 0; l < 4; ++l) u[l] = __ldcg(up + (size_t)((nm >> (4 * l)) & 15u) * G);
+        } else if (A.psi_in) {  // prescribed inflow at the face's vertices
+#pragma unroll
+            for (int l = 0; l < 4; ++l)
+                u[l] = __ldg(A.psi_in + (size_t)__ldg(A.hexv + 8 * (size_t)c + hex_node(f, l)) * G + g);
+        } else {
+            continue;  // vacuum boundary: no inflow
+        }
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             T t = T(0);
@@ -216,27 +232,40 @@ __device__ __forceinline__ void run_task_hex_shared(const SweepArgs<T> &A, uint4
             T a[8][8], b[8], x[8], qv[8];
 #pragma unroll
             for (int j = 0; j < 8; ++j) qv[j] = __ldg(qc + (size_t)j * G);
+            T os = T(0);  // Omega.S1
+            if (A.S1) {
+                const V4<T> s1 = ld_ro(A.S1 + (size_t)c * G + g);
+                os = ox * s1.x + oy * s1.y + oz * s1.z;
+            }
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
-                T bi = T(0);
+                T bi = T(0), ri = T(0);
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
                     const T m = M[8 * i + j];
                     a[i][j] = S[8 * i + j] + sig * m;
                     bi += m * qv[j];
+                    ri += m;
                 }
-                b[i] = bi;
+                b[i] = bi + os * ri;
             }
 #pragma unroll
             for (int f = 0; f < 6; ++f) {
                 if (!((mask >> f) & 1u)) continue;
                 const int32_t n = __ldg(&cg->nbr[f]);
-                if (n < 0) continue;  // vacuum boundary: no inflow
-                const uint32_t nm = __ldg(&cg->nmap[f]);
-                const T *up = psi + (psi_dir + (size_t)n) * 8 * (size_t)G + g;
                 T uv[4];
+                if (n >= 0) {
+                    const uint32_t nm = __ldg(&cg->nmap[f]);
+                    const T *up = psi + (psi_dir + (size_t)n) * 8 * (size_t)G + g;
 #pragma unroll
-                for (int l = 0; l < 4; ++l) uv[l] = __ldcg(up + (size_t)((nm >> (4 * l)) & 15u) * G);
+                    for (int l = 0; l < 4; ++l) uv[l] = __ldcg(up + (size_t)((nm >> (4 * l)) & 15u) * G);
+                } else if (A.psi_in) {  // prescribed inflow at the face's vertices
+#pragma unroll
+                    for (int l = 0; l < 4; ++l)
+                        uv[l] = __ldg(A.psi_in + (size_t)__ldg(A.hexv + 8 * (size_t)c + hex_node(f, l)) * G + g);
+                } else {
+                    continue;  // vacuum boundary: no inflow
+                }
 #pragma unroll
                 for (int kf = 0; kf < 4; ++kf) {
                     T t = T(0);

@@ -155,15 +155,18 @@ __global__ void __launch_bounds__(256) leak_ho_kernel(const T *__restrict__ psi,
     }
 }
 
-// Boundary leakage of trilinear hexahedra (vacuum boundaries): per (boundary cell, group)
-// over the chunk's directions, w_a sum over the boundary outflow faces f (Omega_a . Nbar_f
-// not below the sweep graph's inflow threshold -1e-12 |Nbar_f|) of
-// int_f (Omega_a . N) psi_a = sum_k psi_k sum_d Omega_d sum_l F[f][d][l][k].
+// Boundary leakage of trilinear hexahedra: per (boundary cell, group) over the chunk's
+// directions, w_a sum over the boundary faces f of int_f (Omega_a . N) psi =
+// sum_k psi_k sum_d Omega_d sum_l F[f][d][l][k], psi the cell's own nodal values on an
+// outflow face (Omega_a . Nbar_f not below the sweep graph's inflow threshold
+// -1e-12 |Nbar_f|) and the prescribed inflow at the face's vertices on an inflow face
+// (vacuum, psi_in NULL: nothing).
 template <class T>
 __global__ void __launch_bounds__(256) leak_hex_kernel(const T *__restrict__ psi, const WeightPair *__restrict__ wts,
                                                        const V4<T> *__restrict__ omega, int Dc, int64_t C, int G,
                                                        const uint32_t *__restrict__ bcells, int64_t nb,
-                                                       const HexGeo<T> *__restrict__ geo, double *__restrict__ leak)
+                                                       const HexGeo<T> *__restrict__ geo, const int32_t *__restrict__ hexv,
+                                                       const T *__restrict__ psi_in, double *__restrict__ leak)
 {
     for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < nb * G; u += (int64_t)gridDim.x * blockDim.x) {
         const int64_t b = u / G;
@@ -180,14 +183,16 @@ __global__ void __launch_bounds__(256) leak_hex_kernel(const T *__restrict__ psi
                 if (cg.nbr[f] >= 0) continue;
                 const T nx = cg.nbar[f][0], ny = cg.nbar[f][1], nz = cg.nbar[f][2];
                 const T sf = om.x * nx + om.y * ny + om.z * nz;
-                if (sf < T(-1e-12) * sqrt(nx * nx + ny * ny + nz * nz)) continue;  // inflow face of a vacuum boundary
+                const bool in = sf < T(-1e-12) * sqrt(nx * nx + ny * ny + nz * nz);
+                if (in && !psi_in) continue;  // inflow face of a vacuum boundary
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
                     T col = T(0);
 #pragma unroll
                     for (int l = 0; l < 4; ++l)
                         col += om.x * cg.F[f][0][4 * l + k] + om.y * cg.F[f][1][4 * l + k] + om.z * cg.F[f][2][4 * l + k];
-                    t += col * s[(size_t)hex_node(f, k) * G];
+                    const int v = hex_node(f, k);
+                    t += col * (in ? psi_in[(size_t)hexv[8 * (size_t)c + v] * G + g] : s[(size_t)v * G]);
                 }
             }
             if constexpr (sizeof(T) == 8) {

@@ -676,6 +676,7 @@ struct DeviceState {
     uint4 *task = nullptr;
     uint32_t *down = nullptr;
     int *indeg = nullptr;
+    int32_t *blevel = nullptr;  // [T] longest chain of downwind tasks below each task
     int *counters = nullptr;
     unsigned long long *slots = nullptr;
     uint32_t *seeds = nullptr;
@@ -686,6 +687,7 @@ struct DeviceState {
     void *S1 = nullptr;
     void *psi_in = nullptr;
     int4 *tets = nullptr;
+    int32_t *hexv = nullptr;   // hexahedra with prescribed inflow: [C][8] global vertices
     void *q = nullptr;
     void *psi = nullptr;
     double *vol4 = nullptr;
@@ -994,7 +996,8 @@ template <class T> tf_status create_typed_p2(Problem &p, DeviceState &d, const i
 // cross sections, the per-cell basis integrals int b_i (row sums of M) for the
 // statistics, Q reordered node-major [C][8][G].
 template <class T> tf_status create_typed_hex(Problem &p, DeviceState &d, const int32_t *cell_material,
-                                              const double *sigma_t, const double *sigma_s, const double *Q)
+                                              const double *sigma_t, const double *sigma_s, const double *Q, const double *S1,
+                                              const double *psi_in)
 {
     const Mesh &m = *p.mesh;
     tf_status s;
@@ -1046,6 +1049,13 @@ template <class T> tf_status create_typed_hex(Problem &p, DeviceState &d, const 
             for (int gq = 0; gq < d.G; ++gq)
                 for (int i = 0; i < 8; ++i) Qs[((size_t)c * 8 + i) * d.G + gq] = Q[((size_t)c * d.G + gq) * 8 + i];
         if ((s = upload_typed<T>(d, &d.Q, Qs.data(), Qs.size())) != TF_OK) return s;
+    }
+    if (S1) {  // [C][G] (x, y, z, 0): the linear anisotropic source Omega.S1, constant over each cell
+        if ((s = upload_vec3<T>(d, &d.S1, S1, (size_t)d.C * d.G, nullptr)) != TF_OK) return s;
+    }
+    if (psi_in) {  // isotropic inflow per boundary vertex and group, and the cells' vertices
+        if ((s = upload_typed<T>(d, &d.psi_in, psi_in, (size_t)d.nv * d.G)) != TF_OK) return s;
+        if ((s = upload(d, &d.hexv, m.hexes.data(), sizeof(int32_t) * 8 * (size_t)m.nc)) != TF_OK) return s;
     }
     return TF_OK;
 }
@@ -1217,6 +1227,7 @@ tf_status device_create(Problem &p, const int32_t *cell_material, const double *
     }
     if ((s = upload(d, &d.down, g.down_list.data(), g.down_list.size() * 4)) != TF_OK) return s;
     if ((s = upload(d, &d.indeg, g.task_indeg.data(), (size_t)T * 4)) != TF_OK) return s;
+    if ((s = upload(d, &d.blevel, g.task_blevel.data(), (size_t)T * 4)) != TF_OK) return s;
     if ((s = dmalloc(d, &d.counters, (size_t)T * 4)) != TF_OK) return s;
     // cell volumes / 4 (FP64) for the integrated flux
     {
@@ -1225,8 +1236,8 @@ tf_status device_create(Problem &p, const int32_t *cell_material, const double *
         if ((s = upload(d, &d.vol4, v4.data(), v4.size() * 8)) != TF_OK) return s;
     }
     if (d.hex)
-        s = d.fp64 ? create_typed_hex<double>(p, d, cell_material, sigma_t, sigma_s, Q)
-                   : create_typed_hex<float>(p, d, cell_material, sigma_t, sigma_s, Q);
+        s = d.fp64 ? create_typed_hex<double>(p, d, cell_material, sigma_t, sigma_s, Q, S1, psi_in)
+                   : create_typed_hex<float>(p, d, cell_material, sigma_t, sigma_s, Q, S1, psi_in);
     else if (d.order == 3)
         s = d.fp64 ? create_typed_p3<double>(p, d, cell_material, sigma_t, sigma_s, Q)
                    : create_typed_p3<float>(p, d, cell_material, sigma_t, sigma_s, Q);
@@ -1696,6 +1707,7 @@ template <class T> SweepArgs<T> make_args(Problem &p, int k)
     A.S1 = (const V4<T> *)d.S1;
     A.psi_in = (const T *)d.psi_in;
     A.tets = d.tets;
+    A.hexv = d.hexv;
     A.C = d.C;
     A.G = d.G;
     A.dir_begin = a0;
@@ -1705,6 +1717,8 @@ template <class T> SweepArgs<T> make_args(Problem &p, int k)
     A.wait_limit_ns = (unsigned long long)(p.opt.wait_limit_s * 1e9);
     A.max_cells = p.graph.cells_per_task;
     A.intra = d.patches ? 1 : 0;
+    A.blevel = p.opt.task_order == 1 ? nullptr : d.blevel;
+
     A.aux = d.cells_aux;
     A.warp_smem = d.warp_smem;
     A.dir_group = d.dir_group;
@@ -1750,7 +1764,7 @@ template <class T> void launch_phi(Problem &p, int k, double *phi_out, cudaStrea
             const V4<T> *om = (const V4<T> *)d.omega + a0;
             if (d.hex)
                 leak_hex_kernel<T><<<lb, 256, 0, st>>>(ps, d.wts + a0, om, a1 - a0, d.C, d.G, d.bcells, d.n_bcells,
-                                                       (const HexGeo<T> *)d.geo2, d.leak);
+                                                       (const HexGeo<T> *)d.geo2, d.hexv, (const T *)d.psi_in, d.leak);
             else if (d.order == 3)
                 leak_ho_kernel<T, 20, 10, P3Geo<T>><<<lb, 256, 0, st>>>(ps, d.wts + a0, om, a1 - a0, d.C, d.G, d.bcells,
                                                                         d.n_bcells, (const P3Geo<T> *)d.geo2, tb, d.leak);
@@ -2116,6 +2130,7 @@ struct BatchRun {
     std::vector<Problem *> P;
     int device = 0, n = 0, max_chunks = 0, sm_count = 0;
     bool fp64 = false;
+    bool hex = false;  // the batch holds hexahedral problems
     Ctrl *ctrl = nullptr, *ctrl_host = nullptr;
     unsigned long long *slots = nullptr;
     void *args = nullptr;          // [max_chunks][n] SweepArgs<T>
@@ -2143,7 +2158,10 @@ struct BatchRun {
     }
 };
 
-template <class T> const void *batch_kernel_fn() { return (const void *)sweep_batch_kernel<T>; }
+template <class T> const void *batch_kernel_fn(bool hex)
+{
+    return hex ? (const void *)sweep_batch_kernel<T, true> : (const void *)sweep_batch_kernel<T, false>;
+}
 
 tf_status batch_setup(BatchRun &B, const tf_handle *problems, int32_t n)
 {
@@ -2156,8 +2174,9 @@ tf_status batch_setup(BatchRun &B, const tf_handle *problems, int32_t n)
             return fail(TF_ERR_ARG, "batched problems must share one device and one precision");
         if (p->opt.inject_stall) return fail(TF_ERR_ARG, "inject_stall is not supported in batched launches");
         if (p->reduce) return fail(TF_ERR_ARG, "a problem with a reduce function (direction sharding) cannot be batched");
-        if (p->dev->schedule != TF_SCHED_AMT || p->dev->order != 1 || p->dev->hex)
-            return fail(TF_ERR_ARG, "batched launches run only linear-element problems with the TF_SCHED_AMT schedule");
+        if (p->dev->schedule != TF_SCHED_AMT || p->dev->order != 1)
+            return fail(TF_ERR_ARG, "batched launches run only linear tetrahedra and trilinear hexahedra with the "
+                                    "TF_SCHED_AMT schedule");
         B.max_chunks = std::max(B.max_chunks, p->dev->n_chunks);
         B.warp_smem = std::max(B.warp_smem, p->dev->warp_smem);
     }
@@ -2187,7 +2206,8 @@ tf_status batch_setup(BatchRun &B, const tf_handle *problems, int32_t n)
     TF_CUDA(cudaStreamCreateWithFlags(&B.st, cudaStreamNonBlocking));
     while (B.wpc > 1 && (size_t)B.warp_smem * B.wpc > 227 * 1024) B.wpc /= 2;
     const int dyn = (int)(B.warp_smem * B.wpc);
-    const void *kfn = B.fp64 ? batch_kernel_fn<double>() : batch_kernel_fn<float>();
+    for (Problem *p : B.P) B.hex = B.hex || p->dev->hex;
+    const void *kfn = B.fp64 ? batch_kernel_fn<double>(B.hex) : batch_kernel_fn<float>(B.hex);
     TF_CUDA(ensure_dyn_smem(kfn, dyn));
     int per_sm = 0;
     TF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, 32 * B.wpc, dyn));
@@ -2260,7 +2280,10 @@ tf_status batch_enqueue(BatchRun &B, const std::vector<char> &active, int k, boo
         BA.n_tasks = B.n_tasks[c];
         BA.wait_limit_ns = (unsigned long long)(B.P[0]->opt.wait_limit_s * 1e9);
         BA.warp_smem = B.warp_smem;
-        sweep_batch_kernel<T><<<B.grid, 32 * B.wpc, (size_t)B.warp_smem * B.wpc, st>>>(BA);
+        if (B.hex)
+            sweep_batch_kernel<T, true><<<B.grid, 32 * B.wpc, (size_t)B.warp_smem * B.wpc, st>>>(BA);
+        else
+            sweep_batch_kernel<T, false><<<B.grid, 32 * B.wpc, (size_t)B.warp_smem * B.wpc, st>>>(BA);
         TF_CUDA(cudaGetLastError());
         end_kernel<<<1, 1, 0, st>>>(B.ctrl);
         for (int i : B.part[c]) launch_phi<T>(*B.P[i], c, B.P[i]->dev->phi_buf[1 - k], st);

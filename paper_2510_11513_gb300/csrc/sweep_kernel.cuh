@@ -159,6 +159,7 @@ template <class T> struct SweepArgs {
     const V4<T> *S1;            // [C][G] or NULL
     const T *psi_in;            // [nv][G] or NULL
     const int4 *tets;           // [C] (only with psi_in)
+    const int32_t *hexv;        // hexahedra: [C][8] global vertices (only with psi_in)
     int64_t C;
     int32_t G;
     int32_t dir_begin;          // first direction of the chunk
@@ -182,6 +183,8 @@ template <class T> struct SweepArgs {
     int32_t keep_max;            // ready tasks a warp keeps and runs next (1..4)
     int32_t intra;               // 1: a task's cells may depend on each other (spatial patches)
     const uint8_t *aux;          // patches, staged variants: per cell entry, its in-task upwind handoffs
+    const int32_t *blevel;       // [tasks] longest chain of downwind tasks below each task (global ids), or NULL
+
     const void *p3tab;           // third-order element: P3Dev<T> tables (mode 7)
 };
 
@@ -446,6 +449,23 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
 }
 __device__ __forceinline__ void fence_proxy_async_shared() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 __device__ __forceinline__ void fence_proxy_async_global() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
+// Per-thread asynchronous 16-byte copy global -> shared (through L2, not L1), tracked by the
+// thread's commit groups; no proxy change: the copy reads and writes as the thread itself does.
+__device__ __forceinline__ void cp_async16(void *dst, const void *src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+// The entries gg = lane, lane + 32, ... < G of one row (V4<T> each) copied by the lane that reads them.
+template <class T> __device__ __forceinline__ void copy_row_own(V4<T> *dst, const V4<T> *src, int lane, int G)
+{
+    for (int gg = lane; gg < G; gg += 32) {
+#pragma unroll
+        for (int h = 0; h < (int)(sizeof(V4<T>) / 16); ++h)
+            cp_async16(reinterpret_cast<char *>(dst + gg) + 16 * h, reinterpret_cast<const char *>(src + gg) + 16 * h);
+    }
+}
 
 // Bounded wait on an mbarrier phase; false (and the error word set) after limit_ns.
 // Lane 0 adds the SM cycles it spent in the wait (try_wait may suspend the
@@ -790,23 +810,23 @@ __device__ __forceinline__ void solve_staged_cell(const SweepArgs<T> &A, const u
     }
 }
 
-// One task through the staged pipeline.  Stage of cell k = k mod NS; for each
-// stage two mbarriers (geometry+source, upwind rows) whose phase parities are
-// kept in `ph` (bit s: geometry barrier of stage s, bit 3+s: upwind barrier).
-// Each lane first reads the neighbour list of its cell(s) straight from the
-// records, so every copy of cell k (record, source row, upwind rows) is issued
-// together, NS - 1 cells ahead of the solve.  Returns false if a wait ran out
-// (error word set).
-// Spatial patches (A.intra): an upwind cell may be cell p < k of the same task;
-// the host marks each cell entry (A.aux, one byte).  If p was solved before
-// cell k's copies are issued (p <= k - NS), its row is copied like any other,
-// after every lane has ordered its own stores of that row before the copy (proxy
-// fence; the row is still in L2, so the copy costs no device-memory read);
-// otherwise the lanes write the entries of p's solution they computed into k's
-// upwind slot as they finish p (a lane reads back only what it wrote).
+// One task through the staged pipeline.  Stage of cell k = k mod NS holds its
+// cell record, its source row and its upwind rows (interior inflow faces in face
+// order).  The copies of cell k are issued NS - 1 cells ahead of its solve as
+// per-lane asynchronous 16-byte copies (cp.async): each lane copies the entries
+// of the rows it will itself read (groups lane, lane + 32, ...), lanes 0.. the
+// record that every lane reads; each issue is one commit group per lane, and a
+// solve first waits until its cell's group is complete (then the warp syncs, for
+// the record).  No copy goes through the bulk-copy unit, so no issue queues behind
+// another warp's copies.  Returns false if a wait ran out (error word set).
+// Spatial patches (A.intra): an upwind cell may be cell p < k of the same task; the
+// host marks each cell entry (A.aux, one byte).  If p was solved before cell k's
+// copies are issued (p <= k - NS), each lane copies its own entries of p's row back
+// (L2; the lane wrote them itself); otherwise the lanes write the entries of p's
+// solution they computed into k's upwind slot as they finish p.
 template <class T, int NPL, int NS = 3>
 __device__ __forceinline__ bool run_task_staged(const SweepArgs<T> &A, uint4 ti, int lane, T ox, T oy, T oz,
-                                                size_t psi_dir, unsigned char *wsm, uint64_t *bars, uint32_t &ph,
+                                                size_t psi_dir, unsigned char *wsm, uint64_t *, uint32_t &,
                                                 unsigned long long *wacc)
 {
     static_assert(NS == 2 || NS == 3, "two or three stages");
@@ -821,59 +841,52 @@ __device__ __forceinline__ bool run_task_staged(const SweepArgs<T> &A, uint4 ti,
     int4 n_lo = make_int4(-1, -1, -1, -1), n_hi = n_lo;
     if (lane < (int)ncell) n_lo = __ldg(reinterpret_cast<const int4 *>(A.geo[e_lo >> 4].nbr));
     if (lane + 32 < (int)ncell) n_hi = __ldg(reinterpret_cast<const int4 *>(A.geo[e_hi >> 4].nbr));
-    // psi rows written by other warps (generic proxy, acquired through the
-    // queue) are read here by the async proxy
-    if (lane == 0) fence_proxy_async_global();
-    // Copies of cell k into stage k mod NS, one per lane: lane 0 the record, lane 1 the
-    // source row, lanes 2.. the upwind rows (interior inflow faces in face order) that
-    // are not filled by the lanes.
+    constexpr int REC_CHUNKS = (int)(sizeof(CellGeo<T>) / 16);
     auto issue = [&](uint32_t k) {
         const int src = (int)(k & 31u);
         const bool hi = k >= 32u;
         const uint32_t ek = __shfl_sync(FULL, hi ? e_hi : e_lo, src);
         const uint32_t ak = intra ? __shfl_sync(FULL, hi ? a_hi : a_lo, src) : 0u;
-        int4 nb;
-        nb.x = __shfl_sync(FULL, hi ? n_hi.x : n_lo.x, src);
-        nb.y = __shfl_sync(FULL, hi ? n_hi.y : n_lo.y, src);
-        nb.z = __shfl_sync(FULL, hi ? n_hi.z : n_lo.z, src);
-        nb.w = __shfl_sync(FULL, hi ? n_hi.w : n_lo.w, src);
+        int nb[4];
+        nb[0] = __shfl_sync(FULL, hi ? n_hi.x : n_lo.x, src);
+        nb[1] = __shfl_sync(FULL, hi ? n_hi.y : n_lo.y, src);
+        nb[2] = __shfl_sync(FULL, hi ? n_hi.z : n_lo.z, src);
+        nb[3] = __shfl_sync(FULL, hi ? n_hi.w : n_lo.w, src);
         const uint32_t s = k % (uint32_t)NS, mask = ek & 15u, c = ek >> 4;
-        const uint32_t upm = (((mask & 1u) && nb.x >= 0) ? 1u : 0u) | (((mask & 2u) && nb.y >= 0) ? 2u : 0u) |
-                             (((mask & 4u) && nb.z >= 0) ? 4u : 0u) | (((mask & 8u) && nb.w >= 0) ? 8u : 0u);
-        const uint32_t n_up = __popc(upm);
-        const uint32_t copied = ((1u << n_up) - 1u) & ~(ak & 7u);  // upwind slots filled by a copy
         unsigned char *st = wsm + s * L.stage;
-        fence_proxy_async_shared();  // this lane's generic accesses of the stage (cell k - NS) before async writes
-        if (ak & 8u) fence_proxy_async_global();  // this lane's stores of the task's earlier rows before the copies
-        if (lane == 0) {
-            mbar_arrive_expect_tx(&bars[s], (uint32_t)sizeof(CellGeo<T>) + L.row);
-            mbar_arrive_expect_tx(&bars[3 + s], (uint32_t)__popc(copied) * L.row);
+        if (lane < REC_CHUNKS)
+            cp_async16(st + 16 * lane, reinterpret_cast<const char *>(A.geo + c) + 16 * lane);
+        copy_row_own<T>(reinterpret_cast<V4<T> *>(st + sizeof(CellGeo<T>)), A.q + (size_t)c * A.G, lane, A.G);
+        uint32_t r = 0;
+#pragma unroll
+        for (int f = 0; f < 4; ++f) {
+            if (!((mask >> f) & 1u) || nb[f] < 0) continue;
+            if (!((ak >> r) & 1u))  // not handed over by the lanes: copy this lane's entries of the row
+                copy_row_own<T>(reinterpret_cast<V4<T> *>(st + sizeof(CellGeo<T>) + (1u + r) * L.row),
+                                A.psi + (psi_dir + (size_t)nb[f]) * A.G, lane, A.G);
+            ++r;
         }
-        __syncwarp();
-        if (lane == 0) {
-            bulk_g2s(st, A.geo + c, (uint32_t)sizeof(CellGeo<T>), &bars[s]);
-        } else if (lane == 1) {
-            bulk_g2s(st + sizeof(CellGeo<T>), A.q + (size_t)c * A.G, L.row, &bars[s]);
-        } else if (lane < 2 + (int)n_up && ((copied >> (lane - 2)) & 1u)) {
-            uint32_t m = upm;
-            for (int r = 2; r < lane; ++r) m &= m - 1u;  // drop the faces of lanes 2 .. lane - 1
-            const int f = __ffs(m) - 1;
-            const int nbf = f == 0 ? nb.x : (f == 1 ? nb.y : (f == 2 ? nb.z : nb.w));
-            bulk_g2s(st + sizeof(CellGeo<T>) + (uint32_t)(lane - 1) * L.row, A.psi + (psi_dir + (size_t)nbf) * A.G,
-                     L.row, &bars[3 + s]);
-        }
+        cp_async_commit();
     };
     issue(0);
-    if (NS == 3 && ncell > 1) issue(1);
+    if (NS == 3) {
+        if (ncell > 1)
+            issue(1);
+        else
+            cp_async_commit();
+    }
     for (uint32_t k = 0; k < ncell; ++k) {
         const uint32_t s = k % (uint32_t)NS;
         const uint32_t ek = __shfl_sync(FULL, k < 32 ? e_lo : e_hi, k & 31);
         const uint32_t ak = intra ? __shfl_sync(FULL, k < 32 ? a_lo : a_hi, k & 31) : 0u;
-        if (k + NS - 1 < ncell) issue(k + NS - 1);
-        if (!mbar_wait(&bars[s], (ph >> s) & 1u, A.wait_limit_ns, &A.ctrl->error, wacc)) return false;
-        ph ^= 1u << s;
-        if (!mbar_wait(&bars[3 + s], (ph >> (3 + s)) & 1u, A.wait_limit_ns, &A.ctrl->error, wacc)) return false;
-        ph ^= 1u << (3 + s);
+        if (k + NS - 1 < ncell)
+            issue(k + NS - 1);
+        else
+            cp_async_commit();  // an empty group keeps NS - 1 groups behind this cell's
+        const long long c0 = clock64();
+        cp_async_wait<NS - 1>();
+        __syncwarp();  // the record, copied by lanes 0.., is read by every lane
+        if (lane == 0) *wacc += (unsigned long long)(clock64() - c0);
         // the upwind slots of the next cells (already issued) that take this cell's solution
         V4<T> *fill0 = nullptr, *fill1 = nullptr;
         if (ak & 0x30u)
@@ -883,7 +896,7 @@ __device__ __forceinline__ bool run_task_staged(const SweepArgs<T> &A, uint4 ti,
             fill1 = reinterpret_cast<V4<T> *>(wsm + ((k + 2) % (uint32_t)NS) * L.stage + sizeof(CellGeo<T>) +
                                               ((ak >> 6) & 3u) * L.row);
         solve_staged_cell<T, NPL>(A, wsm + s * L.stage, ek, lane, ox, oy, oz, psi_dir, L, fill0, fill1);
-        __syncwarp();
+        __syncwarp();  // every lane has read the stage's record before a later issue overwrites it
     }
     return true;
 }
@@ -1317,12 +1330,31 @@ __global__ void __launch_bounds__(128, MODE == 7 ? (sizeof(T) == 4 ? 3 : 2) : MO
                 ready = atom_add_acq_rel(A.counters + d, -1) == 1;
             }
             const unsigned rb = __ballot_sync(FULL, ready);
-            // the first (keep_max - nk) ready lanes push their task on the warp's stack
+            // the warp keeps (keep_max - nk) of the tasks it made ready, those with the longest
+            // chain of downwind tasks first, so a direction's critical path does not wait in the
+            // queue behind the other ready tasks; it queues the others
             const int room = A.keep_max - nk;
-            const int rank = __popc(rb & ((1u << lane) - 1u));
-            const bool kept = ready && rank < room;
-            if (kept) ks[nk + rank] = d;
-            nk += min(room, __popc(rb));
+            bool kept = false;
+            if (A.blevel) {
+                uint32_t key = ready ? ((uint32_t)min(__ldg(A.blevel + d), (1 << 25) - 1) << 6) | (uint32_t)(63 - lane)
+                                     : 0u;
+                const int take = min(room, __popc(rb));
+                for (int r = 0; r < take; ++r) {
+                    const uint32_t km = __reduce_max_sync(FULL, key);
+                    if (key == km) {
+                        kept = true;
+                        ks[nk + r] = d;
+                        key = 0u;
+                    }
+                }
+                nk += take;
+            } else {
+                // the first (keep_max - nk) ready lanes push their task on the warp's stack
+                const int rank = __popc(rb & ((1u << lane) - 1u));
+                kept = ready && rank < room;
+                if (kept) ks[nk + rank] = d;
+                nk += min(room, __popc(rb));
+            }
             if (ready && !kept) {
                 const unsigned long long slot = atomicAdd(&A.ctrl->tail, 1ull);
                 if (slot < A.n_tasks)
@@ -1380,6 +1412,17 @@ __global__ void __launch_bounds__(128, MODE == 7 ? (sizeof(T) == 4 ? 3 : 2) : MO
 }
 
 // ------------------------------------------------------------------ batched launch
+// The hexahedral tasks of a batch run through calls (not inlined), so that their register
+// demand does not raise the batched kernel's for the tetrahedral variants.
+template <class T>
+__device__ __noinline__ void batch_task_hex(const SweepArgs<T> &A, uint4 ti, int lane, T ox, T oy, T oz,
+                                            size_t psi_dir, unsigned char *wsm)
+{
+    if (A.mode == 9)
+        run_task_hex_shared(A, ti, lane, ox, oy, oz, psi_dir, wsm);
+    else
+        run_task_hex(A, ti, lane, ox, oy, oz, psi_dir);
+}
 // Several independent problems in one persistent launch: their tasks share one
 // ticket queue under global ids (problem k owns [offsets[k], offsets[k+1]));
 // each task runs with its own problem's arguments and kernel variant, and its
@@ -1395,7 +1438,8 @@ template <class T> struct BatchArgs {
     uint32_t warp_smem;
 };
 
-template <class T>
+// HEX: the batch holds hexahedral problems (their tasks run through batch_task_hex).
+template <class T, bool HEX>
 __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 3) sweep_batch_kernel(const BatchArgs<T> B)
 {
     const int lane = threadIdx.x & 31;
@@ -1487,10 +1531,12 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 3) sweep_batch_kerne
             if (A.mode == 3) ok = run_task_pairs(A, ti, lane, om.x, om.y, om.z, psi_dir, wsm, bars, ph, ws + 6);
             else if (A.mode == 2) ok = run_task_staged_any(A, ti, lane, om.x, om.y, om.z, psi_dir, wsm, bars, ph, ws + 6);
             else if (A.mode == 4) ok = run_task_staged_any<T, 2>(A, ti, lane, om.x, om.y, om.z, psi_dir, wsm, bars, ph, ws + 6);
+            else if (HEX && (A.mode == 9 || A.mode == 8)) batch_task_hex(A, ti, lane, om.x, om.y, om.z, psi_dir, wsm);
             else run_task_generic(A, ti, lane, om.x, om.y, om.z, psi_dir);
         } else {
             if (A.mode == 2) ok = run_task_staged_any(A, ti, lane, om.x, om.y, om.z, psi_dir, wsm, bars, ph, ws + 6);
             else if (A.mode == 4) ok = run_task_staged_any<T, 2>(A, ti, lane, om.x, om.y, om.z, psi_dir, wsm, bars, ph, ws + 6);
+            else if (HEX && (A.mode == 9 || A.mode == 8)) batch_task_hex(A, ti, lane, om.x, om.y, om.z, psi_dir, wsm);
             else run_task_generic(A, ti, lane, om.x, om.y, om.z, psi_dir);
         }
         if (!ok) break;
@@ -1505,7 +1551,17 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 3) sweep_batch_kerne
                 ready = atom_add_acq_rel(A.counters + d, -1) == 1;
             }
             const unsigned rb = __ballot_sync(FULL, ready);
-            const int kl = (e0 == 0 && rb) ? __ffs(rb) - 1 : -1;
+            // keep the ready task with the longest downwind chain (see sweep_kernel)
+            int kl = -1;
+            if (e0 == 0 && rb) {
+                if (A.blevel) {
+                    const uint32_t key = ready ? ((uint32_t)min(__ldg(A.blevel + d), (1 << 25) - 1) << 6) | (uint32_t)(63 - lane)
+                                               : 0u;
+                    kl = 63 - (int)(__reduce_max_sync(FULL, key) & 63u);
+                } else {
+                    kl = __ffs(rb) - 1;
+                }
+            }
             if (kl >= 0) keep = __shfl_sync(FULL, d - A.task_begin + base, kl);
             if (ready && (int)lane != kl) {
                 const unsigned long long slot = atomicAdd(&B.ctrl->tail, 1ull);

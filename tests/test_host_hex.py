@@ -71,9 +71,9 @@ def test_errors():
     m = tf.HexMesh(xyz, hexes)
     q = tf.Quadrature(2, 4)
     C = len(hexes)
-    with pytest.raises(tf.TfError) as e:  # hexahedra: no S1 (checked before any device work)
+    with pytest.raises(tf.TfError) as e:  # hexahedra: trilinear only (checked before any device work)
         tf.tf_problem_create(m.h, q.h, 1, 1, np.zeros(C, np.int32), np.ones((1, 1)), np.zeros((1, 1, 1)),
-                             np.zeros((C, 1, 8)), S1=np.zeros((C, 1, 3)))
+                             np.zeros((C, 1, 8)), S1=np.zeros((C, 1, 3)), opt=tf.options(order=2))
     assert e.value.status == tf.TF_ERR_ARG
 
 
