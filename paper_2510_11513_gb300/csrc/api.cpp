@@ -90,8 +90,10 @@ tf_status task_grain(const tf_options &o, const Mesh &m, int32_t n_groups, int32
         b = paired ? std::max(4, std::min(16, 256 / n_groups)) : std::max(2, std::min(64, 1024 / n_groups));
         // second order: a unit is a 10 x 10 solve, about 256 units per task
         if (o.order == 2) b = std::max(2, std::min(32, 256 / n_groups));
-        // third order: a unit is a 20 x 20 solve, about 64 units per task
-        if (o.order == 3) b = std::max(2, std::min(16, 64 / n_groups));
+        // third order: a unit is a 20 x 20 solve, about 32 units per task (a task's time sets the
+        // critical path: on the 16^3-hex box, 128 directions, 16 groups, 4 cells per task left the
+        // warps waiting a quarter of the sweep, 1 or 2 cells under 13 %)
+        if (o.order == 3) b = std::max(1, std::min(16, 32 / n_groups));
         // trilinear hexahedra: an 8 x 8 solve, about 256 units per task as the second order
         if (m.nf == 6) b = std::max(2, std::min(32, 256 / n_groups));
         // Bulk-synchronous schedules: a bucket's tasks must cover the resident warps, and

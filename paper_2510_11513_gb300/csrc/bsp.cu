@@ -84,7 +84,9 @@ __device__ __forceinline__ bool exec_task(const SweepArgs<T> &A, unsigned task, 
     } else if constexpr (MODE == 6) {
         return run_task_p2_staged(A, ti, lane, om.x, om.y, om.z, psi_dir, wsm, bars, ph, wacc);
     } else if constexpr (MODE == 7) {
-        run_task_p3(A, ti, lane, om.x, om.y, om.z, psi_dir, wsm);
+        extern __shared__ __align__(128) unsigned char dsm[];
+        run_task_p3(A, ti, lane, om.x, om.y, om.z, psi_dir, wsm,
+                    reinterpret_cast<const P3Dev<T> *>(dsm + (size_t)(blockDim.x >> 5) * A.warp_smem));
         return true;
     } else if constexpr (MODE == 8) {
         run_task_hex(A, ti, lane, om.x, om.y, om.z, psi_dir);
@@ -119,6 +121,10 @@ __global__ void __launch_bounds__(128, MODE == 7 ? (sizeof(T) == 4 ? 3 : 2) : MO
             fence_proxy_async_shared();
         }
         __syncwarp();
+    }
+    if constexpr (MODE == 7) {  // third order: the element tables after the warps' regions
+        p3_stage_tables<T>(A.p3tab, dsm + (size_t)(blockDim.x >> 5) * A.warp_smem);
+        __syncthreads();
     }
     __shared__ unsigned long long wstat[8][4];  // barrier wait ns, busy ns, tasks, data-wait cycles
     unsigned long long *ws = wstat[threadIdx.x >> 5];

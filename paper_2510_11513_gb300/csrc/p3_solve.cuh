@@ -1,19 +1,23 @@
-// Third-order (twenty-node) upwind-DG element on tetrahedra: cell record, device
-// element tables and the local solve of one (cell, direction, group) unit.
+// Third-order (twenty-node) upwind-DG element on tetrahedra: cell record, element tables
+// and the local solves of one (cell, direction) for all groups.
 // Included by sweep_kernel.cuh inside namespace tf, after the PTX helpers.
 //
 // Nodes: the four vertices, two per edge (0,1) (0,2) (0,3) (1,2) (1,3) (2,3) (first at
 // (lambda_a, lambda_b) = (2/3, 1/3)), the four face centres (face f opposite vertex f);
 // cubic Lagrange basis on that lattice.  Local system as for the lower orders:
-//   [ V sum_k w_k C_k + sigma_t V M + sum_{f inflow} |Omega.N_f| F_f ] psi
-//     = V M q + sum_{f inflow} |Omega.N_f| F_f psi_up,       w_k = Omega . grad lambda_k,
+//   [ W + sigma_t V M ] psi = V M q + sum_{f inflow} |Omega.N_f| F_f psi_up,
+//   W = V sum_k w_k C_k + sum_{f inflow} |Omega.N_f| F_f,   w_k = Omega . grad lambda_k,
 // with the exact tables of p3_tables.cpp (M, C_k per unit volume, F per unit area on the
-// face's ten nodes).  A 20 x 20 system does not fit one thread's registers, so four
-// lanes share a unit: lane s of the four holds rows 4 r + s (r = 0..4) of the matrix and
-// right-hand side in registers, the pivot row is broadcast inside the four with shuffles,
-// and every lane updates its own rows (Gaussian elimination without pivoting: the
-// symmetric part, (1/2) sum_f |Omega.N_f| F_f + sigma_t V M, is positive definite).
-// A warp solves eight units at a time.
+// face's ten nodes).  W depends on the cell and the direction only: the warp forms it once
+// per cell in shared memory, and each group's unit adds sigma_t V M.  A 20 x 20 system does
+// not fit one thread's registers, so four lanes share a unit: lane s of the four holds rows
+// 4 r + s (r = 0..4) of the matrix and right-hand side in registers; the four are lanes
+// u, u + 8, u + 16, u + 24 of the warp (unit u = 0..7), so that the eight lanes holding row k
+// form one quarter of the warp.  At step k they write the eight pivot rows to shared memory
+// (one wavefront per 16-byte store) and every lane reads its unit's row back (Gaussian elimination
+// without pivoting: the symmetric part, (1/2) sum_f |Omega.N_f| F_f + sigma_t V M, is
+// positive definite); the back substitution runs by columns, each unknown broadcast inside
+// the four.  A warp solves eight groups of one cell at a time.
 #pragma once
 
 template <class T> struct alignas(16) P3Geo {
@@ -25,14 +29,20 @@ template <class T> struct alignas(16) P3Geo {
     unsigned long long fmap[4];  // face f, face node r (0..9): the neighbour's local node, 5 bits at bit 5 r
 };
 
-template <class T> struct P3Dev {
-    T M[400];           // int phi_i phi_j / V, row-major
-    T C[4][400];        // int phi_i d phi_j / d lambda_k / V
-    T F[100];           // int_f phi_r phi_c / A_f on a face's ten nodes (the same for every face)
-    int32_t fn[4][10];  // the ten nodes of the face opposite vertex f
-    T FA[4][400];       // F of face f placed in the 20 x 20 matrix (zero off the face's nodes)
-    T FU[4][200];       // [f][i][c]: F(r, c) for the row i = fn[f][r] of the face, zero elsewhere
+// Element tables as the kernel holds them in shared memory (copied once per CTA).
+template <class T> struct alignas(16) P3Dev {
+    T M[400];          // int phi_i phi_j / V, row-major
+    T C[4][400];       // int phi_i d phi_j / d lambda_k / V
+    T FA[4][400];      // F of face f placed in the 20 x 20 matrix (zero off the face's nodes)
+    T FU[4][20][12];   // [f][i][c]: F(r, c) for the row i = fn[f][r] of the face, zero elsewhere (c >= 10: 0)
 };
+static_assert(sizeof(P3Dev<float>) % 16 == 0 && sizeof(P3Dev<double>) % 16 == 0, "tables are copied in 16 B pieces");
+
+// per-warp shared memory of the third-order kernel: the cell's W and two pivot-row buffers of
+// eight units (row and right-hand side; a stride of 28 values puts the eight units' 16-byte
+// pieces in distinct banks)
+constexpr int P3_PSTRIDE = 28;
+template <class T> constexpr uint32_t p3_warp_bytes() { return (uint32_t)((400 + 2 * 8 * P3_PSTRIDE) * sizeof(T)); }
 
 // lattice index of node i in coordinate k (compile-time structure of the element)
 __host__ __device__ constexpr int p3_alpha(int i, int k)
@@ -59,126 +69,209 @@ __host__ __device__ constexpr int p3_face_node(int f, int r)
 }
 
 
-// One unit on four lanes: sub = lane & 3 (rows 4 r + sub), the unit's cell entry e and group g.
+// Copies the element tables into the CTA's shared memory (all threads; the caller synchronises).
+template <class T> __device__ __forceinline__ void p3_stage_tables(const void *src, unsigned char *dst)
+{
+    const uint4 *s = reinterpret_cast<const uint4 *>(src);
+    uint4 *d = reinterpret_cast<uint4 *>(dst);
+    for (int i = threadIdx.x; i < (int)(sizeof(P3Dev<T>) / 16); i += blockDim.x) d[i] = __ldg(s + i);
+}
+
+// four consecutive values of a row in shared memory (16-byte aligned)
+template <class T> struct P3Vec;
+template <> struct P3Vec<float> {
+    float v[4];
+    __device__ __forceinline__ void load(const float *p)
+    {
+        const float4 t = *reinterpret_cast<const float4 *>(p);
+        v[0] = t.x, v[1] = t.y, v[2] = t.z, v[3] = t.w;
+    }
+    __device__ __forceinline__ void store(float *p) const { *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]); }
+};
+template <> struct P3Vec<double> {
+    double v[4];
+    __device__ __forceinline__ void load(const double *p)
+    {
+        const double2 a = reinterpret_cast<const double2 *>(p)[0], b = reinterpret_cast<const double2 *>(p)[1];
+        v[0] = a.x, v[1] = a.y, v[2] = b.x, v[3] = b.y;
+    }
+    __device__ __forceinline__ void store(double *p) const
+    {
+        reinterpret_cast<double2 *>(p)[0] = make_double2(v[0], v[1]);
+        reinterpret_cast<double2 *>(p)[1] = make_double2(v[2], v[3]);
+    }
+};
+
+// A task: per cell, W in shared memory, then the cell's groups eight at a time, four lanes per
+// unit.  tb: the element tables in shared memory; wsm: this warp's region (p3_warp_bytes).
 template <class T>
-__device__ __forceinline__ void p3_unit4(const SweepArgs<T> &A, const P3Geo<T> *__restrict__ geo,
-                                         const P3Dev<T> *__restrict__ tb, int sub, bool live, uint32_t e, int g,
-                                         T ox, T oy, T oz, size_t psi_dir)
+__device__ __forceinline__ void run_task_p3(const SweepArgs<T> &A, uint4 ti, int lane, T ox, T oy, T oz, size_t psi_dir,
+                                            unsigned char *wsm, const P3Dev<T> *tb)
 {
     const unsigned FULL = 0xffffffffu;
+    const P3Geo<T> *geo = reinterpret_cast<const P3Geo<T> *>(A.geo2);
+    T *Wc = reinterpret_cast<T *>(wsm);  // [20][20]
+    T *piv = Wc + 400;                   // [2][8][P3_PSTRIDE]: pivot row (20) and right-hand side (at 20) per unit
     const int G = A.G;
-    const uint32_t c = e >> 4, mask = e & 15u;
-    const P3Geo<T> &cg = geo[c];
-    T w[4];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) w[k] = ox * cg.gl[3 * k] + oy * cg.gl[3 * k + 1] + oz * cg.gl[3 * k + 2];
-    const T V = cg.vol;
-    const T sig = live ? __ldg(A.sigma_t + (size_t)cg.mat * G + g) : T(1);
-    const T *qc = reinterpret_cast<const T *>(A.q) + (size_t)c * 20 * G + g;
-    T q[20];
-#pragma unroll
-    for (int j = 0; j < 20; ++j) q[j] = live ? __ldg(qc + (size_t)j * G) : T(0);
-    // rows 4 r + sub: A = V (sigma_t M + sum_k w_k C_k); C_k(i, j) vanishes unless node j's
-    // lattice index has k, so each entry takes one to three streaming terms
-    T a[5][20], b[5];
-#pragma unroll
-    for (int r = 0; r < 5; ++r) {
-        const int i = 4 * r + sub;
-        T bi = T(0);
-#pragma unroll
-        for (int j = 0; j < 20; ++j) {
-            const T m = __ldg(&tb->M[20 * i + j]);
-            T kij = T(0);
-#pragma unroll
-            for (int k = 0; k < 4; ++k)
-                if (p3_alpha(j, k) > 0) kij += w[k] * __ldg(&tb->C[k][20 * i + j]);
-            a[r][j] = V * (sig * m + kij);
-            bi += m * q[j];
-        }
-        b[r] = V * bi;
-    }
+    const uint32_t ncell = ti.y & 0xffffu;
+    const int slot = lane & 7, sub = lane >> 3;
     T *psi = reinterpret_cast<T *>(A.psi);
-    // inflow faces (one loop body for all four, to keep the kernel's code small): the face
-    // matrices come expanded to the lane's rows from the tables
+    for (uint32_t kc = 0; kc < ncell; ++kc) {
+        const uint32_t e = __ldg(A.cells + ti.x + kc);
+        const uint32_t c = e >> 4, mask = e & 15u;
+        const P3Geo<T> *cg = geo + c;
+        const T V = __ldg(&cg->vol);
+        __syncwarp();  // the previous cell's units are done with Wc
+        {
+            T wv[4], sf[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                wv[k] = V * (ox * __ldg(&cg->gl[3 * k]) + oy * __ldg(&cg->gl[3 * k + 1]) + oz * __ldg(&cg->gl[3 * k + 2]));
+                const T sn = ox * __ldg(&cg->nrm[3 * k]) + oy * __ldg(&cg->nrm[3 * k + 1]) + oz * __ldg(&cg->nrm[3 * k + 2]);
+                sf[k] = ((mask >> k) & 1u) ? fabs(sn) : T(0);
+            }
+            for (int q4 = lane; q4 < 100; q4 += 32) {
+                P3Vec<T> out, t;
+#pragma unroll
+                for (int l = 0; l < 4; ++l) out.v[l] = T(0);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    t.load(&tb->C[k][4 * q4]);
+#pragma unroll
+                    for (int l = 0; l < 4; ++l) out.v[l] += wv[k] * t.v[l];
+                    t.load(&tb->FA[k][4 * q4]);
+#pragma unroll
+                    for (int l = 0; l < 4; ++l) out.v[l] += sf[k] * t.v[l];
+                }
+                out.store(Wc + 4 * q4);
+            }
+        }
+        __syncwarp();
+        const int32_t mat = __ldg(&cg->mat);
+        for (int g0 = 0; g0 < G; g0 += 8) {
+            const bool live = g0 + slot < G;
+            const int g = live ? g0 + slot : g0;  // an idle slot repeats a live group and discards it
+            const T sv = V * __ldg(A.sigma_t + (size_t)mat * G + g);
+            const T *qc = reinterpret_cast<const T *>(A.q) + (size_t)c * 20 * G + g;
+            // upwind faces first: b = sum_f s_f F_f psi_up on the face's rows (one loop body for the four faces)
+            T b[5], q[20];
+#pragma unroll
+            for (int j = 0; j < 20; ++j) q[j] = __ldg(qc + (size_t)j * G);
+#pragma unroll
+            for (int r = 0; r < 5; ++r) b[r] = T(0);
 #pragma unroll 1
-    for (int f = 0; f < 4; ++f) {
-        if (!((mask >> f) & 1u)) continue;
-        const T s = fabs(ox * cg.nrm[3 * f] + oy * cg.nrm[3 * f + 1] + oz * cg.nrm[3 * f + 2]);
-        const int n = cg.nbr[f];
-        T up[10];
-        if (n >= 0 && live) {
-            const unsigned long long fm = cg.fmap[f];
+            for (int f = 0; f < 4; ++f) {
+                const int32_t n = __ldg(&cg->nbr[f]);
+                if (!((mask >> f) & 1u) || n < 0) continue;  // vacuum boundary: no inflow
+                const T s_f = fabs(ox * __ldg(&cg->nrm[3 * f]) + oy * __ldg(&cg->nrm[3 * f + 1]) + oz * __ldg(&cg->nrm[3 * f + 2]));
+                const unsigned long long fm = __ldg(&cg->fmap[f]);
+                const T *un = psi + (psi_dir + (size_t)n) * 20 * (size_t)G + g;
+                T up[12];
 #pragma unroll
-            for (int k = 0; k < 10; ++k)
-                up[k] = __ldcg(psi + ((psi_dir + (size_t)n) * 20 + ((uint32_t)(fm >> (5 * k)) & 31u)) * G + g);
-        } else {
+                for (int kk = 0; kk < 10; ++kk) up[kk] = __ldcg(un + (size_t)((uint32_t)(fm >> (5 * kk)) & 31u) * G);
+                up[10] = up[11] = T(0);
 #pragma unroll
-            for (int k = 0; k < 10; ++k) up[k] = T(0);  // vacuum boundary: no inflow
+                for (int r = 0; r < 5; ++r) {
+                    const T *fu = &tb->FU[f][4 * r + sub][0];
+                    T t = T(0);
+#pragma unroll
+                    for (int c4 = 0; c4 < 3; ++c4) {
+                        P3Vec<T> v;
+                        v.load(fu + 4 * c4);
+#pragma unroll
+                        for (int l = 0; l < 4; ++l) t += v.v[l] * up[4 * c4 + l];
+                    }
+                    b[r] += s_f * t;
+                }
+            }
+            __syncwarp();  // keeps the loads below from being hoisted into the face loop (register pressure)
+            // A = W + sigma_t V M and b = V M q in one pass over the lane's rows of W and M
+            T a[5][20];
+            {
+#pragma unroll
+                for (int r = 0; r < 5; ++r) {
+                    const T *wr = Wc + 20 * (4 * r + sub);
+                    const T *mr = &tb->M[20 * (4 * r + sub)];
+                    T bi = T(0);
+#pragma unroll
+                    for (int j4 = 0; j4 < 5; ++j4) {
+                        P3Vec<T> w, m;
+                        w.load(wr + 4 * j4);
+                        m.load(mr + 4 * j4);
+#pragma unroll
+                        for (int t = 0; t < 4; ++t) {
+                            a[r][4 * j4 + t] = w.v[t] + sv * m.v[t];
+                            bi += m.v[t] * q[4 * j4 + t];
+                        }
+                    }
+                    b[r] += V * bi;
+                }
+            }
+            // elimination: row k lives in lane (k & 3) of the four, register row k >> 2
+#pragma unroll
+            for (int k = 0; k < 20; ++k) {
+                const int owner = k & 3, rk = k >> 2, j0 = k & ~3;
+                T *pr = piv + (k & 1) * 8 * P3_PSTRIDE + slot * P3_PSTRIDE;
+                if (sub == owner) {
+#pragma unroll
+                    for (int j = j0; j < 20; j += 4) {
+                        P3Vec<T> v;
+#pragma unroll
+                        for (int l = 0; l < 4; ++l) v.v[l] = a[rk][j + l];
+                        v.store(pr + j);
+                    }
+                    pr[20] = b[rk];
+                }
+                __syncwarp();
+                // the pivot row four columns at a time: first the piece holding the pivot
+                P3Vec<T> v;
+                v.load(pr + j0);
+                const T rp = rcp(v.v[k - j0]);
+                const T pb = pr[20];
+                T l[5];
+#pragma unroll
+                for (int r = 0; r < 5; ++r) l[r] = a[r][k] * rp;
+                if (sub == owner) a[rk][k] = rp;  // the owner keeps the reciprocal for the back substitution
+#pragma unroll
+                for (int j = j0; j < 20; j += 4) {
+                    if (j > j0) v.load(pr + j);
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) {
+                        if (j + t <= k) continue;
+#pragma unroll
+                        for (int r = 0; r < 5; ++r) {
+                            if (4 * r + 3 <= k) continue;                  // rows of this slot are all at or above k
+                            if (4 * r <= k && 4 * r + sub <= k) continue;  // this lane's row is at or above k
+                            a[r][j + t] -= l[r] * v.v[t];
+                        }
+                    }
+                }
+#pragma unroll
+                for (int r = 0; r < 5; ++r) {
+                    if (4 * r + 3 <= k) continue;
+                    if (4 * r <= k && 4 * r + sub <= k) continue;
+                    b[r] -= l[r] * pb;
+                }
+            }
+            // back substitution by columns: x_i from its owner, then removed from the rows above
+#pragma unroll
+            for (int i = 19; i >= 0; --i) {
+                const int owner = i & 3, ri = i >> 2;
+                const T xi = __shfl_sync(FULL, b[ri] * a[ri][i], 8 * owner + slot);
+                if (sub == owner) b[ri] = xi;
+#pragma unroll
+                for (int r = 0; r < 5; ++r) {
+                    if (4 * r >= i) continue;                          // no row of this slot is above i
+                    if (4 * r + 3 >= i && 4 * r + sub >= i) continue;  // this lane's row is not above i
+                    b[r] -= a[r][i] * xi;
+                }
+            }
+            if (live) {
+                T *out = psi + (psi_dir + c) * 20 * (size_t)G + g;
+#pragma unroll
+                for (int r = 0; r < 5; ++r) out[(size_t)(4 * r + sub) * G] = b[r];
+            }
         }
-#pragma unroll
-        for (int r = 0; r < 5; ++r) {
-            const int i = 4 * r + sub;
-            const T *fa = &tb->FA[f][20 * i];
-            const T *fu = &tb->FU[f][10 * i];
-#pragma unroll
-            for (int j = 0; j < 20; ++j) a[r][j] += s * __ldg(fa + j);
-            T t = T(0);
-#pragma unroll
-            for (int cc = 0; cc < 10; ++cc) t += __ldg(fu + cc) * up[cc];
-            b[r] += s * t;
-        }
-    }
-    // elimination: the pivot row k lives in lane (k & 3) of the four, local row k >> 2
-    T x[20];
-#pragma unroll
-    for (int k = 0; k < 20; ++k) {
-        const int owner = k & 3, rk = k >> 2;
-        T pv[20];
-#pragma unroll
-        for (int j = k; j < 20; ++j) pv[j] = __shfl_sync(FULL, a[rk][j], owner, 4);
-        const T pb = __shfl_sync(FULL, b[rk], owner, 4);
-        const T rp = rcp(pv[k]);
-        if (sub == owner) a[rk][k] = rp;  // the owner keeps the reciprocal for the back substitution
-#pragma unroll
-        for (int r = 0; r < 5; ++r) {
-            if (4 * r + sub <= k) continue;  // rows at or above the pivot are finished
-            const T l = a[r][k] * rp;
-#pragma unroll
-            for (int j = k + 1; j < 20; ++j) a[r][j] -= l * pv[j];
-            b[r] -= l * pb;
-        }
-    }
-#pragma unroll
-    for (int i = 19; i >= 0; --i) {
-        const int owner = i & 3, ri = i >> 2;
-        T s = b[ri];
-#pragma unroll
-        for (int j = i + 1; j < 20; ++j) s -= a[ri][j] * x[j];
-        x[i] = __shfl_sync(FULL, s * a[ri][i], owner, 4);
-    }
-    if (live) {
-        T *out = psi + (psi_dir + c) * 20 * (size_t)G + g;
-#pragma unroll
-        for (int r = 0; r < 5; ++r) out[(size_t)(4 * r + sub) * G] = x[4 * r + sub];
     }
 }
 
-// A task: the warp takes its (cell, group) units eight at a time, four lanes per unit.
-template <class T>
-__device__ __forceinline__ void run_task_p3(const SweepArgs<T> &A, uint4 ti, int lane, T ox, T oy, T oz, size_t psi_dir,
-                                            unsigned char *)
-{
-    const P3Geo<T> *geo = reinterpret_cast<const P3Geo<T> *>(A.geo2);
-    const P3Dev<T> *tb = reinterpret_cast<const P3Dev<T> *>(A.p3tab);
-    const uint32_t ncell = ti.y & 0xffffu;
-    const uint32_t nu = ncell * (uint32_t)A.G;
-    const int slot = lane >> 2, sub = lane & 3;
-    for (uint32_t u0 = 0; u0 < nu; u0 += 8) {
-        const uint32_t u = u0 + (uint32_t)slot;
-        const bool live = u < nu;
-        const uint32_t uu = live ? u : u0;  // an idle slot repeats a live unit's cell and discards it
-        const uint32_t k = uu / (uint32_t)A.G;
-        const int g = (int)(uu - k * (uint32_t)A.G);
-        p3_unit4(A, geo, tb, sub, live, __ldg(A.cells + ti.x + k), g, ox, oy, oz, psi_dir);
-    }
-}

@@ -720,6 +720,7 @@ struct DeviceState {
     int lpc_shift = 0, ppl = 0;
     int mode = 0;  // sweep kernel variant (see sweep_kernel)
     uint32_t warp_smem = 0;
+    uint32_t cta_smem = 0;   // shared memory of the whole CTA after the warps' regions (third-order tables)
     // bulk-synchronous schedules: task ids grouped by (octant, t-level) bucket, per chunk
     int schedule = TF_SCHED_AMT;
     uint32_t *bsp_order = nullptr;
@@ -1116,16 +1117,14 @@ template <class T> tf_status create_typed_p3(Problem &p, DeviceState &d, const i
             dt.M[e] = (T)tab.M[e];
             for (int k = 0; k < 4; ++k) dt.C[k][e] = (T)tab.C[k][e];
         }
-        for (int e = 0; e < 100; ++e) dt.F[e] = (T)tab.F[0][e];
-        for (int f = 0; f < 4; ++f)
-            for (int r = 0; r < 10; ++r) dt.fn[f][r] = tab.fn[f][r];
         for (int f = 0; f < 4; ++f) {
             for (int e = 0; e < 400; ++e) dt.FA[f][e] = T(0);
-            for (int e = 0; e < 200; ++e) dt.FU[f][e] = T(0);
+            for (int i = 0; i < 20; ++i)
+                for (int c = 0; c < 12; ++c) dt.FU[f][i][c] = T(0);
             for (int r = 0; r < 10; ++r)
                 for (int c = 0; c < 10; ++c) {
                     dt.FA[f][20 * tab.fn[f][r] + tab.fn[f][c]] = (T)tab.F[f][10 * r + c];
-                    dt.FU[f][10 * tab.fn[f][r] + c] = (T)tab.F[f][10 * r + c];
+                    dt.FU[f][tab.fn[f][r]][c] = (T)tab.F[f][10 * r + c];
                 }
         }
         P3Dev<T> *tp = nullptr;
@@ -1407,7 +1406,11 @@ tf_status device_create(Problem &p, const int32_t *cell_material, const double *
     const bool p2_staged = d.order == 2 && !d.fp64 && d.G % 32 == 0 && g.cells_per_task <= 32 && p.opt.staging != 1 &&
                            ((p2_stage_bytes(d.G) * 2 + 48 + 127) / 128 * 128) * d.wpc <= 227 * 1024;
     if (p2_staged) d.warp_smem = (p2_stage_bytes(d.G) * 2 + 48 + 127) / 128 * 128;
-    if (d.order == 3) d.warp_smem = 0;  // four lanes per unit, systems in registers
+    // third order: per warp the cell's group-independent matrix and the pivot rows, per CTA the tables
+    if (d.order == 3) {
+        d.warp_smem = ((d.fp64 ? p3_warp_bytes<double>() : p3_warp_bytes<float>()) + 127u) / 128u * 128u;
+        d.cta_smem = d.fp64 ? sizeof(P3Dev<double>) : sizeof(P3Dev<float>);
+    }
     // hexahedra: the group-independent matrices in shared memory once per cell when a batch of
     // 32 units touches at most five cells (G >= 8); staging = 1 keeps every lane on its own
     const bool hex_shared = d.hex && d.G >= 8 && p.opt.staging != 1;
@@ -1501,7 +1504,7 @@ tf_status device_create(Problem &p, const int32_t *cell_material, const double *
                                        : (d.fp64 ? (const void *)source_ho_kernel<double, 10> : (const void *)source_ho_kernel<float, 10>);
         if (smem2 > 48 * 1024) TF_CUDA(ensure_dyn_smem(sfn, (int)smem2));
     }
-    const int dyn = (int)(d.warp_smem * d.wpc);
+    const int dyn = (int)(d.warp_smem * d.wpc + d.cta_smem);
     const void *kfn = d.mode == 9   ? (d.fp64 ? (const void *)sweep_kernel<double, 9> : (const void *)sweep_kernel<float, 9>)
                       : d.mode == 8 ? (d.fp64 ? (const void *)sweep_kernel<double, 8> : (const void *)sweep_kernel<float, 8>)
                       : d.mode == 7 ? (d.fp64 ? (const void *)sweep_kernel<double, 7> : (const void *)sweep_kernel<float, 7>)
@@ -1821,7 +1824,7 @@ template <class T> tf_status launch_step(Problem &p, const double *phi_in, doubl
             TF_CUDA(cudaMemsetAsync(d.bsp_bar, 0, sizeof(unsigned int), st));
             const SweepArgs<T> A = make_args<T>(p, k);
             BspArgs S{d.bsp_order, d.bsp_bucket, d.counters, d.bsp_bar, b0, b1, p.opt.inject_stall ? 1 : 0};
-            const size_t dyn = (size_t)d.warp_smem * d.wpc;
+            const size_t dyn = (size_t)d.warp_smem * d.wpc + d.cta_smem;
             TF_CUDA(record_event(d.ev_start[1 + 2 * k], st));
             if (d.schedule == TF_SCHED_BSP) {
                 TF_CUDA(launch_bsp<T>(A, S, d.mode, d.bsp_grid, 32 * d.wpc, dyn, true, st));
@@ -1856,7 +1859,7 @@ template <class T> tf_status launch_step(Problem &p, const double *phi_in, doubl
                                         d.group_total + gb, ng);
         const SweepArgs<T> A = make_args<T>(p, k);
         TF_CUDA(record_event(d.ev_start[1 + 2 * k], st));
-        const size_t dyn = (size_t)d.warp_smem * d.wpc;
+        const size_t dyn = (size_t)d.warp_smem * d.wpc + d.cta_smem;
         if constexpr (sizeof(T) == 4) {
             if (d.mode == 3) sweep_kernel<T, 3><<<d.grid, 32 * d.wpc, dyn, st>>>(A);
             if (d.mode == 4) sweep_kernel<T, 4><<<d.grid, 32 * d.wpc, dyn, st>>>(A);

@@ -1197,7 +1197,8 @@ __device__ __forceinline__ bool run_task_staged_any(const SweepArgs<T> &A, uint4
 // 4 = as 2 with two stages and six resident CTAs per SM (FP32),
 // 5 = the second-order (ten-node) element, lanes over (cell, group) units,
 // 6 = the second-order element staged in shared memory (FP32, G a multiple of 32),
-// 7 = the third-order element, four lanes per unit with the system in registers,
+// 7 = the third-order element, four lanes per unit with the system in registers and the
+//     cell's group-independent matrix and the element tables in shared memory,
 // 8 = trilinear hexahedra, lanes over (cell, group) units,
 // 9 = trilinear hexahedra with the group-independent matrices formed once per cell in shared memory (G >= 8).
 template <class T, int MODE>
@@ -1218,6 +1219,12 @@ __global__ void __launch_bounds__(128, MODE == 7 ? (sizeof(T) == 4 ? 3 : 2) : MO
             fence_proxy_async_shared();
         }
         __syncwarp();
+    }
+    // third order: the element tables sit in shared memory after the warps' regions
+    const P3Dev<T> *p3s = reinterpret_cast<const P3Dev<T> *>(dsm + (size_t)(blockDim.x >> 5) * A.warp_smem);
+    if constexpr (MODE == 7) {
+        p3_stage_tables<T>(A.p3tab, dsm + (size_t)(blockDim.x >> 5) * A.warp_smem);
+        __syncthreads();
     }
     // per-warp counters live in shared memory (lane 0 updates them) to spare registers
     __shared__ unsigned long long wstat[8][7];  // polls, wait_ns, busy_ns, done, depth, pops, data-wait cycles
@@ -1310,7 +1317,7 @@ __global__ void __launch_bounds__(128, MODE == 7 ? (sizeof(T) == 4 ? 3 : 2) : MO
         } else if constexpr (MODE == 6) {
             if (!run_task_p2_staged(A, ti, lane, om.x, om.y, om.z, psi_dir, wsm, bars, ph, ws + 6)) break;
         } else if constexpr (MODE == 7) {
-            run_task_p3(A, ti, lane, om.x, om.y, om.z, psi_dir, wsm);
+            run_task_p3(A, ti, lane, om.x, om.y, om.z, psi_dir, wsm, p3s);
         } else if constexpr (MODE == 8) {
             run_task_hex(A, ti, lane, om.x, om.y, om.z, psi_dir);
         } else if constexpr (MODE == 9) {

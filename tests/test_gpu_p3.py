@@ -32,7 +32,8 @@ def _box(n, G, seed=5, two_material=False):
 
 
 @pytest.mark.parametrize("precision", [tf.TF_FP64, tf.TF_FP32])
-@pytest.mark.parametrize("G,opts", [(1, {}), (3, dict(cells_per_task=5)), (32, {}), (7, dict(dir_chunk=5))])
+@pytest.mark.parametrize("G,opts", [(1, {}), (3, dict(cells_per_task=5)), (32, {}), (7, dict(dir_chunk=5)), (16, {}),
+                                    (9, dict(cells_per_task=3))])
 def test_one_sweep_matches_oracle(precision, G, opts):
     cfg = _box(n=3, G=G)
     P = o3.Problem3(cfg)
