@@ -674,7 +674,7 @@ def run_batch(args):
 
 
 def learned_leg(tf, torch, kw, train_layouts, eval_layouts, eval_fp64, epochs, batch, lr, seed, tol,
-                weight_floor=None, overshoot_weight=1.0, shrink=1.0, context=None, sample_cells=0):
+                weight_floor=None, overshoot_weight=1.0, shrink=1.0, context=None, sample_cells=0, gen_batch=1):
     """Learned initial flux on the learned-start layouts: converged fluxes of `train_layouts`
     layouts from the plain FP32 solver, the network trained by the library's kernels, then
     `eval_layouts` held-out layouts solved from zero and from the learned start to the same
@@ -683,10 +683,11 @@ def learned_leg(tf, torch, kw, train_layouts, eval_layouts, eval_fp64, epochs, b
 
     dev = torch.device("cuda", torch.cuda.current_device())
     t0 = time.perf_counter()
-    train = [W.random_layout(layout=k, **kw) for k in range(train_layouts)]
+    train = (W.random_layout(layout=k, **kw) for k in range(train_layouts))  # built as consumed
     context = L.CONTEXT_STEPS if context is None else tuple(context)
     X, T, Wt, gen = L.generate(train, tol=tol, max_iters=5000, device=dev, weight_floor=weight_floor,
-                               context=context, sample_cells=sample_cells, seed=seed, precision=tf.TF_FP32)
+                               context=context, sample_cells=sample_cells, seed=seed, batch=gen_batch,
+                               precision=tf.TF_FP32)
     t_gen = time.perf_counter() - t0
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
@@ -739,8 +740,12 @@ def learned_leg(tf, torch, kw, train_layouts, eval_layouts, eval_fp64, epochs, b
             "s_learned": sum(r["s_learned"] for r in rows) / len(rows),
             "s_zero": sum(r["s_zero"] for r in rows) / len(rows),
             "iterations_zero": iz, "iterations_learned": il, "iteration_ratio": il / max(iz, 1),
+            "start_rel_l2_err_mean": sum(r["start_rel_l2_err"] for r in rows) / len(rows),
             "generate_s": round(t_gen, 1), "generate_solve_s": round(sum(g["solve_seconds"] for g in gen), 2),
-            "generate_iterations": [g["iterations"] for g in gen], "train_s": round(t_train, 2),
+            "generate_iterations": ([g["iterations"] for g in gen] if len(gen) <= 64 else
+                                    {"mean": sum(g["iterations"] for g in gen) / len(gen),
+                                     "min": min(g["iterations"] for g in gen), "max": max(g["iterations"] for g in gen)}),
+            "train_s": round(t_train, 2),
             "loss_history": [round(float(h), 5) for h in hist], "per_layout": rows}
 
 
@@ -757,7 +762,7 @@ def run_learned(args):
                                              tuple(int(x) for x in args.context.split(",")))
     r = learned_leg(tf, torch, kw, args.train_layouts, args.eval_layouts, args.eval_fp64, args.epochs,
                     args.train_batch, args.lr, args.seed, args.batch_tol, floor, args.overshoot_weight, args.shrink,
-                    context=ctx, sample_cells=args.sample_cells)
+                    context=ctx, sample_cells=args.sample_cells, gen_batch=args.gen_batch)
     line = {"metric": "time to 1e-6 per layout, learned start (zero-start alongside)", "value": r["s_learned"],
             "unit": "s", "n_gpus": 1, "steps": r["eval_layouts"], "warmup": 0, "ms_per_step": 1e3 * r["s_learned"],
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32+bf16",
@@ -766,7 +771,8 @@ def run_learned(args):
                                          "lr", "tol", "weight_floor", "overshoot_weight", "shrink", "context_steps",
                                          "sample_cells")},
             **{k: r[k] for k in ("iterations_zero", "iterations_learned", "iteration_ratio", "generate_s",
-                                 "generate_solve_s", "generate_iterations", "train_s", "loss_history", "per_layout")},
+                                 "generate_solve_s", "generate_iterations", "train_s", "loss_history",
+                                 "start_rel_l2_err_mean", "per_layout")},
             "zero_start_s": r["s_zero"]}
     print(json.dumps(line), flush=True)
 
@@ -823,6 +829,8 @@ def main():
     ap.add_argument("--context", default="default",
                     help="--config layout: context steps of the inputs ('default', 'none' = one ring, or e.g. 4,16,64)")
     ap.add_argument("--sample-cells", type=int, default=0, help="--config layout: training cells kept per layout (0 = all)")
+    ap.add_argument("--gen-batch", type=int, default=1,
+                    help="--config layout: training layouts solved together in shared launches")
     ap.add_argument("--overshoot-weight", type=float, default=1.0,
                     help="--config layout: loss weight of overshooting outputs (1 = plain squared error)")
     args = ap.parse_args()

@@ -11,6 +11,8 @@ are torch CUDA tensors.
 """
 from __future__ import annotations
 
+import queue
+import threading
 import time
 
 import numpy as np
@@ -66,40 +68,82 @@ def flux_weights(phi: torch.Tensor, n_groups: int, floor: float, stream=None) ->
     return W
 
 
+def _prefetched(items, depth):
+    """The items of an iterable, produced `depth` ahead by a background thread (configurations
+    are built with numpy while the GPU solves the previous ones)."""
+    q = queue.Queue(maxsize=max(1, depth))
+    end = object()
+
+    def produce():
+        try:
+            for it in items:
+                q.put(it)
+        except BaseException as e:  # noqa: BLE001  re-raised in the consumer
+            q.put(e)
+        q.put(end)
+
+    t = threading.Thread(target=produce, daemon=True)
+    t.start()
+    while True:
+        it = q.get()
+        if it is end:
+            break
+        if isinstance(it, BaseException):
+            raise it
+        yield it
+    t.join()
+
+
 def generate(cfgs, tol=1e-6, max_iters=5000, device="cuda", weight_floor=None, context=CONTEXT_STEPS,
-             sample_cells=0, seed=0, **solver_opts):
-    """Training data from the plain solver: for each problem configuration, its
-    features and the targets of its converged zero-start solution, and with
-    `weight_floor` the loss weights of each problem's flux.  sample_cells > 0 keeps a
-    seeded random subset of that many cells per problem (many layouts in bounded memory).
+             sample_cells=0, seed=0, batch=1, **solver_opts):
+    """Training data from the plain solver: for each problem configuration (any iterable; it is
+    read by a background thread, `batch` ahead), its features and the targets of its converged
+    zero-start solution, and with `weight_floor` the loss weights of each problem's flux.
+    sample_cells > 0 keeps a seeded random subset of that many cells per problem (many layouts in
+    bounded memory); batch > 1 solves that many problems together in shared launches.
     Returns (X [samples][I], T [samples][G], W [samples][G] or None, per-problem info dicts)."""
     Xs, Ts, Ws, infos = [], [], [], []
     gen = torch.Generator(device="cpu")
     gen.manual_seed(int(seed))
-    for cfg in cfgs:
+    pending = []
+
+    def solve(chunk):
         t0 = time.perf_counter()
-        prob = tf.Problem.from_config(cfg, **solver_opts)
-        t_setup = time.perf_counter() - t0
-        X = cell_features(prob.mesh, cfg, device, context=context)
-        phi = torch.zeros((prob.n_cells, prob.n_groups, 4), dtype=torch.float64, device=device)
+        probs = [tf.Problem.from_config(c, **solver_opts) for c in chunk]
+        t_setup = (time.perf_counter() - t0) / len(chunk)
+        feats = [cell_features(p.mesh, c, device, context=context) for p, c in zip(probs, chunk)]
+        phis = [torch.zeros((p.n_cells, p.n_groups, 4), dtype=torch.float64, device=device) for p in probs]
         t0 = time.perf_counter()
-        r = prob.source_iterate(phi, tol, max_iters)
+        if len(probs) == 1:
+            rs = [probs[0].source_iterate(phis[0], tol, max_iters)]
+        else:
+            _, rs = tf.source_iterate_batch(probs, phis, tol, max_iters)
         torch.cuda.synchronize()
-        r["solve_seconds"] = time.perf_counter() - t0
-        r["setup_seconds"] = t_setup
-        r["name"] = cfg.get("name", "")
-        T = flux_targets(phi, prob.n_groups)
-        Wt = flux_weights(phi, prob.n_groups, weight_floor) if weight_floor is not None else None
-        if 0 < sample_cells < prob.n_cells:
-            keep = torch.randperm(prob.n_cells, generator=gen)[:sample_cells].to(device)
-            X, T = X[keep], T[keep]
-            Wt = Wt[keep] if Wt is not None else None
-        Xs.append(X)
-        Ts.append(T)
-        if Wt is not None:
-            Ws.append(Wt)
-        infos.append(r)
-        prob.close()
+        t_solve = (time.perf_counter() - t0) / len(probs)
+        for prob, c, X, phi, r in zip(probs, chunk, feats, phis, rs):
+            r["solve_seconds"] = t_solve
+            r["setup_seconds"] = t_setup
+            r["name"] = c.get("name", "")
+            T = flux_targets(phi, prob.n_groups)
+            Wt = flux_weights(phi, prob.n_groups, weight_floor) if weight_floor is not None else None
+            if 0 < sample_cells < prob.n_cells:
+                keep = torch.randperm(prob.n_cells, generator=gen)[:sample_cells].to(device)
+                X, T = X[keep], T[keep]
+                Wt = Wt[keep] if Wt is not None else None
+            Xs.append(X)
+            Ts.append(T)
+            if Wt is not None:
+                Ws.append(Wt)
+            infos.append(r)
+            prob.close()
+
+    for cfg in _prefetched(cfgs, 2 * max(1, int(batch))):
+        pending.append(cfg)
+        if len(pending) == max(1, int(batch)):
+            solve(pending)
+            pending = []
+    if pending:
+        solve(pending)
     return torch.cat(Xs), torch.cat(Ts), (torch.cat(Ws) if Ws else None), infos
 
 
