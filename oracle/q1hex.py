@@ -32,6 +32,7 @@ class _ProblemHex(C.Structure):
         ("face", C.c_void_p), ("nbar", C.c_void_p), ("nbr", C.c_void_p), ("nbr_node", C.c_void_p),
         ("omega", C.c_void_p), ("w", C.c_void_p), ("inflow", C.c_void_p), ("level", C.c_void_p),
         ("material", C.c_void_p), ("sigma_t", C.c_void_p), ("S1", C.c_void_p), ("psi_in", C.c_void_p),
+        ("lag", C.c_void_p), ("psi_prev", C.c_void_p),
     ]
 
 
@@ -44,6 +45,7 @@ def load(src=None):
         lib.orah_face_node.argtypes = [i32, i32]
         lib.orah_geometry.argtypes = [i64, vp, i64, vp, vp, vp, vp, vp, vp, vp, vp]
         lib.orah_graph.argtypes = [i64, vp, vp, i32, vp, vp, vp]
+        lib.orah_graph_lag.argtypes = [i64, vp, vp, i32, vp, vp, vp, vp]
         lib.orah_sweep_direction.argtypes = [C.POINTER(_ProblemHex), i32, vp, vp]
         lib.orah_sweep.argtypes = [C.POINTER(_ProblemHex), vp, i32, vp, vp, vp, i32, C.POINTER(C.c_int)]
         _libs[key] = lib
@@ -78,15 +80,22 @@ def geometry(xyz, hexes, lib=None):
     return g
 
 
-def graph(geom, omega, lib=None):
-    """Inflow-face bitmask [D][C] (uint8, six bits) and t-level [D][C] (int32)."""
+def graph(geom, omega, lib=None, lag=False):
+    """Inflow-face bitmask [D][C] (uint8, six bits) and t-level [D][C] (int32); with lag, also the
+    lagged back edges [D][C] (bit f: inflow face f reads the previous step's upwind psi), chosen
+    whenever no cell is ready as the open inflow faces of the lowest-numbered waiting cell."""
     lib = lib or load()
     omega = np.ascontiguousarray(omega, dtype=np.float64)
     D, nc = omega.shape[0], geom["vol"].shape[0]
     inflow = np.zeros((D, nc), dtype=np.uint8)
     level = np.zeros((D, nc), dtype=np.int32)
-    _check(lib.orah_graph(nc, _p(geom["nbr"]), _p(geom["nbar"]), D, _p(omega), _p(inflow), _p(level)), "graph")
-    return inflow, level
+    if not lag:
+        _check(lib.orah_graph(nc, _p(geom["nbr"]), _p(geom["nbar"]), D, _p(omega), _p(inflow), _p(level)), "graph")
+        return inflow, level
+    lagged = np.zeros((D, nc), dtype=np.uint8)
+    _check(lib.orah_graph_lag(nc, _p(geom["nbr"]), _p(geom["nbar"]), D, _p(omega), _p(inflow), _p(level),
+                              _p(lagged)), "graph_lag")
+    return inflow, level, lagged
 
 
 class ProblemHex:
@@ -94,7 +103,9 @@ class ProblemHex:
 
     NB = NB
 
-    def __init__(self, cfg, omega=None, w=None, S1=None, psi_in=None, src=None):
+    def __init__(self, cfg, omega=None, w=None, S1=None, psi_in=None, src=None, lag=False):
+        """lag: break cycles of the sweep graphs by lagged back edges (graph()); transport steps
+        then read the previous step's psi on those faces (zero before the first step)."""
         self.lib = load(src)
         self.cfg = cfg
         self.geom = geometry(cfg["xyz"], cfg["hexes"], self.lib)
@@ -102,7 +113,11 @@ class ProblemHex:
             omega, w = product_quadrature(cfg["n_polar"], cfg["n_azimuthal"])
         self.omega = np.ascontiguousarray(omega, dtype=np.float64)
         self.w = np.ascontiguousarray(w, dtype=np.float64)
-        self.inflow, self.level = graph(self.geom, self.omega, self.lib)
+        if lag:
+            self.inflow, self.level, self.lag = graph(self.geom, self.omega, self.lib, lag=True)
+        else:
+            self.inflow, self.level = graph(self.geom, self.omega, self.lib)
+            self.lag = None
         self.G = int(cfg["n_groups"])
         self.C = self.geom["vol"].shape[0]
         self.D = self.omega.shape[0]
@@ -118,7 +133,8 @@ class ProblemHex:
         self._s = _ProblemHex(self.C, g["xyz"].shape[0], self.G, self.D, _p(g["xyz"]), _p(g["hexes"]),
                               _p(g["mass"]), _p(g["grad"]), _p(g["face"]), _p(g["nbar"]), _p(g["nbr"]),
                               _p(g["nbr_node"]), _p(self.omega), _p(self.w), _p(self.inflow), _p(self.level),
-                              _p(self.material), _p(self.sigma_t), _p(self.S1), _p(self.psi_in))
+                              _p(self.material), _p(self.sigma_t), _p(self.S1), _p(self.psi_in), _p(self.lag), None)
+        self.psi_prev = None  # lagged faces: psi [D][C][G][8] of the previous transport step
         # int_K b_i dV per cell and node: the row sums of the mass matrix (partition of unity)
         self.p_int = g["mass"].sum(axis=2)
 
@@ -132,12 +148,18 @@ class ProblemHex:
         return q / FOUR_PI
 
     def sweep_direction(self, a, q):
+        self._set_prev()
         psi = np.zeros((self.C, self.G, NB))
         q = np.ascontiguousarray(q, dtype=np.float64)
         _check(self.lib.orah_sweep_direction(C.byref(self._s), int(a), _p(q), _p(psi)), "sweep_direction")
         return psi
 
+    def _set_prev(self):
+        self._s.psi_prev = _p(self.psi_prev) if (self.lag is not None and self.psi_prev is not None) else None
+
     def sweep(self, q, dirs=None, threads=1, keep_psi=False):
+        """phi of the listed directions (all by default); lagged faces read self.psi_prev."""
+        self._set_prev()
         q = np.ascontiguousarray(q, dtype=np.float64)
         dirs = np.arange(self.D, dtype=np.int32) if dirs is None else np.ascontiguousarray(dirs, dtype=np.int32)
         phi = np.zeros((self.C, self.G, NB))
@@ -148,7 +170,13 @@ class ProblemHex:
         return phi, psi, used.value
 
     def transport_step(self, phi, threads=1):
-        return self.sweep(self.source(phi), threads=threads)[0]
+        """One source update and sweep.  With lagged back edges the step reads, and then replaces,
+        self.psi_prev (so consecutive calls are consecutive steps of source iteration)."""
+        if self.lag is None:
+            return self.sweep(self.source(phi), threads=threads)[0]
+        phi_new, psi, _ = self.sweep(self.source(phi), threads=threads, keep_psi=True)
+        self.psi_prev = psi
+        return phi_new
 
     @staticmethod
     def residual(phi_new, phi_old, floor=1.0):
@@ -168,6 +196,7 @@ class ProblemHex:
 
     def source_iterate(self, tol, max_iters, phi0=None, threads=1):
         phi = np.zeros((self.C, self.G, NB)) if phi0 is None else np.array(phi0, dtype=np.float64)
+        self.psi_prev = None
         r = np.inf
         it = 0
         for it in range(1, max_iters + 1):

@@ -85,6 +85,9 @@ typedef struct {
     const double *sigma_t;    /* [M][G] */
     const double *S1;         /* [nc][G][3] or NULL: extra angular source Omega.S1 (constant per cell) */
     const double *psi_in;     /* [nv][G] or NULL: isotropic inflow on boundary vertices (NULL = vacuum) */
+    const uint8_t *lag;       /* [D][nc] or NULL: bit f set iff inflow face f is a lagged back edge */
+    const double *psi_prev;   /* [D][nc][G][8] or NULL (zero): the previous transport step's psi, read
+                               * on lagged faces */
 } orah_problem;
 
 /* face-local node k of face f: the k-th vertex (increasing local index) with bit d equal to s */
@@ -298,18 +301,33 @@ int orah_geometry(int64_t nv, const double *xyz, int64_t nc, const int32_t *hexe
 }
 
 /* Face classification and t-levels per direction (Sec. 2.1), Kahn's algorithm as
- * for the tetrahedral oracle, over six faces.  ORA_ERR_CYCLE if a cell is never reached. */
-int orah_graph(int64_t nc, const int32_t *nbr, const double *nbar, int D, const double *omega,
-               uint8_t *inflow, int32_t *level)
+ * for the tetrahedral oracle, over six faces.  ORA_ERR_CYCLE if a cell is never reached.
+ *
+ * With lag != NULL ([D][nc]) cycles are broken instead (the paper assumes an acyclic
+ * graph; lagging is the usual remedy, not the paper's).  Whenever no cell is ready, a
+ * walk starts at the lowest-numbered waiting cell and steps to the upwind neighbour
+ * across its lowest-numbered open face (inflow, interior, not reached, not lagged);
+ * every waiting cell has one, so the walk comes back to a cell it has visited, and the
+ * face it would cross then closes a cycle: that one face is lagged (it will read the
+ * upwind cell's psi of the previous transport step) and the ordering continues.
+ * Lagged faces do not count for the t-levels. */
+int orah_graph_lag(int64_t nc, const int32_t *nbr, const double *nbar, int D, const double *omega,
+                   uint8_t *inflow, int32_t *level, uint8_t *lag)
 {
     int32_t *indeg = malloc(sizeof(int32_t) * (size_t)(nc > 0 ? nc : 1));
     int64_t *queue = malloc(sizeof(int64_t) * (size_t)(nc > 0 ? nc : 1));
-    if (!indeg || !queue) { free(indeg); free(queue); return ORA_ERR_NOMEM; }
+    int64_t *walk = malloc(sizeof(int64_t) * (size_t)(nc > 0 ? nc : 1));
+    uint8_t *reached = malloc((size_t)(nc > 0 ? nc : 1));
+    if (!indeg || !queue || !walk || !reached) {
+        free(indeg); free(queue); free(walk); free(reached);
+        return ORA_ERR_NOMEM;
+    }
     int status = ORA_OK;
     for (int a = 0; a < D && status == ORA_OK; ++a) {
         const double *O = omega + 3 * a;
         uint8_t *mask = inflow + (size_t)a * nc;
         int32_t *lev = level + (size_t)a * nc;
+        uint8_t *lg = lag ? lag + (size_t)a * nc : NULL;
         for (int64_t c = 0; c < nc; ++c) {
             uint8_t m = 0;
             for (int f = 0; f < 6; ++f) {
@@ -319,34 +337,77 @@ int orah_graph(int64_t nc, const int32_t *nbr, const double *nbar, int D, const 
                 if (s < -eps) m |= (uint8_t)(1u << f);
             }
             mask[c] = m;
+            if (lg) lg[c] = 0;
         }
-        int64_t head = 0, tail = 0;
+        int64_t head = 0, tail = 0, next = 0;
         for (int64_t c = 0; c < nc; ++c) {
             int deg = 0;
             for (int f = 0; f < 6; ++f)
                 if ((mask[c] >> f & 1) && nbr[6 * c + f] >= 0) ++deg;
             indeg[c] = deg;
             lev[c] = 0;
+            walk[c] = -1;
+            reached[c] = deg == 0;
             if (deg == 0) queue[tail++] = c;
         }
-        while (head < tail) {
-            int64_t c = queue[head++];
-            for (int f = 0; f < 6; ++f) {
-                int64_t n = nbr[6 * c + f];
-                if (n < 0) continue;
-                int down = 0;
-                for (int g = 0; g < 6; ++g)
-                    if (nbr[6 * n + g] == c && (mask[n] >> g & 1)) down = 1;
-                if (!down) continue;
-                if (lev[n] < lev[c] + 1) lev[n] = lev[c] + 1;
-                if (--indeg[n] == 0) queue[tail++] = n;
+        int64_t stamp = 0;
+        for (;;) {
+            while (head < tail) {
+                int64_t c = queue[head++];
+                for (int f = 0; f < 6; ++f) {
+                    int64_t n = nbr[6 * c + f];
+                    if (n < 0 || reached[n]) continue;
+                    int down = 0;
+                    for (int g = 0; g < 6; ++g)
+                        if (nbr[6 * n + g] == c && (mask[n] >> g & 1) && !(lg && (lg[n] >> g & 1))) down = 1;
+                    if (!down) continue;
+                    if (lev[n] < lev[c] + 1) lev[n] = lev[c] + 1;
+                    if (--indeg[n] == 0) {
+                        reached[n] = 1;
+                        queue[tail++] = n;
+                    }
+                }
             }
+            if (tail == nc || !lg) break;
+            /* no cell is ready: walk upwind from the lowest-numbered waiting cell to a cycle */
+            while (reached[next]) ++next;
+            int64_t cur = next;
+            walk[cur] = stamp;
+            for (;;) {
+                int fo = -1;
+                int64_t n = -1;
+                for (int f = 0; f < 6 && fo < 0; ++f) {
+                    n = nbr[6 * cur + f];
+                    if ((mask[cur] >> f & 1) && !(lg[cur] >> f & 1) && n >= 0 && !reached[n]) fo = f;
+                }
+                if (fo < 0) { status = ORA_ERR_CYCLE; break; }  /* cannot happen: cur waits on someone */
+                if (walk[n] == stamp) {  /* cur -> n closes a cycle: lag that face */
+                    lg[cur] |= (uint8_t)(1u << fo);
+                    if (--indeg[cur] == 0) {
+                        reached[cur] = 1;
+                        queue[tail++] = cur;
+                    }
+                    break;
+                }
+                walk[n] = stamp;
+                cur = n;
+            }
+            ++stamp;
+            if (status != ORA_OK) break;
         }
-        if (tail != nc) status = ORA_ERR_CYCLE;
+        if (tail != nc && status == ORA_OK) status = ORA_ERR_CYCLE;
     }
     free(indeg);
     free(queue);
+    free(walk);
+    free(reached);
     return status;
+}
+
+int orah_graph(int64_t nc, const int32_t *nbr, const double *nbar, int D, const double *omega,
+               uint8_t *inflow, int32_t *level)
+{
+    return orah_graph_lag(nc, nbr, nbar, D, omega, inflow, level, NULL);
 }
 
 /* Gaussian elimination with partial pivoting on an 8x8 system. */
@@ -441,10 +502,14 @@ int orah_sweep_direction(const orah_problem *P, int a, const double *q, double *
             for (int f = 0; f < 6; ++f) {
                 if (!(mask[c] >> f & 1)) continue;
                 const int64_t n = P->nbr[6 * c + f];
+                const int lagged = P->lag && (P->lag[(size_t)a * nc + c] >> f & 1);
                 double up[4];
                 for (int k = 0; k < 4; ++k) {
                     const int v = face_node(f, k);
-                    if (n >= 0)
+                    if (n >= 0 && lagged)  /* back edge: the upwind cell's psi of the previous step */
+                        up[k] = P->psi_prev ? P->psi_prev[(((size_t)a * nc + n) * G + g) * 8 + P->nbr_node[24 * c + 4 * f + k]]
+                                            : 0.0;
+                    else if (n >= 0)
                         up[k] = psi[((size_t)n * G + g) * 8 + P->nbr_node[24 * c + 4 * f + k]];
                     else if (P->psi_in)
                         up[k] = P->psi_in[(size_t)P->hexes[8 * c + v] * G + g];

@@ -307,7 +307,8 @@ MUTANTS = {
     "mass_without_det": ("Mc[8 * i + j] += wt * det * b[i] * b[j];", "Mc[8 * i + j] += wt * b[i] * b[j];"),
     "face_term_sign": ("Fin[f][k][l] = -((O[0]", "Fin[f][k][l] = ((O[0]"),
     "face_rhs_dropped": ("b[i] += Fin[f][k][l] * up[l];", "b[i] += 0.0 * up[l];"),
-    "upwind_node": ("P->nbr_node[24 * c + 4 * f + k]]", "P->nbr_node[24 * c + 4 * f + (k ^ 1)]]"),
+    "upwind_node": ("psi[((size_t)n * G + g) * 8 + P->nbr_node[24 * c + 4 * f + k]]",
+                    "psi[((size_t)n * G + g) * 8 + P->nbr_node[24 * c + 4 * f + (k ^ 1)]]"),
     "s1_dropped": ("b[i] += os * rowm[i];", "b[i] += 0.0 * os;"),
     "streaming_transposed": ("S[i][j] = (O[0] * Gc[8 * i + j] + O[1] * Gc[64 + 8 * i + j]) + O[2] * Gc[128 + 8 * i + j];",
                              "S[i][j] = (O[0] * Gc[8 * j + i] + O[1] * Gc[64 + 8 * j + i]) + O[2] * Gc[128 + 8 * j + i];"),
@@ -384,3 +385,155 @@ def test_thick_medium_interior_matches_infinite_medium():
     centre = np.linalg.norm(xyz[hexes].mean(axis=1) - 4.0, axis=1) < 1.5
     assert centre.sum() == 8
     assert np.max(np.abs(phi[centre] - 1.0 / 2.5)) < 1e-3
+
+
+# ------------------------------------------------------------- lagged back edges
+# The paper assumes an acyclic sweep graph per direction; twisted hexahedral grids with many
+# directions have cycles.  Lagging one face per cycle (it reads the previous transport step's
+# upwind values) keeps the sweep defined; at convergence the lag must not matter.
+def _cyclic_cfg(G=2, n=4, twist=0.6):
+    return W.hex_problem(W.small_box(n=n, G=G, n_polar=8, n_az=16), twist=twist)
+
+
+def _dependency_graph_without_lags(P, a):
+    """Kahn's algorithm over the non-lagged inflow faces, written out here: returns the
+    longest-upwind-path levels, or None if a cycle remains."""
+    nbr, C = P.geom["nbr"], P.C
+    ups = [[nbr[c, f] for f in range(6) if (P.inflow[a, c] >> f & 1) and nbr[c, f] >= 0
+            and not (P.lag[a, c] >> f & 1)] for c in range(C)]
+    downs = [[] for _ in range(C)]
+    for c in range(C):
+        for u in ups[c]:
+            downs[u].append(c)
+    deg = [len(u) for u in ups]
+    lev = [0] * C
+    ready = [c for c in range(C) if deg[c] == 0]
+    seen = 0
+    while ready:
+        u = ready.pop()
+        seen += 1
+        for c in downs[u]:
+            lev[c] = max(lev[c], lev[u] + 1)
+            deg[c] -= 1
+            if deg[c] == 0:
+                ready.append(c)
+    return lev if seen == C else None
+
+
+def test_lag_changes_nothing_on_an_acyclic_grid():
+    cfg = W.hex_problem(W.small_box(n=4, G=2, n_polar=4, n_az=8), twist=0.25)
+    P0, P1 = H.ProblemHex(cfg), H.ProblemHex(cfg, lag=True)
+    assert not P1.lag.any()
+    assert np.array_equal(P0.inflow, P1.inflow) and np.array_equal(P0.level, P1.level)
+    phi = np.random.default_rng(3).uniform(0, 1, (P0.C, 2, 8))
+    assert np.array_equal(P0.transport_step(phi), P1.transport_step(phi))
+
+
+def test_lagged_faces_break_every_cycle():
+    """The grid has cycles (the plain graph is an error); every lagged face is an interior
+    inflow face, the graph without them is acyclic, and the levels are its longest upwind paths."""
+    cfg = _cyclic_cfg()
+    with pytest.raises(OracleError):
+        H.ProblemHex(cfg)
+    P = H.ProblemHex(cfg, lag=True)
+    lagged_dirs = [a for a in range(P.D) if P.lag[a].any()]
+    assert len(lagged_dirs) >= 8
+    for a in range(P.D):
+        for c in range(P.C):
+            for f in range(6):
+                if P.lag[a, c] >> f & 1:
+                    assert P.inflow[a, c] >> f & 1 and P.geom["nbr"][c, f] >= 0
+        lev = _dependency_graph_without_lags(P, a)
+        assert lev is not None, a
+        assert np.array_equal(np.array(lev), P.level[a]), a
+    # one face per cycle: far fewer lagged faces than inflow faces
+    assert int(np.unpackbits(P.lag).sum()) < 0.02 * int(np.unpackbits(P.inflow).sum())
+
+
+def test_lagged_sweep_iterates_to_the_dense_solve():
+    """For a fixed source, repeating the lagged sweep of one direction (each repetition reads
+    the previous one's upwind values on the lagged faces) converges to the whole-mesh dense
+    solve, which has no sweep order and no lag; with boundary inflow and S1."""
+    cfg = _cyclic_cfg(G=2)
+    xyz, hexes = cfg["xyz"], cfg["hexes"]
+    C = len(hexes)
+    rng = np.random.default_rng(5)
+    S1 = rng.uniform(-1, 1, (C, 2, 3))
+    psi_in = rng.uniform(0, 1, (len(xyz), 2))
+    P = H.ProblemHex(cfg, S1=S1, psi_in=psi_in, lag=True)
+    q = rng.uniform(0, 1, (C, 2, 8))
+    sig = np.asarray(cfg["sigma_t"])[np.asarray(cfg["cell_material"])]
+    for a in [a for a in range(P.D) if P.lag[a].any()][:3]:
+        P.psi_prev = np.zeros((P.D, C, 2, 8))
+        first = None
+        for _ in range(400):
+            psi = P.sweep_direction(a, q)
+            if first is None:
+                first = psi.copy()
+            change = np.max(np.abs(psi - P.psi_prev[a]))
+            P.psi_prev[a] = psi
+            if change < 1e-15 * np.max(np.abs(psi)):
+                break
+        for g in range(2):
+            ref = dense_direction_solve(xyz, hexes, P.omega[a], sig[:, g], q[:, g], S1[:, g], psi_in[:, g])
+            assert np.max(np.abs(psi[:, g] - ref)) < 1e-11 * np.max(np.abs(ref)), (a, g)
+            # the first lagged sweep (zero on the lagged faces) is not yet the answer
+            assert np.max(np.abs(first[:, g] - ref)) > 1e-6 * np.max(np.abs(ref)), (a, g)
+
+
+def test_lagged_source_iteration_converges_to_the_lag_free_answer():
+    """Source iteration with lagged faces converges; at its fixed point every direction's psi is
+    the dense (lag-free) solve of that direction with the converged source."""
+    cfg = _cyclic_cfg(G=2)
+    cfg["Q"] = np.random.default_rng(7).uniform(0.0, 1.0, cfg["Q"].shape)
+    P = H.ProblemHex(cfg, lag=True)
+    phi, it, r = P.source_iterate(1e-12, 2000, threads=8)
+    assert r < 1e-12 and it > 2
+    q = P.source(phi)
+    sig = np.asarray(cfg["sigma_t"])[np.asarray(cfg["cell_material"])]
+    for a in [a for a in range(P.D) if P.lag[a].any()][:3]:
+        for g in range(2):
+            ref = dense_direction_solve(cfg["xyz"], cfg["hexes"], P.omega[a], sig[:, g], q[:, g])
+            assert np.max(np.abs(P.psi_prev[a][:, g] - ref)) < 1e-9 * np.max(np.abs(ref)), (a, g)
+
+
+LAG_MUTANTS = {
+    "lag_reads_current_psi": ("if (n >= 0 && lagged)", "if (n >= 0 && lagged && 0)"),
+    "lag_wrong_face": ("lg[cur] |= (uint8_t)(1u << fo);", "lg[cur] |= (uint8_t)(1u << ((fo + 1) % 6));"),
+    "lag_previous_psi_ignored": ("up[k] = P->psi_prev ? P->psi_prev[", "up[k] = 0 ? P->psi_prev["),
+}
+
+
+def _lag_battery(src):
+    """The dense-solve limit of repeated lagged sweeps on one cyclic direction, against a
+    modified oracle; returns whether it still holds."""
+    cfg = _cyclic_cfg(G=1)
+    C = len(cfg["hexes"])
+    try:
+        P = H.ProblemHex(cfg, lag=True, src=src)
+        a = next(a for a in range(P.D) if P.lag[a].any())
+        q = np.random.default_rng(1).uniform(0, 1, (C, 1, 8))
+        P.psi_prev = np.zeros((P.D, C, 1, 8))
+        for _ in range(300):
+            P.psi_prev[a] = P.sweep_direction(a, q)
+        sig = np.asarray(cfg["sigma_t"])[np.asarray(cfg["cell_material"])]
+        ref = dense_direction_solve(cfg["xyz"], cfg["hexes"], P.omega[a], sig[:, 0], q[:, 0])
+        return bool(np.max(np.abs(P.psi_prev[a][:, 0] - ref)) < 1e-11 * np.max(np.abs(ref)))
+    except (OracleError, StopIteration):
+        return False
+
+
+def test_unmodified_oracle_passes_the_lag_battery():
+    assert _lag_battery(None)
+
+
+@pytest.mark.parametrize("name", sorted(LAG_MUTANTS))
+def test_planted_lag_mistake_is_caught(name, tmp_path):
+    old, new = LAG_MUTANTS[name]
+    with open(H.SRC) as f:
+        text = f.read()
+    assert text.count(old) == 1, name
+    src = tmp_path / f"mut_{name}.c"
+    src.write_text(text.replace(old, new))
+    assert not _lag_battery(str(src)), name
+    os.remove(src)
