@@ -156,7 +156,19 @@ typedef struct {
                               * undershoots put |phi| near 0) */
     double patch_extent;     /* spatial patches: edge of a patch region in mean cell sizes (the edge of
                               * a cube of six tetrahedra of the mean volume); 0 = automatic (2) */
-    double reserved_d[2];
+    int32_t lag_cycles;      /* 0 = a direction whose sweep graph has a cycle is an error (TF_ERR_CYCLE);
+                              * 1 = break the cycles by lagged back edges (hexahedral meshes, t-level
+                              * tasks, problems swept on their own): whenever no cell is ready, a walk
+                              * from the lowest-numbered waiting cell across the lowest-numbered open
+                              * inflow faces (upwind neighbour not yet reached) finds a cycle, and the
+                              * face that closes it is lagged.  A lagged face reads the upwind cell's
+                              * psi of the previous transport step (zero in the first step), so a
+                              * transport step is no longer an exact inversion of the streaming
+                              * operator; source iteration converges to the same answer.  The sweep
+                              * graph with cycles is outside the paper, which assumes a DAG per angle
+                              * (Sec. 1); the particle balance holds only at convergence. */
+    int32_t reserved_i;
+    double reserved_d[1];
 } tf_options;
 
 /* Fills *opt with the defaults above. */
@@ -219,7 +231,8 @@ typedef struct {
     int32_t task_shape;        /* tf_task_shape in use: TF_TASK_LEVELS or TF_TASK_PATCHES */
     double data_wait_seconds;  /* summed over warps: time waiting for rows staged by bulk copies
                                 * (SM cycles at the nominal SM clock) */
-    double reserved_d[5];
+    int64_t lagged_faces;      /* lagged back edges over all directions (lag_cycles) */
+    double reserved_d[4];
 } tf_stats;
 
 /* Mesh of tetrahedra.  xyz: host [n_vertices][3] FP64; tets: host [n_cells][4]
@@ -331,6 +344,12 @@ tf_status tf_quadrature_get(tf_handle quad, int32_t *n_dirs, double *omega, doub
  * buckets), tetrahedral or hexahedral mesh.  inflow [n_dirs][n_cells]: bit f set iff face f is inflow;
  * level [n_dirs][n_cells].  Either may be NULL.  Errors: TF_ERR_CYCLE. */
 tf_status tf_graph_levels(tf_handle mesh, tf_handle quad, uint8_t *inflow, int32_t *level);
+
+/* Host-only: as tf_graph_levels, with cycles broken by lagged back edges (tf_options.lag_cycles):
+ * lag [n_dirs][n_cells], bit f set iff inflow face f is lagged; levels count the other faces
+ * only.  Either output may be NULL.  The paper has no counterpart (it assumes acyclic graphs).
+ * Errors: TF_ERR_ARG. */
+tf_status tf_graph_lag(tf_handle mesh, tf_handle quad, uint8_t *inflow, int32_t *level, uint8_t *lag);
 
 /* Host-only: the tasks a problem with options *opt (NULL = defaults) and n_groups groups on this
  * mesh and quadrature would sweep (t-level blocks or spatial patches, tf_task_shape; the grain

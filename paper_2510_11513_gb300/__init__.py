@@ -14,7 +14,7 @@ from .tfsweep import (TF_ERR_ARG, TF_ERR_CUDA, TF_ERR_CYCLE, TF_ERR_DEVICE, TF_E
                       sweep_batch, tf_destroy, tf_mlp_adam_step, tf_mlp_create, tf_mlp_features, tf_mlp_features_context, tf_mlp_fit_scale,
                       tf_mlp_fit_inputs, tf_mlp_forward, tf_mlp_gradients, tf_mlp_input_scale, tf_mlp_limits, tf_mlp_params, tf_mlp_predict_phi, tf_mlp_scale, tf_mlp_shrink,
                       tf_mlp_targets, tf_mlp_train, tf_mlp_weights,
-                      tf_graph_levels, tf_graph_tasks, tf_mesh_create, tf_mesh_create_hex, tf_mesh_geometry, tf_mesh_hex_integrals, tf_problem_create, tf_problem_psi,
+                      tf_graph_lag, tf_graph_levels, tf_graph_tasks, tf_mesh_create, tf_mesh_create_hex, tf_mesh_geometry, tf_mesh_hex_integrals, tf_problem_create, tf_problem_psi,
                       tf_problem_stats, tf_quadrature_create, tf_quadrature_get, tf_source_iterate, tf_sweep)
 
 __all__ = [n for n in dir() if n.startswith(("tf_", "TF_")) or n in ("HexMesh", "Mesh", "Mlp", "Problem", "Quadrature", "TfError",

@@ -268,6 +268,11 @@ tf_status tf_problem_create(tf_handle mesh, tf_handle quad, int32_t n_groups, in
         delete p;
         return fail(TF_ERR_ARG, "tf_problem_create: order must be 0 to 3 (orders 2 and 3: S1 and psi_inflow NULL)");
     }
+    if (p->opt.lag_cycles != 0 && (p->opt.lag_cycles != 1 || m->nf != 6 || p->opt.task_shape == TF_TASK_PATCHES)) {
+        delete p;
+        return fail(TF_ERR_ARG, "tf_problem_create: lag_cycles is 0 or 1, and lagged back edges take hexahedral "
+                                "meshes with t-level tasks");
+    }
     if (!(p->opt.wait_limit_s > 0.0)) p->opt.wait_limit_s = 10.0;
     if (!(p->opt.residual_floor > 0.0) || p->opt.residual_floor > 1.0) p->opt.residual_floor = 1.0;
     p->mesh = m;
@@ -295,7 +300,7 @@ tf_status tf_problem_create(tf_handle mesh, tf_handle quad, int32_t n_groups, in
     TaskShape shape;
     bool patches = false;
     tf_status s = task_grain(p->opt, *m, n_groups, &B, &patches, &shape);
-    if (s == TF_OK) s = build_task_graph(*m, *q, B, p->graph, patches ? &shape : nullptr);
+    if (s == TF_OK) s = build_task_graph(*m, *q, B, p->graph, patches ? &shape : nullptr, p->opt.lag_cycles == 1);
     if (s == TF_OK) s = device_create(*p, cell_material, sigma_t, sigma_s, Q, S1, psi_inflow);
     if (s != TF_OK) {
         release(p);
@@ -384,6 +389,19 @@ tf_status tf_graph_levels(tf_handle mesh, tf_handle quad, uint8_t *inflow, int32
     return classify_and_level(*m, *q, inflow, level);
 }
 
+tf_status tf_graph_lag(tf_handle mesh, tf_handle quad, uint8_t *inflow, int32_t *level, uint8_t *lag)
+{
+    Mesh *m = as<Mesh>(mesh, Kind::Mesh);
+    Quad *q = as<Quad>(quad, Kind::Quad);
+    if (!m || !q) return fail(TF_ERR_ARG, "tf_graph_lag: mesh or quadrature handle invalid");
+    std::vector<uint8_t> tmp;
+    if (!lag) {
+        tmp.resize((size_t)q->D * m->nc);
+        lag = tmp.data();
+    }
+    return classify_and_level(*m, *q, inflow, level, lag);
+}
+
 tf_status tf_graph_tasks(tf_handle mesh, tf_handle quad, const tf_options *opt, int32_t n_groups, int64_t *n_tasks,
                          int32_t *task_of, int32_t *position, int32_t *indeg)
 {
@@ -400,7 +418,9 @@ tf_status tf_graph_tasks(tf_handle mesh, tf_handle quad, const tf_options *opt, 
     tf_status s = task_grain(o, *m, n_groups, &B, &patches, &shape);
     if (s != TF_OK) return s;
     TaskGraph g;
-    if ((s = build_task_graph(*m, *q, B, g, patches ? &shape : nullptr)) != TF_OK) return s;
+    if ((s = build_task_graph(*m, *q, B, g, patches ? &shape : nullptr, o.lag_cycles == 1 && m->nf == 6 && !patches)) !=
+        TF_OK)
+        return s;
     if (n_tasks) *n_tasks = g.T();
     if (indeg) std::copy(g.task_indeg.begin(), g.task_indeg.end(), indeg);
     for (int64_t t = 0; t < g.T(); ++t)

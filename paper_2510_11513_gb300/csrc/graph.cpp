@@ -35,31 +35,72 @@ inline uint8_t inflow_mask(const double *O, const double *Nc, int nf)
     return m;
 }
 
-// Levels of one direction by Kahn's algorithm; returns false on a cycle.
+// Levels of one direction by Kahn's algorithm; returns false on a cycle.  With lag
+// (non-null, [nc]) cycles are broken instead: whenever no cell is ready, a walk from
+// the lowest-numbered waiting cell steps to the upwind neighbour across its
+// lowest-numbered open face (inflow, interior, not reached, not lagged) until it comes
+// back to a cell it has visited; the face it would cross then closes a cycle and is
+// lagged (lag[c] bit f: the kernel reads the previous transport step's upwind values
+// there), and the ordering continues.  Lagged faces do not count for the levels.
 bool levels_one(const Mesh &m, const uint8_t *mask, int32_t *level, std::vector<int32_t> &indeg,
-                std::vector<int32_t> &queue)
+                std::vector<int32_t> &queue, uint8_t *lag = nullptr)
 {
     const int64_t nc = m.nc;
     const int nf = m.nf;
     indeg.resize(nc);
     queue.resize(nc);
-    int64_t tail = 0;
+    std::vector<uint8_t> reached(nc);
+    std::vector<int64_t> walk(lag ? nc : 0, -1);
+    int64_t tail = 0, head = 0, next = 0, stamp = 0;
     for (int64_t c = 0; c < nc; ++c) {
         int d = 0;
         for (int f = 0; f < nf; ++f) d += ((mask[c] >> f) & 1) && m.nbr[nf * c + f] >= 0;
         indeg[c] = d;
         level[c] = 0;
+        reached[c] = d == 0;
+        if (lag) lag[c] = 0;
         if (d == 0) queue[tail++] = (int32_t)c;
     }
-    for (int64_t head = 0; head < tail; ++head) {
-        const int32_t c = queue[head];
-        for (int f = 0; f < nf; ++f) {
-            const int32_t n = m.nbr[nf * c + f];
-            if (n < 0) continue;
-            if (!((mask[n] >> m.nbr_face[nf * c + f]) & 1)) continue;  // n is not downwind of c
-            level[n] = std::max(level[n], level[c] + 1);
-            if (--indeg[n] == 0) queue[tail++] = n;
+    for (;;) {
+        for (; head < tail; ++head) {
+            const int32_t c = queue[head];
+            for (int f = 0; f < nf; ++f) {
+                const int32_t n = m.nbr[nf * c + f];
+                if (n < 0 || reached[n]) continue;
+                const int fn = m.nbr_face[nf * c + f];
+                if (!((mask[n] >> fn) & 1)) continue;        // n is not downwind of c
+                if (lag && ((lag[n] >> fn) & 1)) continue;   // lagged: not a dependency
+                level[n] = std::max(level[n], level[c] + 1);
+                if (--indeg[n] == 0) {
+                    reached[n] = 1;
+                    queue[tail++] = n;
+                }
+            }
         }
+        if (tail == nc || !lag) break;
+        while (reached[next]) ++next;
+        int64_t cur = next;
+        walk[cur] = stamp;
+        for (;;) {
+            int fo = -1;
+            int32_t n = -1;
+            for (int f = 0; f < nf && fo < 0; ++f) {
+                n = m.nbr[nf * cur + f];
+                if (((mask[cur] >> f) & 1) && !((lag[cur] >> f) & 1) && n >= 0 && !reached[n]) fo = f;
+            }
+            if (fo < 0) return false;  // a waiting cell always waits on someone; never taken
+            if (walk[n] == stamp) {    // cur -> n closes a cycle: lag that face
+                lag[cur] |= (uint8_t)(1u << fo);
+                if (--indeg[cur] == 0) {
+                    reached[cur] = 1;
+                    queue[tail++] = (int32_t)cur;
+                }
+                break;
+            }
+            walk[n] = stamp;
+            cur = n;
+        }
+        ++stamp;
     }
     return tail == nc;
 }
@@ -79,14 +120,15 @@ void run_parallel(int32_t D, const std::function<void(int32_t)> &fn)
 
 }  // namespace
 
-tf_status classify_and_level(const Mesh &m, const Quad &q, uint8_t *inflow, int32_t *level)
+tf_status classify_and_level(const Mesh &m, const Quad &q, uint8_t *inflow, int32_t *level, uint8_t *lag)
 {
     std::atomic<bool> cycle{false};
     run_parallel(q.D, [&](int32_t a) {
         std::vector<uint8_t> mask(m.nc);
         std::vector<int32_t> lev(m.nc), indeg, queue;
         for (int64_t c = 0; c < m.nc; ++c) mask[c] = inflow_mask(&q.omega[3 * a], &m.normal[3 * m.nf * c], m.nf);
-        if (!levels_one(m, mask.data(), lev.data(), indeg, queue)) cycle = true;
+        if (!levels_one(m, mask.data(), lev.data(), indeg, queue, lag ? lag + (size_t)a * m.nc : nullptr))
+            cycle = true;
         if (inflow) std::copy(mask.begin(), mask.end(), inflow + (size_t)a * m.nc);
         if (level) std::copy(lev.begin(), lev.end(), level + (size_t)a * m.nc);
     });
@@ -106,6 +148,7 @@ struct DirTasks {
     std::vector<int32_t> blevel;
     std::vector<uint32_t> down_begin;  // per task + 1
     std::vector<uint32_t> down;        // local task ids
+    std::vector<uint8_t> lag;          // lagged faces of each cell entry, in task order (empty: none)
     bool ok = true;
 };
 
@@ -206,17 +249,21 @@ void patch_tasks(const Mesh &m, const uint8_t *mask, const int32_t *lev, const s
 }
 
 void build_direction(const Mesh &m, const double *O, int32_t B, const std::vector<int32_t> *region, int32_t gap,
-                     DirTasks &out)
+                     bool lag_cycles, DirTasks &out)
 {
     const int64_t nc = m.nc;
     const int nf = m.nf, sh = nf == 6 ? 6 : 4;
-    std::vector<uint8_t> mask(nc);
+    std::vector<uint8_t> mask(nc), lagc(lag_cycles ? nc : 0);
     std::vector<int32_t> lev(nc), indeg, queue;
     for (int64_t c = 0; c < nc; ++c) mask[c] = inflow_mask(O, &m.normal[3 * nf * c], nf);
-    if (!levels_one(m, mask.data(), lev.data(), indeg, queue)) {
+    if (!levels_one(m, mask.data(), lev.data(), indeg, queue, lag_cycles ? lagc.data() : nullptr)) {
         out.ok = false;
         return;
     }
+    bool any_lag = false;
+    for (uint8_t v : lagc) any_lag |= v != 0;
+    // a lagged face is not a dependency
+    auto dep = [&](int64_t c, int f) { return ((mask[c] >> f) & 1) && !(any_lag && ((lagc[c] >> f) & 1)); };
     int32_t L = 0;
     for (int64_t c = 0; c < nc; ++c) L = std::max(L, lev[c] + 1);
     out.levels = L;
@@ -262,7 +309,7 @@ void build_direction(const Mesh &m, const double *O, int32_t B, const std::vecto
         for (uint32_t i = out.cell_begin[b]; i < out.cell_begin[b] + out.ncell[b]; ++i) {
             const int32_t c = (int32_t)(out.cells[i] >> sh);
             for (int f = 0; f < nf; ++f)
-                if (((mask[c] >> f) & 1) && m.nbr[nf * c + f] >= 0 && block_of[m.nbr[nf * c + f]] != b)
+                if (dep(c, f) && m.nbr[nf * c + f] >= 0 && block_of[m.nbr[nf * c + f]] != b)
                     tmp.push_back(block_of[m.nbr[nf * c + f]]);
         }
         std::sort(tmp.begin(), tmp.end());
@@ -273,13 +320,17 @@ void build_direction(const Mesh &m, const double *O, int32_t B, const std::vecto
             const int32_t c = (int32_t)(out.cells[i] >> sh);
             for (int f = 0; f < nf; ++f) {
                 const int32_t n = m.nbr[nf * c + f];
-                if (n >= 0 && ((mask[n] >> m.nbr_face[nf * c + f]) & 1) && block_of[n] != b) tmp.push_back(block_of[n]);
+                if (n >= 0 && dep(n, m.nbr_face[nf * c + f]) && block_of[n] != b) tmp.push_back(block_of[n]);
             }
         }
         std::sort(tmp.begin(), tmp.end());
         tmp.erase(std::unique(tmp.begin(), tmp.end()), tmp.end());
         out.down.insert(out.down.end(), tmp.begin(), tmp.end());
         out.down_begin[b + 1] = (uint32_t)out.down.size();
+    }
+    if (any_lag) {
+        out.lag.resize(out.cells.size());
+        for (size_t i = 0; i < out.cells.size(); ++i) out.lag[i] = lagc[out.cells[i] >> sh];
     }
     // b-level: longest chain of downwind tasks below each task (tasks are in a topological
     // order: t-level blocks by level, patches by round and, inside a patch, by piece)
@@ -325,8 +376,10 @@ static void patch_regions(const Mesh &m, double extent, std::vector<int32_t> &re
     }
 }
 
-tf_status build_task_graph(const Mesh &m, const Quad &q, int32_t B, TaskGraph &g, const TaskShape *shape)
+tf_status build_task_graph(const Mesh &m, const Quad &q, int32_t B, TaskGraph &g, const TaskShape *shape,
+                           bool lag_cycles)
 {
+    if (lag_cycles && shape) return fail(TF_ERR_ARG, "lagged back edges take t-level tasks, not spatial patches");
     if (B < 1 || B > 4096) return fail(TF_ERR_ARG, "cells_per_task must be in [1, 4096]");
     const int sh = m.nf == 6 ? 6 : 4;
     if (m.nc >= (int64_t(1) << (32 - sh)))
@@ -338,7 +391,8 @@ tf_status build_task_graph(const Mesh &m, const Quad &q, int32_t B, TaskGraph &g
     try {
         if (shape) patch_regions(m, shape->extent, region);
         run_parallel(q.D, [&](int32_t a) {
-            build_direction(m, &q.omega[3 * a], B, shape ? &region : nullptr, shape ? shape->gap : 0, per[a]);
+            build_direction(m, &q.omega[3 * a], B, shape ? &region : nullptr, shape ? shape->gap : 0, lag_cycles,
+                            per[a]);
         });
     } catch (const std::bad_alloc &) {
         return fail(TF_ERR_NOMEM, "graph: host allocation failed");
@@ -395,6 +449,35 @@ tf_status build_task_graph(const Mesh &m, const Quad &q, int32_t B, TaskGraph &g
         for (size_t k = 0; k < d.down.size(); ++k) g.down_list[ebeg[a] + k] = (uint32_t)(t0 + d.down[k]);
     });
     g.down_begin[T] = (uint64_t)E;
+    // lagged back edges: per cell entry (lag mask << 26) | first slot, slots numbered by
+    // direction, entry and face; per slot its direction and (cell << 3) | face
+    g.cell_lag.clear();
+    g.lag_slots.clear();
+    g.lag_dir_begin.assign(q.D + 1, 0);
+    bool any = false;
+    for (auto &d : per) any |= !d.lag.empty();
+    if (any) {
+        g.cell_lag.assign(g.cell_list.size(), 0u);
+        int64_t slot = 0;
+        for (int32_t a = 0; a < q.D; ++a) {
+            g.lag_dir_begin[a] = slot;
+            const DirTasks &d = per[a];
+            for (size_t i = 0; i < d.lag.size(); ++i) {
+                if (!d.lag[i]) continue;
+                if (slot >= (int64_t(1) << 26)) return fail(TF_ERR_ARG, "graph: more than 2^26 lagged faces");
+                const uint64_t pos = (uint64_t)a * m.nc + i;
+                g.cell_lag[pos] = ((uint32_t)d.lag[i] << 26) | (uint32_t)slot;
+                const uint32_t c = d.cells[i] >> sh;
+                for (int f = 0; f < m.nf; ++f)
+                    if ((d.lag[i] >> f) & 1) {
+                        g.lag_slots.push_back((uint32_t)a);
+                        g.lag_slots.push_back((c << 3) | (uint32_t)f);
+                        ++slot;
+                    }
+            }
+        }
+        g.lag_dir_begin[q.D] = slot;
+    }
     return TF_OK;
 }
 

@@ -69,14 +69,37 @@ template <class T> __device__ __forceinline__ void hex_solve8(T a[8][8], T b[8],
     }
 }
 
-// One unit: cell entry e = (cell << 6) | inflow mask, group g.  q and psi are node-major per
-// cell, [cell][node][G]; the upwind rows were written by other warps in this launch and are
-// read through L2.  Lanes of one cell read its record at the same addresses (broadcast).
+// Upwind values across interior face f of the cell entry at `pos` for group g: the neighbour's
+// psi of this sweep (written by other warps in this launch, read through L2), or, on a lagged
+// back edge, its psi of the previous transport step from the lag buffer.
 template <class T>
-__device__ __forceinline__ void hex_unit(const SweepArgs<T> &A, const HexGeo<T> *__restrict__ geo, uint32_t e, int g,
+__device__ __forceinline__ void hex_upwind(const SweepArgs<T> &A, const HexGeo<T> *cg, uint32_t pos, int f, int32_t n,
+                                           int g, size_t psi_dir, T u[4])
+{
+    const int G = A.G;
+    const uint32_t lw = A.lagw ? __ldg(A.lagw + pos) : 0u;
+    if ((lw >> (26 + f)) & 1u) {
+        const uint32_t slot = (lw & 0x3ffffffu) + (uint32_t)__popc((lw >> 26) & ((1u << f) - 1u));
+        const T *lb = A.lagbuf + (size_t)slot * 4 * G + g;
+#pragma unroll
+        for (int l = 0; l < 4; ++l) u[l] = __ldg(lb + (size_t)l * G);
+        return;
+    }
+    const uint32_t nm = __ldg(&cg->nmap[f]);
+    const T *up = reinterpret_cast<const T *>(A.psi) + (psi_dir + (size_t)n) * 8 * (size_t)G + g;
+#pragma unroll
+    for (int l = 0; l < 4; ++l) u[l] = __ldcg(up + (size_t)((nm >> (4 * l)) & 15u) * G);
+}
+
+// One unit: the cell entry at position pos of the task cell list ((cell << 6) | inflow mask),
+// group g.  q and psi are node-major per cell, [cell][node][G].  Lanes of one cell read its
+// record at the same addresses (broadcast).
+template <class T>
+__device__ __forceinline__ void hex_unit(const SweepArgs<T> &A, const HexGeo<T> *__restrict__ geo, uint32_t pos, int g,
                                          T ox, T oy, T oz, size_t psi_dir)
 {
     const int G = A.G;
+    const uint32_t e = __ldg(A.cells + pos);
     const uint32_t c = e >> 6, mask = e & 63u;
     const HexGeo<T> *cg = geo + c;
     const T sig = __ldg(A.sigma_t + (size_t)__ldg(&cg->mat) * G + g);
@@ -120,10 +143,7 @@ __device__ __forceinline__ void hex_unit(const SweepArgs<T> &A, const HexGeo<T> 
         const int32_t n = __ldg(&cg->nbr[f]);
         T u[4];
         if (n >= 0) {
-            const uint32_t nm = __ldg(&cg->nmap[f]);
-            const T *up = psi + (psi_dir + (size_t)n) * 8 * (size_t)G + g;
-#pragma unroll
-            for (int l = 0; l < 4; ++l) u[l] = __ldcg(up + (size_t)((nm >> (4 * l)) & 15u) * G);
+            hex_upwind(A, cg, pos, f, n, g, psi_dir, u);
         } else if (A.psi_in) {  // prescribed inflow at the face's vertices
 #pragma unroll
             for (int l = 0; l < 4; ++l)
@@ -156,7 +176,7 @@ __device__ __forceinline__ void run_task_hex(const SweepArgs<T> &A, uint4 ti, in
     for (uint32_t u = lane; u < nu; u += 32) {
         const uint32_t k = u / (uint32_t)A.G;
         const int g = (int)(u - k * (uint32_t)A.G);
-        hex_unit(A, geo, __ldg(A.cells + ti.x + k), g, ox, oy, oz, psi_dir);
+        hex_unit(A, geo, ti.x + k, g, ox, oy, oz, psi_dir);
     }
 }
 
@@ -255,10 +275,7 @@ __device__ __forceinline__ void run_task_hex_shared(const SweepArgs<T> &A, uint4
                 const int32_t n = __ldg(&cg->nbr[f]);
                 T uv[4];
                 if (n >= 0) {
-                    const uint32_t nm = __ldg(&cg->nmap[f]);
-                    const T *up = psi + (psi_dir + (size_t)n) * 8 * (size_t)G + g;
-#pragma unroll
-                    for (int l = 0; l < 4; ++l) uv[l] = __ldcg(up + (size_t)((nm >> (4 * l)) & 15u) * G);
+                    hex_upwind(A, cg, ti.x + k, f, n, g, psi_dir, uv);
                 } else if (A.psi_in) {  // prescribed inflow at the face's vertices
 #pragma unroll
                     for (int l = 0; l < 4; ++l)

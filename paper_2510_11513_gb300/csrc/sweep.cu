@@ -688,6 +688,13 @@ struct DeviceState {
     void *psi_in = nullptr;
     int4 *tets = nullptr;
     int32_t *hexv = nullptr;   // hexahedra with prescribed inflow: [C][8] global vertices
+    // lagged back edges (hexahedra): per cell entry (lag mask << 26) | first slot; per slot its
+    // direction and (cell << 3) | face; the previous step's upwind values [slot][4][G] (T)
+    uint32_t *lagw = nullptr;
+    uint32_t *lag_slots = nullptr;
+    void *lagbuf = nullptr;
+    std::vector<int64_t> lag_dir_begin;
+    int64_t n_lag = 0;
     void *q = nullptr;
     void *psi = nullptr;
     double *vol4 = nullptr;
@@ -1559,6 +1566,18 @@ tf_status device_create(Problem &p, const int32_t *cell_material, const double *
     p.stats.warps_per_cta = d.wpc;
     p.stats.cells_per_task = g.cells_per_task;
     p.stats.task_shape = g.patches ? TF_TASK_PATCHES : TF_TASK_LEVELS;
+    p.stats.lagged_faces = g.n_lagged();
+    if (g.n_lagged() > 0) {
+        // lag words and slots; the lag buffer starts at zero (the first step's lagged faces see
+        // no inflow from the previous step)
+        d.n_lag = g.n_lagged();
+        d.lag_dir_begin = g.lag_dir_begin;
+        if ((s = upload(d, &d.lagw, g.cell_lag.data(), g.cell_lag.size() * 4)) != TF_OK) return s;
+        if ((s = upload(d, &d.lag_slots, g.lag_slots.data(), g.lag_slots.size() * 4)) != TF_OK) return s;
+        const size_t lb = (size_t)d.n_lag * 4 * d.G * d.tsize;
+        if ((s = dmalloc(d, &d.lagbuf, lb)) != TF_OK) return s;
+        TF_CUDA(cudaMemset(d.lagbuf, 0, lb));
+    }
     return TF_OK;
 }
 
@@ -1688,6 +1707,38 @@ void launch_stats(Problem &p, const double *cur, const double *nxt, cudaStream_t
 }
 
 // Sweep arguments of direction chunk k of one problem (queue fields for a launch of its own).
+// Lagged back edges: after a chunk's sweep, the upwind values each lagged face of the chunk's
+// directions will read in the next transport step (thread per slot, face-local node, group).
+template <class T>
+__global__ void lag_gather_kernel(const uint32_t *__restrict__ slots, int64_t s0, int64_t s1,
+                                  const HexGeo<T> *__restrict__ geo, const T *__restrict__ psi, int dir_begin, int64_t C,
+                                  int G, T *__restrict__ lagbuf)
+{
+    const int64_t n = (s1 - s0) * 4 * G;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t s = s0 + i / (4 * G);
+        const int l = (int)((i / G) % 4), g = (int)(i % G);
+        const uint32_t a = slots[2 * s], cf = slots[2 * s + 1];
+        const uint32_t c = cf >> 3, f = cf & 7u;
+        const int32_t nb = geo[c].nbr[f];
+        const uint32_t node = (geo[c].nmap[f] >> (4 * l)) & 15u;
+        lagbuf[(s * 4 + l) * G + g] = psi[(((int64_t)a - dir_begin) * C + nb) * 8 * G + (int64_t)node * G + g];
+    }
+}
+
+template <class T> void launch_lag_gather(Problem &p, int k, cudaStream_t st)
+{
+    DeviceState &d = *p.dev;
+    if (d.n_lag == 0) return;
+    const int a0 = k * d.Dc, a1 = std::min(d.D, a0 + d.Dc);
+    const int64_t s0 = d.lag_dir_begin[a0], s1 = d.lag_dir_begin[a1];
+    if (s1 <= s0) return;
+    const int64_t n = (s1 - s0) * 4 * d.G;
+    const int nb = (int)std::min<int64_t>((n + 255) / 256, (int64_t)d.sm_count * 8);
+    lag_gather_kernel<T><<<nb, 256, 0, st>>>(d.lag_slots, s0, s1, (const HexGeo<T> *)d.geo2, (const T *)d.psi, a0,
+                                             d.C, d.G, (T *)d.lagbuf);
+}
+
 template <class T> SweepArgs<T> make_args(Problem &p, int k)
 {
     DeviceState &d = *p.dev;
@@ -1711,6 +1762,8 @@ template <class T> SweepArgs<T> make_args(Problem &p, int k)
     A.psi_in = (const T *)d.psi_in;
     A.tets = d.tets;
     A.hexv = d.hexv;
+    A.lagw = d.lagw;
+    A.lagbuf = (const T *)d.lagbuf;
     A.C = d.C;
     A.G = d.G;
     A.dir_begin = a0;
@@ -1839,6 +1892,7 @@ template <class T> tf_status launch_step(Problem &p, const double *phi_in, doubl
             }
             TF_CUDA(record_event(d.ev_stop[1 + 2 * k], st));
             end_kernel<<<1, 1, 0, st>>>(d.ctrl);
+            launch_lag_gather<T>(p, k, st);
             TF_CUDA(record_event(d.ev_start[2 + 2 * k], st));
             launch_phi<T>(p, k, phi_out, st);
             TF_CUDA(cudaGetLastError());
@@ -1883,6 +1937,7 @@ template <class T> tf_status launch_step(Problem &p, const double *phi_in, doubl
         TF_CUDA(cudaGetLastError());
         TF_CUDA(record_event(d.ev_stop[1 + 2 * k], st));
         end_kernel<<<1, 1, 0, st>>>(d.ctrl);
+        launch_lag_gather<T>(p, k, st);
         TF_CUDA(record_event(d.ev_start[2 + 2 * k], st));
         launch_phi<T>(p, k, phi_out, st);
         TF_CUDA(cudaGetLastError());
@@ -2177,6 +2232,7 @@ tf_status batch_setup(BatchRun &B, const tf_handle *problems, int32_t n)
             return fail(TF_ERR_ARG, "batched problems must share one device and one precision");
         if (p->opt.inject_stall) return fail(TF_ERR_ARG, "inject_stall is not supported in batched launches");
         if (p->reduce) return fail(TF_ERR_ARG, "a problem with a reduce function (direction sharding) cannot be batched");
+        if (p->dev->n_lag > 0) return fail(TF_ERR_ARG, "a problem with lagged back edges cannot be batched");
         if (p->dev->schedule != TF_SCHED_AMT || p->dev->order != 1)
             return fail(TF_ERR_ARG, "batched launches run only linear tetrahedra and trilinear hexahedra with the "
                                     "TF_SCHED_AMT schedule");

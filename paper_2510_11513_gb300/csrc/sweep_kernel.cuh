@@ -160,6 +160,10 @@ template <class T> struct SweepArgs {
     const T *psi_in;            // [nv][G] or NULL
     const int4 *tets;           // [C] (only with psi_in)
     const int32_t *hexv;        // hexahedra: [C][8] global vertices (only with psi_in)
+    // hexahedra with lagged back edges (else NULL): per cell entry (lag mask << 26) | first slot,
+    // and per slot the upwind values of the previous transport step, [slot][face-local node][G]
+    const uint32_t *lagw;
+    const T *lagbuf;
     int64_t C;
     int32_t G;
     int32_t dir_begin;          // first direction of the chunk

@@ -80,6 +80,13 @@ struct TaskGraph {
     std::vector<uint32_t> cell_list;       // (cell << cell_shift) | inflow mask, [D * nc]
     int32_t cell_shift = 4;                // 4 for tetrahedra, 6 for hexahedra (one mask bit per face)
     bool patches = false;                  // spatial patches: a task's cells may depend on each other
+    // lagged back edges (empty when there are none): per cell entry (lag mask << 26) | first
+    // slot; per slot its direction and (cell << 3) | face; slots of direction a are
+    // [lag_dir_begin[a], lag_dir_begin[a + 1])
+    std::vector<uint32_t> cell_lag;        // [D * nc] or empty
+    std::vector<uint32_t> lag_slots;       // [2 * n_slots]
+    std::vector<int64_t> lag_dir_begin;    // [D + 1]
+    int64_t n_lagged() const { return lag_dir_begin.empty() ? 0 : lag_dir_begin.back(); }
     int64_t T() const { return (int64_t)task_ncell.size(); }
 };
 
@@ -97,9 +104,10 @@ tf_status task_shape_of(const tf_options &o, const Mesh &m, int32_t G, bool *pat
 tf_status task_grain(const tf_options &o, const Mesh &m, int32_t G, int32_t *B, bool *patches, TaskShape *shape);
 
 // Face classification and levels only (no tasks); returns TF_ERR_CYCLE on a cycle.
-tf_status classify_and_level(const Mesh &m, const Quad &q, uint8_t *inflow, int32_t *level);
+// lag (non-null, [D][nc]): break cycles by lagged back edges instead of failing.
+tf_status classify_and_level(const Mesh &m, const Quad &q, uint8_t *inflow, int32_t *level, uint8_t *lag = nullptr);
 tf_status build_task_graph(const Mesh &m, const Quad &q, int32_t cells_per_task, TaskGraph &g,
-                           const TaskShape *shape = nullptr);
+                           const TaskShape *shape = nullptr, bool lag_cycles = false);
 
 struct DeviceState;  // defined in the CUDA part
 

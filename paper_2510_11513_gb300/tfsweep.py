@@ -28,7 +28,7 @@ TF_TASK_AUTO, TF_TASK_LEVELS, TF_TASK_PATCHES = 0, 1, 2
 
 SYMBOLS = (
     "tf_options_default", "tf_mesh_create", "tf_mesh_create_hex", "tf_mesh_hex_integrals", "tf_quadrature_create", "tf_problem_create", "tf_sweep",
-    "tf_source_iterate", "tf_destroy", "tf_mesh_geometry", "tf_quadrature_get", "tf_graph_levels", "tf_graph_tasks",
+    "tf_source_iterate", "tf_destroy", "tf_mesh_geometry", "tf_quadrature_get", "tf_graph_levels", "tf_graph_lag", "tf_graph_tasks",
     "tf_problem_psi", "tf_problem_set_reduce", "tf_problem_stats", "tf_status_string", "tf_last_error", "tf_integrated_flux_noalloc",
     # include/tflearn.h
     "tf_mlp_create", "tf_mlp_params", "tf_mlp_scale", "tf_mlp_limits", "tf_mlp_fit_inputs",
@@ -47,7 +47,7 @@ class tf_options(C.Structure):
         ("pairing", C.c_int32), ("schedule", C.c_int32), ("order", C.c_int32),
         ("keep_ready", C.c_int32), ("task_shape", C.c_int32),
         ("residual_floor", C.c_double), ("patch_extent", C.c_double),
-        ("reserved_d", C.c_double * 2),
+        ("lag_cycles", C.c_int32), ("reserved_i", C.c_int32), ("reserved_d", C.c_double * 1),
     ]
 
 
@@ -72,7 +72,7 @@ class tf_stats(C.Structure):
         ("tuned_cached", C.c_int32), ("tuned_candidates", C.c_int32 * 8), ("tuned_seconds", C.c_double * 8),
         ("n_buckets", C.c_int32), ("tuned_pairing", C.c_int32), ("tuned_staging", C.c_int32),
         ("tuned_window", C.c_int32), ("task_shape", C.c_int32), ("data_wait_seconds", C.c_double),
-        ("reserved_d", C.c_double * 5),
+        ("lagged_faces", C.c_int64), ("reserved_d", C.c_double * 4),
     ]
 
 
@@ -118,6 +118,7 @@ def load(build_if_missing: bool = True):
     lib.tf_mesh_geometry.argtypes = [H, C.POINTER(i64), C.POINTER(i64), vp, vp, vp, vp]
     lib.tf_quadrature_get.argtypes = [H, C.POINTER(i32), vp, vp]
     lib.tf_graph_levels.argtypes = [H, H, vp, vp]
+    lib.tf_graph_lag.argtypes = [H, H, vp, vp, vp]
     lib.tf_graph_tasks.argtypes = [H, H, C.POINTER(tf_options), i32, C.POINTER(i64), vp, vp, vp]
     lib.tf_problem_psi.argtypes = [H, i32, vp, vp]
     lib.tf_problem_stats.argtypes = [H, C.POINTER(tf_stats)]
@@ -296,6 +297,15 @@ def tf_graph_levels(mesh, quad, n_cells, n_dirs):
     level = np.zeros((n_dirs, n_cells), np.int32)
     _check(load().tf_graph_levels(mesh, quad, _ptr(inflow), _ptr(level)), "tf_graph_levels")
     return inflow, level
+
+
+def tf_graph_lag(mesh, quad, n_cells, n_dirs):
+    """(inflow, level, lag) with cycles broken by lagged back edges (tf_options.lag_cycles)."""
+    inflow = np.zeros((n_dirs, n_cells), np.uint8)
+    level = np.zeros((n_dirs, n_cells), np.int32)
+    lag = np.zeros((n_dirs, n_cells), np.uint8)
+    _check(load().tf_graph_lag(mesh, quad, _ptr(inflow), _ptr(level), _ptr(lag)), "tf_graph_lag")
+    return inflow, level, lag
 
 
 def tf_graph_tasks(mesh, quad, n_cells, n_dirs, n_groups, opts=None):

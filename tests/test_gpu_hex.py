@@ -218,3 +218,73 @@ def test_batched_hexahedra_with_tetrahedra(precision):
     for c, x, o in zip(cfgs[:2], ins[:2], outs[:2]):
         ref = oh.ProblemHex(c).transport_step(x, threads=8)
         assert _rel(o.cpu().numpy(), ref) < TOL[precision]
+
+
+# ------------------------------------------------- lagged back edges (grids with cyclic sweep graphs)
+def _cyclic(G, n=4, seed=5):
+    cfg = W.hex_problem(W.small_box(n=n, G=G, n_polar=8, n_az=16, seed=seed), twist=0.6)
+    cfg["Q"] = np.random.default_rng(seed).uniform(0.0, 1.0, cfg["Q"].shape)
+    return cfg
+
+
+@pytest.mark.parametrize("precision", [tf.TF_FP64, tf.TF_FP32])
+@pytest.mark.parametrize("G,opts", [(3, {}), (8, {}), (8, dict(staging=1)), (32, dict(dir_chunk=37))])
+def test_lagged_steps_match_oracle(precision, G, opts):
+    """Two consecutive transport steps with lag_cycles: the first reads zero on the lagged faces,
+    the second the first step's psi (gathered after each direction chunk's sweep); both against
+    the oracle's steps, in both hexahedral modes and over several direction chunks."""
+    cfg = _cyclic(G)
+    P = oh.ProblemHex(cfg, lag=True)
+    prob = tf.Problem.from_config(cfg, precision=precision, lag_cycles=1, **opts)
+    assert prob.stats()["lagged_faces"] == int(np.unpackbits(P.lag).sum()) > 0
+    phi = np.random.default_rng(13).uniform(0.0, 1.0, (P.C, G, 8))
+    for _ in range(2):
+        ref = P.transport_step(phi, threads=8)
+        out = torch.zeros_like(_dev(phi))
+        prob.sweep(_dev(phi), out)
+        assert _rel(out.cpu().numpy(), ref) < TOL[precision]
+        phi = ref
+    st = prob.stats()
+    assert st["tasks_executed"] == st["n_tasks"]
+    assert st["kernel_mode"] == (9 if G >= 8 and opts.get("staging", 0) != 1 else 8)
+
+
+@pytest.mark.parametrize("precision", [tf.TF_FP64, tf.TF_FP32])
+def test_lagged_source_iteration_matches_oracle(precision):
+    """Converged source iteration with lagged faces against the oracle's (whose fixed point is
+    pinned to the lag-free dense solves)."""
+    cfg = _cyclic(4)
+    P = oh.ProblemHex(cfg, lag=True)
+    ref, it_ref, _ = P.source_iterate(1e-10, 2000, threads=8)
+    prob = tf.Problem.from_config(cfg, precision=precision, lag_cycles=1)
+    phi = torch.zeros((P.C, 4, 8), dtype=torch.float64, device="cuda")
+    res = prob.source_iterate(phi, 1e-10 if precision == tf.TF_FP64 else 1e-6, 2000)
+    assert res["converged"]
+    if precision == tf.TF_FP64:
+        assert abs(res["iterations"] - it_ref) <= 1
+    assert _rel(phi.cpu().numpy(), ref) < (1e-8 if precision == tf.TF_FP64 else 2e-5)
+    assert res["balance"] < (1e-8 if precision == tf.TF_FP64 else 1e-5), res["balance"]
+
+
+@pytest.mark.parametrize("schedule", [tf.TF_SCHED_BSP, tf.TF_SCHED_BSP_LAUNCH])
+def test_lagged_bulk_synchronous_schedules_same_result(schedule):
+    cfg = _cyclic(8)
+    a = tf.Problem.from_config(cfg, lag_cycles=1)
+    b = tf.Problem.from_config(cfg, lag_cycles=1, schedule=schedule)
+    phi = _dev(np.random.default_rng(2).uniform(0.0, 1.0, (len(cfg["hexes"]), 8, 8)))
+    for _ in range(2):
+        out_a, out_b = torch.zeros_like(phi), torch.zeros_like(phi)
+        a.sweep(phi, out_a)
+        b.sweep(phi, out_b)
+        assert torch.equal(out_a, out_b)
+        phi = out_a
+
+
+def test_lagged_problem_is_not_batched():
+    cfg = _cyclic(3)
+    a = tf.Problem.from_config(cfg, lag_cycles=1)
+    b = tf.Problem.from_config(_box(n=3, G=3))
+    phis = [torch.zeros((p.n_cells, 3, 8), dtype=torch.float64, device="cuda") for p in (a, b)]
+    with pytest.raises(tf.TfError) as e:
+        tf.sweep_batch([a, b], phis, phis)
+    assert e.value.status == tf.TF_ERR_ARG

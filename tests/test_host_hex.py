@@ -105,3 +105,83 @@ def test_graph_bit_exact_paper_sized_workload():
     inflow, level = tf.tf_graph_levels(m.h, q.h, m.n_cells, q.n_dirs)
     assert np.array_equal(inflow, inflow_ref) and np.array_equal(level, level_ref)
     assert level.max() + 1 == 61
+
+
+# ------------------------------------------------------------- lagged back edges
+@pytest.mark.parametrize("n,twist,jitter,npol,naz", [(4, 0.6, 0.0, 8, 16), (8, 0.5, 0.0, 8, 16),
+                                                      (5, 1.3, 0.15, 4, 16), (8, 0.25, 0.0, 8, 16)])
+def test_lag_sets_match_the_oracle(n, twist, jitter, npol, naz):
+    """tf_graph_lag picks the same lagged faces as the oracle (the same cycle walk), with the
+    same inflow masks and levels; an acyclic grid gets none."""
+    cfg = W.hex_problem(W.small_box(n=n, G=1, n_polar=npol, n_az=naz), twist=twist, jitter=jitter)
+    geom = H.geometry(cfg["xyz"], cfg["hexes"])
+    om, _ = product_quadrature(npol, naz)
+    inflow, level, lag = H.graph(geom, om, lag=True)
+    m = tf.HexMesh(cfg["xyz"], cfg["hexes"])
+    q = tf.Quadrature(npol, naz)
+    i2, l2, g2 = tf.tf_graph_lag(m.h, q.h, m.n_cells, q.n_dirs)
+    assert np.array_equal(inflow, i2) and np.array_equal(level, l2) and np.array_equal(lag, g2)
+    assert lag.any() == (twist > 0.3)
+
+
+def test_lagged_task_graph_is_acyclic_with_the_non_lagged_in_degrees():
+    """Tasks of a problem with lag_cycles on a grid with cycles: every (direction, cell) once,
+    in-degrees = distinct upwind tasks across non-lagged faces, and an acyclic task graph."""
+    cfg = W.hex_problem(W.small_box(n=6, G=4, n_polar=8, n_az=16), twist=0.5)
+    geom = H.geometry(cfg["xyz"], cfg["hexes"])
+    om, _ = product_quadrature(8, 16)
+    inflow, _, lag = H.graph(geom, om, lag=True)
+    assert lag.any()
+    m = tf.HexMesh(cfg["xyz"], cfg["hexes"])
+    q = tf.Quadrature(8, 16)
+    with pytest.raises(tf.TfError) as e:
+        tf.tf_graph_tasks(m.h, q.h, m.n_cells, q.n_dirs, 4)
+    assert e.value.status == tf.TF_ERR_CYCLE
+    task_of, position, indeg = tf.tf_graph_tasks(m.h, q.h, m.n_cells, q.n_dirs, 4, tf.options(lag_cycles=1))
+    D, C = task_of.shape
+    T = len(indeg)
+    nbr = geom["nbr"]
+    edges = set()
+    for a in range(D):
+        for c in range(C):
+            for f in range(6):
+                u = nbr[c, f]
+                if (inflow[a, c] >> f & 1) and u >= 0 and not (lag[a, c] >> f & 1):
+                    assert task_of[a, u] != task_of[a, c]  # t-level blocks hold independent cells
+                    edges.add((int(task_of[a, u]), int(task_of[a, c])))
+    assert sorted(np.unique(task_of)) == list(range(T))
+    deg = np.zeros(T, np.int64)
+    for _, t in edges:
+        deg[t] += 1
+    assert np.array_equal(deg, indeg)
+    out = {}
+    for s_, t in edges:
+        out.setdefault(s_, []).append(t)
+    ready = list(np.flatnonzero(deg == 0))
+    seen = 0
+    while ready:
+        s_ = ready.pop()
+        seen += 1
+        for t in out.get(s_, []):
+            deg[t] -= 1
+            if deg[t] == 0:
+                ready.append(t)
+    assert seen == T
+
+
+def test_lag_option_rejections():
+    """lag_cycles takes 0 or 1, hexahedral meshes and t-level tasks (checked before any device work)."""
+    cfg = W.hex_problem(W.small_box(n=2, G=1, n_polar=2, n_az=4), twist=0.25)
+    m = tf.HexMesh(cfg["xyz"], cfg["hexes"])
+    q = tf.Quadrature(2, 4)
+    C = m.n_cells
+    args = (m.h, q.h, 1, 1, np.zeros(C, np.int32), np.ones((1, 1)), np.zeros((1, 1, 1)), np.zeros((C, 1, 8)))
+    for o in (tf.options(lag_cycles=2), tf.options(lag_cycles=1, task_shape=tf.TF_TASK_PATCHES)):
+        with pytest.raises(tf.TfError) as e:
+            tf.tf_problem_create(*args, opt=o)
+        assert e.value.status == tf.TF_ERR_ARG
+    tet = tf.Mesh(*W.jittered_kuhn_mesh(2, 1))
+    with pytest.raises(tf.TfError) as e:
+        tf.tf_problem_create(tet.h, q.h, 1, 1, np.zeros(tet.n_cells, np.int32), np.ones((1, 1)), np.zeros((1, 1, 1)),
+                             np.zeros((tet.n_cells, 1, 4)), opt=tf.options(lag_cycles=1))
+    assert e.value.status == tf.TF_ERR_ARG
