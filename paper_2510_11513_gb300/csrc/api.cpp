@@ -94,8 +94,10 @@ tf_status task_grain(const tf_options &o, const Mesh &m, int32_t n_groups, int32
         // critical path: on the 16^3-hex box, 128 directions, 16 groups, 4 cells per task left the
         // warps waiting a quarter of the sweep, 1 or 2 cells under 13 %)
         if (o.order == 3) b = std::max(1, std::min(16, 32 / n_groups));
-        // trilinear hexahedra: an 8 x 8 solve, about 256 units per task as the second order
-        if (m.nf == 6) b = std::max(2, std::min(32, 256 / n_groups));
+        // trilinear hexahedra: an 8 x 8 solve, about 256 units per task and at most 8 cells when the
+        // shared-matrix mode runs (G >= 8): on the paper's 16^3 grid (256 directions, 10 groups) 25
+        // cells per task left the warps waiting 65 % of the sweep (3.5 ms), 8 cells 30 % (2.1 ms)
+        if (m.nf == 6) b = std::max(2, std::min(n_groups >= 8 ? 8 : 32, 256 / n_groups));
         // Bulk-synchronous schedules: a bucket's tasks must cover the resident warps, and
         // most buckets hold fewer cells than the many-task grain assumes; a quarter of it
         // (at least 2 cells) took the least time over grains 1..64 on the 16^3-hex,
