@@ -83,11 +83,13 @@ tf_status task_grain(const tf_options &o, const Mesh &m, int32_t n_groups, int32
     if (b == 0 && *patches) {
         b = 64;  // larger patches are cut into pieces of at most 64 cells (a warp's two entry registers)
     } else if (b == 0) {
-        // about 1024 units per task (at most 64 cells); 256 units and 4 to 16 cells on the
-        // FP32 paired path, whose per-task cell table sets how many CTAs fit per SM
+        // about 1024 units per task (at most 64 cells); 256 units and 4 to 8 cells on the
+        // FP32 paired path, whose per-task cell table sets how many CTAs fit per SM (on the
+        // 16^3 box with 128 directions and 16 groups, 16 cells per task left the warps waiting
+        // 63 % of the sweep, 8 cells 42 % and 19 % less time)
         const bool paired = o.precision == TF_FP32 && n_groups % 2 == 0 &&
                             (o.pairing == 2 || (o.pairing == 0 && n_groups % 32 != 0));
-        b = paired ? std::max(4, std::min(16, 256 / n_groups)) : std::max(2, std::min(64, 1024 / n_groups));
+        b = paired ? std::max(4, std::min(8, 256 / n_groups)) : std::max(2, std::min(64, 1024 / n_groups));
         // second order: a unit is a 10 x 10 solve, about 256 units per task
         if (o.order == 2) b = std::max(2, std::min(32, 256 / n_groups));
         // third order: a unit is a 20 x 20 solve, about 32 units per task (a task's time sets the
