@@ -92,10 +92,10 @@ tf_status task_grain(const tf_options &o, const Mesh &m, int32_t n_groups, int32
         b = paired ? std::max(4, std::min(8, 256 / n_groups)) : std::max(2, std::min(64, 1024 / n_groups));
         // second order: a unit is a 10 x 10 solve, about 256 units per task
         if (o.order == 2) b = std::max(2, std::min(32, 256 / n_groups));
-        // third order: a unit is a 20 x 20 solve, about 32 units per task (a task's time sets the
-        // critical path: on the 16^3-hex box, 128 directions, 16 groups, 4 cells per task left the
-        // warps waiting a quarter of the sweep, 1 or 2 cells under 13 %)
-        if (o.order == 3) b = std::max(1, std::min(16, 32 / n_groups));
+        // third order: a unit is a 20 x 20 solve, about 64 units per task (a task's time sets the
+        // critical path; with the source values prefetched a pass ahead, 3 to 4 cells per task took
+        // the least time on the 16^3-hex box, 128 directions, 16 groups)
+        if (o.order == 3) b = std::max(1, std::min(16, 64 / n_groups));
         // trilinear hexahedra: an 8 x 8 solve, about 256 units per task and at most 8 cells when the
         // shared-matrix mode runs (G >= 8): on the paper's 16^3 grid (256 directions, 10 groups) 25
         // cells per task left the warps waiting 65 % of the sweep (3.5 ms), 8 cells 30 % (2.1 ms)

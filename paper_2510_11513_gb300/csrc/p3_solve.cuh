@@ -42,7 +42,17 @@ static_assert(sizeof(P3Dev<float>) % 16 == 0 && sizeof(P3Dev<double>) % 16 == 0,
 // eight units (row and right-hand side; a stride of 28 values puts the eight units' 16-byte
 // pieces in distinct banks)
 constexpr int P3_PSTRIDE = 28;
-template <class T> constexpr uint32_t p3_warp_bytes() { return (uint32_t)((400 + 2 * 8 * P3_PSTRIDE) * sizeof(T)); }
+// and two buffers of the source values of a pass (20 nodes x 8 groups), filled one pass ahead
+template <class T> constexpr uint32_t p3_warp_bytes() { return (uint32_t)((400 + 2 * 8 * P3_PSTRIDE + 2 * 160) * sizeof(T)); }
+
+// one value copied asynchronously into shared memory (through L1: the source is read-only here)
+template <class T> __device__ __forceinline__ void cp_async_elem(T *dst, const T *src)
+{
+    if constexpr (sizeof(T) == 4)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
 
 // lattice index of node i in coordinate k (compile-time structure of the element)
 __host__ __device__ constexpr int p3_alpha(int i, int k)
@@ -112,10 +122,28 @@ __device__ __forceinline__ void run_task_p3(const SweepArgs<T> &A, uint4 ti, int
     const P3Geo<T> *geo = reinterpret_cast<const P3Geo<T> *>(A.geo2);
     T *Wc = reinterpret_cast<T *>(wsm);  // [20][20]
     T *piv = Wc + 400;                   // [2][8][P3_PSTRIDE]: pivot row (20) and right-hand side (at 20) per unit
+    T *qbuf = piv + 2 * 8 * P3_PSTRIDE;  // [2][20][8]: the source values of a pass, by node and unit
     const int G = A.G;
     const uint32_t ncell = ti.y & 0xffffu;
     const int slot = lane & 7, sub = lane >> 3;
     T *psi = reinterpret_cast<T *>(A.psi);
+    const T *qg = reinterpret_cast<const T *>(A.q);
+    // pass p of the task = (cell p / npass, groups 8 (p % npass) ...); its source values are copied
+    // into qbuf[p & 1] while pass p - 1 computes
+    const uint32_t npass = ((uint32_t)G + 7u) / 8u, n_pass = ncell * npass;
+    auto issue_q = [&](uint32_t pp) {
+        const uint32_t kq = pp / npass;
+        const int gq = (int)(pp - kq * npass) * 8;
+        const T *qc = qg + (size_t)(__ldg(A.cells + ti.x + kq) >> 4) * 20 * G;
+        T *dst = qbuf + (pp & 1u) * 160;
+        for (int t = lane; t < 160; t += 32) {
+            const int j = t >> 3, u = t & 7;
+            cp_async_elem(dst + t, qc + (size_t)j * G + (gq + u < G ? gq + u : gq));
+        }
+        cp_async_commit();
+    };
+    issue_q(0);
+    uint32_t pass = 0;
     for (uint32_t kc = 0; kc < ncell; ++kc) {
         const uint32_t e = __ldg(A.cells + ti.x + kc);
         const uint32_t c = e >> 4, mask = e & 15u;
@@ -152,11 +180,14 @@ __device__ __forceinline__ void run_task_p3(const SweepArgs<T> &A, uint4 ti, int
             const bool live = g0 + slot < G;
             const int g = live ? g0 + slot : g0;  // an idle slot repeats a live group and discards it
             const T sv = V * __ldg(A.sigma_t + (size_t)mat * G + g);
-            const T *qc = reinterpret_cast<const T *>(A.q) + (size_t)c * 20 * G + g;
+            // this pass's source values arrived; every lane is done with the buffer refilled next
+            cp_async_wait<0>();
+            __syncwarp();
+            if (pass + 1 < n_pass) issue_q(pass + 1);
+            const T *qs = qbuf + (pass & 1u) * 160 + slot;
+            ++pass;
             // upwind faces first: b = sum_f s_f F_f psi_up on the face's rows (one loop body for the four faces)
-            T b[5], q[20];
-#pragma unroll
-            for (int j = 0; j < 20; ++j) q[j] = __ldg(qc + (size_t)j * G);
+            T b[5];
 #pragma unroll
             for (int r = 0; r < 5; ++r) b[r] = T(0);
 #pragma unroll 1
@@ -201,7 +232,7 @@ __device__ __forceinline__ void run_task_p3(const SweepArgs<T> &A, uint4 ti, int
 #pragma unroll
                         for (int t = 0; t < 4; ++t) {
                             a[r][4 * j4 + t] = w.v[t] + sv * m.v[t];
-                            bi += m.v[t] * q[4 * j4 + t];
+                            bi += m.v[t] * qs[8 * (4 * j4 + t)];
                         }
                     }
                     b[r] += V * bi;
