@@ -104,7 +104,9 @@ tf_status task_grain(const tf_options &o, const Mesh &m, int32_t n_groups, int32
         // most buckets hold fewer cells than the many-task grain assumes; a quarter of it
         // (at least 2 cells) took the least time over grains 1..64 on the 16^3-hex,
         // 128-direction, 16-group and the 48^3-hex, 192-direction, 64-group boxes.
-        if (o.schedule != TF_SCHED_AMT) b = std::max(2, b / 4);
+        // (the quarter of the paired path's former 16-cell grain, where those measurements were made)
+        if (o.schedule != TF_SCHED_AMT)
+            b = std::max(2, (paired && o.order <= 1 && m.nf == 4 ? std::max(4, std::min(16, 256 / n_groups)) : b) / 4);
     }
     if (*patches && b > 64) return fail(TF_ERR_ARG, "spatial patches hold at most 64 cells");
     *B = b;

@@ -70,10 +70,17 @@ def test_bsp_sweep_matches_oracle_and_amt_bitwise(schedule, precision, G, opts):
     assert np.array_equal(b, out_a.cpu().numpy())
     st = bsp.stats()
     assert st["tasks_executed"] == st["n_tasks"]
-    if "cells_per_task" not in opts:  # the bulk-synchronous default grain: a quarter of the t-level blocks', at least 2
-        lv = tf.Problem.from_config(cfg, precision=precision, task_shape=tf.TF_TASK_LEVELS, **opts)
-        assert st["cells_per_task"] == max(2, lv.stats()["cells_per_task"] // 4)
-        lv.close()
+    if "cells_per_task" not in opts:
+        # the bulk-synchronous default grain: a quarter of the t-level blocks', at least 2; on the
+        # packed-pairs path a quarter of 256 / G cells (at most 16), the grain it was measured at
+        pairing = opts.get("pairing", 0)
+        paired = precision == tf.TF_FP32 and G % 2 == 0 and (pairing == 2 or (pairing == 0 and G % 32 != 0))
+        if paired:
+            assert st["cells_per_task"] == max(2, max(4, min(16, 256 // G)) // 4)
+        else:
+            lv = tf.Problem.from_config(cfg, precision=precision, task_shape=tf.TF_TASK_LEVELS, **opts)
+            assert st["cells_per_task"] == max(2, lv.stats()["cells_per_task"] // 4)
+            lv.close()
     assert st["n_buckets"] == _expected_buckets(P, opts.get("dir_chunk", 0))
     assert amt.stats()["n_buckets"] == 0
     # psi of one direction too (the rows the downwind tasks consumed; the last chunk's)
