@@ -391,10 +391,14 @@ def run_ours(args):
     import paper_2510_11513_gb300 as tf
 
     world, rank, local = _dist()
+    torch.cuda.set_device(local)  # before the process group: NCCL binds each rank to its current device
     if world > 1:
+        import datetime
+
         import torch.distributed as dist
-        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
-    torch.cuda.set_device(local)
+        # a rank that fails ends the others' next collective with an error instead of a long wait
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo",
+                                timeout=datetime.timedelta(minutes=5))
     dev = torch.device("cuda", local)
     cfg = make_config(args)
     if args.order >= 2:
