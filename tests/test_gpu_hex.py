@@ -288,3 +288,23 @@ def test_lagged_problem_is_not_batched():
     with pytest.raises(tf.TfError) as e:
         tf.sweep_batch([a, b], phis, phis)
     assert e.value.status == tf.TF_ERR_ARG
+
+
+@pytest.mark.parametrize("precision", [tf.TF_FP64, tf.TF_FP32])
+def test_lagged_steps_with_inflow_and_s1_match_oracle(precision):
+    """Lagged back edges together with prescribed boundary inflow and the S1 source: two
+    consecutive transport steps against the oracle."""
+    cfg = _cyclic(8)
+    C, nv = len(cfg["hexes"]), len(cfg["xyz"])
+    rng = np.random.default_rng(29)
+    S1 = rng.uniform(-1.0, 1.0, (C, 8, 3))
+    psi_in = rng.uniform(0.0, 1.0, (nv, 8))
+    P = oh.ProblemHex(cfg, S1=S1, psi_in=psi_in, lag=True)
+    prob = tf.Problem.from_config(cfg, S1=S1, psi_inflow=psi_in, precision=precision, lag_cycles=1)
+    phi = rng.uniform(0.0, 1.0, (C, 8, 8))
+    for _ in range(2):
+        ref = P.transport_step(phi, threads=8)
+        out = torch.zeros_like(_dev(phi))
+        prob.sweep(_dev(phi), out)
+        assert _rel(out.cpu().numpy(), ref) < TOL[precision]
+        phi = ref
