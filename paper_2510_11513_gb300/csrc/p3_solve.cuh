@@ -42,8 +42,9 @@ static_assert(sizeof(P3Dev<float>) % 16 == 0 && sizeof(P3Dev<double>) % 16 == 0,
 // eight units (row and right-hand side; a stride of 28 values puts the eight units' 16-byte
 // pieces in distinct banks)
 constexpr int P3_PSTRIDE = 28;
+constexpr int P3_PSTRIDE2 = 60;  // two pivot rows per unit (at 0 and 28); 60 keeps the units' pieces in distinct banks
 // and two buffers of the source values of a pass (20 nodes x 8 groups), filled one pass ahead
-template <class T> constexpr uint32_t p3_warp_bytes() { return (uint32_t)((400 + 2 * 8 * P3_PSTRIDE + 2 * 160) * sizeof(T)); }
+template <class T> constexpr uint32_t p3_warp_bytes() { return (uint32_t)((400 + 2 * 8 * P3_PSTRIDE2 + 2 * 160) * sizeof(T)); }
 
 // one value copied asynchronously into shared memory (through L1: the source is read-only here)
 template <class T> __device__ __forceinline__ void cp_async_elem(T *dst, const T *src)
@@ -121,8 +122,8 @@ __device__ __forceinline__ void run_task_p3(const SweepArgs<T> &A, uint4 ti, int
     const unsigned FULL = 0xffffffffu;
     const P3Geo<T> *geo = reinterpret_cast<const P3Geo<T> *>(A.geo2);
     T *Wc = reinterpret_cast<T *>(wsm);  // [20][20]
-    T *piv = Wc + 400;                   // [2][8][P3_PSTRIDE]: pivot row (20) and right-hand side (at 20) per unit
-    T *qbuf = piv + 2 * 8 * P3_PSTRIDE;  // [2][20][8]: the source values of a pass, by node and unit
+    T *piv = Wc + 400;                   // [2][8][P3_PSTRIDE2]: two pivot rows (20) and right-hand sides (at 20) per unit
+    T *qbuf = piv + 2 * 8 * P3_PSTRIDE2;  // [2][20][8]: the source values of a pass, by node and unit
     const int G = A.G;
     const uint32_t ncell = ti.y & 0xffffu;
     const int slot = lane & 7, sub = lane >> 3;
@@ -238,50 +239,70 @@ __device__ __forceinline__ void run_task_p3(const SweepArgs<T> &A, uint4 ti, int
                     b[r] += V * bi;
                 }
             }
-            // elimination: row k lives in lane (k & 3) of the four, register row k >> 2
+            // elimination two columns at a time: rows k and k + 1 (k even) live in lanes (k & 3) and
+            // (k & 3) + 1 of the four, both in register row k >> 2.  Both owners write their row (row
+            // k + 1 not yet reduced by row k) to the pivot buffer; every lane then reduces row k + 1
+            // by row k itself and applies the two pivot rows in the order of single steps.
 #pragma unroll
-            for (int k = 0; k < 20; ++k) {
-                const int owner = k & 3, rk = k >> 2, j0 = k & ~3;
-                T *pr = piv + (k & 1) * 8 * P3_PSTRIDE + slot * P3_PSTRIDE;
-                if (sub == owner) {
+            for (int k = 0; k < 20; k += 2) {
+                const int o0 = k & 3, rk = k >> 2, j0 = k & ~3;
+                T *pr = piv + ((k >> 1) & 1) * 8 * P3_PSTRIDE2 + slot * P3_PSTRIDE2;
+                if (sub == o0 || sub == o0 + 1) {
+                    T *dst = pr + (sub == o0 ? 0 : P3_PSTRIDE);
 #pragma unroll
-                    for (int j = j0; j < 20; j += 4) {
+                    for (int jj = j0; jj < 20; jj += 4) {
                         P3Vec<T> v;
 #pragma unroll
-                        for (int l = 0; l < 4; ++l) v.v[l] = a[rk][j + l];
-                        v.store(pr + j);
+                        for (int l = 0; l < 4; ++l) v.v[l] = a[rk][jj + l];
+                        v.store(dst + jj);
                     }
-                    pr[20] = b[rk];
+                    dst[20] = b[rk];
                 }
                 __syncwarp();
-                // the pivot row four columns at a time: first the piece holding the pivot
-                P3Vec<T> v;
-                v.load(pr + j0);
-                const T rp = rcp(v.v[k - j0]);
-                const T pb = pr[20];
-                T l[5];
+                // the piece of both rows holding columns k and k + 1
+                P3Vec<T> v0, v1;
+                v0.load(pr + j0);
+                v1.load(pr + P3_PSTRIDE + j0);
+                const T rp0 = rcp(v0.v[k - j0]);
+                const T m = v1.v[k - j0] * rp0;                        // row k + 1's multiplier of row k
+                const T rp1 = rcp(v1.v[k + 1 - j0] - m * v0.v[k + 1 - j0]);
+                const T pb0 = pr[20], pb1 = pr[P3_PSTRIDE + 20] - m * pb0;
+                T l0[5], l1[5];
+                bool u0[5], u1[5];  // this lane's row is below k / below k + 1
 #pragma unroll
-                for (int r = 0; r < 5; ++r) l[r] = a[r][k] * rp;
-                if (sub == owner) a[rk][k] = rp;  // the owner keeps the reciprocal for the back substitution
+                for (int r = 0; r < 5; ++r) {
+                    u0[r] = 4 * r + 3 > k && (4 * r > k || 4 * r + sub > k);
+                    u1[r] = 4 * r + 3 > k + 1 && (4 * r > k + 1 || 4 * r + sub > k + 1);
+                    l0[r] = a[r][k] * rp0;
+                    // column k + 1 after the reduction by row k, then its multiplier of row k + 1
+                    const T ak1 = a[r][k + 1] - l0[r] * v0.v[k + 1 - j0];
+                    l1[r] = ak1 * rp1;
+                }
+                if (sub == o0) a[rk][k] = rp0;  // the owners keep the reciprocals for the back substitution
 #pragma unroll
-                for (int j = j0; j < 20; j += 4) {
-                    if (j > j0) v.load(pr + j);
+                for (int jj = j0; jj < 20; jj += 4) {
+                    if (jj > j0) {
+                        v0.load(pr + jj);
+                        v1.load(pr + P3_PSTRIDE + jj);
+                    }
 #pragma unroll
                     for (int t = 0; t < 4; ++t) {
-                        if (j + t <= k) continue;
+                        if (jj + t <= k) continue;
+                        const T w1 = v1.v[t] - m * v0.v[t];  // row k + 1 reduced by row k
 #pragma unroll
                         for (int r = 0; r < 5; ++r) {
-                            if (4 * r + 3 <= k) continue;                  // rows of this slot are all at or above k
-                            if (4 * r <= k && 4 * r + sub <= k) continue;  // this lane's row is at or above k
-                            a[r][j + t] -= l[r] * v.v[t];
+                            if (4 * r + 3 <= k) continue;  // rows of this slot are all at or above k
+                            if (u0[r]) a[r][jj + t] -= l0[r] * v0.v[t];
+                            if (jj + t > k + 1 && u1[r]) a[r][jj + t] -= l1[r] * w1;
                         }
                     }
                 }
+                if (sub == o0 + 1) a[rk][k + 1] = rp1;
 #pragma unroll
                 for (int r = 0; r < 5; ++r) {
                     if (4 * r + 3 <= k) continue;
-                    if (4 * r <= k && 4 * r + sub <= k) continue;
-                    b[r] -= l[r] * pb;
+                    if (u0[r]) b[r] -= l0[r] * pb0;
+                    if (u1[r]) b[r] -= l1[r] * pb1;
                 }
             }
             // back substitution by columns: x_i from its owner, then removed from the rows above
