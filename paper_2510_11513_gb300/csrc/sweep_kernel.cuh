@@ -462,12 +462,21 @@ __device__ __forceinline__ void cp_async16(void *dst, const void *src)
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N> __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 // The entries gg = lane, lane + 32, ... < G of one row (V4<T> each) copied by the lane that reads them.
-template <class T> __device__ __forceinline__ void copy_row_own(V4<T> *dst, const V4<T> *src, int lane, int G)
+template <class T, int NPL = 0> __device__ __forceinline__ void copy_row_own(V4<T> *dst, const V4<T> *src, int lane, int G)
 {
-    for (int gg = lane; gg < G; gg += 32) {
+    if constexpr (NPL > 0) {  // G = 32 NPL: the lane's entries without a loop
 #pragma unroll
-        for (int h = 0; h < (int)(sizeof(V4<T>) / 16); ++h)
-            cp_async16(reinterpret_cast<char *>(dst + gg) + 16 * h, reinterpret_cast<const char *>(src + gg) + 16 * h);
+        for (int k = 0; k < NPL; ++k)
+#pragma unroll
+            for (int h = 0; h < (int)(sizeof(V4<T>) / 16); ++h)
+                cp_async16(reinterpret_cast<char *>(dst + lane + 32 * k) + 16 * h,
+                           reinterpret_cast<const char *>(src + lane + 32 * k) + 16 * h);
+    } else {
+        for (int gg = lane; gg < G; gg += 32) {
+#pragma unroll
+            for (int h = 0; h < (int)(sizeof(V4<T>) / 16); ++h)
+                cp_async16(reinterpret_cast<char *>(dst + gg) + 16 * h, reinterpret_cast<const char *>(src + gg) + 16 * h);
+        }
     }
 }
 
@@ -860,14 +869,14 @@ __device__ __forceinline__ bool run_task_staged(const SweepArgs<T> &A, uint4 ti,
         unsigned char *st = wsm + s * L.stage;
         if (lane < REC_CHUNKS)
             cp_async16(st + 16 * lane, reinterpret_cast<const char *>(A.geo + c) + 16 * lane);
-        copy_row_own<T>(reinterpret_cast<V4<T> *>(st + sizeof(CellGeo<T>)), A.q + (size_t)c * A.G, lane, A.G);
+        copy_row_own<T, NPL>(reinterpret_cast<V4<T> *>(st + sizeof(CellGeo<T>)), A.q + (size_t)c * A.G, lane, A.G);
         uint32_t r = 0;
 #pragma unroll
         for (int f = 0; f < 4; ++f) {
             if (!((mask >> f) & 1u) || nb[f] < 0) continue;
             if (!((ak >> r) & 1u))  // not handed over by the lanes: copy this lane's entries of the row
-                copy_row_own<T>(reinterpret_cast<V4<T> *>(st + sizeof(CellGeo<T>) + (1u + r) * L.row),
-                                A.psi + (psi_dir + (size_t)nb[f]) * A.G, lane, A.G);
+                copy_row_own<T, NPL>(reinterpret_cast<V4<T> *>(st + sizeof(CellGeo<T>) + (1u + r) * L.row),
+                                     A.psi + (psi_dir + (size_t)nb[f]) * A.G, lane, A.G);
             ++r;
         }
         cp_async_commit();
