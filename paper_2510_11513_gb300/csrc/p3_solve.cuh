@@ -13,11 +13,13 @@
 // not fit one thread's registers, so four lanes share a unit: lane s of the four holds rows
 // 4 r + s (r = 0..4) of the matrix and right-hand side in registers; the four are lanes
 // u, u + 8, u + 16, u + 24 of the warp (unit u = 0..7), so that the eight lanes holding row k
-// form one quarter of the warp.  At step k they write the eight pivot rows to shared memory
-// (one wavefront per 16-byte store) and every lane reads its unit's row back (Gaussian elimination
+// form one quarter of the warp.  The elimination takes two columns per step: the lanes holding
+// rows k and k + 1 write them to shared memory (one wavefront per 16-byte store), every lane
+// reads its unit's two rows back and reduces row k + 1 by row k itself (Gaussian elimination
 // without pivoting: the symmetric part, (1/2) sum_f |Omega.N_f| F_f + sigma_t V M, is
 // positive definite); the back substitution runs by columns, each unknown broadcast inside
-// the four.  A warp solves eight groups of one cell at a time.
+// the four.  A warp solves eight groups of one cell at a time (a pass); the next pass's source
+// values are copied into shared memory while the current pass computes.
 #pragma once
 
 template <class T> struct alignas(16) P3Geo {
